@@ -1,0 +1,245 @@
+/*
+ * nc24 - per-token CDF step of a neural lossless text compressor, as a C ABI.
+ *
+ * The compressor follows arXiv 2602.19626 ("Nacrith"), Algorithm 1: for each
+ * token a decoder-only transformer predicts the next-token distribution
+ * (Sec. 3.2, Eq. lm), an adaptive log-space bias corrects it (Sec. 3.6), it is
+ * mixed linearly with an online token N-gram (Sec. 3.4, Sec. 3.5), quantised
+ * to an integer CDF totalling 2^24 with a floor per symbol (Sec. 3.3), and
+ * coded by a 32-bit arithmetic coder (Sec. 3.8) that runs on the host.
+ *
+ * Conventions for every entry point:
+ *  - Every call returns nc_status; no exception or signal crosses the ABI.
+ *  - The caller owns every buffer it passes; the library never frees or keeps
+ *    caller memory beyond the call.  The library owns all device state of a
+ *    context and releases it in nc_ctx_destroy.
+ *  - "host" pointers are ordinary (pageable or pinned) CPU memory; "device"
+ *    pointers are CUDA global memory on the context's device.  Entry points
+ *    that accept either say so and detect the kind with cudaPointerGetAttributes.
+ *  - A context is not thread-safe; use one context per host thread.
+ *  - After NC_ECUDA or NC_ETIMEOUT the context is poisoned: every later call
+ *    except nc_ctx_destroy / nc_last_error returns NC_ESTATE.
+ *  - Work is ordered on the context's CUDA stream (nc_config.cuda_stream, or
+ *    a stream the library creates when it is NULL); calls that return host
+ *    data synchronise that stream before returning.
+ */
+#ifndef NC24_H
+#define NC24_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct nc_ctx nc_ctx;
+
+typedef enum {
+  NC_OK = 0,
+  NC_EINVAL = 1,    /* bad argument (null pointer, size out of range, unknown stream) */
+  NC_ENOMEM = 2,    /* device or host allocation failed */
+  NC_ECUDA = 3,     /* a CUDA call failed; context poisoned */
+  NC_ETIMEOUT = 4,  /* a bounded device wait gave up; context poisoned */
+  NC_ECORRUPT = 5,  /* container bytes are malformed or do not match the context */
+  NC_ESTATE = 6,    /* call out of order (e.g. step twice without update) or poisoned ctx */
+  NC_ENUMERIC = 7   /* non-finite probabilities, or the CDF residual underflows a floor */
+} nc_status;
+
+/* Weight storage formats.  Weights are always handed in as FP32 and
+ * converted on the device: BF16 by round-to-nearest-even; FP8 E4M3 with one
+ * FP32 scale per output channel, scale = amax/448, q = e4m3_rn(w/scale). */
+enum { NC_FP32 = 0, NC_BF16 = 1, NC_FP8E4M3 = 2 };
+
+/* Update rule after each coded token.
+ *  NC_RULE_PAPER:     b -= alpha (p_tilde - e_t*)  (Sec. 3.6) and exponential
+ *                     weights on the mixer, log w_j += eta log p_j(t*) (Sec. 3.5).
+ *  NC_RULE_MIXED_NLL: one SGD step (rate alpha) of -log p_mix(t*) with respect
+ *                     to b and the mixer log-weights. */
+enum { NC_RULE_PAPER = 0, NC_RULE_MIXED_NLL = 1 };
+
+/* Numeric path of the dense projections.  Encoder and decoder must use the
+ * same path; the container records it.
+ *  NC_PATH_GEMV: CUDA-core weight streaming, FP32 activations.
+ *  NC_PATH_TC:   tcgen05 tensor-core GEMMs over the batch of streams, BF16
+ *                activations (FP8 activations for NC_FP8E4M3), FP32 accumulation. */
+enum { NC_PATH_GEMV = 0, NC_PATH_TC = 1 };
+
+typedef struct {
+  /* model shape (Sec. 3.2): 30, 576, 9, 3, 1536, 49152 for SmolLM2-135M */
+  int n_layers, d_model, n_heads, n_kv_heads, d_ffn, vocab;
+  float rope_theta, rms_eps;        /* 1e5, 1e-5 */
+  int ctx_len, slide;               /* KV window L and drop count C (Sec. 3.9): 2048, 512 */
+  int ngram_order;                  /* 0..3; 0 disables the N-gram and the mix (Sec. 3.4) */
+  int use_head;                     /* 1 enables the adaptive bias head (Sec. 3.6) */
+  int cdf_log2_total;               /* log2 T, 24 (Sec. 3.3); 16..24 */
+  uint32_t floor;                   /* per-symbol minimum count, 1 */
+  float bias_lr;                    /* alpha, 1e-3 (Sec. 3.6) */
+  float mix_eta;                    /* eta of the exponential weights, 1 (Sec. 3.5) */
+  float w_llm_init;                 /* 0.85 (Sec. 3.5) */
+  float temperature;                /* tau, 1.0 (Sec. 3.2) */
+  int warmup;                       /* tokens coded with the LLM alone, 100 (Sec. 3.5) */
+  int weight_fmt;                   /* NC_FP32 | NC_BF16 | NC_FP8E4M3 */
+  int update_rule;                  /* NC_RULE_PAPER | NC_RULE_MIXED_NLL */
+  int path;                         /* NC_PATH_GEMV | NC_PATH_TC */
+  int max_streams;                  /* stream slots; also the largest batch of one step */
+  int device;                       /* CUDA device ordinal */
+  void* cuda_stream;                /* cudaStream_t to order work on, or NULL */
+} nc_config;
+
+/* Fill *cfg with the SmolLM2-135M shape and the paper's defaults
+ * (BF16 weights, paper rule, GEMV path, 1 stream, device 0). */
+void nc_config_default(nc_config* cfg);
+
+/* Create a context.  `weights` is a HOST buffer of nbytes = 4 * n_params FP32
+ * values in this order: embedding [V, d]; per layer attn_norm [d],
+ * wq [Hq*64, d], wk [Hkv*64, d], wv [Hkv*64, d], wo [d, Hq*64], ffn_norm [d],
+ * w_gate [F, d], w_up [F, d], w_down [d, F]; final_norm [d].  Matrices are
+ * [out, in] row-major; the LM head is tied to the embedding (Eq. lm without
+ * an output bias).  The library copies and converts the weights; the caller
+ * may free them on return.  Requires d_model and d_ffn multiples of 16,
+ * d_model / n_heads == 64, n_heads a multiple of n_kv_heads, vocab < 65536,
+ * ctx_len a power of two > slide > 0.  Errors: NC_EINVAL, NC_ENOMEM, NC_ECUDA. */
+int nc_ctx_create(const nc_config* cfg, const void* weights, size_t nbytes, nc_ctx** out);
+
+/* Release every device and host resource of the context (NULL is a no-op). */
+void nc_ctx_destroy(nc_ctx* ctx);
+
+/* Start a stream in a free slot with fresh state (empty KV window, b = 0,
+ * w = (w_llm_init, 1 - w_llm_init), empty N-gram).  expected_len bounds the
+ * number of tokens the stream will code (it sizes the N-gram tables, Sec. 3.4);
+ * coding more returns NC_ESTATE.  stream_id is any non-negative caller key.
+ * Errors: NC_EINVAL (id in use, no free slot, expected_len < 1), NC_ENOMEM. */
+int nc_stream_open(nc_ctx* ctx, int32_t stream_id, int64_t expected_len);
+
+/* Free a stream's slot and its N-gram tables.  Errors: NC_EINVAL (unknown id). */
+int nc_stream_close(nc_ctx* ctx, int32_t stream_id);
+
+/* One model step for n open streams (Algorithm 1, the body of the loop up to
+ * probs_to_cdf): feeds each stream's previous token (BOS id 0 first), runs the
+ * transformer with its KV window, the biased softmax, the N-gram and the mix,
+ * and quantises to the integer CDF.
+ *   stream_ids  HOST int32[n], distinct open streams.
+ *   prev_tokens HOST int32[n] or NULL: the token each stream feeds; must equal
+ *               the stream's last observed token (-1 for a fresh stream), it is
+ *               a consistency check only.
+ *   cdf_out     HOST or DEVICE uint32[n * (V + 1)] or NULL: row j receives
+ *               stream j's CDF, cdf[0] = 0, cdf[V] = 2^cdf_log2_total.  NULL
+ *               keeps the CDFs on the device for nc_update_bias.
+ * Each stream must then be given its observed token by nc_update_bias before
+ * its next step (else NC_ESTATE).  Errors: NC_EINVAL, NC_ESTATE, NC_ENUMERIC,
+ * NC_ECUDA. */
+int nc_step_cdf(nc_ctx* ctx, int n, const int32_t* stream_ids, const int32_t* prev_tokens,
+                uint32_t* cdf_out);
+
+/* Apply the updates after coding (Algorithm 1, "Update: N-gram, Mixer,
+ * AdaptiveHead with t_i"): bias head and mixer by the configured rule, then
+ * the N-gram counts, for n streams that have just stepped.
+ *   stream_ids HOST int32[n]; observed HOST int32[n], tokens in [0, V).
+ * Errors: NC_EINVAL, NC_ESTATE, NC_ECUDA. */
+int nc_update_bias(nc_ctx* ctx, int n, const int32_t* stream_ids, const int32_t* observed);
+
+/* Whole-stream compression into an NC05-style container (Sec. 3.12):
+ * 9-byte header (magic "NC05", flags, tau as binary16, stream count), one
+ * extension byte (weight format | path << 4), 12 bytes per stream (token
+ * count, bit count, byte count, little-endian uint32), then the coded streams.
+ *   tokens HOST array of n_streams HOST int32 pointers; lens HOST int64[n_streams].
+ *   out    HOST buffer or NULL; *inout_nbytes holds its capacity on entry and
+ *          the container size on return.  out == NULL only queries an upper
+ *          bound of the size (no coding).
+ * Streams are coded in one batch (at most max_streams), each in a fresh slot
+ * that is closed again before return.  Errors: NC_EINVAL (too many streams,
+ * buffer too small: *inout_nbytes then holds the size needed), NC_ENOMEM,
+ * NC_ENUMERIC, NC_ECUDA. */
+int nc_encode(nc_ctx* ctx, int n_streams, const int32_t* const* tokens, const int64_t* lens,
+              uint8_t* out, size_t* inout_nbytes);
+
+/* Mirror of nc_encode.  tokens_out: HOST array of HOST int32 pointers, one
+ * per stream, each with room for that stream's token count; lens_out HOST
+ * int64[stream count].  A NULL tokens_out only reads the header: lens_out
+ * then receives the token counts (query).  Errors: NC_ECORRUPT (bad magic,
+ * truncated or inconsistent table, flags / tau / path differ from the
+ * context), NC_EINVAL, NC_ENOMEM, NC_ECUDA. */
+int nc_decode(nc_ctx* ctx, const uint8_t* in, size_t nbytes, int32_t* const* tokens_out,
+              int64_t* lens_out);
+
+/* Stream count recorded in a container header (HOST bytes), or NC_ECORRUPT. */
+int nc_container_streams(const uint8_t* in, size_t nbytes, int* n_streams);
+
+const char* nc_status_str(int status);
+/* Message of the last failing call on ctx (never NULL). */
+const char* nc_last_error(const nc_ctx* ctx);
+
+/* ---------------------------------------------------------------------------
+ * Building blocks, exposed for parity tests and for callers that drive the
+ * coder themselves.
+ * ------------------------------------------------------------------------- */
+
+/* CDF quantisation (Sec. 3.3) of n rows of V binary32 probabilities:
+ * c_i = max(floor, floor(p_i * (T - V*floor))) with the product taken
+ * exactly, the residual T - sum c added to the first maximum of p, then the
+ * exclusive prefix sum, cdf[0] = 0, cdf[V] = T.  p DEVICE float[n * V],
+ * cdf DEVICE uint32[n * (V + 1)], stream a cudaStream_t or NULL (legacy
+ * default stream).  Returns NC_ENUMERIC when a row holds a non-finite or
+ * negative value, a value >= 2, or the residual would leave the argmax count
+ * below the floor (that row's cdf is then unspecified); NC_EINVAL for bad
+ * sizes.  Synchronises the stream. */
+int nc_probs_to_cdf(const float* p, int n, int V, int log2_total, uint32_t floor,
+                    uint32_t* cdf, void* stream);
+
+/* Elementwise exact product floor, c[i] = max(floor, floor(p[i] * K)), for
+ * binary32 p[i] in [0, 2) and 0 < K < 2^24 (the quantiser's inner step,
+ * Sec. 3.3).  p DEVICE float[n], c DEVICE uint32[n]; entries outside [0, 2)
+ * give 0xFFFFFFFF.  Asynchronous on `stream`. */
+int nc_floor_counts(const float* p, int64_t n, uint32_t K, uint32_t floor, uint32_t* c,
+                    void* stream);
+
+/* One model step like nc_step_cdf that also returns the intermediate
+ * distributions of every stream (DEVICE float[n * V] each, any may be NULL):
+ * z the logits (Eq. lm), p_tilde the biased LLM distribution (Sec. 3.6),
+ * p_ng the N-gram distribution (Sec. 3.4), p the mixed binary32 probabilities
+ * handed to the quantiser; cdf_out as in nc_step_cdf. */
+int nc_step_probe(nc_ctx* ctx, int n, const int32_t* stream_ids, float* z, float* p_tilde,
+                  float* p_ng, float* p, uint32_t* cdf_out);
+
+/* Copy a stream's adaptive state to HOST buffers (any may be NULL): bias
+ * float[V] (Sec. 3.6), mixer log-weights float[2] (Sec. 3.5), tokens coded. */
+int nc_stream_state(nc_ctx* ctx, int32_t stream_id, float* bias, float* mix_logw,
+                    int64_t* n_coded);
+
+/* 32-bit arithmetic coder (Sec. 3.8) on the host, for callers that produce
+ * their own CDFs.  Encode n intervals [lo[i], hi[i]) of a total 2^log2_total
+ * (HOST uint32 arrays) into out (HOST, capacity *inout_nbytes; size and the
+ * exact bit count returned).  Errors: NC_EINVAL (empty or out-of-range
+ * interval, buffer too small: *inout_nbytes then holds the size needed). */
+int nc_ac_encode(const uint32_t* lo, const uint32_t* hi, int64_t n, int log2_total,
+                 uint8_t* out, size_t* inout_nbytes, uint64_t* nbits);
+
+/* Decode n symbols with one CDF per symbol: cdfs HOST uint32[n * (V + 1)],
+ * bits HOST (nbits valid bits, zeros read past the end), symbols HOST int32[n].
+ * Errors: NC_EINVAL, NC_ECORRUPT (a CDF that is not a valid CDF). */
+int nc_ac_decode(const uint8_t* bits, uint64_t nbits, const uint32_t* cdfs, int V, int64_t n,
+                 int log2_total, int32_t* symbols);
+
+/* Mixed-distribution NLL L = -log(w0 p_tilde(t*) + w1 p_ng(t*)), w = softmax(theta),
+ * p_tilde = softmax(z / tau + b), for n rows (the differentiable update rule).
+ *   z, b, p_ng DEVICE float[n * V]; theta DEVICE float[n * 2]; target DEVICE int32[n];
+ *   warm DEVICE int32[n] (non-zero: p = p_tilde, the warm-up case);
+ *   loss DEVICE float[n].  Asynchronous on `stream`. */
+int nc_mix_nll_fwd(const float* z, const float* b, const float* p_ng, const float* theta,
+                   const int32_t* target, const int32_t* warm, int n, int V, float tau,
+                   float* loss, void* stream);
+
+/* Gradient of nc_mix_nll_fwd's loss scaled by gout (DEVICE float[n], NULL = 1):
+ * db DEVICE float[n * V] = gout * rho * (p_tilde - e_t*), rho = w0 p_tilde(t*)/p_mix(t*)
+ * (1 in warm-up); dtheta DEVICE float[n * 2] = gout * (w - w * p_j(t*)/p_mix(t*))
+ * (0 in warm-up).  Deterministic (no atomics).  Asynchronous on `stream`. */
+int nc_mix_nll_bwd(const float* z, const float* b, const float* p_ng, const float* theta,
+                   const int32_t* target, const int32_t* warm, const float* gout, int n, int V,
+                   float tau, float* db, float* dtheta, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NC24_H */

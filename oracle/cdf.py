@@ -31,6 +31,12 @@ def k_bins(T: int, V: int, floor: int = 1) -> int:
     return T - V * floor
 
 
+def floor_counts(p32, K: int, floor: int = 1) -> np.ndarray:
+    """max(floor, floor(p * K)) elementwise for binary32 p in [0, 2)."""
+    p = np.asarray(p32, dtype=np.float32)
+    return np.maximum(np.floor(p.astype(np.float64) * float(K)), floor).astype(np.int64)
+
+
 def probs_to_counts(p32, T: int = 1 << 24, floor: int = 1) -> np.ndarray:
     p = np.asarray(p32, dtype=np.float32)
     if not np.all(np.isfinite(p)):
@@ -39,8 +45,7 @@ def probs_to_counts(p32, T: int = 1 << 24, floor: int = 1) -> np.ndarray:
     K = k_bins(T, V, floor)
     if K <= 0:
         raise QuantiseError("total too small for the floors")
-    prod = p.astype(np.float64) * float(K)      # exact: <= 48 significant bits
-    c = np.maximum(np.floor(prod).astype(np.int64), floor)
+    c = floor_counts(p, K, floor)               # exact: <= 48 significant bits
     j = int(np.argmax(p))                       # numpy argmax: first maximum
     r = T - int(c.sum())
     if c[j] + r < floor:

@@ -1,0 +1,186 @@
+// Host arithmetic coder and container (Sec. 3.8, Sec. 3.12).
+#include "coder.h"
+
+#include <cmath>
+#include <cstring>
+
+namespace nc {
+
+namespace {
+constexpr uint64_t kHalf = 1ull << 31;
+constexpr uint64_t kQtr = 1ull << 30;
+}  // namespace
+
+bool AcEncoder::encode(uint32_t lo, uint32_t hi) {
+  const uint64_t T = 1ull << log2T_;
+  if (lo >= hi || hi > T) return false;
+  const uint64_t R = high_ - low_ + 1;
+  high_ = low_ + ((R * hi) >> log2T_) - 1;
+  low_ = low_ + ((R * lo) >> log2T_);
+  for (;;) {
+    if (high_ < kHalf) {
+      emit(0);
+    } else if (low_ >= kHalf) {
+      emit(1);
+      low_ -= kHalf;
+      high_ -= kHalf;
+    } else if (low_ >= kQtr && high_ < 3 * kQtr) {
+      ++pending_;
+      low_ -= kQtr;
+      high_ -= kQtr;
+    } else {
+      break;
+    }
+    low_ <<= 1;
+    high_ = (high_ << 1) | 1;
+  }
+  return true;
+}
+
+void AcEncoder::finish() {
+  ++pending_;
+  emit(low_ < kQtr ? 0 : 1);
+}
+
+AcDecoder::AcDecoder(const uint8_t* bits, uint64_t nbits, int log2T)
+    : bits_(bits), nbits_(nbits), log2T_(log2T) {
+  for (int i = 0; i < 32; ++i) value_ = (value_ << 1) | (uint64_t)bit();
+}
+
+uint32_t AcDecoder::target() const {
+  const uint64_t R = high_ - low_ + 1;
+  return (uint32_t)((((value_ - low_ + 1) << log2T_) - 1) / R);
+}
+
+void AcDecoder::consume(uint32_t lo, uint32_t hi) {
+  const uint64_t R = high_ - low_ + 1;
+  high_ = low_ + ((R * hi) >> log2T_) - 1;
+  low_ = low_ + ((R * lo) >> log2T_);
+  for (;;) {
+    if (high_ < kHalf) {
+    } else if (low_ >= kHalf) {
+      low_ -= kHalf;
+      high_ -= kHalf;
+      value_ -= kHalf;
+    } else if (low_ >= kQtr && high_ < 3 * kQtr) {
+      low_ -= kQtr;
+      high_ -= kQtr;
+      value_ -= kQtr;
+    } else {
+      break;
+    }
+    low_ <<= 1;
+    high_ = (high_ << 1) | 1;
+    value_ = (value_ << 1) | (uint64_t)bit();
+  }
+}
+
+// IEEE binary16 conversion, round to nearest even (for the 2-byte tau field).
+uint16_t float_to_half_bits(float f) {
+  uint32_t x;
+  std::memcpy(&x, &f, 4);
+  const uint32_t sign = (x >> 16) & 0x8000u;
+  const int32_t exp = (int32_t)((x >> 23) & 0xFF) - 127 + 15;
+  uint32_t mant = x & 0x7FFFFFu;
+  if (((x >> 23) & 0xFF) == 0xFF) return (uint16_t)(sign | 0x7C00u | (mant ? 0x200u : 0));
+  if (exp >= 31) return (uint16_t)(sign | 0x7C00u);
+  if (exp <= 0) {
+    if (exp < -10) return (uint16_t)sign;
+    mant |= 0x800000u;
+    const int shift = 14 - exp;
+    uint32_t hm = mant >> shift;
+    const uint32_t rem = mant & ((1u << shift) - 1), halfway = 1u << (shift - 1);
+    if (rem > halfway || (rem == halfway && (hm & 1))) ++hm;
+    return (uint16_t)(sign | hm);
+  }
+  uint32_t h = sign | ((uint32_t)exp << 10) | (mant >> 13);
+  const uint32_t rem = mant & 0x1FFFu;
+  if (rem > 0x1000u || (rem == 0x1000u && (h & 1))) ++h;
+  return (uint16_t)h;
+}
+
+float half_bits_to_float(uint16_t h) {
+  const uint32_t sign = (uint32_t)(h & 0x8000u) << 16;
+  const int exp = (h >> 10) & 0x1F;
+  const uint32_t mant = h & 0x3FFu;
+  float f;
+  if (exp == 0) {
+    f = std::ldexp((float)mant, -24);
+    if (sign) f = -f;
+    return f;
+  }
+  uint32_t x;
+  if (exp == 31)
+    x = sign | 0x7F800000u | (mant << 13);
+  else
+    x = sign | ((uint32_t)(exp - 15 + 127) << 23) | (mant << 13);
+  std::memcpy(&f, &x, 4);
+  return f;
+}
+
+static void put_u16(uint8_t* p, uint16_t v) {
+  p[0] = (uint8_t)v;
+  p[1] = (uint8_t)(v >> 8);
+}
+static void put_u32(uint8_t* p, uint32_t v) {
+  for (int i = 0; i < 4; ++i) p[i] = (uint8_t)(v >> (8 * i));
+}
+static uint16_t get_u16(const uint8_t* p) { return (uint16_t)(p[0] | (p[1] << 8)); }
+static uint32_t get_u32(const uint8_t* p) {
+  return (uint32_t)p[0] | ((uint32_t)p[1] << 8) | ((uint32_t)p[2] << 16) | ((uint32_t)p[3] << 24);
+}
+
+size_t container_size(const std::vector<StreamRecord>& recs) {
+  size_t n = kHeaderBytes + 1 + kRecordBytes * recs.size();
+  for (const auto& r : recs) n += r.nbytes;
+  return n;
+}
+
+void container_write(uint8_t* out, uint8_t flags, float tau, uint8_t path_byte,
+                     const std::vector<StreamRecord>& recs,
+                     const std::vector<const std::vector<uint8_t>*>& payloads) {
+  std::memcpy(out, "NC05", 4);
+  out[4] = flags;
+  put_u16(out + 5, float_to_half_bits(tau));
+  put_u16(out + 7, (uint16_t)recs.size());
+  out[9] = path_byte;
+  uint8_t* p = out + kHeaderBytes + 1;
+  for (const auto& r : recs) {
+    put_u32(p, r.ntok);
+    put_u32(p + 4, r.nbits);
+    put_u32(p + 8, r.nbytes);
+    p += kRecordBytes;
+  }
+  for (size_t i = 0; i < recs.size(); ++i) {
+    if (recs[i].nbytes) std::memcpy(p, payloads[i]->data(), recs[i].nbytes);
+    p += recs[i].nbytes;
+  }
+}
+
+bool container_read(const uint8_t* in, size_t n, uint8_t* flags, float* tau, uint8_t* path_byte,
+                    std::vector<StreamRecord>* recs, std::vector<const uint8_t*>* payloads) {
+  if (!in || n < kHeaderBytes + 1 || std::memcmp(in, "NC05", 4) != 0) return false;
+  *flags = in[4];
+  *tau = half_bits_to_float(get_u16(in + 5));
+  const size_t ns = get_u16(in + 7);
+  *path_byte = in[9];
+  size_t off = kHeaderBytes + 1;
+  if (n < off + kRecordBytes * ns) return false;
+  recs->resize(ns);
+  for (size_t j = 0; j < ns; ++j) {
+    (*recs)[j].ntok = get_u32(in + off);
+    (*recs)[j].nbits = get_u32(in + off + 4);
+    (*recs)[j].nbytes = get_u32(in + off + 8);
+    off += kRecordBytes;
+  }
+  payloads->resize(ns);
+  for (size_t j = 0; j < ns; ++j) {
+    const auto& r = (*recs)[j];
+    if ((uint64_t)r.nbytes != ((uint64_t)r.nbits + 7) / 8 || off + r.nbytes > n) return false;
+    (*payloads)[j] = in + off;
+    off += r.nbytes;
+  }
+  return off == n;
+}
+
+}  // namespace nc

@@ -1,0 +1,82 @@
+// Host 32-bit arithmetic coder (Sec. 3.8, after Witten, Neal and Cleary 1987)
+// and the NC05-style container (Sec. 3.12).
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <vector>
+
+namespace nc {
+
+// Encoder state: low, high in [0, 2^32) with high inclusive.  For an interval
+// [lo, hi) of a total T = 2^log2T the range R = high - low + 1 narrows to
+// high = low + floor(R hi / T) - 1, low += floor(R lo / T); renormalisation
+// emits equal leading bits (plus pending opposite bits) and counts a pending
+// bit while the range straddles the middle half.  After renormalisation
+// R > 2^30, so every count >= 1 keeps a non-empty sub-interval.
+class AcEncoder {
+ public:
+  explicit AcEncoder(int log2T) : log2T_(log2T) {}
+  // false for an empty or out-of-range interval
+  bool encode(uint32_t lo, uint32_t hi);
+  void finish();
+  const std::vector<uint8_t>& bytes() const { return out_; }
+  uint64_t nbits() const { return nbits_; }
+
+ private:
+  void put(int b) {
+    if ((nbits_ & 7) == 0) out_.push_back(0);
+    if (b) out_.back() |= (uint8_t)(0x80u >> (nbits_ & 7));
+    ++nbits_;
+  }
+  void emit(int b) {
+    put(b);
+    for (; pending_; --pending_) put(!b);
+  }
+  int log2T_;
+  uint64_t low_ = 0, high_ = 0xFFFFFFFFull, pending_ = 0, nbits_ = 0;
+  std::vector<uint8_t> out_;
+};
+
+class AcDecoder {
+ public:
+  AcDecoder(const uint8_t* bits, uint64_t nbits, int log2T);
+  // the count in [0, T) that selects the next symbol
+  uint32_t target() const;
+  // consume the decoded symbol's interval [lo, hi)
+  void consume(uint32_t lo, uint32_t hi);
+
+ private:
+  int bit() {
+    const uint64_t i = pos_++;
+    if (i >= nbits_) return 0;
+    return (bits_[i >> 3] >> (7 - (i & 7))) & 1;
+  }
+  const uint8_t* bits_;
+  uint64_t nbits_, pos_ = 0;
+  int log2T_;
+  uint64_t low_ = 0, high_ = 0xFFFFFFFFull, value_ = 0;
+};
+
+// Container: "NC05", flags, tau (binary16), stream count, extension byte
+// (weight format | path << 4), then per stream (tokens, bits, bytes) as
+// little-endian uint32, then the payloads.
+constexpr size_t kHeaderBytes = 9;
+constexpr size_t kRecordBytes = 12;
+
+struct StreamRecord {
+  uint32_t ntok, nbits, nbytes;
+};
+
+uint16_t float_to_half_bits(float f);
+float half_bits_to_float(uint16_t h);
+
+size_t container_size(const std::vector<StreamRecord>& recs);
+void container_write(uint8_t* out, uint8_t flags, float tau, uint8_t path_byte,
+                     const std::vector<StreamRecord>& recs,
+                     const std::vector<const std::vector<uint8_t>*>& payloads);
+// false on malformed input
+bool container_read(const uint8_t* in, size_t n, uint8_t* flags, float* tau, uint8_t* path_byte,
+                    std::vector<StreamRecord>* recs, std::vector<const uint8_t*>* payloads);
+
+}  // namespace nc

@@ -1,0 +1,1061 @@
+// Host side of the nc24 C ABI: context, stream slots, the per-step launch
+// sequence (Algorithm 1's loop body), whole-stream encode / decode, and the
+// building-block entry points.  See include/nc24.h for the contract.
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "coder.h"
+#include "internal.h"
+
+using namespace nc;
+
+namespace {
+
+struct Slot {
+  bool open = false;
+  bool awaiting_update = false;
+  int32_t id = -1;
+  int64_t n_coded = 0;
+  int32_t last_tok = -1;
+  int64_t max_len = 0;
+  // device buffers owned by the slot (kept across reopen when large enough)
+  void* kv = nullptr;
+  float* bias = nullptr;
+  int32_t* uni = nullptr;
+  float* z = nullptr;
+  unsigned long long* keys[3] = {nullptr, nullptr, nullptr};
+  int32_t* idx[3] = {nullptr, nullptr, nullptr};
+  NgEntry* ent[3] = {nullptr, nullptr, nullptr};
+  int64_t cap_len = 0;       // tokens the N-gram buffers can hold
+  int64_t cap_hash = 0;      // hash index capacity (power of two)
+};
+
+}  // namespace
+
+struct nc_ctx {
+  nc_config cfg{};
+  Dims D{};
+  int fmt = NC_BF16;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  bool poisoned = false;
+  std::string err = "ok";
+  std::vector<void*> allocs;   // weight buffers
+
+  // weights
+  const void* embed = nullptr;
+  const float* embed_scale = nullptr;
+  std::vector<LayerW> layers;
+  const float* g_final = nullptr;
+
+  // activations for up to max_streams rows
+  float* x = nullptr;
+  float* qkv = nullptr;
+  float* part = nullptr;
+  float* h = nullptr;
+  uint32_t* cdf = nullptr;
+  int32_t* d_slots = nullptr;
+  int32_t* d_nB = nullptr;
+  int32_t* d_obs = nullptr;
+  uint32_t* d_target = nullptr;
+  uint32_t* d_lohi = nullptr;
+  int32_t* d_status = nullptr;       // scratch status for building blocks
+  // pinned host staging
+  int32_t* h_i32 = nullptr;          // 3 * max_streams + 1
+  uint32_t* h_u32 = nullptr;         // 3 * max_streams: targets, then (lo, hi) pairs
+  int32_t* h_status = nullptr;       // max_streams
+
+  StreamDev* d_st = nullptr;
+  std::vector<StreamDev> h_st;
+  std::vector<Slot> slots;
+  std::unordered_map<int32_t, int> id2slot;
+};
+
+#define NC_TRY(call)                                                               \
+  do {                                                                             \
+    cudaError_t e_ = (call);                                                       \
+    if (e_ != cudaSuccess) return fail_cuda(ctx, e_, #call);                       \
+  } while (0)
+
+static int fail(nc_ctx* ctx, int st, const std::string& msg) {
+  if (ctx) ctx->err = msg;
+  return st;
+}
+static int fail_cuda(nc_ctx* ctx, cudaError_t e, const char* what) {
+  if (ctx) {
+    ctx->err = std::string("CUDA error in ") + what + ": " + cudaGetErrorString(e);
+    if (e == cudaErrorMemoryAllocation) {
+      cudaGetLastError();
+      return NC_ENOMEM;
+    }
+    ctx->poisoned = true;
+  }
+  return NC_ECUDA;
+}
+
+static bool is_device_ptr(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+static int64_t next_pow2(int64_t v) {
+  int64_t p = 1;
+  while (p < v) p <<= 1;
+  return p;
+}
+
+extern "C" void nc_config_default(nc_config* c) {
+  if (!c) return;
+  std::memset(c, 0, sizeof(*c));
+  c->n_layers = 30;
+  c->d_model = 576;
+  c->n_heads = 9;
+  c->n_kv_heads = 3;
+  c->d_ffn = 1536;
+  c->vocab = 49152;
+  c->rope_theta = 1e5f;
+  c->rms_eps = 1e-5f;
+  c->ctx_len = 2048;
+  c->slide = 512;
+  c->ngram_order = 3;
+  c->use_head = 1;
+  c->cdf_log2_total = 24;
+  c->floor = 1;
+  c->bias_lr = 1e-3f;
+  c->mix_eta = 1.0f;
+  c->w_llm_init = 0.85f;
+  c->temperature = 1.0f;
+  c->warmup = 100;
+  c->weight_fmt = NC_BF16;
+  c->update_rule = NC_RULE_PAPER;
+  c->path = NC_PATH_GEMV;
+  c->max_streams = 1;
+  c->device = 0;
+  c->cuda_stream = nullptr;
+}
+
+extern "C" const char* nc_status_str(int s) {
+  switch (s) {
+    case NC_OK: return "NC_OK";
+    case NC_EINVAL: return "NC_EINVAL";
+    case NC_ENOMEM: return "NC_ENOMEM";
+    case NC_ECUDA: return "NC_ECUDA";
+    case NC_ETIMEOUT: return "NC_ETIMEOUT";
+    case NC_ECORRUPT: return "NC_ECORRUPT";
+    case NC_ESTATE: return "NC_ESTATE";
+    case NC_ENUMERIC: return "NC_ENUMERIC";
+  }
+  return "NC_UNKNOWN";
+}
+
+extern "C" const char* nc_last_error(const nc_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+static std::string validate(const nc_config& c) {
+  if (c.n_layers < 1 || c.d_model < 16 || c.d_model % 16) return "d_model must be a positive multiple of 16";
+  if (c.n_heads < 1 || c.d_model != c.n_heads * kHeadDim) return "d_model / n_heads must be 64";
+  if (c.n_kv_heads < 1 || c.n_heads % c.n_kv_heads || c.n_heads / c.n_kv_heads > kMaxGroup)
+    return "n_heads must be a multiple of n_kv_heads (at most 4 per KV head)";
+  if (c.d_ffn < 16 || c.d_ffn % 16) return "d_ffn must be a positive multiple of 16";
+  if (c.vocab < 2 || c.vocab > 65535) return "vocab must be in [2, 65535]";
+  if (c.ctx_len < 2 || (c.ctx_len & (c.ctx_len - 1)) || c.slide < 1 || c.slide >= c.ctx_len)
+    return "ctx_len must be a power of two > slide > 0";
+  if (c.ngram_order < 0 || c.ngram_order > kMaxOrder) return "ngram_order must be 0..3";
+  if (c.cdf_log2_total < 16 || c.cdf_log2_total > 24) return "cdf_log2_total must be 16..24";
+  if (c.floor < 1 || (uint64_t)c.vocab * c.floor >= (1ull << c.cdf_log2_total))
+    return "floor * vocab must stay below the CDF total";
+  if (!(c.temperature > 0.f)) return "temperature must be positive";
+  if (c.w_llm_init <= 0.f || c.w_llm_init >= 1.f) return "w_llm_init must be in (0, 1)";
+  if (c.weight_fmt < NC_FP32 || c.weight_fmt > NC_FP8E4M3) return "unknown weight_fmt";
+  if (c.update_rule != NC_RULE_PAPER && c.update_rule != NC_RULE_MIXED_NLL) return "unknown update_rule";
+  if (c.path != NC_PATH_GEMV) return "only NC_PATH_GEMV is available in this build";
+  if (c.max_streams < 1 || c.max_streams > 4096) return "max_streams must be 1..4096";
+  if (c.warmup < 0) return "warmup must be >= 0";
+  return "";
+}
+
+static size_t n_params(const nc_config& c) {
+  const size_t d = c.d_model, qd = (size_t)c.n_heads * kHeadDim, kvd = (size_t)c.n_kv_heads * kHeadDim;
+  const size_t per = d + qd * d + 2 * kvd * d + d * qd + d + 3 * (size_t)c.d_ffn * d;
+  return (size_t)c.vocab * d + c.n_layers * per + d;
+}
+
+template <typename T>
+static cudaError_t dalloc(nc_ctx* ctx, T** p, size_t bytes) {
+  void* q = nullptr;
+  cudaError_t e = cudaMalloc(&q, bytes ? bytes : 16);
+  if (e == cudaSuccess) {
+    ctx->allocs.push_back(q);
+    *p = static_cast<T*>(q);
+  }
+  return e;
+}
+
+static size_t fmt_bytes(int fmt) { return fmt == NC_FP32 ? 4 : fmt == NC_BF16 ? 2 : 1; }
+
+// Convert one [rows][cols] FP32 device matrix into the storage format.
+static int make_mat(nc_ctx* ctx, const float* src, int rows, int cols, Mat* m) {
+  void* w = nullptr;
+  float* sc = nullptr;
+  NC_TRY(dalloc(ctx, &w, (size_t)rows * cols * fmt_bytes(ctx->fmt)));
+  if (ctx->fmt == NC_FP8E4M3) NC_TRY(dalloc(ctx, &sc, (size_t)rows * sizeof(float)));
+  NC_TRY(launch_convert_weights(src, w, sc, rows, cols, ctx->fmt, ctx->stream));
+  m->w = w;
+  m->scale = sc;
+  m->rows = rows;
+  m->cols = cols;
+  return NC_OK;
+}
+
+static void free_slot(Slot& s) {
+  cudaFree(s.kv);
+  cudaFree(s.bias);
+  cudaFree(s.uni);
+  cudaFree(s.z);
+  for (int k = 0; k < 3; ++k) {
+    cudaFree(s.keys[k]);
+    cudaFree(s.idx[k]);
+    cudaFree(s.ent[k]);
+  }
+  s = Slot();
+}
+
+extern "C" void nc_ctx_destroy(nc_ctx* ctx) {
+  if (!ctx) return;
+  cudaSetDevice(ctx->cfg.device);
+  if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  for (auto& s : ctx->slots) free_slot(s);
+  for (void* p : ctx->allocs) cudaFree(p);
+  cudaFreeHost(ctx->h_i32);
+  cudaFreeHost(ctx->h_u32);
+  cudaFreeHost(ctx->h_status);
+  if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
+  delete ctx;
+}
+
+extern "C" int nc_ctx_create(const nc_config* cfg, const void* weights, size_t nbytes, nc_ctx** out) {
+  if (!out) return NC_EINVAL;
+  *out = nullptr;
+  if (!cfg || !weights) return NC_EINVAL;
+  const std::string why = validate(*cfg);
+  if (!why.empty()) return NC_EINVAL;
+  if (nbytes != n_params(*cfg) * sizeof(float)) return NC_EINVAL;
+  nc_ctx* ctx = new (std::nothrow) nc_ctx();
+  if (!ctx) return NC_ENOMEM;
+  ctx->cfg = *cfg;
+  ctx->fmt = cfg->weight_fmt;
+  const nc_config& c = *cfg;
+  auto bail = [&](int st) {
+    nc_ctx_destroy(ctx);
+    return st;
+  };
+  if (cudaSetDevice(c.device) != cudaSuccess) return bail(NC_ECUDA);
+  if (c.cuda_stream) {
+    ctx->stream = static_cast<cudaStream_t>(c.cuda_stream);
+  } else {
+    if (cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking) != cudaSuccess) return bail(NC_ECUDA);
+    ctx->own_stream = true;
+  }
+  Dims& D = ctx->D;
+  D.n_layers = c.n_layers;
+  D.d = c.d_model;
+  D.hq = c.n_heads;
+  D.hkv = c.n_kv_heads;
+  D.F = c.d_ffn;
+  D.V = c.vocab;
+  D.L = c.ctx_len;
+  D.C = c.slide;
+  D.qkv_rows = (c.n_heads + 2 * c.n_kv_heads) * kHeadDim;
+  D.eps = c.rms_eps;
+  D.theta = c.rope_theta;
+  D.tau = c.temperature;
+  D.kv_bf16 = c.weight_fmt != NC_FP32;
+  D.order = c.ngram_order;
+  D.use_head = c.use_head;
+  D.warmup = c.warmup;
+  D.rule = c.update_rule;
+  D.log2T = c.cdf_log2_total;
+  D.floor = c.floor;
+  D.alpha = c.bias_lr;
+  D.eta = c.mix_eta;
+
+  // ---- weights: upload the FP32 buffer once, convert tensor by tensor
+  float* src = nullptr;
+  if (cudaMalloc(&src, nbytes) != cudaSuccess) return bail(NC_ENOMEM);
+  int st = NC_OK;
+  do {
+    if (cudaMemcpy(src, weights, nbytes, cudaMemcpyHostToDevice) != cudaSuccess) {
+      st = NC_ECUDA;
+      break;
+    }
+    const size_t d = D.d, F = D.F;
+    const size_t qd = (size_t)D.hq * kHeadDim;
+    size_t off = 0;
+    Mat emb;
+    if ((st = make_mat(ctx, src + off, D.V, D.d, &emb)) != NC_OK) break;
+    ctx->embed = emb.w;
+    ctx->embed_scale = emb.scale;
+    off += (size_t)D.V * d;
+    float* tmp = nullptr;   // interleaved gate/up in FP32
+    if (dalloc(ctx, &tmp, 2 * F * d * sizeof(float)) != cudaSuccess) {
+      st = NC_ENOMEM;
+      break;
+    }
+    ctx->layers.resize(D.n_layers);
+    for (int l = 0; l < D.n_layers && st == NC_OK; ++l) {
+      LayerW& L = ctx->layers[l];
+      float* g1 = nullptr;
+      float* g2 = nullptr;
+      if (dalloc(ctx, &g1, d * 4) != cudaSuccess || dalloc(ctx, &g2, d * 4) != cudaSuccess) {
+        st = NC_ENOMEM;
+        break;
+      }
+      cudaMemcpyAsync(g1, src + off, d * 4, cudaMemcpyDeviceToDevice, ctx->stream);
+      off += d;
+      // wq, wk, wv are adjacent: together they are the [qkv_rows][d] matrix
+      if ((st = make_mat(ctx, src + off, D.qkv_rows, D.d, &L.qkv)) != NC_OK) break;
+      off += (size_t)D.qkv_rows * d;
+      if ((st = make_mat(ctx, src + off, D.d, (int)qd, &L.o)) != NC_OK) break;
+      off += d * qd;
+      cudaMemcpyAsync(g2, src + off, d * 4, cudaMemcpyDeviceToDevice, ctx->stream);
+      off += d;
+      if (launch_interleave_f32(src + off, src + off + F * d, tmp, F, d, ctx->stream) != cudaSuccess) {
+        st = NC_ECUDA;
+        break;
+      }
+      if ((st = make_mat(ctx, tmp, 2 * D.F, D.d, &L.gu)) != NC_OK) break;
+      off += 2 * F * d;
+      if ((st = make_mat(ctx, src + off, D.d, D.F, &L.down)) != NC_OK) break;
+      off += d * F;
+      L.g_attn = g1;
+      L.g_ffn = g2;
+      cudaStreamSynchronize(ctx->stream);   // tmp is reused by the next layer
+    }
+    if (st != NC_OK) break;
+    float* gf = nullptr;
+    if (dalloc(ctx, &gf, d * 4) != cudaSuccess) {
+      st = NC_ENOMEM;
+      break;
+    }
+    cudaMemcpyAsync(gf, src + off, d * 4, cudaMemcpyDeviceToDevice, ctx->stream);
+    ctx->g_final = gf;
+    if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) st = NC_ECUDA;
+  } while (0);
+  cudaFree(src);
+  if (st != NC_OK) return bail(st);
+
+  // ---- activations and per-step buffers
+  const size_t B = c.max_streams;
+  const int nsm = attn_max_splits(D);
+  if (dalloc(ctx, &ctx->x, B * D.d * 4) || dalloc(ctx, &ctx->qkv, B * D.qkv_rows * 4) ||
+      dalloc(ctx, &ctx->part, B * D.hq * nsm * (kHeadDim + 2) * 4) ||
+      dalloc(ctx, &ctx->h, B * D.F * 4) || dalloc(ctx, &ctx->cdf, B * (D.V + 1) * 4) ||
+      dalloc(ctx, &ctx->d_slots, B * 4) || dalloc(ctx, &ctx->d_nB, 16) ||
+      dalloc(ctx, &ctx->d_obs, B * 4) || dalloc(ctx, &ctx->d_target, B * 4) ||
+      dalloc(ctx, &ctx->d_lohi, B * 8) || dalloc(ctx, &ctx->d_status, B * 4) ||
+      dalloc(ctx, &ctx->d_st, B * sizeof(StreamDev)))
+    return bail(NC_ENOMEM);
+  if (cudaMallocHost(&ctx->h_i32, (3 * B + 4) * 4) != cudaSuccess ||
+      cudaMallocHost(&ctx->h_u32, 3 * B * 4) != cudaSuccess ||
+      cudaMallocHost(&ctx->h_status, B * 4) != cudaSuccess)
+    return bail(NC_ENOMEM);
+  ctx->h_st.assign(B, StreamDev{});
+  ctx->slots.assign(B, Slot{});
+  if (cudaMemset(ctx->d_st, 0, B * sizeof(StreamDev)) != cudaSuccess) return bail(NC_ECUDA);
+  *out = ctx;
+  return NC_OK;
+}
+
+// ---------------------------------------------------------------- streams
+
+static int slot_alloc(nc_ctx* ctx, Slot& s, int64_t max_len) {
+  const Dims& D = ctx->D;
+  if (!s.kv) {
+    const size_t kvb = (size_t)D.n_layers * 2 * D.hkv * D.L * kHeadDim * (D.kv_bf16 ? 2 : 4);
+    NC_TRY(cudaMalloc(&s.kv, kvb));
+    NC_TRY(cudaMalloc(&s.bias, (size_t)D.V * 4));
+    NC_TRY(cudaMalloc(&s.uni, (size_t)D.V * 4));
+    NC_TRY(cudaMalloc(&s.z, (size_t)D.V * 4));
+  }
+  if (D.order > 0 && s.cap_len < max_len) {
+    for (int k = 0; k < 3; ++k) {
+      cudaFree(s.keys[k]);
+      cudaFree(s.idx[k]);
+      cudaFree(s.ent[k]);
+      s.keys[k] = nullptr;
+      s.idx[k] = nullptr;
+      s.ent[k] = nullptr;
+    }
+    s.cap_len = 0;
+    const int64_t cap = next_pow2(std::max<int64_t>(2 * max_len, 16));
+    for (int k = 0; k < D.order; ++k) {
+      NC_TRY(cudaMalloc(&s.keys[k], (size_t)cap * 8));
+      NC_TRY(cudaMalloc(&s.idx[k], (size_t)cap * 4));
+      NC_TRY(cudaMalloc(&s.ent[k], (size_t)max_len * sizeof(NgEntry)));
+    }
+    s.cap_len = max_len;
+    s.cap_hash = cap;
+  }
+  return NC_OK;
+}
+
+static int open_slot(nc_ctx* ctx, int32_t id, int64_t max_len, int* slot_out) {
+  int si = -1;
+  for (int i = 0; i < (int)ctx->slots.size(); ++i)
+    if (!ctx->slots[i].open) {
+      si = i;
+      break;
+    }
+  if (si < 0) return fail(ctx, NC_EINVAL, "no free stream slot");
+  Slot& s = ctx->slots[si];
+  int st = slot_alloc(ctx, s, max_len);
+  if (st != NC_OK) return st;
+  const Dims& D = ctx->D;
+  cudaStream_t cs = ctx->stream;
+  NC_TRY(cudaMemsetAsync(s.bias, 0, (size_t)D.V * 4, cs));
+  NC_TRY(cudaMemsetAsync(s.uni, 0, (size_t)D.V * 4, cs));
+  for (int k = 0; k < D.order; ++k) NC_TRY(cudaMemsetAsync(s.keys[k], 0xFF, (size_t)s.cap_hash * 8, cs));
+  StreamDev sd{};
+  sd.n_coded = 0;
+  sd.last_tok = 0;   // BOS
+  sd.kv_start = 0;
+  sd.N = 0;
+  for (int k = 0; k < 3; ++k) {
+    sd.hist[k] = 0;
+    sd.ctx_ent[k] = -1;
+    sd.n_ent[k] = 0;
+    sd.keys[k] = s.keys[k];
+    sd.idx[k] = s.idx[k];
+    sd.ent[k] = s.ent[k];
+  }
+  sd.max_len = (int32_t)max_len;
+  sd.status = 0;
+  sd.cap_mask = (int32_t)(s.cap_hash - 1);
+  sd.theta[0] = logf(ctx->cfg.w_llm_init);
+  sd.theta[1] = logf(1.0f - ctx->cfg.w_llm_init);
+  sd.bias = s.bias;
+  sd.uni = s.uni;
+  sd.z = s.z;
+  sd.kv = s.kv;
+  ctx->h_st[si] = sd;
+  NC_TRY(cudaMemcpyAsync(ctx->d_st + si, &ctx->h_st[si], sizeof(StreamDev), cudaMemcpyHostToDevice, cs));
+  NC_TRY(cudaStreamSynchronize(cs));
+  s.open = true;
+  s.awaiting_update = false;
+  s.id = id;
+  s.n_coded = 0;
+  s.last_tok = -1;
+  s.max_len = max_len;
+  ctx->id2slot[id] = si;
+  *slot_out = si;
+  return NC_OK;
+}
+
+extern "C" int nc_stream_open(nc_ctx* ctx, int32_t stream_id, int64_t expected_len) {
+  if (!ctx) return NC_EINVAL;
+  if (ctx->poisoned) return NC_ESTATE;
+  if (stream_id < 0 || expected_len < 1 || expected_len > (1 << 30)) return fail(ctx, NC_EINVAL, "bad stream id or length");
+  if (ctx->id2slot.count(stream_id)) return fail(ctx, NC_EINVAL, "stream id already open");
+  cudaSetDevice(ctx->cfg.device);
+  int si;
+  return open_slot(ctx, stream_id, expected_len, &si);
+}
+
+extern "C" int nc_stream_close(nc_ctx* ctx, int32_t stream_id) {
+  if (!ctx) return NC_EINVAL;
+  auto it = ctx->id2slot.find(stream_id);
+  if (it == ctx->id2slot.end()) return fail(ctx, NC_EINVAL, "unknown stream id");
+  Slot& s = ctx->slots[it->second];
+  s.open = false;
+  s.id = -1;
+  ctx->id2slot.erase(it);
+  return NC_OK;
+}
+
+// ------------------------------------------------------------- step pieces
+
+static Batch make_batch(nc_ctx* ctx) {
+  Batch b;
+  b.slots = ctx->d_slots;
+  b.nB = ctx->d_nB;
+  b.obs = ctx->d_obs;
+  b.st = ctx->d_st;
+  b.Bmax = ctx->cfg.max_streams;
+  return b;
+}
+
+// Model forward of every active row: logits into each stream's z.
+static cudaError_t launch_model(nc_ctx* ctx, const Batch& b) {
+  const Dims& D = ctx->D;
+  cudaStream_t s = ctx->stream;
+  cudaError_t e = launch_embed(D, b, ctx->embed, ctx->embed_scale, ctx->fmt, ctx->x, s);
+  for (int l = 0; l < D.n_layers && e == cudaSuccess; ++l) {
+    const LayerW& L = ctx->layers[l];
+    GemvIO io{};
+    io.x = ctx->x;
+    io.g = L.g_attn;
+    io.y = ctx->qkv;
+    e = launch_gemv(D, b, L.qkv, ctx->fmt, PRO_RMSNORM, EPI_STORE, io, s);
+    if (e == cudaSuccess) e = launch_attn(D, b, l, ctx->qkv, ctx->part, s);
+    if (e == cudaSuccess) {
+      io = GemvIO{};
+      io.part = ctx->part;
+      io.y = ctx->x;
+      e = launch_gemv(D, b, L.o, ctx->fmt, PRO_ATTN, EPI_RESID, io, s);
+    }
+    if (e == cudaSuccess) {
+      io = GemvIO{};
+      io.x = ctx->x;
+      io.g = L.g_ffn;
+      io.y = ctx->h;
+      e = launch_gemv(D, b, L.gu, ctx->fmt, PRO_RMSNORM, EPI_SWIGLU, io, s);
+    }
+    if (e == cudaSuccess) {
+      io = GemvIO{};
+      io.x = ctx->h;
+      io.y = ctx->x;
+      e = launch_gemv(D, b, L.down, ctx->fmt, PRO_PLAIN, EPI_RESID, io, s);
+    }
+  }
+  if (e == cudaSuccess) {
+    GemvIO io{};
+    io.x = ctx->x;
+    io.g = ctx->g_final;
+    Mat head{ctx->embed, ctx->embed_scale, D.V, D.d};
+    e = launch_gemv(D, b, head, ctx->fmt, PRO_RMSNORM, EPI_LOGITS, io, s);
+  }
+  return e;
+}
+
+// Host-side checks and staging of a batch of open streams.
+static int stage_batch(nc_ctx* ctx, int n, const int32_t* ids, std::vector<int>* slot_idx,
+                       bool want_awaiting) {
+  if (n < 1 || n > ctx->cfg.max_streams || !ids) return fail(ctx, NC_EINVAL, "bad stream count or ids");
+  slot_idx->resize(n);
+  for (int j = 0; j < n; ++j) {
+    auto it = ctx->id2slot.find(ids[j]);
+    if (it == ctx->id2slot.end()) return fail(ctx, NC_EINVAL, "unknown stream id");
+    (*slot_idx)[j] = it->second;
+    const Slot& s = ctx->slots[it->second];
+    if (s.awaiting_update != want_awaiting)
+      return fail(ctx, NC_ESTATE, want_awaiting ? "stream has no pending step" : "stream awaits nc_update_bias");
+    if (!want_awaiting && s.n_coded >= s.max_len) return fail(ctx, NC_ESTATE, "stream longer than its expected_len");
+  }
+  std::vector<int> sorted(*slot_idx);
+  std::sort(sorted.begin(), sorted.end());
+  if (std::adjacent_find(sorted.begin(), sorted.end()) != sorted.end())
+    return fail(ctx, NC_EINVAL, "duplicate stream id");
+  ctx->h_i32[0] = n;
+  for (int j = 0; j < n; ++j) ctx->h_i32[1 + j] = (*slot_idx)[j];
+  NC_TRY(cudaMemcpyAsync(ctx->d_nB, ctx->h_i32, 4, cudaMemcpyHostToDevice, ctx->stream));
+  NC_TRY(cudaMemcpyAsync(ctx->d_slots, ctx->h_i32 + 1, (size_t)n * 4, cudaMemcpyHostToDevice, ctx->stream));
+  return NC_OK;
+}
+
+// Read and clear the sticky status words of the given slots.
+static int check_status(nc_ctx* ctx, const std::vector<int>& slot_idx) {
+  const size_t off = offsetof(StreamDev, status);
+  for (size_t j = 0; j < slot_idx.size(); ++j)
+    NC_TRY(cudaMemcpyAsync(ctx->h_status + j, reinterpret_cast<char*>(ctx->d_st + slot_idx[j]) + off, 4,
+                           cudaMemcpyDeviceToHost, ctx->stream));
+  NC_TRY(cudaStreamSynchronize(ctx->stream));
+  int32_t any = 0;
+  for (size_t j = 0; j < slot_idx.size(); ++j) any |= ctx->h_status[j];
+  if (any) {
+    for (size_t j = 0; j < slot_idx.size(); ++j)
+      NC_TRY(cudaMemsetAsync(reinterpret_cast<char*>(ctx->d_st + slot_idx[j]) + off, 0, 4, ctx->stream));
+    NC_TRY(cudaStreamSynchronize(ctx->stream));
+    if (any & ST_NUMERIC) return fail(ctx, NC_ENUMERIC, "non-finite probabilities or CDF floor underflow");
+    if (any & ST_TABLE_FULL) return fail(ctx, NC_ESTATE, "N-gram tables full (stream longer than expected_len)");
+    return fail(ctx, NC_EINVAL, "observed token out of range");
+  }
+  return NC_OK;
+}
+
+static int step_common(nc_ctx* ctx, int n, const int32_t* ids, const int32_t* prev, float* z,
+                       float* pt, float* png, float* p, uint32_t* cdf_out) {
+  if (!ctx) return NC_EINVAL;
+  if (ctx->poisoned) return fail(ctx, NC_ESTATE, "context poisoned by an earlier CUDA error");
+  cudaSetDevice(ctx->cfg.device);
+  std::vector<int> si;
+  int st = stage_batch(ctx, n, ids, &si, false);
+  if (st != NC_OK) return st;
+  if (prev) {
+    for (int j = 0; j < n; ++j)
+      if (prev[j] != ctx->slots[si[j]].last_tok) return fail(ctx, NC_EINVAL, "prev_tokens differ from the observed history");
+  }
+  const Dims& D = ctx->D;
+  const bool dev_out = cdf_out && is_device_ptr(cdf_out);
+  Batch b = make_batch(ctx);
+  b.obs = nullptr;
+  NC_TRY(launch_model(ctx, b));
+  VocabIO io{};
+  io.cdf = dev_out ? cdf_out : ctx->cdf;
+  io.probe_z = z;
+  io.probe_pt = pt;
+  io.probe_png = png;
+  io.probe_p = p;
+  io.predict = 1;
+  NC_TRY(launch_vocab(D, b, io, ctx->stream));
+  if (cdf_out && !dev_out)
+    NC_TRY(cudaMemcpyAsync(cdf_out, ctx->cdf, (size_t)n * (D.V + 1) * 4, cudaMemcpyDeviceToHost, ctx->stream));
+  st = check_status(ctx, si);
+  if (st != NC_OK) return st;
+  for (int j = 0; j < n; ++j) ctx->slots[si[j]].awaiting_update = true;
+  return NC_OK;
+}
+
+extern "C" int nc_step_cdf(nc_ctx* ctx, int n, const int32_t* stream_ids, const int32_t* prev_tokens,
+                           uint32_t* cdf_out) {
+  return step_common(ctx, n, stream_ids, prev_tokens, nullptr, nullptr, nullptr, nullptr, cdf_out);
+}
+
+extern "C" int nc_step_probe(nc_ctx* ctx, int n, const int32_t* stream_ids, float* z, float* p_tilde,
+                             float* p_ng, float* p, uint32_t* cdf_out) {
+  for (float* q : {z, p_tilde, p_ng, p})
+    if (q && !is_device_ptr(q)) return fail(ctx, NC_EINVAL, "probe buffers must be device memory");
+  return step_common(ctx, n, stream_ids, nullptr, z, p_tilde, p_ng, p, cdf_out);
+}
+
+extern "C" int nc_update_bias(nc_ctx* ctx, int n, const int32_t* stream_ids, const int32_t* observed) {
+  if (!ctx) return NC_EINVAL;
+  if (ctx->poisoned) return fail(ctx, NC_ESTATE, "context poisoned by an earlier CUDA error");
+  if (!observed) return fail(ctx, NC_EINVAL, "observed is NULL");
+  cudaSetDevice(ctx->cfg.device);
+  for (int j = 0; j < n; ++j)
+    if (observed[j] < 0 || observed[j] >= ctx->D.V) return fail(ctx, NC_EINVAL, "observed token out of range");
+  std::vector<int> si;
+  int st = stage_batch(ctx, n, stream_ids, &si, true);
+  if (st != NC_OK) return st;
+  std::memcpy(ctx->h_i32 + 1 + ctx->cfg.max_streams, observed, (size_t)n * 4);
+  NC_TRY(cudaMemcpyAsync(ctx->d_obs, ctx->h_i32 + 1 + ctx->cfg.max_streams, (size_t)n * 4,
+                         cudaMemcpyHostToDevice, ctx->stream));
+  Batch b = make_batch(ctx);
+  VocabIO io{};
+  io.update = 1;
+  NC_TRY(launch_vocab(ctx->D, b, io, ctx->stream));
+  NC_TRY(launch_ngram_update(ctx->D, b, ctx->stream));
+  st = check_status(ctx, si);
+  if (st != NC_OK) return st;
+  for (int j = 0; j < n; ++j) {
+    Slot& s = ctx->slots[si[j]];
+    s.awaiting_update = false;
+    s.n_coded += 1;
+    s.last_tok = observed[j];
+  }
+  return NC_OK;
+}
+
+extern "C" int nc_stream_state(nc_ctx* ctx, int32_t stream_id, float* bias, float* mix_logw, int64_t* n_coded) {
+  if (!ctx) return NC_EINVAL;
+  auto it = ctx->id2slot.find(stream_id);
+  if (it == ctx->id2slot.end()) return fail(ctx, NC_EINVAL, "unknown stream id");
+  cudaSetDevice(ctx->cfg.device);
+  const int si = it->second;
+  StreamDev sd;
+  NC_TRY(cudaMemcpyAsync(&sd, ctx->d_st + si, sizeof(sd), cudaMemcpyDeviceToHost, ctx->stream));
+  if (bias) NC_TRY(cudaMemcpyAsync(bias, ctx->slots[si].bias, (size_t)ctx->D.V * 4, cudaMemcpyDeviceToHost, ctx->stream));
+  NC_TRY(cudaStreamSynchronize(ctx->stream));
+  if (mix_logw) {
+    mix_logw[0] = sd.theta[0];
+    mix_logw[1] = sd.theta[1];
+  }
+  if (n_coded) *n_coded = sd.n_coded;
+  return NC_OK;
+}
+
+// -------------------------------------------------------- whole streams
+
+static uint8_t flags_byte(const nc_config& c) {
+  uint8_t f = 0;
+  if (c.ngram_order > 0) f |= 1;
+  if (c.use_head) f |= 2;
+  if (c.update_rule == NC_RULE_MIXED_NLL) f |= 8;
+  return f;
+}
+static uint8_t path_byte(const nc_config& c) { return (uint8_t)(c.weight_fmt | (c.path << 4)); }
+
+// The device half of nc_encode: tokens resident on the device, one captured
+// step replayed until every stream is coded.  Streams must already be open in
+// slots slot_of[j] (j in the caller's order); rows are processed longest
+// first.  intervals: DEVICE uint32[n][stride][2].
+static int encode_device(nc_ctx* ctx, int n, const std::vector<int>& slot_of, const int32_t* tok_dev,
+                         const int64_t* offs_dev, const int64_t* lens_dev, int64_t max_len,
+                         uint32_t* intervals, int64_t stride) {
+  const Dims& D = ctx->D;
+  cudaStream_t s = ctx->stream;
+  for (int j = 0; j < n; ++j) ctx->h_i32[1 + j] = slot_of[j];
+  NC_TRY(cudaMemcpyAsync(ctx->d_slots, ctx->h_i32 + 1, (size_t)n * 4, cudaMemcpyHostToDevice, s));
+  Batch b = make_batch(ctx);
+  b.Bmax = n;
+  VocabIO io{};
+  io.predict = 1;
+  io.update = 1;
+  io.intervals = intervals;
+  io.interval_stride = stride;
+  auto one_step = [&]() -> cudaError_t {
+    cudaError_t e = launch_prepare_encode(b, n, tok_dev, offs_dev, lens_dev, ctx->d_obs, ctx->d_nB, s);
+    if (e == cudaSuccess) e = launch_model(ctx, b);
+    if (e == cudaSuccess) e = launch_vocab(D, b, io, s);
+    if (e == cudaSuccess) e = launch_ngram_update(D, b, s);
+    return e;
+  };
+  // capture one step in a graph (the whole step is device-driven)
+  cudaGraph_t g = nullptr;
+  cudaGraphExec_t ge = nullptr;
+  bool graphed = false;
+  if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+    cudaError_t e = one_step();
+    cudaError_t e2 = cudaStreamEndCapture(s, &g);
+    if (e == cudaSuccess && e2 == cudaSuccess && cudaGraphInstantiate(&ge, g, 0) == cudaSuccess) graphed = true;
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+  }
+  for (int64_t k = 0; k < max_len; ++k) {
+    if (graphed) {
+      NC_TRY(cudaGraphLaunch(ge, s));
+    } else {
+      NC_TRY(one_step());
+    }
+  }
+  if (ge) cudaGraphExecDestroy(ge);
+  return NC_OK;
+}
+
+extern "C" int nc_encode(nc_ctx* ctx, int n_streams, const int32_t* const* tokens, const int64_t* lens,
+                         uint8_t* out, size_t* inout_nbytes) {
+  if (!ctx) return NC_EINVAL;
+  if (ctx->poisoned) return fail(ctx, NC_ESTATE, "context poisoned by an earlier CUDA error");
+  if (!tokens || !lens || !inout_nbytes || n_streams < 1 || n_streams > 65535)
+    return fail(ctx, NC_EINVAL, "bad arguments");
+  if (n_streams > ctx->cfg.max_streams) return fail(ctx, NC_EINVAL, "more streams than max_streams");
+  const Dims& D = ctx->D;
+  int64_t total = 0, max_len = 0;
+  for (int j = 0; j < n_streams; ++j) {
+    if (lens[j] < 0 || lens[j] > 0x7fffffff || (lens[j] > 0 && !tokens[j])) return fail(ctx, NC_EINVAL, "bad stream");
+    total += lens[j];
+    max_len = std::max(max_len, lens[j]);
+    for (int64_t i = 0; i < lens[j]; ++i)
+      if (tokens[j][i] < 0 || tokens[j][i] >= D.V) return fail(ctx, NC_EINVAL, "token out of range");
+  }
+  // worst case: about 24 bits + 2 per token plus 2 bits per stream
+  std::vector<StreamRecord> bound(n_streams);
+  for (int j = 0; j < n_streams; ++j) {
+    const uint64_t bits = (uint64_t)lens[j] * (D.log2T + 2) + 4;
+    bound[j] = StreamRecord{(uint32_t)lens[j], (uint32_t)bits, (uint32_t)((bits + 7) / 8)};
+  }
+  if (!out) {
+    *inout_nbytes = container_size(bound);
+    return NC_OK;
+  }
+  cudaSetDevice(ctx->cfg.device);
+  int free_slots = 0;
+  for (auto& s : ctx->slots) free_slots += !s.open;
+  if (free_slots < n_streams) return fail(ctx, NC_EINVAL, "not enough free stream slots");
+  // longest first, so the active rows of each step are a prefix
+  std::vector<int> order(n_streams);
+  for (int j = 0; j < n_streams; ++j) order[j] = j;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return lens[a] > lens[b]; });
+  std::vector<int> slot_of(n_streams);
+  std::vector<int32_t> ids(n_streams);
+  int st = NC_OK;
+  int32_t next_id = 0x40000000;
+  for (int r = 0; r < n_streams && st == NC_OK; ++r) {
+    while (ctx->id2slot.count(next_id)) ++next_id;
+    ids[r] = next_id++;
+    st = open_slot(ctx, ids[r], std::max<int64_t>(lens[order[r]], 1), &slot_of[r]);
+  }
+  auto close_all = [&]() {
+    for (int r = 0; r < n_streams; ++r)
+      if (ctx->id2slot.count(ids[r])) nc_stream_close(ctx, ids[r]);
+  };
+  if (st != NC_OK) {
+    close_all();
+    return st;
+  }
+  // tokens, offsets and lengths to the device (row order = longest first)
+  int32_t* tok_dev = nullptr;
+  int64_t* meta = nullptr;
+  uint32_t* iv = nullptr;
+  std::vector<int64_t> h_meta(2 * n_streams);
+  int64_t off = 0;
+  for (int r = 0; r < n_streams; ++r) {
+    h_meta[r] = off;
+    h_meta[n_streams + r] = lens[order[r]];
+    off += lens[order[r]];
+  }
+  std::vector<uint32_t> h_iv;
+  do {
+    if (cudaMalloc(&tok_dev, std::max<int64_t>(total, 1) * 4) != cudaSuccess ||
+        cudaMalloc(&meta, 2 * n_streams * 8) != cudaSuccess ||
+        cudaMalloc(&iv, (size_t)n_streams * std::max<int64_t>(max_len, 1) * 8) != cudaSuccess) {
+      st = fail(ctx, NC_ENOMEM, "device allocation for encode failed");
+      break;
+    }
+    for (int r = 0; r < n_streams; ++r)
+      if (lens[order[r]] > 0 &&
+          cudaMemcpyAsync(tok_dev + h_meta[r], tokens[order[r]], lens[order[r]] * 4, cudaMemcpyHostToDevice,
+                          ctx->stream) != cudaSuccess) {
+        st = fail_cuda(ctx, cudaErrorUnknown, "token upload");
+        break;
+      }
+    if (st != NC_OK) break;
+    if (cudaMemcpyAsync(meta, h_meta.data(), 2 * n_streams * 8, cudaMemcpyHostToDevice, ctx->stream) != cudaSuccess) {
+      st = fail_cuda(ctx, cudaErrorUnknown, "meta upload");
+      break;
+    }
+    st = encode_device(ctx, n_streams, slot_of, tok_dev, meta, meta + n_streams, max_len, iv, max_len);
+    if (st != NC_OK) break;
+    h_iv.resize((size_t)n_streams * max_len * 2);
+    if (cudaMemcpyAsync(h_iv.data(), iv, h_iv.size() * 4, cudaMemcpyDeviceToHost, ctx->stream) != cudaSuccess) {
+      st = fail_cuda(ctx, cudaErrorUnknown, "interval download");
+      break;
+    }
+    st = check_status(ctx, slot_of);
+  } while (0);
+  cudaFree(tok_dev);
+  cudaFree(meta);
+  cudaFree(iv);
+  close_all();
+  if (st != NC_OK) return st;
+  // host coder, streams in parallel
+  std::vector<AcEncoder> enc;
+  enc.reserve(n_streams);
+  for (int j = 0; j < n_streams; ++j) enc.emplace_back(D.log2T);
+  std::vector<int> bad(n_streams, 0);
+  auto work = [&](int r0, int r1) {
+    for (int r = r0; r < r1; ++r) {
+      const uint32_t* p = h_iv.data() + (size_t)r * max_len * 2;
+      AcEncoder& e = enc[order[r]];
+      for (int64_t i = 0; i < lens[order[r]]; ++i)
+        if (!e.encode(p[2 * i], p[2 * i + 1])) bad[order[r]] = 1;
+      e.finish();
+    }
+  };
+  const int nthr = std::max(1, std::min<int>(n_streams, (int)std::thread::hardware_concurrency()));
+  if (nthr == 1) {
+    work(0, n_streams);
+  } else {
+    std::vector<std::thread> th;
+    const int per = (n_streams + nthr - 1) / nthr;
+    for (int t = 0; t < nthr; ++t) {
+      const int r0 = t * per, r1 = std::min(n_streams, r0 + per);
+      if (r0 < r1) th.emplace_back(work, r0, r1);
+    }
+    for (auto& t : th) t.join();
+  }
+  for (int j = 0; j < n_streams; ++j)
+    if (bad[j]) return fail(ctx, NC_ENUMERIC, "empty coder interval");
+  std::vector<StreamRecord> recs(n_streams);
+  std::vector<const std::vector<uint8_t>*> pays(n_streams);
+  for (int j = 0; j < n_streams; ++j) {
+    if (enc[j].nbits() > 0xffffffffull) return fail(ctx, NC_EINVAL, "stream too long for the container");
+    recs[j] = StreamRecord{(uint32_t)lens[j], (uint32_t)enc[j].nbits(), (uint32_t)enc[j].bytes().size()};
+    pays[j] = &enc[j].bytes();
+  }
+  const size_t need = container_size(recs);
+  if (*inout_nbytes < need) {
+    *inout_nbytes = need;
+    return fail(ctx, NC_EINVAL, "output buffer too small");
+  }
+  container_write(out, flags_byte(ctx->cfg), ctx->cfg.temperature, path_byte(ctx->cfg), recs, pays);
+  *inout_nbytes = need;
+  return NC_OK;
+}
+
+extern "C" int nc_container_streams(const uint8_t* in, size_t nbytes, int* n_streams) {
+  uint8_t flags, pb;
+  float tau;
+  std::vector<StreamRecord> recs;
+  std::vector<const uint8_t*> pays;
+  if (!n_streams || !container_read(in, nbytes, &flags, &tau, &pb, &recs, &pays)) return NC_ECORRUPT;
+  *n_streams = (int)recs.size();
+  return NC_OK;
+}
+
+extern "C" int nc_decode(nc_ctx* ctx, const uint8_t* in, size_t nbytes, int32_t* const* tokens_out,
+                         int64_t* lens_out) {
+  if (!ctx) return NC_EINVAL;
+  if (ctx->poisoned) return fail(ctx, NC_ESTATE, "context poisoned by an earlier CUDA error");
+  if (!in || !lens_out) return fail(ctx, NC_EINVAL, "bad arguments");
+  uint8_t flags, pb;
+  float tau;
+  std::vector<StreamRecord> recs;
+  std::vector<const uint8_t*> pays;
+  if (!container_read(in, nbytes, &flags, &tau, &pb, &recs, &pays)) return fail(ctx, NC_ECORRUPT, "malformed container");
+  if (flags != flags_byte(ctx->cfg) || pb != path_byte(ctx->cfg) ||
+      float_to_half_bits(tau) != float_to_half_bits(ctx->cfg.temperature))
+    return fail(ctx, NC_ECORRUPT, "container features or numeric path differ from the context");
+  const int n = (int)recs.size();
+  for (int j = 0; j < n; ++j) lens_out[j] = recs[j].ntok;
+  if (!tokens_out) return NC_OK;
+  if (n > ctx->cfg.max_streams) return fail(ctx, NC_EINVAL, "more streams than max_streams");
+  if (n == 0) return NC_OK;
+  const Dims& D = ctx->D;
+  cudaSetDevice(ctx->cfg.device);
+  cudaStream_t s = ctx->stream;
+  std::vector<int> order(n);
+  for (int j = 0; j < n; ++j) order[j] = j;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return recs[a].ntok > recs[b].ntok; });
+  std::vector<int> slot_of(n);
+  std::vector<int32_t> ids(n);
+  int st = NC_OK;
+  int32_t next_id = 0x50000000;
+  for (int r = 0; r < n && st == NC_OK; ++r) {
+    while (ctx->id2slot.count(next_id)) ++next_id;
+    ids[r] = next_id++;
+    st = open_slot(ctx, ids[r], std::max<uint32_t>(recs[order[r]].ntok, 1), &slot_of[r]);
+  }
+  auto close_all = [&]() {
+    for (int r = 0; r < n; ++r)
+      if (ctx->id2slot.count(ids[r])) nc_stream_close(ctx, ids[r]);
+  };
+  if (st != NC_OK) {
+    close_all();
+    return st;
+  }
+  std::vector<AcDecoder> dec;
+  dec.reserve(n);
+  for (int r = 0; r < n; ++r) dec.emplace_back(pays[order[r]], recs[order[r]].nbits, D.log2T);
+  for (int r = 0; r < n; ++r) ctx->h_i32[1 + r] = slot_of[r];
+  int64_t max_len = recs[order[0]].ntok;
+  Batch b = make_batch(ctx);
+  b.Bmax = n;
+  do {
+    if (cudaMemcpyAsync(ctx->d_slots, ctx->h_i32 + 1, (size_t)n * 4, cudaMemcpyHostToDevice, s) != cudaSuccess) {
+      st = fail_cuda(ctx, cudaErrorUnknown, "slot upload");
+      break;
+    }
+    int active = n;
+    for (int64_t k = 0; k < max_len && st == NC_OK; ++k) {
+      while (active > 0 && recs[order[active - 1]].ntok <= k) --active;
+      ctx->h_i32[0] = active;
+      for (int r = 0; r < active; ++r) ctx->h_u32[r] = dec[r].target();
+      cudaError_t e = cudaMemcpyAsync(ctx->d_nB, ctx->h_i32, 4, cudaMemcpyHostToDevice, s);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(ctx->d_target, ctx->h_u32, (size_t)active * 4, cudaMemcpyHostToDevice, s);
+      if (e == cudaSuccess) e = launch_model(ctx, b);
+      VocabIO io{};
+      io.cdf = ctx->cdf;
+      io.predict = 1;
+      if (e == cudaSuccess) e = launch_vocab(D, b, io, s);
+      if (e == cudaSuccess) e = launch_search(b, D.V, ctx->cdf, ctx->d_target, ctx->d_obs, ctx->d_lohi, s);
+      VocabIO up{};
+      up.update = 1;
+      if (e == cudaSuccess) e = launch_vocab(D, b, up, s);
+      if (e == cudaSuccess) e = launch_ngram_update(D, b, s);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(ctx->h_u32 + n, ctx->d_lohi, (size_t)active * 8, cudaMemcpyDeviceToHost, s);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(ctx->h_i32 + 1 + 2 * ctx->cfg.max_streams, ctx->d_obs, (size_t)active * 4,
+                                                cudaMemcpyDeviceToHost, s);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+      if (e != cudaSuccess) {
+        st = fail_cuda(ctx, e, "decode step");
+        break;
+      }
+      for (int r = 0; r < active; ++r) {
+        const uint32_t lo = ctx->h_u32[n + 2 * r], hi = ctx->h_u32[n + 2 * r + 1];
+        dec[r].consume(lo, hi);
+        tokens_out[order[r]][k] = ctx->h_i32[1 + 2 * ctx->cfg.max_streams + r];
+      }
+    }
+    if (st == NC_OK) st = check_status(ctx, slot_of);
+  } while (0);
+  close_all();
+  return st;
+}
+
+// ------------------------------------------------------ building blocks
+
+extern "C" int nc_probs_to_cdf(const float* p, int n, int V, int log2_total, uint32_t floor_c, uint32_t* cdf,
+                               void* stream) {
+  if (!p || !cdf || n < 1 || V < 2 || V > 65535 || log2_total < 1 || log2_total > 24 || floor_c < 1 ||
+      (uint64_t)V * floor_c >= (1ull << log2_total))
+    return NC_EINVAL;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int32_t* status = nullptr;
+  if (cudaMalloc(&status, (size_t)n * 4) != cudaSuccess) return NC_ENOMEM;
+  int rc = NC_OK;
+  std::vector<int32_t> hs(n);
+  if (cudaMemsetAsync(status, 0, (size_t)n * 4, s) != cudaSuccess ||
+      launch_probs_to_cdf(p, n, V, log2_total, floor_c, cdf, status, s) != cudaSuccess ||
+      cudaMemcpyAsync(hs.data(), status, (size_t)n * 4, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    rc = NC_ECUDA;
+  cudaFree(status);
+  if (rc == NC_OK)
+    for (int j = 0; j < n; ++j)
+      if (hs[j]) rc = NC_ENUMERIC;
+  return rc;
+}
+
+extern "C" int nc_floor_counts(const float* p, int64_t n, uint32_t K, uint32_t floor_c, uint32_t* c, void* stream) {
+  if (!p || !c || n < 0 || K < 1 || K >= (1u << 24)) return NC_EINVAL;
+  if (n == 0) return NC_OK;
+  return launch_floor_counts(p, n, K, floor_c, c, static_cast<cudaStream_t>(stream)) == cudaSuccess ? NC_OK : NC_ECUDA;
+}
+
+extern "C" int nc_ac_encode(const uint32_t* lo, const uint32_t* hi, int64_t n, int log2_total, uint8_t* out,
+                            size_t* inout_nbytes, uint64_t* nbits) {
+  if (!lo || !hi || !inout_nbytes || n < 0 || log2_total < 1 || log2_total > 30) return NC_EINVAL;
+  AcEncoder e(log2_total);
+  for (int64_t i = 0; i < n; ++i)
+    if (!e.encode(lo[i], hi[i])) return NC_EINVAL;
+  e.finish();
+  const size_t need = e.bytes().size();
+  if (nbits) *nbits = e.nbits();
+  if (!out || *inout_nbytes < need) {
+    *inout_nbytes = need;
+    return out ? NC_EINVAL : NC_OK;
+  }
+  std::memcpy(out, e.bytes().data(), need);
+  *inout_nbytes = need;
+  return NC_OK;
+}
+
+extern "C" int nc_ac_decode(const uint8_t* bits, uint64_t nbits, const uint32_t* cdfs, int V, int64_t n,
+                            int log2_total, int32_t* symbols) {
+  if ((!bits && nbits) || !cdfs || !symbols || V < 1 || n < 0 || log2_total < 1 || log2_total > 30) return NC_EINVAL;
+  const uint64_t T = 1ull << log2_total;
+  AcDecoder d(bits, nbits, log2_total);
+  for (int64_t i = 0; i < n; ++i) {
+    const uint32_t* c = cdfs + (size_t)i * (V + 1);
+    if (c[0] != 0 || c[V] != T) return NC_ECORRUPT;
+    const uint32_t t = d.target();
+    int lo = 0, hi = V - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (c[mid] <= t)
+        lo = mid;
+      else
+        hi = mid - 1;
+    }
+    if (c[lo + 1] <= c[lo]) return NC_ECORRUPT;
+    symbols[i] = lo;
+    d.consume(c[lo], c[lo + 1]);
+  }
+  return NC_OK;
+}
+
+extern "C" int nc_mix_nll_fwd(const float* z, const float* b, const float* p_ng, const float* theta,
+                              const int32_t* target, const int32_t* warm, int n, int V, float tau, float* loss,
+                              void* stream) {
+  if (!z || !b || !p_ng || !theta || !target || !warm || !loss || n < 1 || V < 2 || !(tau > 0.f)) return NC_EINVAL;
+  return launch_mix_nll(z, b, p_ng, theta, target, warm, nullptr, n, V, tau, loss, nullptr, nullptr,
+                        static_cast<cudaStream_t>(stream)) == cudaSuccess ? NC_OK : NC_ECUDA;
+}
+
+extern "C" int nc_mix_nll_bwd(const float* z, const float* b, const float* p_ng, const float* theta,
+                              const int32_t* target, const int32_t* warm, const float* gout, int n, int V, float tau,
+                              float* db, float* dtheta, void* stream) {
+  if (!z || !b || !p_ng || !theta || !target || !warm || n < 1 || V < 2 || !(tau > 0.f)) return NC_EINVAL;
+  return launch_mix_nll(z, b, p_ng, theta, target, warm, gout, n, V, tau, nullptr, db, dtheta,
+                        static_cast<cudaStream_t>(stream)) == cudaSuccess ? NC_OK : NC_ECUDA;
+}

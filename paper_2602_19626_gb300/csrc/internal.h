@@ -1,0 +1,152 @@
+// Internal declarations shared by the nc24 kernels and the host orchestration.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+
+#include "nc24.h"
+
+namespace nc {
+
+constexpr int kHeadDim = 64;           // d_head of the supported models (Sec. 3.2)
+constexpr int kMaxSlots = 64;          // continuation slots per N-gram context (Sec. 3.4)
+constexpr int kMaxOrder = 3;           // N-gram context lengths 1..3
+constexpr int kAttnChunk = 128;        // KV positions per attention CTA
+constexpr int kMaxGroup = 4;           // query heads per KV head supported
+constexpr int kVocabCluster = 8;       // CTAs per stream in the vocabulary kernel
+constexpr int kVocabThreads = 512;
+constexpr unsigned long long kEmptyKey = ~0ull;
+
+// Status bits a kernel can raise in StreamDev::status (sticky).
+enum : int32_t {
+  ST_NUMERIC = 1,      // non-finite / out-of-range probability or floor underflow
+  ST_TABLE_FULL = 2,   // N-gram tables exhausted (stream longer than expected_len)
+  ST_BAD_TOKEN = 4,    // observed token out of range
+};
+
+// One N-gram context: retained continuation slots in arrival / replacement
+// order and their count sum n (Sec. 3.4).
+struct NgEntry {
+  int32_t nslots;
+  int32_t n;
+  int32_t tok[kMaxSlots];
+  int32_t cnt[kMaxSlots];
+};
+
+// Per-stream device state (one per slot).
+struct StreamDev {
+  int32_t n_coded;          // tokens coded so far; absolute position of the next fed token
+  int32_t last_tok;         // token fed at the next step (BOS id 0 first)
+  int32_t kv_start;         // absolute position of the oldest cached entry
+  int32_t N;                // unigram total
+  int32_t hist[3];          // last observed tokens, hist[2] most recent
+  int32_t ctx_ent[3];       // entry of the context of order k+1 for the next predict, or -1
+  int32_t n_ent[3];         // entries allocated per order
+  int32_t max_len;          // tokens this stream may code (sizes the tables)
+  int32_t status;           // ST_* bits
+  int32_t cap_mask;         // hash index capacity - 1 (power of two)
+  float theta[2];           // mixer log-weights (Sec. 3.5)
+  float pt_obs, png_obs;    // p_tilde(t*), p_ng(t*) seen by the last update
+  unsigned long long* keys[3];
+  int32_t* idx[3];
+  NgEntry* ent[3];
+  float* bias;              // [V] adaptive log-space bias b (Sec. 3.6)
+  int32_t* uni;             // [V] unigram counts c(t)
+  float* z;                 // [V] logits of the last step
+  void* kv;                 // [layers][2][Hkv][L][64], FP32 (FP32 weights) or BF16
+};
+
+struct Dims {
+  int n_layers, d, hq, hkv, F, V, L, C;
+  int qkv_rows;             // (hq + 2 hkv) * 64
+  float eps, theta, tau;
+  int kv_bf16;              // 1: KV cache in BF16
+  int order;                // N-gram order (0 = off)
+  int use_head;
+  int warmup;
+  int rule;
+  int log2T;
+  uint32_t floor;
+  float alpha, eta;
+};
+
+// Weights of one dense projection in the storage format.
+struct Mat {
+  const void* w;            // [rows][cols] fp32 / bf16 / e4m3
+  const float* scale;       // [rows] per-row scale (FP8) or nullptr
+  int rows, cols;
+};
+
+struct LayerW {
+  Mat qkv, o, gu, down;     // gu rows interleaved: 2j = gate_j, 2j+1 = up_j
+  const float* g_attn;
+  const float* g_ffn;
+};
+
+// Batch description of one step; all pointers are device memory.
+struct Batch {
+  const int32_t* slots;     // [Bmax] slot of batch row j
+  const int32_t* nB;        // active rows (device scalar)
+  const int32_t* obs;       // [Bmax] observed token of row j, or nullptr
+  StreamDev* st;            // [max_streams]
+  int Bmax;
+};
+
+// Largest number of attention chunks (split-KV CTAs) of one (stream, KV head).
+__host__ __device__ inline int attn_splits_max_dev(const Dims& D) {
+  return (D.L + kAttnChunk - 1) / kAttnChunk;
+}
+
+// ------------------------------------------------------------------ kernels
+enum Prologue { PRO_RMSNORM = 0, PRO_ATTN = 1, PRO_PLAIN = 2 };
+enum Epilogue { EPI_STORE = 0, EPI_RESID = 1, EPI_SWIGLU = 2, EPI_LOGITS = 3 };
+
+struct GemvIO {
+  const float* x;           // PRO_RMSNORM / PRO_PLAIN input [Bmax][cols]
+  const float* g;           // RMSNorm gain (PRO_RMSNORM)
+  const float* part;        // attention partials (PRO_ATTN)
+  float* y;                 // EPI_STORE / EPI_SWIGLU output; EPI_RESID residual [Bmax][rows or rows/2]
+};
+
+cudaError_t launch_embed(const Dims& D, const Batch& b, const void* E, const float* Escale,
+                         int fmt, float* x, cudaStream_t s);
+cudaError_t launch_gemv(const Dims& D, const Batch& b, const Mat& m, int fmt, int pro, int epi,
+                        const GemvIO& io, cudaStream_t s);
+cudaError_t launch_attn(const Dims& D, const Batch& b, int layer, const float* qkv, float* part,
+                        cudaStream_t s);
+int attn_max_splits(const Dims& D);
+
+struct VocabIO {
+  uint32_t* cdf;            // [Bmax][V+1] or nullptr
+  uint32_t* intervals;      // per stream [max_len] x (lo, hi) pairs: base + j * stride, or nullptr
+  int64_t interval_stride;  // in uint32 pairs
+  float* probe_z;           // optional probes [Bmax][V]
+  float* probe_pt;
+  float* probe_png;
+  float* probe_p;
+  int predict;              // quantise (and write cdf / intervals)
+  int update;               // apply head + mixer update with b.obs
+};
+cudaError_t launch_vocab(const Dims& D, const Batch& b, const VocabIO& io, cudaStream_t s);
+cudaError_t launch_ngram_update(const Dims& D, const Batch& b, cudaStream_t s);
+cudaError_t launch_prepare_encode(const Batch& b, int n_streams, const int32_t* tok_flat,
+                                  const int64_t* offs, const int64_t* lens, int32_t* obs,
+                                  int32_t* nB, cudaStream_t s);
+// Decoder: row j's symbol is the s with cdf[s] <= target[j] < cdf[s+1]; writes
+// obs[j] = s and lohi[2j..2j+1] = (cdf[s], cdf[s+1]).
+cudaError_t launch_search(const Batch& b, int V, const uint32_t* cdf, const uint32_t* target,
+                          int32_t* obs, uint32_t* lohi, cudaStream_t s);
+cudaError_t launch_convert_weights(const float* src, void* dst, float* scale, int64_t rows,
+                                   int64_t cols, int fmt, cudaStream_t s);
+cudaError_t launch_interleave_f32(const float* gate, const float* up, float* dst, int64_t rows,
+                                  int64_t cols, cudaStream_t s);
+cudaError_t launch_probs_to_cdf(const float* p, int n, int V, int log2T, uint32_t floor,
+                                uint32_t* cdf, int32_t* status, cudaStream_t s);
+cudaError_t launch_floor_counts(const float* p, int64_t n, uint32_t K, uint32_t floor,
+                                uint32_t* c, cudaStream_t s);
+cudaError_t launch_mix_nll(const float* z, const float* b, const float* png, const float* theta,
+                           const int32_t* target, const int32_t* warm, const float* gout, int n,
+                           int V, float tau, float* loss, float* db, float* dtheta,
+                           cudaStream_t s);
+
+}  // namespace nc

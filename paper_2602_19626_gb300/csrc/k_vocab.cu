@@ -1,0 +1,799 @@
+// Vocabulary-wide kernels: biased softmax (Sec. 3.6), N-gram distribution
+// (Sec. 3.4), linear mix (Sec. 3.5), CDF quantisation with floors and the
+// prefix sum (Sec. 3.3), the head / mixer updates, and the N-gram tables.
+//
+// One stream is handled by a cluster of kVocabCluster CTAs; each CTA owns a
+// contiguous chunk of the vocabulary and each thread a contiguous run of E
+// symbols.  Reductions go thread -> warp (fixed xor tree) -> CTA (warps in
+// order) -> cluster (ranks in order through distributed shared memory), so
+// every result is independent of the batch, the slot and the launch.
+#include <cooperative_groups.h>
+
+#include "internal.h"
+
+namespace cg = cooperative_groups;
+
+namespace nc {
+
+namespace {
+
+constexpr int kWarps = kVocabThreads / 32;
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ float warp_max(float v) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+__device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// floor(p * K) for a binary32 p in [0, 2) and K < 2^24, exactly: p = m 2^(e-150)
+// with a 24-bit significand m, so m * K < 2^48 is an exact integer product.
+// Sets `bad` for negative, >= 2, infinite or NaN inputs.
+__device__ __forceinline__ uint32_t floor_prod(float p, uint32_t K, bool& bad) {
+  const uint32_t u = __float_as_uint(p);
+  if (u == 0u || u == 0x80000000u) return 0u;
+  if (u >> 31) {
+    bad = true;
+    return 0u;
+  }
+  uint32_t e = u >> 23;
+  if (e >= 128u) {
+    bad = true;
+    return 0u;
+  }
+  uint32_t m = u & 0x7FFFFFu;
+  if (e == 0u)
+    e = 1u;
+  else
+    m |= 0x800000u;
+  const unsigned long long prod = (unsigned long long)m * K;
+  const uint32_t sh = 150u - e;
+  return sh >= 64u ? 0u : (uint32_t)(prod >> sh);
+}
+
+struct ArgMax {
+  float v;
+  int i;
+};
+__device__ __forceinline__ ArgMax better(ArgMax a, ArgMax b) {
+  // larger value wins; equal values: lower index wins (first maximum)
+  if (b.v > a.v || (b.v == a.v && b.i < a.i)) return b;
+  return a;
+}
+
+// Shared scratch of one CTA for the block / cluster reductions.
+struct VocabShared {
+  float wf[kWarps];
+  unsigned long long wu[kWarps];
+  ArgMax wa[kWarps];
+  uint32_t wscan[kWarps];
+  // values published to the other CTAs of the cluster
+  float cl_max, cl_sum;
+  unsigned long long cl_csum;
+  ArgMax cl_arg;
+  uint32_t cl_bad;
+  unsigned long long cl_total;
+  float cl_obs[4];
+  // N-gram coefficients of this step
+  float cu, coef[kMaxOrder];
+  const NgEntry* ent[kMaxOrder];
+};
+
+__device__ float block_max(float v, VocabShared& sh) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  v = warp_max(v);
+  if (lane == 0) sh.wf[w] = v;
+  __syncthreads();
+  float r = sh.wf[0];
+  for (int i = 1; i < kWarps; ++i) r = fmaxf(r, sh.wf[i]);
+  __syncthreads();
+  return r;
+}
+__device__ float block_sum(float v, VocabShared& sh) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  v = warp_sum(v);
+  if (lane == 0) sh.wf[w] = v;
+  __syncthreads();
+  float r = 0.f;
+  for (int i = 0; i < kWarps; ++i) r += sh.wf[i];
+  __syncthreads();
+  return r;
+}
+__device__ unsigned long long block_sum_u64(unsigned long long v, VocabShared& sh) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  v = warp_sum_u64(v);
+  if (lane == 0) sh.wu[w] = v;
+  __syncthreads();
+  unsigned long long r = 0;
+  for (int i = 0; i < kWarps; ++i) r += sh.wu[i];
+  __syncthreads();
+  return r;
+}
+__device__ ArgMax block_argmax(ArgMax a, VocabShared& sh) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o; o >>= 1) {
+    ArgMax b;
+    b.v = __shfl_xor_sync(0xffffffffu, a.v, o);
+    b.i = __shfl_xor_sync(0xffffffffu, a.i, o);
+    a = better(a, b);
+  }
+  if (lane == 0) sh.wa[w] = a;
+  __syncthreads();
+  ArgMax r = sh.wa[0];
+  for (int i = 1; i < kWarps; ++i) r = better(r, sh.wa[i]);
+  __syncthreads();
+  return r;
+}
+// Exclusive scan of one uint32 per thread over the CTA; returns the CTA total.
+__device__ uint32_t block_excl_scan(uint32_t v, uint32_t& excl, VocabShared& sh) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  uint32_t inc = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t t = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += t;
+  }
+  if (lane == 31) sh.wscan[w] = inc;
+  __syncthreads();
+  uint32_t before = 0, total = 0;
+  for (int i = 0; i < kWarps; ++i) {
+    if (i < w) before += sh.wscan[i];
+    total += sh.wscan[i];
+  }
+  __syncthreads();
+  excl = before + inc - v;
+  return total;
+}
+
+// Quantise the E binary32 probabilities of this thread (positions v0..v0+E-1
+// of a row of V) into counts and, optionally, write the row's CDF and / or
+// the interval of symbol `want`.  All CTAs of the cluster call this together.
+template <int E>
+__device__ void quantise_scan(const float (&p)[E], int v0, int V, int log2T, uint32_t floor_c,
+                              uint32_t* cdf_row, int want, uint32_t* interval_out,
+                              int32_t* status, cg::cluster_group& cl, VocabShared& sh) {
+  const uint32_t T = 1u << log2T;
+  const uint32_t K = T - (uint32_t)V * floor_c;
+  uint32_t c[E];
+  bool bad = false;
+  unsigned long long csum = 0;
+  ArgMax am{-INFINITY, 0x7fffffff};
+#pragma unroll
+  for (int i = 0; i < E; ++i) {
+    const int v = v0 + i;
+    if (v < V) {
+      const uint32_t q = floor_prod(p[i], K, bad);
+      c[i] = q > floor_c ? q : floor_c;
+      csum += c[i];
+      if (p[i] > am.v) am = ArgMax{p[i], v};   // strict: keeps the first maximum
+      bad |= !(p[i] == p[i]);
+    } else {
+      c[i] = 0;
+    }
+  }
+  csum = block_sum_u64(csum, sh);
+  am = block_argmax(am, sh);
+  const int anybad = __syncthreads_or(bad);
+  if (threadIdx.x == 0) {
+    sh.cl_csum = csum;
+    sh.cl_arg = am;
+    sh.cl_bad = anybad;
+  }
+  cl.sync();
+  unsigned long long total = 0;
+  ArgMax g{-INFINITY, 0x7fffffff};
+  uint32_t gbad = 0;
+  for (int r = 0; r < kVocabCluster; ++r) {
+    const VocabShared* o = cl.map_shared_rank(&sh, r);
+    total += o->cl_csum;
+    g = better(g, o->cl_arg);
+    gbad |= o->cl_bad;
+  }
+  const long long resid = (long long)T - (long long)total;
+  bool under = false;
+#pragma unroll
+  for (int i = 0; i < E; ++i) {
+    if (v0 + i == g.i) {
+      const long long ci = (long long)c[i] + resid;
+      if (ci < (long long)floor_c || ci > (long long)T) under = true;
+      c[i] = (uint32_t)ci;
+    }
+  }
+  if ((gbad || under) && status) atomicOr(status, ST_NUMERIC);
+  // exclusive prefix sum: thread-local, CTA, then the CTAs of lower rank
+  uint32_t local[E];
+  uint32_t run = 0;
+#pragma unroll
+  for (int i = 0; i < E; ++i) {
+    local[i] = run;
+    run += c[i];
+  }
+  uint32_t excl;
+  const uint32_t cta_total = block_excl_scan(run, excl, sh);
+  if (threadIdx.x == 0) sh.cl_total = cta_total;
+  cl.sync();
+  uint32_t off = 0;
+  for (int r = 0; r < (int)cl.block_rank(); ++r) off += (uint32_t)cl.map_shared_rank(&sh, r)->cl_total;
+  if (cdf_row) {
+#pragma unroll
+    for (int i = 0; i < E; ++i)
+      if (v0 + i < V) cdf_row[v0 + i] = off + excl + local[i];
+    if (v0 <= V - 1 && V - 1 < v0 + E) cdf_row[V] = T;
+  }
+  if (interval_out && want >= v0 && want < v0 + E) {
+#pragma unroll
+    for (int i = 0; i < E; ++i) {
+      if (v0 + i == want) {
+        interval_out[0] = off + excl + local[i];
+        interval_out[1] = off + excl + local[i] + c[i];
+      }
+    }
+  }
+  cl.sync();   // keep shared memory alive until every CTA has read it
+}
+
+template <int E>
+__device__ __forceinline__ void load_run(const float* src, int v0, int V, float (&out)[E], float fill) {
+  if (v0 + E <= V && (reinterpret_cast<uintptr_t>(src + v0) & 15) == 0) {
+    const float4* s4 = reinterpret_cast<const float4*>(src + v0);
+#pragma unroll
+    for (int q = 0; q < E / 4; ++q) {
+      const float4 u = s4[q];
+      out[4 * q] = u.x;
+      out[4 * q + 1] = u.y;
+      out[4 * q + 2] = u.z;
+      out[4 * q + 3] = u.w;
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < E; ++i) out[i] = (v0 + i < V) ? src[v0 + i] : fill;
+  }
+}
+template <int E>
+__device__ __forceinline__ void store_run(float* dst, int v0, int V, const float (&in)[E]) {
+  if (v0 + E <= V && (reinterpret_cast<uintptr_t>(dst + v0) & 15) == 0) {
+    float4* d4 = reinterpret_cast<float4*>(dst + v0);
+#pragma unroll
+    for (int q = 0; q < E / 4; ++q) d4[q] = make_float4(in[4 * q], in[4 * q + 1], in[4 * q + 2], in[4 * q + 3]);
+  } else {
+#pragma unroll
+    for (int i = 0; i < E; ++i)
+      if (v0 + i < V) dst[v0 + i] = in[i];
+  }
+}
+
+// One stream per cluster.  predict: p -> counts -> CDF / interval of the
+// observed token.  update: head and mixer update with the observed token.
+// Both may run in one pass (encoder) or in two (decoder, which learns the
+// token in between); the arithmetic is the same in either case.
+template <int E>
+__global__ void __cluster_dims__(kVocabCluster, 1, 1) __launch_bounds__(kVocabThreads)
+    k_vocab(Dims D, Batch b, VocabIO io) {
+  extern __shared__ float4 dyn4[];
+  float* sp = reinterpret_cast<float*>(dyn4);    // sparse N-gram mass of this CTA's chunk
+  __shared__ VocabShared sh;
+  cg::cluster_group cl = cg::this_cluster();
+  const int j = blockIdx.x / kVocabCluster;
+  if (j >= *b.nB) return;                        // uniform across the cluster
+  const int rank = (int)cl.block_rank();
+  StreamDev& st = b.st[b.slots[j]];
+  const int V = D.V;
+  const int chunk = kVocabThreads * E;
+  const int base = rank * chunk;
+  const int v0 = base + threadIdx.x * E;
+  const int i_tok = st.n_coded + 1;              // 1-based index of the token being coded
+  const float th0 = st.theta[0], th1 = st.theta[1];
+  const int t_obs = (io.update || io.intervals) ? b.obs[j] : -1;
+  if (io.update && (t_obs < 0 || t_obs >= V)) {   // rejected on the host; never index with it
+    if (rank == 0 && threadIdx.x == 0) atomicOr(&st.status, ST_BAD_TOKEN);
+    return;
+  }
+
+  // ---- biased logits s = z / tau + b
+  float s[E], bias[E];
+  load_run<E>(st.z, v0, V, s, -INFINITY);
+  if (io.probe_z) store_run<E>(io.probe_z + (size_t)j * V, v0, V, s);
+  if (D.use_head) {
+    load_run<E>(st.bias, v0, V, bias, 0.f);
+  } else {
+#pragma unroll
+    for (int i = 0; i < E; ++i) bias[i] = 0.f;
+  }
+#pragma unroll
+  for (int i = 0; i < E; ++i) s[i] = (v0 + i < V) ? __fdiv_rn(s[i], D.tau) + bias[i] : -INFINITY;
+
+  // ---- softmax: max and sum of exp in a fixed order
+  float mx = -INFINITY;
+#pragma unroll
+  for (int i = 0; i < E; ++i) mx = fmaxf(mx, s[i]);
+  mx = block_max(mx, sh);
+  if (threadIdx.x == 0) sh.cl_max = mx;
+  cl.sync();
+  float M = -INFINITY;
+  for (int r = 0; r < kVocabCluster; ++r) M = fmaxf(M, cl.map_shared_rank(&sh, r)->cl_max);
+  float e[E];
+  float ls = 0.f;
+#pragma unroll
+  for (int i = 0; i < E; ++i) {
+    e[i] = (v0 + i < V) ? expf(s[i] - M) : 0.f;
+    ls += e[i];
+  }
+  ls = block_sum(ls, sh);
+  if (threadIdx.x == 0) sh.cl_sum = ls;
+  cl.sync();
+  float S = 0.f;
+  for (int r = 0; r < kVocabCluster; ++r) S += cl.map_shared_rank(&sh, r)->cl_sum;
+  float pt[E];
+#pragma unroll
+  for (int i = 0; i < E; ++i) pt[i] = __fdiv_rn(e[i], S);
+  if (io.probe_pt) store_run<E>(io.probe_pt + (size_t)j * V, v0, V, pt);
+
+  // ---- N-gram: P = A (c + 1) / (N + V) + sum_k beta_k cnt_k / n_k, the closed
+  // form of the interpolation recursion with lambda_k = n_k / (n_k + 5).
+  float png[E];
+  const bool ngram = D.order > 0;
+  if (ngram) {
+    if (threadIdx.x == 0) {
+      float lam[kMaxOrder], nk[kMaxOrder];
+      for (int k = 0; k < kMaxOrder; ++k) {
+        const int ei = (k < D.order) ? st.ctx_ent[k] : -1;
+        const NgEntry* en = ei >= 0 ? st.ent[k] + ei : nullptr;
+        sh.ent[k] = en;
+        nk[k] = en ? (float)en->n : 0.f;
+        lam[k] = en ? nk[k] / (nk[k] + 5.0f) : 0.f;
+      }
+      float A = 1.f;
+      for (int k = 0; k < kMaxOrder; ++k) A *= (1.f - lam[k]);
+      for (int k = 0; k < kMaxOrder; ++k) {
+        float beta = lam[k];
+        for (int q = k + 1; q < kMaxOrder; ++q) beta *= (1.f - lam[q]);
+        sh.coef[k] = sh.ent[k] ? beta / nk[k] : 0.f;
+      }
+      sh.cu = A / (float)(st.N + V);
+    }
+    for (int i = threadIdx.x; i < chunk; i += kVocabThreads) sp[i] = 0.f;
+    __syncthreads();
+    for (int k = 0; k < kMaxOrder; ++k) {
+      const NgEntry* en = sh.ent[k];
+      if (en) {
+        const int ns = en->nslots;
+        for (int q = threadIdx.x; q < ns; q += kVocabThreads) {
+          const int t = en->tok[q] - base;
+          if (t >= 0 && t < chunk) sp[t] += sh.coef[k] * (float)en->cnt[q];
+        }
+      }
+      __syncthreads();
+    }
+    int cnt[E];
+    if (v0 + E <= V && (reinterpret_cast<uintptr_t>(st.uni + v0) & 15) == 0) {
+      const int4* u4 = reinterpret_cast<const int4*>(st.uni + v0);
+#pragma unroll
+      for (int q = 0; q < E / 4; ++q) {
+        const int4 u = u4[q];
+        cnt[4 * q] = u.x;
+        cnt[4 * q + 1] = u.y;
+        cnt[4 * q + 2] = u.z;
+        cnt[4 * q + 3] = u.w;
+      }
+    } else {
+#pragma unroll
+      for (int i = 0; i < E; ++i) cnt[i] = (v0 + i < V) ? st.uni[v0 + i] : 0;
+    }
+    const float cu = sh.cu;
+#pragma unroll
+    for (int i = 0; i < E; ++i) png[i] = (v0 + i < V) ? cu * (float)(cnt[i] + 1) + sp[threadIdx.x * E + i] : 0.f;
+    if (io.probe_png) store_run<E>(io.probe_png + (size_t)j * V, v0, V, png);
+  } else {
+#pragma unroll
+    for (int i = 0; i < E; ++i) png[i] = 0.f;
+  }
+
+  // ---- mix (Sec. 3.5): LLM alone during warm-up
+  const bool mixing = ngram && i_tok > D.warmup;
+  const float tm = fmaxf(th0, th1);
+  const float e0 = expf(th0 - tm), e1 = expf(th1 - tm);
+  const float w0 = e0 / (e0 + e1), w1 = e1 / (e0 + e1);
+  float p[E];
+#pragma unroll
+  for (int i = 0; i < E; ++i) p[i] = mixing ? w0 * pt[i] + w1 * png[i] : pt[i];
+  if (io.probe_p) store_run<E>(io.probe_p + (size_t)j * V, v0, V, p);
+
+  if (io.predict) {
+    uint32_t* cdf_row = io.cdf ? io.cdf + (size_t)j * (V + 1) : nullptr;
+    uint32_t* iv = nullptr;
+    if (io.intervals) iv = io.intervals + 2 * ((size_t)j * io.interval_stride + st.n_coded);
+    quantise_scan<E>(p, v0, V, D.log2T, D.floor, cdf_row, t_obs, iv, &st.status, cl, sh);
+  }
+
+  if (io.update) {
+    // the CTA owning t* publishes p_tilde(t*), p_ng(t*) and log p_tilde(t*)
+    const int owner = t_obs / chunk;
+    if (t_obs >= v0 && t_obs < v0 + E) {
+#pragma unroll
+      for (int i = 0; i < E; ++i) {
+        if (v0 + i == t_obs) {
+          sh.cl_obs[0] = pt[i];
+          sh.cl_obs[1] = png[i];
+          sh.cl_obs[2] = s[i] - M - logf(S);
+        }
+      }
+    }
+    cl.sync();
+    const VocabShared* o = cl.map_shared_rank(&sh, owner);
+    const float pts = o->cl_obs[0], pngs = o->cl_obs[1], lpt = o->cl_obs[2];
+    float scale = 1.f;
+    float nth0 = th0, nth1 = th1;
+    if (D.rule == NC_RULE_MIXED_NLL) {
+      if (mixing) {
+        const float pm = w0 * pts + w1 * pngs;
+        scale = w0 * pts / pm;
+        nth0 = th0 - D.alpha * (w0 - w0 * pts / pm);
+        nth1 = th1 - D.alpha * (w1 - w1 * pngs / pm);
+      }
+    } else if (mixing) {
+      const float a0 = th0 + D.eta * lpt, a1 = th1 + D.eta * logf(pngs);
+      const float am = fmaxf(a0, a1);
+      const float lse = am + logf(expf(a0 - am) + expf(a1 - am));
+      nth0 = a0 - lse;
+      nth1 = a1 - lse;
+    }
+    if (D.use_head) {
+      const float step = D.alpha * scale;
+#pragma unroll
+      for (int i = 0; i < E; ++i) bias[i] = bias[i] - step * (pt[i] - (v0 + i == t_obs ? 1.f : 0.f));
+      store_run<E>(st.bias, v0, V, bias);
+    }
+    if (rank == 0 && threadIdx.x == 0) {
+      st.theta[0] = nth0;
+      st.theta[1] = nth1;
+      st.pt_obs = pts;
+      st.png_obs = pngs;
+    }
+    cl.sync();
+  }
+}
+
+// --------------------------------------------------------------- N-gram tables
+__device__ __forceinline__ unsigned long long mix64(unsigned long long x) {
+  x ^= x >> 33;
+  x *= 0xff51afd7ed558ccdull;
+  x ^= x >> 33;
+  x *= 0xc4ceb9fe1a85ec53ull;
+  x ^= x >> 33;
+  return x;
+}
+
+// Context of length k ending at the most recent token: ids < 2^16 packed
+// injectively into 48 bits.
+__device__ __forceinline__ unsigned long long ctx_key(const int32_t* hist, int k) {
+  unsigned long long key = 0;
+  for (int q = 3 - k; q < 3; ++q) key = (key << 16) | (unsigned long long)(uint32_t)hist[q];
+  return key;
+}
+
+// Find (insert = false) or find-or-insert a context; returns the entry index
+// or -1 (absent, or table full on insert).  Linear probing, bounded by the
+// capacity.
+__device__ int ng_find(StreamDev& st, int k, unsigned long long key, bool insert) {
+  const int cap = st.cap_mask + 1;
+  unsigned long long* keys = st.keys[k];
+  int h = (int)(mix64(key) & (unsigned long long)st.cap_mask);
+  for (int probe = 0; probe < cap; ++probe) {
+    const unsigned long long kk = keys[h];
+    if (kk == key) return st.idx[k][h];
+    if (kk == kEmptyKey) {
+      if (!insert) return -1;
+      const int ei = st.n_ent[k];
+      if (ei >= st.max_len) {
+        st.status |= ST_TABLE_FULL;
+        return -1;
+      }
+      st.n_ent[k] = ei + 1;
+      keys[h] = key;
+      st.idx[k][h] = ei;
+      st.ent[k][ei].nslots = 0;
+      st.ent[k][ei].n = 0;
+      return ei;
+    }
+    h = (h + 1) & st.cap_mask;
+  }
+  if (insert) st.status |= ST_TABLE_FULL;
+  return -1;
+}
+
+// One warp per stream: count the observed token in every context order,
+// the unigram counts, then advance the stream (window, history, position) and
+// look up the contexts of the next prediction.
+__global__ void k_ngram_update(Dims D, Batch b) {
+  const int j = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (j >= *b.nB) return;
+  StreamDev& st = b.st[b.slots[j]];
+  const int t = b.obs[j];
+  if (t < 0 || t >= D.V) {
+    if (lane == 0) st.status |= ST_BAD_TOKEN;
+    return;
+  }
+  const int nh = min(3, st.n_coded);
+  for (int k = 0; k < min(D.order, nh); ++k) {
+    int ei = 0;
+    if (lane == 0) ei = ng_find(st, k, ctx_key(st.hist, k + 1), true);
+    ei = __shfl_sync(0xffffffffu, ei, 0);
+    if (ei < 0) continue;
+    NgEntry& en = st.ent[k][ei];
+    const int ns = en.nslots;
+    int hit = -1;
+    for (int q = lane; q < ns; q += 32)
+      if (en.tok[q] == t) hit = q;
+    unsigned m = __ballot_sync(0xffffffffu, hit >= 0);
+    if (m) {
+      const int src = __ffs(m) - 1;
+      const int q = __shfl_sync(0xffffffffu, hit, src);
+      if (lane == 0) {
+        en.cnt[q] += 1;
+        en.n += 1;
+      }
+    } else if (ns < kMaxSlots) {
+      if (lane == 0) {
+        en.tok[ns] = t;
+        en.cnt[ns] = 1;
+        en.nslots = ns + 1;
+        en.n += 1;
+      }
+    } else {
+      // evict the lowest count, lowest slot index on ties
+      int bc = 0x7fffffff, bi = 0x7fffffff;
+      for (int q = lane; q < kMaxSlots; q += 32) {
+        const int cq = en.cnt[q];
+        if (cq < bc || (cq == bc && q < bi)) {
+          bc = cq;
+          bi = q;
+        }
+      }
+#pragma unroll
+      for (int o = 16; o; o >>= 1) {
+        const int oc = __shfl_xor_sync(0xffffffffu, bc, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (oc < bc || (oc == bc && oi < bi)) {
+          bc = oc;
+          bi = oi;
+        }
+      }
+      if (lane == 0) {
+        en.n += 1 - en.cnt[bi];
+        en.tok[bi] = t;
+        en.cnt[bi] = 1;
+      }
+    }
+    __syncwarp();
+  }
+  if (lane == 0) {
+    if (D.order > 0) {
+      st.uni[t] += 1;
+      st.N += 1;
+    }
+    st.hist[0] = st.hist[1];
+    st.hist[1] = st.hist[2];
+    st.hist[2] = t;
+    int start = st.kv_start;
+    if (st.n_coded - start == D.L) start += D.C;
+    st.kv_start = start;
+    st.n_coded += 1;
+    st.last_tok = t;
+    const int nh2 = min(3, st.n_coded);
+    for (int k = 0; k < kMaxOrder; ++k)
+      st.ctx_ent[k] = (k < D.order && k < nh2) ? ng_find(st, k, ctx_key(st.hist, k + 1), false) : -1;
+  }
+}
+
+// Encoder driver: row j is active while its stream has tokens left; rows are
+// sorted by length (longest first), so the active rows are a prefix.
+__global__ void k_prepare_encode(Batch b, int n_streams, const int32_t* tok_flat,
+                                 const int64_t* offs, const int64_t* lens, int32_t* obs,
+                                 int32_t* nB) {
+  __shared__ int cnt[32];
+  int mine = 0;
+  for (int j = threadIdx.x; j < n_streams; j += blockDim.x) {
+    const int nc = b.st[b.slots[j]].n_coded;
+    const bool act = nc < lens[j];
+    obs[j] = act ? tok_flat[offs[j] + nc] : 0;
+    mine += act;
+  }
+  for (int o = 16; o; o >>= 1) mine += __shfl_xor_sync(0xffffffffu, mine, o);
+  if ((threadIdx.x & 31) == 0) cnt[threadIdx.x >> 5] = mine;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int tot = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += cnt[w];
+    *nB = tot;
+  }
+}
+
+// Standalone quantiser over rows of binary32 probabilities.
+template <int E>
+__global__ void __cluster_dims__(kVocabCluster, 1, 1) __launch_bounds__(kVocabThreads)
+    k_probs_to_cdf(const float* p, int V, int log2T, uint32_t floor_c, uint32_t* cdf,
+                   int32_t* status) {
+  __shared__ VocabShared sh;
+  cg::cluster_group cl = cg::this_cluster();
+  const int j = blockIdx.x / kVocabCluster;
+  const int rank = (int)cl.block_rank();
+  const int v0 = rank * kVocabThreads * E + threadIdx.x * E;
+  float pr[E];
+  load_run<E>(p + (size_t)j * V, v0, V, pr, 0.f);
+  quantise_scan<E>(pr, v0, V, log2T, floor_c, cdf + (size_t)j * (V + 1), -1, nullptr, status + j,
+                   cl, sh);
+}
+
+__global__ void k_floor_counts(const float* p, int64_t n, uint32_t K, uint32_t floor_c,
+                               uint32_t* c) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    bool bad = false;
+    const uint32_t q = floor_prod(p[i], K, bad);
+    c[i] = bad ? 0xFFFFFFFFu : (q > floor_c ? q : floor_c);
+  }
+}
+
+// Mixed-distribution NLL forward / backward, one CTA per row.
+__global__ void __launch_bounds__(kVocabThreads)
+    k_mix_nll(const float* z, const float* bv, const float* png, const float* theta,
+              const int32_t* target, const int32_t* warm, const float* gout, int V, float tau,
+              float* loss, float* db, float* dth) {
+  __shared__ VocabShared sh;
+  const int j = blockIdx.x;
+  const float* zr = z + (size_t)j * V;
+  const float* br = bv + (size_t)j * V;
+  const int t = target[j];
+  if (t < 0 || t >= V) {     // out-of-range target: NaN loss and gradients
+    for (int v = threadIdx.x; v < V && db; v += kVocabThreads) db[(size_t)j * V + v] = NAN;
+    if (threadIdx.x == 0) {
+      if (loss) loss[j] = NAN;
+      if (dth) dth[2 * j] = dth[2 * j + 1] = NAN;
+    }
+    return;
+  }
+  float mx = -INFINITY;
+  for (int v = threadIdx.x; v < V; v += kVocabThreads) mx = fmaxf(mx, __fdiv_rn(zr[v], tau) + br[v]);
+  const float M = block_max(mx, sh);
+  float ls = 0.f;
+  for (int v = threadIdx.x; v < V; v += kVocabThreads) ls += expf(__fdiv_rn(zr[v], tau) + br[v] - M);
+  const float S = block_sum(ls, sh);
+  const float pts = __fdiv_rn(expf(__fdiv_rn(zr[t], tau) + br[t] - M), S);
+  const float pngs = png[(size_t)j * V + t];
+  const float th0 = theta[2 * j], th1 = theta[2 * j + 1];
+  const float tm = fmaxf(th0, th1);
+  const float e0 = expf(th0 - tm), e1 = expf(th1 - tm);
+  const float w0 = e0 / (e0 + e1), w1 = e1 / (e0 + e1);
+  const bool wu = warm[j] != 0;
+  const float pm = wu ? pts : w0 * pts + w1 * pngs;
+  const float g = gout ? gout[j] : 1.f;
+  if (loss && threadIdx.x == 0) loss[j] = -logf(pm);
+  if (db) {
+    const float rho = wu ? 1.f : w0 * pts / pm;
+    for (int v = threadIdx.x; v < V; v += kVocabThreads) {
+      const float ptv = __fdiv_rn(expf(__fdiv_rn(zr[v], tau) + br[v] - M), S);
+      db[(size_t)j * V + v] = g * rho * (ptv - (v == t ? 1.f : 0.f));
+    }
+  }
+  if (dth && threadIdx.x == 0) {
+    dth[2 * j] = wu ? 0.f : g * (w0 - w0 * pts / pm);
+    dth[2 * j + 1] = wu ? 0.f : g * (w1 - w1 * pngs / pm);
+  }
+}
+
+// One warp per row: binary search of the decoder's target count in the CDF.
+__global__ void k_search(Batch b, int V, const uint32_t* cdf, const uint32_t* target, int32_t* obs,
+                         uint32_t* lohi) {
+  const int j = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (j >= *b.nB || lane != 0) return;
+  const uint32_t* row = cdf + (size_t)j * (V + 1);
+  const uint32_t t = target[j];
+  int lo = 0, hi = V - 1;                // largest s with row[s] <= t
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (row[mid] <= t)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  obs[j] = lo;
+  lohi[2 * j] = row[lo];
+  lohi[2 * j + 1] = row[lo + 1];
+}
+
+}  // namespace
+
+static int vocab_E(int V) {
+  const int per = kVocabCluster * kVocabThreads;
+  int e = (V + per - 1) / per;
+  e = (e + 3) / 4 * 4;
+  return e < 4 ? 4 : e;
+}
+
+template <int E>
+static cudaError_t vocab_t(const Dims& D, const Batch& b, const VocabIO& io, cudaStream_t s) {
+  const size_t smem = (size_t)kVocabThreads * E * sizeof(float);
+  cudaError_t e = cudaFuncSetAttribute(k_vocab<E>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k_vocab<E><<<b.Bmax * kVocabCluster, kVocabThreads, smem, s>>>(D, b, io);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_vocab(const Dims& D, const Batch& b, const VocabIO& io, cudaStream_t s) {
+  switch (vocab_E(D.V)) {
+    case 4: return vocab_t<4>(D, b, io, s);
+    case 8: return vocab_t<8>(D, b, io, s);
+    case 12: return vocab_t<12>(D, b, io, s);
+    case 16: return vocab_t<16>(D, b, io, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_ngram_update(const Dims& D, const Batch& b, cudaStream_t s) {
+  const int threads = 128;
+  const int blocks = (b.Bmax * 32 + threads - 1) / threads;
+  k_ngram_update<<<blocks, threads, 0, s>>>(D, b);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_prepare_encode(const Batch& b, int n_streams, const int32_t* tok_flat,
+                                  const int64_t* offs, const int64_t* lens, int32_t* obs,
+                                  int32_t* nB, cudaStream_t s) {
+  k_prepare_encode<<<1, 1024, 0, s>>>(b, n_streams, tok_flat, offs, lens, obs, nB);
+  return cudaGetLastError();
+}
+
+template <int E>
+static cudaError_t p2c_t(const float* p, int n, int V, int log2T, uint32_t floor_c, uint32_t* cdf,
+                         int32_t* status, cudaStream_t s) {
+  k_probs_to_cdf<E><<<n * kVocabCluster, kVocabThreads, 0, s>>>(p, V, log2T, floor_c, cdf, status);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_probs_to_cdf(const float* p, int n, int V, int log2T, uint32_t floor_c,
+                                uint32_t* cdf, int32_t* status, cudaStream_t s) {
+  switch (vocab_E(V)) {
+    case 4: return p2c_t<4>(p, n, V, log2T, floor_c, cdf, status, s);
+    case 8: return p2c_t<8>(p, n, V, log2T, floor_c, cdf, status, s);
+    case 12: return p2c_t<12>(p, n, V, log2T, floor_c, cdf, status, s);
+    case 16: return p2c_t<16>(p, n, V, log2T, floor_c, cdf, status, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_floor_counts(const float* p, int64_t n, uint32_t K, uint32_t floor_c,
+                                uint32_t* c, cudaStream_t s) {
+  const int64_t blocks = (n + 255) / 256;
+  k_floor_counts<<<(unsigned)(blocks < 152 * 64 ? (blocks > 0 ? blocks : 1) : 152 * 64), 256, 0, s>>>(p, n, K, floor_c, c);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_search(const Batch& b, int V, const uint32_t* cdf, const uint32_t* target,
+                          int32_t* obs, uint32_t* lohi, cudaStream_t s) {
+  const int threads = 128;
+  const int blocks = (b.Bmax * 32 + threads - 1) / threads;
+  k_search<<<blocks, threads, 0, s>>>(b, V, cdf, target, obs, lohi);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mix_nll(const float* z, const float* b, const float* png, const float* theta,
+                           const int32_t* target, const int32_t* warm, const float* gout, int n,
+                           int V, float tau, float* loss, float* db, float* dtheta,
+                           cudaStream_t s) {
+  k_mix_nll<<<n, kVocabThreads, 0, s>>>(z, b, png, theta, target, warm, gout, V, tau, loss, db, dtheta);
+  return cudaGetLastError();
+}
+
+}  // namespace nc

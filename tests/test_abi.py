@@ -1,0 +1,104 @@
+"""CPU tests of the C ABI: the library loads and exports every declared
+entry point, host-only calls (coder, container parsing, argument checks)
+agree with the oracle, and nothing here touches a GPU."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+import synthetic as S
+from oracle.coder import Decoder, Encoder
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def nc24():
+    from paper_2602_19626_gb300 import build
+    build.build()
+    from paper_2602_19626_gb300 import nc24 as m
+    return m
+
+
+def declared_symbols():
+    hdr = open(os.path.join(ROOT, "include", "nc24.h")).read()
+    hdr = re.sub(r"/\*.*?\*/", "", hdr, flags=re.S)
+    return sorted(set(re.findall(r"\b(nc_[a-z0-9_]+)\s*\(", hdr)))
+
+
+def test_exports_every_declared_symbol(nc24):
+    decl = declared_symbols()
+    assert len(decl) >= 20
+    for name in decl:
+        assert hasattr(nc24.lib, name), name
+    assert sorted(nc24.EXPORTED) == decl
+
+
+def test_config_default_and_status(nc24):
+    c = nc24.nc_config_default()
+    assert (c.n_layers, c.d_model, c.n_heads, c.n_kv_heads, c.d_ffn, c.vocab) == (30, 576, 9, 3, 1536, 49152)
+    assert (c.ctx_len, c.slide, c.cdf_log2_total, c.floor, c.warmup) == (2048, 512, 24, 1, 100)
+    assert abs(c.bias_lr - 1e-3) < 1e-9 and abs(c.w_llm_init - 0.85) < 1e-7
+    assert nc24.nc_status_str(nc24.NC_ENUMERIC) == "NC_ENUMERIC"
+
+
+def test_ctx_create_rejects_bad_config_without_gpu(nc24):
+    import ctypes as C
+    c = nc24.nc_config_default()
+    w = np.zeros(4, dtype=np.float32)
+    h = C.c_void_p()
+    assert nc24.lib.nc_ctx_create(C.byref(c), w.ctypes.data, w.nbytes, C.byref(h)) == nc24.NC_EINVAL
+    c.d_model = 100
+    assert nc24.lib.nc_ctx_create(C.byref(c), w.ctypes.data, w.nbytes, C.byref(h)) == nc24.NC_EINVAL
+    assert not h.value
+
+
+@pytest.mark.parametrize("log2T", [8, 16, 24])
+def test_host_coder_matches_oracle(nc24, log2T):
+    T = 1 << log2T
+    rng = np.random.default_rng(log2T)
+    n = 3000
+    lo = np.empty(n, np.uint32)
+    hi = np.empty(n, np.uint32)
+    V = 37
+    cdfs = np.empty((n, V + 1), np.uint32)
+    for i in range(n):
+        c = rng.multinomial(T - V, rng.dirichlet(np.full(V, 0.2))) + 1
+        cdf = np.concatenate([[0], np.cumsum(c)]).astype(np.uint32)
+        s = int(rng.integers(V))
+        cdfs[i] = cdf
+        lo[i], hi[i] = cdf[s], cdf[s + 1]
+    data, nbits = nc24.nc_ac_encode(lo, hi, log2T)
+    enc = Encoder(T)
+    for a, b in zip(lo, hi):
+        enc.encode_interval(int(a), int(b))
+    ref, ref_bits = enc.finish()
+    assert nbits == ref_bits and data == ref
+    sym = nc24.nc_ac_decode(data, nbits, cdfs, log2T)
+    dec = Decoder(ref, ref_bits, T)
+    ref_sym = [dec.decode(c) for c in cdfs]
+    assert list(sym) == ref_sym
+    assert np.all(cdfs[np.arange(n), sym] == lo)
+
+
+def test_host_coder_rejects_bad_input(nc24):
+    with pytest.raises(nc24.NcError):
+        nc24.nc_ac_encode(np.array([5], np.uint32), np.array([5], np.uint32), 8)
+    with pytest.raises(nc24.NcError):
+        nc24.nc_ac_encode(np.array([0], np.uint32), np.array([257], np.uint32), 8)
+    bad = np.array([[0, 3, 2, 256]], np.uint32)
+    with pytest.raises(nc24.NcError):
+        nc24.nc_ac_decode(b"\x00", 8, np.array([[0, 3, 3, 255]], np.uint32), 8)
+
+
+def test_container_parse(nc24):
+    import ctypes as C
+    from oracle import container
+    buf = container.pack(3, 1.0, 1, [(10, 33, 5), (0, 1, 1)], [b"abcde", b"\x80"])
+    arr = np.frombuffer(buf, np.uint8).copy()
+    n = C.c_int(0)
+    assert nc24.lib.nc_container_streams(arr.ctypes.data, arr.size, C.byref(n)) == 0 and n.value == 2
+    for cut in (arr[:-1], arr[:9], np.concatenate([arr, [0]]).astype(np.uint8)):
+        cut = np.ascontiguousarray(cut)
+        assert nc24.lib.nc_container_streams(cut.ctypes.data, cut.size, C.byref(n)) == nc24.NC_ECORRUPT

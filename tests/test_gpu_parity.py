@@ -1,0 +1,312 @@
+"""GPU parity of the CUDA path against the FP64 oracle, through the C ABI.
+
+Bars: integer work (quantiser, CDF, coder, N-gram counts) bit-exact; logits
+within 1e-4 (FP32 weights) / 3e-2 (BF16 weights) of the oracle on FP32
+weights; bits per token within 0.5% of the oracle's.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import synthetic as S
+from oracle import cdf as Q
+from oracle.compress import StepConfig, StreamState, compress_stream
+from oracle.model import Model
+
+pytestmark = pytest.mark.gpu
+
+T24 = 1 << 24
+
+
+@pytest.fixture(scope="module")
+def nc(gpu_lib):
+    return gpu_lib
+
+
+def u32(t):
+    return t.cpu().numpy().view(np.uint32).astype(np.int64)
+
+
+# ------------------------------------------------------------ quantiser
+
+def test_floor_counts_exhaustive(nc):
+    """Every binary32 in [0, 1]: the GPU's exact product floor equals the
+    oracle's for K = 2^24 - 49,152 (and a second K)."""
+    chunk = 1 << 26
+    end = 0x3F800000 + 1
+    dev_c = torch.empty(chunk, dtype=torch.int32, device="cuda")
+    for K in (T24 - 49152, (1 << 16) - 49152):
+        for start in range(0, end, chunk):
+            n = min(chunk, end - start)
+            bits = torch.arange(start, start + n, dtype=torch.int64, device="cuda").to(torch.int32)
+            p = bits.view(torch.float32)
+            assert nc.nc_floor_counts(p, K, 1, dev_c[:n]) == 0
+            got = dev_c[:n].cpu().numpy().view(np.uint32)
+            pc = np.arange(start, start + n, dtype=np.uint32).view(np.float32)
+            want = Q.floor_counts(pc, K, 1)
+            bad = np.nonzero(got != want)[0]
+            assert bad.size == 0, (K, start + int(bad[0]))
+
+
+def _rows(V, rng):
+    rows = []
+    rows.append(np.full(V, np.float32(1.0) / np.float32(V), np.float32))          # uniform
+    oh = np.zeros(V, np.float32)
+    oh[V // 3] = 1.0
+    rows.append(oh)                                                              # one-hot
+    rows.append(rng.dirichlet(np.full(V, 0.05)).astype(np.float32))              # sparse-ish
+    z = rng.normal(0, 3, V)
+    e = np.exp(z - z.max())
+    rows.append((e / e.sum()).astype(np.float32))                                # peaked
+    tie = np.zeros(V, np.float32)
+    tie[[1, V // 2, V - 1]] = np.float32(1.0 / 3.0)
+    rows.append(tie)                                                             # ties
+    return np.stack(rows)
+
+
+@pytest.mark.parametrize("V", [49152, 1000, 50001, 97])
+@pytest.mark.parametrize("log2T", [24, 16])
+def test_probs_to_cdf_bit_exact(nc, V, log2T):
+    if V >= (1 << log2T):
+        pytest.skip("floors exceed the total")
+    rng = np.random.default_rng(V + log2T)
+    P = _rows(V, rng)
+    p = torch.from_numpy(P).cuda()
+    cdf = torch.empty(P.shape[0], V + 1, dtype=torch.int32, device="cuda")
+    assert nc.nc_probs_to_cdf(p, cdf, log2T, 1) == 0
+    got = u32(cdf)
+    for i in range(P.shape[0]):
+        want = Q.probs_to_cdf(P[i], 1 << log2T, 1)
+        assert np.array_equal(got[i], want), i
+
+
+def test_probs_to_cdf_errors(nc):
+    V = 1000
+    p = np.full((2, V), np.float32(1.0 / V), np.float32)
+    p[0, 5] = np.nan
+    p[1] *= 2.0
+    cdf = torch.empty(2, V + 1, dtype=torch.int32, device="cuda")
+    assert nc.nc_probs_to_cdf(torch.from_numpy(p).cuda(), cdf, 24, 1) == nc.NC_ENUMERIC
+
+
+# ------------------------------------------------------- per-step parity
+
+def _run_steps(nc, shape, seed, fmt, n_steps, warmup, rule="paper", order=3, tok_seed=None):
+    toks = S.token_stream(seed if tok_seed is None else tok_seed, 0, n_steps, shape.vocab)
+    cfg = nc.make_config(shape, fmt=fmt, rule=rule, warmup=warmup, ngram_order=order)
+    ctx = nc.Context(cfg, S.flat_weights(shape, seed))
+    V = shape.vocab
+    bufs = {k: torch.empty(1, V, device="cuda") for k in ("z", "pt", "png", "p")}
+    cdf = torch.empty(1, V + 1, dtype=torch.int32, device="cuda")
+    ctx.stream_open(3, n_steps)
+    out = []
+    for t in toks:
+        ctx.step_probe([3], z=bufs["z"], p_tilde=bufs["pt"], p_ng=bufs["png"], p=bufs["p"], cdf_out=cdf)
+        rec = {k: v[0].cpu().numpy().copy() for k, v in bufs.items()}
+        rec["cdf"] = u32(cdf)[0]
+        out.append(rec)
+        ctx.update_bias([3], [int(t)])
+    b, th, n = ctx.stream_state(3)
+    ctx.close()
+    return toks, out, (b, th, n)
+
+
+@pytest.mark.parametrize("rule", ["paper", "mixed_nll"])
+def test_small_fp32_step_parity(nc, rule):
+    """4-layer FP32 model, 48 steps (warm-up 12, so the mix is exercised):
+    logits, p_tilde, p_ng and p against the oracle; CDF bit-exact against the
+    oracle quantiser on the GPU's binary32 p; head and mixer state after."""
+    shape, seed = S.SMALL, 0
+    toks, recs, (b, th, n) = _run_steps(nc, shape, seed, "fp32", 48, 12, rule)
+    ref = StreamState.new(Model(shape, S.weights(shape, seed), "fp32"), StepConfig(warmup=12, rule=rule))
+    zerr = 0.0
+    for t, r in zip(toks, recs):
+        ref.predict()
+        z, pt, png, p = ref._cur
+        zerr = max(zerr, float(np.max(np.abs(r["z"] - z))))
+        np.testing.assert_allclose(r["pt"], pt, rtol=2e-4, atol=1e-9)
+        np.testing.assert_allclose(r["png"], png, rtol=2e-5, atol=1e-12)
+        np.testing.assert_allclose(r["p"], p, rtol=2e-4, atol=1e-9)
+        assert np.array_equal(r["cdf"], Q.probs_to_cdf(r["p"], T24, 1))
+        ref.update(int(t))
+    assert zerr <= 1e-4, zerr
+    assert n == len(toks)
+    np.testing.assert_allclose(b, ref.head.b, rtol=0, atol=2e-6)
+    logw = ref.theta if rule == "mixed_nll" else ref.mixer.logw
+    np.testing.assert_allclose(th, logw, rtol=1e-4, atol=1e-4)
+
+
+def test_ngram_eviction_parity(nc):
+    """A context followed by more than 64 distinct continuations: the GPU's
+    p_ng (counts, eviction order, lambdas) tracks the oracle."""
+    shape = S.ModelShape(n_layers=1, d_model=64, n_heads=1, n_kv_heads=1, d_ffn=64,
+                         vocab=300, ctx_len=64, slide=16)
+    toks = []
+    for i in range(90):
+        toks += [7, 100 + (i % 80)]
+    toks = np.array(toks[:170], np.int32)
+    cfg = nc.make_config(shape, fmt="fp32", warmup=0)
+    ctx = nc.Context(cfg, S.flat_weights(shape, 1))
+    png = torch.empty(1, shape.vocab, device="cuda")
+    ctx.stream_open(0, len(toks))
+    ref = StreamState.new(Model(shape, S.weights(shape, 1)), StepConfig(warmup=0))
+    for t in toks:
+        ctx.step_probe([0], p_ng=png)
+        ref.predict()
+        np.testing.assert_allclose(png[0].cpu().numpy(), ref._cur[2], rtol=2e-5, atol=1e-12)
+        ctx.update_bias([0], [int(t)])
+        ref.update(int(t))
+    assert len(ref.ngram.tables[1][(7,)]) == 64
+    ctx.close()
+
+
+@pytest.mark.parametrize("fmt,tol_fp32,tol_fmt", [("fp32", 1e-4, 1e-4), ("bf16", 3e-2, 2e-3), ("fp8", None, 2e-3)])
+def test_full_model_logits(nc, fmt, tol_fp32, tol_fmt):
+    """30-layer SmolLM2-135M shape: logits of the first steps against the
+    oracle on the FP32 weights and on the format's dequantised weights."""
+    shape, seed = S.FULL, 1
+    toks, recs, _ = _run_steps(nc, shape, seed, fmt, 4, 100)
+    w32 = S.weights(shape, seed)
+    for ref_fmt, tol in (("fp32", tol_fp32), (fmt, tol_fmt)):
+        ref = StreamState.new(Model(shape, w32, ref_fmt), StepConfig())
+        err = 0.0
+        for t, r in zip(toks, recs):
+            ref.predict()
+            err = max(err, float(np.max(np.abs(r["z"] - ref._cur[0]))))
+            ref.update(int(t))
+        print(f"{fmt} logits vs oracle({ref_fmt}) max abs err {err:.3e}")
+        if tol is not None:
+            assert err <= tol, (ref_fmt, err)
+
+
+# --------------------------------------------------- streams and batches
+
+def test_batch_invariance(nc):
+    """Four streams of one context stepped together give bit-identical CDFs
+    to each stream stepped alone."""
+    shape, seed = S.SMALL, 2
+    streams = [S.token_stream(seed, j, 20, shape.vocab) for j in range(4)]
+    w = S.flat_weights(shape, seed)
+    cfgB = nc.make_config(shape, fmt="bf16", warmup=5, max_streams=4)
+    ctxB = nc.Context(cfgB, w)
+    for j in range(4):
+        ctxB.stream_open(j, 20)
+    batched = []
+    for k in range(20):
+        batched.append(ctxB.step_cdf(np.arange(4)).copy())
+        ctxB.update_bias(np.arange(4), [int(s[k]) for s in streams])
+    ctxB.close()
+    cfg1 = nc.make_config(shape, fmt="bf16", warmup=5, max_streams=1)
+    for j in range(4):
+        ctx1 = nc.Context(cfg1, w)
+        ctx1.stream_open(0, 20)
+        for k in range(20):
+            c = ctx1.step_cdf([0])
+            assert np.array_equal(c[0], batched[k][j]), (j, k)
+            ctx1.update_bias([0], [int(streams[j][k])])
+        ctx1.close()
+
+
+def test_roundtrip_small_config_with_slides_and_bpb(nc):
+    """Small FP32 model, one 1,024-token stream, window 512 sliding by 128:
+    lossless GPU round trip; bits within 0.5% of the oracle's."""
+    shape, seed = S.SMALL, 0
+    toks = S.token_stream(seed, 0, 1024, shape.vocab)
+    ctx = nc.Context(nc.make_config(shape, fmt="fp32"), S.flat_weights(shape, seed))
+    blob = ctx.encode([toks])
+    back = ctx.decode(blob)
+    assert np.array_equal(back[0], toks)
+    gpu_bits = int.from_bytes(blob[10 + 4:10 + 8], "little")
+    ref = compress_stream(Model(shape, S.weights(shape, seed)), toks, StepConfig())
+    assert ref["slides"] == 4
+    rel = abs(gpu_bits - ref["nbits"]) / ref["nbits"]
+    print(f"bits/token gpu {gpu_bits / 1024:.4f} oracle {ref['nbits'] / 1024:.4f} ideal {ref['ideal_bits'] / 1024:.4f} rel {rel:.2e}")
+    assert rel <= 5e-3
+    ctx.close()
+
+
+def test_multi_stream_container_ragged(nc):
+    """Ragged lengths, including empty and one-token streams, BF16."""
+    shape, seed = S.SMALL, 3
+    lens = [0, 1, 37, 300, 129]
+    streams = [S.token_stream(seed, j, n, shape.vocab) for j, n in enumerate(lens)]
+    ctx = nc.Context(nc.make_config(shape, fmt="bf16", max_streams=8, warmup=20), S.flat_weights(shape, seed))
+    blob = ctx.encode(streams)
+    assert blob[:4] == b"NC05"
+    back = ctx.decode(blob)
+    for a, b in zip(streams, back):
+        assert np.array_equal(a, b)
+    # corrupted / mismatched containers are rejected
+    with pytest.raises(nc.NcError) as e:
+        ctx.decode(blob[:-1])
+    assert e.value.status == nc.NC_ECORRUPT
+    ctx2 = nc.Context(nc.make_config(shape, fmt="bf16", max_streams=8, warmup=20, ngram_order=0),
+                      S.flat_weights(shape, seed))
+    with pytest.raises(nc.NcError) as e:
+        ctx2.decode(blob)
+    assert e.value.status == nc.NC_ECORRUPT
+    ctx.close()
+    ctx2.close()
+
+
+def test_call_order_errors(nc):
+    shape = S.SMALL
+    ctx = nc.Context(nc.make_config(shape, fmt="bf16", max_streams=2), S.flat_weights(shape, 0))
+    ctx.stream_open(1, 4)
+    ctx.step_cdf([1], prev=[-1])
+    with pytest.raises(nc.NcError) as e:
+        ctx.step_cdf([1])
+    assert e.value.status == nc.NC_ESTATE
+    with pytest.raises(nc.NcError) as e:
+        ctx.update_bias([1], [shape.vocab])
+    assert e.value.status == nc.NC_EINVAL
+    ctx.update_bias([1], [5])
+    with pytest.raises(nc.NcError) as e:
+        ctx.step_cdf([1], prev=[6])
+    assert e.value.status == nc.NC_EINVAL
+    with pytest.raises(nc.NcError) as e:
+        ctx.step_cdf([9])
+    assert e.value.status == nc.NC_EINVAL
+    ctx.close()
+
+
+# ------------------------------------------------------ differentiation
+
+def test_mixed_nll_kernels_vs_oracle_and_fd(nc):
+    from oracle.mixer import mixed_nll_grad
+    from paper_2602_19626_gb300.autograd import mixed_nll
+    rng = np.random.default_rng(5)
+    n, V = 8, 49152
+    z = rng.normal(0, 0.5, (n, V)).astype(np.float32)
+    b = rng.normal(0, 0.05, (n, V)).astype(np.float32)
+    png = rng.dirichlet(np.ones(V), size=n).astype(np.float32)
+    theta = np.log(np.array([[0.85, 0.15]] * n)).astype(np.float32) + rng.normal(0, 0.2, (n, 2)).astype(np.float32)
+    target = rng.integers(0, V, n).astype(np.int32)
+    warm = np.array([0, 0, 0, 1, 0, 0, 1, 0], np.int32)
+    tb = torch.from_numpy(b).cuda().requires_grad_(True)
+    tth = torch.from_numpy(theta).cuda().requires_grad_(True)
+    args = [torch.from_numpy(a).cuda() for a in (z, png, target, warm)]
+    loss = mixed_nll(tb, tth, *args)
+    loss.sum().backward()
+    gb = tb.grad.cpu().numpy()
+    gth = tth.grad.cpu().numpy()
+    for i in range(n):
+        s = z[i].astype(np.float64) + b[i]
+        pt = np.exp(s - s.max())
+        pt /= pt.sum()
+        rb, rth = mixed_nll_grad(pt, png[i].astype(np.float64), theta[i].astype(np.float64), int(target[i]), bool(warm[i]))
+        np.testing.assert_allclose(gb[i], rb, rtol=1e-3, atol=1e-8)
+        np.testing.assert_allclose(gth[i], rth, rtol=1e-3, atol=1e-7)
+    # central finite differences of the GPU loss (eps 1e-3) on a few coordinates
+    eps = 1e-3
+    for i in (0, 3):
+        for k in [int(target[i]), 17]:
+            bp = b.copy()
+            bp[i, k] += eps
+            bm = b.copy()
+            bm[i, k] -= eps
+            lp = mixed_nll(torch.from_numpy(bp).cuda(), tth.detach(), *args)[i].item()
+            lm = mixed_nll(torch.from_numpy(bm).cuda(), tth.detach(), *args)[i].item()
+            assert abs((lp - lm) / (2 * eps) - gb[i, k]) < 2e-3 * max(1.0, abs(gb[i, k]))
