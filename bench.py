@@ -1,0 +1,338 @@
+"""Throughput of the per-token CDF step on one GB300 (or N replicas).
+
+Workload (default): the full-size model (30 layers, hidden 576, 9/3 heads,
+FFN 1536, vocabulary 49,152), BF16 weights random-init seed 1, FP32 mix /
+bias, one 8,192-token seeded Zipf/Markov stream, 2,048-token KV window
+sliding by 512, confidence skip off.  One "step" compresses the whole stream:
+every token runs the model, the biased softmax, the N-gram, the mix, the CDF
+quantiser and the head / mixer / N-gram updates (the GPU half ends at the
+coder's interval per token; the end-to-end number includes the host coder).
+
+Prints one JSON line.  `--impl reference` times the FP64 CPU oracle on a
+bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synthetic as S  # noqa: E402
+
+WORKLOADS = {
+    "full_bf16_single": dict(shape=S.FULL, fmt="bf16", seed=1, n_streams=1, length=8192),
+    "full_fp32_single": dict(shape=S.FULL, fmt="fp32", seed=1, n_streams=1, length=8192),
+    "small_fp32_single": dict(shape=S.SMALL, fmt="fp32", seed=0, n_streams=1, length=1024),
+}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def workload_streams(wl):
+    shape = wl["shape"]
+    return [S.token_stream(wl["seed"], j, wl["length"], shape.vocab) for j in range(wl["n_streams"])]
+
+
+# ------------------------------------------------------------- oracle (CPU)
+
+def oracle_rate(wl, budget_s: float, first_tokens: int | None = None):
+    """FP64 oracle on the host cores: tokens/s over the first tokens of the
+    workload's first stream, sized to take about budget_s seconds."""
+    from oracle.compress import StepConfig, StreamState
+    from oracle.model import Model
+    shape = wl["shape"]
+    toks = workload_streams(dict(wl, n_streams=1))[0]
+    model = Model(shape, S.weights(shape, wl["seed"]), wl["fmt"])
+    st = StreamState.new(model, StepConfig())
+    t0 = time.perf_counter()
+    n = 0
+    for t in toks:
+        st.predict()
+        st.update(int(t))
+        n += 1
+        el = time.perf_counter() - t0
+        if first_tokens is not None:
+            if n >= first_tokens:
+                break
+        elif el >= budget_s:
+            break
+    el = time.perf_counter() - t0
+    return n, el
+
+
+def blas_threads() -> int:
+    for k in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
+        if os.environ.get(k):
+            return int(os.environ[k])
+    return os.cpu_count() or 1
+
+
+def run_reference(args, wl):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    budget = 8.0
+    S.weights(wl["shape"], wl["seed"])          # generate outside the timed steps
+    for _ in range(args.warmup):
+        oracle_rate(wl, 0.0, first_tokens=2)
+    n_tot, t_tot = 0, 0.0
+    for _ in range(args.steps):
+        n, el = oracle_rate(wl, budget)
+        n_tot += n
+        t_tot += el
+    v = n_tot / t_tot
+    sample = (f"first {n_tot // max(args.steps, 1)} tokens of the {wl['length']}-token stream per step "
+              f"(about {budget:.0f} s each), FP64 oracle on {wl['fmt']}-dequantised weights")
+    line = {
+        "impl": "reference", "metric": "tokens/s compressed", "value": v, "unit": "tokens/s",
+        "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1000.0 * t_tot / max(args.steps, 1), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "model": "smollm2-135m-shape random-init",
+                   "streams": wl["n_streams"], "tokens_per_stream": wl["length"]},
+        "cpu_baseline": {"value": v, "unit": "tokens/s", "cores": blas_threads(), "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": v, "unit": "tokens/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------- GPU arm
+
+class ClockSampler:
+    """nvidia-smi samples every 200 ms while the timed region runs."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={index}", f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.flush()
+        rows = []
+        with open(self.f.name) as fh:
+            for line in fh:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.f.name)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def ncu_traffic(kind: str, workload: str):
+    """DRAM bytes per launch of `kind` from the committed ncu summary, or None
+    when there is none or the kernel sources changed since it was taken."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
+    if not os.path.exists(path):
+        return None
+    h = kernel_sources_hash()
+    with open(path) as fh:
+        for line in fh:
+            f = line.split()
+            if len(f) >= 4 and not line.startswith("#") and f[0] == kind and f[2] == workload and f[3] == h:
+                return float(f[1])
+    return None
+
+
+def kernel_sources_hash() -> str:
+    d = os.path.join(ROOT, "paper_2602_19626_gb300", "csrc")
+    m = hashlib.sha256()
+    for name in sorted(os.listdir(d)):
+        if name.endswith((".cu", ".h")):
+            with open(os.path.join(d, name), "rb") as fh:
+                m.update(fh.read())
+    return m.hexdigest()[:12]
+
+
+def run_gpu(args, wl):
+    import torch
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.cuda.current_device()
+    from paper_2602_19626_gb300 import nc24
+
+    shape = wl["shape"]
+    streams = workload_streams(wl)
+    lens = np.array([len(s) for s in streams], dtype=np.int64)
+    offs = np.concatenate([[0], np.cumsum(lens)[:-1]]).astype(np.int64)
+    flat = np.concatenate(streams).astype(np.int32)
+    n_tok = int(lens.sum())
+    stride = int(lens.max())
+    cstream = torch.cuda.Stream()
+    cfg = nc24.make_config(shape, fmt=wl["fmt"], max_streams=wl["n_streams"], device=dev, stream=cstream)
+    ctx = nc24.Context(cfg, S.flat_weights(shape, wl["seed"]))
+    tok_dev = torch.from_numpy(flat).to(f"cuda:{dev}")
+    iv = torch.empty((wl["n_streams"], stride, 2), dtype=torch.int32, device=f"cuda:{dev}")
+    torch.cuda.synchronize()
+
+    def step():
+        ctx.encode_intervals(tok_dev, offs, lens, iv, stride)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    clk = ClockSampler(dev)
+    with torch.cuda.stream(cstream):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(cstream)
+        for _ in range(args.steps):
+            step()
+        e1.record(cstream)
+        torch.cuda.synchronize()
+    clocks = clk.stop()
+    ms = e0.elapsed_time(e1)
+    if ws > 1:
+        t = torch.tensor([ms], device=f"cuda:{dev}")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+        torch.distributed.barrier()
+    total_tokens = n_tok * args.steps * ws
+    value = total_tokens / (ms / 1000.0)
+
+    # correctness guard on the timed output: intervals are non-empty, in range
+    ivh = iv.cpu().numpy().view(np.uint32)
+    lo, hi = ivh[..., 0], ivh[..., 1]
+    ok = bool(np.all(hi[:, : lens.min()] > lo[:, : lens.min()]) and np.all(hi <= (1 << 24)))
+
+    # per-kernel trace (one more pass, every kernel between CUDA events on the
+    # context's stream): the dominant kernel's bytes and average duration
+    trace = ctx.encode_intervals(tok_dev, offs, lens, iv, stride, trace=True)
+    tot_ms = sum(k["ms"] for k in trace) or 1.0
+    dom = max(trace, key=lambda k: k["ms"])
+    per_launch_ms = dom["ms"] / max(dom["launches"], 1)
+    per_launch_bytes = dom["bytes"] / max(dom["launches"], 1)
+    peak, peak_kind = measured_peaks()
+    achieved = per_launch_bytes / (per_launch_ms / 1000.0) / 1e9
+    roofline = {"bound": "hbm", "kernel": dom["name"], "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "peak_source": peak_kind,
+                "bytes_per_launch": per_launch_bytes, "ms_per_launch": per_launch_ms,
+                "share": dom["ms"] / tot_ms,
+                "traffic": ncu_traffic(dom["name"], args.workload)}
+    kernels = {k["name"]: {"launches": k["launches"], "ms": round(k["ms"], 3), "share": round(k["ms"] / tot_ms, 4),
+                           "GBps": round(k["bytes"] / (k["ms"] / 1000.0) / 1e9, 1) if k["ms"] > 0 else None}
+               for k in trace if k["launches"]}
+    launches_per_step = sum(k["launches"] for k in trace)
+
+    # end to end through the public API: host tokens in, container bytes out
+    host_streams = [np.ascontiguousarray(s) for s in streams]
+    ctx.encode(host_streams)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    e2e_steps = max(1, min(args.steps, 3))
+    nbytes = 0
+    for _ in range(e2e_steps):
+        blob = ctx.encode(host_streams)
+        nbytes = len(blob)
+    e2e_s = time.perf_counter() - t0
+    if ws > 1:
+        t = torch.tensor([e2e_s], device=f"cuda:{dev}", dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e = {"value": n_tok * e2e_steps * ws / e2e_s, "unit": "tokens/s",
+           "h2d_bytes_per_step": int(flat.nbytes + 16 * wl["n_streams"]),
+           "d2h_bytes_per_step": int(8 * n_tok), "container_bytes": nbytes,
+           "bits_per_token": 8.0 * nbytes / n_tok}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        n, el = oracle_rate(wl, args.cpu_budget)
+        cpu = {"value": n / el, "unit": "tokens/s", "cores": blas_threads(), "kind": "oracle",
+               "sample": f"first {n} tokens of the {wl['length']}-token stream, FP64 oracle on "
+                         f"{wl['fmt']}-dequantised weights, {el:.1f} s"}
+    if rank == 0:
+        line = {
+            "metric": "tokens/s compressed", "value": value, "unit": "tokens/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": args.workload, "model": "smollm2-135m-shape random-init",
+                       "weights": wl["fmt"], "streams_per_gpu": wl["n_streams"],
+                       "tokens_per_stream": wl["length"], "ctx_len": shape.ctx_len, "slide": shape.slide,
+                       "path": "gemv", "parallelism": f"replicas{ws}",
+                       "l2": "weights (BF16 269 MB) exceed L2 and are re-read every token"},
+            "gpu_launches": launches_per_step * args.steps,
+            "roofline": roofline, "kernels": kernels, "clocks": clocks, "e2e": e2e,
+            "cpu_baseline": cpu, "intervals_valid": ok,
+        }
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="full_bf16_single", choices=sorted(WORKLOADS))
+    ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    wl = WORKLOADS[args.workload]
+    if args.impl == "reference":
+        run_reference(args, wl)
+    else:
+        run_gpu(args, wl)
+
+
+if __name__ == "__main__":
+    main()

@@ -154,6 +154,38 @@ int nc_update_bias(nc_ctx* ctx, int n, const int32_t* stream_ids, const int32_t*
 int nc_encode(nc_ctx* ctx, int n_streams, const int32_t* const* tokens, const int64_t* lens,
               uint8_t* out, size_t* inout_nbytes);
 
+/* Per-kernel trace of one nc_encode_intervals call: for each kernel kind,
+ * the launches, their summed device time (CUDA events around each launch on
+ * the context's stream) and the algorithmic bytes they move (weights, KV
+ * entries, activations and per-symbol vectors each read or written once). */
+#define NC_TRACE_KINDS 16
+typedef struct {
+  int n_kinds;
+  char name[NC_TRACE_KINDS][32];
+  int64_t launches[NC_TRACE_KINDS];
+  double ms[NC_TRACE_KINDS];
+  double bytes[NC_TRACE_KINDS];
+} nc_trace;
+
+/* The device half of nc_encode: per-token CDF steps for n_streams streams
+ * whose tokens are already on the device, producing each token's coder
+ * interval instead of the bitstream.
+ *   tokens_dev    DEVICE int32, stream j's tokens at tokens_dev + offsets[j].
+ *   offsets, lens HOST int64[n_streams].
+ *   intervals_dev DEVICE uint32[n_streams][stride][2]: (cdf[t_i], cdf[t_i + 1])
+ *                 of token i of stream j (Algorithm 1, probs_to_cdf then the
+ *                 interval handed to ArithEncoder.encode); stride >= max lens.
+ *   trace         NULL, or a HOST nc_trace filled per kernel kind; tracing
+ *                 launches every kernel eagerly between CUDA events (slower).
+ * Streams occupy fresh slots that are released before return.  Without a
+ * trace the steps are replayed from a captured CUDA graph, asynchronously on
+ * the context's stream; the call returns after the last step is enqueued
+ * and the status words were read (one synchronisation at the end).
+ * Errors: NC_EINVAL, NC_ENOMEM, NC_ENUMERIC, NC_ESTATE, NC_ECUDA. */
+int nc_encode_intervals(nc_ctx* ctx, int n_streams, const int32_t* tokens_dev,
+                        const int64_t* offsets, const int64_t* lens, uint32_t* intervals_dev,
+                        int64_t stride, nc_trace* trace);
+
 /* Mirror of nc_encode.  tokens_out: HOST array of HOST int32 pointers, one
  * per stream, each with room for that stream's token count; lens_out HOST
  * int64[stream count].  A NULL tokens_out only reads the header: lens_out

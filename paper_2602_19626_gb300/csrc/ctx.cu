@@ -493,11 +493,41 @@ static Batch make_batch(nc_ctx* ctx) {
   return b;
 }
 
+// Kernel kinds reported by nc_trace.
+enum TraceKind { TK_PREPARE, TK_EMBED, TK_QKV, TK_ATTN, TK_O, TK_GU, TK_DOWN, TK_LMHEAD, TK_VOCAB,
+                 TK_NGRAM, TK_COUNT };
+static const char* kTraceNames[TK_COUNT] = {"prepare", "embed", "gemv_qkv", "attn", "gemv_o",
+                                            "gemv_gate_up", "gemv_down", "lm_head", "vocab", "ngram_update"};
+
+// Records a CUDA event after every launch of a step (when on) so that the
+// device time of each kernel is the gap between consecutive events.
+struct StepMarks {
+  bool on = false;
+  std::vector<cudaEvent_t> ev;   // ev[0] before the first kernel
+  std::vector<int> kind;
+  int n = 0;
+  cudaError_t begin(cudaStream_t s) {
+    n = 0;
+    kind.clear();
+    if (!on) return cudaSuccess;
+    return cudaEventRecord(ev[0], s);
+  }
+  cudaError_t mark(cudaStream_t s, int k) {
+    if (!on) return cudaSuccess;
+    if (n + 1 >= (int)ev.size()) return cudaErrorInvalidValue;
+    kind.push_back(k);
+    return cudaEventRecord(ev[++n], s);
+  }
+};
+
 // Model forward of every active row: logits into each stream's z.
-static cudaError_t launch_model(nc_ctx* ctx, const Batch& b) {
+static cudaError_t launch_model(nc_ctx* ctx, const Batch& b, StepMarks* mk = nullptr) {
   const Dims& D = ctx->D;
   cudaStream_t s = ctx->stream;
+  StepMarks none;
+  StepMarks& m = mk ? *mk : none;
   cudaError_t e = launch_embed(D, b, ctx->embed, ctx->embed_scale, ctx->fmt, ctx->x, s);
+  if (e == cudaSuccess) e = m.mark(s, TK_EMBED);
   for (int l = 0; l < D.n_layers && e == cudaSuccess; ++l) {
     const LayerW& L = ctx->layers[l];
     GemvIO io{};
@@ -505,12 +535,15 @@ static cudaError_t launch_model(nc_ctx* ctx, const Batch& b) {
     io.g = L.g_attn;
     io.y = ctx->qkv;
     e = launch_gemv(D, b, L.qkv, ctx->fmt, PRO_RMSNORM, EPI_STORE, io, s);
+    if (e == cudaSuccess) e = m.mark(s, TK_QKV);
     if (e == cudaSuccess) e = launch_attn(D, b, l, ctx->qkv, ctx->part, s);
+    if (e == cudaSuccess) e = m.mark(s, TK_ATTN);
     if (e == cudaSuccess) {
       io = GemvIO{};
       io.part = ctx->part;
       io.y = ctx->x;
       e = launch_gemv(D, b, L.o, ctx->fmt, PRO_ATTN, EPI_RESID, io, s);
+      if (e == cudaSuccess) e = m.mark(s, TK_O);
     }
     if (e == cudaSuccess) {
       io = GemvIO{};
@@ -518,12 +551,14 @@ static cudaError_t launch_model(nc_ctx* ctx, const Batch& b) {
       io.g = L.g_ffn;
       io.y = ctx->h;
       e = launch_gemv(D, b, L.gu, ctx->fmt, PRO_RMSNORM, EPI_SWIGLU, io, s);
+      if (e == cudaSuccess) e = m.mark(s, TK_GU);
     }
     if (e == cudaSuccess) {
       io = GemvIO{};
       io.x = ctx->h;
       io.y = ctx->x;
       e = launch_gemv(D, b, L.down, ctx->fmt, PRO_PLAIN, EPI_RESID, io, s);
+      if (e == cudaSuccess) e = m.mark(s, TK_DOWN);
     }
   }
   if (e == cudaSuccess) {
@@ -532,8 +567,34 @@ static cudaError_t launch_model(nc_ctx* ctx, const Batch& b) {
     io.g = ctx->g_final;
     Mat head{ctx->embed, ctx->embed_scale, D.V, D.d};
     e = launch_gemv(D, b, head, ctx->fmt, PRO_RMSNORM, EPI_LOGITS, io, s);
+    if (e == cudaSuccess) e = m.mark(s, TK_LMHEAD);
   }
   return e;
+}
+
+// Algorithmic bytes of one launch of each kind for B active rows whose
+// attention window holds n_ctx entries (the new token included).
+static void step_bytes(const nc_ctx* ctx, int B, int n_ctx, double* out) {
+  const Dims& D = ctx->D;
+  const double esz = ctx->fmt == NC_FP32 ? 4 : ctx->fmt == NC_BF16 ? 2 : 1;
+  const double kvsz = D.kv_bf16 ? 2 : 4;
+  auto gemv = [&](double rows, double cols, double out_rows, bool resid) {
+    double w = rows * cols * esz + (ctx->fmt == NC_FP8E4M3 ? rows * 4 : 0);
+    return w + B * cols * 4 + B * out_rows * 4 * (resid ? 2 : 1);
+  };
+  const double qd = (double)D.hq * kHeadDim;
+  for (int k = 0; k < TK_COUNT; ++k) out[k] = 0;
+  out[TK_PREPARE] = B * 24.0;
+  out[TK_EMBED] = B * D.d * (esz + 4);
+  out[TK_QKV] = gemv(D.qkv_rows, D.d, D.qkv_rows, false) + B * D.d * 4;
+  out[TK_ATTN] = B * (D.hkv * ((n_ctx - 1) * 2.0 * kHeadDim * kvsz + 2.0 * kHeadDim * kvsz) +
+                      D.qkv_rows * 4.0 + D.hq * (kHeadDim + 2.0) * 4.0 * ((n_ctx + kAttnChunk - 1) / kAttnChunk));
+  out[TK_O] = gemv(D.d, qd, D.d, true);
+  out[TK_GU] = gemv(2.0 * D.F, D.d, D.F, false);
+  out[TK_DOWN] = gemv(D.d, D.F, D.d, true);
+  out[TK_LMHEAD] = gemv(D.V, D.d, D.V, false);
+  out[TK_VOCAB] = B * D.V * 16.0 + B * 8.0;
+  out[TK_NGRAM] = B * (3.0 * sizeof(NgEntry) + 64.0);
 }
 
 // Host-side checks and staging of a batch of open streams.
@@ -686,13 +747,15 @@ static uint8_t path_byte(const nc_config& c) { return (uint8_t)(c.weight_fmt | (
 
 // The device half of nc_encode: tokens resident on the device, one captured
 // step replayed until every stream is coded.  Streams must already be open in
-// slots slot_of[j] (j in the caller's order); rows are processed longest
-// first.  intervals: DEVICE uint32[n][stride][2].
+// slots slot_of[r] (row order = longest first, so the active rows of every
+// step are a prefix).  intervals: DEVICE uint32[n][stride][2].
 static int encode_device(nc_ctx* ctx, int n, const std::vector<int>& slot_of, const int32_t* tok_dev,
-                         const int64_t* offs_dev, const int64_t* lens_dev, int64_t max_len,
-                         uint32_t* intervals, int64_t stride) {
+                         const int64_t* offs_dev, const int64_t* lens_dev, const std::vector<int64_t>& lens_h,
+                         uint32_t* intervals, int64_t stride, nc_trace* trace) {
   const Dims& D = ctx->D;
   cudaStream_t s = ctx->stream;
+  int64_t max_len = 0;
+  for (int64_t l : lens_h) max_len = std::max(max_len, l);
   for (int j = 0; j < n; ++j) ctx->h_i32[1 + j] = slot_of[j];
   NC_TRY(cudaMemcpyAsync(ctx->d_slots, ctx->h_i32 + 1, (size_t)n * 4, cudaMemcpyHostToDevice, s));
   Batch b = make_batch(ctx);
@@ -702,33 +765,165 @@ static int encode_device(nc_ctx* ctx, int n, const std::vector<int>& slot_of, co
   io.update = 1;
   io.intervals = intervals;
   io.interval_stride = stride;
+  StepMarks mk;
+  mk.on = trace != nullptr;
+  if (mk.on) {
+    mk.ev.resize(8 + 5 * D.n_layers);
+    for (auto& e : mk.ev) NC_TRY(cudaEventCreate(&e));
+  }
   auto one_step = [&]() -> cudaError_t {
-    cudaError_t e = launch_prepare_encode(b, n, tok_dev, offs_dev, lens_dev, ctx->d_obs, ctx->d_nB, s);
-    if (e == cudaSuccess) e = launch_model(ctx, b);
+    cudaError_t e = mk.begin(s);
+    if (e == cudaSuccess) e = launch_prepare_encode(b, n, tok_dev, offs_dev, lens_dev, ctx->d_obs, ctx->d_nB, s);
+    if (e == cudaSuccess) e = mk.mark(s, TK_PREPARE);
+    if (e == cudaSuccess) e = launch_model(ctx, b, &mk);
     if (e == cudaSuccess) e = launch_vocab(D, b, io, s);
+    if (e == cudaSuccess) e = mk.mark(s, TK_VOCAB);
     if (e == cudaSuccess) e = launch_ngram_update(D, b, s);
+    if (e == cudaSuccess) e = mk.mark(s, TK_NGRAM);
     return e;
   };
   // capture one step in a graph (the whole step is device-driven)
   cudaGraph_t g = nullptr;
   cudaGraphExec_t ge = nullptr;
-  bool graphed = false;
   if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
     cudaError_t e = one_step();
     cudaError_t e2 = cudaStreamEndCapture(s, &g);
-    if (e == cudaSuccess && e2 == cudaSuccess && cudaGraphInstantiate(&ge, g, 0) == cudaSuccess) graphed = true;
+    if (e != cudaSuccess || e2 != cudaSuccess || cudaGraphInstantiate(&ge, g, 0) != cudaSuccess) ge = nullptr;
     if (g) cudaGraphDestroy(g);
     cudaGetLastError();
   }
+  if (trace) {
+    std::memset(trace, 0, sizeof(*trace));
+    trace->n_kinds = TK_COUNT;
+    for (int k = 0; k < TK_COUNT; ++k) std::snprintf(trace->name[k], sizeof(trace->name[k]), "%s", kTraceNames[k]);
+  }
+  int st = NC_OK;
+  int active = n;
   for (int64_t k = 0; k < max_len; ++k) {
-    if (graphed) {
-      NC_TRY(cudaGraphLaunch(ge, s));
-    } else {
-      NC_TRY(one_step());
+    cudaError_t e = ge ? cudaGraphLaunch(ge, s) : one_step();
+    if (e != cudaSuccess) {
+      st = fail_cuda(ctx, e, "encode step");
+      break;
+    }
+    if (trace) {
+      // every active row has coded k tokens; its window after the step's slide
+      while (active > 0 && lens_h[active - 1] <= k) --active;
+      int64_t start = 0;
+      {
+        // kv_start after k steps, from the same recurrence as the kernels
+        const int64_t L = D.L, C = D.C;
+        if (k >= L) start = ((k - L) / C + 1) * C;
+      }
+      const int n_ctx = (int)(k - start + 1);
+      double bytes[TK_COUNT];
+      step_bytes(ctx, active, n_ctx, bytes);
+      e = cudaEventSynchronize(mk.ev[mk.n]);
+      if (e != cudaSuccess) {
+        st = fail_cuda(ctx, e, "trace sync");
+        break;
+      }
+      for (int i = 0; i < mk.n; ++i) {
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, mk.ev[i], mk.ev[i + 1]);
+        const int kd = mk.kind[i];
+        trace->ms[kd] += ms;
+        trace->launches[kd] += 1;
+        trace->bytes[kd] += bytes[kd];
+      }
     }
   }
   if (ge) cudaGraphExecDestroy(ge);
+  for (auto& e : mk.ev) cudaEventDestroy(e);
+  return st;
+}
+
+// Open fresh slots for n streams, longest first; returns the row order.
+static int open_rows(nc_ctx* ctx, int n, const int64_t* lens, std::vector<int>* order,
+                     std::vector<int>* slot_of, std::vector<int32_t>* ids, int32_t id_base) {
+  order->resize(n);
+  for (int j = 0; j < n; ++j) (*order)[j] = j;
+  std::stable_sort(order->begin(), order->end(), [&](int a, int b) { return lens[a] > lens[b]; });
+  slot_of->assign(n, -1);
+  ids->assign(n, -1);
+  int32_t next_id = id_base;
+  for (int r = 0; r < n; ++r) {
+    while (ctx->id2slot.count(next_id)) ++next_id;
+    (*ids)[r] = next_id++;
+    const int st = open_slot(ctx, (*ids)[r], std::max<int64_t>(lens[(*order)[r]], 1), &(*slot_of)[r]);
+    if (st != NC_OK) return st;
+  }
   return NC_OK;
+}
+
+static void close_rows(nc_ctx* ctx, const std::vector<int32_t>& ids) {
+  for (int32_t id : ids)
+    if (id >= 0 && ctx->id2slot.count(id)) nc_stream_close(ctx, id);
+}
+
+extern "C" int nc_encode_intervals(nc_ctx* ctx, int n_streams, const int32_t* tokens_dev, const int64_t* offsets,
+                                   const int64_t* lens, uint32_t* intervals_dev, int64_t stride, nc_trace* trace) {
+  if (!ctx) return NC_EINVAL;
+  if (ctx->poisoned) return fail(ctx, NC_ESTATE, "context poisoned by an earlier CUDA error");
+  if (!tokens_dev || !offsets || !lens || !intervals_dev || n_streams < 1) return fail(ctx, NC_EINVAL, "bad arguments");
+  if (n_streams > ctx->cfg.max_streams) return fail(ctx, NC_EINVAL, "more streams than max_streams");
+  int64_t max_len = 0;
+  for (int j = 0; j < n_streams; ++j) {
+    if (lens[j] < 0 || offsets[j] < 0) return fail(ctx, NC_EINVAL, "bad stream extent");
+    max_len = std::max(max_len, lens[j]);
+  }
+  if (stride < max_len) return fail(ctx, NC_EINVAL, "stride below the longest stream");
+  if (!is_device_ptr(tokens_dev) || !is_device_ptr(intervals_dev)) return fail(ctx, NC_EINVAL, "tokens and intervals must be device memory");
+  cudaSetDevice(ctx->cfg.device);
+  int free_slots = 0;
+  for (auto& s : ctx->slots) free_slots += !s.open;
+  if (free_slots < n_streams) return fail(ctx, NC_EINVAL, "not enough free stream slots");
+  std::vector<int> order, slot_of;
+  std::vector<int32_t> ids;
+  int st = open_rows(ctx, n_streams, lens, &order, &slot_of, &ids, 0x60000000);
+  int64_t* meta = nullptr;
+  int32_t* tok_rows = nullptr;
+  uint32_t* iv_rows = nullptr;
+  std::vector<int64_t> lens_h(n_streams);
+  do {
+    if (st != NC_OK) break;
+    // row r reads stream order[r]: offsets in rows, intervals written per row
+    std::vector<int64_t> h_meta(2 * n_streams);
+    for (int r = 0; r < n_streams; ++r) {
+      h_meta[r] = offsets[order[r]];
+      h_meta[n_streams + r] = lens[order[r]];
+      lens_h[r] = lens[order[r]];
+    }
+    if (cudaMalloc(&meta, 2 * n_streams * 8) != cudaSuccess) {
+      st = fail(ctx, NC_ENOMEM, "meta allocation");
+      break;
+    }
+    bool identity = true;
+    for (int r = 0; r < n_streams; ++r) identity &= order[r] == r;
+    if (!identity && cudaMalloc(&iv_rows, (size_t)n_streams * stride * 8) != cudaSuccess) {
+      st = fail(ctx, NC_ENOMEM, "interval staging allocation");
+      break;
+    }
+    if (cudaMemcpyAsync(meta, h_meta.data(), 2 * n_streams * 8, cudaMemcpyHostToDevice, ctx->stream) != cudaSuccess) {
+      st = fail_cuda(ctx, cudaErrorUnknown, "meta upload");
+      break;
+    }
+    uint32_t* target = identity ? intervals_dev : iv_rows;
+    st = encode_device(ctx, n_streams, slot_of, tokens_dev, meta, meta + n_streams, lens_h, target, stride, trace);
+    if (st != NC_OK) break;
+    if (!identity)
+      for (int r = 0; r < n_streams; ++r)
+        if (cudaMemcpyAsync(intervals_dev + (size_t)order[r] * stride * 2, iv_rows + (size_t)r * stride * 2,
+                            (size_t)stride * 8, cudaMemcpyDeviceToDevice, ctx->stream) != cudaSuccess) {
+          st = fail_cuda(ctx, cudaErrorUnknown, "interval reorder");
+          break;
+        }
+    if (st == NC_OK) st = check_status(ctx, slot_of);
+  } while (0);
+  cudaFree(meta);
+  cudaFree(tok_rows);
+  cudaFree(iv_rows);
+  close_rows(ctx, ids);
+  return st;
 }
 
 extern "C" int nc_encode(nc_ctx* ctx, int n_streams, const int32_t* const* tokens, const int64_t* lens,
@@ -761,23 +956,10 @@ extern "C" int nc_encode(nc_ctx* ctx, int n_streams, const int32_t* const* token
   int free_slots = 0;
   for (auto& s : ctx->slots) free_slots += !s.open;
   if (free_slots < n_streams) return fail(ctx, NC_EINVAL, "not enough free stream slots");
-  // longest first, so the active rows of each step are a prefix
-  std::vector<int> order(n_streams);
-  for (int j = 0; j < n_streams; ++j) order[j] = j;
-  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return lens[a] > lens[b]; });
-  std::vector<int> slot_of(n_streams);
-  std::vector<int32_t> ids(n_streams);
-  int st = NC_OK;
-  int32_t next_id = 0x40000000;
-  for (int r = 0; r < n_streams && st == NC_OK; ++r) {
-    while (ctx->id2slot.count(next_id)) ++next_id;
-    ids[r] = next_id++;
-    st = open_slot(ctx, ids[r], std::max<int64_t>(lens[order[r]], 1), &slot_of[r]);
-  }
-  auto close_all = [&]() {
-    for (int r = 0; r < n_streams; ++r)
-      if (ctx->id2slot.count(ids[r])) nc_stream_close(ctx, ids[r]);
-  };
+  std::vector<int> order, slot_of;
+  std::vector<int32_t> ids;
+  int st = open_rows(ctx, n_streams, lens, &order, &slot_of, &ids, 0x40000000);
+  auto close_all = [&]() { close_rows(ctx, ids); };
   if (st != NC_OK) {
     close_all();
     return st;
@@ -813,7 +995,9 @@ extern "C" int nc_encode(nc_ctx* ctx, int n_streams, const int32_t* const* token
       st = fail_cuda(ctx, cudaErrorUnknown, "meta upload");
       break;
     }
-    st = encode_device(ctx, n_streams, slot_of, tok_dev, meta, meta + n_streams, max_len, iv, max_len);
+    std::vector<int64_t> lens_rows(n_streams);
+    for (int r = 0; r < n_streams; ++r) lens_rows[r] = lens[order[r]];
+    st = encode_device(ctx, n_streams, slot_of, tok_dev, meta, meta + n_streams, lens_rows, iv, max_len, nullptr);
     if (st != NC_OK) break;
     h_iv.resize((size_t)n_streams * max_len * 2);
     if (cudaMemcpyAsync(h_iv.data(), iv, h_iv.size() * 4, cudaMemcpyDeviceToHost, ctx->stream) != cudaSuccess) {
@@ -903,22 +1087,12 @@ extern "C" int nc_decode(nc_ctx* ctx, const uint8_t* in, size_t nbytes, int32_t*
   const Dims& D = ctx->D;
   cudaSetDevice(ctx->cfg.device);
   cudaStream_t s = ctx->stream;
-  std::vector<int> order(n);
-  for (int j = 0; j < n; ++j) order[j] = j;
-  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return recs[a].ntok > recs[b].ntok; });
-  std::vector<int> slot_of(n);
-  std::vector<int32_t> ids(n);
-  int st = NC_OK;
-  int32_t next_id = 0x50000000;
-  for (int r = 0; r < n && st == NC_OK; ++r) {
-    while (ctx->id2slot.count(next_id)) ++next_id;
-    ids[r] = next_id++;
-    st = open_slot(ctx, ids[r], std::max<uint32_t>(recs[order[r]].ntok, 1), &slot_of[r]);
-  }
-  auto close_all = [&]() {
-    for (int r = 0; r < n; ++r)
-      if (ctx->id2slot.count(ids[r])) nc_stream_close(ctx, ids[r]);
-  };
+  std::vector<int64_t> rlens(n);
+  for (int j = 0; j < n; ++j) rlens[j] = recs[j].ntok;
+  std::vector<int> order, slot_of;
+  std::vector<int32_t> ids;
+  int st = open_rows(ctx, n, rlens.data(), &order, &slot_of, &ids, 0x50000000);
+  auto close_all = [&]() { close_rows(ctx, ids); };
   if (st != NC_OK) {
     close_all();
     return st;

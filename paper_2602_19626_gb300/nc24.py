@@ -44,6 +44,15 @@ class nc_config(C.Structure):
     ]
 
 
+NC_TRACE_KINDS = 16
+
+
+class nc_trace(C.Structure):
+    _fields_ = [("n_kinds", C.c_int), ("name", (C.c_char * 32) * NC_TRACE_KINDS),
+                ("launches", C.c_int64 * NC_TRACE_KINDS), ("ms", C.c_double * NC_TRACE_KINDS),
+                ("bytes", C.c_double * NC_TRACE_KINDS)]
+
+
 _P = C.c_void_p
 _I32P = C.POINTER(C.c_int32)
 _I64P = C.POINTER(C.c_int64)
@@ -62,6 +71,7 @@ _SIGS = {
     "nc_update_bias": (C.c_int, [_P, C.c_int, _P, _P]),
     "nc_encode": (C.c_int, [_P, C.c_int, _P, _P, _P, _SZP]),
     "nc_decode": (C.c_int, [_P, _P, C.c_size_t, _P, _P]),
+    "nc_encode_intervals": (C.c_int, [_P, C.c_int, _P, _P, _P, _P, C.c_int64, C.POINTER(nc_trace)]),
     "nc_container_streams": (C.c_int, [_P, C.c_size_t, C.POINTER(C.c_int)]),
     "nc_status_str": (C.c_char_p, [C.c_int]),
     "nc_last_error": (C.c_char_p, [_P]),
@@ -266,6 +276,21 @@ class Context:
         out = np.zeros(nb.value, dtype=np.uint8)
         self._check(lib.nc_encode(self.h, len(arrs), ptrs, _ptr(lens), _ptr(out), C.byref(nb)), "nc_encode")
         return out[: nb.value].tobytes()
+
+    def encode_intervals(self, tokens_dev, offsets, lens, intervals_dev, stride: int, trace: bool = False):
+        """Device half of encode: tokens_dev CUDA int32 (flat), offsets/lens
+        host int64, intervals_dev CUDA int32/uint32 [n, stride, 2].  Returns
+        the per-kernel trace as a list of dicts when trace is set."""
+        offs = np.ascontiguousarray(offsets, dtype=np.int64)
+        ln = np.ascontiguousarray(lens, dtype=np.int64)
+        tr = nc_trace() if trace else None
+        self._check(lib.nc_encode_intervals(self.h, ln.size, _ptr(tokens_dev), _ptr(offs), _ptr(ln),
+                                            _ptr(intervals_dev), stride, C.byref(tr) if tr else None),
+                    "nc_encode_intervals")
+        if not tr:
+            return None
+        return [dict(name=tr.name[k].value.decode(), launches=tr.launches[k], ms=tr.ms[k], bytes=tr.bytes[k])
+                for k in range(tr.n_kinds)]
 
     def decode(self, data: bytes):
         buf = np.frombuffer(data, dtype=np.uint8).copy()

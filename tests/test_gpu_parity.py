@@ -162,10 +162,14 @@ def test_ngram_eviction_parity(nc):
     ctx.close()
 
 
-@pytest.mark.parametrize("fmt,tol_fp32,tol_fmt", [("fp32", 1e-4, 1e-4), ("bf16", 3e-2, 2e-3), ("fp8", None, 2e-3)])
+# BF16 / FP8 weights keep the KV cache in BF16; against the oracle on the
+# dequantised weights (FP64 cache) the cache's rounding (relative 2^-9 per
+# stored element) leaves a few 1e-3 on logits of magnitude ~1.
+@pytest.mark.parametrize("fmt,tol_fp32,tol_fmt", [("fp32", 1e-4, 1e-4), ("bf16", 3e-2, 5e-3), ("fp8", None, 5e-3)])
 def test_full_model_logits(nc, fmt, tol_fp32, tol_fmt):
     """30-layer SmolLM2-135M shape: logits of the first steps against the
-    oracle on the FP32 weights and on the format's dequantised weights."""
+    oracle on the FP32 weights and on the format's dequantised weights (FP8
+    against FP32 weights is reported, not bounded)."""
     shape, seed = S.FULL, 1
     toks, recs, _ = _run_steps(nc, shape, seed, fmt, 4, 100)
     w32 = S.weights(shape, seed)
