@@ -503,6 +503,7 @@ static const char* kTraceNames[TK_COUNT] = {"prepare", "embed", "gemv_qkv", "att
 // device time of each kernel is the gap between consecutive events.
 struct StepMarks {
   bool on = false;
+  bool capturing = false;        // inside stream capture: record external event nodes
   std::vector<cudaEvent_t> ev;   // ev[0] before the first kernel
   std::vector<int> kind;
   int n = 0;
@@ -510,13 +511,16 @@ struct StepMarks {
     n = 0;
     kind.clear();
     if (!on) return cudaSuccess;
-    return cudaEventRecord(ev[0], s);
+    return record(ev[0], s);
+  }
+  cudaError_t record(cudaEvent_t e, cudaStream_t s) {
+    return capturing ? cudaEventRecordWithFlags(e, s, cudaEventRecordExternal) : cudaEventRecord(e, s);
   }
   cudaError_t mark(cudaStream_t s, int k) {
     if (!on) return cudaSuccess;
     if (n + 1 >= (int)ev.size()) return cudaErrorInvalidValue;
     kind.push_back(k);
-    return cudaEventRecord(ev[++n], s);
+    return record(ev[++n], s);
   }
 };
 
@@ -786,7 +790,9 @@ static int encode_device(nc_ctx* ctx, int n, const std::vector<int>& slot_of, co
   cudaGraph_t g = nullptr;
   cudaGraphExec_t ge = nullptr;
   if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+    mk.capturing = true;
     cudaError_t e = one_step();
+    mk.capturing = false;
     cudaError_t e2 = cudaStreamEndCapture(s, &g);
     if (e != cudaSuccess || e2 != cudaSuccess || cudaGraphInstantiate(&ge, g, 0) != cudaSuccess) ge = nullptr;
     if (g) cudaGraphDestroy(g);
