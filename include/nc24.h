@@ -239,6 +239,19 @@ int nc_step_probe(nc_ctx* ctx, int n, const int32_t* stream_ids, float* z, float
 int nc_stream_state(nc_ctx* ctx, int32_t stream_id, float* bias, float* mix_logw,
                     int64_t* n_coded);
 
+/* Tensor-core GEMM (tcgen05, the projections of the batched path):
+ * Y[n][m] = sum_k W[m][k] X[n][k] with FP32 accumulation.
+ *   W DEVICE [M][K], X DEVICE [N][K]: BF16 (fp8 = 0) or FP8 E4M3 (fp8 = 1),
+ *     row-major, 16-byte aligned, K * element size a multiple of 16.
+ *   w_scale DEVICE float[M], x_scale DEVICE float[N] (FP8 only): the product
+ *     is scaled by w_scale[m] * x_scale[n].
+ *   bn: batch tile, 32 | 64 | 128 | 256 (results do not depend on it).
+ *   Y DEVICE float[N][M].  Synchronises `stream`.
+ * Errors: NC_EINVAL, NC_ENOMEM, NC_ECUDA, NC_ETIMEOUT (a bounded pipeline
+ * wait gave up). */
+int nc_gemm_tc(const void* W, const void* X, const float* w_scale, const float* x_scale, int fp8, int M,
+               int N, int K, int bn, float* Y, void* stream);
+
 /* 32-bit arithmetic coder (Sec. 3.8) on the host, for callers that produce
  * their own CDFs.  Encode n intervals [lo[i], hi[i]) of a total 2^log2_total
  * (HOST uint32 arrays) into out (HOST, capacity *inout_nbytes; size and the

@@ -3,12 +3,15 @@
 // building-block entry points.  See include/nc24.h for the contract.
 #include <algorithm>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <string>
 #include <thread>
 #include <unordered_map>
 #include <vector>
+
+#include <cuda.h>
 
 #include "coder.h"
 #include "internal.h"
@@ -34,6 +37,15 @@ struct Slot {
   NgEntry* ent[3] = {nullptr, nullptr, nullptr};
   int64_t cap_len = 0;       // tokens the N-gram buffers can hold
   int64_t cap_hash = 0;      // hash index capacity (power of two)
+};
+
+// One projection on the tensor-core path: tensor maps of the weights (box of
+// 128 rows) and of the batch operand (box of bn rows), and the tuned bn.
+struct TcMat {
+  CUtensorMap a;
+  CUtensorMap b;
+  int M = 0, K = 0, bn = 0;
+  const float* scale = nullptr;
 };
 
 }  // namespace
@@ -70,6 +82,11 @@ struct nc_ctx {
   int32_t* h_i32 = nullptr;          // 3 * max_streams + 1
   uint32_t* h_u32 = nullptr;         // 3 * max_streams: targets, then (lo, hi) pairs
   int32_t* h_status = nullptr;       // max_streams
+
+  // tensor-core path
+  std::vector<TcMat> tc;             // per layer: qkv, o, gate/up, down; then the LM head
+  void* opnd = nullptr;              // [max_streams][max(d, F)] BF16 / E4M3 GEMM operand
+  float* opnd_scale = nullptr;       // [max_streams] E4M3 row scales
 
   StreamDev* d_st = nullptr;
   std::vector<StreamDev> h_st;
@@ -177,7 +194,8 @@ static std::string validate(const nc_config& c) {
   if (c.w_llm_init <= 0.f || c.w_llm_init >= 1.f) return "w_llm_init must be in (0, 1)";
   if (c.weight_fmt < NC_FP32 || c.weight_fmt > NC_FP8E4M3) return "unknown weight_fmt";
   if (c.update_rule != NC_RULE_PAPER && c.update_rule != NC_RULE_MIXED_NLL) return "unknown update_rule";
-  if (c.path != NC_PATH_GEMV) return "only NC_PATH_GEMV is available in this build";
+  if (c.path != NC_PATH_GEMV && c.path != NC_PATH_TC) return "unknown path";
+  if (c.path == NC_PATH_TC && c.weight_fmt == NC_FP32) return "the tensor-core path needs BF16 or FP8 weights";
   if (c.max_streams < 1 || c.max_streams > 4096) return "max_streams must be 1..4096";
   if (c.warmup < 0) return "warmup must be >= 0";
   return "";
@@ -242,6 +260,114 @@ extern "C" void nc_ctx_destroy(nc_ctx* ctx) {
   delete ctx;
 }
 
+static int tc_bn_candidates(int Bmax, int* out) {
+  int n = 0;
+  for (int bn : {32, 64, 128, 256}) {
+    out[n++] = bn;
+    if (bn >= Bmax) break;
+  }
+  return n;
+}
+
+// Tensor maps of every projection on the tensor-core path, and the autotuned
+// batch tile bn per projection shape: each candidate is timed on the real
+// weights with max_streams rows (the batch tile does not change the
+// arithmetic of any output element, so the choice never changes results).
+static int tc_setup(nc_ctx* ctx) {
+  const Dims& D = ctx->D;
+  const int B = ctx->cfg.max_streams;
+  const int kb = ctx->fmt == NC_BF16;
+  const int esz = kb ? 2 : 1;
+  const int Kmax = std::max(std::max(D.d, D.hq * kHeadDim), D.F);
+  if (dalloc(ctx, &ctx->opnd, (size_t)B * Kmax * esz) || dalloc(ctx, &ctx->opnd_scale, (size_t)B * 4))
+    return fail(ctx, NC_ENOMEM, "tensor-core operand allocation");
+  NC_TRY(cudaMemset(ctx->opnd, 0, (size_t)B * Kmax * esz));
+  NC_TRY(cudaMemset(ctx->opnd_scale, 0, (size_t)B * 4));
+  auto add = [&](const Mat& m) {
+    TcMat t;
+    t.M = m.rows;
+    t.K = m.cols;
+    t.scale = m.scale;
+    if (!tc_encode_tmap(&t.a, m.w, esz, m.cols, m.rows, 128)) return false;
+    ctx->tc.push_back(t);
+    return true;
+  };
+  for (const LayerW& L : ctx->layers)
+    if (!add(L.qkv) || !add(L.o) || !add(L.gu) || !add(L.down)) return fail(ctx, NC_ECUDA, "tensor map encoding failed");
+  Mat head{ctx->embed, ctx->embed_scale, D.V, D.d};
+  if (!add(head)) return fail(ctx, NC_ECUDA, "tensor map encoding failed");
+  // autotune bn per distinct shape (layer 0's matrices and the LM head)
+  float* scratch = nullptr;
+  size_t maxM = 0;
+  for (const TcMat& t : ctx->tc) maxM = std::max(maxM, (size_t)t.M);
+  NC_TRY(cudaMalloc(&scratch, maxM * B * 4));
+  int32_t* nB = nullptr;
+  NC_TRY(cudaMalloc(&nB, 4));
+  NC_TRY(cudaMemcpy(nB, &B, 4, cudaMemcpyHostToDevice));
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  int cands[4];
+  const int nc = tc_bn_candidates(B, cands);
+  int chosen[5] = {0, 0, 0, 0, 0};
+  const int probe_idx[5] = {0, 1, 2, 3, (int)ctx->tc.size() - 1};
+  int st = NC_OK;
+  for (int q = 0; q < 5 && st == NC_OK; ++q) {
+    TcMat& t = ctx->tc[probe_idx[q]];
+    float best = 1e30f;
+    for (int ci = 0; ci < nc; ++ci) {
+      TcMat tt = t;
+      if (!tc_encode_tmap(&tt.b, ctx->opnd, esz, t.K, B, cands[ci])) {
+        st = fail(ctx, NC_ECUDA, "tensor map encoding failed");
+        break;
+      }
+      TcGemm g{};
+      g.tmap_a = &tt.a;
+      g.tmap_b = &tt.b;
+      g.M = t.M;
+      g.K = t.K;
+      g.Bmax = B;
+      g.bn = cands[ci];
+      g.kind_bf16 = kb;
+      g.nB = nB;
+      g.w_scale = t.scale;
+      g.x_scale = ctx->opnd_scale;
+      g.y = scratch;
+      g.status = ctx->d_status;
+      float ms_sum = 0.f;
+      for (int rep = 0; rep < 4; ++rep) {
+        cudaEventRecord(e0, ctx->stream);
+        cudaError_t e = launch_gemm_tc(g, EPI_STORE, ctx->stream, false);
+        cudaEventRecord(e1, ctx->stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        if (e != cudaSuccess) {
+          st = fail_cuda(ctx, e, "tensor-core autotune");
+          break;
+        }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (rep) ms_sum += ms;
+      }
+      if (st != NC_OK) break;
+      if (ms_sum < best) {
+        best = ms_sum;
+        chosen[q] = cands[ci];
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(scratch);
+  cudaFree(nB);
+  if (st != NC_OK) return st;
+  for (size_t i = 0; i < ctx->tc.size(); ++i) {
+    TcMat& t = ctx->tc[i];
+    t.bn = (i + 1 == ctx->tc.size()) ? chosen[4] : chosen[i % 4];
+    if (!tc_encode_tmap(&t.b, ctx->opnd, esz, t.K, B, t.bn)) return fail(ctx, NC_ECUDA, "tensor map encoding failed");
+  }
+  return NC_OK;
+}
+
 extern "C" int nc_ctx_create(const nc_config* cfg, const void* weights, size_t nbytes, nc_ctx** out) {
   if (!out) return NC_EINVAL;
   *out = nullptr;
@@ -266,6 +392,10 @@ extern "C" int nc_ctx_create(const nc_config* cfg, const void* weights, size_t n
     ctx->own_stream = true;
   }
   Dims& D = ctx->D;
+  {
+    const char* e = std::getenv("NC24_PDL");     // NC24_PDL=0 launches without PDL
+    D.pdl = (e && e[0] == '0') ? 0 : 1;
+  }
   D.n_layers = c.n_layers;
   D.d = c.d_model;
   D.hq = c.n_heads;
@@ -371,6 +501,11 @@ extern "C" int nc_ctx_create(const nc_config* cfg, const void* weights, size_t n
   ctx->h_st.assign(B, StreamDev{});
   ctx->slots.assign(B, Slot{});
   if (cudaMemset(ctx->d_st, 0, B * sizeof(StreamDev)) != cudaSuccess) return bail(NC_ECUDA);
+  if (cudaMemset(ctx->d_status, 0, B * 4) != cudaSuccess) return bail(NC_ECUDA);
+  if (c.path == NC_PATH_TC) {
+    const int st2 = tc_setup(ctx);
+    if (st2 != NC_OK) return bail(st2);
+  }
   *out = ctx;
   return NC_OK;
 }
@@ -525,11 +660,14 @@ struct StepMarks {
 };
 
 // Model forward of every active row: logits into each stream's z.
+static cudaError_t launch_model_tc(nc_ctx* ctx, const Batch& b, StepMarks& m);
+
 static cudaError_t launch_model(nc_ctx* ctx, const Batch& b, StepMarks* mk = nullptr) {
   const Dims& D = ctx->D;
   cudaStream_t s = ctx->stream;
   StepMarks none;
   StepMarks& m = mk ? *mk : none;
+  if (ctx->cfg.path == NC_PATH_TC) return launch_model_tc(ctx, b, m);
   cudaError_t e = launch_embed(D, b, ctx->embed, ctx->embed_scale, ctx->fmt, ctx->x, s);
   if (e == cudaSuccess) e = m.mark(s, TK_EMBED);
   for (int l = 0; l < D.n_layers && e == cudaSuccess; ++l) {
@@ -573,6 +711,57 @@ static cudaError_t launch_model(nc_ctx* ctx, const Batch& b, StepMarks* mk = nul
     e = launch_gemv(D, b, head, ctx->fmt, PRO_RMSNORM, EPI_LOGITS, io, s);
     if (e == cudaSuccess) e = m.mark(s, TK_LMHEAD);
   }
+  return e;
+}
+
+// Model forward on the tensor-core path: each projection is one tcgen05 GEMM
+// over the batch, fed by a small kernel that writes its BF16 / E4M3 operand.
+static cudaError_t launch_model_tc(nc_ctx* ctx, const Batch& b, StepMarks& m) {
+  const Dims& D = ctx->D;
+  cudaStream_t s = ctx->stream;
+  const int kb = ctx->fmt == NC_BF16;
+  auto gemm = [&](const TcMat& t, int epi, float* y, float* h) {
+    TcGemm g{};
+    g.tmap_a = &t.a;
+    g.tmap_b = &t.b;
+    g.M = t.M;
+    g.K = t.K;
+    g.Bmax = b.Bmax;
+    g.bn = t.bn;
+    g.kind_bf16 = kb;
+    g.nB = b.nB;
+    g.w_scale = t.scale;
+    g.x_scale = ctx->opnd_scale;
+    g.y = y;
+    g.h_out = h;
+    g.st = b.st;
+    g.slots = b.slots;
+    g.status = ctx->d_status;
+    return launch_gemm_tc(g, epi, s, D.pdl);
+  };
+  cudaError_t e = launch_embed(D, b, ctx->embed, ctx->embed_scale, ctx->fmt, ctx->x, s);
+  if (e == cudaSuccess) e = m.mark(s, TK_EMBED);
+  for (int l = 0; l < D.n_layers && e == cudaSuccess; ++l) {
+    const LayerW& L = ctx->layers[l];
+    const TcMat* T = &ctx->tc[4 * l];
+    e = launch_act_rmsnorm(D, b, ctx->x, L.g_attn, D.d, kb, ctx->opnd, ctx->opnd_scale, s);
+    if (e == cudaSuccess) e = gemm(T[0], EPI_STORE, ctx->qkv, nullptr);
+    if (e == cudaSuccess) e = m.mark(s, TK_QKV);
+    if (e == cudaSuccess) e = launch_attn(D, b, l, ctx->qkv, ctx->part, s);
+    if (e == cudaSuccess) e = m.mark(s, TK_ATTN);
+    if (e == cudaSuccess) e = launch_act_merge(D, b, ctx->part, kb, ctx->opnd, ctx->opnd_scale, s);
+    if (e == cudaSuccess) e = gemm(T[1], EPI_RESID, ctx->x, nullptr);
+    if (e == cudaSuccess) e = m.mark(s, TK_O);
+    if (e == cudaSuccess) e = launch_act_rmsnorm(D, b, ctx->x, L.g_ffn, D.d, kb, ctx->opnd, ctx->opnd_scale, s);
+    if (e == cudaSuccess) e = gemm(T[2], EPI_SWIGLU, nullptr, ctx->h);
+    if (e == cudaSuccess) e = m.mark(s, TK_GU);
+    if (e == cudaSuccess) e = launch_act_plain(D, b, ctx->h, D.F, kb, ctx->opnd, ctx->opnd_scale, s);
+    if (e == cudaSuccess) e = gemm(T[3], EPI_RESID, ctx->x, nullptr);
+    if (e == cudaSuccess) e = m.mark(s, TK_DOWN);
+  }
+  if (e == cudaSuccess) e = launch_act_rmsnorm(D, b, ctx->x, ctx->g_final, D.d, kb, ctx->opnd, ctx->opnd_scale, s);
+  if (e == cudaSuccess) e = gemm(ctx->tc.back(), EPI_LOGITS, nullptr, nullptr);
+  if (e == cudaSuccess) e = m.mark(s, TK_LMHEAD);
   return e;
 }
 
@@ -626,9 +815,19 @@ static int stage_batch(nc_ctx* ctx, int n, const int32_t* ids, std::vector<int>*
   return NC_OK;
 }
 
-// Read and clear the sticky status words of the given slots.
+// Read and clear the sticky status words of the given slots (and the
+// context-wide word of the tensor-core GEMMs).
 static int check_status(nc_ctx* ctx, const std::vector<int>& slot_idx) {
   const size_t off = offsetof(StreamDev, status);
+  if (ctx->cfg.path == NC_PATH_TC) {
+    int32_t w = 0;
+    NC_TRY(cudaMemcpyAsync(&w, ctx->d_status, 4, cudaMemcpyDeviceToHost, ctx->stream));
+    NC_TRY(cudaStreamSynchronize(ctx->stream));
+    if (w) {
+      ctx->poisoned = true;
+      return fail(ctx, NC_ETIMEOUT, "a tensor-core pipeline wait gave up");
+    }
+  }
   for (size_t j = 0; j < slot_idx.size(); ++j)
     NC_TRY(cudaMemcpyAsync(ctx->h_status + j, reinterpret_cast<char*>(ctx->d_st + slot_idx[j]) + off, 4,
                            cudaMemcpyDeviceToHost, ctx->stream));
@@ -1180,6 +1379,42 @@ extern "C" int nc_floor_counts(const float* p, int64_t n, uint32_t K, uint32_t f
   if (!p || !c || n < 0 || K < 1 || K >= (1u << 24)) return NC_EINVAL;
   if (n == 0) return NC_OK;
   return launch_floor_counts(p, n, K, floor_c, c, static_cast<cudaStream_t>(stream)) == cudaSuccess ? NC_OK : NC_ECUDA;
+}
+
+extern "C" int nc_gemm_tc(const void* W, const void* X, const float* w_scale, const float* x_scale, int fp8, int M,
+                          int N, int K, int bn, float* Y, void* stream) {
+  if (!W || !X || !Y || M < 1 || N < 1 || K < 1 || (fp8 && (!w_scale || !x_scale))) return NC_EINVAL;
+  if (bn != 32 && bn != 64 && bn != 128 && bn != 256) return NC_EINVAL;
+  const int esz = fp8 ? 1 : 2;
+  if ((K * esz) % 16 || (reinterpret_cast<uintptr_t>(W) | reinterpret_cast<uintptr_t>(X)) % 16) return NC_EINVAL;
+  TcMat t;
+  if (!tc_encode_tmap(&t.a, W, esz, K, M, 128) || !tc_encode_tmap(&t.b, X, esz, K, N, bn)) return NC_EINVAL;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int32_t* dev = nullptr;
+  if (cudaMalloc(&dev, 8) != cudaSuccess) return NC_ENOMEM;
+  const int32_t h[2] = {N, 0};
+  int rc = NC_OK;
+  int32_t back[2] = {0, 0};
+  TcGemm g{};
+  g.tmap_a = &t.a;
+  g.tmap_b = &t.b;
+  g.M = M;
+  g.K = K;
+  g.Bmax = N;
+  g.bn = bn;
+  g.kind_bf16 = !fp8;
+  g.nB = dev;
+  g.w_scale = w_scale;
+  g.x_scale = x_scale;
+  g.y = Y;
+  g.status = dev + 1;
+  if (cudaMemcpyAsync(dev, h, 8, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+      launch_gemm_tc(g, EPI_STORE, s, false) != cudaSuccess ||
+      cudaMemcpyAsync(back, dev, 8, cudaMemcpyDeviceToHost, s) != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess)
+    rc = NC_ECUDA;
+  cudaFree(dev);
+  if (rc == NC_OK && back[1]) rc = NC_ETIMEOUT;
+  return rc;
 }
 
 extern "C" int nc_ac_encode(const uint32_t* lo, const uint32_t* hi, int64_t n, int log2_total, uint8_t* out,

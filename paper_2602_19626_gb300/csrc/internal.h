@@ -22,6 +22,7 @@ enum : int32_t {
   ST_NUMERIC = 1,      // non-finite / out-of-range probability or floor underflow
   ST_TABLE_FULL = 2,   // N-gram tables exhausted (stream longer than expected_len)
   ST_BAD_TOKEN = 4,    // observed token out of range
+  ST_TIMEOUT = 8,      // a bounded device wait gave up
 };
 
 // One N-gram context: retained continuation slots in arrival / replacement
@@ -57,6 +58,7 @@ struct StreamDev {
 };
 
 struct Dims {
+  int pdl;                  // launch step kernels with programmatic dependent launch
   int n_layers, d, hq, hkv, F, V, L, C;
   int qkv_rows;             // (hq + 2 hkv) * 64
   float eps, theta, tau;
@@ -91,6 +93,31 @@ struct Batch {
   StreamDev* st;            // [max_streams]
   int Bmax;
 };
+
+// Programmatic dependent launch: a kernel launched with the PDL attribute may
+// start while its predecessor still runs.  Each step kernel loads only data
+// no in-flight kernel writes (weights, KV entries of earlier tokens, state of
+// earlier steps) before pdl_wait(), and signals its own dependents only
+// after pdl_wait(); so when a kernel's pdl_wait() returns, every earlier
+// kernel of the stream has completed and its writes are visible.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_kernel(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                                 cudaStream_t s, bool pdl, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = pdl ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
+}
 
 // Largest number of attention chunks (split-KV CTAs) of one (stream, KV head).
 __host__ __device__ inline int attn_splits_max_dev(const Dims& D) {
@@ -140,6 +167,31 @@ cudaError_t launch_convert_weights(const float* src, void* dst, float* scale, in
                                    int64_t cols, int fmt, cudaStream_t s);
 cudaError_t launch_interleave_f32(const float* gate, const float* up, float* dst, int64_t rows,
                                   int64_t cols, cudaStream_t s);
+// tcgen05 GEMM of one projection: Y[n][m] = sum_k W[m][k] X[n][k] with W the
+// weights [M, K] and X the batch operand [Bmax, K] (BF16, or E4M3 with
+// per-row scales), FP32 accumulation, fused epilogue.
+struct TcGemm {
+  const void* tmap_a;       // host copy of the weights' CUtensorMap (box 128 rows)
+  const void* tmap_b;       // host copy of the operand's CUtensorMap (box bn rows)
+  int M, K, Bmax, bn, kind_bf16;
+  const int32_t* nB;
+  const float* w_scale;     // FP8: [M]
+  const float* x_scale;     // FP8: [Bmax]
+  float* y;                 // EPI_STORE / EPI_RESID: [Bmax][M]
+  float* h_out;             // EPI_SWIGLU: [Bmax][M / 2]
+  StreamDev* st;            // EPI_LOGITS
+  const int32_t* slots;
+  int32_t* status;          // error word (ST_TIMEOUT)
+};
+bool tc_encode_tmap(void* tmap, const void* base, int elem_bytes, int64_t inner, int64_t outer, int box_outer);
+cudaError_t launch_gemm_tc(const TcGemm& g, int epi, cudaStream_t s, bool pdl);
+cudaError_t launch_act_rmsnorm(const Dims& D, const Batch& b, const float* x, const float* gain, int cols,
+                               int kind_bf16, void* out, float* out_scale, cudaStream_t s);
+cudaError_t launch_act_merge(const Dims& D, const Batch& b, const float* part, int kind_bf16, void* out,
+                             float* out_scale, cudaStream_t s);
+cudaError_t launch_act_plain(const Dims& D, const Batch& b, const float* x, int cols, int kind_bf16, void* out,
+                             float* out_scale, cudaStream_t s);
+
 cudaError_t launch_probs_to_cdf(const float* p, int n, int V, int log2T, uint32_t floor,
                                 uint32_t* cdf, int32_t* status, cudaStream_t s);
 cudaError_t launch_floor_counts(const float* p, int64_t n, uint32_t K, uint32_t floor,

@@ -1,0 +1,481 @@
+// tcgen05 tensor-core GEMM for the batched projections.
+//
+// Y[n][m] = sum_k W[m][k] X[n][k]: the weight matrix W [M, K] is the MMA's A
+// operand (M = output channels, 128 per CTA), the batch of activation rows
+// X [N, K] is the B operand (N = streams, BN per CTA).  Both are K-major and
+// staged by TMA into 128-byte-swizzled shared memory through a ring of
+// STAGES buffers; one thread issues tcgen05.mma (kind::f16 for BF16,
+// kind::f8f6f4 for FP8 E4M3) into an FP32 accumulator in tensor memory; after
+// the last K block the four warps read the accumulator back with tcgen05.ld
+// and apply the fused epilogue.  Every output element accumulates its K
+// blocks in the same order whatever BN, the grid or the batch, so results
+// do not depend on how many streams share a step.
+//
+// Every wait on an mbarrier is bounded; a wait that gives up records an error
+// in the context's status word, skips the remaining work and still frees the
+// tensor memory it holds.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_fp8.h>
+
+#include "internal.h"
+
+namespace nc {
+
+namespace {
+
+constexpr int kTcThreads = 128;
+constexpr int kTileM = 128;
+constexpr int kKBlockBytes = 128;            // one 128-byte swizzle row per operand row
+constexpr uint32_t kWaitLimit = 1u << 22;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+
+// Bounded wait for the phase with the given parity; false when it gave up.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  const uint32_t a = smem_u32(bar);
+  for (uint32_t it = 0; it < kWaitLimit; ++it) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (ok) return true;
+  }
+  return false;
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int c0, int c1) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::"r"(
+          smem_u32(dst)),
+      "l"(map), "r"(smem_u32(bar)), "r"(c0), "r"(c1)
+      : "memory");
+}
+
+// Shared-memory matrix descriptor of a K-major operand tile in the 128-byte
+// swizzle layout: rows of 128 bytes, 8-row (1024-byte) swizzle atoms.
+__device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFFu);      // start address, 16-byte units
+  d |= (uint64_t)1 << 16;                        // leading byte offset (unused when swizzled)
+  d |= (uint64_t)(1024 >> 4) << 32;              // stride byte offset: between 8-row groups
+  d |= (uint64_t)1 << 46;                        // descriptor version
+  d |= (uint64_t)2 << 61;                        // 128-byte swizzle
+  return d;
+}
+
+// Instruction descriptor: FP32 accumulator, K-major A and B, shape M x N.
+__host__ __device__ constexpr uint32_t idesc(int kind_bf16, int M, int N) {
+  return (1u << 4)                                     // D format F32
+         | ((kind_bf16 ? 1u : 0u) << 7)                // A: BF16 (kind::f16) or E4M3 (kind::f8f6f4)
+         | ((kind_bf16 ? 1u : 0u) << 10)               // B: same type as A
+         | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_issue(int kind_bf16, uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t id,
+                                          uint32_t accum) {
+  if (kind_bf16) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+            d_tmem),
+        "l"(a), "l"(b), "r"(id), "r"(accum));
+  } else {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+            d_tmem),
+        "l"(a), "l"(b), "r"(id), "r"(accum));
+  }
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ float silu(float a) { return a / (1.0f + expf(-a)); }
+
+template <int BN>
+__host__ __device__ constexpr uint32_t tmem_cols() {
+  return BN <= 32 ? 32 : BN <= 64 ? 64 : BN <= 128 ? 128 : 256;
+}
+
+template <int BN, int STAGES>
+__host__ __device__ constexpr size_t tc_smem_bytes() {
+  return 1024 /* alignment slack */ + (size_t)STAGES * (kTileM + BN) * kKBlockBytes + 256;
+}
+
+template <int BN, int STAGES, int KIND_BF16, int EPI>
+__global__ void __launch_bounds__(kTcThreads, 1)
+    k_gemm_tc(const __grid_constant__ CUtensorMap tA, const __grid_constant__ CUtensorMap tB, TcGemm g) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+  uint8_t* sA = base;
+  uint8_t* sB = base + (size_t)STAGES * kTileM * kKBlockBytes;
+  uint64_t* full = reinterpret_cast<uint64_t*>(sB + (size_t)STAGES * BN * kKBlockBytes);
+  uint64_t* empty = full + STAGES;
+  uint64_t* done = empty + STAGES;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
+  uint32_t* fail = tmem_slot + 1;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m0 = blockIdx.x * kTileM;
+  const int n0 = blockIdx.y * BN;
+  const int kblk = KIND_BF16 ? 64 : 128;             // elements per 128-byte K block
+  const int nk = (g.K + kblk - 1) / kblk;            // the tail block reads zeros past K
+  constexpr uint32_t kCols = tmem_cols<BN>();
+  constexpr uint32_t kStageBytes = (kTileM + BN) * kKBlockBytes;
+
+  pdl_wait();
+  pdl_trigger();
+  const int B = *g.nB;
+  if (n0 >= B) return;                            // uniform across the CTA
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(full + s, 1);
+      mbar_init(empty + s, 1);
+    }
+    mbar_init(done, 1);
+    *fail = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(kCols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+  const bool active = true;
+
+  if (active && threadIdx.x == 0) {
+    // TMA producer
+    for (int kb = 0; kb < nk; ++kb) {
+      const int s = kb % STAGES;
+      const uint32_t ph = (uint32_t)(kb / STAGES) & 1u;
+      if (kb >= STAGES && !mbar_wait(empty + s, ph ^ 1u)) {
+        atomicOr(fail, 1u);
+        break;
+      }
+      mbar_expect_tx(full + s, kStageBytes);
+      const int kc = kb * kblk;
+      tma_load_2d(sA + (size_t)s * kTileM * kKBlockBytes, &tA, full + s, kc, m0);
+      tma_load_2d(sB + (size_t)s * BN * kKBlockBytes, &tB, full + s, kc, n0);
+    }
+  } else if (active && threadIdx.x == 32) {
+    // MMA issuer: 4 instructions of 32 bytes of K per 128-byte block
+    const uint32_t id = idesc(KIND_BF16, kTileM, BN);
+    bool ok = true;
+    for (int kb = 0; kb < nk && ok; ++kb) {
+      const int s = kb % STAGES;
+      const uint32_t ph = (uint32_t)(kb / STAGES) & 1u;
+      if (!mbar_wait(full + s, ph)) {
+        atomicOr(fail, 2u);
+        ok = false;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t a0 = smem_u32(sA + (size_t)s * kTileM * kKBlockBytes);
+      const uint32_t b0 = smem_u32(sB + (size_t)s * BN * kKBlockBytes);
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+        mma_issue(KIND_BF16, tmem, sdesc_sw128(a0 + 32 * k), sdesc_sw128(b0 + 32 * k), id, (kb | k) ? 1u : 0u);
+      mma_commit(empty + s);
+    }
+    mma_commit(done);
+  }
+  __syncwarp();
+  // accumulator ready (or the pipeline gave up)
+  bool ready = active;
+  if (active && !mbar_wait(done, 0)) {
+    atomicOr(fail, 4u);
+    ready = false;
+  }
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (ready && *fail == 0) {
+    const int r = m0 + warp * 32 + lane;           // weight row = TMEM lane
+    const uint32_t tw = tmem + ((uint32_t)(warp * 32) << 16);
+    float ws = 1.f;
+    if (!KIND_BF16 && r < g.M) ws = g.w_scale[r];
+#pragma unroll 1
+    for (int c = 0; c < BN; c += 16) {
+      float v[16];
+      tmem_ld16(tw + (uint32_t)c, v);
+#pragma unroll
+      for (int i = 0; i < 16; ++i) {
+        const int n = n0 + c + i;
+        float y = v[i];
+        if (!KIND_BF16) y *= ws * (n < B ? g.x_scale[n] : 0.f);
+        if (EPI == EPI_SWIGLU) {
+          const float up = __shfl_xor_sync(0xffffffffu, y, 1);   // rows 2j (gate), 2j + 1 (up)
+          if (n < B && r < g.M && (r & 1) == 0) {
+            const float h = silu(y) * up;
+            g.h_out[(size_t)n * (g.M / 2) + (r >> 1)] = h;
+          }
+        } else if (n < B && r < g.M) {
+          if (EPI == EPI_STORE) {
+            g.y[(size_t)n * g.M + r] = y;
+          } else if (EPI == EPI_RESID) {
+            g.y[(size_t)n * g.M + r] += y;
+          } else {
+            g.st[g.slots[n]].z[r] = y;
+          }
+        }
+      }
+    }
+  }
+  if (threadIdx.x == 0 && *fail && g.status) atomicOr(g.status, ST_TIMEOUT);
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kCols));
+}
+
+using EncodeTiled = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                 const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiled encode_fn() {
+  static EncodeTiled fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiled>(p);
+  }
+  return fn;
+}
+
+template <int BN, int STAGES, int KB, int EPI>
+cudaError_t launch_tc_t(const TcGemm& g, cudaStream_t s, bool pdl) {
+  constexpr size_t smem = tc_smem_bytes<BN, STAGES>();
+  auto kern = k_gemm_tc<BN, STAGES, KB, EPI>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  dim3 grid((g.M + kTileM - 1) / kTileM, (g.Bmax + BN - 1) / BN);
+  const CUtensorMap* a = reinterpret_cast<const CUtensorMap*>(g.tmap_a);
+  const CUtensorMap* b = reinterpret_cast<const CUtensorMap*>(g.tmap_b);
+  return launch_kernel(kern, grid, dim3(kTcThreads), smem, s, pdl, *a, *b, g);
+}
+
+template <int BN, int KB, int EPI>
+cudaError_t launch_tc_bn(const TcGemm& g, cudaStream_t s, bool pdl) {
+  return launch_tc_t<BN, BN >= 256 ? 4 : 6, KB, EPI>(g, s, pdl);
+}
+
+template <int KB, int EPI>
+cudaError_t launch_tc_epi(const TcGemm& g, cudaStream_t s, bool pdl) {
+  switch (g.bn) {
+    case 32: return launch_tc_bn<32, KB, EPI>(g, s, pdl);
+    case 64: return launch_tc_bn<64, KB, EPI>(g, s, pdl);
+    case 128: return launch_tc_bn<128, KB, EPI>(g, s, pdl);
+    case 256: return launch_tc_bn<256, KB, EPI>(g, s, pdl);
+  }
+  return cudaErrorInvalidValue;
+}
+
+// ------------------------------------------------- activation preparation
+// RMSNorm of x into the GEMM operand (BF16, or E4M3 with one scale per row).
+template <int KB>
+__global__ void k_act_rmsnorm(Dims D, Batch b, const float* x, const float* gain, int cols, void* out,
+                              float* out_scale) {
+  __shared__ float red[32];
+  __shared__ float sc;
+  pdl_wait();
+  pdl_trigger();
+  const int j = blockIdx.x;
+  if (j >= *b.nB) return;
+  const float* xr = x + (size_t)j * cols;
+  float ss = 0.f;
+  for (int c = threadIdx.x; c < cols; c += blockDim.x) ss = fmaf(xr[c], xr[c], ss);
+  for (int o = 16; o; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = ss;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float t = 0.f;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    sc = 1.0f / sqrtf(t / (float)cols + D.eps);
+  }
+  __syncthreads();
+  const float inv = sc;
+  if (KB) {
+    __nv_bfloat16* o = static_cast<__nv_bfloat16*>(out) + (size_t)j * cols;
+    for (int c = threadIdx.x; c < cols; c += blockDim.x) o[c] = __float2bfloat16_rn(xr[c] * inv * gain[c]);
+  } else {
+    // per-row E4M3 scale: amax / 448 (max is order-independent)
+    float m = 0.f;
+    for (int c = threadIdx.x; c < cols; c += blockDim.x) m = fmaxf(m, fabsf(xr[c] * inv * gain[c]));
+    for (int o = 16; o; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      float t = 0.f;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t = fmaxf(t, red[w]);
+      const float s = t > 0.f ? __fdiv_rn(t, 448.0f) : 1.0f;
+      out_scale[j] = s;
+      red[0] = s;
+    }
+    __syncthreads();
+    const float s = red[0];
+    __nv_fp8_storage_t* o = static_cast<__nv_fp8_storage_t*>(out) + (size_t)j * cols;
+    for (int c = threadIdx.x; c < cols; c += blockDim.x)
+      o[c] = __nv_cvt_float_to_fp8(__fdiv_rn(xr[c] * inv * gain[c], s), __NV_SATFINITE, __NV_E4M3);
+  }
+}
+
+// Write a row held in shared memory as the GEMM operand: BF16, or E4M3 with
+// the row's scale amax / 448.
+template <int KB>
+__device__ void write_operand(const float* buf, int cols, int j, void* out, float* out_scale, float* red) {
+  if (KB) {
+    __nv_bfloat16* o = static_cast<__nv_bfloat16*>(out) + (size_t)j * cols;
+    for (int c = threadIdx.x; c < cols; c += blockDim.x) o[c] = __float2bfloat16_rn(buf[c]);
+    return;
+  }
+  float m = 0.f;
+  for (int c = threadIdx.x; c < cols; c += blockDim.x) m = fmaxf(m, fabsf(buf[c]));
+  for (int o = 16; o; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float t = 0.f;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t = fmaxf(t, red[w]);
+    const float sc = t > 0.f ? __fdiv_rn(t, 448.0f) : 1.0f;
+    out_scale[j] = sc;
+    red[32] = sc;
+  }
+  __syncthreads();
+  const float sc = red[32];
+  __nv_fp8_storage_t* o = static_cast<__nv_fp8_storage_t*>(out) + (size_t)j * cols;
+  for (int c = threadIdx.x; c < cols; c += blockDim.x)
+    o[c] = __nv_cvt_float_to_fp8(__fdiv_rn(buf[c], sc), __NV_SATFINITE, __NV_E4M3);
+}
+
+// Merge the split-KV attention partials of every head (same arithmetic as the
+// GEMV path's attention prologue) into the O-projection operand.
+template <int KB>
+__global__ void k_act_merge(Dims D, Batch b, const float* part, void* out, float* out_scale) {
+  __shared__ float buf[kMaxGroup * 16 * kHeadDim];
+  __shared__ float red[33];
+  pdl_wait();
+  pdl_trigger();
+  const int j = blockIdx.x;
+  if (j >= *b.nB) return;
+  const StreamDev& st = b.st[b.slots[j]];
+  int start = st.kv_start;
+  if (st.n_coded - start == D.L) start += D.C;
+  const int n = st.n_coded - start + 1;
+  const int ns = (n + kAttnChunk - 1) / kAttnChunk;
+  const int nsm = attn_splits_max_dev(D);
+  const int cols = D.hq * kHeadDim;
+  for (int e = threadIdx.x; e < cols; e += blockDim.x) {
+    const int h = e / kHeadDim, dd = e % kHeadDim;
+    const float* ph = part + ((size_t)j * D.hq + h) * nsm * (kHeadDim + 2);
+    float M = -INFINITY;
+    for (int s = 0; s < ns; ++s) M = fmaxf(M, ph[s * (kHeadDim + 2) + kHeadDim]);
+    float l = 0.f, acc = 0.f;
+    for (int s = 0; s < ns; ++s) {
+      const float* p = ph + s * (kHeadDim + 2);
+      const float f = expf(p[kHeadDim] - M);
+      l = fmaf(p[kHeadDim + 1], f, l);
+      acc = fmaf(p[dd], f, acc);
+    }
+    buf[e] = acc / l;
+  }
+  __syncthreads();
+  write_operand<KB>(buf, cols, j, out, out_scale, red);
+}
+
+// An FP32 activation row (the SwiGLU output) as the GEMM operand.
+template <int KB>
+__global__ void k_act_plain(Dims D, Batch b, const float* x, int cols, void* out, float* out_scale) {
+  __shared__ float red[33];
+  pdl_wait();
+  pdl_trigger();
+  const int j = blockIdx.x;
+  if (j >= *b.nB) return;
+  write_operand<KB>(x + (size_t)j * cols, cols, j, out, out_scale, red);
+}
+
+}  // namespace
+
+cudaError_t launch_act_merge(const Dims& D, const Batch& b, const float* part, int kind_bf16, void* out,
+                             float* out_scale, cudaStream_t s) {
+  return launch_kernel(kind_bf16 ? k_act_merge<1> : k_act_merge<0>, dim3(b.Bmax), dim3(256), 0, s, D.pdl, D, b,
+                       part, out, out_scale);
+}
+
+cudaError_t launch_act_plain(const Dims& D, const Batch& b, const float* x, int cols, int kind_bf16, void* out,
+                             float* out_scale, cudaStream_t s) {
+  return launch_kernel(kind_bf16 ? k_act_plain<1> : k_act_plain<0>, dim3(b.Bmax), dim3(256), 0, s, D.pdl, D, b, x,
+                       cols, out, out_scale);
+}
+
+bool tc_encode_tmap(void* tmap, const void* base, int elem_bytes, int64_t inner, int64_t outer, int box_outer) {
+  EncodeTiled fn = encode_fn();
+  if (!fn) return false;
+  cuuint64_t dims[2] = {(cuuint64_t)inner, (cuuint64_t)outer};
+  cuuint64_t strides[1] = {(cuuint64_t)(inner * elem_bytes)};
+  cuuint32_t box[2] = {(cuuint32_t)(kKBlockBytes / elem_bytes), (cuuint32_t)box_outer};
+  cuuint32_t es[2] = {1, 1};
+  const CUtensorMapDataType dt = elem_bytes == 2 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_UINT8;
+  return fn(reinterpret_cast<CUtensorMap*>(tmap), dt, 2, const_cast<void*>(base), dims, strides, box, es,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+cudaError_t launch_gemm_tc(const TcGemm& g, int epi, cudaStream_t s, bool pdl) {
+  if (g.kind_bf16) {
+    switch (epi) {
+      case EPI_STORE: return launch_tc_epi<1, EPI_STORE>(g, s, pdl);
+      case EPI_RESID: return launch_tc_epi<1, EPI_RESID>(g, s, pdl);
+      case EPI_SWIGLU: return launch_tc_epi<1, EPI_SWIGLU>(g, s, pdl);
+      case EPI_LOGITS: return launch_tc_epi<1, EPI_LOGITS>(g, s, pdl);
+    }
+  } else {
+    switch (epi) {
+      case EPI_STORE: return launch_tc_epi<0, EPI_STORE>(g, s, pdl);
+      case EPI_RESID: return launch_tc_epi<0, EPI_RESID>(g, s, pdl);
+      case EPI_SWIGLU: return launch_tc_epi<0, EPI_SWIGLU>(g, s, pdl);
+      case EPI_LOGITS: return launch_tc_epi<0, EPI_LOGITS>(g, s, pdl);
+    }
+  }
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_act_rmsnorm(const Dims& D, const Batch& b, const float* x, const float* gain, int cols,
+                               int kind_bf16, void* out, float* out_scale, cudaStream_t s) {
+  return launch_kernel(kind_bf16 ? k_act_rmsnorm<1> : k_act_rmsnorm<0>, dim3(b.Bmax), dim3(256), 0, s, D.pdl, D, b,
+                       x, gain, cols, out, out_scale);
+}
+
+}  // namespace nc

@@ -101,6 +101,8 @@ __device__ __forceinline__ float silu(float a) { return a / (1.0f + expf(-a)); }
 template <int FMT>
 __global__ void k_embed(Dims D, Batch b, const void* E, const float* Escale, float* x) {
   const int j = blockIdx.x;
+  pdl_wait();
+  pdl_trigger();
   if (j >= *b.nB) return;
   const StreamDev& st = b.st[b.slots[j]];
   const int tok = st.last_tok;
@@ -135,9 +137,9 @@ __global__ void __launch_bounds__(kGemvThreads) k_gemv(Dims D, Batch b, Mat m, G
   __shared__ float inv_rms[kGemvBT];
   using W = WFmt<FMT>;
   constexpr int VW = W::VW;
+  constexpr int kHold = 8;                       // 16-byte vectors per row held in registers
   const int cols = m.cols;
   const int nvec = cols / VW;
-  const int B = *b.nB;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int row0 = (blockIdx.x * kGemvWarps + warp) * kRowsPerWarp;
   const bool have_rows = row0 < m.rows;
@@ -148,6 +150,20 @@ __global__ void __launch_bounds__(kGemvThreads) k_gemv(Dims D, Batch b, Mat m, G
   const uint4* w1 = reinterpret_cast<const uint4*>(static_cast<const char*>(m.w) +
                                                    (size_t)row1 * cols * W::ESZ);
   const int nsm = attn_splits_max_dev(D);
+  // Weights do not depend on earlier kernels: fetch this warp's rows before
+  // waiting on the predecessor, so the fetch overlaps its execution.
+  uint4 h0[kHold], h1[kHold];
+#pragma unroll
+  for (int k = 0; k < kHold; ++k) {
+    const int v = lane + 32 * k;
+    if (have_rows && v < nvec) {
+      h0[k] = ld_stream(w0 + v);
+      h1[k] = ld_stream(w1 + v);
+    }
+  }
+  pdl_wait();
+  pdl_trigger();
+  const int B = *b.nB;
 
   for (int b0 = 0; b0 < B; b0 += kGemvBT) {
     const int nb = min(kGemvBT, B - b0);
@@ -204,7 +220,37 @@ __global__ void __launch_bounds__(kGemvThreads) k_gemv(Dims D, Batch b, Mat m, G
       float acc0[kGemvBT], acc1[kGemvBT];
 #pragma unroll
       for (int bt = 0; bt < kGemvBT; ++bt) acc0[bt] = acc1[bt] = 0.f;
-      for (int v0 = lane; v0 < nvec; v0 += 32 * kLoadBatch) {
+      // lane l accumulates vectors l, l + 32, l + 64, ... in increasing order:
+      // first the held ones, then the rest of a long row streamed in batches
+      auto fma_vec = [&](const uint4& a0, const uint4& a1, int v) {
+        float f0[VW], f1[VW];
+        W::deq(a0, f0);
+        W::deq(a1, f1);
+#pragma unroll
+        for (int bt = 0; bt < kGemvBT; ++bt) {
+          if (bt < nb) {
+            const float4* xr = reinterpret_cast<const float4*>(xs + bt * cols + v * VW);
+#pragma unroll
+            for (int q = 0; q < VW / 4; ++q) {
+              const float4 xv = xr[q];
+              acc0[bt] = fmaf(f0[4 * q + 0], xv.x, acc0[bt]);
+              acc0[bt] = fmaf(f0[4 * q + 1], xv.y, acc0[bt]);
+              acc0[bt] = fmaf(f0[4 * q + 2], xv.z, acc0[bt]);
+              acc0[bt] = fmaf(f0[4 * q + 3], xv.w, acc0[bt]);
+              acc1[bt] = fmaf(f1[4 * q + 0], xv.x, acc1[bt]);
+              acc1[bt] = fmaf(f1[4 * q + 1], xv.y, acc1[bt]);
+              acc1[bt] = fmaf(f1[4 * q + 2], xv.z, acc1[bt]);
+              acc1[bt] = fmaf(f1[4 * q + 3], xv.w, acc1[bt]);
+            }
+          }
+        }
+      };
+#pragma unroll
+      for (int k = 0; k < kHold; ++k) {
+        const int v = lane + 32 * k;
+        if (v < nvec) fma_vec(h0[k], h1[k], v);
+      }
+      for (int v0 = lane + 32 * kHold; v0 < nvec; v0 += 32 * kLoadBatch) {
         uint4 u0[kLoadBatch], u1[kLoadBatch];
 #pragma unroll
         for (int k = 0; k < kLoadBatch; ++k) {
@@ -217,29 +263,7 @@ __global__ void __launch_bounds__(kGemvThreads) k_gemv(Dims D, Batch b, Mat m, G
 #pragma unroll
         for (int k = 0; k < kLoadBatch; ++k) {
           const int v = v0 + 32 * k;
-          if (v < nvec) {
-            float f0[VW], f1[VW];
-            W::deq(u0[k], f0);
-            W::deq(u1[k], f1);
-#pragma unroll
-            for (int bt = 0; bt < kGemvBT; ++bt) {
-              if (bt < nb) {
-                const float4* xr = reinterpret_cast<const float4*>(xs + bt * cols + v * VW);
-#pragma unroll
-                for (int q = 0; q < VW / 4; ++q) {
-                  const float4 xv = xr[q];
-                  acc0[bt] = fmaf(f0[4 * q + 0], xv.x, acc0[bt]);
-                  acc0[bt] = fmaf(f0[4 * q + 1], xv.y, acc0[bt]);
-                  acc0[bt] = fmaf(f0[4 * q + 2], xv.z, acc0[bt]);
-                  acc0[bt] = fmaf(f0[4 * q + 3], xv.w, acc0[bt]);
-                  acc1[bt] = fmaf(f1[4 * q + 0], xv.x, acc1[bt]);
-                  acc1[bt] = fmaf(f1[4 * q + 1], xv.y, acc1[bt]);
-                  acc1[bt] = fmaf(f1[4 * q + 2], xv.z, acc1[bt]);
-                  acc1[bt] = fmaf(f1[4 * q + 3], xv.w, acc1[bt]);
-                }
-              }
-            }
-          }
+          if (v < nvec) fma_vec(u0[k], u1[k], v);
         }
       }
       float s0 = 1.f, s1 = 1.f;
@@ -308,6 +332,8 @@ __global__ void __launch_bounds__(128) k_attn(Dims D, Batch b, int layer, const 
   __shared__ float wm[4][kMaxGroup], wl[4][kMaxGroup];
   __shared__ float wacc[4][kMaxGroup][kHeadDim];
 
+  // ---- before waiting on the QKV projection: rotation angles of position a
+  // (FP64 angle, rounded once) and this lane's cached key (earlier tokens)
   if (tid < kHeadDim / 2) {
     const double inv_freq = pow((double)D.theta, -2.0 * tid / (double)kHeadDim);
     double sd, cd;
@@ -315,6 +341,47 @@ __global__ void __launch_bounds__(128) k_attn(Dims D, Batch b, int layer, const 
     cs[tid] = (float)cd;
     sn[tid] = (float)sd;
   }
+  const size_t plane = (size_t)D.L * kHeadDim;     // one [L][64] K or V plane
+  const size_t layer_off = (size_t)layer * 2 * D.hkv * plane;
+  const size_t koff = layer_off + (size_t)g * plane;
+  const size_t voff = layer_off + (size_t)(D.hkv + g) * plane;
+  const int p_lo = start + s * kAttnChunk + warp * 32;
+  const int p = p_lo + lane;
+  const bool valid = p <= a;
+  float kr[kHeadDim];
+  if (valid && p != a) {
+    const size_t ri = (size_t)(p & (D.L - 1)) * kHeadDim;
+    if (KBF16) {
+      const __nv_bfloat16* kvb = static_cast<const __nv_bfloat16*>(st.kv);
+      const uint4* src = reinterpret_cast<const uint4*>(kvb + koff + ri);
+#pragma unroll
+      for (int q = 0; q < kHeadDim / 8; ++q) {
+        const uint4 u = src[q];
+        const uint32_t w[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          kr[8 * q + 2 * i] = __uint_as_float(w[i] << 16);
+          kr[8 * q + 2 * i + 1] = __uint_as_float(w[i] & 0xFFFF0000u);
+        }
+      }
+      asm volatile("prefetch.global.L2 [%0];" ::"l"(kvb + voff + ri));
+    } else {
+      const float* kvf = static_cast<const float*>(st.kv);
+      const float4* src = reinterpret_cast<const float4*>(kvf + koff + ri);
+#pragma unroll
+      for (int q = 0; q < kHeadDim / 4; ++q) {
+        const float4 u = src[q];
+        kr[4 * q] = u.x;
+        kr[4 * q + 1] = u.y;
+        kr[4 * q + 2] = u.z;
+        kr[4 * q + 3] = u.w;
+      }
+      asm volatile("prefetch.global.L2 [%0];" ::"l"(kvf + voff + ri));
+      asm volatile("prefetch.global.L2 [%0];" ::"l"(kvf + voff + ri + 32));
+    }
+  }
+  pdl_wait();
+  pdl_trigger();
   __syncthreads();
   const float* row = qkv + (size_t)j * D.qkv_rows;
   for (int e = tid; e < (grp + 1) * (kHeadDim / 2); e += blockDim.x) {
@@ -334,10 +401,7 @@ __global__ void __launch_bounds__(128) k_attn(Dims D, Batch b, int layer, const 
   if (tid < kHeadDim) vn[tid] = row[(D.hq + D.hkv) * kHeadDim + g * kHeadDim + tid];
   __syncthreads();
 
-  const size_t plane = (size_t)D.L * kHeadDim;     // one [L][64] K or V plane
-  const size_t layer_off = (size_t)layer * 2 * D.hkv * plane;
-  const size_t koff = layer_off + (size_t)g * plane;
-  const size_t voff = layer_off + (size_t)(D.hkv + g) * plane;
+  // the last chunk appends the new key / value at ring index a mod L
   if (s == ns - 1 && tid < kHeadDim) {
     const size_t ri = (size_t)(a & (D.L - 1)) * kHeadDim + tid;
     if (KBF16) {
@@ -351,42 +415,13 @@ __global__ void __launch_bounds__(128) k_attn(Dims D, Batch b, int layer, const 
     }
   }
 
-  const int p_lo = start + s * kAttnChunk + warp * 32;
-  const int p = p_lo + lane;
-  const bool valid = p <= a;
   float sc[kMaxGroup];
 #pragma unroll
   for (int h = 0; h < kMaxGroup; ++h) sc[h] = 0.f;
   if (valid) {
-    float kr[kHeadDim];
     if (p == a) {
 #pragma unroll
       for (int d = 0; d < kHeadDim; ++d) kr[d] = kn[d];
-    } else {
-      const size_t ri = (size_t)(p & (D.L - 1)) * kHeadDim;
-      if (KBF16) {
-        const uint4* src = reinterpret_cast<const uint4*>(static_cast<const __nv_bfloat16*>(st.kv) + koff + ri);
-#pragma unroll
-        for (int q = 0; q < kHeadDim / 8; ++q) {
-          const uint4 u = src[q];
-          const uint32_t w[4] = {u.x, u.y, u.z, u.w};
-#pragma unroll
-          for (int i = 0; i < 4; ++i) {
-            kr[8 * q + 2 * i] = __uint_as_float(w[i] << 16);
-            kr[8 * q + 2 * i + 1] = __uint_as_float(w[i] & 0xFFFF0000u);
-          }
-        }
-      } else {
-        const float4* src = reinterpret_cast<const float4*>(static_cast<const float*>(st.kv) + koff + ri);
-#pragma unroll
-        for (int q = 0; q < kHeadDim / 4; ++q) {
-          const float4 u = src[q];
-          kr[4 * q] = u.x;
-          kr[4 * q + 1] = u.y;
-          kr[4 * q + 2] = u.z;
-          kr[4 * q + 3] = u.w;
-        }
-      }
     }
 #pragma unroll
     for (int h = 0; h < kMaxGroup; ++h) {
@@ -522,13 +557,8 @@ int attn_max_splits(const Dims& D) { return (D.L + kAttnChunk - 1) / kAttnChunk;
 cudaError_t launch_embed(const Dims& D, const Batch& b, const void* E, const float* Escale,
                          int fmt, float* x, cudaStream_t s) {
   const int thr = 256;
-  if (fmt == NC_FP32)
-    k_embed<NC_FP32><<<b.Bmax, thr, 0, s>>>(D, b, E, Escale, x);
-  else if (fmt == NC_BF16)
-    k_embed<NC_BF16><<<b.Bmax, thr, 0, s>>>(D, b, E, Escale, x);
-  else
-    k_embed<NC_FP8E4M3><<<b.Bmax, thr, 0, s>>>(D, b, E, Escale, x);
-  return cudaGetLastError();
+  auto kern = fmt == NC_FP32 ? k_embed<NC_FP32> : fmt == NC_BF16 ? k_embed<NC_BF16> : k_embed<NC_FP8E4M3>;
+  return launch_kernel(kern, dim3(b.Bmax), dim3(thr), 0, s, D.pdl, D, b, E, Escale, x);
 }
 
 template <int FMT, int PRO, int EPI>
@@ -540,8 +570,7 @@ static cudaError_t gemv_t(const Dims& D, const Batch& b, const Mat& m, const Gem
   auto kern = k_gemv<FMT, PRO, EPI>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  kern<<<grid, kGemvThreads, smem, s>>>(D, b, m, io);
-  return cudaGetLastError();
+  return launch_kernel(kern, dim3(grid), dim3(kGemvThreads), smem, s, D.pdl, D, b, m, io);
 }
 
 template <int FMT>
@@ -565,11 +594,7 @@ cudaError_t launch_gemv(const Dims& D, const Batch& b, const Mat& m, int fmt, in
 cudaError_t launch_attn(const Dims& D, const Batch& b, int layer, const float* qkv, float* part,
                         cudaStream_t s) {
   dim3 grid(attn_max_splits(D), D.hkv, b.Bmax);
-  if (D.kv_bf16)
-    k_attn<1><<<grid, 128, 0, s>>>(D, b, layer, qkv, part);
-  else
-    k_attn<0><<<grid, 128, 0, s>>>(D, b, layer, qkv, part);
-  return cudaGetLastError();
+  return launch_kernel(D.kv_bf16 ? k_attn<1> : k_attn<0>, grid, dim3(128), 0, s, D.pdl, D, b, layer, qkv, part);
 }
 
 cudaError_t launch_convert_weights(const float* src, void* dst, float* scale, int64_t rows,

@@ -293,52 +293,17 @@ __global__ void __cluster_dims__(kVocabCluster, 1, 1) __launch_bounds__(kVocabTh
   const int v0 = base + threadIdx.x * E;
   const int i_tok = st.n_coded + 1;              // 1-based index of the token being coded
   const float th0 = st.theta[0], th1 = st.theta[1];
-  const int t_obs = (io.update || io.intervals) ? b.obs[j] : -1;
-  if (io.update && (t_obs < 0 || t_obs >= V)) {   // rejected on the host; never index with it
-    if (rank == 0 && threadIdx.x == 0) atomicOr(&st.status, ST_BAD_TOKEN);
-    return;
-  }
 
-  // ---- biased logits s = z / tau + b
-  float s[E], bias[E];
-  load_run<E>(st.z, v0, V, s, -INFINITY);
-  if (io.probe_z) store_run<E>(io.probe_z + (size_t)j * V, v0, V, s);
+  // ---- before waiting on the LM head: bias and the N-gram distribution
+  // (state of earlier steps only)
+  float bias[E];
   if (D.use_head) {
     load_run<E>(st.bias, v0, V, bias, 0.f);
   } else {
 #pragma unroll
     for (int i = 0; i < E; ++i) bias[i] = 0.f;
   }
-#pragma unroll
-  for (int i = 0; i < E; ++i) s[i] = (v0 + i < V) ? __fdiv_rn(s[i], D.tau) + bias[i] : -INFINITY;
-
-  // ---- softmax: max and sum of exp in a fixed order
-  float mx = -INFINITY;
-#pragma unroll
-  for (int i = 0; i < E; ++i) mx = fmaxf(mx, s[i]);
-  mx = block_max(mx, sh);
-  if (threadIdx.x == 0) sh.cl_max = mx;
-  cl.sync();
-  float M = -INFINITY;
-  for (int r = 0; r < kVocabCluster; ++r) M = fmaxf(M, cl.map_shared_rank(&sh, r)->cl_max);
-  float e[E];
-  float ls = 0.f;
-#pragma unroll
-  for (int i = 0; i < E; ++i) {
-    e[i] = (v0 + i < V) ? expf(s[i] - M) : 0.f;
-    ls += e[i];
-  }
-  ls = block_sum(ls, sh);
-  if (threadIdx.x == 0) sh.cl_sum = ls;
-  cl.sync();
-  float S = 0.f;
-  for (int r = 0; r < kVocabCluster; ++r) S += cl.map_shared_rank(&sh, r)->cl_sum;
-  float pt[E];
-#pragma unroll
-  for (int i = 0; i < E; ++i) pt[i] = __fdiv_rn(e[i], S);
-  if (io.probe_pt) store_run<E>(io.probe_pt + (size_t)j * V, v0, V, pt);
-
-  // ---- N-gram: P = A (c + 1) / (N + V) + sum_k beta_k cnt_k / n_k, the closed
+  // N-gram: P = A (c + 1) / (N + V) + sum_k beta_k cnt_k / n_k, the closed
   // form of the interpolation recursion with lambda_k = n_k / (n_k + 5).
   float png[E];
   const bool ngram = D.order > 0;
@@ -392,11 +357,53 @@ __global__ void __cluster_dims__(kVocabCluster, 1, 1) __launch_bounds__(kVocabTh
     const float cu = sh.cu;
 #pragma unroll
     for (int i = 0; i < E; ++i) png[i] = (v0 + i < V) ? cu * (float)(cnt[i] + 1) + sp[threadIdx.x * E + i] : 0.f;
-    if (io.probe_png) store_run<E>(io.probe_png + (size_t)j * V, v0, V, png);
   } else {
 #pragma unroll
     for (int i = 0; i < E; ++i) png[i] = 0.f;
   }
+
+  pdl_wait();
+  pdl_trigger();
+  const int t_obs = (io.update || io.intervals) ? b.obs[j] : -1;
+  if (io.update && (t_obs < 0 || t_obs >= V)) {   // rejected on the host; never index with it
+    if (rank == 0 && threadIdx.x == 0) atomicOr(&st.status, ST_BAD_TOKEN);
+    cl.sync();
+    return;
+  }
+  if (io.probe_png && ngram) store_run<E>(io.probe_png + (size_t)j * V, v0, V, png);
+
+  // ---- biased logits s = z / tau + b
+  float s[E];
+  load_run<E>(st.z, v0, V, s, -INFINITY);
+  if (io.probe_z) store_run<E>(io.probe_z + (size_t)j * V, v0, V, s);
+#pragma unroll
+  for (int i = 0; i < E; ++i) s[i] = (v0 + i < V) ? __fdiv_rn(s[i], D.tau) + bias[i] : -INFINITY;
+
+  // ---- softmax: max and sum of exp in a fixed order
+  float mx = -INFINITY;
+#pragma unroll
+  for (int i = 0; i < E; ++i) mx = fmaxf(mx, s[i]);
+  mx = block_max(mx, sh);
+  if (threadIdx.x == 0) sh.cl_max = mx;
+  cl.sync();
+  float M = -INFINITY;
+  for (int r = 0; r < kVocabCluster; ++r) M = fmaxf(M, cl.map_shared_rank(&sh, r)->cl_max);
+  float e[E];
+  float ls = 0.f;
+#pragma unroll
+  for (int i = 0; i < E; ++i) {
+    e[i] = (v0 + i < V) ? expf(s[i] - M) : 0.f;
+    ls += e[i];
+  }
+  ls = block_sum(ls, sh);
+  if (threadIdx.x == 0) sh.cl_sum = ls;
+  cl.sync();
+  float S = 0.f;
+  for (int r = 0; r < kVocabCluster; ++r) S += cl.map_shared_rank(&sh, r)->cl_sum;
+  float pt[E];
+#pragma unroll
+  for (int i = 0; i < E; ++i) pt[i] = __fdiv_rn(e[i], S);
+  if (io.probe_pt) store_run<E>(io.probe_pt + (size_t)j * V, v0, V, pt);
 
   // ---- mix (Sec. 3.5): LLM alone during warm-up
   const bool mixing = ngram && i_tok > D.warmup;
@@ -515,6 +522,8 @@ __device__ int ng_find(StreamDev& st, int k, unsigned long long key, bool insert
 // the unigram counts, then advance the stream (window, history, position) and
 // look up the contexts of the next prediction.
 __global__ void k_ngram_update(Dims D, Batch b) {
+  pdl_wait();
+  pdl_trigger();
   const int j = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (j >= *b.nB) return;
@@ -602,6 +611,8 @@ __global__ void k_prepare_encode(Batch b, int n_streams, const int32_t* tok_flat
                                  const int64_t* offs, const int64_t* lens, int32_t* obs,
                                  int32_t* nB) {
   __shared__ int cnt[32];
+  pdl_wait();
+  pdl_trigger();
   int mine = 0;
   for (int j = threadIdx.x; j < n_streams; j += blockDim.x) {
     const int nc = b.st[b.slots[j]].n_coded;
@@ -695,6 +706,8 @@ __global__ void __launch_bounds__(kVocabThreads)
 // One warp per row: binary search of the decoder's target count in the CDF.
 __global__ void k_search(Batch b, int V, const uint32_t* cdf, const uint32_t* target, int32_t* obs,
                          uint32_t* lohi) {
+  pdl_wait();
+  pdl_trigger();
   const int j = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (j >= *b.nB || lane != 0) return;
@@ -727,8 +740,7 @@ static cudaError_t vocab_t(const Dims& D, const Batch& b, const VocabIO& io, cud
   const size_t smem = (size_t)kVocabThreads * E * sizeof(float);
   cudaError_t e = cudaFuncSetAttribute(k_vocab<E>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  k_vocab<E><<<b.Bmax * kVocabCluster, kVocabThreads, smem, s>>>(D, b, io);
-  return cudaGetLastError();
+  return launch_kernel(k_vocab<E>, dim3(b.Bmax * kVocabCluster), dim3(kVocabThreads), smem, s, D.pdl, D, b, io);
 }
 
 cudaError_t launch_vocab(const Dims& D, const Batch& b, const VocabIO& io, cudaStream_t s) {
@@ -744,15 +756,14 @@ cudaError_t launch_vocab(const Dims& D, const Batch& b, const VocabIO& io, cudaS
 cudaError_t launch_ngram_update(const Dims& D, const Batch& b, cudaStream_t s) {
   const int threads = 128;
   const int blocks = (b.Bmax * 32 + threads - 1) / threads;
-  k_ngram_update<<<blocks, threads, 0, s>>>(D, b);
-  return cudaGetLastError();
+  return launch_kernel(k_ngram_update, dim3(blocks), dim3(threads), 0, s, D.pdl, D, b);
 }
 
 cudaError_t launch_prepare_encode(const Batch& b, int n_streams, const int32_t* tok_flat,
                                   const int64_t* offs, const int64_t* lens, int32_t* obs,
                                   int32_t* nB, cudaStream_t s) {
-  k_prepare_encode<<<1, 1024, 0, s>>>(b, n_streams, tok_flat, offs, lens, obs, nB);
-  return cudaGetLastError();
+  return launch_kernel(k_prepare_encode, dim3(1), dim3(1024), 0, s, true, b, n_streams, tok_flat, offs, lens,
+                       obs, nB);
 }
 
 template <int E>

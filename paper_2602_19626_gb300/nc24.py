@@ -79,6 +79,7 @@ _SIGS = {
     "nc_floor_counts": (C.c_int, [_P, C.c_int64, C.c_uint32, C.c_uint32, _P, _P]),
     "nc_step_probe": (C.c_int, [_P, C.c_int, _P, _P, _P, _P, _P, _P]),
     "nc_stream_state": (C.c_int, [_P, C.c_int32, _P, _P, _P]),
+    "nc_gemm_tc": (C.c_int, [_P, _P, _P, _P, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, _P, _P]),
     "nc_ac_encode": (C.c_int, [_P, _P, C.c_int64, C.c_int, _P, _SZP, C.POINTER(C.c_uint64)]),
     "nc_ac_decode": (C.c_int, [_P, C.c_uint64, _P, C.c_int, C.c_int64, C.c_int, _P]),
     "nc_mix_nll_fwd": (C.c_int, [_P, _P, _P, _P, _P, _P, C.c_int, C.c_int, C.c_float, _P, _P]),
@@ -145,6 +146,14 @@ def nc_floor_counts(p, K, floor, c, stream=None) -> int:
     return lib.nc_floor_counts(_ptr(p), p.numel(), K, floor, _ptr(c), _stream_ptr(stream))
 
 
+def nc_gemm_tc(W, X, Y, bn=128, w_scale=None, x_scale=None, fp8=False, stream=None) -> int:
+    """W CUDA [M, K], X CUDA [N, K] (bf16, or uint8 E4M3 bytes with fp8); Y CUDA float32 [N, M]."""
+    M, K = W.shape
+    N = X.shape[0]
+    return lib.nc_gemm_tc(_ptr(W), _ptr(X), _ptr(w_scale), _ptr(x_scale), int(fp8), M, N, K, bn, _ptr(Y),
+                          _stream_ptr(stream))
+
+
 def nc_ac_encode(lo: np.ndarray, hi: np.ndarray, log2_total: int):
     """Encode intervals on the host; returns (bytes, nbits)."""
     lo = np.ascontiguousarray(lo, dtype=np.uint32)
@@ -188,7 +197,7 @@ def nc_mix_nll_bwd(z, b, p_ng, theta, target, warm, gout, tau, db, dtheta, strea
 
 def make_config(shape, fmt="bf16", rule="paper", max_streams=1, ngram_order=3, use_head=True,
                 warmup=100, log2_total=24, floor=1, alpha=1e-3, eta=1.0, w_llm=0.85, tau=1.0,
-                device=0, stream=None) -> nc_config:
+                device=0, stream=None, path="gemv") -> nc_config:
     """nc_config from a shape with the fields of synthetic.ModelShape."""
     c = nc_config_default()
     c.n_layers, c.d_model, c.n_heads = shape.n_layers, shape.d_model, shape.n_heads
@@ -201,7 +210,7 @@ def make_config(shape, fmt="bf16", rule="paper", max_streams=1, ngram_order=3, u
     c.warmup = warmup
     c.weight_fmt = FMT[fmt] if isinstance(fmt, str) else fmt
     c.update_rule = RULE[rule] if isinstance(rule, str) else rule
-    c.path = NC_PATH_GEMV
+    c.path = NC_PATH_GEMV if path == "gemv" else NC_PATH_TC
     c.max_streams, c.device = max_streams, device
     c.cuda_stream = _stream_ptr(stream) if stream is not None else None
     return c
