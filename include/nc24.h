@@ -219,6 +219,27 @@ const char* nc_last_error(const nc_ctx* ctx);
 int nc_probs_to_cdf(const float* p, int n, int V, int log2_total, uint32_t floor,
                     uint32_t* cdf, void* stream);
 
+/* nc_probs_to_cdf for callers that cannot let a library allocate device
+ * memory: for example a process whose allocator already holds all free HBM,
+ * a latency-critical loop where a cudaMalloc / cudaFree would synchronise
+ * the device, or code sharing a GPU with a framework that owns every
+ * allocation.  The paper has no counterpart; it is an interface addition.
+ * Same arguments, results and errors as nc_probs_to_cdf, but it calls no
+ * cudaMalloc, cudaFree or other allocating routine: the per-row status words
+ * live in a fixed device array of NC_NOALLOC_MAX_ROWS int32 that the library
+ * image carries, so every GPU that loads the library holds those 16 KB until
+ * the process exits.
+ *  - n > NC_NOALLOC_MAX_ROWS returns NC_EINVAL (split the rows over calls).
+ *  - The first call on a device looks up the array's device address
+ *    (cudaGetSymbolAddress); make that first call before any stream capture.
+ *  - Every call, on any stream, shares the one array; each call clears the
+ *    words it uses.  Calls whose GPU work overlaps (another host thread, or
+ *    another stream) race on it: serialise them.
+ *  - Synchronises `stream`. */
+#define NC_NOALLOC_MAX_ROWS 4096
+int nc_probs_to_cdf_noalloc(const float* p, int n, int V, int log2_total, uint32_t floor,
+                            uint32_t* cdf, void* stream);
+
 /* Elementwise exact product floor, c[i] = max(floor, floor(p[i] * K)), for
  * binary32 p[i] in [0, 2) and 0 < K < 2^24 (the quantiser's inner step,
  * Sec. 3.3).  p DEVICE float[n], c DEVICE uint32[n]; entries outside [0, 2)

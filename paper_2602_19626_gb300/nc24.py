@@ -76,6 +76,7 @@ _SIGS = {
     "nc_status_str": (C.c_char_p, [C.c_int]),
     "nc_last_error": (C.c_char_p, [_P]),
     "nc_probs_to_cdf": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, C.c_uint32, _P, _P]),
+    "nc_probs_to_cdf_noalloc": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, C.c_uint32, _P, _P]),
     "nc_floor_counts": (C.c_int, [_P, C.c_int64, C.c_uint32, C.c_uint32, _P, _P]),
     "nc_step_probe": (C.c_int, [_P, C.c_int, _P, _P, _P, _P, _P, _P]),
     "nc_stream_state": (C.c_int, [_P, C.c_int32, _P, _P, _P]),
@@ -140,6 +141,16 @@ def nc_probs_to_cdf(p, cdf, log2_total=24, floor=1, stream=None) -> int:
     """p: CUDA float32 [n, V]; cdf: CUDA int32/uint32 [n, V + 1]."""
     n, V = p.shape
     return lib.nc_probs_to_cdf(_ptr(p), n, V, log2_total, floor, _ptr(cdf), _stream_ptr(stream))
+
+
+NC_NOALLOC_MAX_ROWS = 4096
+
+
+def nc_probs_to_cdf_noalloc(p, cdf, log2_total=24, floor=1, stream=None) -> int:
+    """As nc_probs_to_cdf, without allocating device memory (at most
+    NC_NOALLOC_MAX_ROWS rows per call; calls must not overlap on the GPU)."""
+    n, V = p.shape
+    return lib.nc_probs_to_cdf_noalloc(_ptr(p), n, V, log2_total, floor, _ptr(cdf), _stream_ptr(stream))
 
 
 def nc_floor_counts(p, K, floor, c, stream=None) -> int:
