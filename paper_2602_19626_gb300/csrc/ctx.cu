@@ -70,6 +70,8 @@ struct nc_ctx {
   float* x = nullptr;
   float* qkv = nullptr;
   float* part = nullptr;
+  int* tickets = nullptr;            // [max_streams][hkv] attention merge tickets
+  float* attn_out = nullptr;         // [max_streams][hq * 64]
   float* h = nullptr;
   uint32_t* cdf = nullptr;
   int32_t* d_slots = nullptr;
@@ -488,6 +490,7 @@ extern "C" int nc_ctx_create(const nc_config* cfg, const void* weights, size_t n
   const int nsm = attn_max_splits(D);
   if (dalloc(ctx, &ctx->x, B * D.d * 4) || dalloc(ctx, &ctx->qkv, B * D.qkv_rows * 4) ||
       dalloc(ctx, &ctx->part, B * D.hq * nsm * (kHeadDim + 2) * 4) ||
+      dalloc(ctx, &ctx->tickets, B * D.hkv * 4) || dalloc(ctx, &ctx->attn_out, B * D.hq * kHeadDim * 4) ||
       dalloc(ctx, &ctx->h, B * D.F * 4) || dalloc(ctx, &ctx->cdf, B * (D.V + 1) * 4) ||
       dalloc(ctx, &ctx->d_slots, B * 4) || dalloc(ctx, &ctx->d_nB, 16) ||
       dalloc(ctx, &ctx->d_obs, B * 4) || dalloc(ctx, &ctx->d_target, B * 4) ||
@@ -501,7 +504,9 @@ extern "C" int nc_ctx_create(const nc_config* cfg, const void* weights, size_t n
   ctx->h_st.assign(B, StreamDev{});
   ctx->slots.assign(B, Slot{});
   if (cudaMemset(ctx->d_st, 0, B * sizeof(StreamDev)) != cudaSuccess) return bail(NC_ECUDA);
-  if (cudaMemset(ctx->d_status, 0, B * 4) != cudaSuccess) return bail(NC_ECUDA);
+  if (cudaMemset(ctx->d_status, 0, B * 4) != cudaSuccess ||
+      cudaMemset(ctx->tickets, 0, B * D.hkv * 4) != cudaSuccess)
+    return bail(NC_ECUDA);
   if (c.path == NC_PATH_TC) {
     const int st2 = tc_setup(ctx);
     if (st2 != NC_OK) return bail(st2);
@@ -678,13 +683,13 @@ static cudaError_t launch_model(nc_ctx* ctx, const Batch& b, StepMarks* mk = nul
     io.y = ctx->qkv;
     e = launch_gemv(D, b, L.qkv, ctx->fmt, PRO_RMSNORM, EPI_STORE, io, s);
     if (e == cudaSuccess) e = m.mark(s, TK_QKV);
-    if (e == cudaSuccess) e = launch_attn(D, b, l, ctx->qkv, ctx->part, s);
+    if (e == cudaSuccess) e = launch_attn(D, b, l, ctx->qkv, ctx->part, ctx->tickets, ctx->attn_out, s);
     if (e == cudaSuccess) e = m.mark(s, TK_ATTN);
     if (e == cudaSuccess) {
       io = GemvIO{};
-      io.part = ctx->part;
+      io.x = ctx->attn_out;
       io.y = ctx->x;
-      e = launch_gemv(D, b, L.o, ctx->fmt, PRO_ATTN, EPI_RESID, io, s);
+      e = launch_gemv(D, b, L.o, ctx->fmt, PRO_PLAIN, EPI_RESID, io, s);
       if (e == cudaSuccess) e = m.mark(s, TK_O);
     }
     if (e == cudaSuccess) {
@@ -747,9 +752,9 @@ static cudaError_t launch_model_tc(nc_ctx* ctx, const Batch& b, StepMarks& m) {
     e = launch_act_rmsnorm(D, b, ctx->x, L.g_attn, D.d, kb, ctx->opnd, ctx->opnd_scale, s);
     if (e == cudaSuccess) e = gemm(T[0], EPI_STORE, ctx->qkv, nullptr);
     if (e == cudaSuccess) e = m.mark(s, TK_QKV);
-    if (e == cudaSuccess) e = launch_attn(D, b, l, ctx->qkv, ctx->part, s);
+    if (e == cudaSuccess) e = launch_attn(D, b, l, ctx->qkv, ctx->part, ctx->tickets, ctx->attn_out, s);
     if (e == cudaSuccess) e = m.mark(s, TK_ATTN);
-    if (e == cudaSuccess) e = launch_act_merge(D, b, ctx->part, kb, ctx->opnd, ctx->opnd_scale, s);
+    if (e == cudaSuccess) e = launch_act_plain(D, b, ctx->attn_out, D.hq * kHeadDim, kb, ctx->opnd, ctx->opnd_scale, s);
     if (e == cudaSuccess) e = gemm(T[1], EPI_RESID, ctx->x, nullptr);
     if (e == cudaSuccess) e = m.mark(s, TK_O);
     if (e == cudaSuccess) e = launch_act_rmsnorm(D, b, ctx->x, L.g_ffn, D.d, kb, ctx->opnd, ctx->opnd_scale, s);

@@ -125,13 +125,12 @@ __host__ __device__ inline int attn_splits_max_dev(const Dims& D) {
 }
 
 // ------------------------------------------------------------------ kernels
-enum Prologue { PRO_RMSNORM = 0, PRO_ATTN = 1, PRO_PLAIN = 2 };
+enum Prologue { PRO_RMSNORM = 0, PRO_PLAIN = 2 };
 enum Epilogue { EPI_STORE = 0, EPI_RESID = 1, EPI_SWIGLU = 2, EPI_LOGITS = 3 };
 
 struct GemvIO {
   const float* x;           // PRO_RMSNORM / PRO_PLAIN input [Bmax][cols]
   const float* g;           // RMSNorm gain (PRO_RMSNORM)
-  const float* part;        // attention partials (PRO_ATTN)
   float* y;                 // EPI_STORE / EPI_SWIGLU output; EPI_RESID residual [Bmax][rows or rows/2]
 };
 
@@ -139,8 +138,10 @@ cudaError_t launch_embed(const Dims& D, const Batch& b, const void* E, const flo
                          int fmt, float* x, cudaStream_t s);
 cudaError_t launch_gemv(const Dims& D, const Batch& b, const Mat& m, int fmt, int pro, int epi,
                         const GemvIO& io, cudaStream_t s);
-cudaError_t launch_attn(const Dims& D, const Batch& b, int layer, const float* qkv, float* part,
-                        cudaStream_t s);
+// Split-KV attention; the last chunk of each (row, KV head) merges the
+// partials into attn_out [Bmax][hq * 64].  tickets: int [Bmax][hkv], zero.
+cudaError_t launch_attn(const Dims& D, const Batch& b, int layer, const float* qkv, float* part, int* tickets,
+                        float* attn_out, cudaStream_t s);
 int attn_max_splits(const Dims& D);
 
 struct VocabIO {
@@ -187,8 +188,6 @@ bool tc_encode_tmap(void* tmap, const void* base, int elem_bytes, int64_t inner,
 cudaError_t launch_gemm_tc(const TcGemm& g, int epi, cudaStream_t s, bool pdl);
 cudaError_t launch_act_rmsnorm(const Dims& D, const Batch& b, const float* x, const float* gain, int cols,
                                int kind_bf16, void* out, float* out_scale, cudaStream_t s);
-cudaError_t launch_act_merge(const Dims& D, const Batch& b, const float* part, int kind_bf16, void* out,
-                             float* out_scale, cudaStream_t s);
 cudaError_t launch_act_plain(const Dims& D, const Batch& b, const float* x, int cols, int kind_bf16, void* out,
                              float* out_scale, cudaStream_t s);
 

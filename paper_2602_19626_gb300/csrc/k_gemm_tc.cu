@@ -380,42 +380,7 @@ __device__ void write_operand(const float* buf, int cols, int j, void* out, floa
     o[c] = __nv_cvt_float_to_fp8(__fdiv_rn(buf[c], sc), __NV_SATFINITE, __NV_E4M3);
 }
 
-// Merge the split-KV attention partials of every head (same arithmetic as the
-// GEMV path's attention prologue) into the O-projection operand.
-template <int KB>
-__global__ void k_act_merge(Dims D, Batch b, const float* part, void* out, float* out_scale) {
-  __shared__ float buf[kMaxGroup * 16 * kHeadDim];
-  __shared__ float red[33];
-  pdl_wait();
-  pdl_trigger();
-  const int j = blockIdx.x;
-  if (j >= *b.nB) return;
-  const StreamDev& st = b.st[b.slots[j]];
-  int start = st.kv_start;
-  if (st.n_coded - start == D.L) start += D.C;
-  const int n = st.n_coded - start + 1;
-  const int ns = (n + kAttnChunk - 1) / kAttnChunk;
-  const int nsm = attn_splits_max_dev(D);
-  const int cols = D.hq * kHeadDim;
-  for (int e = threadIdx.x; e < cols; e += blockDim.x) {
-    const int h = e / kHeadDim, dd = e % kHeadDim;
-    const float* ph = part + ((size_t)j * D.hq + h) * nsm * (kHeadDim + 2);
-    float M = -INFINITY;
-    for (int s = 0; s < ns; ++s) M = fmaxf(M, ph[s * (kHeadDim + 2) + kHeadDim]);
-    float l = 0.f, acc = 0.f;
-    for (int s = 0; s < ns; ++s) {
-      const float* p = ph + s * (kHeadDim + 2);
-      const float f = expf(p[kHeadDim] - M);
-      l = fmaf(p[kHeadDim + 1], f, l);
-      acc = fmaf(p[dd], f, acc);
-    }
-    buf[e] = acc / l;
-  }
-  __syncthreads();
-  write_operand<KB>(buf, cols, j, out, out_scale, red);
-}
-
-// An FP32 activation row (the SwiGLU output) as the GEMM operand.
+// An FP32 activation row (attention output, SwiGLU output) as the GEMM operand.
 template <int KB>
 __global__ void k_act_plain(Dims D, Batch b, const float* x, int cols, void* out, float* out_scale) {
   __shared__ float red[33];
@@ -427,12 +392,6 @@ __global__ void k_act_plain(Dims D, Batch b, const float* x, int cols, void* out
 }
 
 }  // namespace
-
-cudaError_t launch_act_merge(const Dims& D, const Batch& b, const float* part, int kind_bf16, void* out,
-                             float* out_scale, cudaStream_t s) {
-  return launch_kernel(kind_bf16 ? k_act_merge<1> : k_act_merge<0>, dim3(b.Bmax), dim3(256), 0, s, D.pdl, D, b,
-                       part, out, out_scale);
-}
 
 cudaError_t launch_act_plain(const Dims& D, const Batch& b, const float* x, int cols, int kind_bf16, void* out,
                              float* out_scale, cudaStream_t s) {

@@ -149,7 +149,6 @@ __global__ void __launch_bounds__(kGemvThreads) k_gemv(Dims D, Batch b, Mat m, G
                                                    (size_t)row0 * cols * W::ESZ);
   const uint4* w1 = reinterpret_cast<const uint4*>(static_cast<const char*>(m.w) +
                                                    (size_t)row1 * cols * W::ESZ);
-  const int nsm = attn_splits_max_dev(D);
   // Weights do not depend on earlier kernels: fetch this warp's rows before
   // waiting on the predecessor, so the fetch overlaps its execution.
   uint4 h0[kHold], h1[kHold];
@@ -192,26 +191,6 @@ __global__ void __launch_bounds__(kGemvThreads) k_gemv(Dims D, Batch b, Mat m, G
       for (int bt = 0; bt < nb; ++bt) {
         const float* xr = io.x + (size_t)(b0 + bt) * cols;
         for (int c = threadIdx.x; c < cols; c += kGemvThreads) xs[bt * cols + c] = xr[c];
-      }
-    } else {  // PRO_ATTN: merge the split-KV partials (m, l, acc) of every head
-      for (int bt = 0; bt < nb; ++bt) {
-        const StreamDev& st = b.st[b.slots[b0 + bt]];
-        const int n = st.n_coded - window_start(D, st) + 1;
-        const int ns = (n + kAttnChunk - 1) / kAttnChunk;
-        for (int e = threadIdx.x; e < cols; e += kGemvThreads) {
-          const int h = e / kHeadDim, dd = e % kHeadDim;
-          const float* ph = io.part + ((size_t)(b0 + bt) * D.hq + h) * nsm * (kHeadDim + 2);
-          float M = -INFINITY;
-          for (int s = 0; s < ns; ++s) M = fmaxf(M, ph[s * (kHeadDim + 2) + kHeadDim]);
-          float l = 0.f, acc = 0.f;
-          for (int s = 0; s < ns; ++s) {
-            const float* p = ph + s * (kHeadDim + 2);
-            const float f = expf(p[kHeadDim] - M);
-            l = fmaf(p[kHeadDim + 1], f, l);
-            acc = fmaf(p[dd], f, acc);
-          }
-          xs[bt * cols + e] = acc / l;
-        }
       }
     }
     __syncthreads();
@@ -313,7 +292,7 @@ __global__ void __launch_bounds__(kGemvThreads) k_gemv(Dims D, Batch b, Mat m, G
 // running max m, sum l and unnormalised accumulator of the chunk.
 template <int KBF16>
 __global__ void __launch_bounds__(128) k_attn(Dims D, Batch b, int layer, const float* qkv,
-                                              float* part) {
+                                              float* part, int* tickets, float* attn_out) {
   const int j = blockIdx.z;
   if (j >= *b.nB) return;
   StreamDev& st = b.st[b.slots[j]];
@@ -378,6 +357,21 @@ __global__ void __launch_bounds__(128) k_attn(Dims D, Batch b, int layer, const 
       }
       asm volatile("prefetch.global.L2 [%0];" ::"l"(kvf + voff + ri));
       asm volatile("prefetch.global.L2 [%0];" ::"l"(kvf + voff + ri + 32));
+    }
+  }
+  // values of the warp's 32 cached positions: lane owns dims 2*lane, 2*lane+1
+  const int nvalid = min(32, a - p_lo + 1);
+  uint32_t vb[32];        // BF16 pairs
+  float2 vf[KBF16 ? 1 : 32];
+#pragma unroll
+  for (int i = 0; i < 32; ++i) {
+    const int pi = p_lo + i;
+    if (i < nvalid && pi != a) {
+      const size_t ri = (size_t)(pi & (D.L - 1)) * kHeadDim + 2 * lane;
+      if (KBF16)
+        vb[i] = *reinterpret_cast<const uint32_t*>(static_cast<const __nv_bfloat16*>(st.kv) + voff + ri);
+      else
+        vf[KBF16 ? 0 : i] = *reinterpret_cast<const float2*>(static_cast<const float*>(st.kv) + voff + ri);
     }
   }
   pdl_wait();
@@ -446,24 +440,20 @@ __global__ void __launch_bounds__(128) k_attn(Dims D, Batch b, int layer, const 
   float acc[kMaxGroup][2];
 #pragma unroll
   for (int h = 0; h < kMaxGroup; ++h) acc[h][0] = acc[h][1] = 0.f;
-  const int nvalid = min(32, a - p_lo + 1);
-  for (int i = 0; i < nvalid; ++i) {
+#pragma unroll
+  for (int i = 0; i < 32; ++i) {
+    if (i >= nvalid) break;
     const int pi = p_lo + i;
     float v0, v1;
     if (pi == a) {
       v0 = vn[2 * lane];
       v1 = vn[2 * lane + 1];
+    } else if (KBF16) {
+      v0 = __uint_as_float(vb[i] << 16);
+      v1 = __uint_as_float(vb[i] & 0xFFFF0000u);
     } else {
-      const size_t ri = (size_t)(pi & (D.L - 1)) * kHeadDim + 2 * lane;
-      if (KBF16) {
-        const uint32_t u = *reinterpret_cast<const uint32_t*>(static_cast<const __nv_bfloat16*>(st.kv) + voff + ri);
-        v0 = __uint_as_float(u << 16);
-        v1 = __uint_as_float(u & 0xFFFF0000u);
-      } else {
-        const float2 u = *reinterpret_cast<const float2*>(static_cast<const float*>(st.kv) + voff + ri);
-        v0 = u.x;
-        v1 = u.y;
-      }
+      v0 = vf[KBF16 ? 0 : i].x;
+      v1 = vf[KBF16 ? 0 : i].y;
     }
 #pragma unroll
     for (int h = 0; h < kMaxGroup; ++h) {
@@ -506,6 +496,34 @@ __global__ void __launch_bounds__(128) k_attn(Dims D, Batch b, int layer, const 
       out[kHeadDim] = M;
       out[kHeadDim + 1] = l;
     }
+  }
+  // The last chunk to finish (atomic ticket) merges the chunks of this
+  // (stream, KV head) in chunk order, so the result does not depend on which
+  // CTA finished last.
+  __shared__ int last;
+  __threadfence();
+  __syncthreads();
+  if (tid == 0) {
+    const int t = atomicAdd(tickets + j * D.hkv + g, 1);
+    last = (t == ns - 1);
+    if (last) tickets[j * D.hkv + g] = 0;
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  for (int e = tid; e < grp * kHeadDim; e += blockDim.x) {
+    const int h = e / kHeadDim, dd = e % kHeadDim;
+    const float* ph = part + ((size_t)j * D.hq + g * grp + h) * nsm * (kHeadDim + 2);
+    float M = -INFINITY;
+    for (int q = 0; q < ns; ++q) M = fmaxf(M, __ldcg(ph + q * (kHeadDim + 2) + kHeadDim));
+    float l = 0.f, acc = 0.f;
+    for (int q = 0; q < ns; ++q) {
+      const float* pq = ph + q * (kHeadDim + 2);
+      const float f = expf(__ldcg(pq + kHeadDim) - M);
+      l = fmaf(__ldcg(pq + kHeadDim + 1), f, l);
+      acc = fmaf(__ldcg(pq + dd), f, acc);
+    }
+    attn_out[(size_t)j * D.hq * kHeadDim + (g * grp + h) * kHeadDim + dd] = acc / l;
   }
 }
 
@@ -577,7 +595,6 @@ template <int FMT>
 static cudaError_t gemv_f(const Dims& D, const Batch& b, const Mat& m, int pro, int epi,
                           const GemvIO& io, cudaStream_t s) {
   if (pro == PRO_RMSNORM && epi == EPI_STORE) return gemv_t<FMT, PRO_RMSNORM, EPI_STORE>(D, b, m, io, s);
-  if (pro == PRO_ATTN && epi == EPI_RESID) return gemv_t<FMT, PRO_ATTN, EPI_RESID>(D, b, m, io, s);
   if (pro == PRO_RMSNORM && epi == EPI_SWIGLU) return gemv_t<FMT, PRO_RMSNORM, EPI_SWIGLU>(D, b, m, io, s);
   if (pro == PRO_PLAIN && epi == EPI_RESID) return gemv_t<FMT, PRO_PLAIN, EPI_RESID>(D, b, m, io, s);
   if (pro == PRO_RMSNORM && epi == EPI_LOGITS) return gemv_t<FMT, PRO_RMSNORM, EPI_LOGITS>(D, b, m, io, s);
@@ -591,10 +608,11 @@ cudaError_t launch_gemv(const Dims& D, const Batch& b, const Mat& m, int fmt, in
   return gemv_f<NC_FP8E4M3>(D, b, m, pro, epi, io, s);
 }
 
-cudaError_t launch_attn(const Dims& D, const Batch& b, int layer, const float* qkv, float* part,
-                        cudaStream_t s) {
+cudaError_t launch_attn(const Dims& D, const Batch& b, int layer, const float* qkv, float* part, int* tickets,
+                        float* attn_out, cudaStream_t s) {
   dim3 grid(attn_max_splits(D), D.hkv, b.Bmax);
-  return launch_kernel(D.kv_bf16 ? k_attn<1> : k_attn<0>, grid, dim3(128), 0, s, D.pdl, D, b, layer, qkv, part);
+  return launch_kernel(D.kv_bf16 ? k_attn<1> : k_attn<0>, grid, dim3(128), 0, s, D.pdl, D, b, layer, qkv, part,
+                       tickets, attn_out);
 }
 
 cudaError_t launch_convert_weights(const float* src, void* dst, float* scale, int64_t rows,

@@ -70,19 +70,20 @@ __device__ __forceinline__ ArgMax better(ArgMax a, ArgMax b) {
   return a;
 }
 
-// Shared scratch of one CTA for the block / cluster reductions.
+// Shared scratch of one CTA: block-reduction slots, the values it publishes
+// to the other CTAs of its cluster, and the step's N-gram coefficients.
 struct VocabShared {
-  float wf[kWarps];
-  unsigned long long wu[kWarps];
+  float wm[kWarps], wsum[kWarps];
+  unsigned long long wc[kWarps], wb[kWarps];
   ArgMax wa[kWarps];
   uint32_t wscan[kWarps];
-  // values published to the other CTAs of the cluster
-  float cl_max, cl_sum;
-  unsigned long long cl_csum;
+  // published to the cluster
+  float cl_m, cl_s;
+  unsigned long long cl_csum, cl_below;
   ArgMax cl_arg;
   uint32_t cl_bad;
-  unsigned long long cl_total;
-  float cl_obs[4];
+  uint32_t cl_total;
+  float cl_obs[3];          // p_tilde(t*), p_ng(t*), log p_tilde(t*) (owner CTA of t*)
   // N-gram coefficients of this step
   float cu, coef[kMaxOrder];
   const NgEntry* ent[kMaxOrder];
@@ -91,155 +92,33 @@ struct VocabShared {
 __device__ float block_max(float v, VocabShared& sh) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   v = warp_max(v);
-  if (lane == 0) sh.wf[w] = v;
+  if (lane == 0) sh.wm[w] = v;
   __syncthreads();
-  float r = sh.wf[0];
-  for (int i = 1; i < kWarps; ++i) r = fmaxf(r, sh.wf[i]);
+  float r = sh.wm[0];
+  for (int i = 1; i < kWarps; ++i) r = fmaxf(r, sh.wm[i]);
   __syncthreads();
   return r;
 }
 __device__ float block_sum(float v, VocabShared& sh) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   v = warp_sum(v);
-  if (lane == 0) sh.wf[w] = v;
+  if (lane == 0) sh.wsum[w] = v;
   __syncthreads();
   float r = 0.f;
-  for (int i = 0; i < kWarps; ++i) r += sh.wf[i];
+  for (int i = 0; i < kWarps; ++i) r += sh.wsum[i];
   __syncthreads();
   return r;
-}
-__device__ unsigned long long block_sum_u64(unsigned long long v, VocabShared& sh) {
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  v = warp_sum_u64(v);
-  if (lane == 0) sh.wu[w] = v;
-  __syncthreads();
-  unsigned long long r = 0;
-  for (int i = 0; i < kWarps; ++i) r += sh.wu[i];
-  __syncthreads();
-  return r;
-}
-__device__ ArgMax block_argmax(ArgMax a, VocabShared& sh) {
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-#pragma unroll
-  for (int o = 16; o; o >>= 1) {
-    ArgMax b;
-    b.v = __shfl_xor_sync(0xffffffffu, a.v, o);
-    b.i = __shfl_xor_sync(0xffffffffu, a.i, o);
-    a = better(a, b);
-  }
-  if (lane == 0) sh.wa[w] = a;
-  __syncthreads();
-  ArgMax r = sh.wa[0];
-  for (int i = 1; i < kWarps; ++i) r = better(r, sh.wa[i]);
-  __syncthreads();
-  return r;
-}
-// Exclusive scan of one uint32 per thread over the CTA; returns the CTA total.
-__device__ uint32_t block_excl_scan(uint32_t v, uint32_t& excl, VocabShared& sh) {
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  uint32_t inc = v;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const uint32_t t = __shfl_up_sync(0xffffffffu, inc, o);
-    if (lane >= o) inc += t;
-  }
-  if (lane == 31) sh.wscan[w] = inc;
-  __syncthreads();
-  uint32_t before = 0, total = 0;
-  for (int i = 0; i < kWarps; ++i) {
-    if (i < w) before += sh.wscan[i];
-    total += sh.wscan[i];
-  }
-  __syncthreads();
-  excl = before + inc - v;
-  return total;
 }
 
-// Quantise the E binary32 probabilities of this thread (positions v0..v0+E-1
-// of a row of V) into counts and, optionally, write the row's CDF and / or
-// the interval of symbol `want`.  All CTAs of the cluster call this together.
-template <int E>
-__device__ void quantise_scan(const float (&p)[E], int v0, int V, int log2T, uint32_t floor_c,
-                              uint32_t* cdf_row, int want, uint32_t* interval_out,
-                              int32_t* status, cg::cluster_group& cl, VocabShared& sh) {
-  const uint32_t T = 1u << log2T;
-  const uint32_t K = T - (uint32_t)V * floor_c;
-  uint32_t c[E];
-  bool bad = false;
-  unsigned long long csum = 0;
-  ArgMax am{-INFINITY, 0x7fffffff};
-#pragma unroll
-  for (int i = 0; i < E; ++i) {
-    const int v = v0 + i;
-    if (v < V) {
-      const uint32_t q = floor_prod(p[i], K, bad);
-      c[i] = q > floor_c ? q : floor_c;
-      csum += c[i];
-      if (p[i] > am.v) am = ArgMax{p[i], v};   // strict: keeps the first maximum
-      bad |= !(p[i] == p[i]);
-    } else {
-      c[i] = 0;
-    }
-  }
-  csum = block_sum_u64(csum, sh);
-  am = block_argmax(am, sh);
-  const int anybad = __syncthreads_or(bad);
-  if (threadIdx.x == 0) {
-    sh.cl_csum = csum;
-    sh.cl_arg = am;
-    sh.cl_bad = anybad;
-  }
-  cl.sync();
-  unsigned long long total = 0;
-  ArgMax g{-INFINITY, 0x7fffffff};
-  uint32_t gbad = 0;
-  for (int r = 0; r < kVocabCluster; ++r) {
-    const VocabShared* o = cl.map_shared_rank(&sh, r);
-    total += o->cl_csum;
-    g = better(g, o->cl_arg);
-    gbad |= o->cl_bad;
-  }
-  const long long resid = (long long)T - (long long)total;
-  bool under = false;
-#pragma unroll
-  for (int i = 0; i < E; ++i) {
-    if (v0 + i == g.i) {
-      const long long ci = (long long)c[i] + resid;
-      if (ci < (long long)floor_c || ci > (long long)T) under = true;
-      c[i] = (uint32_t)ci;
-    }
-  }
-  if ((gbad || under) && status) atomicOr(status, ST_NUMERIC);
-  // exclusive prefix sum: thread-local, CTA, then the CTAs of lower rank
-  uint32_t local[E];
-  uint32_t run = 0;
-#pragma unroll
-  for (int i = 0; i < E; ++i) {
-    local[i] = run;
-    run += c[i];
-  }
-  uint32_t excl;
-  const uint32_t cta_total = block_excl_scan(run, excl, sh);
-  if (threadIdx.x == 0) sh.cl_total = cta_total;
-  cl.sync();
-  uint32_t off = 0;
-  for (int r = 0; r < (int)cl.block_rank(); ++r) off += (uint32_t)cl.map_shared_rank(&sh, r)->cl_total;
-  if (cdf_row) {
-#pragma unroll
-    for (int i = 0; i < E; ++i)
-      if (v0 + i < V) cdf_row[v0 + i] = off + excl + local[i];
-    if (v0 <= V - 1 && V - 1 < v0 + E) cdf_row[V] = T;
-  }
-  if (interval_out && want >= v0 && want < v0 + E) {
-#pragma unroll
-    for (int i = 0; i < E; ++i) {
-      if (v0 + i == want) {
-        interval_out[0] = off + excl + local[i];
-        interval_out[1] = off + excl + local[i] + c[i];
-      }
-    }
-  }
-  cl.sync();   // keep shared memory alive until every CTA has read it
+// Online-softmax pair (max, sum of exp relative to max); combining is exact
+// in its max and has a fixed rounding for a fixed order of operands.
+struct MS {
+  float m, s;
+};
+__device__ __forceinline__ MS ms_combine(MS a, MS b) {
+  const float M = fmaxf(a.m, b.m);
+  if (M == -INFINITY) return MS{M, 0.f};
+  return MS{M, a.s * expf(a.m - M) + b.s * expf(b.m - M)};
 }
 
 template <int E>
@@ -272,10 +151,182 @@ __device__ __forceinline__ void store_run(float* dst, int v0, int V, const float
   }
 }
 
-// One stream per cluster.  predict: p -> counts -> CDF / interval of the
-// observed token.  update: head and mixer update with the observed token.
-// Both may run in one pass (encoder) or in two (decoder, which learns the
-// token in between); the arithmetic is the same in either case.
+// Round 1: softmax statistics (M, S) of s over the cluster's vocabulary.
+template <int E>
+__device__ MS softmax_stats(const float (&s)[E], cg::cluster_group& cl, VocabShared& sh) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  MS t{-INFINITY, 0.f};
+#pragma unroll
+  for (int i = 0; i < E; ++i) t.m = fmaxf(t.m, s[i]);
+  if (t.m != -INFINITY) {
+#pragma unroll
+    for (int i = 0; i < E; ++i) t.s += expf(s[i] - t.m);
+  }
+#pragma unroll
+  for (int o = 16; o; o >>= 1) {
+    MS u{__shfl_xor_sync(0xffffffffu, t.m, o), __shfl_xor_sync(0xffffffffu, t.s, o)};
+    t = ms_combine(t, u);
+  }
+  if (lane == 0) {
+    sh.wm[w] = t.m;
+    sh.wsum[w] = t.s;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    MS b{sh.wm[0], sh.wsum[0]};
+    for (int i = 1; i < kWarps; ++i) b = ms_combine(b, MS{sh.wm[i], sh.wsum[i]});
+    sh.cl_m = b.m;
+    sh.cl_s = b.s;
+  }
+  cl.sync();
+  MS g{-INFINITY, 0.f};
+  for (int r = 0; r < kVocabCluster; ++r) {
+    const VocabShared* o = cl.map_shared_rank(&sh, r);
+    g = ms_combine(g, MS{o->cl_m, o->cl_s});
+  }
+  return g;
+}
+
+struct QuantResult {
+  long long resid;          // T - sum of floored counts, added to the first maximum
+  int argmax;
+  unsigned long long below; // sum of floored counts of symbols below `want`
+  bool bad;                 // non-finite / out-of-range probability, or floor underflow
+};
+
+// Round 2: floor-quantise the thread's E probabilities into c[], reduce the
+// count sum, the first argmax and (for `want` >= 0) the count sum below
+// `want` over the cluster.  The CTA owning `want` also publishes obs[3]
+// (read by every CTA after this round through cl_obs of the owner rank).
+template <int E>
+__device__ QuantResult quantise_round(const float (&p)[E], int v0, int V, int log2T, uint32_t floor_c,
+                                      bool quantise, int want, const float* obs, uint32_t (&c)[E],
+                                      cg::cluster_group& cl, VocabShared& sh) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const uint32_t T = 1u << log2T;
+  const uint32_t K = T - (uint32_t)V * floor_c;
+  bool bad = false;
+  unsigned long long csum = 0, below = 0;
+  ArgMax am{-INFINITY, 0x7fffffff};
+#pragma unroll
+  for (int i = 0; i < E; ++i) {
+    const int v = v0 + i;
+    c[i] = 0;
+    if (quantise && v < V) {
+      const uint32_t q = floor_prod(p[i], K, bad);
+      c[i] = q > floor_c ? q : floor_c;
+      csum += c[i];
+      if (v < want) below += c[i];
+      if (p[i] > am.v) am = ArgMax{p[i], v};   // strict: keeps the first maximum
+      bad |= !(p[i] == p[i]);
+    }
+  }
+  if (obs && want >= v0 && want < v0 + E) {
+    sh.cl_obs[0] = obs[0];
+    sh.cl_obs[1] = obs[1];
+    sh.cl_obs[2] = obs[2];
+  }
+  if (quantise) {
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+      csum += __shfl_xor_sync(0xffffffffu, csum, o);
+      below += __shfl_xor_sync(0xffffffffu, below, o);
+      ArgMax b2;
+      b2.v = __shfl_xor_sync(0xffffffffu, am.v, o);
+      b2.i = __shfl_xor_sync(0xffffffffu, am.i, o);
+      am = better(am, b2);
+    }
+    const unsigned any_bad = __ballot_sync(0xffffffffu, bad);
+    if (lane == 0) {
+      sh.wc[w] = csum;
+      sh.wb[w] = below;
+      sh.wa[w] = am;
+      sh.wscan[w] = any_bad ? 1u : 0u;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      unsigned long long tc = 0, tb = 0;
+      ArgMax ta{-INFINITY, 0x7fffffff};
+      uint32_t tbad = 0;
+      for (int i = 0; i < kWarps; ++i) {
+        tc += sh.wc[i];
+        tb += sh.wb[i];
+        ta = better(ta, sh.wa[i]);
+        tbad |= sh.wscan[i];
+      }
+      sh.cl_csum = tc;
+      sh.cl_below = tb;
+      sh.cl_arg = ta;
+      sh.cl_bad = tbad;
+    }
+  }
+  cl.sync();
+  QuantResult r{0, -1, 0, false};
+  if (quantise) {
+    unsigned long long total = 0;
+    ArgMax g{-INFINITY, 0x7fffffff};
+    for (int q = 0; q < kVocabCluster; ++q) {
+      const VocabShared* o = cl.map_shared_rank(&sh, q);
+      total += o->cl_csum;
+      r.below += o->cl_below;
+      g = better(g, o->cl_arg);
+      r.bad |= o->cl_bad != 0;
+    }
+    r.resid = (long long)T - (long long)total;
+    r.argmax = g.i;
+#pragma unroll
+    for (int i = 0; i < E; ++i) {
+      if (v0 + i == g.i) {
+        const long long ci = (long long)c[i] + r.resid;
+        if (ci < (long long)floor_c || ci > (long long)T) r.bad = true;
+        c[i] = (uint32_t)ci;
+      }
+    }
+  }
+  return r;
+}
+
+// Round 3: exclusive prefix sum of the final counts into cdf_row.
+template <int E>
+__device__ void scan_round(const uint32_t (&c)[E], int v0, int V, uint32_t T, uint32_t* cdf_row,
+                           cg::cluster_group& cl, VocabShared& sh) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  uint32_t local[E];
+  uint32_t run = 0;
+#pragma unroll
+  for (int i = 0; i < E; ++i) {
+    local[i] = run;
+    run += c[i];
+  }
+  uint32_t inc = run;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t t = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += t;
+  }
+  if (lane == 31) sh.wscan[w] = inc;
+  __syncthreads();
+  uint32_t before = 0, total = 0;
+  for (int i = 0; i < kWarps; ++i) {
+    if (i < w) before += sh.wscan[i];
+    total += sh.wscan[i];
+  }
+  if (threadIdx.x == 0) sh.cl_total = total;
+  cl.sync();
+  uint32_t off = 0;
+  for (int r = 0; r < (int)cl.block_rank(); ++r) off += cl.map_shared_rank(&sh, r)->cl_total;
+  const uint32_t base = off + before + inc - run;
+#pragma unroll
+  for (int i = 0; i < E; ++i)
+    if (v0 + i < V) cdf_row[v0 + i] = base + local[i];
+  if (v0 <= V - 1 && V - 1 < v0 + E) cdf_row[V] = T;
+}
+
+// One stream per cluster.  predict: p -> counts -> CDF and / or the coder
+// interval of the observed token.  update: head and mixer update with the
+// observed token.  Both may run in one pass (encoder) or in two (decoder,
+// which learns the token in between); the arithmetic is the same in either
+// case.
 template <int E>
 __global__ void __cluster_dims__(kVocabCluster, 1, 1) __launch_bounds__(kVocabThreads)
     k_vocab(Dims D, Batch b, VocabIO io) {
@@ -367,42 +418,21 @@ __global__ void __cluster_dims__(kVocabCluster, 1, 1) __launch_bounds__(kVocabTh
   const int t_obs = (io.update || io.intervals) ? b.obs[j] : -1;
   if (io.update && (t_obs < 0 || t_obs >= V)) {   // rejected on the host; never index with it
     if (rank == 0 && threadIdx.x == 0) atomicOr(&st.status, ST_BAD_TOKEN);
-    cl.sync();
-    return;
+    return;                                       // uniform across the cluster
   }
   if (io.probe_png && ngram) store_run<E>(io.probe_png + (size_t)j * V, v0, V, png);
 
-  // ---- biased logits s = z / tau + b
+  // ---- biased logits s = z / tau + b and their softmax (round 1)
   float s[E];
   load_run<E>(st.z, v0, V, s, -INFINITY);
   if (io.probe_z) store_run<E>(io.probe_z + (size_t)j * V, v0, V, s);
 #pragma unroll
   for (int i = 0; i < E; ++i) s[i] = (v0 + i < V) ? __fdiv_rn(s[i], D.tau) + bias[i] : -INFINITY;
-
-  // ---- softmax: max and sum of exp in a fixed order
-  float mx = -INFINITY;
-#pragma unroll
-  for (int i = 0; i < E; ++i) mx = fmaxf(mx, s[i]);
-  mx = block_max(mx, sh);
-  if (threadIdx.x == 0) sh.cl_max = mx;
-  cl.sync();
-  float M = -INFINITY;
-  for (int r = 0; r < kVocabCluster; ++r) M = fmaxf(M, cl.map_shared_rank(&sh, r)->cl_max);
-  float e[E];
-  float ls = 0.f;
-#pragma unroll
-  for (int i = 0; i < E; ++i) {
-    e[i] = (v0 + i < V) ? expf(s[i] - M) : 0.f;
-    ls += e[i];
-  }
-  ls = block_sum(ls, sh);
-  if (threadIdx.x == 0) sh.cl_sum = ls;
-  cl.sync();
-  float S = 0.f;
-  for (int r = 0; r < kVocabCluster; ++r) S += cl.map_shared_rank(&sh, r)->cl_sum;
+  const MS ms = softmax_stats<E>(s, cl, sh);
+  const float M = ms.m, S = ms.s;
   float pt[E];
 #pragma unroll
-  for (int i = 0; i < E; ++i) pt[i] = __fdiv_rn(e[i], S);
+  for (int i = 0; i < E; ++i) pt[i] = (v0 + i < V) ? __fdiv_rn(expf(s[i] - M), S) : 0.f;
   if (io.probe_pt) store_run<E>(io.probe_pt + (size_t)j * V, v0, V, pt);
 
   // ---- mix (Sec. 3.5): LLM alone during warm-up
@@ -415,28 +445,39 @@ __global__ void __cluster_dims__(kVocabCluster, 1, 1) __launch_bounds__(kVocabTh
   for (int i = 0; i < E; ++i) p[i] = mixing ? w0 * pt[i] + w1 * png[i] : pt[i];
   if (io.probe_p) store_run<E>(io.probe_p + (size_t)j * V, v0, V, p);
 
-  if (io.predict) {
-    uint32_t* cdf_row = io.cdf ? io.cdf + (size_t)j * (V + 1) : nullptr;
-    uint32_t* iv = nullptr;
-    if (io.intervals) iv = io.intervals + 2 * ((size_t)j * io.interval_stride + st.n_coded);
-    quantise_scan<E>(p, v0, V, D.log2T, D.floor, cdf_row, t_obs, iv, &st.status, cl, sh);
+  // ---- round 2: counts, residual, argmax, interval; publish t*'s values
+  float obs[3] = {0.f, 0.f, 0.f};
+  if (t_obs >= v0 && t_obs < v0 + E) {
+#pragma unroll
+    for (int i = 0; i < E; ++i) {
+      if (v0 + i == t_obs) {
+        obs[0] = pt[i];
+        obs[1] = png[i];
+        obs[2] = s[i] - M - logf(S);
+      }
+    }
   }
-
-  if (io.update) {
-    // the CTA owning t* publishes p_tilde(t*), p_ng(t*) and log p_tilde(t*)
-    const int owner = t_obs / chunk;
-    if (t_obs >= v0 && t_obs < v0 + E) {
+  uint32_t c[E];
+  const QuantResult q = quantise_round<E>(p, v0, V, D.log2T, D.floor, io.predict != 0, t_obs,
+                                          io.update ? obs : nullptr, c, cl, sh);
+  if (io.predict) {
+    if (q.bad && threadIdx.x == 0 && rank == 0) atomicOr(&st.status, ST_NUMERIC);
+    if (io.intervals && t_obs >= v0 && t_obs < v0 + E) {
+      const unsigned long long lo = q.below + (q.argmax < t_obs ? (unsigned long long)q.resid : 0ull);
 #pragma unroll
       for (int i = 0; i < E; ++i) {
         if (v0 + i == t_obs) {
-          sh.cl_obs[0] = pt[i];
-          sh.cl_obs[1] = png[i];
-          sh.cl_obs[2] = s[i] - M - logf(S);
+          uint32_t* iv = io.intervals + 2 * ((size_t)j * io.interval_stride + st.n_coded);
+          iv[0] = (uint32_t)lo;
+          iv[1] = (uint32_t)(lo + c[i]);
         }
       }
     }
-    cl.sync();
-    const VocabShared* o = cl.map_shared_rank(&sh, owner);
+    if (io.cdf) scan_round<E>(c, v0, V, 1u << D.log2T, io.cdf + (size_t)j * (V + 1), cl, sh);
+  }
+
+  if (io.update) {
+    const VocabShared* o = cl.map_shared_rank(&sh, t_obs / chunk);
     const float pts = o->cl_obs[0], pngs = o->cl_obs[1], lpt = o->cl_obs[2];
     float scale = 1.f;
     float nth0 = th0, nth1 = th1;
@@ -466,8 +507,8 @@ __global__ void __cluster_dims__(kVocabCluster, 1, 1) __launch_bounds__(kVocabTh
       st.pt_obs = pts;
       st.png_obs = pngs;
     }
-    cl.sync();
   }
+  cl.sync();   // keep this CTA's shared memory alive until the cluster has read it
 }
 
 // --------------------------------------------------------------- N-gram tables
@@ -642,8 +683,11 @@ __global__ void __cluster_dims__(kVocabCluster, 1, 1) __launch_bounds__(kVocabTh
   const int v0 = rank * kVocabThreads * E + threadIdx.x * E;
   float pr[E];
   load_run<E>(p + (size_t)j * V, v0, V, pr, 0.f);
-  quantise_scan<E>(pr, v0, V, log2T, floor_c, cdf + (size_t)j * (V + 1), -1, nullptr, status + j,
-                   cl, sh);
+  uint32_t c[E];
+  const QuantResult q = quantise_round<E>(pr, v0, V, log2T, floor_c, true, -1, nullptr, c, cl, sh);
+  if (q.bad && threadIdx.x == 0 && rank == 0) atomicOr(status + j, ST_NUMERIC);
+  scan_round<E>(c, v0, V, 1u << log2T, cdf + (size_t)j * (V + 1), cl, sh);
+  cl.sync();
 }
 
 __global__ void k_floor_counts(const float* p, int64_t n, uint32_t K, uint32_t floor_c,
