@@ -161,6 +161,7 @@ int nc_encode(nc_ctx* ctx, int n_streams, const int32_t* const* tokens, const in
 #define NC_TRACE_KINDS 16
 typedef struct {
   int n_kinds;
+  int graphed;                      /* 1: the traced steps were replayed from a CUDA graph */
   char name[NC_TRACE_KINDS][32];
   int64_t launches[NC_TRACE_KINDS];
   double ms[NC_TRACE_KINDS];

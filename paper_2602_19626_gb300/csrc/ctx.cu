@@ -72,6 +72,10 @@ struct nc_ctx {
   float* part = nullptr;
   int* tickets = nullptr;            // [max_streams][hkv] attention merge tickets
   float* attn_out = nullptr;         // [max_streams][hq * 64]
+  LayerW* d_layers = nullptr;        // device copy of the layer table (persistent step)
+  unsigned* step_bar = nullptr;      // persistent step: barrier counter and error word
+  int* step_err = nullptr;
+  bool use_step = false;             // GEMV path: one cooperative launch per step
   float* h = nullptr;
   uint32_t* cdf = nullptr;
   int32_t* d_slots = nullptr;
@@ -507,6 +511,18 @@ extern "C" int nc_ctx_create(const nc_config* cfg, const void* weights, size_t n
   if (cudaMemset(ctx->d_status, 0, B * 4) != cudaSuccess ||
       cudaMemset(ctx->tickets, 0, B * D.hkv * 4) != cudaSuccess)
     return bail(NC_ECUDA);
+  if (prepare_model_kernels(D, ctx->fmt) != cudaSuccess || prepare_vocab_kernels(D) != cudaSuccess ||
+      (c.path == NC_PATH_TC && prepare_tc_kernels() != cudaSuccess))
+    return bail(NC_ECUDA);
+  if (c.path == NC_PATH_GEMV && step_supported(D, c.max_streams)) {
+    const char* e = std::getenv("NC24_STEP");     // NC24_STEP=0: one kernel per phase
+    ctx->use_step = !(e && e[0] == '0');
+  }
+  if (dalloc(ctx, &ctx->d_layers, D.n_layers * sizeof(LayerW)) || dalloc(ctx, &ctx->step_bar, 16) ||
+      dalloc(ctx, &ctx->step_err, 16) ||
+      cudaMemcpy(ctx->d_layers, ctx->layers.data(), D.n_layers * sizeof(LayerW), cudaMemcpyHostToDevice) ||
+      cudaMemset(ctx->step_err, 0, 16))
+    return bail(NC_ENOMEM);
   if (c.path == NC_PATH_TC) {
     const int st2 = tc_setup(ctx);
     if (st2 != NC_OK) return bail(st2);
@@ -635,9 +651,10 @@ static Batch make_batch(nc_ctx* ctx) {
 
 // Kernel kinds reported by nc_trace.
 enum TraceKind { TK_PREPARE, TK_EMBED, TK_QKV, TK_ATTN, TK_O, TK_GU, TK_DOWN, TK_LMHEAD, TK_VOCAB,
-                 TK_NGRAM, TK_COUNT };
+                 TK_NGRAM, TK_STEP, TK_COUNT };
 static const char* kTraceNames[TK_COUNT] = {"prepare", "embed", "gemv_qkv", "attn", "gemv_o",
-                                            "gemv_gate_up", "gemv_down", "lm_head", "vocab", "ngram_update"};
+                                            "gemv_gate_up", "gemv_down", "lm_head", "vocab", "ngram_update",
+                                            "model_step"};
 
 // Records a CUDA event after every launch of a step (when on) so that the
 // device time of each kernel is the gap between consecutive events.
@@ -667,12 +684,48 @@ struct StepMarks {
 // Model forward of every active row: logits into each stream's z.
 static cudaError_t launch_model_tc(nc_ctx* ctx, const Batch& b, StepMarks& m);
 
+struct EncodeRows {            // encoder rows for the persistent step
+  const int32_t* tok_flat;
+  const int64_t* offs;
+  const int64_t* lens;
+};
+
+static StepArgs step_args(nc_ctx* ctx, const EncodeRows* enc) {
+  StepArgs A{};
+  A.embed = ctx->embed;
+  A.embed_scale = ctx->embed_scale;
+  A.layers = ctx->d_layers;
+  A.g_final = ctx->g_final;
+  A.x = ctx->x;
+  A.qkv = ctx->qkv;
+  A.part = ctx->part;
+  A.tickets = ctx->tickets;
+  A.attn_out = ctx->attn_out;
+  A.h = ctx->h;
+  A.bar = ctx->step_bar;
+  A.err = ctx->step_err;
+  if (enc) {
+    A.encode = 1;
+    A.tok_flat = enc->tok_flat;
+    A.offs = enc->offs;
+    A.lens = enc->lens;
+    A.obs = ctx->d_obs;
+    A.nB_out = ctx->d_nB;
+  }
+  return A;
+}
+
 static cudaError_t launch_model(nc_ctx* ctx, const Batch& b, StepMarks* mk = nullptr) {
   const Dims& D = ctx->D;
   cudaStream_t s = ctx->stream;
   StepMarks none;
   StepMarks& m = mk ? *mk : none;
   if (ctx->cfg.path == NC_PATH_TC) return launch_model_tc(ctx, b, m);
+  if (ctx->use_step) {
+    cudaError_t e = launch_step(D, b, ctx->fmt, step_args(ctx, nullptr), s);
+    if (e == cudaSuccess) e = m.mark(s, TK_STEP);
+    return e;
+  }
   cudaError_t e = launch_embed(D, b, ctx->embed, ctx->embed_scale, ctx->fmt, ctx->x, s);
   if (e == cudaSuccess) e = m.mark(s, TK_EMBED);
   for (int l = 0; l < D.n_layers && e == cudaSuccess; ++l) {
@@ -824,6 +877,15 @@ static int stage_batch(nc_ctx* ctx, int n, const int32_t* ids, std::vector<int>*
 // context-wide word of the tensor-core GEMMs).
 static int check_status(nc_ctx* ctx, const std::vector<int>& slot_idx) {
   const size_t off = offsetof(StreamDev, status);
+  {
+    int32_t w = 0;
+    NC_TRY(cudaMemcpyAsync(&w, ctx->step_err, 4, cudaMemcpyDeviceToHost, ctx->stream));
+    NC_TRY(cudaStreamSynchronize(ctx->stream));
+    if (w) {
+      ctx->poisoned = true;
+      return fail(ctx, NC_ETIMEOUT, "a grid barrier of the persistent step gave up");
+    }
+  }
   if (ctx->cfg.path == NC_PATH_TC) {
     int32_t w = 0;
     NC_TRY(cudaMemcpyAsync(&w, ctx->d_status, 4, cudaMemcpyDeviceToHost, ctx->stream));
@@ -976,14 +1038,20 @@ static int encode_device(nc_ctx* ctx, int n, const std::vector<int>& slot_of, co
   StepMarks mk;
   mk.on = trace != nullptr;
   if (mk.on) {
-    mk.ev.resize(8 + 5 * D.n_layers);
+    mk.ev.resize(12 + 5 * D.n_layers);
     for (auto& e : mk.ev) NC_TRY(cudaEventCreate(&e));
   }
+  const EncodeRows rows{tok_dev, offs_dev, lens_dev};
   auto one_step = [&]() -> cudaError_t {
     cudaError_t e = mk.begin(s);
-    if (e == cudaSuccess) e = launch_prepare_encode(b, n, tok_dev, offs_dev, lens_dev, ctx->d_obs, ctx->d_nB, s);
-    if (e == cudaSuccess) e = mk.mark(s, TK_PREPARE);
-    if (e == cudaSuccess) e = launch_model(ctx, b, &mk);
+    if (ctx->use_step) {
+      if (e == cudaSuccess) e = launch_step(D, b, ctx->fmt, step_args(ctx, &rows), s);
+      if (e == cudaSuccess) e = mk.mark(s, TK_STEP);
+    } else {
+      if (e == cudaSuccess) e = launch_prepare_encode(b, n, tok_dev, offs_dev, lens_dev, ctx->d_obs, ctx->d_nB, s);
+      if (e == cudaSuccess) e = mk.mark(s, TK_PREPARE);
+      if (e == cudaSuccess) e = launch_model(ctx, b, &mk);
+    }
     if (e == cudaSuccess) e = launch_vocab(D, b, io, s);
     if (e == cudaSuccess) e = mk.mark(s, TK_VOCAB);
     if (e == cudaSuccess) e = launch_ngram_update(D, b, s);
@@ -1004,6 +1072,7 @@ static int encode_device(nc_ctx* ctx, int n, const std::vector<int>& slot_of, co
   }
   if (trace) {
     std::memset(trace, 0, sizeof(*trace));
+    trace->graphed = ge != nullptr;
     trace->n_kinds = TK_COUNT;
     for (int k = 0; k < TK_COUNT; ++k) std::snprintf(trace->name[k], sizeof(trace->name[k]), "%s", kTraceNames[k]);
   }

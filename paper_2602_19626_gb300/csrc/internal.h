@@ -191,6 +191,39 @@ cudaError_t launch_act_rmsnorm(const Dims& D, const Batch& b, const float* x, co
 cudaError_t launch_act_plain(const Dims& D, const Batch& b, const float* x, int cols, int kind_bf16, void* out,
                              float* out_scale, cudaStream_t s);
 
+// Persistent step kernel (k_step.cu): the model forward of up to 8 rows in
+// one cooperative launch.
+struct StepArgs {
+  const void* embed;
+  const float* embed_scale;
+  const LayerW* layers;     // device array [n_layers]
+  const float* g_final;
+  float* x;
+  float* qkv;
+  float* part;
+  int* tickets;
+  float* attn_out;
+  float* h;
+  unsigned* bar;            // grid-barrier arrival counter (reset per launch)
+  int* err;                 // ST_TIMEOUT when a barrier gave up
+  int encode;               // 1: rows active while tokens are left (tok_flat / offs / lens)
+  const int32_t* tok_flat;
+  const int64_t* offs;
+  const int64_t* lens;
+  int32_t* obs;
+  int32_t* nB_out;
+};
+size_t step_smem_bytes(const Dims& D);
+bool step_supported(const Dims& D, int Bmax);
+cudaError_t launch_step(const Dims& D, const Batch& b, int fmt, const StepArgs& A, cudaStream_t s);
+
+// Kernel attributes (dynamic shared memory limits) set once, outside any
+// stream capture.
+cudaError_t prepare_model_kernels(const Dims& D, int fmt);
+cudaError_t prepare_vocab_kernels(const Dims& D);
+cudaError_t prepare_tc_kernels();
+cudaError_t prepare_step_kernel(const Dims& D, int fmt);
+
 cudaError_t launch_probs_to_cdf(const float* p, int n, int V, int log2T, uint32_t floor,
                                 uint32_t* cdf, int32_t* status, cudaStream_t s);
 cudaError_t launch_floor_counts(const float* p, int64_t n, uint32_t K, uint32_t floor,

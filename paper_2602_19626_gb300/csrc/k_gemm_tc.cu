@@ -275,11 +275,24 @@ EncodeTiled encode_fn() {
 }
 
 template <int BN, int STAGES, int KB, int EPI>
+cudaError_t prepare_tc_t() {
+  return cudaFuncSetAttribute(k_gemm_tc<BN, STAGES, KB, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)tc_smem_bytes<BN, STAGES>());
+}
+
+template <int KB, int EPI>
+cudaError_t prepare_tc_epi() {
+  cudaError_t e = prepare_tc_t<32, 6, KB, EPI>();
+  if (e == cudaSuccess) e = prepare_tc_t<64, 6, KB, EPI>();
+  if (e == cudaSuccess) e = prepare_tc_t<128, 6, KB, EPI>();
+  if (e == cudaSuccess) e = prepare_tc_t<256, 4, KB, EPI>();
+  return e;
+}
+
+template <int BN, int STAGES, int KB, int EPI>
 cudaError_t launch_tc_t(const TcGemm& g, cudaStream_t s, bool pdl) {
   constexpr size_t smem = tc_smem_bytes<BN, STAGES>();
   auto kern = k_gemm_tc<BN, STAGES, KB, EPI>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
   dim3 grid((g.M + kTileM - 1) / kTileM, (g.Bmax + BN - 1) / BN);
   const CUtensorMap* a = reinterpret_cast<const CUtensorMap*>(g.tmap_a);
   const CUtensorMap* b = reinterpret_cast<const CUtensorMap*>(g.tmap_b);
@@ -410,6 +423,24 @@ bool tc_encode_tmap(void* tmap, const void* base, int elem_bytes, int64_t inner,
   return fn(reinterpret_cast<CUtensorMap*>(tmap), dt, 2, const_cast<void*>(base), dims, strides, box, es,
             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+cudaError_t prepare_tc_kernels() {
+  cudaError_t e = cudaSuccess;
+  for (int kb = 0; kb < 2 && e == cudaSuccess; ++kb) {
+    if (kb) {
+      e = prepare_tc_epi<1, EPI_STORE>();
+      if (e == cudaSuccess) e = prepare_tc_epi<1, EPI_RESID>();
+      if (e == cudaSuccess) e = prepare_tc_epi<1, EPI_SWIGLU>();
+      if (e == cudaSuccess) e = prepare_tc_epi<1, EPI_LOGITS>();
+    } else {
+      e = prepare_tc_epi<0, EPI_STORE>();
+      if (e == cudaSuccess) e = prepare_tc_epi<0, EPI_RESID>();
+      if (e == cudaSuccess) e = prepare_tc_epi<0, EPI_SWIGLU>();
+      if (e == cudaSuccess) e = prepare_tc_epi<0, EPI_LOGITS>();
+    }
+  }
+  return e;
 }
 
 cudaError_t launch_gemm_tc(const TcGemm& g, int epi, cudaStream_t s, bool pdl) {

@@ -782,9 +782,19 @@ static int vocab_E(int V) {
 template <int E>
 static cudaError_t vocab_t(const Dims& D, const Batch& b, const VocabIO& io, cudaStream_t s) {
   const size_t smem = (size_t)kVocabThreads * E * sizeof(float);
-  cudaError_t e = cudaFuncSetAttribute(k_vocab<E>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
   return launch_kernel(k_vocab<E>, dim3(b.Bmax * kVocabCluster), dim3(kVocabThreads), smem, s, D.pdl, D, b, io);
+}
+
+cudaError_t prepare_vocab_kernels(const Dims& D) {
+  const int E = vocab_E(D.V);
+  const int smem = kVocabThreads * E * (int)sizeof(float);
+  switch (E) {
+    case 4: return cudaFuncSetAttribute(k_vocab<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    case 8: return cudaFuncSetAttribute(k_vocab<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    case 12: return cudaFuncSetAttribute(k_vocab<12>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    case 16: return cudaFuncSetAttribute(k_vocab<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  }
+  return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_vocab(const Dims& D, const Batch& b, const VocabIO& io, cudaStream_t s) {

@@ -1,0 +1,560 @@
+// Device building blocks of the decode step, shared by the one-kernel-per-
+// phase path (k_model.cu) and the persistent step kernel (k_step.cu), so the
+// two compute every value with the same operations in the same order.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp8.h>
+
+#include "internal.h"
+
+namespace nc {
+namespace dev {
+
+constexpr int kRed = 256;          // threads of the fixed-order RMSNorm reduction
+constexpr int kBT = 8;             // streams per activation tile in shared memory
+constexpr int kHold = 8;           // 16-byte weight vectors per row held in registers
+constexpr int kLoadBatch = 4;      // further vectors per row in flight per lane
+
+__device__ __forceinline__ uint4 ld_stream(const uint4* p) {
+  uint4 r;
+  asm volatile("ld.global.nc.L1::no_allocate.v4.u32 {%0,%1,%2,%3}, [%4];"
+               : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w)
+               : "l"(p));
+  return r;
+}
+
+template <int FMT>
+struct WFmt;
+template <>
+struct WFmt<NC_FP32> {
+  static constexpr int VW = 4;
+  static constexpr int ESZ = 4;
+  __device__ static void deq(const uint4& u, float* f) {
+    f[0] = __uint_as_float(u.x);
+    f[1] = __uint_as_float(u.y);
+    f[2] = __uint_as_float(u.z);
+    f[3] = __uint_as_float(u.w);
+  }
+};
+template <>
+struct WFmt<NC_BF16> {
+  static constexpr int VW = 8;
+  static constexpr int ESZ = 2;
+  __device__ static void deq(const uint4& u, float* f) {
+    const uint32_t w[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      f[2 * i] = __uint_as_float(w[i] << 16);
+      f[2 * i + 1] = __uint_as_float(w[i] & 0xFFFF0000u);
+    }
+  }
+};
+template <>
+struct WFmt<NC_FP8E4M3> {
+  static constexpr int VW = 16;
+  static constexpr int ESZ = 1;
+  __device__ static void deq(const uint4& u, float* f) {
+    const uint32_t w[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      __half2_raw lo = __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)(w[i] & 0xFFFF), __NV_E4M3);
+      __half2_raw hi = __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)(w[i] >> 16), __NV_E4M3);
+      float2 a = __half22float2(*reinterpret_cast<__half2*>(&lo));
+      float2 b = __half22float2(*reinterpret_cast<__half2*>(&hi));
+      f[4 * i] = a.x;
+      f[4 * i + 1] = a.y;
+      f[4 * i + 2] = b.x;
+      f[4 * i + 3] = b.y;
+    }
+  }
+};
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ float warp_max(float v) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// Window bookkeeping shared by every kernel of a step: the fed token sits at
+// absolute position a = n_coded; a full window (L entries) first drops its
+// oldest C entries (Sec. 3.9).  Returns the first cached position.
+__device__ __forceinline__ int window_start(const Dims& D, const StreamDev& st) {
+  int start = st.kv_start;
+  if (st.n_coded - start == D.L) start += D.C;
+  return start;
+}
+
+__device__ __forceinline__ float silu(float a) { return a / (1.0f + expf(-a)); }
+
+// Embedding value of token `tok`, column c, in the storage format.
+template <int FMT>
+__device__ __forceinline__ float embed_at(const void* E, const float* Escale, int d, int tok, int c) {
+  if (FMT == NC_FP32) return static_cast<const float*>(E)[(size_t)tok * d + c];
+  if (FMT == NC_BF16) return __bfloat162float(static_cast<const __nv_bfloat16*>(E)[(size_t)tok * d + c]);
+  __nv_fp8_e4m3 q;
+  q.__x = static_cast<const __nv_fp8_storage_t*>(E)[(size_t)tok * d + c];
+  return float(q) * Escale[tok];
+}
+
+// Shared-memory scratch of a GEMV prologue.
+struct ProScratch {
+  float red[kRed / 32][kBT];
+  float inv[kBT];
+};
+
+// Prologue of a GEMV tile: xs[bt][c] = activation of stream b0 + bt, column c.
+// RMSNorm sums x^2 over columns c = t, t + 256, ... per virtual thread t,
+// then lanes by a fixed xor tree, then the 8 warps in order, whatever the
+// block size.  `src` gives the raw value of (row, column); loads that read
+// data written by other blocks of the same launch must bypass L1 (the
+// callers pass __ldcg-based sources).  `sync` synchronises the block.
+template <bool RMS, typename Src, typename Sync>
+__device__ void prologue(const Dims& D, Src src, const float* gain, int cols, int b0, int nb, float* xs,
+                         ProScratch& ps, int tid, int nthreads, Sync sync) {
+  if (RMS) {
+    if (tid < kRed) {
+      const int lane = tid & 31, w = tid >> 5;
+      for (int bt = 0; bt < nb; ++bt) {
+        float ss = 0.f;
+        for (int c = tid; c < cols; c += kRed) {
+          const float v = src(b0 + bt, c);
+          ss = fmaf(v, v, ss);
+        }
+        ss = warp_sum(ss);
+        if (lane == 0) ps.red[w][bt] = ss;
+      }
+    }
+    sync();
+    if (tid < nb) {
+      float ss = 0.f;
+      for (int w = 0; w < kRed / 32; ++w) ss += ps.red[w][tid];
+      ps.inv[tid] = 1.0f / sqrtf(ss / (float)cols + D.eps);
+    }
+    sync();
+    for (int bt = 0; bt < nb; ++bt)
+      for (int c = tid; c < cols; c += nthreads) xs[bt * cols + c] = src(b0 + bt, c) * ps.inv[bt] * gain[c];
+  } else {
+    for (int bt = 0; bt < nb; ++bt)
+      for (int c = tid; c < cols; c += nthreads) xs[bt * cols + c] = src(b0 + bt, c);
+  }
+  sync();
+}
+
+// Rows of row pair rp (odd row counts duplicate the last row, which is not
+// written back).
+__device__ __forceinline__ void rowpair_rows(const Mat& m, int rp, int& r0, int& r1, bool& has1) {
+  r0 = 2 * rp;
+  has1 = r0 + 1 < m.rows;
+  r1 = has1 ? r0 + 1 : r0;
+}
+
+template <int FMT, int HOLD = kHold>
+__device__ __forceinline__ void load_rowpair(const Mat& m, int rp, int lane, uint4 (&h0)[HOLD],
+                                             uint4 (&h1)[HOLD]) {
+  using W = WFmt<FMT>;
+  int r0, r1;
+  bool has1;
+  rowpair_rows(m, rp, r0, r1, has1);
+  const int nvec = m.cols / W::VW;
+  const uint4* w0 = reinterpret_cast<const uint4*>(static_cast<const char*>(m.w) + (size_t)r0 * m.cols * W::ESZ);
+  const uint4* w1 = reinterpret_cast<const uint4*>(static_cast<const char*>(m.w) + (size_t)r1 * m.cols * W::ESZ);
+#pragma unroll
+  for (int k = 0; k < HOLD; ++k) {
+    const int v = lane + 32 * k;
+    if (v < nvec) {
+      h0[k] = ld_stream(w0 + v);
+      h1[k] = ld_stream(w1 + v);
+    }
+  }
+}
+
+// Where a GEMV writes: EPI_STORE / EPI_RESID into y [B][rows], EPI_SWIGLU
+// into y [B][rows / 2], EPI_LOGITS into each stream's logits.
+struct GemvOut {
+  float* y;
+  StreamDev* st;
+  const int32_t* slots;
+};
+
+// One row pair for streams b0 .. b0 + nb - 1: lane l accumulates the weight
+// vectors l, l + 32, ... of both rows in increasing order (the held ones, then
+// the rest of a long row), a fixed xor tree sums the lanes, lane bt writes
+// stream b0 + bt.
+template <int FMT, int EPI, int HOLD = kHold, int BT = kBT>
+__device__ __forceinline__ void gemv_rowpair(const Mat& m, int rp, const float* xs, int b0, int nb,
+                                             const uint4 (&h0)[HOLD], const uint4 (&h1)[HOLD], int lane,
+                                             const GemvOut& out) {
+  using W = WFmt<FMT>;
+  constexpr int VW = W::VW;
+  int r0, r1;
+  bool has1;
+  rowpair_rows(m, rp, r0, r1, has1);
+  const int cols = m.cols;
+  const int nvec = cols / VW;
+  const uint4* w0 = reinterpret_cast<const uint4*>(static_cast<const char*>(m.w) + (size_t)r0 * cols * W::ESZ);
+  const uint4* w1 = reinterpret_cast<const uint4*>(static_cast<const char*>(m.w) + (size_t)r1 * cols * W::ESZ);
+  float acc0[BT], acc1[BT];
+#pragma unroll
+  for (int bt = 0; bt < BT; ++bt) acc0[bt] = acc1[bt] = 0.f;
+  auto fma_vec = [&](const uint4& a0, const uint4& a1, int v) {
+    float f0[VW], f1[VW];
+    W::deq(a0, f0);
+    W::deq(a1, f1);
+#pragma unroll
+    for (int bt = 0; bt < BT; ++bt) {
+      if (bt < nb) {
+        const float4* xr = reinterpret_cast<const float4*>(xs + bt * cols + v * VW);
+#pragma unroll
+        for (int q = 0; q < VW / 4; ++q) {
+          const float4 xv = xr[q];
+          acc0[bt] = fmaf(f0[4 * q + 0], xv.x, acc0[bt]);
+          acc0[bt] = fmaf(f0[4 * q + 1], xv.y, acc0[bt]);
+          acc0[bt] = fmaf(f0[4 * q + 2], xv.z, acc0[bt]);
+          acc0[bt] = fmaf(f0[4 * q + 3], xv.w, acc0[bt]);
+          acc1[bt] = fmaf(f1[4 * q + 0], xv.x, acc1[bt]);
+          acc1[bt] = fmaf(f1[4 * q + 1], xv.y, acc1[bt]);
+          acc1[bt] = fmaf(f1[4 * q + 2], xv.z, acc1[bt]);
+          acc1[bt] = fmaf(f1[4 * q + 3], xv.w, acc1[bt]);
+        }
+      }
+    }
+  };
+#pragma unroll
+  for (int k = 0; k < HOLD; ++k) {
+    const int v = lane + 32 * k;
+    if (v < nvec) fma_vec(h0[k], h1[k], v);
+  }
+  for (int v0 = lane + 32 * HOLD; v0 < nvec; v0 += 32 * kLoadBatch) {
+    uint4 u0[kLoadBatch], u1[kLoadBatch];
+#pragma unroll
+    for (int k = 0; k < kLoadBatch; ++k) {
+      const int v = v0 + 32 * k;
+      if (v < nvec) {
+        u0[k] = ld_stream(w0 + v);
+        u1[k] = ld_stream(w1 + v);
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < kLoadBatch; ++k) {
+      const int v = v0 + 32 * k;
+      if (v < nvec) fma_vec(u0[k], u1[k], v);
+    }
+  }
+  float s0 = 1.f, s1 = 1.f;
+  if (FMT == NC_FP8E4M3) {
+    s0 = m.scale[r0];
+    s1 = m.scale[r1];
+  }
+#pragma unroll
+  for (int bt = 0; bt < BT; ++bt) {
+    if (bt < nb) {
+      float y0 = warp_sum(acc0[bt]);
+      float y1 = warp_sum(acc1[bt]);
+      if (FMT == NC_FP8E4M3) {
+        y0 *= s0;
+        y1 *= s1;
+      }
+      if (lane == bt) {
+        const int j = b0 + bt;
+        if (EPI == EPI_STORE) {
+          out.y[(size_t)j * m.rows + r0] = y0;
+          if (has1) out.y[(size_t)j * m.rows + r1] = y1;
+        } else if (EPI == EPI_RESID) {
+          float* p0 = out.y + (size_t)j * m.rows + r0;
+          *p0 = __ldcg(p0) + y0;
+          if (has1) {
+            float* p1 = out.y + (size_t)j * m.rows + r1;
+            *p1 = __ldcg(p1) + y1;
+          }
+        } else if (EPI == EPI_SWIGLU) {
+          out.y[(size_t)j * (m.rows / 2) + r0 / 2] = silu(y0) * y1;
+        } else {
+          float* z = out.st[out.slots[j]].z;
+          z[r0] = y0;
+          if (has1) z[r1] = y1;
+        }
+      }
+    }
+  }
+}
+
+// ----------------------------------------------------------------- attention
+// One unit of split-KV decode attention: stream row j, KV head g, chunk s of
+// <= kAttnChunk cached positions, computed by 128 threads (4 warps of 32
+// positions).  The fed token's q and k are rotated (rotate-half RoPE) at its
+// absolute position a; cached keys were rotated at their own absolute
+// positions when appended.  Scores depend only on position differences, so
+// this equals the relabelled positions of the sliding window (Sec. 3.9).
+// The last chunk appends the new k, v at ring index a mod L.  Each chunk
+// writes its running max m, sum l and unnormalised accumulator; the chunk
+// that finishes last (atomic ticket) merges all chunks of (j, g) in chunk
+// order into attn_out, so the result does not depend on the finishing order.
+struct AttnSmem {
+  float qs[kMaxGroup][kHeadDim];
+  float kn[kHeadDim], vn[kHeadDim];
+  float cs[kHeadDim / 2], sn[kHeadDim / 2];
+  float wm[4][kMaxGroup], wl[4][kMaxGroup];
+  float wacc[4][kMaxGroup][kHeadDim];
+  int last;
+};
+
+struct AttnIO {
+  const float* qkv;      // [B][qkv_rows], written by the QKV projection
+  float* part;           // [B][hq][nsm][66]
+  int* tickets;          // [B][hkv]
+  float* attn_out;       // [B][hq * 64]
+};
+
+// Values of the unit that do not depend on the QKV projection: the cached
+// key of this lane's position and the values of its warp's 32 positions.
+template <int KBF16>
+struct AttnPre {
+  float kr[kHeadDim];
+  uint32_t vb[32];
+  float2 vf[KBF16 ? 1 : 32];
+};
+
+template <int KBF16>
+__device__ __forceinline__ void attn_preload(const Dims& D, const StreamDev& st, int layer, int g, int s,
+                                             int start, int a, int tid, AttnSmem& sm, AttnPre<KBF16>& pre) {
+  const int warp = tid >> 5, lane = tid & 31;
+  if (tid < kHeadDim / 2) {
+    const double inv_freq = pow((double)D.theta, -2.0 * tid / (double)kHeadDim);
+    double sd, cd;
+    sincos((double)a * inv_freq, &sd, &cd);
+    sm.cs[tid] = (float)cd;
+    sm.sn[tid] = (float)sd;
+  }
+  const size_t plane = (size_t)D.L * kHeadDim;
+  const size_t layer_off = (size_t)layer * 2 * D.hkv * plane;
+  const size_t koff = layer_off + (size_t)g * plane;
+  const size_t voff = layer_off + (size_t)(D.hkv + g) * plane;
+  const int p_lo = start + s * kAttnChunk + warp * 32;
+  const int p = p_lo + lane;
+  if (p < a) {
+    const size_t ri = (size_t)(p & (D.L - 1)) * kHeadDim;
+    if (KBF16) {
+      const uint4* src = reinterpret_cast<const uint4*>(static_cast<const __nv_bfloat16*>(st.kv) + koff + ri);
+#pragma unroll
+      for (int q = 0; q < kHeadDim / 8; ++q) {
+        const uint4 u = src[q];
+        const uint32_t w[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          pre.kr[8 * q + 2 * i] = __uint_as_float(w[i] << 16);
+          pre.kr[8 * q + 2 * i + 1] = __uint_as_float(w[i] & 0xFFFF0000u);
+        }
+      }
+    } else {
+      const float4* src = reinterpret_cast<const float4*>(static_cast<const float*>(st.kv) + koff + ri);
+#pragma unroll
+      for (int q = 0; q < kHeadDim / 4; ++q) {
+        const float4 u = src[q];
+        pre.kr[4 * q] = u.x;
+        pre.kr[4 * q + 1] = u.y;
+        pre.kr[4 * q + 2] = u.z;
+        pre.kr[4 * q + 3] = u.w;
+      }
+    }
+  }
+  const int nvalid = min(32, a - p_lo + 1);
+#pragma unroll
+  for (int i = 0; i < 32; ++i) {
+    const int pi = p_lo + i;
+    if (i < nvalid && pi != a) {
+      const size_t ri = (size_t)(pi & (D.L - 1)) * kHeadDim + 2 * lane;
+      if (KBF16)
+        pre.vb[i] = *reinterpret_cast<const uint32_t*>(static_cast<const __nv_bfloat16*>(st.kv) + voff + ri);
+      else
+        pre.vf[KBF16 ? 0 : i] = *reinterpret_cast<const float2*>(static_cast<const float*>(st.kv) + voff + ri);
+    }
+  }
+}
+
+// L2 prefetch of the cached keys and values a unit will read (no registers).
+__device__ __forceinline__ void attn_prefetch(const Dims& D, const StreamDev& st, int layer, int g, int s,
+                                              int start, int a, int tid) {
+  const int warp = tid >> 5, lane = tid & 31;
+  const size_t plane = (size_t)D.L * kHeadDim;
+  const size_t layer_off = (size_t)layer * 2 * D.hkv * plane;
+  const size_t esz = D.kv_bf16 ? 2 : 4;
+  const int p = start + s * kAttnChunk + warp * 32 + lane;
+  if (p < a) {
+    const char* base = static_cast<const char*>(st.kv);
+    const size_t ri = (size_t)(p & (D.L - 1)) * kHeadDim;
+    for (int part = 0; part < (int)(kHeadDim * esz / 128); ++part) {
+      asm volatile("prefetch.global.L2 [%0];" ::"l"(base + (layer_off + (size_t)g * plane + ri) * esz + 128 * part));
+      asm volatile("prefetch.global.L2 [%0];" ::"l"(base + (layer_off + (size_t)(D.hkv + g) * plane + ri) * esz + 128 * part));
+    }
+  }
+}
+
+// The unit's work once the QKV projection is complete.  `sync` synchronises
+// the unit's 128 threads.
+template <int KBF16, typename Sync>
+__device__ void attn_compute(const Dims& D, StreamDev& st, int layer, int j, int g, int s, int start, int a,
+                             int ns, int tid, AttnSmem& sm, AttnPre<KBF16>& pre, const AttnIO& io, Sync sync) {
+  const int grp = D.hq / D.hkv;
+  const int warp = tid >> 5, lane = tid & 31;
+  sync();
+  const float* row = io.qkv + (size_t)j * D.qkv_rows;
+  for (int e = tid; e < (grp + 1) * (kHeadDim / 2); e += 128) {
+    const int h = e / (kHeadDim / 2), dd = e % (kHeadDim / 2);
+    const float* src = h < grp ? row + (g * grp + h) * kHeadDim : row + D.hq * kHeadDim + g * kHeadDim;
+    const float x1 = __ldcg(src + dd), x2 = __ldcg(src + dd + kHeadDim / 2);
+    const float r1 = x1 * sm.cs[dd] - x2 * sm.sn[dd];
+    const float r2 = x2 * sm.cs[dd] + x1 * sm.sn[dd];
+    if (h < grp) {   // the 1/sqrt(64) score scale is a power of two: exact
+      sm.qs[h][dd] = r1 * 0.125f;
+      sm.qs[h][dd + kHeadDim / 2] = r2 * 0.125f;
+    } else {
+      sm.kn[dd] = r1;
+      sm.kn[dd + kHeadDim / 2] = r2;
+    }
+  }
+  if (tid < kHeadDim) sm.vn[tid] = __ldcg(row + (D.hq + D.hkv) * kHeadDim + g * kHeadDim + tid);
+  sync();
+
+  const size_t plane = (size_t)D.L * kHeadDim;
+  const size_t layer_off = (size_t)layer * 2 * D.hkv * plane;
+  const size_t koff = layer_off + (size_t)g * plane;
+  const size_t voff = layer_off + (size_t)(D.hkv + g) * plane;
+  if (s == ns - 1 && tid < kHeadDim) {
+    const size_t ri = (size_t)(a & (D.L - 1)) * kHeadDim + tid;
+    if (KBF16) {
+      __nv_bfloat16* kv = static_cast<__nv_bfloat16*>(st.kv);
+      kv[koff + ri] = __float2bfloat16_rn(sm.kn[tid]);
+      kv[voff + ri] = __float2bfloat16_rn(sm.vn[tid]);
+    } else {
+      float* kv = static_cast<float*>(st.kv);
+      kv[koff + ri] = sm.kn[tid];
+      kv[voff + ri] = sm.vn[tid];
+    }
+  }
+
+  const int p_lo = start + s * kAttnChunk + warp * 32;
+  const int p = p_lo + lane;
+  const bool valid = p <= a;
+  float sc[kMaxGroup];
+#pragma unroll
+  for (int h = 0; h < kMaxGroup; ++h) sc[h] = 0.f;
+  if (valid) {
+    if (p == a) {
+#pragma unroll
+      for (int d = 0; d < kHeadDim; ++d) pre.kr[d] = sm.kn[d];
+    }
+#pragma unroll
+    for (int h = 0; h < kMaxGroup; ++h) {
+      if (h < grp) {
+        float acc = 0.f;
+#pragma unroll
+        for (int d = 0; d < kHeadDim; ++d) acc = fmaf(sm.qs[h][d], pre.kr[d], acc);
+        sc[h] = acc;
+      }
+    }
+  }
+  float mh[kMaxGroup], eh[kMaxGroup], lh[kMaxGroup];
+#pragma unroll
+  for (int h = 0; h < kMaxGroup; ++h) {
+    if (h < grp) {
+      mh[h] = warp_max(valid ? sc[h] : -INFINITY);
+      eh[h] = valid ? expf(sc[h] - mh[h]) : 0.f;
+      lh[h] = warp_sum(eh[h]);
+    }
+  }
+  // P V: lane owns output dims 2*lane, 2*lane + 1
+  float acc[kMaxGroup][2];
+#pragma unroll
+  for (int h = 0; h < kMaxGroup; ++h) acc[h][0] = acc[h][1] = 0.f;
+  const int nvalid = min(32, a - p_lo + 1);
+#pragma unroll
+  for (int i = 0; i < 32; ++i) {
+    if (i >= nvalid) break;
+    const int pi = p_lo + i;
+    float v0, v1;
+    if (pi == a) {
+      v0 = sm.vn[2 * lane];
+      v1 = sm.vn[2 * lane + 1];
+    } else if (KBF16) {
+      v0 = __uint_as_float(pre.vb[i] << 16);
+      v1 = __uint_as_float(pre.vb[i] & 0xFFFF0000u);
+    } else {
+      v0 = pre.vf[KBF16 ? 0 : i].x;
+      v1 = pre.vf[KBF16 ? 0 : i].y;
+    }
+#pragma unroll
+    for (int h = 0; h < kMaxGroup; ++h) {
+      if (h < grp) {
+        const float e = __shfl_sync(0xffffffffu, eh[h], i);
+        acc[h][0] = fmaf(e, v0, acc[h][0]);
+        acc[h][1] = fmaf(e, v1, acc[h][1]);
+      }
+    }
+  }
+#pragma unroll
+  for (int h = 0; h < kMaxGroup; ++h) {
+    if (h < grp) {
+      if (lane == 0) {
+        sm.wm[warp][h] = nvalid > 0 ? mh[h] : -INFINITY;
+        sm.wl[warp][h] = nvalid > 0 ? lh[h] : 0.f;
+      }
+      sm.wacc[warp][h][2 * lane] = acc[h][0];
+      sm.wacc[warp][h][2 * lane + 1] = acc[h][1];
+    }
+  }
+  sync();
+  const int nsm = attn_splits_max_dev(D);
+  for (int e = tid; e < grp * kHeadDim; e += 128) {
+    const int h = e / kHeadDim, dd = e % kHeadDim;
+    float M = -INFINITY;
+    for (int w = 0; w < 4; ++w)
+      if (start + s * kAttnChunk + w * 32 <= a) M = fmaxf(M, sm.wm[w][h]);
+    float l = 0.f, o = 0.f;
+    for (int w = 0; w < 4; ++w) {
+      if (start + s * kAttnChunk + w * 32 <= a) {
+        const float f = expf(sm.wm[w][h] - M);
+        l = fmaf(sm.wl[w][h], f, l);
+        o = fmaf(sm.wacc[w][h][dd], f, o);
+      }
+    }
+    float* out = io.part + (((size_t)j * D.hq + g * grp + h) * nsm + s) * (kHeadDim + 2);
+    out[dd] = o;
+    if (dd == 0) {
+      out[kHeadDim] = M;
+      out[kHeadDim + 1] = l;
+    }
+  }
+  __threadfence();
+  sync();
+  if (tid == 0) {
+    const int t = atomicAdd(io.tickets + j * D.hkv + g, 1);
+    sm.last = (t == ns - 1);
+    if (sm.last) io.tickets[j * D.hkv + g] = 0;
+  }
+  sync();
+  if (!sm.last) return;
+  __threadfence();
+  for (int e = tid; e < grp * kHeadDim; e += 128) {
+    const int h = e / kHeadDim, dd = e % kHeadDim;
+    const float* ph = io.part + ((size_t)j * D.hq + g * grp + h) * nsm * (kHeadDim + 2);
+    float M = -INFINITY;
+    for (int q = 0; q < ns; ++q) M = fmaxf(M, __ldcg(ph + q * (kHeadDim + 2) + kHeadDim));
+    float l = 0.f, o = 0.f;
+    for (int q = 0; q < ns; ++q) {
+      const float* pq = ph + q * (kHeadDim + 2);
+      const float f = expf(__ldcg(pq + kHeadDim) - M);
+      l = fmaf(__ldcg(pq + kHeadDim + 1), f, l);
+      o = fmaf(__ldcg(pq + dd), f, o);
+    }
+    io.attn_out[(size_t)j * D.hq * kHeadDim + (g * grp + h) * kHeadDim + dd] = o / l;
+  }
+}
+
+}  // namespace dev
+}  // namespace nc

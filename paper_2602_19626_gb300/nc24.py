@@ -48,7 +48,7 @@ NC_TRACE_KINDS = 16
 
 
 class nc_trace(C.Structure):
-    _fields_ = [("n_kinds", C.c_int), ("name", (C.c_char * 32) * NC_TRACE_KINDS),
+    _fields_ = [("n_kinds", C.c_int), ("graphed", C.c_int), ("name", (C.c_char * 32) * NC_TRACE_KINDS),
                 ("launches", C.c_int64 * NC_TRACE_KINDS), ("ms", C.c_double * NC_TRACE_KINDS),
                 ("bytes", C.c_double * NC_TRACE_KINDS)]
 
@@ -309,8 +309,8 @@ class Context:
                     "nc_encode_intervals")
         if not tr:
             return None
-        return [dict(name=tr.name[k].value.decode(), launches=tr.launches[k], ms=tr.ms[k], bytes=tr.bytes[k])
-                for k in range(tr.n_kinds)]
+        return [dict(name=tr.name[k].value.decode(), launches=tr.launches[k], ms=tr.ms[k], bytes=tr.bytes[k],
+                     graphed=bool(tr.graphed)) for k in range(tr.n_kinds)]
 
     def decode(self, data: bytes):
         buf = np.frombuffer(data, dtype=np.uint8).copy()
