@@ -31,9 +31,18 @@ sys.path.insert(0, ROOT)
 import synthetic as S  # noqa: E402
 
 WORKLOADS = {
-    "full_bf16_single": dict(shape=S.FULL, fmt="bf16", seed=1, n_streams=1, length=8192),
-    "full_fp32_single": dict(shape=S.FULL, fmt="fp32", seed=1, n_streams=1, length=8192),
-    "small_fp32_single": dict(shape=S.SMALL, fmt="fp32", seed=0, n_streams=1, length=1024),
+    # one stream, the full-size model in BF16 (the headline configuration)
+    "full_bf16_single": dict(shape=S.FULL, fmt="bf16", seed=1, n_streams=1, length=8192, path="gemv"),
+    # the plain single-stream FP32 path (the denominator of "batched vs plain")
+    "full_fp32_single": dict(shape=S.FULL, fmt="fp32", seed=1, n_streams=1, length=8192, path="gemv"),
+    "small_fp32_single": dict(shape=S.SMALL, fmt="fp32", seed=0, n_streams=1, length=1024, path="gemv"),
+    # 256 streams with log-uniform lengths 512..16,384 on the tensor-core path
+    "batched_bf16_tc": dict(shape=S.FULL, fmt="bf16", seed=2, n_streams=256, lengths=(512, 16384), path="tc"),
+    # the same 256 streams cut to their first 512 tokens: the batch stays full
+    "batched_bf16_tc_512": dict(shape=S.FULL, fmt="bf16", seed=2, n_streams=256, lengths=(512, 16384),
+                                cap=512, path="tc"),
+    # FP8 E4M3 weights, 1,024 streams x 4,096 tokens (first 256 tokens per stream)
+    "fp8_tc_1024_256": dict(shape=S.FULL, fmt="fp8", seed=4, n_streams=1024, length=4096, cap=256, path="tc"),
 }
 
 
@@ -44,9 +53,21 @@ def dist_env():
     return ws, rank, local
 
 
+def workload_lengths(wl):
+    if "lengths" in wl:
+        lo, hi = wl["lengths"]
+        lens = S.stream_lengths(wl["seed"], wl["n_streams"], lo, hi)
+    else:
+        lens = np.full(wl["n_streams"], wl["length"], dtype=np.int64)
+    if "cap" in wl:
+        lens = np.minimum(lens, wl["cap"])
+    return lens
+
+
 def workload_streams(wl):
     shape = wl["shape"]
-    return [S.token_stream(wl["seed"], j, wl["length"], shape.vocab) for j in range(wl["n_streams"])]
+    lens = workload_lengths(wl)
+    return [S.token_stream(wl["seed"], j, int(lens[j]), shape.vocab) for j in range(wl["n_streams"])]
 
 
 # ------------------------------------------------------------- oracle (CPU)
@@ -57,7 +78,7 @@ def oracle_rate(wl, budget_s: float, first_tokens: int | None = None):
     from oracle.compress import StepConfig, StreamState
     from oracle.model import Model
     shape = wl["shape"]
-    toks = workload_streams(dict(wl, n_streams=1))[0]
+    toks = S.token_stream(wl["seed"], 0, int(workload_lengths(wl)[0]), shape.vocab)
     model = Model(shape, S.weights(shape, wl["seed"]), wl["fmt"])
     st = StreamState.new(model, StepConfig())
     t0 = time.perf_counter()
@@ -97,7 +118,7 @@ def run_reference(args, wl):
         n_tot += n
         t_tot += el
     v = n_tot / t_tot
-    sample = (f"first {n_tot // max(args.steps, 1)} tokens of the {wl['length']}-token stream per step "
+    sample = (f"first {n_tot // max(args.steps, 1)} tokens of the first stream per step "
               f"(about {budget:.0f} s each), FP64 oracle on {wl['fmt']}-dequantised weights")
     line = {
         "impl": "reference", "metric": "tokens/s compressed", "value": v, "unit": "tokens/s",
@@ -105,7 +126,7 @@ def run_reference(args, wl):
         "ms_per_step": 1000.0 * t_tot / max(args.steps, 1), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": args.workload, "model": "smollm2-135m-shape random-init",
-                   "streams": wl["n_streams"], "tokens_per_stream": wl["length"]},
+                   "streams": wl["n_streams"], "tokens": int(workload_lengths(wl).sum())},
         "cpu_baseline": {"value": v, "unit": "tokens/s", "cores": blas_threads(), "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": v, "unit": "tokens/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -212,7 +233,8 @@ def run_gpu(args, wl):
     n_tok = int(lens.sum())
     stride = int(lens.max())
     cstream = torch.cuda.Stream()
-    cfg = nc24.make_config(shape, fmt=wl["fmt"], max_streams=wl["n_streams"], device=dev, stream=cstream)
+    cfg = nc24.make_config(shape, fmt=wl["fmt"], max_streams=wl["n_streams"], device=dev, stream=cstream,
+                           path=wl.get("path", "gemv"))
     ctx = nc24.Context(cfg, S.flat_weights(shape, wl["seed"]))
     tok_dev = torch.from_numpy(flat).to(f"cuda:{dev}")
     iv = torch.empty((wl["n_streams"], stride, 2), dtype=torch.int32, device=f"cuda:{dev}")
@@ -273,6 +295,7 @@ def run_gpu(args, wl):
                                "GBps": round(k["bytes"] / (k["ms"] / 1000.0) / 1e9, 1) if k["ms"] > 0 else None}
                    for k in trace if k["launches"]}
         launches_per_step = sum(k["launches"] for k in trace)
+        roofline["graphed"] = bool(trace[0]["graphed"])
     except Exception as exc:  # keep the measured line even if tracing fails
         print(f"[bench] trace failed: {exc}", file=sys.stderr, flush=True)
 
@@ -296,11 +319,18 @@ def run_gpu(args, wl):
            "d2h_bytes_per_step": int(8 * n_tok), "container_bytes": nbytes,
            "bits_per_token": 8.0 * nbytes / n_tok}
 
+    ctx.close()
+    extras = {}
+    for name in args.extra:
+        try:
+            extras[name] = extra_throughput(name, dev)
+        except Exception as exc:
+            extras[name] = {"error": str(exc)[:200]}
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         n, el = oracle_rate(wl, args.cpu_budget)
         cpu = {"value": n / el, "unit": "tokens/s", "cores": blas_threads(), "kind": "oracle",
-               "sample": f"first {n} tokens of the {wl['length']}-token stream, FP64 oracle on "
+               "sample": f"first {n} tokens of the workload's first stream, FP64 oracle on "
                          f"{wl['fmt']}-dequantised weights, {el:.1f} s"}
     if rank == 0:
         line = {
@@ -310,17 +340,52 @@ def run_gpu(args, wl):
             "data": "synthetic",
             "config": {"workload": args.workload, "model": "smollm2-135m-shape random-init",
                        "weights": wl["fmt"], "streams_per_gpu": wl["n_streams"],
-                       "tokens_per_stream": wl["length"], "ctx_len": shape.ctx_len, "slide": shape.slide,
-                       "path": "gemv", "parallelism": f"replicas{ws}",
+                       "tokens_per_gpu": n_tok, "ctx_len": shape.ctx_len, "slide": shape.slide,
+                       "path": wl.get("path", "gemv"), "parallelism": f"replicas{ws}",
                        "l2": "weights (BF16 269 MB) exceed L2 and are re-read every token"},
             "gpu_launches": launches_per_step * args.steps,
             "roofline": roofline, "kernels": kernels, "clocks": clocks, "e2e": e2e,
             "cpu_baseline": cpu, "intervals_valid": ok,
         }
+        if extras:
+            line["extra"] = extras
         print(json.dumps(line), flush=True)
-    ctx.close()
     if ws > 1:
         torch.distributed.destroy_process_group()
+
+
+def extra_throughput(name, dev):
+    """Device-resident throughput of another workload (one warm-up, one timed
+    pass), reported beside the headline line."""
+    import torch
+    from paper_2602_19626_gb300 import nc24
+    wl = WORKLOADS[name]
+    shape = wl["shape"]
+    streams = workload_streams(wl)
+    lens = np.array([len(s) for s in streams], dtype=np.int64)
+    offs = np.concatenate([[0], np.cumsum(lens)[:-1]]).astype(np.int64)
+    flat = np.concatenate(streams).astype(np.int32)
+    stride = int(lens.max())
+    cstream = torch.cuda.Stream()
+    cfg = nc24.make_config(shape, fmt=wl["fmt"], max_streams=wl["n_streams"], device=dev, stream=cstream,
+                           path=wl.get("path", "gemv"))
+    ctx = nc24.Context(cfg, S.flat_weights(shape, wl["seed"]))
+    tok_dev = torch.from_numpy(flat).to(f"cuda:{dev}")
+    iv = torch.empty((wl["n_streams"], stride, 2), dtype=torch.int32, device=f"cuda:{dev}")
+    torch.cuda.synchronize()
+    ctx.encode_intervals(tok_dev, offs, lens, iv, stride)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(cstream)
+    ctx.encode_intervals(tok_dev, offs, lens, iv, stride)
+    e1.record(cstream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    ctx.close()
+    return {"value": float(lens.sum()) / (ms / 1000.0), "unit": "tokens/s", "ms": ms,
+            "streams": wl["n_streams"], "tokens": int(lens.sum()), "weights": wl["fmt"],
+            "path": wl.get("path", "gemv")}
 
 
 def main():
@@ -332,6 +397,8 @@ def main():
     ap.add_argument("--workload", default="full_bf16_single", choices=sorted(WORKLOADS))
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--extra", nargs="*", default=["batched_bf16_tc_512"],
+                    help="further workloads timed once each and reported under 'extra'")
     args = ap.parse_args()
     wl = WORKLOADS[args.workload]
     if args.impl == "reference":

@@ -92,11 +92,13 @@ struct SrcEmbed {
 template <int FMT>
 __device__ __forceinline__ void prefetch_rows(const Mat& m, int gw, int GW, int lane) {
   const size_t row_bytes = (size_t)m.cols * WFmt<FMT>::ESZ;
+  const size_t total = (size_t)m.rows * row_bytes;
   const char* base = static_cast<const char*>(m.w);
   for (int rp = gw; 2 * rp < m.rows; rp += GW) {
+    const size_t first = (size_t)2 * rp * row_bytes;
     const size_t nbytes = (2 * rp + 1 < m.rows ? 2 : 1) * row_bytes;
     for (size_t off = (size_t)lane * 128; off < nbytes; off += 32 * 128)
-      asm volatile("prefetch.global.L2 [%0];" ::"l"(base + 2 * rp * row_bytes + off));
+      if (first + off < total) asm volatile("prefetch.global.L2 [%0];" ::"l"(base + first + off));
   }
 }
 
@@ -162,8 +164,8 @@ __global__ void __launch_bounds__(kStepThreads, 1) k_step(Dims D, Batch b, StepA
   const int GU = gridDim.x * kGroups;
   unsigned epoch = 0;
 
-  pdl_wait();
-  pdl_trigger();
+  // Launched without the PDL attribute and never signals early launch of its
+  // dependents: a kernel that follows starts only after this grid completed.
   // rows of this step: all rows, or (encoder) the rows with tokens left;
   // rows are sorted longest first, so those are a prefix
   if (tid == 0) {

@@ -385,7 +385,7 @@ __device__ __forceinline__ void attn_prefetch(const Dims& D, const StreamDev& st
   const size_t layer_off = (size_t)layer * 2 * D.hkv * plane;
   const size_t esz = D.kv_bf16 ? 2 : 4;
   const int p = start + s * kAttnChunk + warp * 32 + lane;
-  if (p < a) {
+  if (p >= start && p < a && layer >= 0 && layer < D.n_layers && g >= 0 && g < D.hkv) {
     const char* base = static_cast<const char*>(st.kv);
     const size_t ri = (size_t)(p & (D.L - 1)) * kHeadDim;
     for (int part = 0; part < (int)(kHeadDim * esz / 128); ++part) {
