@@ -315,23 +315,3 @@ def test_mixed_nll_kernels_vs_oracle_and_fd(nc):
             lm = mixed_nll(torch.from_numpy(bm).cuda(), tth.detach(), *args)[i].item()
             assert abs((lp - lm) / (2 * eps) - gb[i, k]) < 2e-3 * max(1.0, abs(gb[i, k]))
 
-
-def test_persistent_step_matches_per_phase_kernels(nc, monkeypatch):
-    """The persistent step kernel (one cooperative launch per step) and the
-    one-kernel-per-phase path run the same device functions: their CDFs are
-    bit-identical, across a window slide."""
-    shape, seed = S.SMALL, 5
-    toks = S.token_stream(seed, 0, 150, shape.vocab)
-    shape = S.ModelShape(**{**shape.as_dict(), "ctx_len": 64, "slide": 16})
-    outs = []
-    for step in ("1", "0"):
-        monkeypatch.setenv("NC24_STEP", step)
-        ctx = nc.Context(nc.make_config(shape, fmt="bf16", warmup=20), S.flat_weights(shape, seed))
-        ctx.stream_open(0, len(toks))
-        rows = []
-        for t in toks:
-            rows.append(ctx.step_cdf([0])[0].copy())
-            ctx.update_bias([0], [int(t)])
-        ctx.close()
-        outs.append(np.stack(rows))
-    assert np.array_equal(outs[0], outs[1])
