@@ -397,10 +397,14 @@ def main():
     ap.add_argument("--workload", default="full_bf16_single", choices=sorted(WORKLOADS))
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--tokens", type=int, default=0,
+                    help="cut every stream to this many tokens (short runs for profiling)")
     ap.add_argument("--extra", nargs="*", default=["batched_bf16_tc_512"],
                     help="further workloads timed once each and reported under 'extra'")
     args = ap.parse_args()
     wl = WORKLOADS[args.workload]
+    if args.tokens > 0:
+        wl = dict(wl, cap=min(wl.get("cap", args.tokens), args.tokens))
     if args.impl == "reference":
         run_reference(args, wl)
     else:
