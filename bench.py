@@ -53,21 +53,26 @@ def dist_env():
     return ws, rank, local
 
 
-def workload_lengths(wl):
+def workload_lengths(wl, world: int = 1):
+    """Lengths of the whole job: world x n_streams streams (weak scaling)."""
+    n = wl["n_streams"] * world
     if "lengths" in wl:
         lo, hi = wl["lengths"]
-        lens = S.stream_lengths(wl["seed"], wl["n_streams"], lo, hi)
+        lens = S.stream_lengths(wl["seed"], n, lo, hi)
     else:
-        lens = np.full(wl["n_streams"], wl["length"], dtype=np.int64)
+        lens = np.full(n, wl["length"], dtype=np.int64)
     if "cap" in wl:
         lens = np.minimum(lens, wl["cap"])
     return lens
 
 
-def workload_streams(wl):
+def workload_streams(wl, world: int = 1, rank: int = 0):
+    """This rank's share of the job's streams (longest-first bin packing)."""
+    from paper_2602_19626_gb300.partition import partition_streams
     shape = wl["shape"]
-    lens = workload_lengths(wl)
-    return [S.token_stream(wl["seed"], j, int(lens[j]), shape.vocab) for j in range(wl["n_streams"])]
+    lens = workload_lengths(wl, world)
+    mine = partition_streams(lens, world)[rank]
+    return [S.token_stream(wl["seed"], j, int(lens[j]), shape.vocab) for j in sorted(mine)]
 
 
 # ------------------------------------------------------------- oracle (CPU)
@@ -226,18 +231,18 @@ def run_gpu(args, wl):
     from paper_2602_19626_gb300 import nc24
 
     shape = wl["shape"]
-    streams = workload_streams(wl)
+    streams = workload_streams(wl, ws, rank)
     lens = np.array([len(s) for s in streams], dtype=np.int64)
     offs = np.concatenate([[0], np.cumsum(lens)[:-1]]).astype(np.int64)
     flat = np.concatenate(streams).astype(np.int32)
     n_tok = int(lens.sum())
     stride = int(lens.max())
     cstream = torch.cuda.Stream()
-    cfg = nc24.make_config(shape, fmt=wl["fmt"], max_streams=wl["n_streams"], device=dev, stream=cstream,
+    cfg = nc24.make_config(shape, fmt=wl["fmt"], max_streams=len(streams), device=dev, stream=cstream,
                            path=wl.get("path", "gemv"))
     ctx = nc24.Context(cfg, S.flat_weights(shape, wl["seed"]))
     tok_dev = torch.from_numpy(flat).to(f"cuda:{dev}")
-    iv = torch.empty((wl["n_streams"], stride, 2), dtype=torch.int32, device=f"cuda:{dev}")
+    iv = torch.empty((len(streams), stride, 2), dtype=torch.int32, device=f"cuda:{dev}")
     torch.cuda.synchronize()
 
     def step():
@@ -265,7 +270,13 @@ def run_gpu(args, wl):
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         ms = float(t.item())
         torch.distributed.barrier()
-    total_tokens = n_tok * args.steps * ws
+    if ws > 1:
+        t = torch.tensor([n_tok], device=f"cuda:{dev}", dtype=torch.float64)
+        torch.distributed.all_reduce(t)
+        job_tokens = float(t.item())
+    else:
+        job_tokens = float(n_tok)
+    total_tokens = job_tokens * args.steps
     value = total_tokens / (ms / 1000.0)
     print(f"[bench] timed {args.steps} steps: {ms:.1f} ms, {value:.1f} tokens/s", file=sys.stderr, flush=True)
 
@@ -314,8 +325,8 @@ def run_gpu(args, wl):
         t = torch.tensor([e2e_s], device=f"cuda:{dev}", dtype=torch.float64)
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         e2e_s = float(t.item())
-    e2e = {"value": n_tok * e2e_steps * ws / e2e_s, "unit": "tokens/s",
-           "h2d_bytes_per_step": int(flat.nbytes + 16 * wl["n_streams"]),
+    e2e = {"value": job_tokens * e2e_steps / e2e_s, "unit": "tokens/s",
+           "h2d_bytes_per_step": int(flat.nbytes + 16 * len(streams)),
            "d2h_bytes_per_step": int(8 * n_tok), "container_bytes": nbytes,
            "bits_per_token": 8.0 * nbytes / n_tok}
 

@@ -3,6 +3,7 @@
 // building-block entry points.  See include/nc24.h for the contract.
 #include <algorithm>
 #include <cstdio>
+#include <cmath>
 #include <cstdlib>
 #include <cstring>
 #include <new>
@@ -189,6 +190,7 @@ static std::string validate(const nc_config& c) {
   if (c.n_kv_heads < 1 || c.n_heads % c.n_kv_heads || c.n_heads / c.n_kv_heads > kMaxGroup)
     return "n_heads must be a multiple of n_kv_heads (at most 4 per KV head)";
   if (c.d_ffn < 16 || c.d_ffn % 16) return "d_ffn must be a positive multiple of 16";
+  if (c.d_model > 4096 || c.d_ffn > 4096) return "d_model and d_ffn must be at most 4096";
   if (c.vocab < 2 || c.vocab > 65535) return "vocab must be in [2, 65535]";
   if (c.ctx_len < 2 || (c.ctx_len & (c.ctx_len - 1)) || c.slide < 1 || c.slide >= c.ctx_len)
     return "ctx_len must be a power of two > slide > 0";
@@ -383,6 +385,7 @@ extern "C" int nc_ctx_create(const nc_config* cfg, const void* weights, size_t n
   if (nbytes != n_params(*cfg) * sizeof(float)) return NC_EINVAL;
   nc_ctx* ctx = new (std::nothrow) nc_ctx();
   if (!ctx) return NC_ENOMEM;
+  cudaGetLastError();                              // a stale error of an earlier call is not ours
   ctx->cfg = *cfg;
   ctx->fmt = cfg->weight_fmt;
   const nc_config& c = *cfg;
@@ -411,6 +414,22 @@ extern "C" int nc_ctx_create(const nc_config* cfg, const void* weights, size_t n
   D.L = c.ctx_len;
   D.C = c.slide;
   D.qkv_rows = (c.n_heads + 2 * c.n_kv_heads) * kHeadDim;
+  {
+    // RoPE table: (cos, sin) of v * 256^k * theta^(-2j/64), FP64 then rounded
+    std::vector<float2> tab((size_t)kRopeLevels * 256 * 32);
+    for (int k = 0; k < kRopeLevels; ++k)
+      for (int v = 0; v < 256; ++v)
+        for (int jf = 0; jf < 32; ++jf) {
+          const double inv = std::pow((double)c.rope_theta, -2.0 * jf / (double)kHeadDim);
+          const double ang = (double)v * std::ldexp(1.0, 8 * k) * inv;
+          tab[((size_t)k * 256 + v) * 32 + jf] = make_float2((float)std::cos(ang), (float)std::sin(ang));
+        }
+    float2* dtab = nullptr;
+    if (dalloc(ctx, &dtab, tab.size() * sizeof(float2)) != cudaSuccess ||
+        cudaMemcpy(dtab, tab.data(), tab.size() * sizeof(float2), cudaMemcpyHostToDevice) != cudaSuccess)
+      return bail(NC_ENOMEM);
+    D.rope_tab = dtab;
+  }
   D.eps = c.rms_eps;
   D.theta = c.rope_theta;
   D.tau = c.temperature;
@@ -571,6 +590,7 @@ static int open_slot(nc_ctx* ctx, int32_t id, int64_t max_len, int* slot_out) {
       break;
     }
   if (si < 0) return fail(ctx, NC_EINVAL, "no free stream slot");
+  if (max_len >= kMaxPosition) return fail(ctx, NC_EINVAL, "stream longer than 2^24 - 1 tokens");
   Slot& s = ctx->slots[si];
   int st = slot_alloc(ctx, s, max_len);
   if (st != NC_OK) return st;
@@ -618,7 +638,8 @@ static int open_slot(nc_ctx* ctx, int32_t id, int64_t max_len, int* slot_out) {
 extern "C" int nc_stream_open(nc_ctx* ctx, int32_t stream_id, int64_t expected_len) {
   if (!ctx) return NC_EINVAL;
   if (ctx->poisoned) return NC_ESTATE;
-  if (stream_id < 0 || expected_len < 1 || expected_len > (1 << 30)) return fail(ctx, NC_EINVAL, "bad stream id or length");
+  if (stream_id < 0 || expected_len < 1 || expected_len >= kMaxPosition)
+    return fail(ctx, NC_EINVAL, "bad stream id or length (at most 2^24 - 1 tokens)");
   if (ctx->id2slot.count(stream_id)) return fail(ctx, NC_EINVAL, "stream id already open");
   cudaSetDevice(ctx->cfg.device);
   int si;
@@ -914,6 +935,7 @@ static int check_status(nc_ctx* ctx, const std::vector<int>& slot_idx) {
 static int step_common(nc_ctx* ctx, int n, const int32_t* ids, const int32_t* prev, float* z,
                        float* pt, float* png, float* p, uint32_t* cdf_out) {
   if (!ctx) return NC_EINVAL;
+  cudaGetLastError();
   if (ctx->poisoned) return fail(ctx, NC_ESTATE, "context poisoned by an earlier CUDA error");
   cudaSetDevice(ctx->cfg.device);
   std::vector<int> si;
@@ -958,6 +980,7 @@ extern "C" int nc_step_probe(nc_ctx* ctx, int n, const int32_t* stream_ids, floa
 
 extern "C" int nc_update_bias(nc_ctx* ctx, int n, const int32_t* stream_ids, const int32_t* observed) {
   if (!ctx) return NC_EINVAL;
+  cudaGetLastError();
   if (ctx->poisoned) return fail(ctx, NC_ESTATE, "context poisoned by an earlier CUDA error");
   if (!observed) return fail(ctx, NC_EINVAL, "observed is NULL");
   cudaSetDevice(ctx->cfg.device);
@@ -1457,6 +1480,8 @@ extern "C" int nc_floor_counts(const float* p, int64_t n, uint32_t K, uint32_t f
 extern "C" int nc_gemm_tc(const void* W, const void* X, const float* w_scale, const float* x_scale, int fp8, int M,
                           int N, int K, int bn, float* Y, void* stream) {
   if (!W || !X || !Y || M < 1 || N < 1 || K < 1 || (fp8 && (!w_scale || !x_scale))) return NC_EINVAL;
+  cudaGetLastError();                              // a stale error of an earlier call is not ours
+  if (prepare_tc_kernels() != cudaSuccess) return NC_ECUDA;
   if (bn != 32 && bn != 64 && bn != 128 && bn != 256) return NC_EINVAL;
   const int esz = fp8 ? 1 : 2;
   if ((K * esz) % 16 || (reinterpret_cast<uintptr_t>(W) | reinterpret_cast<uintptr_t>(X)) % 16) return NC_EINVAL;

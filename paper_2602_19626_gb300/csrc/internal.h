@@ -57,8 +57,15 @@ struct StreamDev {
   void* kv;                 // [layers][2][Hkv][L][64], FP32 (FP32 weights) or BF16
 };
 
+// RoPE angles: position p = h 2^16 + m 2^8 + l (p < 2^24); rope_tab holds
+// (cos, sin) of l w_j, m 2^8 w_j and h 2^16 w_j for the 32 frequencies w_j,
+// each computed in FP64 and rounded once; the rotation of p is their product.
+constexpr int kRopeLevels = 3;
+constexpr int kMaxPosition = 1 << 24;
+
 struct Dims {
   int pdl;                  // launch step kernels with programmatic dependent launch
+  const float2* rope_tab;   // [kRopeLevels][256][32]
   int n_layers, d, hq, hkv, F, V, L, C;
   int qkv_rows;             // (hq + 2 hkv) * 64
   float eps, theta, tau;

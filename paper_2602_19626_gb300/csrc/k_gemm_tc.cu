@@ -426,6 +426,8 @@ bool tc_encode_tmap(void* tmap, const void* base, int elem_bytes, int64_t inner,
 }
 
 cudaError_t prepare_tc_kernels() {
+  static bool done = false;                        // per-kernel attributes: once per process
+  if (done) return cudaSuccess;
   cudaError_t e = cudaSuccess;
   for (int kb = 0; kb < 2 && e == cudaSuccess; ++kb) {
     if (kb) {
@@ -440,6 +442,7 @@ cudaError_t prepare_tc_kernels() {
       if (e == cudaSuccess) e = prepare_tc_epi<0, EPI_LOGITS>();
     }
   }
+  done = e == cudaSuccess;
   return e;
 }
 

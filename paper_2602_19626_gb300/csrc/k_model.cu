@@ -36,7 +36,7 @@ __global__ void k_embed(Dims D, Batch b, const void* E, const float* Escale, flo
 // warp owns one row pair (gemv_rowpair).  The activation tile for up to kBT
 // streams sits in shared memory; larger batches loop over tiles with the
 // warp's weights kept in registers.
-template <int FMT, int PRO, int EPI>
+template <int FMT, int PRO, int EPI, int HOLD, int BT>
 __global__ void __launch_bounds__(kGemvThreads) k_gemv(Dims D, Batch b, Mat m, GemvIO io) {
   extern __shared__ float4 smem4[];
   float* xs = reinterpret_cast<float*>(smem4);   // [kBT][cols]
@@ -46,8 +46,8 @@ __global__ void __launch_bounds__(kGemvThreads) k_gemv(Dims D, Batch b, Mat m, G
   const bool have = 2 * rp < m.rows;
   // Weights do not depend on earlier kernels: fetch this warp's rows before
   // waiting on the predecessor, so the fetch overlaps its execution.
-  uint4 h0[kHold], h1[kHold];
-  if (have) load_rowpair<FMT>(m, rp, lane, h0, h1);
+  uint4 h0[HOLD], h1[HOLD];
+  if (have) load_rowpair<FMT, HOLD>(m, rp, lane, h0, h1);
   pdl_wait();
   pdl_trigger();
   const int B = *b.nB;
@@ -55,10 +55,10 @@ __global__ void __launch_bounds__(kGemvThreads) k_gemv(Dims D, Batch b, Mat m, G
   const int cols = m.cols;
   auto src = [&](int row, int c) { return __ldcg(io.x + (size_t)row * cols + c); };
   auto sync = [] { __syncthreads(); };
-  for (int b0 = 0; b0 < B; b0 += kBT) {
-    const int nb = min(kBT, B - b0);
+  for (int b0 = 0; b0 < B; b0 += BT) {
+    const int nb = min(BT, B - b0);
     prologue<PRO == PRO_RMSNORM>(D, src, io.g, cols, b0, nb, xs, ps, threadIdx.x, kGemvThreads, sync);
-    if (have) gemv_rowpair<FMT, EPI>(m, rp, xs, b0, nb, h0, h1, lane, out);
+    if (have) gemv_rowpair<FMT, EPI, HOLD, BT>(m, rp, xs, b0, nb, h0, h1, lane, out);
     __syncthreads();
   }
 }
@@ -142,7 +142,17 @@ static cudaError_t gemv_t(const Dims& D, const Batch& b, const Mat& m, const Gem
   const int rows_per_block = kGemvWarps * 2;
   const int grid = (m.rows + rows_per_block - 1) / rows_per_block;
   const size_t smem = (size_t)kBT * m.cols * sizeof(float);
-  return launch_kernel(k_gemv<FMT, PRO, EPI>, dim3(grid), dim3(kGemvThreads), smem, s, D.pdl, D, b, m, io);
+  // rows of at most 96 vectors (3 per lane) hold them all with 3 registers
+  // quads; longer rows hold 8 and stream the rest
+  // a context of one stream uses the one-stream tile (fewer registers)
+  const bool short_row = m.cols / WFmt<FMT>::VW <= 96;
+  if (b.Bmax == 1)
+    return short_row
+               ? launch_kernel(k_gemv<FMT, PRO, EPI, 3, 1>, dim3(grid), dim3(kGemvThreads), smem, s, D.pdl, D, b, m, io)
+               : launch_kernel(k_gemv<FMT, PRO, EPI, 8, 1>, dim3(grid), dim3(kGemvThreads), smem, s, D.pdl, D, b, m, io);
+  return short_row
+             ? launch_kernel(k_gemv<FMT, PRO, EPI, 3, kBT>, dim3(grid), dim3(kGemvThreads), smem, s, D.pdl, D, b, m, io)
+             : launch_kernel(k_gemv<FMT, PRO, EPI, 8, kBT>, dim3(grid), dim3(kGemvThreads), smem, s, D.pdl, D, b, m, io);
 }
 
 template <int FMT>
@@ -155,17 +165,35 @@ static cudaError_t gemv_f(const Dims& D, const Batch& b, const Mat& m, int pro, 
   return cudaErrorInvalidValue;
 }
 
+// The dynamic shared-memory cap is a per-kernel global: set it to the
+// largest activation tile any supported model needs (kBT rows of the widest
+// projection input, 4,096 columns), not to the current model's, so that
+// contexts of different shapes can coexist.
+constexpr int kMaxGemvCols = 4096;
+
 template <int FMT>
 static cudaError_t prepare_gemv_f(int cmax) {
-  const int smem = kBT * cmax * (int)sizeof(float);
+  const int smem = kBT * (cmax > kMaxGemvCols ? cmax : kMaxGemvCols) * (int)sizeof(float);
   cudaError_t e = cudaSuccess;
   auto set = [&](auto kern) {
     if (e == cudaSuccess) e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   };
-  set(k_gemv<FMT, PRO_RMSNORM, EPI_STORE>);
-  set(k_gemv<FMT, PRO_RMSNORM, EPI_SWIGLU>);
-  set(k_gemv<FMT, PRO_PLAIN, EPI_RESID>);
-  set(k_gemv<FMT, PRO_RMSNORM, EPI_LOGITS>);
+  set(k_gemv<FMT, PRO_RMSNORM, EPI_STORE, 3, 1>);
+  set(k_gemv<FMT, PRO_RMSNORM, EPI_SWIGLU, 3, 1>);
+  set(k_gemv<FMT, PRO_PLAIN, EPI_RESID, 3, 1>);
+  set(k_gemv<FMT, PRO_RMSNORM, EPI_LOGITS, 3, 1>);
+  set(k_gemv<FMT, PRO_RMSNORM, EPI_STORE, 8, 1>);
+  set(k_gemv<FMT, PRO_RMSNORM, EPI_SWIGLU, 8, 1>);
+  set(k_gemv<FMT, PRO_PLAIN, EPI_RESID, 8, 1>);
+  set(k_gemv<FMT, PRO_RMSNORM, EPI_LOGITS, 8, 1>);
+  set(k_gemv<FMT, PRO_RMSNORM, EPI_STORE, 3, kBT>);
+  set(k_gemv<FMT, PRO_RMSNORM, EPI_SWIGLU, 3, kBT>);
+  set(k_gemv<FMT, PRO_PLAIN, EPI_RESID, 3, kBT>);
+  set(k_gemv<FMT, PRO_RMSNORM, EPI_LOGITS, 3, kBT>);
+  set(k_gemv<FMT, PRO_RMSNORM, EPI_STORE, 8, kBT>);
+  set(k_gemv<FMT, PRO_RMSNORM, EPI_SWIGLU, 8, kBT>);
+  set(k_gemv<FMT, PRO_PLAIN, EPI_RESID, 8, kBT>);
+  set(k_gemv<FMT, PRO_RMSNORM, EPI_LOGITS, 8, kBT>);
   return e;
 }
 

@@ -325,11 +325,13 @@ __device__ __forceinline__ void attn_preload(const Dims& D, const StreamDev& st,
                                              int start, int a, int tid, AttnSmem& sm, AttnPre<KBF16>& pre) {
   const int warp = tid >> 5, lane = tid & 31;
   if (tid < kHeadDim / 2) {
-    const double inv_freq = pow((double)D.theta, -2.0 * tid / (double)kHeadDim);
-    double sd, cd;
-    sincos((double)a * inv_freq, &sd, &cd);
-    sm.cs[tid] = (float)cd;
-    sm.sn[tid] = (float)sd;
+    // rotation of position a: product of the three table rotations
+    const float2 t1 = D.rope_tab[(0 * 256 + (a & 255)) * 32 + tid];
+    const float2 t2 = D.rope_tab[(1 * 256 + ((a >> 8) & 255)) * 32 + tid];
+    const float2 t3 = D.rope_tab[(2 * 256 + ((a >> 16) & 255)) * 32 + tid];
+    const float c12 = t1.x * t2.x - t1.y * t2.y, s12 = t1.x * t2.y + t1.y * t2.x;
+    sm.cs[tid] = c12 * t3.x - s12 * t3.y;
+    sm.sn[tid] = c12 * t3.y + s12 * t3.x;
   }
   const size_t plane = (size_t)D.L * kHeadDim;
   const size_t layer_off = (size_t)layer * 2 * D.hkv * plane;
@@ -540,17 +542,42 @@ __device__ void attn_compute(const Dims& D, StreamDev& st, int layer, int j, int
   sync();
   if (!sm.last) return;
   __threadfence();
+  constexpr int kUnrolled = 16;                   // chunks merged from registers
   for (int e = tid; e < grp * kHeadDim; e += 128) {
     const int h = e / kHeadDim, dd = e % kHeadDim;
     const float* ph = io.part + ((size_t)j * D.hq + g * grp + h) * nsm * (kHeadDim + 2);
-    float M = -INFINITY;
-    for (int q = 0; q < ns; ++q) M = fmaxf(M, __ldcg(ph + q * (kHeadDim + 2) + kHeadDim));
-    float l = 0.f, o = 0.f;
-    for (int q = 0; q < ns; ++q) {
-      const float* pq = ph + q * (kHeadDim + 2);
-      const float f = expf(__ldcg(pq + kHeadDim) - M);
-      l = fmaf(__ldcg(pq + kHeadDim + 1), f, l);
-      o = fmaf(__ldcg(pq + dd), f, o);
+    float M = -INFINITY, l = 0.f, o = 0.f;
+    if (ns <= kUnrolled) {
+      // issue every load first (one round trip), then merge in chunk order
+      float mv[kUnrolled], lv[kUnrolled], av[kUnrolled];
+#pragma unroll
+      for (int q = 0; q < kUnrolled; ++q) {
+        if (q < ns) {
+          const float* pq = ph + q * (kHeadDim + 2);
+          mv[q] = __ldcg(pq + kHeadDim);
+          lv[q] = __ldcg(pq + kHeadDim + 1);
+          av[q] = __ldcg(pq + dd);
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < kUnrolled; ++q)
+        if (q < ns) M = fmaxf(M, mv[q]);
+#pragma unroll
+      for (int q = 0; q < kUnrolled; ++q) {
+        if (q < ns) {
+          const float f = expf(mv[q] - M);
+          l = fmaf(lv[q], f, l);
+          o = fmaf(av[q], f, o);
+        }
+      }
+    } else {
+      for (int q = 0; q < ns; ++q) M = fmaxf(M, __ldcg(ph + q * (kHeadDim + 2) + kHeadDim));
+      for (int q = 0; q < ns; ++q) {
+        const float* pq = ph + q * (kHeadDim + 2);
+        const float f = expf(__ldcg(pq + kHeadDim) - M);
+        l = fmaf(__ldcg(pq + kHeadDim + 1), f, l);
+        o = fmaf(__ldcg(pq + dd), f, o);
+      }
     }
     io.attn_out[(size_t)j * D.hq * kHeadDim + (g * grp + h) * kHeadDim + dd] = o / l;
   }
