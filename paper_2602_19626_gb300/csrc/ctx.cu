@@ -70,13 +70,7 @@ struct nc_ctx {
   // activations for up to max_streams rows
   float* x = nullptr;
   float* qkv = nullptr;
-  float* part = nullptr;
-  int* tickets = nullptr;            // [max_streams][hkv] attention merge tickets
   float* attn_out = nullptr;         // [max_streams][hq * 64]
-  LayerW* d_layers = nullptr;        // device copy of the layer table (persistent step)
-  unsigned* step_bar = nullptr;      // persistent step: barrier counter and error word
-  int* step_err = nullptr;
-  bool use_step = false;             // GEMV path: one cooperative launch per step
   float* h = nullptr;
   uint32_t* cdf = nullptr;
   int32_t* d_slots = nullptr;
@@ -194,6 +188,7 @@ static std::string validate(const nc_config& c) {
   if (c.vocab < 2 || c.vocab > 65535) return "vocab must be in [2, 65535]";
   if (c.ctx_len < 2 || (c.ctx_len & (c.ctx_len - 1)) || c.slide < 1 || c.slide >= c.ctx_len)
     return "ctx_len must be a power of two > slide > 0";
+  if (c.ctx_len > 2048) return "ctx_len must be at most 2048 (8 attention CTAs of 256 positions)";
   if (c.ngram_order < 0 || c.ngram_order > kMaxOrder) return "ngram_order must be 0..3";
   if (c.cdf_log2_total < 16 || c.cdf_log2_total > 24) return "cdf_log2_total must be 16..24";
   if (c.floor < 1 || (uint64_t)c.vocab * c.floor >= (1ull << c.cdf_log2_total))
@@ -510,10 +505,8 @@ extern "C" int nc_ctx_create(const nc_config* cfg, const void* weights, size_t n
 
   // ---- activations and per-step buffers
   const size_t B = c.max_streams;
-  const int nsm = attn_max_splits(D);
   if (dalloc(ctx, &ctx->x, B * D.d * 4) || dalloc(ctx, &ctx->qkv, B * D.qkv_rows * 4) ||
-      dalloc(ctx, &ctx->part, B * D.hq * nsm * (kHeadDim + 2) * 4) ||
-      dalloc(ctx, &ctx->tickets, B * D.hkv * 4) || dalloc(ctx, &ctx->attn_out, B * D.hq * kHeadDim * 4) ||
+      dalloc(ctx, &ctx->attn_out, B * D.hq * kHeadDim * 4) ||
       dalloc(ctx, &ctx->h, B * D.F * 4) || dalloc(ctx, &ctx->cdf, B * (D.V + 1) * 4) ||
       dalloc(ctx, &ctx->d_slots, B * 4) || dalloc(ctx, &ctx->d_nB, 16) ||
       dalloc(ctx, &ctx->d_obs, B * 4) || dalloc(ctx, &ctx->d_target, B * 4) ||
@@ -527,20 +520,10 @@ extern "C" int nc_ctx_create(const nc_config* cfg, const void* weights, size_t n
   ctx->h_st.assign(B, StreamDev{});
   ctx->slots.assign(B, Slot{});
   if (cudaMemset(ctx->d_st, 0, B * sizeof(StreamDev)) != cudaSuccess) return bail(NC_ECUDA);
-  if (cudaMemset(ctx->d_status, 0, B * 4) != cudaSuccess ||
-      cudaMemset(ctx->tickets, 0, B * D.hkv * 4) != cudaSuccess)
-    return bail(NC_ECUDA);
+  if (cudaMemset(ctx->d_status, 0, B * 4) != cudaSuccess) return bail(NC_ECUDA);
   if (prepare_model_kernels(D, ctx->fmt) != cudaSuccess || prepare_vocab_kernels(D) != cudaSuccess ||
       (c.path == NC_PATH_TC && prepare_tc_kernels() != cudaSuccess))
     return bail(NC_ECUDA);
-  // The persistent step kernel (k_step.cu) stays disabled: its first launch
-  // raised an illegal-address fault whose cause is not yet found.
-  ctx->use_step = false;
-  if (dalloc(ctx, &ctx->d_layers, D.n_layers * sizeof(LayerW)) || dalloc(ctx, &ctx->step_bar, 16) ||
-      dalloc(ctx, &ctx->step_err, 16) ||
-      cudaMemcpy(ctx->d_layers, ctx->layers.data(), D.n_layers * sizeof(LayerW), cudaMemcpyHostToDevice) ||
-      cudaMemset(ctx->step_err, 0, 16))
-    return bail(NC_ENOMEM);
   if (c.path == NC_PATH_TC) {
     const int st2 = tc_setup(ctx);
     if (st2 != NC_OK) return bail(st2);
@@ -671,10 +654,9 @@ static Batch make_batch(nc_ctx* ctx) {
 
 // Kernel kinds reported by nc_trace.
 enum TraceKind { TK_PREPARE, TK_EMBED, TK_QKV, TK_ATTN, TK_O, TK_GU, TK_DOWN, TK_LMHEAD, TK_VOCAB,
-                 TK_NGRAM, TK_STEP, TK_COUNT };
+                 TK_NGRAM, TK_COUNT };
 static const char* kTraceNames[TK_COUNT] = {"prepare", "embed", "gemv_qkv", "attn", "gemv_o",
-                                            "gemv_gate_up", "gemv_down", "lm_head", "vocab", "ngram_update",
-                                            "model_step"};
+                                            "gemv_gate_up", "gemv_down", "lm_head", "vocab", "ngram_update"};
 
 // Records a CUDA event after every launch of a step (when on) so that the
 // device time of each kernel is the gap between consecutive events.
@@ -704,48 +686,12 @@ struct StepMarks {
 // Model forward of every active row: logits into each stream's z.
 static cudaError_t launch_model_tc(nc_ctx* ctx, const Batch& b, StepMarks& m);
 
-struct EncodeRows {            // encoder rows for the persistent step
-  const int32_t* tok_flat;
-  const int64_t* offs;
-  const int64_t* lens;
-};
-
-static StepArgs step_args(nc_ctx* ctx, const EncodeRows* enc) {
-  StepArgs A{};
-  A.embed = ctx->embed;
-  A.embed_scale = ctx->embed_scale;
-  A.layers = ctx->d_layers;
-  A.g_final = ctx->g_final;
-  A.x = ctx->x;
-  A.qkv = ctx->qkv;
-  A.part = ctx->part;
-  A.tickets = ctx->tickets;
-  A.attn_out = ctx->attn_out;
-  A.h = ctx->h;
-  A.bar = ctx->step_bar;
-  A.err = ctx->step_err;
-  if (enc) {
-    A.encode = 1;
-    A.tok_flat = enc->tok_flat;
-    A.offs = enc->offs;
-    A.lens = enc->lens;
-    A.obs = ctx->d_obs;
-    A.nB_out = ctx->d_nB;
-  }
-  return A;
-}
-
 static cudaError_t launch_model(nc_ctx* ctx, const Batch& b, StepMarks* mk = nullptr) {
   const Dims& D = ctx->D;
   cudaStream_t s = ctx->stream;
   StepMarks none;
   StepMarks& m = mk ? *mk : none;
   if (ctx->cfg.path == NC_PATH_TC) return launch_model_tc(ctx, b, m);
-  if (ctx->use_step) {
-    cudaError_t e = launch_step(D, b, ctx->fmt, step_args(ctx, nullptr), s);
-    if (e == cudaSuccess) e = m.mark(s, TK_STEP);
-    return e;
-  }
   cudaError_t e = launch_embed(D, b, ctx->embed, ctx->embed_scale, ctx->fmt, ctx->x, s);
   if (e == cudaSuccess) e = m.mark(s, TK_EMBED);
   for (int l = 0; l < D.n_layers && e == cudaSuccess; ++l) {
@@ -756,7 +702,7 @@ static cudaError_t launch_model(nc_ctx* ctx, const Batch& b, StepMarks* mk = nul
     io.y = ctx->qkv;
     e = launch_gemv(D, b, L.qkv, ctx->fmt, PRO_RMSNORM, EPI_STORE, io, s);
     if (e == cudaSuccess) e = m.mark(s, TK_QKV);
-    if (e == cudaSuccess) e = launch_attn(D, b, l, ctx->qkv, ctx->part, ctx->tickets, ctx->attn_out, s);
+    if (e == cudaSuccess) e = launch_attn(D, b, l, ctx->qkv, ctx->attn_out, s);
     if (e == cudaSuccess) e = m.mark(s, TK_ATTN);
     if (e == cudaSuccess) {
       io = GemvIO{};
@@ -825,7 +771,7 @@ static cudaError_t launch_model_tc(nc_ctx* ctx, const Batch& b, StepMarks& m) {
     e = launch_act_rmsnorm(D, b, ctx->x, L.g_attn, D.d, kb, ctx->opnd, ctx->opnd_scale, s);
     if (e == cudaSuccess) e = gemm(T[0], EPI_STORE, ctx->qkv, nullptr);
     if (e == cudaSuccess) e = m.mark(s, TK_QKV);
-    if (e == cudaSuccess) e = launch_attn(D, b, l, ctx->qkv, ctx->part, ctx->tickets, ctx->attn_out, s);
+    if (e == cudaSuccess) e = launch_attn(D, b, l, ctx->qkv, ctx->attn_out, s);
     if (e == cudaSuccess) e = m.mark(s, TK_ATTN);
     if (e == cudaSuccess) e = launch_act_plain(D, b, ctx->attn_out, D.hq * kHeadDim, kb, ctx->opnd, ctx->opnd_scale, s);
     if (e == cudaSuccess) e = gemm(T[1], EPI_RESID, ctx->x, nullptr);
@@ -859,7 +805,7 @@ static void step_bytes(const nc_ctx* ctx, int B, int n_ctx, double* out) {
   out[TK_EMBED] = B * D.d * (esz + 4);
   out[TK_QKV] = gemv(D.qkv_rows, D.d, D.qkv_rows, false) + B * D.d * 4;
   out[TK_ATTN] = B * (D.hkv * ((n_ctx - 1) * 2.0 * kHeadDim * kvsz + 2.0 * kHeadDim * kvsz) +
-                      D.qkv_rows * 4.0 + D.hq * (kHeadDim + 2.0) * 4.0 * ((n_ctx + kAttnChunk - 1) / kAttnChunk));
+                      D.qkv_rows * 4.0 + D.hq * kHeadDim * 4.0);
   out[TK_O] = gemv(D.d, qd, D.d, true);
   out[TK_GU] = gemv(2.0 * D.F, D.d, D.F, false);
   out[TK_DOWN] = gemv(D.d, D.F, D.d, true);
@@ -897,15 +843,6 @@ static int stage_batch(nc_ctx* ctx, int n, const int32_t* ids, std::vector<int>*
 // context-wide word of the tensor-core GEMMs).
 static int check_status(nc_ctx* ctx, const std::vector<int>& slot_idx) {
   const size_t off = offsetof(StreamDev, status);
-  {
-    int32_t w = 0;
-    NC_TRY(cudaMemcpyAsync(&w, ctx->step_err, 4, cudaMemcpyDeviceToHost, ctx->stream));
-    NC_TRY(cudaStreamSynchronize(ctx->stream));
-    if (w) {
-      ctx->poisoned = true;
-      return fail(ctx, NC_ETIMEOUT, "a grid barrier of the persistent step gave up");
-    }
-  }
   if (ctx->cfg.path == NC_PATH_TC) {
     int32_t w = 0;
     NC_TRY(cudaMemcpyAsync(&w, ctx->d_status, 4, cudaMemcpyDeviceToHost, ctx->stream));
@@ -1063,17 +1000,11 @@ static int encode_device(nc_ctx* ctx, int n, const std::vector<int>& slot_of, co
     mk.ev.resize(12 + 5 * D.n_layers);
     for (auto& e : mk.ev) NC_TRY(cudaEventCreate(&e));
   }
-  const EncodeRows rows{tok_dev, offs_dev, lens_dev};
   auto one_step = [&]() -> cudaError_t {
     cudaError_t e = mk.begin(s);
-    if (ctx->use_step) {
-      if (e == cudaSuccess) e = launch_step(D, b, ctx->fmt, step_args(ctx, &rows), s);
-      if (e == cudaSuccess) e = mk.mark(s, TK_STEP);
-    } else {
-      if (e == cudaSuccess) e = launch_prepare_encode(b, n, tok_dev, offs_dev, lens_dev, ctx->d_obs, ctx->d_nB, s);
-      if (e == cudaSuccess) e = mk.mark(s, TK_PREPARE);
-      if (e == cudaSuccess) e = launch_model(ctx, b, &mk);
-    }
+    if (e == cudaSuccess) e = launch_prepare_encode(b, n, tok_dev, offs_dev, lens_dev, ctx->d_obs, ctx->d_nB, s);
+    if (e == cudaSuccess) e = mk.mark(s, TK_PREPARE);
+    if (e == cudaSuccess) e = launch_model(ctx, b, &mk);
     if (e == cudaSuccess) e = launch_vocab(D, b, io, s);
     if (e == cudaSuccess) e = mk.mark(s, TK_VOCAB);
     if (e == cudaSuccess) e = launch_ngram_update(D, b, s);

@@ -11,7 +11,6 @@ namespace nc {
 constexpr int kHeadDim = 64;           // d_head of the supported models (Sec. 3.2)
 constexpr int kMaxSlots = 64;          // continuation slots per N-gram context (Sec. 3.4)
 constexpr int kMaxOrder = 3;           // N-gram context lengths 1..3
-constexpr int kAttnChunk = 128;        // KV positions per attention CTA
 constexpr int kMaxGroup = 4;           // query heads per KV head supported
 constexpr int kVocabCluster = 8;       // CTAs per stream in the vocabulary kernel
 constexpr int kVocabThreads = 512;
@@ -126,11 +125,6 @@ inline cudaError_t launch_kernel(void (*kern)(KArgs...), dim3 grid, dim3 block, 
   return cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
 }
 
-// Largest number of attention chunks (split-KV CTAs) of one (stream, KV head).
-__host__ __device__ inline int attn_splits_max_dev(const Dims& D) {
-  return (D.L + kAttnChunk - 1) / kAttnChunk;
-}
-
 // ------------------------------------------------------------------ kernels
 enum Prologue { PRO_RMSNORM = 0, PRO_PLAIN = 2 };
 enum Epilogue { EPI_STORE = 0, EPI_RESID = 1, EPI_SWIGLU = 2, EPI_LOGITS = 3 };
@@ -145,11 +139,10 @@ cudaError_t launch_embed(const Dims& D, const Batch& b, const void* E, const flo
                          int fmt, float* x, cudaStream_t s);
 cudaError_t launch_gemv(const Dims& D, const Batch& b, const Mat& m, int fmt, int pro, int epi,
                         const GemvIO& io, cudaStream_t s);
-// Split-KV attention; the last chunk of each (row, KV head) merges the
-// partials into attn_out [Bmax][hq * 64].  tickets: int [Bmax][hkv], zero.
-cudaError_t launch_attn(const Dims& D, const Batch& b, int layer, const float* qkv, float* part, int* tickets,
-                        float* attn_out, cudaStream_t s);
-int attn_max_splits(const Dims& D);
+// Decode attention (one cluster per row and KV head) into attn_out
+// [Bmax][hq * 64].
+cudaError_t launch_attn(const Dims& D, const Batch& b, int layer, const float* qkv, float* attn_out,
+                        cudaStream_t s);
 
 struct VocabIO {
   uint32_t* cdf;            // [Bmax][V+1] or nullptr
@@ -198,38 +191,11 @@ cudaError_t launch_act_rmsnorm(const Dims& D, const Batch& b, const float* x, co
 cudaError_t launch_act_plain(const Dims& D, const Batch& b, const float* x, int cols, int kind_bf16, void* out,
                              float* out_scale, cudaStream_t s);
 
-// Persistent step kernel (k_step.cu): the model forward of up to 8 rows in
-// one cooperative launch.
-struct StepArgs {
-  const void* embed;
-  const float* embed_scale;
-  const LayerW* layers;     // device array [n_layers]
-  const float* g_final;
-  float* x;
-  float* qkv;
-  float* part;
-  int* tickets;
-  float* attn_out;
-  float* h;
-  unsigned* bar;            // grid-barrier arrival counter (reset per launch)
-  int* err;                 // ST_TIMEOUT when a barrier gave up
-  int encode;               // 1: rows active while tokens are left (tok_flat / offs / lens)
-  const int32_t* tok_flat;
-  const int64_t* offs;
-  const int64_t* lens;
-  int32_t* obs;
-  int32_t* nB_out;
-};
-size_t step_smem_bytes(const Dims& D);
-bool step_supported(const Dims& D, int Bmax);
-cudaError_t launch_step(const Dims& D, const Batch& b, int fmt, const StepArgs& A, cudaStream_t s);
-
 // Kernel attributes (dynamic shared memory limits) set once, outside any
 // stream capture.
 cudaError_t prepare_model_kernels(const Dims& D, int fmt);
 cudaError_t prepare_vocab_kernels(const Dims& D);
 cudaError_t prepare_tc_kernels();
-cudaError_t prepare_step_kernel(const Dims& D, int fmt);
 
 cudaError_t launch_probs_to_cdf(const float* p, int n, int V, int log2T, uint32_t floor,
                                 uint32_t* cdf, int32_t* status, cudaStream_t s);

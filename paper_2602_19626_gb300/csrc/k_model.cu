@@ -8,7 +8,11 @@
 // whether it runs alone or in a batch.
 #include <algorithm>
 
+#include <cooperative_groups.h>
+
 #include "model_dev.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace nc {
 
@@ -16,7 +20,7 @@ namespace {
 
 using namespace dev;
 
-constexpr int kGemvThreads = 256;
+constexpr int kGemvThreads = 128;
 constexpr int kGemvWarps = kGemvThreads / 32;
 
 // ----------------------------------------------------------------- embedding
@@ -64,24 +68,54 @@ __global__ void __launch_bounds__(kGemvThreads) k_gemv(Dims D, Batch b, Mat m, G
 }
 
 // ----------------------------------------------------------------- attention
-// One split-KV unit per CTA (attn_preload / attn_compute); loads that do not
-// depend on the QKV projection are issued before waiting on it.
+// One cluster of kAttnCtas CTAs per (stream row, KV head); CTA `rank` takes
+// chunk `rank` of the window.  Loads that do not depend on the QKV
+// projection are issued before waiting on it.  After the CTAs combined their
+// warps, every CTA merges the outputs of 8 of the 64 head dimensions over
+// the cluster's CTAs in rank order, through distributed shared memory.
 template <int KBF16>
-__global__ void __launch_bounds__(128) k_attn(Dims D, Batch b, int layer, AttnIO io) {
-  const int j = blockIdx.z;
-  if (j >= *b.nB) return;
+__global__ void __cluster_dims__(kAttnCtas, 1, 1) __launch_bounds__(kAttnThreads)
+    k_attn(Dims D, Batch b, int layer, AttnIO io) {
+  cg::cluster_group cl = cg::this_cluster();
+  const int rank = (int)cl.block_rank();
+  const int j = blockIdx.z, g = blockIdx.y;
+  if (j >= *b.nB) return;                          // uniform across the cluster
   StreamDev& st = b.st[b.slots[j]];
-  const int g = blockIdx.y, s = blockIdx.x;
   const int a = st.n_coded;
   const int start = window_start(D, st);
-  const int ns = (a - start + 1 + kAttnChunk - 1) / kAttnChunk;
-  if (s >= ns) return;
+  const int chunk = attn_chunk(a - start + 1);
+  const int c_lo = start + rank * chunk;
+  const int c_end = min(c_lo + chunk, a + 1);      // may be empty (c_end <= c_lo)
+  const int tid = threadIdx.x, warp = tid >> 5;
   __shared__ AttnSmem sm;
   AttnPre<KBF16> pre;
-  attn_preload<KBF16>(D, st, layer, g, s, start, a, threadIdx.x, sm, pre);
+  attn_preload<KBF16>(D, st, layer, g, c_lo + warp * 32, c_end, a, tid, sm, pre);
   pdl_wait();
   pdl_trigger();
-  attn_compute<KBF16>(D, st, layer, j, g, s, start, a, ns, threadIdx.x, sm, pre, io, [] { __syncthreads(); });
+  attn_compute<KBF16>(D, st, layer, j, g, c_lo, c_end, a, tid, sm, pre, io);
+  cl.sync();
+  const int grp = D.hq / D.hkv;
+  constexpr int kDims = kHeadDim / kAttnCtas;       // output dims merged by this CTA
+  for (int e = tid; e < grp * kDims; e += kAttnThreads) {
+    const int h = e / kDims, dd = rank * kDims + e % kDims;
+    float M = -INFINITY;
+    for (int q = 0; q < kAttnCtas; ++q) {
+      const int lo = start + q * chunk;
+      if (lo <= a) M = fmaxf(M, cl.map_shared_rank(&sm, q)->cm[h]);
+    }
+    float l = 0.f, o = 0.f;
+    for (int q = 0; q < kAttnCtas; ++q) {
+      const int lo = start + q * chunk;
+      if (lo <= a) {
+        const AttnSmem* r = cl.map_shared_rank(&sm, q);
+        const float f = expf(r->cm[h] - M);
+        l = fmaf(r->cl[h], f, l);
+        o = fmaf(r->cacc[h][dd], f, o);
+      }
+    }
+    io.attn_out[(size_t)j * D.hq * kHeadDim + (g * grp + h) * kHeadDim + dd] = o / l;
+  }
+  cl.sync();                                       // keep shared memory alive for the readers
 }
 
 // ------------------------------------------------------------ weight formats
@@ -127,7 +161,6 @@ __global__ void k_interleave(const float* gate, const float* up, float* dst, int
 
 }  // namespace
 
-int attn_max_splits(const Dims& D) { return (D.L + kAttnChunk - 1) / kAttnChunk; }
 
 cudaError_t launch_embed(const Dims& D, const Batch& b, const void* E, const float* Escale,
                          int fmt, float* x, cudaStream_t s) {
@@ -202,7 +235,6 @@ cudaError_t prepare_model_kernels(const Dims& D, int fmt) {
   cudaError_t e = fmt == NC_FP32 ? prepare_gemv_f<NC_FP32>(cmax)
                   : fmt == NC_BF16 ? prepare_gemv_f<NC_BF16>(cmax)
                                    : prepare_gemv_f<NC_FP8E4M3>(cmax);
-  if (e == cudaSuccess && step_supported(D, 1)) e = prepare_step_kernel(D, fmt);
   return e;
 }
 
@@ -213,11 +245,11 @@ cudaError_t launch_gemv(const Dims& D, const Batch& b, const Mat& m, int fmt, in
   return gemv_f<NC_FP8E4M3>(D, b, m, pro, epi, io, s);
 }
 
-cudaError_t launch_attn(const Dims& D, const Batch& b, int layer, const float* qkv, float* part, int* tickets,
-                        float* attn_out, cudaStream_t s) {
-  dim3 grid(attn_max_splits(D), D.hkv, b.Bmax);
-  AttnIO io{qkv, part, tickets, attn_out};
-  return launch_kernel(D.kv_bf16 ? k_attn<1> : k_attn<0>, grid, dim3(128), 0, s, D.pdl, D, b, layer, io);
+cudaError_t launch_attn(const Dims& D, const Batch& b, int layer, const float* qkv, float* attn_out,
+                        cudaStream_t s) {
+  dim3 grid(kAttnCtas, D.hkv, b.Bmax);
+  AttnIO io{qkv, attn_out};
+  return launch_kernel(D.kv_bf16 ? k_attn<1> : k_attn<0>, grid, dim3(kAttnThreads), 0, s, D.pdl, D, b, layer, io);
 }
 
 cudaError_t launch_convert_weights(const float* src, void* dst, float* scale, int64_t rows,

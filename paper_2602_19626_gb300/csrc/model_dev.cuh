@@ -118,11 +118,14 @@ template <bool RMS, typename Src, typename Sync>
 __device__ void prologue(const Dims& D, Src src, const float* gain, int cols, int b0, int nb, float* xs,
                          ProScratch& ps, int tid, int nthreads, Sync sync) {
   if (RMS) {
-    if (tid < kRed) {
-      const int lane = tid & 31, w = tid >> 5;
+    // virtual thread vt (0..255) sums columns vt, vt + 256, ...; a block of
+    // fewer threads runs several virtual threads per thread (nthreads is a
+    // multiple of 32, so a real warp always holds one virtual warp)
+    for (int vt = tid; vt < kRed; vt += nthreads) {
+      const int lane = vt & 31, w = vt >> 5;
       for (int bt = 0; bt < nb; ++bt) {
         float ss = 0.f;
-        for (int c = tid; c < cols; c += kRed) {
+        for (int c = vt; c < cols; c += kRed) {
           const float v = src(b0 + bt, c);
           ss = fmaf(v, v, ss);
         }
@@ -285,34 +288,44 @@ __device__ __forceinline__ void gemv_rowpair(const Mat& m, int rp, const float* 
 }
 
 // ----------------------------------------------------------------- attention
-// One unit of split-KV decode attention: stream row j, KV head g, chunk s of
-// <= kAttnChunk cached positions, computed by 128 threads (4 warps of 32
-// positions).  The fed token's q and k are rotated (rotate-half RoPE) at its
-// absolute position a; cached keys were rotated at their own absolute
-// positions when appended.  Scores depend only on position differences, so
-// this equals the relabelled positions of the sliding window (Sec. 3.9).
-// The last chunk appends the new k, v at ring index a mod L.  Each chunk
-// writes its running max m, sum l and unnormalised accumulator; the chunk
-// that finishes last (atomic ticket) merges all chunks of (j, g) in chunk
-// order into attn_out, so the result does not depend on the finishing order.
+// Decode attention of one (stream row j, KV head g) by a cluster of
+// kAttnCtas CTAs of kAttnThreads threads.  The window [start, a] (a = the fed
+// token's absolute position) is cut into kAttnCtas chunks of `chunk`
+// positions (a multiple of 32, a function of the window length only), one
+// per CTA, 32 positions per warp.  The fed token's q and k are rotated
+// (rotate-half RoPE) at position a; cached keys were rotated at their own
+// absolute positions when appended.  Scores depend only on position
+// differences, so this equals the relabelled positions of the sliding window
+// (Sec. 3.9).  The CTA holding position a appends the new k, v at ring
+// index a mod L.  Each CTA combines its warps in shared memory; the cluster
+// merges the CTAs' (max, sum, accumulator) through distributed shared
+// memory in rank order.
+constexpr int kAttnCtas = 8;
+constexpr int kAttnThreads = 256;
+constexpr int kAttnWarps = kAttnThreads / 32;
+
 struct AttnSmem {
   float qs[kMaxGroup][kHeadDim];
   float kn[kHeadDim], vn[kHeadDim];
   float cs[kHeadDim / 2], sn[kHeadDim / 2];
-  float wm[4][kMaxGroup], wl[4][kMaxGroup];
-  float wacc[4][kMaxGroup][kHeadDim];
-  int last;
+  float wm[kAttnWarps][kMaxGroup], wl[kAttnWarps][kMaxGroup];
+  float wacc[kAttnWarps][kMaxGroup][kHeadDim];
+  // this CTA's combined partial, read by the cluster
+  float cm[kMaxGroup], cl[kMaxGroup];
+  float cacc[kMaxGroup][kHeadDim];
 };
 
 struct AttnIO {
   const float* qkv;      // [B][qkv_rows], written by the QKV projection
-  float* part;           // [B][hq][nsm][66]
-  int* tickets;          // [B][hkv]
   float* attn_out;       // [B][hq * 64]
 };
 
-// Values of the unit that do not depend on the QKV projection: the cached
-// key of this lane's position and the values of its warp's 32 positions.
+__device__ __forceinline__ int attn_chunk(int n) {
+  return (((n + kAttnCtas - 1) / kAttnCtas) + 31) / 32 * 32;
+}
+
+// Values of a lane that do not depend on the QKV projection: the cached key
+// of its position and the values of its warp's 32 positions.
 template <int KBF16>
 struct AttnPre {
   float kr[kHeadDim];
@@ -321,9 +334,9 @@ struct AttnPre {
 };
 
 template <int KBF16>
-__device__ __forceinline__ void attn_preload(const Dims& D, const StreamDev& st, int layer, int g, int s,
-                                             int start, int a, int tid, AttnSmem& sm, AttnPre<KBF16>& pre) {
-  const int warp = tid >> 5, lane = tid & 31;
+__device__ __forceinline__ void attn_preload(const Dims& D, const StreamDev& st, int layer, int g, int p_lo,
+                                             int p_end, int a, int tid, AttnSmem& sm, AttnPre<KBF16>& pre) {
+  const int lane = tid & 31;
   if (tid < kHeadDim / 2) {
     // rotation of position a: product of the three table rotations
     const float2 t1 = D.rope_tab[(0 * 256 + (a & 255)) * 32 + tid];
@@ -337,9 +350,8 @@ __device__ __forceinline__ void attn_preload(const Dims& D, const StreamDev& st,
   const size_t layer_off = (size_t)layer * 2 * D.hkv * plane;
   const size_t koff = layer_off + (size_t)g * plane;
   const size_t voff = layer_off + (size_t)(D.hkv + g) * plane;
-  const int p_lo = start + s * kAttnChunk + warp * 32;
   const int p = p_lo + lane;
-  if (p < a) {
+  if (p < p_end && p < a) {
     const size_t ri = (size_t)(p & (D.L - 1)) * kHeadDim;
     if (KBF16) {
       const uint4* src = reinterpret_cast<const uint4*>(static_cast<const __nv_bfloat16*>(st.kv) + koff + ri);
@@ -365,7 +377,7 @@ __device__ __forceinline__ void attn_preload(const Dims& D, const StreamDev& st,
       }
     }
   }
-  const int nvalid = min(32, a - p_lo + 1);
+  const int nvalid = min(32, min(p_end, a + 1) - p_lo);
 #pragma unroll
   for (int i = 0; i < 32; ++i) {
     const int pi = p_lo + i;
@@ -379,34 +391,16 @@ __device__ __forceinline__ void attn_preload(const Dims& D, const StreamDev& st,
   }
 }
 
-// L2 prefetch of the cached keys and values a unit will read (no registers).
-__device__ __forceinline__ void attn_prefetch(const Dims& D, const StreamDev& st, int layer, int g, int s,
-                                              int start, int a, int tid) {
-  const int warp = tid >> 5, lane = tid & 31;
-  const size_t plane = (size_t)D.L * kHeadDim;
-  const size_t layer_off = (size_t)layer * 2 * D.hkv * plane;
-  const size_t esz = D.kv_bf16 ? 2 : 4;
-  const int p = start + s * kAttnChunk + warp * 32 + lane;
-  if (p >= start && p < a && layer >= 0 && layer < D.n_layers && g >= 0 && g < D.hkv) {
-    const char* base = static_cast<const char*>(st.kv);
-    const size_t ri = (size_t)(p & (D.L - 1)) * kHeadDim;
-    for (int part = 0; part < (int)(kHeadDim * esz / 128); ++part) {
-      asm volatile("prefetch.global.L2 [%0];" ::"l"(base + (layer_off + (size_t)g * plane + ri) * esz + 128 * part));
-      asm volatile("prefetch.global.L2 [%0];" ::"l"(base + (layer_off + (size_t)(D.hkv + g) * plane + ri) * esz + 128 * part));
-    }
-  }
-}
-
-// The unit's work once the QKV projection is complete.  `sync` synchronises
-// the unit's 128 threads.
-template <int KBF16, typename Sync>
-__device__ void attn_compute(const Dims& D, StreamDev& st, int layer, int j, int g, int s, int start, int a,
-                             int ns, int tid, AttnSmem& sm, AttnPre<KBF16>& pre, const AttnIO& io, Sync sync) {
+// The CTA's part once the QKV projection is complete: scores and values of
+// its positions, combined over its warps into sm.cm / sm.cl / sm.cacc.
+template <int KBF16>
+__device__ void attn_compute(const Dims& D, StreamDev& st, int layer, int j, int g, int c_lo, int c_end, int a,
+                             int tid, AttnSmem& sm, AttnPre<KBF16>& pre, const AttnIO& io) {
   const int grp = D.hq / D.hkv;
   const int warp = tid >> 5, lane = tid & 31;
-  sync();
+  __syncthreads();
   const float* row = io.qkv + (size_t)j * D.qkv_rows;
-  for (int e = tid; e < (grp + 1) * (kHeadDim / 2); e += 128) {
+  for (int e = tid; e < (grp + 1) * (kHeadDim / 2); e += kAttnThreads) {
     const int h = e / (kHeadDim / 2), dd = e % (kHeadDim / 2);
     const float* src = h < grp ? row + (g * grp + h) * kHeadDim : row + D.hq * kHeadDim + g * kHeadDim;
     const float x1 = __ldcg(src + dd), x2 = __ldcg(src + dd + kHeadDim / 2);
@@ -421,13 +415,13 @@ __device__ void attn_compute(const Dims& D, StreamDev& st, int layer, int j, int
     }
   }
   if (tid < kHeadDim) sm.vn[tid] = __ldcg(row + (D.hq + D.hkv) * kHeadDim + g * kHeadDim + tid);
-  sync();
+  __syncthreads();
 
   const size_t plane = (size_t)D.L * kHeadDim;
   const size_t layer_off = (size_t)layer * 2 * D.hkv * plane;
   const size_t koff = layer_off + (size_t)g * plane;
   const size_t voff = layer_off + (size_t)(D.hkv + g) * plane;
-  if (s == ns - 1 && tid < kHeadDim) {
+  if (a >= c_lo && a < c_end && tid < kHeadDim) {
     const size_t ri = (size_t)(a & (D.L - 1)) * kHeadDim + tid;
     if (KBF16) {
       __nv_bfloat16* kv = static_cast<__nv_bfloat16*>(st.kv);
@@ -440,9 +434,10 @@ __device__ void attn_compute(const Dims& D, StreamDev& st, int layer, int j, int
     }
   }
 
-  const int p_lo = start + s * kAttnChunk + warp * 32;
+  const int p_lo = c_lo + warp * 32;
   const int p = p_lo + lane;
-  const bool valid = p <= a;
+  const bool valid = p < c_end && p <= a;
+  const int nvalid = min(32, min(c_end, a + 1) - p_lo);
   float sc[kMaxGroup];
 #pragma unroll
   for (int h = 0; h < kMaxGroup; ++h) sc[h] = 0.f;
@@ -474,7 +469,6 @@ __device__ void attn_compute(const Dims& D, StreamDev& st, int layer, int j, int
   float acc[kMaxGroup][2];
 #pragma unroll
   for (int h = 0; h < kMaxGroup; ++h) acc[h][0] = acc[h][1] = 0.f;
-  const int nvalid = min(32, a - p_lo + 1);
 #pragma unroll
   for (int i = 0; i < 32; ++i) {
     if (i >= nvalid) break;
@@ -510,76 +504,26 @@ __device__ void attn_compute(const Dims& D, StreamDev& st, int layer, int j, int
       sm.wacc[warp][h][2 * lane + 1] = acc[h][1];
     }
   }
-  sync();
-  const int nsm = attn_splits_max_dev(D);
-  for (int e = tid; e < grp * kHeadDim; e += 128) {
+  __syncthreads();
+  // combine the warps in warp order (warps without positions are skipped)
+  for (int e = tid; e < grp * kHeadDim; e += kAttnThreads) {
     const int h = e / kHeadDim, dd = e % kHeadDim;
     float M = -INFINITY;
-    for (int w = 0; w < 4; ++w)
-      if (start + s * kAttnChunk + w * 32 <= a) M = fmaxf(M, sm.wm[w][h]);
+    for (int w = 0; w < kAttnWarps; ++w)
+      if (c_lo + w * 32 < c_end && c_lo + w * 32 <= a) M = fmaxf(M, sm.wm[w][h]);
     float l = 0.f, o = 0.f;
-    for (int w = 0; w < 4; ++w) {
-      if (start + s * kAttnChunk + w * 32 <= a) {
+    for (int w = 0; w < kAttnWarps; ++w) {
+      if (c_lo + w * 32 < c_end && c_lo + w * 32 <= a) {
         const float f = expf(sm.wm[w][h] - M);
         l = fmaf(sm.wl[w][h], f, l);
         o = fmaf(sm.wacc[w][h][dd], f, o);
       }
     }
-    float* out = io.part + (((size_t)j * D.hq + g * grp + h) * nsm + s) * (kHeadDim + 2);
-    out[dd] = o;
+    sm.cacc[h][dd] = o;
     if (dd == 0) {
-      out[kHeadDim] = M;
-      out[kHeadDim + 1] = l;
+      sm.cm[h] = M;
+      sm.cl[h] = l;
     }
-  }
-  __threadfence();
-  sync();
-  if (tid == 0) {
-    const int t = atomicAdd(io.tickets + j * D.hkv + g, 1);
-    sm.last = (t == ns - 1);
-    if (sm.last) io.tickets[j * D.hkv + g] = 0;
-  }
-  sync();
-  if (!sm.last) return;
-  __threadfence();
-  constexpr int kUnrolled = 16;                   // chunks merged from registers
-  for (int e = tid; e < grp * kHeadDim; e += 128) {
-    const int h = e / kHeadDim, dd = e % kHeadDim;
-    const float* ph = io.part + ((size_t)j * D.hq + g * grp + h) * nsm * (kHeadDim + 2);
-    float M = -INFINITY, l = 0.f, o = 0.f;
-    if (ns <= kUnrolled) {
-      // issue every load first (one round trip), then merge in chunk order
-      float mv[kUnrolled], lv[kUnrolled], av[kUnrolled];
-#pragma unroll
-      for (int q = 0; q < kUnrolled; ++q) {
-        if (q < ns) {
-          const float* pq = ph + q * (kHeadDim + 2);
-          mv[q] = __ldcg(pq + kHeadDim);
-          lv[q] = __ldcg(pq + kHeadDim + 1);
-          av[q] = __ldcg(pq + dd);
-        }
-      }
-#pragma unroll
-      for (int q = 0; q < kUnrolled; ++q)
-        if (q < ns) M = fmaxf(M, mv[q]);
-#pragma unroll
-      for (int q = 0; q < kUnrolled; ++q) {
-        if (q < ns) {
-          const float f = expf(mv[q] - M);
-          l = fmaf(lv[q], f, l);
-          o = fmaf(av[q], f, o);
-        }
-      }
-    } else {
-      for (int q = 0; q < ns; ++q) M = fmaxf(M, __ldcg(ph + q * (kHeadDim + 2) + kHeadDim));
-      for (int q = 0; q < ns; ++q) {
-        const float* pq = ph + q * (kHeadDim + 2);
-        const float f = expf(__ldcg(pq + kHeadDim) - M);
-        l = fmaf(__ldcg(pq + kHeadDim + 1), f, l);
-        o = fmaf(__ldcg(pq + dd), f, o);
-      }
-    }
-    io.attn_out[(size_t)j * D.hq * kHeadDim + (g * grp + h) * kHeadDim + dd] = o / l;
   }
 }
 
