@@ -212,7 +212,7 @@ def kernel_sources_hash() -> str:
     d = os.path.join(ROOT, "paper_2602_19626_gb300", "csrc")
     m = hashlib.sha256()
     for name in sorted(os.listdir(d)):
-        if name.endswith((".cu", ".h")):
+        if name.endswith((".cu", ".cuh", ".h", ".cpp")):
             with open(os.path.join(d, name), "rb") as fh:
                 m.update(fh.read())
     return m.hexdigest()[:12]

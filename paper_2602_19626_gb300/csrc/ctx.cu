@@ -429,6 +429,19 @@ extern "C" int nc_ctx_create(const nc_config* cfg, const void* weights, size_t n
   D.theta = c.rope_theta;
   D.tau = c.temperature;
   D.kv_bf16 = c.weight_fmt != NC_FP32;
+  {
+    // Attention CTAs per (stream, KV head): the largest of 8, 4, 2, 1 that
+    // keeps the launch within about two waves of two CTAs per SM; results
+    // do not depend on it.  NC24_ATTN_CLUSTER=1|2|4|8 overrides.
+    int nsm = 0;
+    if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c.device) != cudaSuccess || nsm <= 0)
+      return bail(NC_ECUDA);
+    int S = 8;
+    while (S > 1 && (int64_t)c.n_kv_heads * c.max_streams * S > 4 * (int64_t)nsm) S /= 2;
+    const char* e = std::getenv("NC24_ATTN_CLUSTER");
+    if (e && (e[0] == '1' || e[0] == '2' || e[0] == '4' || e[0] == '8') && e[1] == 0) S = e[0] - '0';
+    D.attn_cluster = S;
+  }
   D.order = c.ngram_order;
   D.use_head = c.use_head;
   D.warmup = c.warmup;

@@ -68,54 +68,66 @@ __global__ void __launch_bounds__(kGemvThreads) k_gemv(Dims D, Batch b, Mat m, G
 }
 
 // ----------------------------------------------------------------- attention
-// One cluster of kAttnCtas CTAs per (stream row, KV head); CTA `rank` takes
-// chunk `rank` of the window.  Loads that do not depend on the QKV
-// projection are issued before waiting on it.  After the CTAs combined their
-// warps, every CTA merges the outputs of 8 of the 64 head dimensions over
-// the cluster's CTAs in rank order, through distributed shared memory.
-template <int KBF16>
-__global__ void __cluster_dims__(kAttnCtas, 1, 1) __launch_bounds__(kAttnThreads)
-    k_attn(Dims D, Batch b, int layer, AttnIO io) {
-  cg::cluster_group cl = cg::this_cluster();
-  const int rank = (int)cl.block_rank();
+// One cluster of S CTAs per (stream row, KV head).  CTA `rank` owns chunks
+// rank, rank + S, ...; the loads of its first chunk do not depend on the
+// QKV projection and are issued before waiting on it.  The owner of a chunk
+// stores its (max, sum) and each CTA's 64 / S accumulator dims into that
+// CTA's shared memory; after one cluster barrier every CTA merges its dims
+// over all chunks in chunk order from local shared memory.
+template <int KBF16, int S>
+__global__ void __launch_bounds__(kAttnThreads) k_attn(Dims D, Batch b, int layer, AttnIO io) {
+  const int rank = S > 1 ? (int)cg::this_cluster().block_rank() : 0;
   const int j = blockIdx.z, g = blockIdx.y;
   if (j >= *b.nB) return;                          // uniform across the cluster
   StreamDev& st = b.st[b.slots[j]];
   const int a = st.n_coded;
   const int start = window_start(D, st);
-  const int chunk = attn_chunk(a - start + 1);
-  const int c_lo = start + rank * chunk;
-  const int c_end = min(c_lo + chunk, a + 1);      // may be empty (c_end <= c_lo)
-  const int tid = threadIdx.x, warp = tid >> 5;
-  __shared__ AttnSmem sm;
+  const int nc = (a - start) / kAttnChunk + 1;     // the last chunk holds position a
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  __shared__ AttnSmem<S> sm;
+  // every CTA of the cluster must have started before shared memory is
+  // written remotely: arrive now, wait before the first remote store
+  if (S > 1) asm volatile("barrier.cluster.arrive.relaxed.aligned;" ::: "memory");
   AttnPre<KBF16> pre;
-  attn_preload<KBF16>(D, st, layer, g, c_lo + warp * 32, c_end, a, tid, sm, pre);
+  attn_rope(D, a, tid, sm);
+  if (rank < nc) {
+    const int c_lo = start + rank * kAttnChunk;
+    attn_load<KBF16>(D, st, layer, g, c_lo + warp * 32, min(c_lo + kAttnChunk, a + 1), a, lane, pre);
+  }
   pdl_wait();
   pdl_trigger();
-  attn_compute<KBF16>(D, st, layer, j, g, c_lo, c_end, a, tid, sm, pre, io);
-  cl.sync();
+  attn_qkv<KBF16>(D, st, layer, j, g, a, (nc - 1) % S == rank, tid, sm, io);
+  auto dst = [&](int r) -> AttnSmem<S>* {
+    if (S == 1) return &sm;
+    return cg::this_cluster().map_shared_rank(&sm, r);
+  };
+  if (S > 1) asm volatile("barrier.cluster.wait.aligned;" ::: "memory");
+  for (int c = rank; c < nc; c += S) {
+    const int c_lo = start + c * kAttnChunk;
+    const int c_end = min(c_lo + kAttnChunk, a + 1);
+    if (c != rank) attn_load<KBF16>(D, st, layer, g, c_lo + warp * 32, c_end, a, lane, pre);
+    attn_chunk<KBF16, S>(D, c, c_lo, c_end, a, tid, sm, pre, dst);
+  }
+  if (S > 1) cg::this_cluster().sync();            // every chunk's partial has arrived
   const int grp = D.hq / D.hkv;
-  constexpr int kDims = kHeadDim / kAttnCtas;       // output dims merged by this CTA
+  constexpr int kDims = AttnSmem<S>::kDims;
   for (int e = tid; e < grp * kDims; e += kAttnThreads) {
-    const int h = e / kDims, dd = rank * kDims + e % kDims;
+    const int h = e / kDims, dl = e % kDims;
     float M = -INFINITY;
-    for (int q = 0; q < kAttnCtas; ++q) {
-      const int lo = start + q * chunk;
-      if (lo <= a) M = fmaxf(M, cl.map_shared_rank(&sm, q)->cm[h]);
-    }
+#pragma unroll
+    for (int c = 0; c < kAttnMaxChunks; ++c)
+      if (c < nc) M = fmaxf(M, sm.rm[c][h]);
     float l = 0.f, o = 0.f;
-    for (int q = 0; q < kAttnCtas; ++q) {
-      const int lo = start + q * chunk;
-      if (lo <= a) {
-        const AttnSmem* r = cl.map_shared_rank(&sm, q);
-        const float f = expf(r->cm[h] - M);
-        l = fmaf(r->cl[h], f, l);
-        o = fmaf(r->cacc[h][dd], f, o);
+#pragma unroll
+    for (int c = 0; c < kAttnMaxChunks; ++c) {
+      if (c < nc) {
+        const float f = expf(sm.rm[c][h] - M);
+        l = fmaf(sm.rl[c][h], f, l);
+        o = fmaf(sm.racc[c][h][dl], f, o);
       }
     }
-    io.attn_out[(size_t)j * D.hq * kHeadDim + (g * grp + h) * kHeadDim + dd] = o / l;
+    io.attn_out[(size_t)j * D.hq * kHeadDim + (g * grp + h) * kHeadDim + rank * kDims + dl] = o / l;
   }
-  cl.sync();                                       // keep shared memory alive for the readers
 }
 
 // ------------------------------------------------------------ weight formats
@@ -247,9 +259,17 @@ cudaError_t launch_gemv(const Dims& D, const Batch& b, const Mat& m, int fmt, in
 
 cudaError_t launch_attn(const Dims& D, const Batch& b, int layer, const float* qkv, float* attn_out,
                         cudaStream_t s) {
-  dim3 grid(kAttnCtas, D.hkv, b.Bmax);
+  const int S = D.attn_cluster;
+  dim3 grid(S, D.hkv, b.Bmax);
   AttnIO io{qkv, attn_out};
-  return launch_kernel(D.kv_bf16 ? k_attn<1> : k_attn<0>, grid, dim3(kAttnThreads), 0, s, D.pdl, D, b, layer, io);
+  auto pick = [&](auto k1, auto k0) { return D.kv_bf16 ? k1 : k0; };
+  switch (S) {
+    case 1: return launch_kernel_cluster(pick(k_attn<1, 1>, k_attn<0, 1>), grid, dim3(kAttnThreads), 0, s, D.pdl, 1, D, b, layer, io);
+    case 2: return launch_kernel_cluster(pick(k_attn<1, 2>, k_attn<0, 2>), grid, dim3(kAttnThreads), 0, s, D.pdl, 2, D, b, layer, io);
+    case 4: return launch_kernel_cluster(pick(k_attn<1, 4>, k_attn<0, 4>), grid, dim3(kAttnThreads), 0, s, D.pdl, 4, D, b, layer, io);
+    case 8: return launch_kernel_cluster(pick(k_attn<1, 8>, k_attn<0, 8>), grid, dim3(kAttnThreads), 0, s, D.pdl, 8, D, b, layer, io);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 cudaError_t launch_convert_weights(const float* src, void* dst, float* scale, int64_t rows,

@@ -288,31 +288,39 @@ __device__ __forceinline__ void gemv_rowpair(const Mat& m, int rp, const float* 
 }
 
 // ----------------------------------------------------------------- attention
-// Decode attention of one (stream row j, KV head g) by a cluster of
-// kAttnCtas CTAs of kAttnThreads threads.  The window [start, a] (a = the fed
-// token's absolute position) is cut into kAttnCtas chunks of `chunk`
-// positions (a multiple of 32, a function of the window length only), one
-// per CTA, 32 positions per warp.  The fed token's q and k are rotated
-// (rotate-half RoPE) at position a; cached keys were rotated at their own
-// absolute positions when appended.  Scores depend only on position
-// differences, so this equals the relabelled positions of the sliding window
-// (Sec. 3.9).  The CTA holding position a appends the new k, v at ring
-// index a mod L.  Each CTA combines its warps in shared memory; the cluster
-// merges the CTAs' (max, sum, accumulator) through distributed shared
-// memory in rank order.
-constexpr int kAttnCtas = 8;
+// Decode attention of one (stream row j, KV head g).  The window [start, a]
+// (a = the fed token's absolute position) is cut into chunks of kAttnChunk
+// positions, chunk c = [start + c * 256, ...), and a chunk into 32-position
+// blocks, one per warp.  The arithmetic is fixed by the window alone:
+// scores, max and P V inside a block (warp shuffles in lane order), the
+// blocks of a chunk combined in block order, then the chunks in chunk order.
+// Which CTA computes which chunk is a launch choice that does not change a
+// bit: a cluster of S CTAs (S = 1, 2, 4 or 8) takes chunks c = rank,
+// rank + S, ..., keeps each chunk's (max, sum, accumulator) in its shared
+// memory, and the chunk merge reads them through distributed shared memory.
+//
+// The fed token's q and k are rotated (rotate-half RoPE) at position a;
+// cached keys were rotated at their own absolute positions when appended.
+// Scores depend only on position differences, so this equals the
+// relabelled positions of the sliding window (Sec. 3.9).  The CTA that owns
+// the chunk holding position a appends the new k, v at ring index a mod L.
 constexpr int kAttnThreads = 256;
 constexpr int kAttnWarps = kAttnThreads / 32;
+constexpr int kAttnChunk = kAttnWarps * 32;          // positions per chunk
+constexpr int kAttnMaxChunks = 2048 / kAttnChunk;    // ctx_len <= 2048
 
+template <int S>
 struct AttnSmem {
+  static constexpr int kDims = kHeadDim / S;         // output dims merged by one CTA
   float qs[kMaxGroup][kHeadDim];
   float kn[kHeadDim], vn[kHeadDim];
   float cs[kHeadDim / 2], sn[kHeadDim / 2];
   float wm[kAttnWarps][kMaxGroup], wl[kAttnWarps][kMaxGroup];
   float wacc[kAttnWarps][kMaxGroup][kHeadDim];
-  // this CTA's combined partial, read by the cluster
-  float cm[kMaxGroup], cl[kMaxGroup];
-  float cacc[kMaxGroup][kHeadDim];
+  // every chunk's (max, sum) and this CTA's dims of its accumulator, written
+  // by the chunk's owner (a remote store when the owner is another CTA)
+  float rm[kAttnMaxChunks][kMaxGroup], rl[kAttnMaxChunks][kMaxGroup];
+  float racc[kAttnMaxChunks][kMaxGroup][kDims];
 };
 
 struct AttnIO {
@@ -320,25 +328,21 @@ struct AttnIO {
   float* attn_out;       // [B][hq * 64]
 };
 
-__device__ __forceinline__ int attn_chunk(int n) {
-  return (((n + kAttnCtas - 1) / kAttnCtas) + 31) / 32 * 32;
-}
-
 // Values of a lane that do not depend on the QKV projection: the cached key
 // of its position and the values of its warp's 32 positions.
 template <int KBF16>
 struct AttnPre {
-  float kr[kHeadDim];
+  float kr[KBF16 ? 1 : kHeadDim];       // FP32 cache: the key
+  uint32_t kb[KBF16 ? kHeadDim / 2 : 1];  // BF16 cache: the key as packed pairs
   uint32_t vb[32];
   float2 vf[KBF16 ? 1 : 32];
 };
 
-template <int KBF16>
-__device__ __forceinline__ void attn_preload(const Dims& D, const StreamDev& st, int layer, int g, int p_lo,
-                                             int p_end, int a, int tid, AttnSmem& sm, AttnPre<KBF16>& pre) {
-  const int lane = tid & 31;
+// cos / sin of position a for the 32 rotation pairs: the product of the
+// three table rotations (a split into 8-bit digits).
+template <typename Sm>
+__device__ __forceinline__ void attn_rope(const Dims& D, int a, int tid, Sm& sm) {
   if (tid < kHeadDim / 2) {
-    // rotation of position a: product of the three table rotations
     const float2 t1 = D.rope_tab[(0 * 256 + (a & 255)) * 32 + tid];
     const float2 t2 = D.rope_tab[(1 * 256 + ((a >> 8) & 255)) * 32 + tid];
     const float2 t3 = D.rope_tab[(2 * 256 + ((a >> 16) & 255)) * 32 + tid];
@@ -346,10 +350,20 @@ __device__ __forceinline__ void attn_preload(const Dims& D, const StreamDev& st,
     sm.cs[tid] = c12 * t3.x - s12 * t3.y;
     sm.sn[tid] = c12 * t3.y + s12 * t3.x;
   }
+}
+
+__device__ __forceinline__ size_t attn_plane_off(const Dims& D, int layer, int which) {
   const size_t plane = (size_t)D.L * kHeadDim;
-  const size_t layer_off = (size_t)layer * 2 * D.hkv * plane;
-  const size_t koff = layer_off + (size_t)g * plane;
-  const size_t voff = layer_off + (size_t)(D.hkv + g) * plane;
+  return (size_t)layer * 2 * D.hkv * plane + (size_t)which * plane;
+}
+
+// Cached K of position p_lo + lane and V of positions p_lo .. p_lo + 31
+// (positions >= p_end and position a itself are not loaded).
+template <int KBF16>
+__device__ __forceinline__ void attn_load(const Dims& D, const StreamDev& st, int layer, int g, int p_lo,
+                                          int p_end, int a, int lane, AttnPre<KBF16>& pre) {
+  const size_t koff = attn_plane_off(D, layer, g);
+  const size_t voff = attn_plane_off(D, layer, D.hkv + g);
   const int p = p_lo + lane;
   if (p < p_end && p < a) {
     const size_t ri = (size_t)(p & (D.L - 1)) * kHeadDim;
@@ -358,12 +372,10 @@ __device__ __forceinline__ void attn_preload(const Dims& D, const StreamDev& st,
 #pragma unroll
       for (int q = 0; q < kHeadDim / 8; ++q) {
         const uint4 u = src[q];
-        const uint32_t w[4] = {u.x, u.y, u.z, u.w};
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-          pre.kr[8 * q + 2 * i] = __uint_as_float(w[i] << 16);
-          pre.kr[8 * q + 2 * i + 1] = __uint_as_float(w[i] & 0xFFFF0000u);
-        }
+        pre.kb[4 * q] = u.x;
+        pre.kb[4 * q + 1] = u.y;
+        pre.kb[4 * q + 2] = u.z;
+        pre.kb[4 * q + 3] = u.w;
       }
     } else {
       const float4* src = reinterpret_cast<const float4*>(static_cast<const float*>(st.kv) + koff + ri);
@@ -391,13 +403,13 @@ __device__ __forceinline__ void attn_preload(const Dims& D, const StreamDev& st,
   }
 }
 
-// The CTA's part once the QKV projection is complete: scores and values of
-// its positions, combined over its warps into sm.cm / sm.cl / sm.cacc.
-template <int KBF16>
-__device__ void attn_compute(const Dims& D, StreamDev& st, int layer, int j, int g, int c_lo, int c_end, int a,
-                             int tid, AttnSmem& sm, AttnPre<KBF16>& pre, const AttnIO& io) {
+// Once the QKV projection is complete: rotated, pre-scaled q of the group's
+// heads and the new k, v into shared memory; the owner of position a
+// appends k, v to the ring.
+template <int KBF16, typename Sm>
+__device__ void attn_qkv(const Dims& D, StreamDev& st, int layer, int j, int g, int a, bool append, int tid,
+                         Sm& sm, const AttnIO& io) {
   const int grp = D.hq / D.hkv;
-  const int warp = tid >> 5, lane = tid & 31;
   __syncthreads();
   const float* row = io.qkv + (size_t)j * D.qkv_rows;
   for (int e = tid; e < (grp + 1) * (kHeadDim / 2); e += kAttnThreads) {
@@ -416,13 +428,9 @@ __device__ void attn_compute(const Dims& D, StreamDev& st, int layer, int j, int
   }
   if (tid < kHeadDim) sm.vn[tid] = __ldcg(row + (D.hq + D.hkv) * kHeadDim + g * kHeadDim + tid);
   __syncthreads();
-
-  const size_t plane = (size_t)D.L * kHeadDim;
-  const size_t layer_off = (size_t)layer * 2 * D.hkv * plane;
-  const size_t koff = layer_off + (size_t)g * plane;
-  const size_t voff = layer_off + (size_t)(D.hkv + g) * plane;
-  if (a >= c_lo && a < c_end && tid < kHeadDim) {
+  if (append && tid < kHeadDim) {
     const size_t ri = (size_t)(a & (D.L - 1)) * kHeadDim + tid;
+    const size_t koff = attn_plane_off(D, layer, g), voff = attn_plane_off(D, layer, D.hkv + g);
     if (KBF16) {
       __nv_bfloat16* kv = static_cast<__nv_bfloat16*>(st.kv);
       kv[koff + ri] = __float2bfloat16_rn(sm.kn[tid]);
@@ -433,7 +441,16 @@ __device__ void attn_compute(const Dims& D, StreamDev& st, int layer, int j, int
       kv[voff + ri] = sm.vn[tid];
     }
   }
+}
 
+// One chunk [c_lo, c_end): scores and values of each warp's block, then the
+// blocks combined in block order into local chunk slot lc.
+// `dst(r)` is the shared memory of cluster rank r.
+template <int KBF16, int S, typename Dst>
+__device__ void attn_chunk(const Dims& D, int c, int c_lo, int c_end, int a, int tid, AttnSmem<S>& sm,
+                           AttnPre<KBF16>& pre, Dst dst) {
+  const int grp = D.hq / D.hkv;
+  const int warp = tid >> 5, lane = tid & 31;
   const int p_lo = c_lo + warp * 32;
   const int p = p_lo + lane;
   const bool valid = p < c_end && p <= a;
@@ -441,17 +458,32 @@ __device__ void attn_compute(const Dims& D, StreamDev& st, int layer, int j, int
   float sc[kMaxGroup];
 #pragma unroll
   for (int h = 0; h < kMaxGroup; ++h) sc[h] = 0.f;
-  if (valid) {
-    if (p == a) {
+  if (valid && p != a) {
 #pragma unroll
-      for (int d = 0; d < kHeadDim; ++d) pre.kr[d] = sm.kn[d];
+    for (int h = 0; h < kMaxGroup; ++h) {
+      if (h < grp) {
+        float acc = 0.f;
+        if (KBF16) {
+#pragma unroll
+          for (int i = 0; i < kHeadDim / 2; ++i) {
+            const uint32_t w = pre.kb[KBF16 ? i : 0];
+            acc = fmaf(sm.qs[h][2 * i], __uint_as_float(w << 16), acc);
+            acc = fmaf(sm.qs[h][2 * i + 1], __uint_as_float(w & 0xFFFF0000u), acc);
+          }
+        } else {
+#pragma unroll
+          for (int d = 0; d < kHeadDim; ++d) acc = fmaf(sm.qs[h][d], pre.kr[KBF16 ? 0 : d], acc);
+        }
+        sc[h] = acc;
+      }
     }
+  } else if (p == a) {   // the new key enters in FP32 from shared memory
 #pragma unroll
     for (int h = 0; h < kMaxGroup; ++h) {
       if (h < grp) {
         float acc = 0.f;
 #pragma unroll
-        for (int d = 0; d < kHeadDim; ++d) acc = fmaf(sm.qs[h][d], pre.kr[d], acc);
+        for (int d = 0; d < kHeadDim; ++d) acc = fmaf(sm.qs[h][d], sm.kn[d], acc);
         sc[h] = acc;
       }
     }
@@ -505,7 +537,7 @@ __device__ void attn_compute(const Dims& D, StreamDev& st, int layer, int j, int
     }
   }
   __syncthreads();
-  // combine the warps in warp order (warps without positions are skipped)
+  // combine the blocks in block order (blocks without positions are skipped)
   for (int e = tid; e < grp * kHeadDim; e += kAttnThreads) {
     const int h = e / kHeadDim, dd = e % kHeadDim;
     float M = -INFINITY;
@@ -519,12 +551,15 @@ __device__ void attn_compute(const Dims& D, StreamDev& st, int layer, int j, int
         o = fmaf(sm.wacc[w][h][dd], f, o);
       }
     }
-    sm.cacc[h][dd] = o;
-    if (dd == 0) {
-      sm.cm[h] = M;
-      sm.cl[h] = l;
+    constexpr int kDims = AttnSmem<S>::kDims;
+    AttnSmem<S>* r = dst(dd / kDims);
+    r->racc[c][h][dd % kDims] = o;
+    if (dd % kDims == 0) {
+      r->rm[c][h] = M;
+      r->rl[c][h] = l;
     }
   }
+  __syncthreads();   // wm / wl / wacc are rewritten by the next chunk
 }
 
 }  // namespace dev

@@ -213,6 +213,32 @@ def test_batch_invariance(nc):
         ctx1.close()
 
 
+@pytest.mark.parametrize("fmt", ["bf16", "fp32"])
+def test_attention_split_invariance(nc, monkeypatch, fmt):
+    """The attention's CTAs per (stream, KV head) (1, 2, 4, 8) is a launch
+    choice: coder intervals of two ragged streams are bit-identical for all
+    four, over windows of up to 2,048 positions (8 chunks of 256) and a
+    slide, with BF16 and FP32 caches."""
+    import dataclasses
+    shape = dataclasses.replace(S.SMALL, ctx_len=2048, slide=512)
+    seed = 5
+    lens = np.array([2300, 700], dtype=np.int64)
+    toks = [S.token_stream(seed, j, int(n), shape.vocab) for j, n in enumerate(lens)]
+    flat = torch.from_numpy(np.concatenate(toks).astype(np.int32)).cuda()
+    offs = np.array([0, lens[0]], dtype=np.int64)
+    w = S.flat_weights(shape, seed)
+    got = {}
+    for split in ("1", "2", "4", "8"):
+        monkeypatch.setenv("NC24_ATTN_CLUSTER", split)
+        ctx = nc.Context(nc.make_config(shape, fmt=fmt, max_streams=2), w)
+        iv = torch.zeros((2, int(lens.max()), 2), dtype=torch.int32, device="cuda")
+        ctx.encode_intervals(flat, offs, lens, iv, int(lens.max()))
+        got[split] = iv.cpu().numpy()
+        ctx.close()
+    for split in ("2", "4", "8"):
+        assert np.array_equal(got[split], got["1"]), split
+
+
 def test_roundtrip_small_config_with_slides_and_bpb(nc):
     """Small FP32 model, one 1,024-token stream, window 512 sliding by 128:
     lossless GPU round trip; bits within 0.5% of the oracle's."""
