@@ -30,19 +30,32 @@ sys.path.insert(0, ROOT)
 
 import synthetic as S  # noqa: E402
 
+# prefill_rows: the encoder runs the model over up to this many (stream,
+# position) rows per forward pass (0: one position per step).  It changes no
+# coded bit; the decoder always steps one position at a time.
 WORKLOADS = {
     # one stream, the full-size model in BF16 (the headline configuration)
-    "full_bf16_single": dict(shape=S.FULL, fmt="bf16", seed=1, n_streams=1, length=8192, path="gemv"),
+    "full_bf16_single": dict(shape=S.FULL, fmt="bf16", seed=1, n_streams=1, length=8192, path="gemv",
+                             prefill_rows=4096),
+    # the same, one position per model step (what the decoder runs)
+    "full_bf16_single_stepwise": dict(shape=S.FULL, fmt="bf16", seed=1, n_streams=1, length=8192, path="gemv",
+                                      prefill_rows=0),
     # the plain single-stream FP32 path (the denominator of "batched vs plain")
-    "full_fp32_single": dict(shape=S.FULL, fmt="fp32", seed=1, n_streams=1, length=8192, path="gemv"),
-    "small_fp32_single": dict(shape=S.SMALL, fmt="fp32", seed=0, n_streams=1, length=1024, path="gemv"),
+    "full_fp32_single": dict(shape=S.FULL, fmt="fp32", seed=1, n_streams=1, length=8192, path="gemv",
+                             prefill_rows=0),
+    "small_fp32_single": dict(shape=S.SMALL, fmt="fp32", seed=0, n_streams=1, length=1024, path="gemv",
+                              prefill_rows=0),
     # 256 streams with log-uniform lengths 512..16,384 on the tensor-core path
-    "batched_bf16_tc": dict(shape=S.FULL, fmt="bf16", seed=2, n_streams=256, lengths=(512, 16384), path="tc"),
+    "batched_bf16_tc": dict(shape=S.FULL, fmt="bf16", seed=2, n_streams=256, lengths=(512, 16384), path="tc",
+                            prefill_rows=4096),
     # the same 256 streams cut to their first 512 tokens: the batch stays full
     "batched_bf16_tc_512": dict(shape=S.FULL, fmt="bf16", seed=2, n_streams=256, lengths=(512, 16384),
-                                cap=512, path="tc"),
+                                cap=512, path="tc", prefill_rows=4096),
+    "batched_bf16_tc_512_stepwise": dict(shape=S.FULL, fmt="bf16", seed=2, n_streams=256, lengths=(512, 16384),
+                                         cap=512, path="tc", prefill_rows=0),
     # FP8 E4M3 weights, 1,024 streams x 4,096 tokens (first 256 tokens per stream)
-    "fp8_tc_1024_256": dict(shape=S.FULL, fmt="fp8", seed=4, n_streams=1024, length=4096, cap=256, path="tc"),
+    "fp8_tc_1024_256": dict(shape=S.FULL, fmt="fp8", seed=4, n_streams=1024, length=4096, cap=256, path="tc",
+                            prefill_rows=4096),
 }
 
 
@@ -218,6 +231,19 @@ def kernel_sources_hash() -> str:
     return m.hexdigest()[:12]
 
 
+def prefill_positions(wl, n_streams: int, max_len: int) -> int:
+    """Positions per model forward: the library's rule (largest power of two m
+    with n m <= prefill_rows dividing the window and the slide, below the
+    longest stream), or 1."""
+    shape, rows = wl["shape"], wl.get("prefill_rows", 0)
+    if rows < 2:
+        return 1
+    m = 1
+    while 2 * m * n_streams <= rows and shape.slide % (2 * m) == 0 and shape.ctx_len % (2 * m) == 0 and m < max_len:
+        m *= 2
+    return m if m >= 2 else 1
+
+
 def run_gpu(args, wl):
     import torch
     ws, rank, local = dist_env()
@@ -239,7 +265,7 @@ def run_gpu(args, wl):
     stride = int(lens.max())
     cstream = torch.cuda.Stream()
     cfg = nc24.make_config(shape, fmt=wl["fmt"], max_streams=len(streams), device=dev, stream=cstream,
-                           path=wl.get("path", "gemv"))
+                           path=wl.get("path", "gemv"), prefill_rows=wl.get("prefill_rows", 0))
     ctx = nc24.Context(cfg, S.flat_weights(shape, wl["seed"]))
     tok_dev = torch.from_numpy(flat).to(f"cuda:{dev}")
     iv = torch.empty((len(streams), stride, 2), dtype=torch.int32, device=f"cuda:{dev}")
@@ -353,7 +379,10 @@ def run_gpu(args, wl):
                        "weights": wl["fmt"], "streams_per_gpu": wl["n_streams"],
                        "tokens_per_gpu": n_tok, "ctx_len": shape.ctx_len, "slide": shape.slide,
                        "path": wl.get("path", "gemv"), "parallelism": f"replicas{ws}",
-                       "l2": "weights (BF16 269 MB) exceed L2 and are re-read every token"},
+                       "prefill_rows": wl.get("prefill_rows", 0),
+                       "positions_per_forward": prefill_positions(wl, len(streams), int(lens.max())),
+                       "l2": "inputs larger than L2: weights (BF16 269 MB) are re-read every model "
+                             "forward, and each timed step codes the whole workload"},
             "gpu_launches": launches_per_step * args.steps,
             "roofline": roofline, "kernels": kernels, "clocks": clocks, "e2e": e2e,
             "cpu_baseline": cpu, "intervals_valid": ok,
@@ -379,7 +408,7 @@ def extra_throughput(name, dev):
     stride = int(lens.max())
     cstream = torch.cuda.Stream()
     cfg = nc24.make_config(shape, fmt=wl["fmt"], max_streams=wl["n_streams"], device=dev, stream=cstream,
-                           path=wl.get("path", "gemv"))
+                           path=wl.get("path", "gemv"), prefill_rows=wl.get("prefill_rows", 0))
     ctx = nc24.Context(cfg, S.flat_weights(shape, wl["seed"]))
     tok_dev = torch.from_numpy(flat).to(f"cuda:{dev}")
     iv = torch.empty((wl["n_streams"], stride, 2), dtype=torch.int32, device=f"cuda:{dev}")
@@ -410,7 +439,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--tokens", type=int, default=0,
                     help="cut every stream to this many tokens (short runs for profiling)")
-    ap.add_argument("--extra", nargs="*", default=["batched_bf16_tc_512"],
+    ap.add_argument("--extra", nargs="*", default=["full_bf16_single_stepwise", "batched_bf16_tc_512"],
                     help="further workloads timed once each and reported under 'extra'")
     args = ap.parse_args()
     wl = WORKLOADS[args.workload]

@@ -85,6 +85,15 @@ typedef struct {
   int max_streams;                  /* stream slots; also the largest batch of one step */
   int device;                       /* CUDA device ordinal */
   void* cuda_stream;                /* cudaStream_t to order work on, or NULL */
+  int prefill_rows;                 /* encoder only: run the model over up to this many
+                                       (stream, position) rows per forward pass, positions
+                                       p .. p + m - 1 of every stream between window slides,
+                                       with the per-token vocabulary pass and updates after
+                                       it in order.  0 or 1: one position per step.  Changes
+                                       no result; the decoder replays the same CDFs one
+                                       position at a time.  At most 32768; needs
+                                       prefill_rows x vocab x 4 bytes of logits on the
+                                       device. */
 } nc_config;
 
 /* Fill *cfg with the SmolLM2-135M shape and the paper's defaults

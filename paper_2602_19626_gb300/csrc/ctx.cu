@@ -44,8 +44,9 @@ struct Slot {
 // 128 rows) and of the batch operand (box of bn rows), and the tuned bn.
 struct TcMat {
   CUtensorMap a;
-  CUtensorMap b;
-  int M = 0, K = 0, bn = 0;
+  CUtensorMap b;                     // operand of a decode step (max_streams rows)
+  CUtensorMap bp;                    // operand of a prefill forward (prefill_rows rows)
+  int M = 0, K = 0, bn = 0, bnp = 0;
   const float* scale = nullptr;
 };
 
@@ -67,11 +68,21 @@ struct nc_ctx {
   std::vector<LayerW> layers;
   const float* g_final = nullptr;
 
-  // activations for up to max_streams rows
+  // activations for up to max(max_streams, prefill_rows) rows
   float* x = nullptr;
   float* qkv = nullptr;
-  float* attn_out = nullptr;         // [max_streams][hq * 64]
+  float* attn_out = nullptr;         // [rows][hq * 64]
   float* h = nullptr;
+  // encoder prefill (P = prefill_rows rows per forward pass)
+  int P = 0;
+  int32_t* f_slots = nullptr;        // [P] slot, position and input token of each forward row
+  int32_t* f_pos = nullptr;
+  int32_t* f_tok = nullptr;
+  int32_t* d_nB_fwd = nullptr;       // forward rows
+  int32_t* d_zidx = nullptr;         // [max_streams] first forward row of each stream
+  int32_t* f_obs = nullptr;          // [P] observed token of (position, stream)
+  int32_t* f_nb = nullptr;           // [P] active streams per position
+  float* zrows = nullptr;            // [P][V] logits of the forward rows
   uint32_t* cdf = nullptr;
   int32_t* d_slots = nullptr;
   int32_t* d_nB = nullptr;
@@ -86,8 +97,8 @@ struct nc_ctx {
 
   // tensor-core path
   std::vector<TcMat> tc;             // per layer: qkv, o, gate/up, down; then the LM head
-  void* opnd = nullptr;              // [max_streams][max(d, F)] BF16 / E4M3 GEMM operand
-  float* opnd_scale = nullptr;       // [max_streams] E4M3 row scales
+  void* opnd = nullptr;              // [rows][max(d, F)] BF16 / E4M3 GEMM operand
+  float* opnd_scale = nullptr;       // [rows] E4M3 row scales
 
   StreamDev* d_st = nullptr;
   std::vector<StreamDev> h_st;
@@ -160,6 +171,7 @@ extern "C" void nc_config_default(nc_config* c) {
   c->max_streams = 1;
   c->device = 0;
   c->cuda_stream = nullptr;
+  c->prefill_rows = 0;
 }
 
 extern "C" const char* nc_status_str(int s) {
@@ -201,6 +213,7 @@ static std::string validate(const nc_config& c) {
   if (c.path == NC_PATH_TC && c.weight_fmt == NC_FP32) return "the tensor-core path needs BF16 or FP8 weights";
   if (c.max_streams < 1 || c.max_streams > 4096) return "max_streams must be 1..4096";
   if (c.warmup < 0) return "warmup must be >= 0";
+  if (c.prefill_rows < 0 || c.prefill_rows > 32768) return "prefill_rows must be 0..32768";
   return "";
 }
 
@@ -274,18 +287,20 @@ static int tc_bn_candidates(int Bmax, int* out) {
 
 // Tensor maps of every projection on the tensor-core path, and the autotuned
 // batch tile bn per projection shape: each candidate is timed on the real
-// weights with max_streams rows (the batch tile does not change the
-// arithmetic of any output element, so the choice never changes results).
+// weights with max_streams rows, and again with prefill_rows rows for the
+// encoder's prefill forward (the batch tile does not change the arithmetic
+// of any output element, so the choice never changes results).
 static int tc_setup(nc_ctx* ctx) {
   const Dims& D = ctx->D;
   const int B = ctx->cfg.max_streams;
+  const int R = std::max(B, ctx->P);                 // operand rows
   const int kb = ctx->fmt == NC_BF16;
   const int esz = kb ? 2 : 1;
   const int Kmax = std::max(std::max(D.d, D.hq * kHeadDim), D.F);
-  if (dalloc(ctx, &ctx->opnd, (size_t)B * Kmax * esz) || dalloc(ctx, &ctx->opnd_scale, (size_t)B * 4))
+  if (dalloc(ctx, &ctx->opnd, (size_t)R * Kmax * esz) || dalloc(ctx, &ctx->opnd_scale, (size_t)R * 4))
     return fail(ctx, NC_ENOMEM, "tensor-core operand allocation");
-  NC_TRY(cudaMemset(ctx->opnd, 0, (size_t)B * Kmax * esz));
-  NC_TRY(cudaMemset(ctx->opnd_scale, 0, (size_t)B * 4));
+  NC_TRY(cudaMemset(ctx->opnd, 0, (size_t)R * Kmax * esz));
+  NC_TRY(cudaMemset(ctx->opnd_scale, 0, (size_t)R * 4));
   auto add = [&](const Mat& m) {
     TcMat t;
     t.M = m.rows;
@@ -299,65 +314,65 @@ static int tc_setup(nc_ctx* ctx) {
     if (!add(L.qkv) || !add(L.o) || !add(L.gu) || !add(L.down)) return fail(ctx, NC_ECUDA, "tensor map encoding failed");
   Mat head{ctx->embed, ctx->embed_scale, D.V, D.d};
   if (!add(head)) return fail(ctx, NC_ECUDA, "tensor map encoding failed");
-  // autotune bn per distinct shape (layer 0's matrices and the LM head)
+  // autotune bn per distinct shape (layer 0's matrices and the LM head), for
+  // a decode step (B rows) and for a prefill forward (P rows)
   float* scratch = nullptr;
   size_t maxM = 0;
   for (const TcMat& t : ctx->tc) maxM = std::max(maxM, (size_t)t.M);
-  NC_TRY(cudaMalloc(&scratch, maxM * B * 4));
+  NC_TRY(cudaMalloc(&scratch, maxM * R * 4));
   int32_t* nB = nullptr;
   NC_TRY(cudaMalloc(&nB, 4));
-  NC_TRY(cudaMemcpy(nB, &B, 4, cudaMemcpyHostToDevice));
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
-  int cands[4];
-  const int nc = tc_bn_candidates(B, cands);
-  int chosen[5] = {0, 0, 0, 0, 0};
   const int probe_idx[5] = {0, 1, 2, 3, (int)ctx->tc.size() - 1};
-  int st = NC_OK;
-  for (int q = 0; q < 5 && st == NC_OK; ++q) {
-    TcMat& t = ctx->tc[probe_idx[q]];
-    float best = 1e30f;
-    for (int ci = 0; ci < nc; ++ci) {
-      TcMat tt = t;
-      if (!tc_encode_tmap(&tt.b, ctx->opnd, esz, t.K, B, cands[ci])) {
-        st = fail(ctx, NC_ECUDA, "tensor map encoding failed");
-        break;
-      }
-      TcGemm g{};
-      g.tmap_a = &tt.a;
-      g.tmap_b = &tt.b;
-      g.M = t.M;
-      g.K = t.K;
-      g.Bmax = B;
-      g.bn = cands[ci];
-      g.kind_bf16 = kb;
-      g.nB = nB;
-      g.w_scale = t.scale;
-      g.x_scale = ctx->opnd_scale;
-      g.y = scratch;
-      g.status = ctx->d_status;
-      float ms_sum = 0.f;
-      for (int rep = 0; rep < 4; ++rep) {
-        cudaEventRecord(e0, ctx->stream);
-        cudaError_t e = launch_gemm_tc(g, EPI_STORE, ctx->stream, false);
-        cudaEventRecord(e1, ctx->stream);
-        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
-        if (e != cudaSuccess) {
-          st = fail_cuda(ctx, e, "tensor-core autotune");
-          break;
+  auto tune = [&](int rows, int* chosen) -> int {
+    int cands[4];
+    const int nc = tc_bn_candidates(rows, cands);
+    NC_TRY(cudaMemcpy(nB, &rows, 4, cudaMemcpyHostToDevice));
+    for (int q = 0; q < 5; ++q) {
+      TcMat& t = ctx->tc[probe_idx[q]];
+      float best = 1e30f;
+      chosen[q] = cands[0];
+      for (int ci = 0; ci < nc; ++ci) {
+        TcMat tt = t;
+        if (!tc_encode_tmap(&tt.b, ctx->opnd, esz, t.K, rows, cands[ci]))
+          return fail(ctx, NC_ECUDA, "tensor map encoding failed");
+        TcGemm g{};
+        g.tmap_a = &tt.a;
+        g.tmap_b = &tt.b;
+        g.M = t.M;
+        g.K = t.K;
+        g.Bmax = rows;
+        g.bn = cands[ci];
+        g.kind_bf16 = kb;
+        g.nB = nB;
+        g.w_scale = t.scale;
+        g.x_scale = ctx->opnd_scale;
+        g.y = scratch;
+        g.status = ctx->d_status;
+        float ms_sum = 0.f;
+        for (int rep = 0; rep < 4; ++rep) {
+          cudaEventRecord(e0, ctx->stream);
+          cudaError_t e = launch_gemm_tc(g, EPI_STORE, ctx->stream, false);
+          cudaEventRecord(e1, ctx->stream);
+          if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+          if (e != cudaSuccess) return fail_cuda(ctx, e, "tensor-core autotune");
+          float ms = 0.f;
+          cudaEventElapsedTime(&ms, e0, e1);
+          if (rep) ms_sum += ms;
         }
-        float ms = 0.f;
-        cudaEventElapsedTime(&ms, e0, e1);
-        if (rep) ms_sum += ms;
-      }
-      if (st != NC_OK) break;
-      if (ms_sum < best) {
-        best = ms_sum;
-        chosen[q] = cands[ci];
+        if (ms_sum < best) {
+          best = ms_sum;
+          chosen[q] = cands[ci];
+        }
       }
     }
-  }
+    return NC_OK;
+  };
+  int chosen[5] = {0, 0, 0, 0, 0}, chosen_p[5] = {0, 0, 0, 0, 0};
+  int st = tune(B, chosen);
+  if (st == NC_OK && ctx->P > 0) st = tune(ctx->P, chosen_p);
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   cudaFree(scratch);
@@ -365,8 +380,14 @@ static int tc_setup(nc_ctx* ctx) {
   if (st != NC_OK) return st;
   for (size_t i = 0; i < ctx->tc.size(); ++i) {
     TcMat& t = ctx->tc[i];
-    t.bn = (i + 1 == ctx->tc.size()) ? chosen[4] : chosen[i % 4];
+    const int q = (i + 1 == ctx->tc.size()) ? 4 : (int)(i % 4);
+    t.bn = chosen[q];
     if (!tc_encode_tmap(&t.b, ctx->opnd, esz, t.K, B, t.bn)) return fail(ctx, NC_ECUDA, "tensor map encoding failed");
+    if (ctx->P > 0) {
+      t.bnp = chosen_p[q];
+      if (!tc_encode_tmap(&t.bp, ctx->opnd, esz, t.K, ctx->P, t.bnp))
+        return fail(ctx, NC_ECUDA, "tensor map encoding failed");
+    }
   }
   return NC_OK;
 }
@@ -430,17 +451,15 @@ extern "C" int nc_ctx_create(const nc_config* cfg, const void* weights, size_t n
   D.tau = c.temperature;
   D.kv_bf16 = c.weight_fmt != NC_FP32;
   {
-    // Attention CTAs per (stream, KV head): the largest of 8, 4, 2, 1 that
-    // keeps the launch within about two waves of two CTAs per SM; results
-    // do not depend on it.  NC24_ATTN_CLUSTER=1|2|4|8 overrides.
+    // Attention CTAs per (stream, KV head) are picked per launch from its
+    // rows (results do not depend on them); NC24_ATTN_CLUSTER=1|2|4|8 fixes them.
     int nsm = 0;
     if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c.device) != cudaSuccess || nsm <= 0)
       return bail(NC_ECUDA);
-    int S = 8;
-    while (S > 1 && (int64_t)c.n_kv_heads * c.max_streams * S > 4 * (int64_t)nsm) S /= 2;
+    D.n_sm = nsm;
+    D.attn_cluster = 0;                            // by the rows of each launch
     const char* e = std::getenv("NC24_ATTN_CLUSTER");
-    if (e && (e[0] == '1' || e[0] == '2' || e[0] == '4' || e[0] == '8') && e[1] == 0) S = e[0] - '0';
-    D.attn_cluster = S;
+    if (e && (e[0] == '1' || e[0] == '2' || e[0] == '4' || e[0] == '8') && e[1] == 0) D.attn_cluster = e[0] - '0';
   }
   D.order = c.ngram_order;
   D.use_head = c.use_head;
@@ -518,9 +537,17 @@ extern "C" int nc_ctx_create(const nc_config* cfg, const void* weights, size_t n
 
   // ---- activations and per-step buffers
   const size_t B = c.max_streams;
-  if (dalloc(ctx, &ctx->x, B * D.d * 4) || dalloc(ctx, &ctx->qkv, B * D.qkv_rows * 4) ||
-      dalloc(ctx, &ctx->attn_out, B * D.hq * kHeadDim * 4) ||
-      dalloc(ctx, &ctx->h, B * D.F * 4) || dalloc(ctx, &ctx->cdf, B * (D.V + 1) * 4) ||
+  ctx->P = c.prefill_rows >= 2 ? c.prefill_rows : 0;
+  const size_t RA = std::max(B, (size_t)ctx->P);     // activation rows
+  if (ctx->P > 0 &&
+      (dalloc(ctx, &ctx->f_slots, (size_t)ctx->P * 4) || dalloc(ctx, &ctx->f_pos, (size_t)ctx->P * 4) ||
+       dalloc(ctx, &ctx->f_tok, (size_t)ctx->P * 4) || dalloc(ctx, &ctx->d_nB_fwd, 16) ||
+       dalloc(ctx, &ctx->d_zidx, B * 4) || dalloc(ctx, &ctx->zrows, (size_t)ctx->P * D.V * 4) ||
+       dalloc(ctx, &ctx->f_obs, (size_t)ctx->P * 4) || dalloc(ctx, &ctx->f_nb, (size_t)ctx->P * 4)))
+    return bail(NC_ENOMEM);
+  if (dalloc(ctx, &ctx->x, RA * D.d * 4) || dalloc(ctx, &ctx->qkv, RA * D.qkv_rows * 4) ||
+      dalloc(ctx, &ctx->attn_out, RA * D.hq * kHeadDim * 4) ||
+      dalloc(ctx, &ctx->h, RA * D.F * 4) || dalloc(ctx, &ctx->cdf, B * (D.V + 1) * 4) ||
       dalloc(ctx, &ctx->d_slots, B * 4) || dalloc(ctx, &ctx->d_nB, 16) ||
       dalloc(ctx, &ctx->d_obs, B * 4) || dalloc(ctx, &ctx->d_target, B * 4) ||
       dalloc(ctx, &ctx->d_lohi, B * 8) || dalloc(ctx, &ctx->d_status, B * 4) ||
@@ -656,7 +683,7 @@ extern "C" int nc_stream_close(nc_ctx* ctx, int32_t stream_id) {
 // ------------------------------------------------------------- step pieces
 
 static Batch make_batch(nc_ctx* ctx) {
-  Batch b;
+  Batch b{};
   b.slots = ctx->d_slots;
   b.nB = ctx->d_nB;
   b.obs = ctx->d_obs;
@@ -714,6 +741,7 @@ static cudaError_t launch_model(nc_ctx* ctx, const Batch& b, StepMarks* mk = nul
     io.g = L.g_attn;
     io.y = ctx->qkv;
     e = launch_gemv(D, b, L.qkv, ctx->fmt, PRO_RMSNORM, EPI_STORE, io, s);
+    if (e == cudaSuccess && b.pos) e = launch_kv_append(D, b, l, ctx->qkv, s);
     if (e == cudaSuccess) e = m.mark(s, TK_QKV);
     if (e == cudaSuccess) e = launch_attn(D, b, l, ctx->qkv, ctx->attn_out, s);
     if (e == cudaSuccess) e = m.mark(s, TK_ATTN);
@@ -758,13 +786,15 @@ static cudaError_t launch_model_tc(nc_ctx* ctx, const Batch& b, StepMarks& m) {
   cudaStream_t s = ctx->stream;
   const int kb = ctx->fmt == NC_BF16;
   auto gemm = [&](const TcMat& t, int epi, float* y, float* h) {
+    const bool pf = b.pos != nullptr;               // prefill forward: P-row operand map
     TcGemm g{};
     g.tmap_a = &t.a;
-    g.tmap_b = &t.b;
+    g.tmap_b = pf ? &t.bp : &t.b;
     g.M = t.M;
     g.K = t.K;
     g.Bmax = b.Bmax;
-    g.bn = t.bn;
+    g.bn = pf ? t.bnp : t.bn;
+    g.zrows = b.z_out;
     g.kind_bf16 = kb;
     g.nB = b.nB;
     g.w_scale = t.scale;
@@ -783,6 +813,7 @@ static cudaError_t launch_model_tc(nc_ctx* ctx, const Batch& b, StepMarks& m) {
     const TcMat* T = &ctx->tc[4 * l];
     e = launch_act_rmsnorm(D, b, ctx->x, L.g_attn, D.d, kb, ctx->opnd, ctx->opnd_scale, s);
     if (e == cudaSuccess) e = gemm(T[0], EPI_STORE, ctx->qkv, nullptr);
+    if (e == cudaSuccess && b.pos) e = launch_kv_append(D, b, l, ctx->qkv, s);
     if (e == cudaSuccess) e = m.mark(s, TK_QKV);
     if (e == cudaSuccess) e = launch_attn(D, b, l, ctx->qkv, ctx->attn_out, s);
     if (e == cudaSuccess) e = m.mark(s, TK_ATTN);
@@ -803,8 +834,8 @@ static cudaError_t launch_model_tc(nc_ctx* ctx, const Batch& b, StepMarks& m) {
 }
 
 // Algorithmic bytes of one launch of each kind for B active rows whose
-// attention window holds n_ctx entries (the new token included).
-static void step_bytes(const nc_ctx* ctx, int B, int n_ctx, double* out) {
+// attention windows hold ctx_sum entries in total (the fed tokens included).
+static void step_bytes(const nc_ctx* ctx, int B, double ctx_sum, double* out) {
   const Dims& D = ctx->D;
   const double esz = ctx->fmt == NC_FP32 ? 4 : ctx->fmt == NC_BF16 ? 2 : 1;
   const double kvsz = D.kv_bf16 ? 2 : 4;
@@ -817,8 +848,7 @@ static void step_bytes(const nc_ctx* ctx, int B, int n_ctx, double* out) {
   out[TK_PREPARE] = B * 24.0;
   out[TK_EMBED] = B * D.d * (esz + 4);
   out[TK_QKV] = gemv(D.qkv_rows, D.d, D.qkv_rows, false) + B * D.d * 4;
-  out[TK_ATTN] = B * (D.hkv * ((n_ctx - 1) * 2.0 * kHeadDim * kvsz + 2.0 * kHeadDim * kvsz) +
-                      D.qkv_rows * 4.0 + D.hq * kHeadDim * 4.0);
+  out[TK_ATTN] = D.hkv * 2.0 * kHeadDim * kvsz * ctx_sum + B * (D.qkv_rows * 4.0 + D.hq * kHeadDim * 4.0);
   out[TK_O] = gemv(D.d, qd, D.d, true);
   out[TK_GU] = gemv(2.0 * D.F, D.d, D.F, false);
   out[TK_DOWN] = gemv(D.d, D.F, D.d, true);
@@ -987,6 +1017,138 @@ static uint8_t flags_byte(const nc_config& c) {
 }
 static uint8_t path_byte(const nc_config& c) { return (uint8_t)(c.weight_fmt | (c.path << 4)); }
 
+// Positions per prefill forward for n streams: the largest power of two m
+// with n m <= prefill_rows that divides the window length L and the slide C
+// (so no chunk of positions crosses a slide: every row of a forward sees its
+// window start fixed) and is not above the longest stream; 0 = no prefill.
+static int prefill_chunk(const nc_ctx* ctx, int n, int64_t max_len) {
+  const Dims& D = ctx->D;
+  if (ctx->P < 2 || n < 1) return 0;
+  int m = 1;
+  while ((int64_t)2 * m * n <= ctx->P && D.C % (2 * m) == 0 && D.L % (2 * m) == 0 && m < max_len) m *= 2;
+  return m >= 2 ? m : 0;
+}
+
+// Encoder with prefill: per chunk of m positions, one model forward over the
+// n m (stream, position) rows (KV appended for all rows first, logits of
+// every row kept), then the m vocabulary passes and updates of each stream
+// in order.  Every row's arithmetic is the decode step's, so the intervals
+// are those of one position per step.  Streams sorted longest first.
+static int encode_prefill(nc_ctx* ctx, int n, int m, const int32_t* tok_dev, const int64_t* offs_dev,
+                          const int64_t* lens_dev, const std::vector<int64_t>& lens_h, uint32_t* intervals,
+                          int64_t stride, nc_trace* trace) {
+  const Dims& D = ctx->D;
+  cudaStream_t s = ctx->stream;
+  int64_t max_len = 0;
+  for (int64_t l : lens_h) max_len = std::max(max_len, l);
+  Batch b = make_batch(ctx);                      // stream rows (slots only)
+  b.Bmax = n;
+  Batch f = make_batch(ctx);                      // (stream, position) rows of the forward
+  f.slots = ctx->f_slots;
+  f.nB = ctx->d_nB_fwd;
+  f.obs = nullptr;
+  f.Bmax = n * m;
+  f.pos = ctx->f_pos;
+  f.tok = ctx->f_tok;
+  f.z_out = ctx->zrows;
+  VocabIO io{};
+  io.predict = 1;
+  io.update = 1;
+  io.intervals = intervals;
+  io.interval_stride = stride;
+  StepMarks mk;
+  mk.on = trace != nullptr;
+  const int fwd_marks = 1 + 1 + 5 * D.n_layers + 1;   // prepare, embed, 5 per layer, LM head
+  if (mk.on) {
+    mk.ev.resize(fwd_marks + 2 * m + 2);
+    for (auto& e : mk.ev) NC_TRY(cudaEventCreate(&e));
+  }
+  auto one_chunk = [&]() -> cudaError_t {
+    cudaError_t e = mk.begin(s);
+    if (e == cudaSuccess)
+      e = launch_prepare_prefill(b, n, m, D.V, tok_dev, offs_dev, lens_dev, ctx->f_slots, ctx->f_pos, ctx->f_tok,
+                                 ctx->d_nB_fwd, ctx->f_obs, ctx->f_nb, ctx->d_zidx, s);
+    if (e == cudaSuccess) e = mk.mark(s, TK_PREPARE);
+    if (e == cudaSuccess) e = launch_model(ctx, f, &mk);
+    for (int r = 0; r < m && e == cudaSuccess; ++r) {
+      Batch br = b;                                 // position p0 + r of every stream
+      br.nB = ctx->f_nb + r;
+      br.obs = ctx->f_obs + (size_t)r * n;
+      br.z_in = ctx->zrows + (size_t)r * D.V;
+      br.z_idx = ctx->d_zidx;
+      e = launch_vocab(D, br, io, s);
+      if (e == cudaSuccess) e = mk.mark(s, TK_VOCAB);
+      if (e == cudaSuccess) e = launch_ngram_update(D, br, s);
+      if (e == cudaSuccess) e = mk.mark(s, TK_NGRAM);
+    }
+    return e;
+  };
+  cudaGraph_t g = nullptr;
+  cudaGraphExec_t ge = nullptr;
+  if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+    mk.capturing = true;
+    cudaError_t e = one_chunk();
+    mk.capturing = false;
+    cudaError_t e2 = cudaStreamEndCapture(s, &g);
+    if (e != cudaSuccess || e2 != cudaSuccess || cudaGraphInstantiate(&ge, g, 0) != cudaSuccess) ge = nullptr;
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+  }
+  if (trace) {
+    std::memset(trace, 0, sizeof(*trace));
+    trace->graphed = ge != nullptr;
+    trace->n_kinds = TK_COUNT;
+    for (int k = 0; k < TK_COUNT; ++k) std::snprintf(trace->name[k], sizeof(trace->name[k]), "%s", kTraceNames[k]);
+  }
+  auto start_at = [&](int64_t a) -> int64_t { return a < D.L ? 0 : ((a - D.L) / D.C + 1) * D.C; };
+  int st = NC_OK;
+  for (int64_t p = 0; p < max_len; p += m) {
+    cudaError_t e = ge ? cudaGraphLaunch(ge, s) : one_chunk();
+    if (e != cudaSuccess) {
+      st = fail_cuda(ctx, e, "prefill encode chunk");
+      break;
+    }
+    if (trace) {
+      // forward: the live rows and their windows; then each position's active streams
+      int64_t rows = 0;
+      double ctx_sum = 0;
+      for (int j = 0; j < n; ++j)
+        for (int64_t a = p; a < std::min(p + m, lens_h[j]); ++a) {
+          ++rows;
+          ctx_sum += (double)(a - start_at(a) + 1);
+        }
+      double fwd[TK_COUNT];
+      step_bytes(ctx, (int)rows, ctx_sum, fwd);
+      fwd[TK_PREPARE] = n * (double)m * 28;
+      e = cudaEventSynchronize(mk.ev[mk.n]);
+      if (e != cudaSuccess) {
+        st = fail_cuda(ctx, e, "trace sync");
+        break;
+      }
+      for (int i = 0; i < mk.n; ++i) {
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, mk.ev[i], mk.ev[i + 1]);
+        const int kd = mk.kind[i];
+        double by = fwd[kd];
+        if (i >= fwd_marks) {
+          const int64_t a = p + (i - fwd_marks) / 2;
+          int act = 0;
+          for (int j = 0; j < n; ++j) act += lens_h[j] > a;
+          double per[TK_COUNT];
+          step_bytes(ctx, act, 0.0, per);
+          by = per[kd];
+        }
+        trace->ms[kd] += ms;
+        trace->launches[kd] += 1;
+        trace->bytes[kd] += by;
+      }
+    }
+  }
+  if (ge) cudaGraphExecDestroy(ge);
+  for (auto& e : mk.ev) cudaEventDestroy(e);
+  return st;
+}
+
 // The device half of nc_encode: tokens resident on the device, one captured
 // step replayed until every stream is coded.  Streams must already be open in
 // slots slot_of[r] (row order = longest first, so the active rows of every
@@ -1000,6 +1162,8 @@ static int encode_device(nc_ctx* ctx, int n, const std::vector<int>& slot_of, co
   for (int64_t l : lens_h) max_len = std::max(max_len, l);
   for (int j = 0; j < n; ++j) ctx->h_i32[1 + j] = slot_of[j];
   NC_TRY(cudaMemcpyAsync(ctx->d_slots, ctx->h_i32 + 1, (size_t)n * 4, cudaMemcpyHostToDevice, s));
+  const int m = prefill_chunk(ctx, n, max_len);
+  if (m >= 2) return encode_prefill(ctx, n, m, tok_dev, offs_dev, lens_dev, lens_h, intervals, stride, trace);
   Batch b = make_batch(ctx);
   b.Bmax = n;
   VocabIO io{};
@@ -1061,7 +1225,7 @@ static int encode_device(nc_ctx* ctx, int n, const std::vector<int>& slot_of, co
       }
       const int n_ctx = (int)(k - start + 1);
       double bytes[TK_COUNT];
-      step_bytes(ctx, active, n_ctx, bytes);
+      step_bytes(ctx, active, (double)active * n_ctx, bytes);
       e = cudaEventSynchronize(mk.ev[mk.n]);
       if (e != cudaSuccess) {
         st = fail_cuda(ctx, e, "trace sync");

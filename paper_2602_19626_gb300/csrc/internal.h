@@ -69,7 +69,8 @@ struct Dims {
   int qkv_rows;             // (hq + 2 hkv) * 64
   float eps, theta, tau;
   int kv_bf16;              // 1: KV cache in BF16
-  int attn_cluster;         // CTAs per (stream, KV head) in attention: 1, 2, 4 or 8
+  int attn_cluster;         // CTAs per (stream, KV head) in attention: 1, 2, 4 or 8; 0 = by batch size
+  int n_sm;                 // SMs of the device
   int order;                // N-gram order (0 = off)
   int use_head;
   int warmup;
@@ -99,6 +100,18 @@ struct Batch {
   const int32_t* obs;       // [Bmax] observed token of row j, or nullptr
   StreamDev* st;            // [max_streams]
   int Bmax;
+  // Prefill forward (encoder): row j feeds position pos[j] (-1: no position)
+  // of stream slots[j] with token tok[j], the KV ring already holds every
+  // row's k and v, and the LM head writes row j's logits to z_out + j V.
+  // All nullptr in a decode step (position = n_coded, token = last_tok).
+  const int32_t* pos;
+  const int32_t* tok;
+  float* z_out;
+  // Vocabulary pass after a prefill: row j's logits are z_in + z_idx[j] V
+  // (nullptr: the stream's own z).  The pass then reads nothing before its
+  // wait on the previous kernel.
+  const float* z_in;
+  const int32_t* z_idx;
 };
 
 // Programmatic dependent launch: a kernel launched with the PDL attribute may
@@ -182,6 +195,18 @@ cudaError_t launch_ngram_update(const Dims& D, const Batch& b, cudaStream_t s);
 cudaError_t launch_prepare_encode(const Batch& b, int n_streams, const int32_t* tok_flat,
                                   const int64_t* offs, const int64_t* lens, int32_t* obs,
                                   int32_t* nB, cudaStream_t s);
+// Encoder prefill of positions p0 .. p0 + m - 1 (p0 = n_coded of row 0, the
+// longest stream) for n_streams rows: forward row i = j m + r gets the slot of
+// stream row j, position p0 + r (or -1 past the stream's end) and its input
+// token; *nB_fwd = m x (streams with tokens left).  For the sequential pass
+// of position p0 + r: nb_step[r] active rows, observed tokens
+// obs_step[r n + j], logits at forward row z_idx[j] + r (z_idx[j] = j m).
+cudaError_t launch_prepare_prefill(const Batch& b, int n_streams, int m, int V, const int32_t* tok_flat,
+                                   const int64_t* offs, const int64_t* lens, int32_t* f_slots, int32_t* f_pos,
+                                   int32_t* f_tok, int32_t* nB_fwd, int32_t* obs_step, int32_t* nb_step,
+                                   int32_t* z_idx, cudaStream_t s);
+// Prefill: rotate and append the k, v of every row to the KV ring of `layer`.
+cudaError_t launch_kv_append(const Dims& D, const Batch& b, int layer, const float* qkv, cudaStream_t s);
 // Decoder: row j's symbol is the s with cdf[s] <= target[j] < cdf[s+1]; writes
 // obs[j] = s and lohi[2j..2j+1] = (cdf[s], cdf[s+1]).
 cudaError_t launch_search(const Batch& b, int V, const uint32_t* cdf, const uint32_t* target,
@@ -202,7 +227,8 @@ struct TcGemm {
   const float* x_scale;     // FP8: [Bmax]
   float* y;                 // EPI_STORE / EPI_RESID: [Bmax][M]
   float* h_out;             // EPI_SWIGLU: [Bmax][M / 2]
-  StreamDev* st;            // EPI_LOGITS
+  StreamDev* st;            // EPI_LOGITS: each stream's z, or
+  float* zrows;             // EPI_LOGITS: [Bmax][M] when set
   const int32_t* slots;
   int32_t* status;          // error word (ST_TIMEOUT)
 };

@@ -245,7 +245,10 @@ __global__ void __launch_bounds__(kTcThreads, 1)
           } else if (EPI == EPI_RESID) {
             g.y[(size_t)n * g.M + r] += y;
           } else {
-            g.st[g.slots[n]].z[r] = y;
+            if (g.zrows)
+              g.zrows[(size_t)n * g.M + r] = y;
+            else
+              g.st[g.slots[n]].z[r] = y;
           }
         }
       }

@@ -30,7 +30,7 @@ __global__ void k_embed(Dims D, Batch b, const void* E, const float* Escale, flo
   pdl_wait();
   pdl_trigger();
   if (j >= *b.nB) return;
-  const int tok = b.st[b.slots[j]].last_tok;
+  const int tok = b.tok ? b.tok[j] : b.st[b.slots[j]].last_tok;
   for (int c = threadIdx.x; c < D.d; c += blockDim.x) x[(size_t)j * D.d + c] = embed_at<FMT>(E, Escale, D.d, tok, c);
 }
 
@@ -55,7 +55,7 @@ __global__ void __launch_bounds__(kGemvThreads) k_gemv(Dims D, Batch b, Mat m, G
   pdl_wait();
   pdl_trigger();
   const int B = *b.nB;
-  GemvOut out{io.y, b.st, b.slots};
+  GemvOut out{io.y, b.st, b.slots, b.z_out};
   const int cols = m.cols;
   auto src = [&](int row, int c) { return __ldcg(io.x + (size_t)row * cols + c); };
   auto sync = [] { __syncthreads(); };
@@ -80,23 +80,36 @@ __global__ void __launch_bounds__(kAttnThreads) k_attn(Dims D, Batch b, int laye
   const int j = blockIdx.z, g = blockIdx.y;
   if (j >= *b.nB) return;                          // uniform across the cluster
   StreamDev& st = b.st[b.slots[j]];
-  const int a = st.n_coded;
-  const int start = window_start(D, st);
-  const int nc = (a - start) / kAttnChunk + 1;     // the last chunk holds position a
+  const int a = b.pos ? b.pos[j] : st.n_coded;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int grp = D.hq / D.hkv;
+  if (a < 0) {                                     // prefill row past the stream's end
+    pdl_wait();
+    pdl_trigger();
+    for (int e = tid; e < grp * kHeadDim / S; e += kAttnThreads)
+      io.attn_out[(size_t)j * D.hq * kHeadDim + (g * grp + e / (kHeadDim / S)) * kHeadDim +
+                  rank * (kHeadDim / S) + e % (kHeadDim / S)] = 0.f;
+    return;                                        // uniform across the cluster
+  }
+  const int start = b.pos ? window_start_at(D, a) : window_start(D, st);
+  const int nc = (a - start) / kAttnChunk + 1;     // the last chunk holds position a
   __shared__ AttnSmem<S> sm;
   // every CTA of the cluster must have started before shared memory is
   // written remotely: arrive now, wait before the first remote store
   if (S > 1) asm volatile("barrier.cluster.arrive.relaxed.aligned;" ::: "memory");
   AttnPre<KBF16> pre;
   attn_rope(D, a, tid, sm);
+  // a prefill's ring entries of this chunk of positions were written by the
+  // append pass just before: wait for it before loading any of them
+  if (b.pos) pdl_wait();
   if (rank < nc) {
     const int c_lo = start + rank * kAttnChunk;
     attn_load<KBF16>(D, st, layer, g, c_lo + warp * 32, min(c_lo + kAttnChunk, a + 1), a, lane, pre);
   }
   pdl_wait();
   pdl_trigger();
-  attn_qkv<KBF16>(D, st, layer, j, g, a, (nc - 1) % S == rank, tid, sm, io);
+  // a prefill appended every row's k, v before this launch
+  attn_qkv<KBF16>(D, st, layer, j, g, a, !b.pos && (nc - 1) % S == rank, tid, sm, io);
   auto dst = [&](int r) -> AttnSmem<S>* {
     if (S == 1) return &sm;
     return cg::this_cluster().map_shared_rank(&sm, r);
@@ -109,7 +122,6 @@ __global__ void __launch_bounds__(kAttnThreads) k_attn(Dims D, Batch b, int laye
     attn_chunk<KBF16, S>(D, c, c_lo, c_end, a, tid, sm, pre, dst);
   }
   if (S > 1) cg::this_cluster().sync();            // every chunk's partial has arrived
-  const int grp = D.hq / D.hkv;
   constexpr int kDims = AttnSmem<S>::kDims;
   for (int e = tid; e < grp * kDims; e += kAttnThreads) {
     const int h = e / kDims, dl = e % kDims;
@@ -128,6 +140,28 @@ __global__ void __launch_bounds__(kAttnThreads) k_attn(Dims D, Batch b, int laye
     }
     io.attn_out[(size_t)j * D.hq * kHeadDim + (g * grp + h) * kHeadDim + rank * kDims + dl] = o / l;
   }
+}
+
+// Prefill: the k, v of row j (position pos[j]) rotated exactly as the decode
+// attention rotates the fed token's, appended to the ring of `layer`.
+struct AppendSmem {
+  float qs[kMaxGroup][kHeadDim];
+  float kn[kHeadDim], vn[kHeadDim];
+  float cs[kHeadDim / 2], sn[kHeadDim / 2];
+};
+
+template <int KBF16>
+__global__ void __launch_bounds__(kAttnThreads) k_kv_append(Dims D, Batch b, int layer, AttnIO io) {
+  const int j = blockIdx.y, g = blockIdx.x;
+  pdl_wait();
+  pdl_trigger();
+  if (j >= *b.nB) return;
+  const int a = b.pos[j];
+  if (a < 0) return;
+  StreamDev& st = b.st[b.slots[j]];
+  __shared__ AppendSmem sm;
+  attn_rope(D, a, threadIdx.x, sm);
+  attn_qkv<KBF16>(D, st, layer, j, g, a, true, threadIdx.x, sm, io);
 }
 
 // ------------------------------------------------------------ weight formats
@@ -257,9 +291,18 @@ cudaError_t launch_gemv(const Dims& D, const Batch& b, const Mat& m, int fmt, in
   return gemv_f<NC_FP8E4M3>(D, b, m, pro, epi, io, s);
 }
 
+// CTAs per (row, KV head): the largest of 8, 4, 2, 1 that keeps the launch
+// within about two waves of two CTAs per SM.  Results do not depend on it.
+static int attn_split(const Dims& D, const Batch& b) {
+  if (D.attn_cluster) return D.attn_cluster;
+  int S = 8;
+  while (S > 1 && (int64_t)D.hkv * b.Bmax * S > 4 * (int64_t)D.n_sm) S /= 2;
+  return S;
+}
+
 cudaError_t launch_attn(const Dims& D, const Batch& b, int layer, const float* qkv, float* attn_out,
                         cudaStream_t s) {
-  const int S = D.attn_cluster;
+  const int S = attn_split(D, b);
   dim3 grid(S, D.hkv, b.Bmax);
   AttnIO io{qkv, attn_out};
   auto pick = [&](auto k1, auto k0) { return D.kv_bf16 ? k1 : k0; };
@@ -270,6 +313,12 @@ cudaError_t launch_attn(const Dims& D, const Batch& b, int layer, const float* q
     case 8: return launch_kernel_cluster(pick(k_attn<1, 8>, k_attn<0, 8>), grid, dim3(kAttnThreads), 0, s, D.pdl, 8, D, b, layer, io);
     default: return cudaErrorInvalidValue;
   }
+}
+
+cudaError_t launch_kv_append(const Dims& D, const Batch& b, int layer, const float* qkv, cudaStream_t s) {
+  AttnIO io{qkv, nullptr};
+  return launch_kernel(D.kv_bf16 ? k_kv_append<1> : k_kv_append<0>, dim3(D.hkv, b.Bmax), dim3(kAttnThreads), 0, s,
+                       D.pdl, D, b, layer, io);
 }
 
 cudaError_t launch_convert_weights(const float* src, void* dst, float* scale, int64_t rows,

@@ -7,6 +7,8 @@
 // symbols.  Reductions go thread -> warp (fixed xor tree) -> CTA (warps in
 // order) -> cluster (ranks in order through distributed shared memory), so
 // every result is independent of the batch, the slot and the launch.
+#include <algorithm>
+
 #include <cooperative_groups.h>
 
 #include "internal.h"
@@ -335,6 +337,9 @@ __global__ void __cluster_dims__(kVocabCluster, 1, 1) __launch_bounds__(kVocabTh
   __shared__ VocabShared sh;
   cg::cluster_group cl = cg::this_cluster();
   const int j = blockIdx.x / kVocabCluster;
+  // after a prefill the previous kernel is the N-gram update of the previous
+  // position: nothing of the stream's state may be read before it completed
+  if (b.z_in) pdl_wait();
   if (j >= *b.nB) return;                        // uniform across the cluster
   const int rank = (int)cl.block_rank();
   StreamDev& st = b.st[b.slots[j]];
@@ -424,7 +429,7 @@ __global__ void __cluster_dims__(kVocabCluster, 1, 1) __launch_bounds__(kVocabTh
 
   // ---- biased logits s = z / tau + b and their softmax (round 1)
   float s[E];
-  load_run<E>(st.z, v0, V, s, -INFINITY);
+  load_run<E>(b.z_in ? b.z_in + (size_t)b.z_idx[j] * V : st.z, v0, V, s, -INFINITY);
   if (io.probe_z) store_run<E>(io.probe_z + (size_t)j * V, v0, V, s);
 #pragma unroll
   for (int i = 0; i < E; ++i) s[i] = (v0 + i < V) ? __fdiv_rn(s[i], D.tau) + bias[i] : -INFINITY;
@@ -671,6 +676,43 @@ __global__ void k_prepare_encode(Batch b, int n_streams, const int32_t* tok_flat
   }
 }
 
+// Encoder prefill of positions p0 .. p0 + m - 1 (p0 = n_coded of row 0;
+// rows sorted longest first, so the streams with tokens left are a prefix).
+// Forward row i = j m + r: slot, position (-1 past the stream's end) and
+// input token.  Sequential pass r: active rows nb_step[r], observed tokens
+// obs_step[r n + j]; row j's logits sit at forward row z_idx[j] + r.
+__global__ void k_prepare_prefill(Batch b, int n_streams, int m, int V, const int32_t* tok_flat, const int64_t* offs,
+                                  const int64_t* lens, int32_t* f_slots, int32_t* f_pos, int32_t* f_tok,
+                                  int32_t* nB_fwd, int32_t* obs_step, int32_t* nb_step, int32_t* z_idx) {
+  pdl_wait();
+  pdl_trigger();
+  const int p0 = b.st[b.slots[0]].n_coded;
+  const int tid = threadIdx.x + blockIdx.x * blockDim.x, nthr = blockDim.x * gridDim.x;
+  for (int i = tid; i < n_streams * m; i += nthr) {
+    const int j = i / m, r = i % m;
+    const int64_t a = (int64_t)p0 + r;
+    const bool live = a < lens[j];
+    f_slots[i] = b.slots[j];
+    f_pos[i] = live ? (int)a : -1;
+    // BOS (id 0) at position 0; an id outside the vocabulary is fed as 0 here
+    // and rejected by the vocabulary pass that codes it
+    const int t = (live && a > 0) ? tok_flat[offs[j] + a - 1] : 0;
+    f_tok[i] = (t >= 0 && t < V) ? t : 0;
+    obs_step[r * n_streams + j] = live ? tok_flat[offs[j] + a] : 0;
+  }
+  for (int r = tid; r < m; r += nthr) {
+    int act = 0;
+    while (act < n_streams && lens[act] > (int64_t)p0 + r) ++act;
+    nb_step[r] = act;
+  }
+  for (int j = tid; j < n_streams; j += nthr) z_idx[j] = j * m;
+  if (tid == 0) {
+    int live = 0;
+    while (live < n_streams && lens[live] > p0) ++live;
+    *nB_fwd = live * m;
+  }
+}
+
 // Standalone quantiser over rows of binary32 probabilities.
 template <int E>
 __global__ void __cluster_dims__(kVocabCluster, 1, 1) __launch_bounds__(kVocabThreads)
@@ -818,6 +860,16 @@ cudaError_t launch_prepare_encode(const Batch& b, int n_streams, const int32_t* 
                                   int32_t* nB, cudaStream_t s) {
   return launch_kernel(k_prepare_encode, dim3(1), dim3(1024), 0, s, true, b, n_streams, tok_flat, offs, lens,
                        obs, nB);
+}
+
+cudaError_t launch_prepare_prefill(const Batch& b, int n_streams, int m, int V, const int32_t* tok_flat,
+                                   const int64_t* offs, const int64_t* lens, int32_t* f_slots, int32_t* f_pos,
+                                   int32_t* f_tok, int32_t* nB_fwd, int32_t* obs_step, int32_t* nb_step,
+                                   int32_t* z_idx, cudaStream_t s) {
+  const int rows = n_streams * m;
+  const int blocks = std::min((rows + 255) / 256, 64);
+  return launch_kernel(k_prepare_prefill, dim3(blocks), dim3(256), 0, s, true, b, n_streams, m, V, tok_flat, offs,
+                       lens, f_slots, f_pos, f_tok, nB_fwd, obs_step, nb_step, z_idx);
 }
 
 template <int E>

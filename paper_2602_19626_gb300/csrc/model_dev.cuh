@@ -90,6 +90,12 @@ __device__ __forceinline__ int window_start(const Dims& D, const StreamDev& st) 
   return start;
 }
 
+// The same window start as a function of the fed position a alone: the
+// cache first fills at a = L, then every C positions drops the oldest C.
+__device__ __forceinline__ int window_start_at(const Dims& D, int a) {
+  return a < D.L ? 0 : ((a - D.L) / D.C + 1) * D.C;
+}
+
 __device__ __forceinline__ float silu(float a) { return a / (1.0f + expf(-a)); }
 
 // Embedding value of token `tok`, column c, in the storage format.
@@ -183,6 +189,7 @@ struct GemvOut {
   float* y;
   StreamDev* st;
   const int32_t* slots;
+  float* zrows;             // EPI_LOGITS into [B][rows] instead of each stream's z
 };
 
 // One row pair for streams b0 .. b0 + nb - 1: lane l accumulates the weight
@@ -278,7 +285,7 @@ __device__ __forceinline__ void gemv_rowpair(const Mat& m, int rp, const float* 
         } else if (EPI == EPI_SWIGLU) {
           out.y[(size_t)j * (m.rows / 2) + r0 / 2] = silu(y0) * y1;
         } else {
-          float* z = out.st[out.slots[j]].z;
+          float* z = out.zrows ? out.zrows + (size_t)j * m.rows : out.st[out.slots[j]].z;
           z[r0] = y0;
           if (has1) z[r1] = y1;
         }

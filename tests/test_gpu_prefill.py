@@ -1,0 +1,80 @@
+"""GPU tests of the encoder's chunked prefill, through the C ABI.
+
+With prefill_rows set, the encoder runs the model over m positions of every
+stream in one forward pass (between window slides) and then the per-token
+vocabulary passes in order.  Every row's arithmetic is the decode step's, so
+the coder intervals must equal, bit for bit, those of one position per step,
+and a container written with prefill must decode one position per step.
+"""
+import dataclasses
+
+import numpy as np
+import pytest
+import torch
+
+import synthetic as S
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def nc(gpu_lib):
+    return gpu_lib
+
+
+def intervals(nc, shape, w, fmt, path, toks, prefill_rows, max_streams):
+    lens = np.array([len(t) for t in toks], dtype=np.int64)
+    offs = np.concatenate([[0], np.cumsum(lens)[:-1]]).astype(np.int64)
+    flat = torch.from_numpy(np.concatenate(toks).astype(np.int32)).cuda()
+    stride = max(int(lens.max()), 1)
+    ctx = nc.Context(nc.make_config(shape, fmt=fmt, path=path, warmup=20, max_streams=max_streams,
+                                    prefill_rows=prefill_rows), w)
+    iv = torch.full((len(toks), stride, 2), -1, dtype=torch.int32, device="cuda")
+    ctx.encode_intervals(flat, offs, lens, iv, stride)
+    out = iv.cpu().numpy()
+    ctx.close()
+    return out
+
+
+@pytest.mark.parametrize("fmt,path", [("fp32", "gemv"), ("bf16", "gemv"), ("bf16", "tc"), ("fp8", "tc")])
+def test_prefill_intervals_equal_decode(nc, fmt, path):
+    """Small model (window 512, slide 128): three ragged streams, one
+    crossing four slides; prefill chunks of 64 positions (3 streams, 256
+    rows) and of 128 (1 stream) give the decode intervals exactly."""
+    shape, seed = S.SMALL, 6
+    w = S.flat_weights(shape, seed)
+    toks = [S.token_stream(seed, j, n, shape.vocab) for j, n in enumerate([1000, 130, 1])]
+    ref = intervals(nc, shape, w, fmt, path, toks, 0, 3)
+    got = intervals(nc, shape, w, fmt, path, toks, 256, 3)
+    assert np.array_equal(got, ref)
+    one = intervals(nc, shape, w, fmt, path, toks[:1], 1024, 1)
+    assert np.array_equal(one[0], ref[0])
+
+
+def test_prefill_full_model_single_stream(nc):
+    """Full-size BF16 model, one 700-token stream: a 512-position prefill
+    chunk then a partial one give the decode intervals exactly."""
+    shape, seed = S.FULL, 1
+    w = S.flat_weights(shape, seed)
+    toks = [S.token_stream(seed, 0, 700, shape.vocab)]
+    ref = intervals(nc, shape, w, "bf16", "gemv", toks, 0, 1)
+    got = intervals(nc, shape, w, "bf16", "gemv", toks, 4096, 1)
+    assert np.array_equal(got, ref)
+
+
+def test_prefill_container_decodes_per_position(nc):
+    """A container written with prefill decodes, one position per step, to
+    the original streams; it is byte-identical to the one written without."""
+    shape, seed = dataclasses.replace(S.SMALL, ctx_len=256, slide=64), 7
+    w = S.flat_weights(shape, seed)
+    streams = [S.token_stream(seed, 20 + j, n, shape.vocab) for j, n in enumerate([400, 0, 65, 3])]
+    enc = nc.Context(nc.make_config(shape, fmt="bf16", warmup=10, max_streams=4, prefill_rows=128), w)
+    blob = enc.encode(streams)
+    enc.close()
+    dec = nc.Context(nc.make_config(shape, fmt="bf16", warmup=10, max_streams=4), w)
+    plain = dec.encode(streams)
+    back = dec.decode(blob)
+    dec.close()
+    assert blob == plain
+    for a, b in zip(streams, back):
+        assert np.array_equal(a, b)
