@@ -34,10 +34,16 @@ import synthetic as S  # noqa: E402
 # position) rows per forward pass (0: one position per step).  It changes no
 # coded bit; the decoder always steps one position at a time.
 WORKLOADS = {
-    # one stream, the full-size model in BF16 (the headline configuration)
-    "full_bf16_single": dict(shape=S.FULL, fmt="bf16", seed=1, n_streams=1, length=8192, path="gemv",
+    # one stream, the full-size model in BF16 weights (the headline
+    # configuration): tensor-core path, encoder prefill of 512 positions
+    "full_bf16_single": dict(shape=S.FULL, fmt="bf16", seed=1, n_streams=1, length=8192, path="tc",
                              prefill_rows=4096),
-    # the same, one position per model step (what the decoder runs)
+    # the same, one position per model step (what its decoder runs)
+    "full_bf16_single_tc_stepwise": dict(shape=S.FULL, fmt="bf16", seed=1, n_streams=1, length=8192, path="tc",
+                                         prefill_rows=0),
+    # the CUDA-core GEMV path (FP32 activations), with and without prefill
+    "full_bf16_single_gemv": dict(shape=S.FULL, fmt="bf16", seed=1, n_streams=1, length=8192, path="gemv",
+                                  prefill_rows=4096),
     "full_bf16_single_stepwise": dict(shape=S.FULL, fmt="bf16", seed=1, n_streams=1, length=8192, path="gemv",
                                       prefill_rows=0),
     # the plain single-stream FP32 path (the denominator of "batched vs plain")
@@ -53,6 +59,10 @@ WORKLOADS = {
                                 cap=512, path="tc", prefill_rows=4096),
     "batched_bf16_tc_512_stepwise": dict(shape=S.FULL, fmt="bf16", seed=2, n_streams=256, lengths=(512, 16384),
                                          cap=512, path="tc", prefill_rows=0),
+    # a small case of the batched prefill for profiling: 32 streams x 256
+    # tokens, 4,096 forward rows (128 positions per stream), 1.5 GB of KV
+    "prof_tc_32x256": dict(shape=S.FULL, fmt="bf16", seed=2, n_streams=32, length=256, path="tc",
+                           prefill_rows=4096),
     # FP8 E4M3 weights, 1,024 streams x 4,096 tokens (first 256 tokens per stream)
     "fp8_tc_1024_256": dict(shape=S.FULL, fmt="fp8", seed=4, n_streams=1024, length=4096, cap=256, path="tc",
                             prefill_rows=4096),
@@ -373,7 +383,8 @@ def run_gpu(args, wl):
         line = {
             "metric": "tokens/s compressed", "value": value, "unit": "tokens/s", "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "bf16" if wl.get("path", "gemv") == "tc" else "f32",
             "data": "synthetic",
             "config": {"workload": args.workload, "model": "smollm2-135m-shape random-init",
                        "weights": wl["fmt"], "streams_per_gpu": wl["n_streams"],
@@ -439,7 +450,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--tokens", type=int, default=0,
                     help="cut every stream to this many tokens (short runs for profiling)")
-    ap.add_argument("--extra", nargs="*", default=["full_bf16_single_stepwise", "batched_bf16_tc_512"],
+    ap.add_argument("--extra", nargs="*",
+                    default=["full_bf16_single_tc_stepwise", "full_bf16_single_stepwise", "batched_bf16_tc_512"],
                     help="further workloads timed once each and reported under 'extra'")
     args = ap.parse_args()
     wl = WORKLOADS[args.workload]

@@ -975,8 +975,8 @@ extern "C" int nc_update_bias(nc_ctx* ctx, int n, const int32_t* stream_ids, con
   Batch b = make_batch(ctx);
   VocabIO io{};
   io.update = 1;
+  io.ngram = 1;
   NC_TRY(launch_vocab(ctx->D, b, io, ctx->stream));
-  NC_TRY(launch_ngram_update(ctx->D, b, ctx->stream));
   st = check_status(ctx, si);
   if (st != NC_OK) return st;
   for (int j = 0; j < n; ++j) {
@@ -1051,16 +1051,18 @@ static int encode_prefill(nc_ctx* ctx, int n, int m, const int32_t* tok_dev, con
   f.pos = ctx->f_pos;
   f.tok = ctx->f_tok;
   f.z_out = ctx->zrows;
+  f.pm = m;
   VocabIO io{};
   io.predict = 1;
   io.update = 1;
+  io.ngram = 1;
   io.intervals = intervals;
   io.interval_stride = stride;
   StepMarks mk;
   mk.on = trace != nullptr;
   const int fwd_marks = 1 + 1 + 5 * D.n_layers + 1;   // prepare, embed, 5 per layer, LM head
   if (mk.on) {
-    mk.ev.resize(fwd_marks + 2 * m + 2);
+    mk.ev.resize(fwd_marks + m + 2);
     for (auto& e : mk.ev) NC_TRY(cudaEventCreate(&e));
   }
   auto one_chunk = [&]() -> cudaError_t {
@@ -1078,8 +1080,6 @@ static int encode_prefill(nc_ctx* ctx, int n, int m, const int32_t* tok_dev, con
       br.z_idx = ctx->d_zidx;
       e = launch_vocab(D, br, io, s);
       if (e == cudaSuccess) e = mk.mark(s, TK_VOCAB);
-      if (e == cudaSuccess) e = launch_ngram_update(D, br, s);
-      if (e == cudaSuccess) e = mk.mark(s, TK_NGRAM);
     }
     return e;
   };
@@ -1131,7 +1131,7 @@ static int encode_prefill(nc_ctx* ctx, int n, int m, const int32_t* tok_dev, con
         const int kd = mk.kind[i];
         double by = fwd[kd];
         if (i >= fwd_marks) {
-          const int64_t a = p + (i - fwd_marks) / 2;
+          const int64_t a = p + (i - fwd_marks);
           int act = 0;
           for (int j = 0; j < n; ++j) act += lens_h[j] > a;
           double per[TK_COUNT];
@@ -1169,6 +1169,7 @@ static int encode_device(nc_ctx* ctx, int n, const std::vector<int>& slot_of, co
   VocabIO io{};
   io.predict = 1;
   io.update = 1;
+  io.ngram = 1;
   io.intervals = intervals;
   io.interval_stride = stride;
   StepMarks mk;
@@ -1184,8 +1185,6 @@ static int encode_device(nc_ctx* ctx, int n, const std::vector<int>& slot_of, co
     if (e == cudaSuccess) e = launch_model(ctx, b, &mk);
     if (e == cudaSuccess) e = launch_vocab(D, b, io, s);
     if (e == cudaSuccess) e = mk.mark(s, TK_VOCAB);
-    if (e == cudaSuccess) e = launch_ngram_update(D, b, s);
-    if (e == cudaSuccess) e = mk.mark(s, TK_NGRAM);
     return e;
   };
   // capture one step in a graph (the whole step is device-driven)
@@ -1533,8 +1532,8 @@ extern "C" int nc_decode(nc_ctx* ctx, const uint8_t* in, size_t nbytes, int32_t*
       if (e == cudaSuccess) e = launch_search(b, D.V, ctx->cdf, ctx->d_target, ctx->d_obs, ctx->d_lohi, s);
       VocabIO up{};
       up.update = 1;
+      up.ngram = 1;
       if (e == cudaSuccess) e = launch_vocab(D, b, up, s);
-      if (e == cudaSuccess) e = launch_ngram_update(D, b, s);
       if (e == cudaSuccess) e = cudaMemcpyAsync(ctx->h_u32 + n, ctx->d_lohi, (size_t)active * 8, cudaMemcpyDeviceToHost, s);
       if (e == cudaSuccess) e = cudaMemcpyAsync(ctx->h_i32 + 1 + 2 * ctx->cfg.max_streams, ctx->d_obs, (size_t)active * 4,
                                                 cudaMemcpyDeviceToHost, s);

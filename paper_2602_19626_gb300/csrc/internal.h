@@ -107,6 +107,7 @@ struct Batch {
   const int32_t* pos;
   const int32_t* tok;
   float* z_out;
+  int pm;                   // rows j m .. j m + m - 1 are stream j's consecutive positions
   // Vocabulary pass after a prefill: row j's logits are z_in + z_idx[j] V
   // (nullptr: the stream's own z).  The pass then reads nothing before its
   // wait on the previous kernel.
@@ -189,9 +190,9 @@ struct VocabIO {
   float* probe_p;
   int predict;              // quantise (and write cdf / intervals)
   int update;               // apply head + mixer update with b.obs
+  int ngram;                // with update: also the N-gram update and the stream's bookkeeping
 };
 cudaError_t launch_vocab(const Dims& D, const Batch& b, const VocabIO& io, cudaStream_t s);
-cudaError_t launch_ngram_update(const Dims& D, const Batch& b, cudaStream_t s);
 cudaError_t launch_prepare_encode(const Batch& b, int n_streams, const int32_t* tok_flat,
                                   const int64_t* offs, const int64_t* lens, int32_t* obs,
                                   int32_t* nB, cudaStream_t s);

@@ -117,7 +117,10 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-__device__ __forceinline__ float silu(float a) { return a / (1.0f + expf(-a)); }
+// SiLU of the tensor-core path: a * (1 / (1 + e^-a)) with the fast exponential
+// and a correctly rounded reciprocal (1 / inf = 0 for very negative a).  The
+// decode step and the prefill forward run this same code.
+__device__ __forceinline__ float silu_tc(float a) { return a * __frcp_rn(1.0f + __expf(-a)); }
 
 template <int BN>
 __host__ __device__ constexpr uint32_t tmem_cols() {
@@ -150,8 +153,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   constexpr uint32_t kCols = tmem_cols<BN>();
   constexpr uint32_t kStageBytes = (kTileM + BN) * kKBlockBytes;
 
-  pdl_wait();
-  pdl_trigger();
+  // the row count was written by the step's prepare kernel, several launches
+  // back, so it may be read before the wait on the previous kernel
   const int B = *g.nB;
   if (n0 >= B) return;                            // uniform across the CTA
   if (threadIdx.x == 0) {
@@ -174,18 +177,31 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   const uint32_t tmem = *tmem_slot;
   const bool active = true;
 
+  // weight tiles of the first stages do not depend on the previous kernel:
+  // in flight before waiting on it; the operand tiles only after
+  if (threadIdx.x == 0) {
+    for (int kb = 0; kb < nk && kb < STAGES; ++kb) {
+      mbar_expect_tx(full + kb, kStageBytes);
+      tma_load_2d(sA + (size_t)kb * kTileM * kKBlockBytes, &tA, full + kb, kb * kblk, m0);
+    }
+  }
+  pdl_wait();
+  pdl_trigger();
+
   if (active && threadIdx.x == 0) {
     // TMA producer
     for (int kb = 0; kb < nk; ++kb) {
       const int s = kb % STAGES;
       const uint32_t ph = (uint32_t)(kb / STAGES) & 1u;
-      if (kb >= STAGES && !mbar_wait(empty + s, ph ^ 1u)) {
-        atomicOr(fail, 1u);
-        break;
-      }
-      mbar_expect_tx(full + s, kStageBytes);
       const int kc = kb * kblk;
-      tma_load_2d(sA + (size_t)s * kTileM * kKBlockBytes, &tA, full + s, kc, m0);
+      if (kb >= STAGES) {
+        if (!mbar_wait(empty + s, ph ^ 1u)) {
+          atomicOr(fail, 1u);
+          break;
+        }
+        mbar_expect_tx(full + s, kStageBytes);
+        tma_load_2d(sA + (size_t)s * kTileM * kKBlockBytes, &tA, full + s, kc, m0);
+      }
       tma_load_2d(sB + (size_t)s * BN * kKBlockBytes, &tB, full + s, kc, n0);
     }
   } else if (active && threadIdx.x == 32) {
@@ -228,22 +244,31 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     for (int c = 0; c < BN; c += 16) {
       float v[16];
       tmem_ld16(tw + (uint32_t)c, v);
+      // loads of this 16-column group first (row scales, residuals), so
+      // they are in flight together
+      float xs[16], res[16];
+#pragma unroll
+      for (int i = 0; i < 16; ++i) {
+        const int n = n0 + c + i;
+        xs[i] = (!KIND_BF16 && n < B) ? __ldg(g.x_scale + n) : 0.f;
+        res[i] = (EPI == EPI_RESID && n < B && r < g.M) ? __ldcg(g.y + (size_t)n * g.M + r) : 0.f;
+      }
 #pragma unroll
       for (int i = 0; i < 16; ++i) {
         const int n = n0 + c + i;
         float y = v[i];
-        if (!KIND_BF16) y *= ws * (n < B ? g.x_scale[n] : 0.f);
+        if (!KIND_BF16) y *= ws * xs[i];
         if (EPI == EPI_SWIGLU) {
           const float up = __shfl_xor_sync(0xffffffffu, y, 1);   // rows 2j (gate), 2j + 1 (up)
           if (n < B && r < g.M && (r & 1) == 0) {
-            const float h = silu(y) * up;
+            const float h = silu_tc(y) * up;
             g.h_out[(size_t)n * (g.M / 2) + (r >> 1)] = h;
           }
         } else if (n < B && r < g.M) {
           if (EPI == EPI_STORE) {
             g.y[(size_t)n * g.M + r] = y;
           } else if (EPI == EPI_RESID) {
-            g.y[(size_t)n * g.M + r] += y;
+            g.y[(size_t)n * g.M + r] = res[i] + y;
           } else {
             if (g.zrows)
               g.zrows[(size_t)n * g.M + r] = y;

@@ -68,6 +68,35 @@ __global__ void __launch_bounds__(kGemvThreads) k_gemv(Dims D, Batch b, Mat m, G
 }
 
 // ----------------------------------------------------------------- attention
+// Merge of a query's nc chunk partials in chunk order into its output dims
+// (kDims per head, head h at out + h * 64): M = max of the chunk maxima, then
+// sum and accumulator weighted by exp(m_c - M), the factor computed once per
+// (head, chunk).  No chunk (a row past a stream's end) writes zeros.
+template <typename Sm, int KD>
+__device__ void merge_chunks(Sm& sm, const float (*rm)[kMaxGroup], const float (*rl)[kMaxGroup],
+                             const float (*racc)[kMaxGroup][KD], int nc, int grp, int tid, float* out) {
+  if (tid < grp) {
+    const int h = tid;
+    float M = -INFINITY;
+    for (int c = 0; c < nc; ++c) M = fmaxf(M, rm[c][h]);
+    float l = 0.f;
+    for (int c = 0; c < nc; ++c) {
+      const float f = expf(rm[c][h] - M);
+      sm.mf[h][c] = f;
+      l = fmaf(rl[c][h], f, l);
+    }
+    sm.mL[h] = l;
+  }
+  __syncthreads();
+  for (int e = tid; e < grp * KD; e += kAttnThreads) {
+    const int h = e / KD, dl = e % KD;
+    float o = 0.f;
+    for (int c = 0; c < nc; ++c) o = fmaf(racc[c][h][dl], sm.mf[h][c], o);
+    out[h * kHeadDim + dl] = nc ? o / sm.mL[h] : 0.f;
+  }
+  __syncthreads();
+}
+
 // One cluster of S CTAs per (stream row, KV head).  CTA `rank` owns chunks
 // rank, rank + S, ...; the loads of its first chunk do not depend on the
 // QKV projection and are issued before waiting on it.  The owner of a chunk
@@ -119,26 +148,106 @@ __global__ void __launch_bounds__(kAttnThreads) k_attn(Dims D, Batch b, int laye
     const int c_lo = start + c * kAttnChunk;
     const int c_end = min(c_lo + kAttnChunk, a + 1);
     if (c != rank) attn_load<KBF16>(D, st, layer, g, c_lo + warp * 32, c_end, a, lane, pre);
-    attn_chunk<KBF16, S>(D, c, c_lo, c_end, a, tid, sm, pre, dst);
+    attn_chunk<KBF16>(D, c_lo, c_end, a, tid, sm, sm, pre, [&](int h, int dd, float o, float M, float l) {
+      constexpr int kDims = AttnSmem<S>::kDims;
+      AttnSmem<S>* r = dst(dd / kDims);
+      r->racc[c][h][dd % kDims] = o;
+      if (dd % kDims == 0) {
+        r->rm[c][h] = M;
+        r->rl[c][h] = l;
+      }
+    });
   }
   if (S > 1) cg::this_cluster().sync();            // every chunk's partial has arrived
   constexpr int kDims = AttnSmem<S>::kDims;
-  for (int e = tid; e < grp * kDims; e += kAttnThreads) {
-    const int h = e / kDims, dl = e % kDims;
-    float M = -INFINITY;
-#pragma unroll
-    for (int c = 0; c < kAttnMaxChunks; ++c)
-      if (c < nc) M = fmaxf(M, sm.rm[c][h]);
-    float l = 0.f, o = 0.f;
-#pragma unroll
-    for (int c = 0; c < kAttnMaxChunks; ++c) {
-      if (c < nc) {
-        const float f = expf(sm.rm[c][h] - M);
-        l = fmaf(sm.rl[c][h], f, l);
-        o = fmaf(sm.racc[c][h][dl], f, o);
-      }
+  merge_chunks(sm, sm.rm, sm.rl, sm.racc, nc, grp, tid,
+               io.attn_out + (size_t)j * D.hq * kHeadDim + g * grp * kHeadDim + rank * kDims);
+}
+
+// ------------------------------------------------------ prefill attention
+// Query side of one prefill row: its rotation, rotated and scaled query
+// heads, and the fed token's k and v.
+struct RowQ {
+  float qs[kMaxGroup][kHeadDim];
+  float kn[kHeadDim], vn[kHeadDim];
+  float cs[kHeadDim / 2], sn[kHeadDim / 2];
+};
+
+constexpr int kRowsMax = 8;                         // query rows per CTA
+
+template <int S>
+struct RowsSmem {
+  static constexpr int kDims = kHeadDim / S;
+  RowQ q[kRowsMax];
+  float wm[kAttnWarps][kMaxGroup], wl[kAttnWarps][kMaxGroup];
+  float wacc[kAttnWarps][kMaxGroup][kHeadDim];
+  float we[kAttnWarps][kMaxGroup][32];
+  float cf[kMaxGroup][kAttnWarps], cM[kMaxGroup], cL[kMaxGroup];
+  float mf[kMaxGroup][kAttnMaxChunks], mL[kMaxGroup];
+  float rm[kRowsMax][kAttnMaxChunks][kMaxGroup], rl[kRowsMax][kAttnMaxChunks][kMaxGroup];
+  float racc[kRowsMax][kAttnMaxChunks][kMaxGroup][kDims];
+};
+
+// Prefill attention of rq consecutive rows of one stream (consecutive
+// positions, one window start) and one KV head.  Each warp loads the keys
+// and values of its 32 positions of a chunk once and runs every row's block
+// computation on them (the row's own position in FP32, later positions
+// masked); chunks are split over a cluster of S CTAs and merged per row in
+// chunk order.  Each row's output is the decode attention's, bit for bit.
+template <int KBF16, int S>
+__global__ void __launch_bounds__(kAttnThreads, 2) k_attn_rows(Dims D, Batch b, int layer, int rq, AttnIO io) {
+  extern __shared__ float4 dyn4[];
+  RowsSmem<S>& sm = *reinterpret_cast<RowsSmem<S>*>(dyn4);
+  const int rank = S > 1 ? (int)cg::this_cluster().block_rank() : 0;
+  const int g = blockIdx.y, i0 = blockIdx.z * rq;
+  if (i0 >= *b.nB) return;                         // uniform across the cluster
+  if (S > 1) asm volatile("barrier.cluster.arrive.relaxed.aligned;" ::: "memory");
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int grp = D.hq / D.hkv;
+  constexpr int kDims = RowsSmem<S>::kDims;
+  StreamDev& st = b.st[b.slots[i0]];
+  int a_max = -1;
+  for (int r = 0; r < rq; ++r) a_max = max(a_max, b.pos[i0 + r]);
+  pdl_wait();                                      // the append pass wrote this chunk of positions
+  pdl_trigger();
+  const int start = window_start_at(D, max(a_max, 0));
+  const int nc_max = a_max < 0 ? 0 : (a_max - start) / kAttnChunk + 1;
+  for (int r = 0; r < rq; ++r) {
+    const int a = b.pos[i0 + r];
+    if (a < 0) continue;                           // uniform across the CTA
+    attn_rope(D, a, tid, sm.q[r]);
+    attn_qkv<KBF16>(D, st, layer, i0 + r, g, a, false, tid, sm.q[r], io);
+  }
+  auto dst = [&](int rk) -> RowsSmem<S>* {
+    if (S == 1) return &sm;
+    return cg::this_cluster().map_shared_rank(&sm, rk);
+  };
+  if (S > 1) asm volatile("barrier.cluster.wait.aligned;" ::: "memory");
+  for (int c = rank; c < nc_max; c += S) {
+    const int c_lo = start + c * kAttnChunk;
+    AttnPre<KBF16> pre;
+    attn_load<KBF16>(D, st, layer, g, c_lo + warp * 32, min(c_lo + kAttnChunk, a_max + 1), a_max + 1, lane, pre);
+    for (int r = 0; r < rq; ++r) {
+      const int a = b.pos[i0 + r];
+      if (a < 0 || c > (a - start) / kAttnChunk) continue;   // uniform across the CTA
+      attn_chunk<KBF16>(D, c_lo, min(c_lo + kAttnChunk, a + 1), a, tid, sm.q[r], sm, pre,
+                        [&](int h, int dd, float o, float M, float l) {
+                          RowsSmem<S>* t = dst(dd / kDims);
+                          t->racc[r][c][h][dd % kDims] = o;
+                          if (dd % kDims == 0) {
+                            t->rm[r][c][h] = M;
+                            t->rl[r][c][h] = l;
+                          }
+                        });
     }
-    io.attn_out[(size_t)j * D.hq * kHeadDim + (g * grp + h) * kHeadDim + rank * kDims + dl] = o / l;
+  }
+  if (S > 1) cg::this_cluster().sync();            // every chunk's partial has arrived
+  else __syncthreads();
+  for (int r = 0; r < rq; ++r) {
+    const int a = b.pos[i0 + r];
+    const int nc = a < 0 ? 0 : (a - start) / kAttnChunk + 1;
+    merge_chunks(sm, sm.rm[r], sm.rl[r], sm.racc[r], nc, grp, tid,
+                 io.attn_out + (size_t)(i0 + r) * D.hq * kHeadDim + g * grp * kHeadDim + rank * kDims);
   }
 }
 
@@ -276,11 +385,24 @@ static cudaError_t prepare_gemv_f(int cmax) {
   return e;
 }
 
+template <int S>
+static cudaError_t prepare_rows_s() {
+  cudaError_t e = cudaFuncSetAttribute(k_attn_rows<1, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)sizeof(RowsSmem<S>));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_attn_rows<0, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(RowsSmem<S>));
+  return e;
+}
+
 cudaError_t prepare_model_kernels(const Dims& D, int fmt) {
   const int cmax = std::max(std::max(D.d, D.hq * kHeadDim), D.F);
   cudaError_t e = fmt == NC_FP32 ? prepare_gemv_f<NC_FP32>(cmax)
                   : fmt == NC_BF16 ? prepare_gemv_f<NC_BF16>(cmax)
                                    : prepare_gemv_f<NC_FP8E4M3>(cmax);
+  if (e == cudaSuccess) e = prepare_rows_s<1>();
+  if (e == cudaSuccess) e = prepare_rows_s<2>();
+  if (e == cudaSuccess) e = prepare_rows_s<4>();
+  if (e == cudaSuccess) e = prepare_rows_s<8>();
   return e;
 }
 
@@ -300,8 +422,40 @@ static int attn_split(const Dims& D, const Batch& b) {
   return S;
 }
 
+template <int S>
+static size_t rows_smem() {
+  return sizeof(RowsSmem<S>);
+}
+
+template <int S>
+static cudaError_t launch_attn_rows_s(const Dims& D, const Batch& b, int layer, int rq, const AttnIO& io,
+                                      cudaStream_t s) {
+  dim3 grid(S, D.hkv, b.Bmax / rq);
+  return launch_kernel_cluster(D.kv_bf16 ? k_attn_rows<1, S> : k_attn_rows<0, S>, grid, dim3(kAttnThreads),
+                               rows_smem<S>(), s, D.pdl, S, D, b, layer, rq, io);
+}
+
+// Prefill rows (b.pm consecutive positions per stream): rq rows per CTA
+// group, S CTAs per group as for decode.
+static cudaError_t launch_attn_rows(const Dims& D, const Batch& b, int layer, const AttnIO& io, cudaStream_t s) {
+  const int rq = std::min(kRowsMax, b.pm);
+  int S = 8;
+  if (D.attn_cluster) S = D.attn_cluster;
+  else
+    while (S > 1 && (int64_t)D.hkv * (b.Bmax / rq) * S > 4 * (int64_t)D.n_sm) S /= 2;
+  switch (S) {
+    case 1: return launch_attn_rows_s<1>(D, b, layer, rq, io, s);
+    case 2: return launch_attn_rows_s<2>(D, b, layer, rq, io, s);
+    case 4: return launch_attn_rows_s<4>(D, b, layer, rq, io, s);
+    case 8: return launch_attn_rows_s<8>(D, b, layer, rq, io, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
 cudaError_t launch_attn(const Dims& D, const Batch& b, int layer, const float* qkv, float* attn_out,
                         cudaStream_t s) {
+  if (b.pos && b.pm >= 2 && b.pm % 2 == 0 && b.Bmax % std::min(kRowsMax, b.pm) == 0)
+    return launch_attn_rows(D, b, layer, AttnIO{qkv, attn_out}, s);
   const int S = attn_split(D, b);
   dim3 grid(S, D.hkv, b.Bmax);
   AttnIO io{qkv, attn_out};

@@ -87,7 +87,7 @@ struct VocabShared {
   uint32_t cl_total;
   float cl_obs[3];          // p_tilde(t*), p_ng(t*), log p_tilde(t*) (owner CTA of t*)
   // N-gram coefficients of this step
-  float cu, coef[kMaxOrder];
+  float cu, coef[kMaxOrder], nk[kMaxOrder];
   const NgEntry* ent[kMaxOrder];
 };
 
@@ -329,6 +329,8 @@ __device__ void scan_round(const uint32_t (&c)[E], int v0, int V, uint32_t T, ui
 // observed token.  Both may run in one pass (encoder) or in two (decoder,
 // which learns the token in between); the arithmetic is the same in either
 // case.
+__device__ void ngram_update_row(const Dims& D, const Batch& b, int j, int warp, int lane);
+
 template <int E>
 __global__ void __cluster_dims__(kVocabCluster, 1, 1) __launch_bounds__(kVocabThreads)
     k_vocab(Dims D, Batch b, VocabIO io) {
@@ -362,16 +364,41 @@ __global__ void __cluster_dims__(kVocabCluster, 1, 1) __launch_bounds__(kVocabTh
   // N-gram: P = A (c + 1) / (N + V) + sum_k beta_k cnt_k / n_k, the closed
   // form of the interpolation recursion with lambda_k = n_k / (n_k + 5).
   float png[E];
+  int cnt[E];
+  // logits: after a prefill they are final already (the wait came first)
+  float s[E];
+  if (b.z_in) load_run<E>(b.z_in + (size_t)b.z_idx[j] * V, v0, V, s, -INFINITY);
   const bool ngram = D.order > 0;
   if (ngram) {
+    // unigram counts first: independent of the context entries below
+    if (v0 + E <= V && (reinterpret_cast<uintptr_t>(st.uni + v0) & 15) == 0) {
+      const int4* u4 = reinterpret_cast<const int4*>(st.uni + v0);
+#pragma unroll
+      for (int q = 0; q < E / 4; ++q) {
+        const int4 u = u4[q];
+        cnt[4 * q] = u.x;
+        cnt[4 * q + 1] = u.y;
+        cnt[4 * q + 2] = u.z;
+        cnt[4 * q + 3] = u.w;
+      }
+    } else {
+#pragma unroll
+      for (int i = 0; i < E; ++i) cnt[i] = (v0 + i < V) ? st.uni[v0 + i] : 0;
+    }
+    // the orders' context entries and counts, one thread each
+    if (threadIdx.x < kMaxOrder) {
+      const int k = threadIdx.x;
+      const int ei = (k < D.order) ? st.ctx_ent[k] : -1;
+      const NgEntry* en = ei >= 0 ? st.ent[k] + ei : nullptr;
+      sh.ent[k] = en;
+      sh.nk[k] = en ? (float)en->n : 0.f;
+    }
+    __syncthreads();
     if (threadIdx.x == 0) {
       float lam[kMaxOrder], nk[kMaxOrder];
       for (int k = 0; k < kMaxOrder; ++k) {
-        const int ei = (k < D.order) ? st.ctx_ent[k] : -1;
-        const NgEntry* en = ei >= 0 ? st.ent[k] + ei : nullptr;
-        sh.ent[k] = en;
-        nk[k] = en ? (float)en->n : 0.f;
-        lam[k] = en ? nk[k] / (nk[k] + 5.0f) : 0.f;
+        nk[k] = sh.nk[k];
+        lam[k] = sh.ent[k] ? nk[k] / (nk[k] + 5.0f) : 0.f;
       }
       float A = 1.f;
       for (int k = 0; k < kMaxOrder; ++k) A *= (1.f - lam[k]);
@@ -395,21 +422,6 @@ __global__ void __cluster_dims__(kVocabCluster, 1, 1) __launch_bounds__(kVocabTh
       }
       __syncthreads();
     }
-    int cnt[E];
-    if (v0 + E <= V && (reinterpret_cast<uintptr_t>(st.uni + v0) & 15) == 0) {
-      const int4* u4 = reinterpret_cast<const int4*>(st.uni + v0);
-#pragma unroll
-      for (int q = 0; q < E / 4; ++q) {
-        const int4 u = u4[q];
-        cnt[4 * q] = u.x;
-        cnt[4 * q + 1] = u.y;
-        cnt[4 * q + 2] = u.z;
-        cnt[4 * q + 3] = u.w;
-      }
-    } else {
-#pragma unroll
-      for (int i = 0; i < E; ++i) cnt[i] = (v0 + i < V) ? st.uni[v0 + i] : 0;
-    }
     const float cu = sh.cu;
 #pragma unroll
     for (int i = 0; i < E; ++i) png[i] = (v0 + i < V) ? cu * (float)(cnt[i] + 1) + sp[threadIdx.x * E + i] : 0.f;
@@ -428,8 +440,7 @@ __global__ void __cluster_dims__(kVocabCluster, 1, 1) __launch_bounds__(kVocabTh
   if (io.probe_png && ngram) store_run<E>(io.probe_png + (size_t)j * V, v0, V, png);
 
   // ---- biased logits s = z / tau + b and their softmax (round 1)
-  float s[E];
-  load_run<E>(b.z_in ? b.z_in + (size_t)b.z_idx[j] * V : st.z, v0, V, s, -INFINITY);
+  if (!b.z_in) load_run<E>(st.z, v0, V, s, -INFINITY);
   if (io.probe_z) store_run<E>(io.probe_z + (size_t)j * V, v0, V, s);
 #pragma unroll
   for (int i = 0; i < E; ++i) s[i] = (v0 + i < V) ? __fdiv_rn(s[i], D.tau) + bias[i] : -INFINITY;
@@ -514,6 +525,9 @@ __global__ void __cluster_dims__(kVocabCluster, 1, 1) __launch_bounds__(kVocabTh
     }
   }
   cl.sync();   // keep this CTA's shared memory alive until the cluster has read it
+  // the N-gram update and bookkeeping of this row, once every CTA has read
+  // the stream's state
+  if (io.update && io.ngram && rank == 0) ngram_update_row(D, b, j, threadIdx.x >> 5, threadIdx.x & 31);
 }
 
 // --------------------------------------------------------------- N-gram tables
@@ -548,7 +562,7 @@ __device__ int ng_find(StreamDev& st, int k, unsigned long long key, bool insert
       if (!insert) return -1;
       const int ei = st.n_ent[k];
       if (ei >= st.max_len) {
-        st.status |= ST_TABLE_FULL;
+        atomicOr(&st.status, ST_TABLE_FULL);
         return -1;
       }
       st.n_ent[k] = ei + 1;
@@ -560,79 +574,93 @@ __device__ int ng_find(StreamDev& st, int k, unsigned long long key, bool insert
     }
     h = (h + 1) & st.cap_mask;
   }
-  if (insert) st.status |= ST_TABLE_FULL;
+  if (insert) atomicOr(&st.status, ST_TABLE_FULL);
   return -1;
 }
 
 // One warp per stream: count the observed token in every context order,
 // the unigram counts, then advance the stream (window, history, position) and
 // look up the contexts of the next prediction.
-__global__ void k_ngram_update(Dims D, Batch b) {
-  pdl_wait();
-  pdl_trigger();
-  const int j = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  if (j >= *b.nB) return;
-  StreamDev& st = b.st[b.slots[j]];
-  const int t = b.obs[j];
-  if (t < 0 || t >= D.V) {
-    if (lane == 0) st.status |= ST_BAD_TOKEN;
-    return;
-  }
-  const int nh = min(3, st.n_coded);
-  for (int k = 0; k < min(D.order, nh); ++k) {
+// The N-gram update of row j and the stream's bookkeeping for the next step.
+// Warp k (k < 3) owns order k: it counts the observed token t in the entry
+// of the context of length k + 1 (inserting the context if new), then looks
+// up the entry of the next context (t appended) for the next prediction.
+// The orders use separate tables, so the warps run concurrently; within an
+// order the lookup follows the update.  Warp 0 also updates the unigram
+// counts and the stream's position, history and window start.
+__device__ void ngram_update_order(const Dims& D, StreamDev& st, int t, int k, int lane) {
+  const int nh = min(3, st.n_coded);               // contexts before t
+  if (k < D.order && k < nh) {
     int ei = 0;
     if (lane == 0) ei = ng_find(st, k, ctx_key(st.hist, k + 1), true);
     ei = __shfl_sync(0xffffffffu, ei, 0);
-    if (ei < 0) continue;
-    NgEntry& en = st.ent[k][ei];
-    const int ns = en.nslots;
-    int hit = -1;
-    for (int q = lane; q < ns; q += 32)
-      if (en.tok[q] == t) hit = q;
-    unsigned m = __ballot_sync(0xffffffffu, hit >= 0);
-    if (m) {
-      const int src = __ffs(m) - 1;
-      const int q = __shfl_sync(0xffffffffu, hit, src);
-      if (lane == 0) {
-        en.cnt[q] += 1;
-        en.n += 1;
-      }
-    } else if (ns < kMaxSlots) {
-      if (lane == 0) {
-        en.tok[ns] = t;
-        en.cnt[ns] = 1;
-        en.nslots = ns + 1;
-        en.n += 1;
-      }
-    } else {
-      // evict the lowest count, lowest slot index on ties
-      int bc = 0x7fffffff, bi = 0x7fffffff;
-      for (int q = lane; q < kMaxSlots; q += 32) {
-        const int cq = en.cnt[q];
-        if (cq < bc || (cq == bc && q < bi)) {
-          bc = cq;
-          bi = q;
+    if (ei >= 0) {
+      NgEntry& en = st.ent[k][ei];
+      const int ns = en.nslots;
+      int hit = -1;
+      for (int q = lane; q < ns; q += 32)
+        if (en.tok[q] == t) hit = q;
+      unsigned m = __ballot_sync(0xffffffffu, hit >= 0);
+      if (m) {
+        const int src = __ffs(m) - 1;
+        const int q = __shfl_sync(0xffffffffu, hit, src);
+        if (lane == 0) {
+          en.cnt[q] += 1;
+          en.n += 1;
         }
-      }
+      } else if (ns < kMaxSlots) {
+        if (lane == 0) {
+          en.tok[ns] = t;
+          en.cnt[ns] = 1;
+          en.nslots = ns + 1;
+          en.n += 1;
+        }
+      } else {
+        // evict the lowest count, lowest slot index on ties
+        int bc = 0x7fffffff, bi = 0x7fffffff;
+        for (int q = lane; q < kMaxSlots; q += 32) {
+          const int cq = en.cnt[q];
+          if (cq < bc || (cq == bc && q < bi)) {
+            bc = cq;
+            bi = q;
+          }
+        }
 #pragma unroll
-      for (int o = 16; o; o >>= 1) {
-        const int oc = __shfl_xor_sync(0xffffffffu, bc, o);
-        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-        if (oc < bc || (oc == bc && oi < bi)) {
-          bc = oc;
-          bi = oi;
+        for (int o = 16; o; o >>= 1) {
+          const int oc = __shfl_xor_sync(0xffffffffu, bc, o);
+          const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+          if (oc < bc || (oc == bc && oi < bi)) {
+            bc = oc;
+            bi = oi;
+          }
         }
-      }
-      if (lane == 0) {
-        en.n += 1 - en.cnt[bi];
-        en.tok[bi] = t;
-        en.cnt[bi] = 1;
+        if (lane == 0) {
+          en.n += 1 - en.cnt[bi];
+          en.tok[bi] = t;
+          en.cnt[bi] = 1;
+        }
       }
     }
     __syncwarp();
   }
+  // the next context: the last k + 1 tokens with t appended
   if (lane == 0) {
+    int nhist[3] = {st.hist[1], st.hist[2], t};
+    const int nh2 = min(3, st.n_coded + 1);
+    st.ctx_ent[k] = (k < D.order && k < nh2) ? ng_find(st, k, ctx_key(nhist, k + 1), false) : -1;
+  }
+}
+
+__device__ void ngram_update_row(const Dims& D, const Batch& b, int j, int warp, int lane) {
+  StreamDev& st = b.st[b.slots[j]];
+  const int t = b.obs[j];
+  if (t < 0 || t >= D.V) {
+    if (warp == 0 && lane == 0) atomicOr(&st.status, ST_BAD_TOKEN);
+    return;
+  }
+  if (warp < kMaxOrder) ngram_update_order(D, st, t, warp, lane);
+  __syncthreads();                                 // every order has read the old history
+  if (warp == 0 && lane == 0) {
     if (D.order > 0) {
       st.uni[t] += 1;
       st.N += 1;
@@ -645,9 +673,6 @@ __global__ void k_ngram_update(Dims D, Batch b) {
     st.kv_start = start;
     st.n_coded += 1;
     st.last_tok = t;
-    const int nh2 = min(3, st.n_coded);
-    for (int k = 0; k < kMaxOrder; ++k)
-      st.ctx_ent[k] = (k < D.order && k < nh2) ? ng_find(st, k, ctx_key(st.hist, k + 1), false) : -1;
   }
 }
 
@@ -849,11 +874,6 @@ cudaError_t launch_vocab(const Dims& D, const Batch& b, const VocabIO& io, cudaS
   return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_ngram_update(const Dims& D, const Batch& b, cudaStream_t s) {
-  const int threads = 128;
-  const int blocks = (b.Bmax * 32 + threads - 1) / threads;
-  return launch_kernel(k_ngram_update, dim3(blocks), dim3(threads), 0, s, D.pdl, D, b);
-}
 
 cudaError_t launch_prepare_encode(const Batch& b, int n_streams, const int32_t* tok_flat,
                                   const int64_t* offs, const int64_t* lens, int32_t* obs,

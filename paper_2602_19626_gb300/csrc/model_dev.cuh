@@ -317,13 +317,16 @@ constexpr int kAttnChunk = kAttnWarps * 32;          // positions per chunk
 constexpr int kAttnMaxChunks = 2048 / kAttnChunk;    // ctx_len <= 2048
 
 template <int S>
-struct AttnSmem {
+struct __align__(16) AttnSmem {
   static constexpr int kDims = kHeadDim / S;         // output dims merged by one CTA
   float qs[kMaxGroup][kHeadDim];
   float kn[kHeadDim], vn[kHeadDim];
   float cs[kHeadDim / 2], sn[kHeadDim / 2];
   float wm[kAttnWarps][kMaxGroup], wl[kAttnWarps][kMaxGroup];
   float wacc[kAttnWarps][kMaxGroup][kHeadDim];
+  float we[kAttnWarps][kMaxGroup][32];               // each warp's softmax numerators
+  float cf[kMaxGroup][kAttnWarps], cM[kMaxGroup], cL[kMaxGroup];   // block combine factors
+  float mf[kMaxGroup][kAttnMaxChunks], mL[kMaxGroup];              // chunk merge factors
   // every chunk's (max, sum) and this CTA's dims of its accumulator, written
   // by the chunk's owner (a remote store when the owner is another CTA)
   float rm[kAttnMaxChunks][kMaxGroup], rl[kAttnMaxChunks][kMaxGroup];
@@ -353,9 +356,12 @@ __device__ __forceinline__ void attn_rope(const Dims& D, int a, int tid, Sm& sm)
     const float2 t1 = D.rope_tab[(0 * 256 + (a & 255)) * 32 + tid];
     const float2 t2 = D.rope_tab[(1 * 256 + ((a >> 8) & 255)) * 32 + tid];
     const float2 t3 = D.rope_tab[(2 * 256 + ((a >> 16) & 255)) * 32 + tid];
-    const float c12 = t1.x * t2.x - t1.y * t2.y, s12 = t1.x * t2.y + t1.y * t2.x;
-    sm.cs[tid] = c12 * t3.x - s12 * t3.y;
-    sm.sn[tid] = c12 * t3.y + s12 * t3.x;
+    // explicit roundings: no multiply-add contraction, so every kernel that
+    // rotates a position gets the same bits
+    const float c12 = __fsub_rn(__fmul_rn(t1.x, t2.x), __fmul_rn(t1.y, t2.y));
+    const float s12 = __fadd_rn(__fmul_rn(t1.x, t2.y), __fmul_rn(t1.y, t2.x));
+    sm.cs[tid] = __fsub_rn(__fmul_rn(c12, t3.x), __fmul_rn(s12, t3.y));
+    sm.sn[tid] = __fadd_rn(__fmul_rn(c12, t3.y), __fmul_rn(s12, t3.x));
   }
 }
 
@@ -423,8 +429,8 @@ __device__ void attn_qkv(const Dims& D, StreamDev& st, int layer, int j, int g, 
     const int h = e / (kHeadDim / 2), dd = e % (kHeadDim / 2);
     const float* src = h < grp ? row + (g * grp + h) * kHeadDim : row + D.hq * kHeadDim + g * kHeadDim;
     const float x1 = __ldcg(src + dd), x2 = __ldcg(src + dd + kHeadDim / 2);
-    const float r1 = x1 * sm.cs[dd] - x2 * sm.sn[dd];
-    const float r2 = x2 * sm.cs[dd] + x1 * sm.sn[dd];
+    const float r1 = __fsub_rn(__fmul_rn(x1, sm.cs[dd]), __fmul_rn(x2, sm.sn[dd]));
+    const float r2 = __fadd_rn(__fmul_rn(x2, sm.cs[dd]), __fmul_rn(x1, sm.sn[dd]));
     if (h < grp) {   // the 1/sqrt(64) score scale is a power of two: exact
       sm.qs[h][dd] = r1 * 0.125f;
       sm.qs[h][dd + kHeadDim / 2] = r2 * 0.125f;
@@ -450,12 +456,15 @@ __device__ void attn_qkv(const Dims& D, StreamDev& st, int layer, int j, int g, 
   }
 }
 
-// One chunk [c_lo, c_end): scores and values of each warp's block, then the
-// blocks combined in block order into local chunk slot lc.
-// `dst(r)` is the shared memory of cluster rank r.
-template <int KBF16, int S, typename Dst>
-__device__ void attn_chunk(const Dims& D, int c, int c_lo, int c_end, int a, int tid, AttnSmem<S>& sm,
-                           AttnPre<KBF16>& pre, Dst dst) {
+// One chunk [c_lo, c_end) for the query of position a: scores and values of
+// each warp's block, then the blocks combined in block order.  `q` holds the
+// rotated, scaled query heads (qs) and the fed token's k, v (kn, vn), used in
+// FP32 at position a whatever `pre` holds there; `sm` is the block scratch
+// (wm, wl, wacc).  put(h, dd, o, M, l) receives the chunk's accumulator of
+// head h, dim dd with the chunk's max and sum.
+template <int KBF16, typename Qv, typename Sc, typename Put>
+__device__ void attn_chunk(const Dims& D, int c_lo, int c_end, int a, int tid, const Qv& q, Sc& sm,
+                           AttnPre<KBF16>& pre, Put put) {
   const int grp = D.hq / D.hkv;
   const int warp = tid >> 5, lane = tid & 31;
   const int p_lo = c_lo + warp * 32;
@@ -474,12 +483,12 @@ __device__ void attn_chunk(const Dims& D, int c, int c_lo, int c_end, int a, int
 #pragma unroll
           for (int i = 0; i < kHeadDim / 2; ++i) {
             const uint32_t w = pre.kb[KBF16 ? i : 0];
-            acc = fmaf(sm.qs[h][2 * i], __uint_as_float(w << 16), acc);
-            acc = fmaf(sm.qs[h][2 * i + 1], __uint_as_float(w & 0xFFFF0000u), acc);
+            acc = fmaf(q.qs[h][2 * i], __uint_as_float(w << 16), acc);
+            acc = fmaf(q.qs[h][2 * i + 1], __uint_as_float(w & 0xFFFF0000u), acc);
           }
         } else {
 #pragma unroll
-          for (int d = 0; d < kHeadDim; ++d) acc = fmaf(sm.qs[h][d], pre.kr[KBF16 ? 0 : d], acc);
+          for (int d = 0; d < kHeadDim; ++d) acc = fmaf(q.qs[h][d], pre.kr[KBF16 ? 0 : d], acc);
         }
         sc[h] = acc;
       }
@@ -490,7 +499,7 @@ __device__ void attn_chunk(const Dims& D, int c, int c_lo, int c_end, int a, int
       if (h < grp) {
         float acc = 0.f;
 #pragma unroll
-        for (int d = 0; d < kHeadDim; ++d) acc = fmaf(sm.qs[h][d], sm.kn[d], acc);
+        for (int d = 0; d < kHeadDim; ++d) acc = fmaf(q.qs[h][d], q.kn[d], acc);
         sc[h] = acc;
       }
     }
@@ -504,31 +513,46 @@ __device__ void attn_chunk(const Dims& D, int c, int c_lo, int c_end, int a, int
       lh[h] = warp_sum(eh[h]);
     }
   }
-  // P V: lane owns output dims 2*lane, 2*lane + 1
+  // P V: lane owns output dims 2*lane, 2*lane + 1; the numerators of the
+  // warp's 32 positions are read back from shared memory four at a time
+#pragma unroll
+  for (int h = 0; h < kMaxGroup; ++h)
+    if (h < grp) sm.we[warp][h][lane] = eh[h];
+  __syncwarp();
   float acc[kMaxGroup][2];
 #pragma unroll
   for (int h = 0; h < kMaxGroup; ++h) acc[h][0] = acc[h][1] = 0.f;
 #pragma unroll
-  for (int i = 0; i < 32; ++i) {
-    if (i >= nvalid) break;
-    const int pi = p_lo + i;
-    float v0, v1;
-    if (pi == a) {
-      v0 = sm.vn[2 * lane];
-      v1 = sm.vn[2 * lane + 1];
-    } else if (KBF16) {
-      v0 = __uint_as_float(pre.vb[i] << 16);
-      v1 = __uint_as_float(pre.vb[i] & 0xFFFF0000u);
-    } else {
-      v0 = pre.vf[KBF16 ? 0 : i].x;
-      v1 = pre.vf[KBF16 ? 0 : i].y;
-    }
+  for (int i4 = 0; i4 < 32; i4 += 4) {
+    if (i4 >= nvalid) break;
+    float4 e4[kMaxGroup];
 #pragma unroll
-    for (int h = 0; h < kMaxGroup; ++h) {
-      if (h < grp) {
-        const float e = __shfl_sync(0xffffffffu, eh[h], i);
-        acc[h][0] = fmaf(e, v0, acc[h][0]);
-        acc[h][1] = fmaf(e, v1, acc[h][1]);
+    for (int h = 0; h < kMaxGroup; ++h)
+      if (h < grp) e4[h] = *reinterpret_cast<const float4*>(&sm.we[warp][h][i4]);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int i = i4 + k;
+      if (i < nvalid) {
+        const int pi = p_lo + i;
+        float v0, v1;
+        if (pi == a) {
+          v0 = q.vn[2 * lane];
+          v1 = q.vn[2 * lane + 1];
+        } else if (KBF16) {
+          v0 = __uint_as_float(pre.vb[i] << 16);
+          v1 = __uint_as_float(pre.vb[i] & 0xFFFF0000u);
+        } else {
+          v0 = pre.vf[KBF16 ? 0 : i].x;
+          v1 = pre.vf[KBF16 ? 0 : i].y;
+        }
+#pragma unroll
+        for (int h = 0; h < kMaxGroup; ++h) {
+          if (h < grp) {
+            const float e = k == 0 ? e4[h].x : k == 1 ? e4[h].y : k == 2 ? e4[h].z : e4[h].w;
+            acc[h][0] = fmaf(e, v0, acc[h][0]);
+            acc[h][1] = fmaf(e, v1, acc[h][1]);
+          }
+        }
       }
     }
   }
@@ -544,29 +568,30 @@ __device__ void attn_chunk(const Dims& D, int c, int c_lo, int c_end, int a, int
     }
   }
   __syncthreads();
-  // combine the blocks in block order (blocks without positions are skipped)
+  // combine the blocks in block order; blocks 0 .. nblk - 1 hold positions.
+  // The factor of block w, exp(m_w - M), is computed once per head.
+  const int nblk = (min(c_end, a + 1) - c_lo + 31) / 32;
+  if (tid < grp) {
+    const int h = tid;
+    float M = -INFINITY;
+    for (int w = 0; w < nblk; ++w) M = fmaxf(M, sm.wm[w][h]);
+    float l = 0.f;
+    for (int w = 0; w < nblk; ++w) {
+      const float f = expf(sm.wm[w][h] - M);
+      sm.cf[h][w] = f;
+      l = fmaf(sm.wl[w][h], f, l);
+    }
+    sm.cM[h] = M;
+    sm.cL[h] = l;
+  }
+  __syncthreads();
   for (int e = tid; e < grp * kHeadDim; e += kAttnThreads) {
     const int h = e / kHeadDim, dd = e % kHeadDim;
-    float M = -INFINITY;
-    for (int w = 0; w < kAttnWarps; ++w)
-      if (c_lo + w * 32 < c_end && c_lo + w * 32 <= a) M = fmaxf(M, sm.wm[w][h]);
-    float l = 0.f, o = 0.f;
-    for (int w = 0; w < kAttnWarps; ++w) {
-      if (c_lo + w * 32 < c_end && c_lo + w * 32 <= a) {
-        const float f = expf(sm.wm[w][h] - M);
-        l = fmaf(sm.wl[w][h], f, l);
-        o = fmaf(sm.wacc[w][h][dd], f, o);
-      }
-    }
-    constexpr int kDims = AttnSmem<S>::kDims;
-    AttnSmem<S>* r = dst(dd / kDims);
-    r->racc[c][h][dd % kDims] = o;
-    if (dd % kDims == 0) {
-      r->rm[c][h] = M;
-      r->rl[c][h] = l;
-    }
+    float o = 0.f;
+    for (int w = 0; w < nblk; ++w) o = fmaf(sm.wacc[w][h][dd], sm.cf[h][w], o);
+    put(h, dd, o, sm.cM[h], sm.cL[h]);
   }
-  __syncthreads();   // wm / wl / wacc are rewritten by the next chunk
+  __syncthreads();   // the scratch is rewritten by the next chunk
 }
 
 }  // namespace dev

@@ -78,3 +78,17 @@ def test_prefill_container_decodes_per_position(nc):
     assert blob == plain
     for a, b in zip(streams, back):
         assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("split", ["1", "2", "4", "8"])
+def test_prefill_attention_split(nc, monkeypatch, split):
+    """Windows up to 2,048 positions (8 chunks) with a slide: the prefill's
+    multi-row attention with 1, 2, 4 or 8 CTAs per row group gives the
+    decode intervals exactly."""
+    shape, seed = dataclasses.replace(S.SMALL, ctx_len=2048, slide=512), 8
+    w = S.flat_weights(shape, seed)
+    toks = [S.token_stream(seed, j, n, shape.vocab) for j, n in enumerate([2300, 700])]
+    ref = intervals(nc, shape, w, "bf16", "gemv", toks, 0, 2)
+    monkeypatch.setenv("NC24_ATTN_CLUSTER", split)
+    got = intervals(nc, shape, w, "bf16", "gemv", toks, 1024, 2)
+    assert np.array_equal(got, ref)
