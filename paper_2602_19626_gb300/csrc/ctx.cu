@@ -1062,7 +1062,7 @@ static int encode_prefill(nc_ctx* ctx, int n, int m, const int32_t* tok_dev, con
   mk.on = trace != nullptr;
   const int fwd_marks = 1 + 1 + 5 * D.n_layers + 1;   // prepare, embed, 5 per layer, LM head
   if (mk.on) {
-    mk.ev.resize(fwd_marks + m + 2);
+    mk.ev.resize(fwd_marks + 1 + 2);
     for (auto& e : mk.ev) NC_TRY(cudaEventCreate(&e));
   }
   auto one_chunk = [&]() -> cudaError_t {
@@ -1072,15 +1072,12 @@ static int encode_prefill(nc_ctx* ctx, int n, int m, const int32_t* tok_dev, con
                                  ctx->d_nB_fwd, ctx->f_obs, ctx->f_nb, ctx->d_zidx, s);
     if (e == cudaSuccess) e = mk.mark(s, TK_PREPARE);
     if (e == cudaSuccess) e = launch_model(ctx, f, &mk);
-    for (int r = 0; r < m && e == cudaSuccess; ++r) {
-      Batch br = b;                                 // position p0 + r of every stream
-      br.nB = ctx->f_nb + r;
-      br.obs = ctx->f_obs + (size_t)r * n;
-      br.z_in = ctx->zrows + (size_t)r * D.V;
+    if (e == cudaSuccess) {
+      Batch br = b;                                 // every stream's m positions, in order
       br.z_idx = ctx->d_zidx;
-      e = launch_vocab(D, br, io, s);
-      if (e == cudaSuccess) e = mk.mark(s, TK_VOCAB);
+      e = launch_vocab_seq(D, br, io, m, ctx->zrows, ctx->f_nb, ctx->f_obs, s);
     }
+    if (e == cudaSuccess) e = mk.mark(s, TK_VOCAB);
     return e;
   };
   cudaGraph_t g = nullptr;
@@ -1130,13 +1127,15 @@ static int encode_prefill(nc_ctx* ctx, int n, int m, const int32_t* tok_dev, con
         cudaEventElapsedTime(&ms, mk.ev[i], mk.ev[i + 1]);
         const int kd = mk.kind[i];
         double by = fwd[kd];
-        if (i >= fwd_marks) {
-          const int64_t a = p + (i - fwd_marks);
-          int act = 0;
-          for (int j = 0; j < n; ++j) act += lens_h[j] > a;
-          double per[TK_COUNT];
-          step_bytes(ctx, act, 0.0, per);
-          by = per[kd];
+        if (i >= fwd_marks) {                       // the chunk's vocabulary passes
+          by = 0;
+          for (int64_t a = p; a < p + m; ++a) {
+            int act = 0;
+            for (int j = 0; j < n; ++j) act += lens_h[j] > a;
+            double per[TK_COUNT];
+            step_bytes(ctx, act, 0.0, per);
+            by += per[kd];
+          }
         }
         trace->ms[kd] += ms;
         trace->launches[kd] += 1;

@@ -12,8 +12,10 @@ constexpr int kHeadDim = 64;           // d_head of the supported models (Sec. 3
 constexpr int kMaxSlots = 64;          // continuation slots per N-gram context (Sec. 3.4)
 constexpr int kMaxOrder = 3;           // N-gram context lengths 1..3
 constexpr int kMaxGroup = 4;           // query heads per KV head supported
-constexpr int kVocabCluster = 8;       // CTAs per stream in the vocabulary kernel
+constexpr int kVocabCluster = 8;       // CTAs per row in the standalone quantiser kernels
 constexpr int kVocabThreads = 512;
+constexpr int kStepCluster = 8;        // CTAs per stream in the per-token vocabulary pass
+constexpr int kStepThreads = 512;
 constexpr unsigned long long kEmptyKey = ~0ull;
 
 // Status bits a kernel can raise in StreamDev::status (sticky).
@@ -193,6 +195,11 @@ struct VocabIO {
   int ngram;                // with update: also the N-gram update and the stream's bookkeeping
 };
 cudaError_t launch_vocab(const Dims& D, const Batch& b, const VocabIO& io, cudaStream_t s);
+// The vocabulary passes of a prefill chunk in one launch: stream row j runs
+// positions 0 .. m - 1 of the chunk in order while j < nb_step[r], with the
+// observed tokens obs_step[r Bmax + j] and the logits zrows + (z_idx[j] + r) V.
+cudaError_t launch_vocab_seq(const Dims& D, const Batch& b, const VocabIO& io, int m, const float* zrows,
+                             const int32_t* nb_step, const int32_t* obs_step, cudaStream_t s);
 cudaError_t launch_prepare_encode(const Batch& b, int n_streams, const int32_t* tok_flat,
                                   const int64_t* offs, const int64_t* lens, int32_t* obs,
                                   int32_t* nB, cudaStream_t s);

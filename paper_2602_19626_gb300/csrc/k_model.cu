@@ -174,37 +174,51 @@ struct RowQ {
 };
 
 constexpr int kRowsMax = 8;                         // query rows per CTA
+constexpr int kRowQFloats = sizeof(RowQ) / sizeof(float);
 
-template <int S>
-struct RowsSmem {
-  static constexpr int kDims = kHeadDim / S;
-  RowQ q[kRowsMax];
-  float wm[kAttnWarps][kMaxGroup], wl[kAttnWarps][kMaxGroup];
-  float wacc[kAttnWarps][kMaxGroup][kHeadDim];
-  float we[kAttnWarps][kMaxGroup][32];
-  float cf[kMaxGroup][kAttnWarps], cM[kMaxGroup], cL[kMaxGroup];
-  float mf[kMaxGroup][kAttnMaxChunks], mL[kMaxGroup];
-  float rm[kRowsMax][kAttnMaxChunks][kMaxGroup], rl[kRowsMax][kAttnMaxChunks][kMaxGroup];
-  float racc[kRowsMax][kAttnMaxChunks][kMaxGroup][kDims];
+// Shared-memory layout of the multi-row attention, in floats, for rq rows,
+// grp query heads per KV head and kd merged dims per CTA.
+struct RowsLayout {
+  int q, we, wm, wl, wacc, cf, cM, cL, rm, rl, racc, mf, mL, total;
+  __host__ __device__ RowsLayout(int rq, int grp, int kd) {
+    int o = 0;
+    q = o;    o += rq * kRowQFloats;
+    we = o;   o += kAttnWarps * grp * 32;
+    wm = o;   o += rq * kAttnWarps * grp;
+    wl = o;   o += rq * kAttnWarps * grp;
+    wacc = o; o += rq * kAttnWarps * grp * kHeadDim;
+    cf = o;   o += rq * grp * kAttnWarps;
+    cM = o;   o += rq * grp;
+    cL = o;   o += rq * grp;
+    rm = o;   o += rq * kAttnMaxChunks * grp;
+    rl = o;   o += rq * kAttnMaxChunks * grp;
+    racc = o; o += rq * kAttnMaxChunks * grp * kd;
+    mf = o;   o += grp * kAttnMaxChunks;
+    mL = o;   o += grp;
+    total = (o + 3) & ~3;
+  }
 };
 
 // Prefill attention of rq consecutive rows of one stream (consecutive
-// positions, one window start) and one KV head.  Each warp loads the keys
-// and values of its 32 positions of a chunk once and runs every row's block
-// computation on them (the row's own position in FP32, later positions
-// masked); chunks are split over a cluster of S CTAs and merged per row in
-// chunk order.  Each row's output is the decode attention's, bit for bit.
+// positions, one window start) and one KV head.  Per chunk, each warp loads
+// the keys and values of its 32 positions once and computes every row's
+// block (attn_block, as the decode attention does); then the blocks of all
+// rows are combined in block order.  Chunks are split over a cluster of S
+// CTAs and merged per row in chunk order, so every row's output equals the
+// decode attention's bit for bit.
 template <int KBF16, int S>
 __global__ void __launch_bounds__(kAttnThreads, 2) k_attn_rows(Dims D, Batch b, int layer, int rq, AttnIO io) {
   extern __shared__ float4 dyn4[];
-  RowsSmem<S>& sm = *reinterpret_cast<RowsSmem<S>*>(dyn4);
+  float* sm = reinterpret_cast<float*>(dyn4);
   const int rank = S > 1 ? (int)cg::this_cluster().block_rank() : 0;
   const int g = blockIdx.y, i0 = blockIdx.z * rq;
   if (i0 >= *b.nB) return;                         // uniform across the cluster
   if (S > 1) asm volatile("barrier.cluster.arrive.relaxed.aligned;" ::: "memory");
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int grp = D.hq / D.hkv;
-  constexpr int kDims = RowsSmem<S>::kDims;
+  constexpr int kd = kHeadDim / S;
+  const RowsLayout L(rq, grp, kd);
+  RowQ* qv = reinterpret_cast<RowQ*>(sm + L.q);
   StreamDev& st = b.st[b.slots[i0]];
   int a_max = -1;
   for (int r = 0; r < rq; ++r) a_max = max(a_max, b.pos[i0 + r]);
@@ -215,39 +229,113 @@ __global__ void __launch_bounds__(kAttnThreads, 2) k_attn_rows(Dims D, Batch b, 
   for (int r = 0; r < rq; ++r) {
     const int a = b.pos[i0 + r];
     if (a < 0) continue;                           // uniform across the CTA
-    attn_rope(D, a, tid, sm.q[r]);
-    attn_qkv<KBF16>(D, st, layer, i0 + r, g, a, false, tid, sm.q[r], io);
+    attn_rope(D, a, tid, qv[r]);
+    attn_qkv<KBF16>(D, st, layer, i0 + r, g, a, false, tid, qv[r], io);
   }
-  auto dst = [&](int rk) -> RowsSmem<S>* {
-    if (S == 1) return &sm;
-    return cg::this_cluster().map_shared_rank(&sm, rk);
+  auto dst = [&](int rk) -> float* {
+    if (S == 1) return sm;
+    return cg::this_cluster().map_shared_rank(sm, rk);
+  };
+  // chunk c of row r exists when position start + 256 c <= a_r
+  auto has = [&](int r, int c) {
+    const int a = b.pos[i0 + r];
+    return a >= 0 && c <= (a - start) / kAttnChunk;
   };
   if (S > 1) asm volatile("barrier.cluster.wait.aligned;" ::: "memory");
   for (int c = rank; c < nc_max; c += S) {
     const int c_lo = start + c * kAttnChunk;
     AttnPre<KBF16> pre;
     attn_load<KBF16>(D, st, layer, g, c_lo + warp * 32, min(c_lo + kAttnChunk, a_max + 1), a_max + 1, lane, pre);
+    // every row's block of this warp
     for (int r = 0; r < rq; ++r) {
+      if (!has(r, c)) continue;                    // uniform across the CTA
       const int a = b.pos[i0 + r];
-      if (a < 0 || c > (a - start) / kAttnChunk) continue;   // uniform across the CTA
-      attn_chunk<KBF16>(D, c_lo, min(c_lo + kAttnChunk, a + 1), a, tid, sm.q[r], sm, pre,
-                        [&](int h, int dd, float o, float M, float l) {
-                          RowsSmem<S>* t = dst(dd / kDims);
-                          t->racc[r][c][h][dd % kDims] = o;
-                          if (dd % kDims == 0) {
-                            t->rm[r][c][h] = M;
-                            t->rl[r][c][h] = l;
-                          }
-                        });
+      float mh[kMaxGroup], lh[kMaxGroup], acc[kMaxGroup][2];
+      const int nvalid = attn_block<KBF16>(D, c_lo + warp * 32, min(c_lo + kAttnChunk, a + 1), a, lane, qv[r],
+                                           sm + L.we + warp * grp * 32, pre, mh, lh, acc);
+      float* wacc = sm + L.wacc + ((r * kAttnWarps + warp) * grp) * kHeadDim;
+#pragma unroll
+      for (int h = 0; h < kMaxGroup; ++h) {
+        if (h < grp) {
+          if (lane == 0) {
+            sm[L.wm + (r * kAttnWarps + warp) * grp + h] = nvalid > 0 ? mh[h] : -INFINITY;
+            sm[L.wl + (r * kAttnWarps + warp) * grp + h] = nvalid > 0 ? lh[h] : 0.f;
+          }
+          wacc[h * kHeadDim + 2 * lane] = acc[h][0];
+          wacc[h * kHeadDim + 2 * lane + 1] = acc[h][1];
+        }
+      }
     }
+    __syncthreads();
+    // per (row, head): the block factors exp(m_w - M), M and the sum
+    for (int t = tid; t < rq * grp; t += kAttnThreads) {
+      const int r = t / grp, h = t % grp;
+      if (!has(r, c)) continue;
+      const int a = b.pos[i0 + r];
+      const int nblk = (min(c_lo + kAttnChunk, a + 1) - c_lo + 31) / 32;
+      const float* wm = sm + L.wm + r * kAttnWarps * grp;
+      const float* wl = sm + L.wl + r * kAttnWarps * grp;
+      float M = -INFINITY;
+      for (int w = 0; w < nblk; ++w) M = fmaxf(M, wm[w * grp + h]);
+      float l = 0.f;
+      for (int w = 0; w < nblk; ++w) {
+        const float f = expf(wm[w * grp + h] - M);
+        sm[L.cf + t * kAttnWarps + w] = f;
+        l = fmaf(wl[w * grp + h], f, l);
+      }
+      sm[L.cM + t] = M;
+      sm[L.cL + t] = l;
+    }
+    __syncthreads();
+    // per (row, head, dim): the chunk accumulator, stored with the chunk's
+    // (M, l) into the shared memory of the CTA merging that dim
+    for (int e = tid; e < rq * grp * kHeadDim; e += kAttnThreads) {
+      const int t = e / kHeadDim, dd = e % kHeadDim, r = t / grp, h = t % grp;
+      if (!has(r, c)) continue;
+      const int a = b.pos[i0 + r];
+      const int nblk = (min(c_lo + kAttnChunk, a + 1) - c_lo + 31) / 32;
+      float o = 0.f;
+      for (int w = 0; w < nblk; ++w)
+        o = fmaf(sm[L.wacc + ((r * kAttnWarps + w) * grp + h) * kHeadDim + dd], sm[L.cf + t * kAttnWarps + w], o);
+      float* tgt = dst(dd / kd);
+      const int rc = (r * kAttnMaxChunks + c) * grp + h;
+      tgt[L.racc + rc * kd + dd % kd] = o;
+      if (dd % kd == 0) {
+        tgt[L.rm + rc] = sm[L.cM + t];
+        tgt[L.rl + rc] = sm[L.cL + t];
+      }
+    }
+    __syncthreads();
   }
   if (S > 1) cg::this_cluster().sync();            // every chunk's partial has arrived
   else __syncthreads();
+  // per row: merge its chunks in chunk order
   for (int r = 0; r < rq; ++r) {
     const int a = b.pos[i0 + r];
     const int nc = a < 0 ? 0 : (a - start) / kAttnChunk + 1;
-    merge_chunks(sm, sm.rm[r], sm.rl[r], sm.racc[r], nc, grp, tid,
-                 io.attn_out + (size_t)(i0 + r) * D.hq * kHeadDim + g * grp * kHeadDim + rank * kDims);
+    if (tid < grp) {
+      const int h = tid;
+      float M = -INFINITY;
+      for (int c = 0; c < nc; ++c) M = fmaxf(M, sm[L.rm + (r * kAttnMaxChunks + c) * grp + h]);
+      float l = 0.f;
+      for (int c = 0; c < nc; ++c) {
+        const int rc = (r * kAttnMaxChunks + c) * grp + h;
+        const float f = expf(sm[L.rm + rc] - M);
+        sm[L.mf + h * kAttnMaxChunks + c] = f;
+        l = fmaf(sm[L.rl + rc], f, l);
+      }
+      sm[L.mL + h] = l;
+    }
+    __syncthreads();
+    float* out = io.attn_out + (size_t)(i0 + r) * D.hq * kHeadDim + g * grp * kHeadDim + rank * kd;
+    for (int e = tid; e < grp * kd; e += kAttnThreads) {
+      const int h = e / kd, dl = e % kd;
+      float o = 0.f;
+      for (int c = 0; c < nc; ++c)
+        o = fmaf(sm[L.racc + ((r * kAttnMaxChunks + c) * grp + h) * kd + dl], sm[L.mf + h * kAttnMaxChunks + c], o);
+      out[h * kHeadDim + dl] = nc ? o / sm[L.mL + h] : 0.f;
+    }
+    __syncthreads();
   }
 }
 
@@ -385,12 +473,13 @@ static cudaError_t prepare_gemv_f(int cmax) {
   return e;
 }
 
+static size_t rows_smem(int rq, int grp, int S) { return (size_t)RowsLayout(rq, grp, kHeadDim / S).total * 4; }
+
 template <int S>
-static cudaError_t prepare_rows_s() {
-  cudaError_t e = cudaFuncSetAttribute(k_attn_rows<1, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)sizeof(RowsSmem<S>));
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_attn_rows<0, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(RowsSmem<S>));
+static cudaError_t prepare_rows_s(int grp) {
+  const int bytes = (int)rows_smem(kRowsMax, grp, S);
+  cudaError_t e = cudaFuncSetAttribute(k_attn_rows<1, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_attn_rows<0, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
   return e;
 }
 
@@ -399,10 +488,11 @@ cudaError_t prepare_model_kernels(const Dims& D, int fmt) {
   cudaError_t e = fmt == NC_FP32 ? prepare_gemv_f<NC_FP32>(cmax)
                   : fmt == NC_BF16 ? prepare_gemv_f<NC_BF16>(cmax)
                                    : prepare_gemv_f<NC_FP8E4M3>(cmax);
-  if (e == cudaSuccess) e = prepare_rows_s<1>();
-  if (e == cudaSuccess) e = prepare_rows_s<2>();
-  if (e == cudaSuccess) e = prepare_rows_s<4>();
-  if (e == cudaSuccess) e = prepare_rows_s<8>();
+  const int grp = D.hq / D.hkv;
+  if (e == cudaSuccess) e = prepare_rows_s<1>(grp);
+  if (e == cudaSuccess) e = prepare_rows_s<2>(grp);
+  if (e == cudaSuccess) e = prepare_rows_s<4>(grp);
+  if (e == cudaSuccess) e = prepare_rows_s<8>(grp);
   return e;
 }
 
@@ -423,26 +513,24 @@ static int attn_split(const Dims& D, const Batch& b) {
 }
 
 template <int S>
-static size_t rows_smem() {
-  return sizeof(RowsSmem<S>);
-}
-
-template <int S>
 static cudaError_t launch_attn_rows_s(const Dims& D, const Batch& b, int layer, int rq, const AttnIO& io,
                                       cudaStream_t s) {
   dim3 grid(S, D.hkv, b.Bmax / rq);
   return launch_kernel_cluster(D.kv_bf16 ? k_attn_rows<1, S> : k_attn_rows<0, S>, grid, dim3(kAttnThreads),
-                               rows_smem<S>(), s, D.pdl, S, D, b, layer, rq, io);
+                               rows_smem(rq, D.hq / D.hkv, S), s, D.pdl, S, D, b, layer, rq, io);
 }
 
 // Prefill rows (b.pm consecutive positions per stream): rq rows per CTA
 // group, S CTAs per group as for decode.
 static cudaError_t launch_attn_rows(const Dims& D, const Batch& b, int layer, const AttnIO& io, cudaStream_t s) {
-  const int rq = std::min(kRowsMax, b.pm);
+  int rq = std::min(kRowsMax, b.pm);
   int S = 8;
   if (D.attn_cluster) S = D.attn_cluster;
   else
     while (S > 1 && (int64_t)D.hkv * (b.Bmax / rq) * S > 4 * (int64_t)D.n_sm) S /= 2;
+  // one CTA owning every chunk keeps all chunk partials: 4 rows keep two
+  // CTAs per SM within shared memory
+  if (S == 1) rq = std::min(rq, 4);
   switch (S) {
     case 1: return launch_attn_rows_s<1>(D, b, layer, rq, io, s);
     case 2: return launch_attn_rows_s<2>(D, b, layer, rq, io, s);

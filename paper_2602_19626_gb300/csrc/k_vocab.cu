@@ -2,7 +2,8 @@
 // (Sec. 3.4), linear mix (Sec. 3.5), CDF quantisation with floors and the
 // prefix sum (Sec. 3.3), the head / mixer updates, and the N-gram tables.
 //
-// One stream is handled by a cluster of kVocabCluster CTAs; each CTA owns a
+// One stream is handled by a cluster of CTAs (kStepCluster for the per-token
+// step, kVocabCluster for the standalone quantiser); each CTA owns a
 // contiguous chunk of the vocabulary and each thread a contiguous run of E
 // symbols.  Reductions go thread -> warp (fixed xor tree) -> CTA (warps in
 // order) -> cluster (ranks in order through distributed shared memory), so
@@ -74,11 +75,13 @@ __device__ __forceinline__ ArgMax better(ArgMax a, ArgMax b) {
 
 // Shared scratch of one CTA: block-reduction slots, the values it publishes
 // to the other CTAs of its cluster, and the step's N-gram coefficients.
-struct VocabShared {
-  float wm[kWarps], wsum[kWarps];
-  unsigned long long wc[kWarps], wb[kWarps];
-  ArgMax wa[kWarps];
-  uint32_t wscan[kWarps];
+template <int NW>
+struct VocabSharedT {
+  static constexpr int kNW = NW;
+  float wm[NW], wsum[NW];
+  unsigned long long wc[NW], wb[NW];
+  ArgMax wa[NW];
+  uint32_t wscan[NW];
   // published to the cluster
   float cl_m, cl_s;
   unsigned long long cl_csum, cl_below;
@@ -90,24 +93,28 @@ struct VocabShared {
   float cu, coef[kMaxOrder], nk[kMaxOrder];
   const NgEntry* ent[kMaxOrder];
 };
+using VocabShared = VocabSharedT<kWarps>;                         // standalone quantiser
+using StepShared = VocabSharedT<kStepThreads / 32>;               // the per-token step
 
-__device__ float block_max(float v, VocabShared& sh) {
+template <typename Sh>
+__device__ float block_max(float v, Sh& sh) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   v = warp_max(v);
   if (lane == 0) sh.wm[w] = v;
   __syncthreads();
   float r = sh.wm[0];
-  for (int i = 1; i < kWarps; ++i) r = fmaxf(r, sh.wm[i]);
+  for (int i = 1; i < Sh::kNW; ++i) r = fmaxf(r, sh.wm[i]);
   __syncthreads();
   return r;
 }
-__device__ float block_sum(float v, VocabShared& sh) {
+template <typename Sh>
+__device__ float block_sum(float v, Sh& sh) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   v = warp_sum(v);
   if (lane == 0) sh.wsum[w] = v;
   __syncthreads();
   float r = 0.f;
-  for (int i = 0; i < kWarps; ++i) r += sh.wsum[i];
+  for (int i = 0; i < Sh::kNW; ++i) r += sh.wsum[i];
   __syncthreads();
   return r;
 }
@@ -154,8 +161,8 @@ __device__ __forceinline__ void store_run(float* dst, int v0, int V, const float
 }
 
 // Round 1: softmax statistics (M, S) of s over the cluster's vocabulary.
-template <int E>
-__device__ MS softmax_stats(const float (&s)[E], cg::cluster_group& cl, VocabShared& sh) {
+template <int E, int CL, typename Sh>
+__device__ MS softmax_stats(const float (&s)[E], cg::cluster_group& cl, Sh& sh) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   MS t{-INFINITY, 0.f};
 #pragma unroll
@@ -176,14 +183,14 @@ __device__ MS softmax_stats(const float (&s)[E], cg::cluster_group& cl, VocabSha
   __syncthreads();
   if (threadIdx.x == 0) {
     MS b{sh.wm[0], sh.wsum[0]};
-    for (int i = 1; i < kWarps; ++i) b = ms_combine(b, MS{sh.wm[i], sh.wsum[i]});
+    for (int i = 1; i < Sh::kNW; ++i) b = ms_combine(b, MS{sh.wm[i], sh.wsum[i]});
     sh.cl_m = b.m;
     sh.cl_s = b.s;
   }
   cl.sync();
   MS g{-INFINITY, 0.f};
-  for (int r = 0; r < kVocabCluster; ++r) {
-    const VocabShared* o = cl.map_shared_rank(&sh, r);
+  for (int r = 0; r < CL; ++r) {
+    const Sh* o = cl.map_shared_rank(&sh, r);
     g = ms_combine(g, MS{o->cl_m, o->cl_s});
   }
   return g;
@@ -200,10 +207,10 @@ struct QuantResult {
 // count sum, the first argmax and (for `want` >= 0) the count sum below
 // `want` over the cluster.  The CTA owning `want` also publishes obs[3]
 // (read by every CTA after this round through cl_obs of the owner rank).
-template <int E>
+template <int E, int CL, typename Sh>
 __device__ QuantResult quantise_round(const float (&p)[E], int v0, int V, int log2T, uint32_t floor_c,
                                       bool quantise, int want, const float* obs, uint32_t (&c)[E],
-                                      cg::cluster_group& cl, VocabShared& sh) {
+                                      cg::cluster_group& cl, Sh& sh) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const uint32_t T = 1u << log2T;
   const uint32_t K = T - (uint32_t)V * floor_c;
@@ -250,7 +257,7 @@ __device__ QuantResult quantise_round(const float (&p)[E], int v0, int V, int lo
       unsigned long long tc = 0, tb = 0;
       ArgMax ta{-INFINITY, 0x7fffffff};
       uint32_t tbad = 0;
-      for (int i = 0; i < kWarps; ++i) {
+      for (int i = 0; i < Sh::kNW; ++i) {
         tc += sh.wc[i];
         tb += sh.wb[i];
         ta = better(ta, sh.wa[i]);
@@ -267,8 +274,8 @@ __device__ QuantResult quantise_round(const float (&p)[E], int v0, int V, int lo
   if (quantise) {
     unsigned long long total = 0;
     ArgMax g{-INFINITY, 0x7fffffff};
-    for (int q = 0; q < kVocabCluster; ++q) {
-      const VocabShared* o = cl.map_shared_rank(&sh, q);
+    for (int q = 0; q < CL; ++q) {
+      const Sh* o = cl.map_shared_rank(&sh, q);
       total += o->cl_csum;
       r.below += o->cl_below;
       g = better(g, o->cl_arg);
@@ -289,9 +296,9 @@ __device__ QuantResult quantise_round(const float (&p)[E], int v0, int V, int lo
 }
 
 // Round 3: exclusive prefix sum of the final counts into cdf_row.
-template <int E>
+template <int E, typename Sh>
 __device__ void scan_round(const uint32_t (&c)[E], int v0, int V, uint32_t T, uint32_t* cdf_row,
-                           cg::cluster_group& cl, VocabShared& sh) {
+                           cg::cluster_group& cl, Sh& sh) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   uint32_t local[E];
   uint32_t run = 0;
@@ -309,7 +316,7 @@ __device__ void scan_round(const uint32_t (&c)[E], int v0, int V, uint32_t T, ui
   if (lane == 31) sh.wscan[w] = inc;
   __syncthreads();
   uint32_t before = 0, total = 0;
-  for (int i = 0; i < kWarps; ++i) {
+  for (int i = 0; i < Sh::kNW; ++i) {
     if (i < w) before += sh.wscan[i];
     total += sh.wscan[i];
   }
@@ -331,22 +338,18 @@ __device__ void scan_round(const uint32_t (&c)[E], int v0, int V, uint32_t T, ui
 // case.
 __device__ void ngram_update_row(const Dims& D, const Batch& b, int j, int warp, int lane);
 
+// One position of stream row j, by the cluster CTA `rank`: predict (biased
+// softmax, N-gram, mix, quantise; the coder interval or the CDF) and the
+// head and mixer update.  `bias` holds this thread's bias run (loaded here
+// unless have_bias); `waited`: the caller already waited on the previous
+// kernel.  Returns false when the observed token is out of range (flagged,
+// nothing updated).  The caller runs the N-gram update after it.
 template <int E>
-__global__ void __cluster_dims__(kVocabCluster, 1, 1) __launch_bounds__(kVocabThreads)
-    k_vocab(Dims D, Batch b, VocabIO io) {
-  extern __shared__ float4 dyn4[];
-  float* sp = reinterpret_cast<float*>(dyn4);    // sparse N-gram mass of this CTA's chunk
-  __shared__ VocabShared sh;
-  cg::cluster_group cl = cg::this_cluster();
-  const int j = blockIdx.x / kVocabCluster;
-  // after a prefill the previous kernel is the N-gram update of the previous
-  // position: nothing of the stream's state may be read before it completed
-  if (b.z_in) pdl_wait();
-  if (j >= *b.nB) return;                        // uniform across the cluster
-  const int rank = (int)cl.block_rank();
+__device__ bool vocab_pass(const Dims& D, const Batch& b, const VocabIO& io, int j, int rank, cg::cluster_group& cl,
+                           StepShared& sh, float* sp, float (&bias)[E], bool have_bias, bool waited) {
   StreamDev& st = b.st[b.slots[j]];
   const int V = D.V;
-  const int chunk = kVocabThreads * E;
+  const int chunk = kStepThreads * E;
   const int base = rank * chunk;
   const int v0 = base + threadIdx.x * E;
   const int i_tok = st.n_coded + 1;              // 1-based index of the token being coded
@@ -354,12 +357,13 @@ __global__ void __cluster_dims__(kVocabCluster, 1, 1) __launch_bounds__(kVocabTh
 
   // ---- before waiting on the LM head: bias and the N-gram distribution
   // (state of earlier steps only)
-  float bias[E];
-  if (D.use_head) {
-    load_run<E>(st.bias, v0, V, bias, 0.f);
-  } else {
+  if (!have_bias) {
+    if (D.use_head) {
+      load_run<E>(st.bias, v0, V, bias, 0.f);
+    } else {
 #pragma unroll
-    for (int i = 0; i < E; ++i) bias[i] = 0.f;
+      for (int i = 0; i < E; ++i) bias[i] = 0.f;
+    }
   }
   // N-gram: P = A (c + 1) / (N + V) + sum_k beta_k cnt_k / n_k, the closed
   // form of the interpolation recursion with lambda_k = n_k / (n_k + 5).
@@ -409,13 +413,13 @@ __global__ void __cluster_dims__(kVocabCluster, 1, 1) __launch_bounds__(kVocabTh
       }
       sh.cu = A / (float)(st.N + V);
     }
-    for (int i = threadIdx.x; i < chunk; i += kVocabThreads) sp[i] = 0.f;
+    for (int i = threadIdx.x; i < chunk; i += kStepThreads) sp[i] = 0.f;
     __syncthreads();
     for (int k = 0; k < kMaxOrder; ++k) {
       const NgEntry* en = sh.ent[k];
       if (en) {
         const int ns = en->nslots;
-        for (int q = threadIdx.x; q < ns; q += kVocabThreads) {
+        for (int q = threadIdx.x; q < ns; q += kStepThreads) {
           const int t = en->tok[q] - base;
           if (t >= 0 && t < chunk) sp[t] += sh.coef[k] * (float)en->cnt[q];
         }
@@ -430,25 +434,29 @@ __global__ void __cluster_dims__(kVocabCluster, 1, 1) __launch_bounds__(kVocabTh
     for (int i = 0; i < E; ++i) png[i] = 0.f;
   }
 
-  pdl_wait();
-  pdl_trigger();
+  if (!waited) {
+    pdl_wait();
+    pdl_trigger();
+  }
   const int t_obs = (io.update || io.intervals) ? b.obs[j] : -1;
   if (io.update && (t_obs < 0 || t_obs >= V)) {   // rejected on the host; never index with it
     if (rank == 0 && threadIdx.x == 0) atomicOr(&st.status, ST_BAD_TOKEN);
-    return;                                       // uniform across the cluster
+    return false;                                 // uniform across the cluster
   }
   if (io.probe_png && ngram) store_run<E>(io.probe_png + (size_t)j * V, v0, V, png);
 
   // ---- biased logits s = z / tau + b and their softmax (round 1)
   if (!b.z_in) load_run<E>(st.z, v0, V, s, -INFINITY);
   if (io.probe_z) store_run<E>(io.probe_z + (size_t)j * V, v0, V, s);
+  const float inv_tau = 1.0f / D.tau;             // exact for tau = 1
 #pragma unroll
-  for (int i = 0; i < E; ++i) s[i] = (v0 + i < V) ? __fdiv_rn(s[i], D.tau) + bias[i] : -INFINITY;
-  const MS ms = softmax_stats<E>(s, cl, sh);
+  for (int i = 0; i < E; ++i) s[i] = (v0 + i < V) ? fmaf(s[i], inv_tau, bias[i]) : -INFINITY;
+  const MS ms = softmax_stats<E, kStepCluster>(s, cl, sh);
   const float M = ms.m, S = ms.s;
   float pt[E];
+  const float inv_S = 1.0f / S;
 #pragma unroll
-  for (int i = 0; i < E; ++i) pt[i] = (v0 + i < V) ? __fdiv_rn(expf(s[i] - M), S) : 0.f;
+  for (int i = 0; i < E; ++i) pt[i] = (v0 + i < V) ? expf(s[i] - M) * inv_S : 0.f;
   if (io.probe_pt) store_run<E>(io.probe_pt + (size_t)j * V, v0, V, pt);
 
   // ---- mix (Sec. 3.5): LLM alone during warm-up
@@ -474,7 +482,7 @@ __global__ void __cluster_dims__(kVocabCluster, 1, 1) __launch_bounds__(kVocabTh
     }
   }
   uint32_t c[E];
-  const QuantResult q = quantise_round<E>(p, v0, V, D.log2T, D.floor, io.predict != 0, t_obs,
+  const QuantResult q = quantise_round<E, kStepCluster>(p, v0, V, D.log2T, D.floor, io.predict != 0, t_obs,
                                           io.update ? obs : nullptr, c, cl, sh);
   if (io.predict) {
     if (q.bad && threadIdx.x == 0 && rank == 0) atomicOr(&st.status, ST_NUMERIC);
@@ -483,7 +491,7 @@ __global__ void __cluster_dims__(kVocabCluster, 1, 1) __launch_bounds__(kVocabTh
 #pragma unroll
       for (int i = 0; i < E; ++i) {
         if (v0 + i == t_obs) {
-          uint32_t* iv = io.intervals + 2 * ((size_t)j * io.interval_stride + st.n_coded);
+          uint32_t* iv = io.intervals + 2 * ((size_t)j * io.interval_stride + (i_tok - 1));
           iv[0] = (uint32_t)lo;
           iv[1] = (uint32_t)(lo + c[i]);
         }
@@ -493,7 +501,7 @@ __global__ void __cluster_dims__(kVocabCluster, 1, 1) __launch_bounds__(kVocabTh
   }
 
   if (io.update) {
-    const VocabShared* o = cl.map_shared_rank(&sh, t_obs / chunk);
+    const StepShared* o = cl.map_shared_rank(&sh, t_obs / chunk);
     const float pts = o->cl_obs[0], pngs = o->cl_obs[1], lpt = o->cl_obs[2];
     float scale = 1.f;
     float nth0 = th0, nth1 = th1;
@@ -524,10 +532,58 @@ __global__ void __cluster_dims__(kVocabCluster, 1, 1) __launch_bounds__(kVocabTh
       st.png_obs = pngs;
     }
   }
+  return true;
+}
+
+template <int E>
+__global__ void __launch_bounds__(kStepThreads, 1) k_vocab(Dims D, Batch b, VocabIO io) {
+  extern __shared__ float4 dyn4[];
+  float* sp = reinterpret_cast<float*>(dyn4);    // sparse N-gram mass of this CTA's chunk
+  __shared__ StepShared sh;
+  cg::cluster_group cl = cg::this_cluster();
+  const int j = blockIdx.x / kStepCluster;
+  // after a prefill the previous kernel is the N-gram update of the previous
+  // position: nothing of the stream's state may be read before it completed
+  if (b.z_in) {
+    pdl_wait();
+    pdl_trigger();
+  }
+  if (j >= *b.nB) return;                        // uniform across the cluster
+  const int rank = (int)cl.block_rank();
+  float bias[E];
+  if (!vocab_pass<E>(D, b, io, j, rank, cl, sh, sp, bias, false, b.z_in != nullptr)) return;
   cl.sync();   // keep this CTA's shared memory alive until the cluster has read it
   // the N-gram update and bookkeeping of this row, once every CTA has read
   // the stream's state
   if (io.update && io.ngram && rank == 0) ngram_update_row(D, b, j, threadIdx.x >> 5, threadIdx.x & 31);
+}
+
+// The vocabulary passes of a prefill chunk: the cluster of stream row j runs
+// positions p0 .. p0 + m - 1 in order (while the stream has tokens), each
+// one vocab_pass and the N-gram update, with the bias kept in registers and
+// a cluster barrier between positions.
+template <int E>
+__global__ void __launch_bounds__(kStepThreads, 1)
+    k_vocab_seq(Dims D, Batch b, VocabIO io, int m, int n_streams, const float* zrows, const int32_t* nb_step,
+                const int32_t* obs_step) {
+  extern __shared__ float4 dyn4[];
+  float* sp = reinterpret_cast<float*>(dyn4);
+  __shared__ StepShared sh;
+  cg::cluster_group cl = cg::this_cluster();
+  const int j = blockIdx.x / kStepCluster;
+  pdl_wait();
+  pdl_trigger();
+  const int rank = (int)cl.block_rank();
+  float bias[E];
+  for (int r = 0; r < m; ++r) {
+    if (j >= nb_step[r]) break;                    // uniform across the cluster
+    Batch br = b;
+    br.obs = obs_step + (size_t)r * n_streams;
+    br.z_in = zrows + (size_t)r * D.V;
+    if (!vocab_pass<E>(D, br, io, j, rank, cl, sh, sp, bias, r > 0, true)) break;
+    if (io.ngram && rank == 0) ngram_update_row(D, br, j, threadIdx.x >> 5, threadIdx.x & 31);
+    cl.sync();   // the stream's state of this position is final for the next
+  }
 }
 
 // --------------------------------------------------------------- N-gram tables
@@ -751,7 +807,7 @@ __global__ void __cluster_dims__(kVocabCluster, 1, 1) __launch_bounds__(kVocabTh
   float pr[E];
   load_run<E>(p + (size_t)j * V, v0, V, pr, 0.f);
   uint32_t c[E];
-  const QuantResult q = quantise_round<E>(pr, v0, V, log2T, floor_c, true, -1, nullptr, c, cl, sh);
+  const QuantResult q = quantise_round<E, kVocabCluster>(pr, v0, V, log2T, floor_c, true, -1, nullptr, c, cl, sh);
   if (q.bad && threadIdx.x == 0 && rank == 0) atomicOr(status + j, ST_NUMERIC);
   scan_round<E>(c, v0, V, 1u << log2T, cdf + (size_t)j * (V + 1), cl, sh);
   cl.sync();
@@ -839,8 +895,9 @@ __global__ void k_search(Batch b, int V, const uint32_t* cdf, const uint32_t* ta
 
 }  // namespace
 
-static int vocab_E(int V) {
-  const int per = kVocabCluster * kVocabThreads;
+// Elements per thread for a vocabulary of V over `ctas` CTAs of `threads`.
+static int vocab_E(int V, int ctas = kVocabCluster, int threads = kVocabThreads) {
+  const int per = ctas * threads;
   int e = (V + per - 1) / per;
   e = (e + 3) / 4 * 4;
   return e < 4 ? 4 : e;
@@ -848,24 +905,52 @@ static int vocab_E(int V) {
 
 template <int E>
 static cudaError_t vocab_t(const Dims& D, const Batch& b, const VocabIO& io, cudaStream_t s) {
-  const size_t smem = (size_t)kVocabThreads * E * sizeof(float);
-  return launch_kernel(k_vocab<E>, dim3(b.Bmax * kVocabCluster), dim3(kVocabThreads), smem, s, D.pdl, D, b, io);
+  const size_t smem = (size_t)kStepThreads * E * sizeof(float);
+  return launch_kernel_cluster(k_vocab<E>, dim3(b.Bmax * kStepCluster), dim3(kStepThreads), smem, s, D.pdl,
+                               kStepCluster, D, b, io);
+}
+
+template <int E>
+static cudaError_t prepare_vocab_t() {
+  cudaError_t e = cudaFuncSetAttribute(k_vocab<E>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       kStepThreads * E * (int)sizeof(float));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_vocab_seq<E>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             kStepThreads * E * (int)sizeof(float));
+  return e;
 }
 
 cudaError_t prepare_vocab_kernels(const Dims& D) {
-  const int E = vocab_E(D.V);
-  const int smem = kVocabThreads * E * (int)sizeof(float);
-  switch (E) {
-    case 4: return cudaFuncSetAttribute(k_vocab<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    case 8: return cudaFuncSetAttribute(k_vocab<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    case 12: return cudaFuncSetAttribute(k_vocab<12>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    case 16: return cudaFuncSetAttribute(k_vocab<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  switch (vocab_E(D.V, kStepCluster, kStepThreads)) {
+    case 4: return prepare_vocab_t<4>();
+    case 8: return prepare_vocab_t<8>();
+    case 12: return prepare_vocab_t<12>();
+    case 16: return prepare_vocab_t<16>();
+  }
+  return cudaErrorInvalidValue;
+}
+
+template <int E>
+static cudaError_t vocab_seq_t(const Dims& D, const Batch& b, const VocabIO& io, int m, const float* zrows,
+                               const int32_t* nb_step, const int32_t* obs_step, cudaStream_t s) {
+  const size_t smem = (size_t)kStepThreads * E * sizeof(float);
+  return launch_kernel_cluster(k_vocab_seq<E>, dim3(b.Bmax * kStepCluster), dim3(kStepThreads), smem, s, D.pdl,
+                               kStepCluster, D, b, io, m, b.Bmax, zrows, nb_step, obs_step);
+}
+
+cudaError_t launch_vocab_seq(const Dims& D, const Batch& b, const VocabIO& io, int m, const float* zrows,
+                             const int32_t* nb_step, const int32_t* obs_step, cudaStream_t s) {
+  switch (vocab_E(D.V, kStepCluster, kStepThreads)) {
+    case 4: return vocab_seq_t<4>(D, b, io, m, zrows, nb_step, obs_step, s);
+    case 8: return vocab_seq_t<8>(D, b, io, m, zrows, nb_step, obs_step, s);
+    case 12: return vocab_seq_t<12>(D, b, io, m, zrows, nb_step, obs_step, s);
+    case 16: return vocab_seq_t<16>(D, b, io, m, zrows, nb_step, obs_step, s);
   }
   return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_vocab(const Dims& D, const Batch& b, const VocabIO& io, cudaStream_t s) {
-  switch (vocab_E(D.V)) {
+  switch (vocab_E(D.V, kStepCluster, kStepThreads)) {
     case 4: return vocab_t<4>(D, b, io, s);
     case 8: return vocab_t<8>(D, b, io, s);
     case 12: return vocab_t<12>(D, b, io, s);

@@ -456,18 +456,18 @@ __device__ void attn_qkv(const Dims& D, StreamDev& st, int layer, int j, int g, 
   }
 }
 
-// One chunk [c_lo, c_end) for the query of position a: scores and values of
-// each warp's block, then the blocks combined in block order.  `q` holds the
-// rotated, scaled query heads (qs) and the fed token's k, v (kn, vn), used in
-// FP32 at position a whatever `pre` holds there; `sm` is the block scratch
-// (wm, wl, wacc).  put(h, dd, o, M, l) receives the chunk's accumulator of
-// head h, dim dd with the chunk's max and sum.
-template <int KBF16, typename Qv, typename Sc, typename Put>
-__device__ void attn_chunk(const Dims& D, int c_lo, int c_end, int a, int tid, const Qv& q, Sc& sm,
-                           AttnPre<KBF16>& pre, Put put) {
+// One warp's block of 32 positions p_lo .. p_lo + 31 of a chunk ending at
+// c_end, for the query of position a: scores of the group's heads, the
+// warp's softmax numerators (max mh, sum lh) and P V (lane owns output dims
+// 2 lane, 2 lane + 1).  `q` holds the rotated, scaled query heads (qs) and
+// the fed token's k, v (kn, vn), used in FP32 at position a whatever `pre`
+// holds there.  `we` is the warp's [head][32] scratch for the numerators.
+// Returns the number of positions of the block (<= 0: none).
+template <int KBF16, typename Qv>
+__device__ __forceinline__ int attn_block(const Dims& D, int p_lo, int c_end, int a, int lane, const Qv& q,
+                                          float* we, const AttnPre<KBF16>& pre, float (&mh)[kMaxGroup],
+                                          float (&lh)[kMaxGroup], float (&acc)[kMaxGroup][2]) {
   const int grp = D.hq / D.hkv;
-  const int warp = tid >> 5, lane = tid & 31;
-  const int p_lo = c_lo + warp * 32;
   const int p = p_lo + lane;
   const bool valid = p < c_end && p <= a;
   const int nvalid = min(32, min(c_end, a + 1) - p_lo);
@@ -478,33 +478,33 @@ __device__ void attn_chunk(const Dims& D, int c_lo, int c_end, int a, int tid, c
 #pragma unroll
     for (int h = 0; h < kMaxGroup; ++h) {
       if (h < grp) {
-        float acc = 0.f;
+        float dot = 0.f;
         if (KBF16) {
 #pragma unroll
           for (int i = 0; i < kHeadDim / 2; ++i) {
             const uint32_t w = pre.kb[KBF16 ? i : 0];
-            acc = fmaf(q.qs[h][2 * i], __uint_as_float(w << 16), acc);
-            acc = fmaf(q.qs[h][2 * i + 1], __uint_as_float(w & 0xFFFF0000u), acc);
+            dot = fmaf(q.qs[h][2 * i], __uint_as_float(w << 16), dot);
+            dot = fmaf(q.qs[h][2 * i + 1], __uint_as_float(w & 0xFFFF0000u), dot);
           }
         } else {
 #pragma unroll
-          for (int d = 0; d < kHeadDim; ++d) acc = fmaf(q.qs[h][d], pre.kr[KBF16 ? 0 : d], acc);
+          for (int d = 0; d < kHeadDim; ++d) dot = fmaf(q.qs[h][d], pre.kr[KBF16 ? 0 : d], dot);
         }
-        sc[h] = acc;
+        sc[h] = dot;
       }
     }
   } else if (p == a) {   // the new key enters in FP32 from shared memory
 #pragma unroll
     for (int h = 0; h < kMaxGroup; ++h) {
       if (h < grp) {
-        float acc = 0.f;
+        float dot = 0.f;
 #pragma unroll
-        for (int d = 0; d < kHeadDim; ++d) acc = fmaf(q.qs[h][d], q.kn[d], acc);
-        sc[h] = acc;
+        for (int d = 0; d < kHeadDim; ++d) dot = fmaf(q.qs[h][d], q.kn[d], dot);
+        sc[h] = dot;
       }
     }
   }
-  float mh[kMaxGroup], eh[kMaxGroup], lh[kMaxGroup];
+  float eh[kMaxGroup];
 #pragma unroll
   for (int h = 0; h < kMaxGroup; ++h) {
     if (h < grp) {
@@ -517,9 +517,8 @@ __device__ void attn_chunk(const Dims& D, int c_lo, int c_end, int a, int tid, c
   // warp's 32 positions are read back from shared memory four at a time
 #pragma unroll
   for (int h = 0; h < kMaxGroup; ++h)
-    if (h < grp) sm.we[warp][h][lane] = eh[h];
+    if (h < grp) we[h * 32 + lane] = eh[h];
   __syncwarp();
-  float acc[kMaxGroup][2];
 #pragma unroll
   for (int h = 0; h < kMaxGroup; ++h) acc[h][0] = acc[h][1] = 0.f;
 #pragma unroll
@@ -528,7 +527,7 @@ __device__ void attn_chunk(const Dims& D, int c_lo, int c_end, int a, int tid, c
     float4 e4[kMaxGroup];
 #pragma unroll
     for (int h = 0; h < kMaxGroup; ++h)
-      if (h < grp) e4[h] = *reinterpret_cast<const float4*>(&sm.we[warp][h][i4]);
+      if (h < grp) e4[h] = *reinterpret_cast<const float4*>(we + h * 32 + i4);
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
       const int i = i4 + k;
@@ -556,6 +555,21 @@ __device__ void attn_chunk(const Dims& D, int c_lo, int c_end, int a, int tid, c
       }
     }
   }
+  __syncwarp();                                    // `we` may be rewritten by the caller
+  return nvalid;
+}
+
+// One chunk [c_lo, c_end) for the query of position a: every warp's block
+// (attn_block), then the blocks combined in block order into the chunk's
+// (max M, sum l, accumulator o).  `sm` is the scratch (wm, wl, wacc, we, cf,
+// cM, cL).  put(h, dd, o, M, l) receives the accumulator of head h, dim dd.
+template <int KBF16, typename Qv, typename Sc, typename Put>
+__device__ void attn_chunk(const Dims& D, int c_lo, int c_end, int a, int tid, const Qv& q, Sc& sm,
+                           AttnPre<KBF16>& pre, Put put) {
+  const int grp = D.hq / D.hkv;
+  const int warp = tid >> 5, lane = tid & 31;
+  float mh[kMaxGroup], lh[kMaxGroup], acc[kMaxGroup][2];
+  const int nvalid = attn_block<KBF16>(D, c_lo + warp * 32, c_end, a, lane, q, &sm.we[warp][0][0], pre, mh, lh, acc);
 #pragma unroll
   for (int h = 0; h < kMaxGroup; ++h) {
     if (h < grp) {
