@@ -208,12 +208,55 @@ class ClockSampler:
 
 
 def measured_peaks():
+    """(HBM GB/s, dense BF16 tensor TFLOP/s burst, source)."""
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
         with open(p) as fh:
             d = json.load(fh)
-        return float(d["hbm_gbs"]), "measured"
-    return 6800.0, "fallback"
+        return float(d["hbm_gbs"]), float(d["bf16_tflops"]), "measured"
+    return 6800.0, 1900.0, "fallback"
+
+
+# CUDA-core FP32 peak: SMs x 128 FP32 lanes x 2 flops per fused multiply-add
+# x SM clock (the maximum SM clock of the part, 2,070 MHz)
+FP32_LANES_PER_SM = 128
+
+
+def fp32_peak_tflops(n_sm: int, sm_mhz: float) -> float:
+    return n_sm * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
+
+
+TC_KINDS = {"gemv_qkv", "gemv_o", "gemv_gate_up", "gemv_down", "lm_head"}
+
+
+def roofline_of(kind: dict, path: str, fmt: str, n_sm: int, sm_max_mhz: float) -> dict:
+    """The bound of one traced kernel kind from its arithmetic intensity:
+    HBM below the ridge, else the tensor pipe (projections on the
+    tensor-core path) or the CUDA-core FP32 pipe (everything else)."""
+    hbm, bf16, src = measured_peaks()
+    per_ms = kind["ms"] / max(kind["launches"], 1)
+    per_bytes = kind["bytes"] / max(kind["launches"], 1)
+    per_flops = kind.get("flops", 0.0) / max(kind["launches"], 1)
+    ai = per_flops / per_bytes if per_bytes else 0.0
+    if path == "tc" and kind["name"] in TC_KINDS:
+        # FP8 peak = measured BF16 x the nominal 2x ratio of the FP8 rate
+        peak_c, unit_peak = (bf16 * 2 if fmt == "fp8" else bf16), "tensor"
+        peak_src = f"{src} bf16{' x2 (fp8 nominal ratio)' if fmt == 'fp8' else ''}"
+    else:
+        peak_c, unit_peak = fp32_peak_tflops(n_sm, sm_max_mhz), "alu"
+        peak_src = f"derived: {n_sm} SMs x 128 FP32 lanes x 2 x {sm_max_mhz:.0f} MHz"
+    ridge = peak_c * 1e12 / (hbm * 1e9)
+    out = {"kernel": kind["name"], "ms_per_launch": per_ms, "bytes_per_launch": per_bytes,
+           "flops_per_launch": per_flops, "intensity": ai}
+    if ai > ridge:
+        achieved = per_flops / (per_ms / 1000.0) / 1e12
+        out.update({"bound": unit_peak, "achieved": achieved, "peak": peak_c, "unit": "TFLOP/s",
+                    "frac": achieved / peak_c, "peak_source": peak_src})
+    else:
+        achieved = per_bytes / (per_ms / 1000.0) / 1e9
+        out.update({"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                    "peak_source": src})
+    return out
 
 
 def ncu_traffic(kind: str, workload: str):
@@ -328,18 +371,14 @@ def run_gpu(args, wl):
         trace = ctx.encode_intervals(tok_dev, offs, lens, iv, stride, trace=True)
         tot_ms = sum(k["ms"] for k in trace) or 1.0
         dom = max(trace, key=lambda k: k["ms"])
-        per_launch_ms = dom["ms"] / max(dom["launches"], 1)
-        per_launch_bytes = dom["bytes"] / max(dom["launches"], 1)
-        peak, peak_kind = measured_peaks()
-        achieved = per_launch_bytes / (per_launch_ms / 1000.0) / 1e9
-        roofline = {"bound": "hbm", "kernel": dom["name"], "achieved": achieved, "peak": peak, "unit": "GB/s",
-                    "frac": achieved / peak, "peak_source": peak_kind,
-                    "bytes_per_launch": per_launch_bytes, "ms_per_launch": per_launch_ms,
-                    "share": dom["ms"] / tot_ms,
-                    "traffic": ncu_traffic(dom["name"], args.workload)}
+        n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+        roofline = roofline_of(dom, wl.get("path", "gemv"), wl["fmt"], n_sm, 2070.0)
+        roofline["share"] = dom["ms"] / tot_ms
+        roofline["traffic"] = ncu_traffic(dom["name"], args.workload)
         kernels = {k["name"]: {"launches": k["launches"], "ms": round(k["ms"], 3),
                                "share": round(k["ms"] / tot_ms, 4),
-                               "GBps": round(k["bytes"] / (k["ms"] / 1000.0) / 1e9, 1) if k["ms"] > 0 else None}
+                               "GBps": round(k["bytes"] / (k["ms"] / 1000.0) / 1e9, 1) if k["ms"] > 0 else None,
+                               "TFLOPs": round(k["flops"] / (k["ms"] / 1000.0) / 1e12, 2) if k["ms"] > 0 else None}
                    for k in trace if k["launches"]}
         launches_per_step = sum(k["launches"] for k in trace)
         roofline["graphed"] = bool(trace[0]["graphed"])

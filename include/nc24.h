@@ -165,8 +165,10 @@ int nc_encode(nc_ctx* ctx, int n_streams, const int32_t* const* tokens, const in
 
 /* Per-kernel trace of one nc_encode_intervals call: for each kernel kind,
  * the launches, their summed device time (CUDA events around each launch on
- * the context's stream) and the algorithmic bytes they move (weights, KV
- * entries, activations and per-symbol vectors each read or written once). */
+ * the context's stream), the algorithmic bytes they move (weights, distinct
+ * KV entries, activations and per-symbol vectors each read or written once)
+ * and their arithmetic (2 per multiply-add of the projections and of the
+ * attention's scores and weighted values). */
 #define NC_TRACE_KINDS 16
 typedef struct {
   int n_kinds;
@@ -175,6 +177,7 @@ typedef struct {
   int64_t launches[NC_TRACE_KINDS];
   double ms[NC_TRACE_KINDS];
   double bytes[NC_TRACE_KINDS];
+  double flops[NC_TRACE_KINDS];
 } nc_trace;
 
 /* The device half of nc_encode: per-token CDF steps for n_streams streams

@@ -833,9 +833,11 @@ static cudaError_t launch_model_tc(nc_ctx* ctx, const Batch& b, StepMarks& m) {
   return e;
 }
 
-// Algorithmic bytes of one launch of each kind for B active rows whose
-// attention windows hold ctx_sum entries in total (the fed tokens included).
-static void step_bytes(const nc_ctx* ctx, int B, double ctx_sum, double* out) {
+// Algorithmic bytes and arithmetic of one launch of each kind for B active
+// rows whose attention windows hold ctx_sum entries in total (the fed tokens
+// included), kv_unique of them distinct (a prefill's rows of one stream
+// share their window).
+static void step_cost(const nc_ctx* ctx, int B, double ctx_sum, double kv_unique, double* out, double* fl) {
   const Dims& D = ctx->D;
   const double esz = ctx->fmt == NC_FP32 ? 4 : ctx->fmt == NC_BF16 ? 2 : 1;
   const double kvsz = D.kv_bf16 ? 2 : 4;
@@ -844,17 +846,23 @@ static void step_bytes(const nc_ctx* ctx, int B, double ctx_sum, double* out) {
     return w + B * cols * 4 + B * out_rows * 4 * (resid ? 2 : 1);
   };
   const double qd = (double)D.hq * kHeadDim;
-  for (int k = 0; k < TK_COUNT; ++k) out[k] = 0;
+  for (int k = 0; k < TK_COUNT; ++k) out[k] = fl[k] = 0;
   out[TK_PREPARE] = B * 24.0;
   out[TK_EMBED] = B * D.d * (esz + 4);
   out[TK_QKV] = gemv(D.qkv_rows, D.d, D.qkv_rows, false) + B * D.d * 4;
-  out[TK_ATTN] = D.hkv * 2.0 * kHeadDim * kvsz * ctx_sum + B * (D.qkv_rows * 4.0 + D.hq * kHeadDim * 4.0);
+  out[TK_ATTN] = D.hkv * 2.0 * kHeadDim * kvsz * kv_unique + B * (D.qkv_rows * 4.0 + qd * 4.0);
   out[TK_O] = gemv(D.d, qd, D.d, true);
   out[TK_GU] = gemv(2.0 * D.F, D.d, D.F, false);
   out[TK_DOWN] = gemv(D.d, D.F, D.d, true);
   out[TK_LMHEAD] = gemv(D.V, D.d, D.V, false);
   out[TK_VOCAB] = B * D.V * 16.0 + B * 8.0;
   out[TK_NGRAM] = B * (3.0 * sizeof(NgEntry) + 64.0);
+  fl[TK_QKV] = 2.0 * B * D.qkv_rows * D.d;
+  fl[TK_ATTN] = 2.0 * 2.0 * qd * ctx_sum;          // scores and weighted values
+  fl[TK_O] = 2.0 * B * D.d * qd;
+  fl[TK_GU] = 2.0 * B * 2.0 * D.F * D.d;
+  fl[TK_DOWN] = 2.0 * B * D.d * D.F;
+  fl[TK_LMHEAD] = 2.0 * B * (double)D.V * D.d;
 }
 
 // Host-side checks and staging of a batch of open streams.
@@ -1106,16 +1114,20 @@ static int encode_prefill(nc_ctx* ctx, int n, int m, const int32_t* tok_dev, con
       break;
     }
     if (trace) {
-      // forward: the live rows and their windows; then each position's active streams
+      // forward: the live rows and their windows (a stream's rows share the
+      // window of its last row); then each position's active streams
       int64_t rows = 0;
-      double ctx_sum = 0;
-      for (int j = 0; j < n; ++j)
-        for (int64_t a = p; a < std::min(p + m, lens_h[j]); ++a) {
+      double ctx_sum = 0, kv_unique = 0;
+      for (int j = 0; j < n; ++j) {
+        const int64_t last = std::min(p + m, lens_h[j]) - 1;
+        if (last >= p) kv_unique += (double)(last - start_at(last) + 1);
+        for (int64_t a = p; a <= last; ++a) {
           ++rows;
           ctx_sum += (double)(a - start_at(a) + 1);
         }
-      double fwd[TK_COUNT];
-      step_bytes(ctx, (int)rows, ctx_sum, fwd);
+      }
+      double fwd[TK_COUNT], ffl[TK_COUNT];
+      step_cost(ctx, (int)rows, ctx_sum, kv_unique, fwd, ffl);
       fwd[TK_PREPARE] = n * (double)m * 28;
       e = cudaEventSynchronize(mk.ev[mk.n]);
       if (e != cudaSuccess) {
@@ -1126,20 +1138,22 @@ static int encode_prefill(nc_ctx* ctx, int n, int m, const int32_t* tok_dev, con
         float ms = 0.f;
         cudaEventElapsedTime(&ms, mk.ev[i], mk.ev[i + 1]);
         const int kd = mk.kind[i];
-        double by = fwd[kd];
+        double by = fwd[kd], fo = ffl[kd];
         if (i >= fwd_marks) {                       // the chunk's vocabulary passes
-          by = 0;
+          by = fo = 0;
           for (int64_t a = p; a < p + m; ++a) {
             int act = 0;
             for (int j = 0; j < n; ++j) act += lens_h[j] > a;
-            double per[TK_COUNT];
-            step_bytes(ctx, act, 0.0, per);
+            double per[TK_COUNT], pfl[TK_COUNT];
+            step_cost(ctx, act, 0.0, 0.0, per, pfl);
             by += per[kd];
+            fo += pfl[kd];
           }
         }
         trace->ms[kd] += ms;
         trace->launches[kd] += 1;
         trace->bytes[kd] += by;
+        trace->flops[kd] += fo;
       }
     }
   }
@@ -1222,8 +1236,8 @@ static int encode_device(nc_ctx* ctx, int n, const std::vector<int>& slot_of, co
         if (k >= L) start = ((k - L) / C + 1) * C;
       }
       const int n_ctx = (int)(k - start + 1);
-      double bytes[TK_COUNT];
-      step_bytes(ctx, active, (double)active * n_ctx, bytes);
+      double bytes[TK_COUNT], flops[TK_COUNT];
+      step_cost(ctx, active, (double)active * n_ctx, (double)active * n_ctx, bytes, flops);
       e = cudaEventSynchronize(mk.ev[mk.n]);
       if (e != cudaSuccess) {
         st = fail_cuda(ctx, e, "trace sync");
@@ -1236,6 +1250,7 @@ static int encode_device(nc_ctx* ctx, int n, const std::vector<int>& slot_of, co
         trace->ms[kd] += ms;
         trace->launches[kd] += 1;
         trace->bytes[kd] += bytes[kd];
+        trace->flops[kd] += flops[kd];
       }
     }
   }

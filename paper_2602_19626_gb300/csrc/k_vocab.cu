@@ -119,16 +119,10 @@ __device__ float block_sum(float v, Sh& sh) {
   return r;
 }
 
-// Online-softmax pair (max, sum of exp relative to max); combining is exact
-// in its max and has a fixed rounding for a fixed order of operands.
+// Softmax statistics: the maximum and the sum of exp(s - max).
 struct MS {
   float m, s;
 };
-__device__ __forceinline__ MS ms_combine(MS a, MS b) {
-  const float M = fmaxf(a.m, b.m);
-  if (M == -INFINITY) return MS{M, 0.f};
-  return MS{M, a.s * expf(a.m - M) + b.s * expf(b.m - M)};
-}
 
 template <int E>
 __device__ __forceinline__ void load_run(const float* src, int v0, int V, float (&out)[E], float fill) {
@@ -160,40 +154,53 @@ __device__ __forceinline__ void store_run(float* dst, int v0, int V, const float
   }
 }
 
-// Round 1: softmax statistics (M, S) of s over the cluster's vocabulary.
+// Round 1 of the step: the softmax of s over the cluster's vocabulary in
+// two passes.  The maximum M (exact, order-free), then the numerators
+// e_i = exp(s_i - M) and their sum S: thread (i in order) -> warp (xor tree)
+// -> CTA (warps in order) -> cluster (ranks in order).  e_i is returned for
+// p_i = e_i / S.
 template <int E, int CL, typename Sh>
-__device__ MS softmax_stats(const float (&s)[E], cg::cluster_group& cl, Sh& sh) {
+__device__ MS softmax_two_pass(const float (&s)[E], float (&e)[E], cg::cluster_group& cl, Sh& sh) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  MS t{-INFINITY, 0.f};
+  float m = -INFINITY;
 #pragma unroll
-  for (int i = 0; i < E; ++i) t.m = fmaxf(t.m, s[i]);
-  if (t.m != -INFINITY) {
-#pragma unroll
-    for (int i = 0; i < E; ++i) t.s += expf(s[i] - t.m);
-  }
-#pragma unroll
-  for (int o = 16; o; o >>= 1) {
-    MS u{__shfl_xor_sync(0xffffffffu, t.m, o), __shfl_xor_sync(0xffffffffu, t.s, o)};
-    t = ms_combine(t, u);
-  }
-  if (lane == 0) {
-    sh.wm[w] = t.m;
-    sh.wsum[w] = t.s;
-  }
+  for (int i = 0; i < E; ++i) m = fmaxf(m, s[i]);
+  m = warp_max(m);
+  if (lane == 0) sh.wm[w] = m;
   __syncthreads();
   if (threadIdx.x == 0) {
-    MS b{sh.wm[0], sh.wsum[0]};
-    for (int i = 1; i < Sh::kNW; ++i) b = ms_combine(b, MS{sh.wm[i], sh.wsum[i]});
-    sh.cl_m = b.m;
-    sh.cl_s = b.s;
+    float b = sh.wm[0];
+    for (int i = 1; i < Sh::kNW; ++i) b = fmaxf(b, sh.wm[i]);
+    sh.cl_m = b;
   }
   cl.sync();
-  MS g{-INFINITY, 0.f};
-  for (int r = 0; r < CL; ++r) {
-    const Sh* o = cl.map_shared_rank(&sh, r);
-    g = ms_combine(g, MS{o->cl_m, o->cl_s});
+  float M = -INFINITY;
+#pragma unroll
+  for (int r = 0; r < CL; ++r) M = fmaxf(M, cl.map_shared_rank(&sh, r)->cl_m);
+  float t = 0.f;
+  if (M != -INFINITY) {
+#pragma unroll
+    for (int i = 0; i < E; ++i) {
+      e[i] = expf(s[i] - M);
+      t += e[i];
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < E; ++i) e[i] = 0.f;
   }
-  return g;
+  t = warp_sum(t);
+  if (lane == 0) sh.wsum[w] = t;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float b = 0.f;
+    for (int i = 0; i < Sh::kNW; ++i) b += sh.wsum[i];
+    sh.cl_s = b;
+  }
+  cl.sync();
+  float S = 0.f;
+#pragma unroll
+  for (int r = 0; r < CL; ++r) S += cl.map_shared_rank(&sh, r)->cl_s;
+  return MS{M, S};
 }
 
 struct QuantResult {
@@ -451,12 +458,12 @@ __device__ bool vocab_pass(const Dims& D, const Batch& b, const VocabIO& io, int
   const float inv_tau = 1.0f / D.tau;             // exact for tau = 1
 #pragma unroll
   for (int i = 0; i < E; ++i) s[i] = (v0 + i < V) ? fmaf(s[i], inv_tau, bias[i]) : -INFINITY;
-  const MS ms = softmax_stats<E, kStepCluster>(s, cl, sh);
-  const float M = ms.m, S = ms.s;
   float pt[E];
+  const MS ms = softmax_two_pass<E, kStepCluster>(s, pt, cl, sh);
+  const float M = ms.m, S = ms.s;
   const float inv_S = 1.0f / S;
 #pragma unroll
-  for (int i = 0; i < E; ++i) pt[i] = (v0 + i < V) ? expf(s[i] - M) * inv_S : 0.f;
+  for (int i = 0; i < E; ++i) pt[i] = (v0 + i < V) ? pt[i] * inv_S : 0.f;
   if (io.probe_pt) store_run<E>(io.probe_pt + (size_t)j * V, v0, V, pt);
 
   // ---- mix (Sec. 3.5): LLM alone during warm-up

@@ -51,7 +51,7 @@ NC_TRACE_KINDS = 16
 class nc_trace(C.Structure):
     _fields_ = [("n_kinds", C.c_int), ("graphed", C.c_int), ("name", (C.c_char * 32) * NC_TRACE_KINDS),
                 ("launches", C.c_int64 * NC_TRACE_KINDS), ("ms", C.c_double * NC_TRACE_KINDS),
-                ("bytes", C.c_double * NC_TRACE_KINDS)]
+                ("bytes", C.c_double * NC_TRACE_KINDS), ("flops", C.c_double * NC_TRACE_KINDS)]
 
 
 _P = C.c_void_p
@@ -312,7 +312,7 @@ class Context:
         if not tr:
             return None
         return [dict(name=tr.name[k].value.decode(), launches=tr.launches[k], ms=tr.ms[k], bytes=tr.bytes[k],
-                     graphed=bool(tr.graphed)) for k in range(tr.n_kinds)]
+                     flops=tr.flops[k], graphed=bool(tr.graphed)) for k in range(tr.n_kinds)]
 
     def decode(self, data: bytes):
         buf = np.frombuffer(data, dtype=np.uint8).copy()
