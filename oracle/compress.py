@@ -1,14 +1,20 @@
 """The compression loop of Algorithm 1 and its mirror-image decompression.
 
-Per stream, for i = 1..n (Algorithm 1; confidence skip off):
+Per stream, for i = 1..n (Algorithm 1):
     z       = LLM(t_1..t_{i-1})      (BOS at position 0 feeds the first step)
     p_llm   = softmax(z / tau)                        (Sec. 3.2)
     p_tilde = softmax(log p_llm + b)                  (Sec. 3.6)
     p_ng    = N-gram prediction                        (Sec. 3.4)
-    p       = p_tilde during warm-up (i <= 100), else w_llm p_tilde + w_ng p_ng
-                                                       (Sec. 3.5)
+    p       = p_ng when the confidence skip is on and H(p_ng) < 1.5 bits
+              (Sec. 3.7, Algorithm 1); else p_tilde during warm-up
+              (i <= 100), else w_llm p_tilde + w_ng p_ng (Sec. 3.5)
     cdf     = probs_to_cdf(binary32(p), 2^24)          (Sec. 3.3)
-    encode t_i; then update head, mixer and N-gram with t_i.
+    encode t_i; then update head, mixer and N-gram with t_i (a skipped token
+    updates the N-gram only: the LLM produced no distribution for the head
+    and the mixer to learn from).
+The LLM step still runs on a skipped token, so that the KV cache holds every
+token (the paper evaluates skipped tokens later, in a batch; the cache is the
+same).
 The order "head acts on the LLM distribution, then the mix, then the
 quantiser" follows the ablation's build-up (CDF-24, then head, then N-gram).
 
@@ -43,6 +49,7 @@ class StepConfig:
     use_ngram: bool = True
     use_head: bool = True
     rule: str = "paper"          # or "mixed_nll"
+    skip: bool = False           # confidence-based LLM skip (Sec. 3.7)
 
     @property
     def T(self) -> int:
@@ -56,7 +63,18 @@ class StepConfig:
             f |= container.FLAG_HEAD
         if self.rule == "mixed_nll":
             f |= container.FLAG_MIXED_NLL
+        if self.skip:
+            f |= container.FLAG_SKIP
         return f
+
+
+SKIP_BITS = 1.5                   # the skip threshold on H(p_ng) in bits (Sec. 3.7)
+
+
+def entropy_bits(p: np.ndarray) -> float:
+    """Shannon entropy -sum p log2 p in bits, with 0 log 0 = 0."""
+    q = p[p > 0]
+    return float(-np.sum(q * np.log2(q)))
 
 
 @dataclass
@@ -72,6 +90,7 @@ class StreamState:
     i: int = 0                        # tokens coded so far
     last: int = 0                     # token fed at the next step (BOS first)
     ideal_bits: float = 0.0
+    skipped: int = 0                  # tokens coded by the N-gram alone
     records: list = field(default_factory=list)
 
     @classmethod
@@ -95,7 +114,10 @@ class StreamState:
         pl = llm_softmax(z, cfg.tau)
         pt = self.head.adjust(pl) if cfg.use_head else pl
         png = self.ngram.predict() if cfg.use_ngram else None
-        if cfg.use_ngram and i > cfg.warmup:
+        self._skip = bool(cfg.skip and cfg.use_ngram and entropy_bits(png) < SKIP_BITS)
+        if self._skip:
+            p = png
+        elif cfg.use_ngram and i > cfg.warmup:
             if cfg.rule == "mixed_nll":
                 w = np.exp(self.theta - self.theta.max())
                 w /= w.sum()
@@ -117,7 +139,9 @@ class StreamState:
         i = self.i + 1
         self.ideal_bits += -np.log2(p[t])
         warm = i <= cfg.warmup or not cfg.use_ngram
-        if cfg.rule == "mixed_nll":
+        if self._skip:
+            self.skipped += 1
+        elif cfg.rule == "mixed_nll":
             gb, gth = mixed_nll_grad(pt, png if png is not None else pt, self.theta, t, warm)
             if cfg.use_head:
                 self.head.b -= cfg.alpha * gb
@@ -142,7 +166,7 @@ def compress_stream(model, tokens, cfg: StepConfig, record_steps: int = 0):
         st.update(int(t))
     payload, nbits = enc.finish()
     return dict(payload=payload, nbits=nbits, ideal_bits=st.ideal_bits,
-                records=st.records, min_range=enc.min_range, slides=st.cache.slides)
+                records=st.records, min_range=enc.min_range, slides=st.cache.slides, skipped=st.skipped)
 
 
 def decompress_stream(model, payload: bytes, nbits: int, n: int, cfg: StepConfig):
