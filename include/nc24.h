@@ -94,6 +94,11 @@ typedef struct {
                                        position at a time.  At most 32768; needs
                                        prefill_rows x vocab x 4 bytes of logits on the
                                        device. */
+  int skip;                         /* 1: confidence-based LLM skip (Sec. 3.7): a token whose
+                                       N-gram distribution has entropy below 1.5 bits is
+                                       coded with p = p_ng, and only the N-gram learns from
+                                       it.  Needs ngram_order > 0.  Recorded in the
+                                       container's flags. */
 } nc_config;
 
 /* Fill *cfg with the SmolLM2-135M shape and the paper's defaults

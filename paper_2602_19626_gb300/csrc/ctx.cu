@@ -172,6 +172,7 @@ extern "C" void nc_config_default(nc_config* c) {
   c->device = 0;
   c->cuda_stream = nullptr;
   c->prefill_rows = 0;
+  c->skip = 0;
 }
 
 extern "C" const char* nc_status_str(int s) {
@@ -462,6 +463,7 @@ extern "C" int nc_ctx_create(const nc_config* cfg, const void* weights, size_t n
     if (e && (e[0] == '1' || e[0] == '2' || e[0] == '4' || e[0] == '8') && e[1] == 0) D.attn_cluster = e[0] - '0';
   }
   D.order = c.ngram_order;
+  D.skip = c.skip && c.ngram_order > 0;
   D.use_head = c.use_head;
   D.warmup = c.warmup;
   D.rule = c.update_rule;
@@ -1020,6 +1022,7 @@ static uint8_t flags_byte(const nc_config& c) {
   uint8_t f = 0;
   if (c.ngram_order > 0) f |= 1;
   if (c.use_head) f |= 2;
+  if (c.ngram_order > 0 && c.skip) f |= 4;
   if (c.update_rule == NC_RULE_MIXED_NLL) f |= 8;
   return f;
 }

@@ -14,6 +14,7 @@ constexpr int kMaxOrder = 3;           // N-gram context lengths 1..3
 constexpr int kMaxGroup = 4;           // query heads per KV head supported
 constexpr int kVocabCluster = 8;       // CTAs per row in the standalone quantiser kernels
 constexpr int kVocabThreads = 512;
+constexpr float kSkipBits = 1.5f;      // the skip threshold on the N-gram entropy (Sec. 3.7)
 constexpr int kStepCluster = 8;        // CTAs per stream in the per-token vocabulary pass
 constexpr int kStepThreads = 512;
 constexpr unsigned long long kEmptyKey = ~0ull;
@@ -74,6 +75,7 @@ struct Dims {
   int attn_cluster;         // CTAs per (stream, KV head) in attention: 1, 2, 4 or 8; 0 = by batch size
   int n_sm;                 // SMs of the device
   int order;                // N-gram order (0 = off)
+  int skip;                 // confidence skip: p = p_ng when H(p_ng) < kSkipBits
   int use_head;
   int warmup;
   int rule;

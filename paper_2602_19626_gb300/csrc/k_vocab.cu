@@ -78,12 +78,12 @@ __device__ __forceinline__ ArgMax better(ArgMax a, ArgMax b) {
 template <int NW>
 struct VocabSharedT {
   static constexpr int kNW = NW;
-  float wm[NW], wsum[NW];
+  float wm[NW], wsum[NW], wh[NW];
   unsigned long long wc[NW], wb[NW];
   ArgMax wa[NW];
   uint32_t wscan[NW];
   // published to the cluster
-  float cl_m, cl_s;
+  float cl_m, cl_s, cl_h;
   unsigned long long cl_csum, cl_below;
   ArgMax cl_arg;
   uint32_t cl_bad;
@@ -160,7 +160,8 @@ __device__ __forceinline__ void store_run(float* dst, int v0, int V, const float
 // -> CTA (warps in order) -> cluster (ranks in order).  e_i is returned for
 // p_i = e_i / S.
 template <int E, int CL, typename Sh>
-__device__ MS softmax_two_pass(const float (&s)[E], float (&e)[E], cg::cluster_group& cl, Sh& sh) {
+__device__ MS softmax_two_pass(const float (&s)[E], float (&e)[E], float h_in, float& h_out, cg::cluster_group& cl,
+                               Sh& sh) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   float m = -INFINITY;
 #pragma unroll
@@ -188,18 +189,32 @@ __device__ MS softmax_two_pass(const float (&s)[E], float (&e)[E], cg::cluster_g
 #pragma unroll
     for (int i = 0; i < E; ++i) e[i] = 0.f;
   }
+  // the second sum of the round: h_in, this thread's share of another sum
+  // (the N-gram entropy), reduced in the same order
   t = warp_sum(t);
-  if (lane == 0) sh.wsum[w] = t;
+  const float hw = warp_sum(h_in);
+  if (lane == 0) {
+    sh.wsum[w] = t;
+    sh.wh[w] = hw;
+  }
   __syncthreads();
   if (threadIdx.x == 0) {
-    float b = 0.f;
-    for (int i = 0; i < Sh::kNW; ++i) b += sh.wsum[i];
+    float b = 0.f, bh = 0.f;
+    for (int i = 0; i < Sh::kNW; ++i) {
+      b += sh.wsum[i];
+      bh += sh.wh[i];
+    }
     sh.cl_s = b;
+    sh.cl_h = bh;
   }
   cl.sync();
-  float S = 0.f;
+  float S = 0.f, H = 0.f;
 #pragma unroll
-  for (int r = 0; r < CL; ++r) S += cl.map_shared_rank(&sh, r)->cl_s;
+  for (int r = 0; r < CL; ++r) {
+    S += cl.map_shared_rank(&sh, r)->cl_s;
+    H += cl.map_shared_rank(&sh, r)->cl_h;
+  }
+  h_out = H;
   return MS{M, S};
 }
 
@@ -458,8 +473,17 @@ __device__ bool vocab_pass(const Dims& D, const Batch& b, const VocabIO& io, int
   const float inv_tau = 1.0f / D.tau;             // exact for tau = 1
 #pragma unroll
   for (int i = 0; i < E; ++i) s[i] = (v0 + i < V) ? fmaf(s[i], inv_tau, bias[i]) : -INFINITY;
-  float pt[E];
-  const MS ms = softmax_two_pass<E, kStepCluster>(s, pt, cl, sh);
+  // the N-gram entropy in bits (confidence skip, Sec. 3.7), -p log2 p summed
+  // with the softmax normaliser
+  float h_in = 0.f;
+  if (D.skip) {
+#pragma unroll
+    for (int i = 0; i < E; ++i)
+      if (v0 + i < V && png[i] > 0.f) h_in -= png[i] * log2f(png[i]);
+  }
+  float pt[E], H = 0.f;
+  const MS ms = softmax_two_pass<E, kStepCluster>(s, pt, h_in, H, cl, sh);
+  const bool skipped = D.skip && H < kSkipBits;
   const float M = ms.m, S = ms.s;
   const float inv_S = 1.0f / S;
 #pragma unroll
@@ -473,7 +497,7 @@ __device__ bool vocab_pass(const Dims& D, const Batch& b, const VocabIO& io, int
   const float w0 = e0 / (e0 + e1), w1 = e1 / (e0 + e1);
   float p[E];
 #pragma unroll
-  for (int i = 0; i < E; ++i) p[i] = mixing ? w0 * pt[i] + w1 * png[i] : pt[i];
+  for (int i = 0; i < E; ++i) p[i] = skipped ? png[i] : mixing ? w0 * pt[i] + w1 * png[i] : pt[i];
   if (io.probe_p) store_run<E>(io.probe_p + (size_t)j * V, v0, V, p);
 
   // ---- round 2: counts, residual, argmax, interval; publish t*'s values
@@ -507,7 +531,7 @@ __device__ bool vocab_pass(const Dims& D, const Batch& b, const VocabIO& io, int
     if (io.cdf) scan_round<E>(c, v0, V, 1u << D.log2T, io.cdf + (size_t)j * (V + 1), cl, sh);
   }
 
-  if (io.update) {
+  if (io.update && !skipped) {                     // a skipped token teaches the N-gram only
     const StepShared* o = cl.map_shared_rank(&sh, t_obs / chunk);
     const float pts = o->cl_obs[0], pngs = o->cl_obs[1], lpt = o->cl_obs[2];
     float scale = 1.f;

@@ -41,7 +41,7 @@ class nc_config(C.Structure):
         ("temperature", C.c_float),
         ("warmup", C.c_int), ("weight_fmt", C.c_int), ("update_rule", C.c_int), ("path", C.c_int),
         ("max_streams", C.c_int), ("device", C.c_int), ("cuda_stream", C.c_void_p),
-        ("prefill_rows", C.c_int),
+        ("prefill_rows", C.c_int), ("skip", C.c_int),
     ]
 
 
@@ -209,7 +209,7 @@ def nc_mix_nll_bwd(z, b, p_ng, theta, target, warm, gout, tau, db, dtheta, strea
 
 def make_config(shape, fmt="bf16", rule="paper", max_streams=1, ngram_order=3, use_head=True,
                 warmup=100, log2_total=24, floor=1, alpha=1e-3, eta=1.0, w_llm=0.85, tau=1.0,
-                device=0, stream=None, path="gemv", prefill_rows=0) -> nc_config:
+                device=0, stream=None, path="gemv", prefill_rows=0, skip=False) -> nc_config:
     """nc_config from a shape with the fields of synthetic.ModelShape."""
     c = nc_config_default()
     c.n_layers, c.d_model, c.n_heads = shape.n_layers, shape.d_model, shape.n_heads
@@ -226,6 +226,7 @@ def make_config(shape, fmt="bf16", rule="paper", max_streams=1, ngram_order=3, u
     c.max_streams, c.device = max_streams, device
     c.cuda_stream = _stream_ptr(stream) if stream is not None else None
     c.prefill_rows = prefill_rows
+    c.skip = int(bool(skip))
     return c
 
 
