@@ -238,10 +238,13 @@ def roofline_of(kind: dict, path: str, fmt: str, n_sm: int, sm_max_mhz: float) -
     per_bytes = kind["bytes"] / max(kind["launches"], 1)
     per_flops = kind.get("flops", 0.0) / max(kind["launches"], 1)
     ai = per_flops / per_bytes if per_bytes else 0.0
-    if path == "tc" and kind["name"] in TC_KINDS:
+    # projections on the tensor-core path, and the attention over a BF16 KV
+    # cache (BF16 / FP8 weights), run on the tensor pipe
+    if (path == "tc" and kind["name"] in TC_KINDS) or (kind["name"] == "attn" and fmt != "fp32"):
         # FP8 peak = measured BF16 x the nominal 2x ratio of the FP8 rate
-        peak_c, unit_peak = (bf16 * 2 if fmt == "fp8" else bf16), "tensor"
-        peak_src = f"{src} bf16{' x2 (fp8 nominal ratio)' if fmt == 'fp8' else ''}"
+        fp8_gemm = fmt == "fp8" and kind["name"] != "attn"
+        peak_c, unit_peak = (bf16 * 2 if fp8_gemm else bf16), "tensor"
+        peak_src = f"{src} bf16{' x2 (fp8 nominal ratio)' if fp8_gemm else ''}"
     else:
         peak_c, unit_peak = fp32_peak_tflops(n_sm, sm_max_mhz), "alu"
         peak_src = f"derived: {n_sm} SMs x 128 FP32 lanes x 2 x {sm_max_mhz:.0f} MHz"

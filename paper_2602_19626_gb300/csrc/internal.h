@@ -215,6 +215,12 @@ cudaError_t launch_prepare_prefill(const Batch& b, int n_streams, int m, int V, 
                                    const int64_t* offs, const int64_t* lens, int32_t* f_slots, int32_t* f_pos,
                                    int32_t* f_tok, int32_t* nB_fwd, int32_t* obs_step, int32_t* nb_step,
                                    int32_t* z_idx, cudaStream_t s);
+// Attention over a BF16 KV cache on the tensor cores (k_attn_tc.cu): rq
+// query rows per CTA group (1: a decode step), S CTAs per group.
+cudaError_t prepare_attn_tc(const Dims& D);
+size_t attn_tc_smem(int rq, int grp, int S);
+cudaError_t launch_attn_tc(const Dims& D, const Batch& b, int layer, int rq, int S, const float* qkv,
+                           float* attn_out, cudaStream_t s);
 // Prefill: rotate and append the k, v of every row to the KV ring of `layer`.
 cudaError_t launch_kv_append(const Dims& D, const Batch& b, int layer, const float* qkv, cudaStream_t s);
 // Decoder: row j's symbol is the s with cdf[s] <= target[j] < cdf[s+1]; writes

@@ -165,7 +165,12 @@ def test_ngram_eviction_parity(nc):
 # BF16 / FP8 weights keep the KV cache in BF16; against the oracle on the
 # dequantised weights (FP64 cache) the cache's rounding (relative 2^-9 per
 # stored element) leaves a few 1e-3 on logits of magnitude ~1.
-@pytest.mark.parametrize("fmt,tol_fp32,tol_fmt", [("fp32", 1e-4, 1e-4), ("bf16", 3e-2, 5e-3), ("fp8", None, 5e-3)])
+# Against the dequantised-weight oracle the BF16 / FP8 paths differ by their
+# activation arithmetic alone: the KV cache in BF16, and the tensor-core
+# attention's BF16 query and probabilities (relative rounding 2^-9 each), whose
+# effect on the 30-layer logits measures about 9e-3; the bound is 1.5e-2.
+@pytest.mark.parametrize("fmt,tol_fp32,tol_fmt", [("fp32", 1e-4, 1e-4), ("bf16", 3e-2, 1.5e-2),
+                                                   ("fp8", None, 1.5e-2)])
 def test_full_model_logits(nc, fmt, tol_fp32, tol_fmt):
     """30-layer SmolLM2-135M shape: logits of the first steps against the
     oracle on the FP32 weights and on the format's dequantised weights (FP8
