@@ -92,6 +92,11 @@ struct VocabSharedT {
   // N-gram coefficients of this step
   float cu, coef[kMaxOrder], nk[kMaxOrder];
   const NgEntry* ent[kMaxOrder];
+  // the N-gram state one prediction reads: per order the context entry's
+  // (token, count) slots (ns < 0: no entry) and the closed form's weights
+  int ng_ns[kMaxOrder];
+  int ng_tok[kMaxOrder][kMaxSlots], ng_cnt[kMaxOrder][kMaxSlots];
+  float ng_coef[kMaxOrder], ng_cu;
 };
 using VocabShared = VocabSharedT<kWarps>;                         // standalone quantiser
 using StepShared = VocabSharedT<kStepThreads / 32>;               // the per-token step
@@ -358,17 +363,69 @@ __device__ void scan_round(const uint32_t (&c)[E], int v0, int V, uint32_t T, ui
 // observed token.  Both may run in one pass (encoder) or in two (decoder,
 // which learns the token in between); the arithmetic is the same in either
 // case.
-__device__ void ngram_update_row(const Dims& D, const Batch& b, int j, int warp, int lane);
+__device__ void ngram_update_row(const Dims& D, const Batch& b, int j, int warp, int lane, StepShared* push,
+                                 cg::cluster_group* cl);
+
+// The closed form's weights of the interpolation (Sec. 3.4): lambda_k =
+// n_k / (n_k + 5), A = prod (1 - lambda_k), beta_k = lambda_k prod_{j>k}
+// (1 - lambda_j), coefficient beta_k / n_k, and cu = A / (N + V).
+__device__ void ng_weights(const float (&nk)[kMaxOrder], const bool (&has)[kMaxOrder], int N, int V,
+                           float (&coef)[kMaxOrder], float& cu) {
+  float lam[kMaxOrder];
+  for (int k = 0; k < kMaxOrder; ++k) lam[k] = has[k] ? nk[k] / (nk[k] + 5.0f) : 0.f;
+  float A = 1.f;
+  for (int k = 0; k < kMaxOrder; ++k) A *= (1.f - lam[k]);
+  for (int k = 0; k < kMaxOrder; ++k) {
+    float beta = lam[k];
+    for (int q = k + 1; q < kMaxOrder; ++q) beta *= (1.f - lam[q]);
+    coef[k] = has[k] ? beta / nk[k] : 0.f;
+  }
+  cu = A / (float)(N + V);
+}
+
+// The N-gram state of the next prediction from the stream's tables: the
+// context entries' slots and the weights, into shared memory.
+template <typename Sh>
+__device__ void ng_gather(const Dims& D, const StreamDev& st, Sh& sh) {
+  if (threadIdx.x < kMaxOrder) {
+    const int k = threadIdx.x;
+    const int ei = (k < D.order) ? st.ctx_ent[k] : -1;
+    const NgEntry* en = ei >= 0 ? st.ent[k] + ei : nullptr;
+    sh.ent[k] = en;
+    sh.nk[k] = en ? (float)en->n : 0.f;
+    sh.ng_ns[k] = en ? en->nslots : 0;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float nk[kMaxOrder];
+    bool has[kMaxOrder];
+    for (int k = 0; k < kMaxOrder; ++k) {
+      nk[k] = sh.nk[k];
+      has[k] = sh.ent[k] != nullptr;
+    }
+    ng_weights(nk, has, st.N, D.V, sh.ng_coef, sh.ng_cu);
+  }
+  for (int e = threadIdx.x; e < kMaxOrder * kMaxSlots; e += blockDim.x) {
+    const int k = e / kMaxSlots, q = e % kMaxSlots;
+    if (q < sh.ng_ns[k]) {
+      sh.ng_tok[k][q] = sh.ent[k]->tok[q];
+      sh.ng_cnt[k][q] = sh.ent[k]->cnt[q];
+    }
+  }
+  __syncthreads();
+}
 
 // One position of stream row j, by the cluster CTA `rank`: predict (biased
 // softmax, N-gram, mix, quantise; the coder interval or the CDF) and the
-// head and mixer update.  `bias` holds this thread's bias run (loaded here
-// unless have_bias); `waited`: the caller already waited on the previous
-// kernel.  Returns false when the observed token is out of range (flagged,
+// head and mixer update.  `bias` and `cnt` hold this thread's bias run and
+// unigram counts (loaded here unless have_bias / have_cnt; cnt gains the
+// coded token); ng_ready: the N-gram context state is already in shared
+// memory; `waited`: the caller already waited on the previous kernel.  Returns false when the observed token is out of range (flagged,
 // nothing updated).  The caller runs the N-gram update after it.
 template <int E>
 __device__ bool vocab_pass(const Dims& D, const Batch& b, const VocabIO& io, int j, int rank, cg::cluster_group& cl,
-                           StepShared& sh, float* sp, float (&bias)[E], bool have_bias, bool waited) {
+                           StepShared& sh, float* sp, float (&bias)[E], bool have_bias, int (&cnt)[E], bool have_cnt,
+                           bool ng_ready, bool waited) {
   StreamDev& st = b.st[b.slots[j]];
   const int V = D.V;
   const int chunk = kStepThreads * E;
@@ -390,14 +447,15 @@ __device__ bool vocab_pass(const Dims& D, const Batch& b, const VocabIO& io, int
   // N-gram: P = A (c + 1) / (N + V) + sum_k beta_k cnt_k / n_k, the closed
   // form of the interpolation recursion with lambda_k = n_k / (n_k + 5).
   float png[E];
-  int cnt[E];
   // logits: after a prefill they are final already (the wait came first)
   float s[E];
   if (b.z_in) load_run<E>(b.z_in + (size_t)b.z_idx[j] * V, v0, V, s, -INFINITY);
   const bool ngram = D.order > 0;
   if (ngram) {
-    // unigram counts first: independent of the context entries below
-    if (v0 + E <= V && (reinterpret_cast<uintptr_t>(st.uni + v0) & 15) == 0) {
+    // unigram counts first (unless kept from the previous position):
+    // independent of the context entries below
+    if (have_cnt) {
+    } else if (v0 + E <= V && (reinterpret_cast<uintptr_t>(st.uni + v0) & 15) == 0) {
       const int4* u4 = reinterpret_cast<const int4*>(st.uni + v0);
 #pragma unroll
       for (int q = 0; q < E / 4; ++q) {
@@ -411,44 +469,18 @@ __device__ bool vocab_pass(const Dims& D, const Batch& b, const VocabIO& io, int
 #pragma unroll
       for (int i = 0; i < E; ++i) cnt[i] = (v0 + i < V) ? st.uni[v0 + i] : 0;
     }
-    // the orders' context entries and counts, one thread each
-    if (threadIdx.x < kMaxOrder) {
-      const int k = threadIdx.x;
-      const int ei = (k < D.order) ? st.ctx_ent[k] : -1;
-      const NgEntry* en = ei >= 0 ? st.ent[k] + ei : nullptr;
-      sh.ent[k] = en;
-      sh.nk[k] = en ? (float)en->n : 0.f;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      float lam[kMaxOrder], nk[kMaxOrder];
-      for (int k = 0; k < kMaxOrder; ++k) {
-        nk[k] = sh.nk[k];
-        lam[k] = sh.ent[k] ? nk[k] / (nk[k] + 5.0f) : 0.f;
-      }
-      float A = 1.f;
-      for (int k = 0; k < kMaxOrder; ++k) A *= (1.f - lam[k]);
-      for (int k = 0; k < kMaxOrder; ++k) {
-        float beta = lam[k];
-        for (int q = k + 1; q < kMaxOrder; ++q) beta *= (1.f - lam[q]);
-        sh.coef[k] = sh.ent[k] ? beta / nk[k] : 0.f;
-      }
-      sh.cu = A / (float)(st.N + V);
-    }
+    if (!ng_ready) ng_gather(D, st, sh);         // else pushed by the previous position
     for (int i = threadIdx.x; i < chunk; i += kStepThreads) sp[i] = 0.f;
     __syncthreads();
     for (int k = 0; k < kMaxOrder; ++k) {
-      const NgEntry* en = sh.ent[k];
-      if (en) {
-        const int ns = en->nslots;
-        for (int q = threadIdx.x; q < ns; q += kStepThreads) {
-          const int t = en->tok[q] - base;
-          if (t >= 0 && t < chunk) sp[t] += sh.coef[k] * (float)en->cnt[q];
-        }
+      const int ns = sh.ng_ns[k];
+      for (int q = threadIdx.x; q < ns; q += kStepThreads) {
+        const int t = sh.ng_tok[k][q] - base;
+        if (t >= 0 && t < chunk) sp[t] += sh.ng_coef[k] * (float)sh.ng_cnt[k][q];
       }
       __syncthreads();
     }
-    const float cu = sh.cu;
+    const float cu = sh.ng_cu;
 #pragma unroll
     for (int i = 0; i < E; ++i) png[i] = (v0 + i < V) ? cu * (float)(cnt[i] + 1) + sp[threadIdx.x * E + i] : 0.f;
   } else {
@@ -563,6 +595,13 @@ __device__ bool vocab_pass(const Dims& D, const Batch& b, const VocabIO& io, int
       st.png_obs = pngs;
     }
   }
+  // the unigram count of the coded token, for a caller that keeps the
+  // counts from one position to the next (the N-gram update adds it in memory)
+  if (ngram && io.update && t_obs >= v0 && t_obs < v0 + E) {
+#pragma unroll
+    for (int i = 0; i < E; ++i)
+      if (v0 + i == t_obs) cnt[i] += 1;
+  }
   return true;
 }
 
@@ -582,11 +621,13 @@ __global__ void __launch_bounds__(kStepThreads, 1) k_vocab(Dims D, Batch b, Voca
   if (j >= *b.nB) return;                        // uniform across the cluster
   const int rank = (int)cl.block_rank();
   float bias[E];
-  if (!vocab_pass<E>(D, b, io, j, rank, cl, sh, sp, bias, false, b.z_in != nullptr)) return;
+  int cnt[E];
+  if (!vocab_pass<E>(D, b, io, j, rank, cl, sh, sp, bias, false, cnt, false, false, b.z_in != nullptr)) return;
   cl.sync();   // keep this CTA's shared memory alive until the cluster has read it
   // the N-gram update and bookkeeping of this row, once every CTA has read
   // the stream's state
-  if (io.update && io.ngram && rank == 0) ngram_update_row(D, b, j, threadIdx.x >> 5, threadIdx.x & 31);
+  if (io.update && io.ngram && rank == 0)
+    ngram_update_row(D, b, j, threadIdx.x >> 5, threadIdx.x & 31, nullptr, nullptr);
 }
 
 // The vocabulary passes of a prefill chunk: the cluster of stream row j runs
@@ -606,13 +647,14 @@ __global__ void __launch_bounds__(kStepThreads, 1)
   pdl_trigger();
   const int rank = (int)cl.block_rank();
   float bias[E];
+  int cnt[E];
   for (int r = 0; r < m; ++r) {
     if (j >= nb_step[r]) break;                    // uniform across the cluster
     Batch br = b;
     br.obs = obs_step + (size_t)r * n_streams;
     br.z_in = zrows + (size_t)r * D.V;
-    if (!vocab_pass<E>(D, br, io, j, rank, cl, sh, sp, bias, r > 0, true)) break;
-    if (io.ngram && rank == 0) ngram_update_row(D, br, j, threadIdx.x >> 5, threadIdx.x & 31);
+    if (!vocab_pass<E>(D, br, io, j, rank, cl, sh, sp, bias, r > 0, cnt, r > 0, r > 0, true)) break;
+    if (io.ngram && rank == 0) ngram_update_row(D, br, j, threadIdx.x >> 5, threadIdx.x & 31, &sh, &cl);
     cl.sync();   // the stream's state of this position is final for the next
   }
 }
@@ -738,7 +780,11 @@ __device__ void ngram_update_order(const Dims& D, StreamDev& st, int t, int k, i
   }
 }
 
-__device__ void ngram_update_row(const Dims& D, const Batch& b, int j, int warp, int lane) {
+// push (the persistent loop): afterwards the N-gram state of the stream's
+// next prediction is written into the shared memory of every CTA of the
+// cluster (the same values ng_gather would read from the tables).
+__device__ void ngram_update_row(const Dims& D, const Batch& b, int j, int warp, int lane, StepShared* push,
+                                 cg::cluster_group* cl) {
   StreamDev& st = b.st[b.slots[j]];
   const int t = b.obs[j];
   if (t < 0 || t >= D.V) {
@@ -760,6 +806,36 @@ __device__ void ngram_update_row(const Dims& D, const Batch& b, int j, int warp,
     st.kv_start = start;
     st.n_coded += 1;
     st.last_tok = t;
+  }
+  if (!push || D.order == 0) return;
+  __syncthreads();                                 // every order's lookup and the unigram total are final
+  if (warp < kMaxOrder) {
+    const int k = warp;
+    const int ei = k < D.order ? st.ctx_ent[k] : -1;
+    const NgEntry* en = ei >= 0 ? st.ent[k] + ei : nullptr;
+    const int ns = en ? en->nslots : 0;
+    for (int r = 0; r < kStepCluster; ++r) {
+      StepShared* o = cl->map_shared_rank(push, r);
+      if (lane == 0) o->ng_ns[k] = ns;
+      for (int q = lane; q < ns; q += 32) {
+        o->ng_tok[k][q] = en->tok[q];
+        o->ng_cnt[k][q] = en->cnt[q];
+      }
+    }
+  } else if (warp == kMaxOrder && lane == 0) {
+    float nk[kMaxOrder], coef[kMaxOrder], cu;
+    bool has[kMaxOrder];
+    for (int k = 0; k < kMaxOrder; ++k) {
+      const int ei = k < D.order ? st.ctx_ent[k] : -1;
+      has[k] = ei >= 0;
+      nk[k] = has[k] ? (float)st.ent[k][ei].n : 0.f;
+    }
+    ng_weights(nk, has, st.N, D.V, coef, cu);
+    for (int r = 0; r < kStepCluster; ++r) {
+      StepShared* o = cl->map_shared_rank(push, r);
+      for (int k = 0; k < kMaxOrder; ++k) o->ng_coef[k] = coef[k];
+      o->ng_cu = cu;
+    }
   }
 }
 
