@@ -67,8 +67,8 @@ struct TcLayout {
     rm = take(rq * kAttnMaxChunks * grp * 4);
     rl = take(rq * kAttnMaxChunks * grp * 4);
     racc = take(rq * kAttnMaxChunks * grp * kd * 4);
-    mf = take(grp * kAttnMaxChunks * 4);
-    mL = take(grp * 4);
+    mf = take(R * kAttnMaxChunks * 4);
+    mL = take(R * 4);
     total = o;
   }
 };
@@ -209,18 +209,28 @@ __device__ void load_tile(const Dims& D, const StreamDev& st, int layer, int g, 
   const size_t koff = attn_plane_off(D, layer, g);
   const size_t voff = attn_plane_off(D, layer, D.hkv + g);
   const __nv_bfloat16* kv = static_cast<const __nv_bfloat16*>(st.kv);
-  // 256 rows x 8 segments of 16 bytes, for K and for V
-  for (int e = tid; e < kAttnChunk * 8; e += kAttnThreads) {
+  // 256 rows x 8 segments of 16 bytes, for K and for V: every load of this
+  // thread is issued before the first store, so they are in flight together
+  constexpr int kPer = kAttnChunk * 8 / kAttnThreads;
+  uint4 uk[kPer], uv[kPer];
+#pragma unroll
+  for (int i = 0; i < kPer; ++i) {
+    const int e = tid + i * kAttnThreads;
     const int row = e >> 3, seg = e & 7;
     const int p = c_lo + row;
-    uint4 uk = make_uint4(0, 0, 0, 0), uv = uk;
+    uk[i] = uv[i] = make_uint4(0, 0, 0, 0);
     if (p <= last && p != own) {
       const size_t ri = (size_t)(p & (D.L - 1)) * kHeadDim + seg * 8;
-      uk = *reinterpret_cast<const uint4*>(kv + koff + ri);
-      uv = *reinterpret_cast<const uint4*>(kv + voff + ri);
+      uk[i] = __ldg(reinterpret_cast<const uint4*>(kv + koff + ri));
+      uv[i] = __ldg(reinterpret_cast<const uint4*>(kv + voff + ri));
     }
-    *reinterpret_cast<uint4*>(kt + row * kTileStride + seg * 8) = uk;
-    *reinterpret_cast<uint4*>(vt + row * kTileStride + seg * 8) = uv;
+  }
+#pragma unroll
+  for (int i = 0; i < kPer; ++i) {
+    const int e = tid + i * kAttnThreads;
+    const int row = e >> 3, seg = e & 7;
+    *reinterpret_cast<uint4*>(kt + row * kTileStride + seg * 8) = uk[i];
+    *reinterpret_cast<uint4*>(vt + row * kTileStride + seg * 8) = uv[i];
   }
 }
 
@@ -351,32 +361,32 @@ __global__ void __launch_bounds__(kAttnThreads, 1) k_attn_tc(Dims D, Batch b, in
   const float* racc = reinterpret_cast<const float*>(sm + L.racc);
   float* mf = reinterpret_cast<float*>(sm + L.mf);
   float* mL = reinterpret_cast<float*>(sm + L.mL);
-  for (int r = 0; r < rq; ++r) {
+  // every (row, head): the chunk factors, then every output dim
+  for (int t = tid; t < R; t += kAttnThreads) {
+    const int r = t / grp, h = t % grp;
     const int a = a_row[r];
     const int nc = a < 0 ? 0 : (a - start) / kAttnChunk + 1;
-    if (tid < grp) {
-      const int h = tid;
-      float M = -INFINITY;
-      for (int c = 0; c < nc; ++c) M = fmaxf(M, rm[(r * kAttnMaxChunks + c) * grp + h]);
-      float l = 0.f;
-      for (int c = 0; c < nc; ++c) {
-        const int rc = (r * kAttnMaxChunks + c) * grp + h;
-        const float f = expf(rm[rc] - M);
-        mf[h * kAttnMaxChunks + c] = f;
-        l = fmaf(rl[rc], f, l);
-      }
-      mL[h] = l;
+    float M = -INFINITY;
+    for (int c = 0; c < nc; ++c) M = fmaxf(M, rm[(r * kAttnMaxChunks + c) * grp + h]);
+    float l = 0.f;
+    for (int c = 0; c < nc; ++c) {
+      const int rc = (r * kAttnMaxChunks + c) * grp + h;
+      const float f = expf(rm[rc] - M);
+      mf[t * kAttnMaxChunks + c] = f;
+      l = fmaf(rl[rc], f, l);
     }
-    __syncthreads();
-    float* out = io.attn_out + (size_t)(i0 + r) * D.hq * kHeadDim + g * grp * kHeadDim + rank * kd;
-    for (int e = tid; e < grp * kd; e += kAttnThreads) {
-      const int h = e / kd, dl = e % kd;
-      float o = 0.f;
-      for (int c = 0; c < nc; ++c)
-        o = fmaf(racc[((r * kAttnMaxChunks + c) * grp + h) * kd + dl], mf[h * kAttnMaxChunks + c], o);
-      out[h * kHeadDim + dl] = nc ? o / mL[h] : 0.f;
-    }
-    __syncthreads();
+    mL[t] = l;
+  }
+  __syncthreads();
+  for (int e = tid; e < R * kd; e += kAttnThreads) {
+    const int t = e / kd, dl = e % kd, r = t / grp, h = t % grp;
+    const int a = a_row[r];
+    const int nc = a < 0 ? 0 : (a - start) / kAttnChunk + 1;
+    float o = 0.f;
+    for (int c = 0; c < nc; ++c)
+      o = fmaf(racc[((r * kAttnMaxChunks + c) * grp + h) * kd + dl], mf[t * kAttnMaxChunks + c], o);
+    io.attn_out[(size_t)(i0 + r) * D.hq * kHeadDim + (g * grp + h) * kHeadDim + rank * kd + dl] =
+        nc ? o / mL[t] : 0.f;
   }
 }
 
