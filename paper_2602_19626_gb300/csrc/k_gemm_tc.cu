@@ -6,8 +6,9 @@
 // staged by TMA into 128-byte-swizzled shared memory through a ring of
 // STAGES buffers; one thread issues tcgen05.mma (kind::f16 for BF16,
 // kind::f8f6f4 for FP8 E4M3) into an FP32 accumulator in tensor memory; after
-// the last K block the four warps read the accumulator back with tcgen05.ld
-// and apply the fused epilogue.  Every output element accumulates its K
+// the last K block the eight warps read the accumulator back with tcgen05.ld
+// (two warps per lane quarter, one per half of the columns) and apply the
+// fused epilogue.  Every output element accumulates its K
 // blocks in the same order whatever BN, the grid or the batch, so results
 // do not depend on how many streams share a step.
 //
@@ -24,7 +25,7 @@ namespace nc {
 
 namespace {
 
-constexpr int kTcThreads = 128;
+constexpr int kTcThreads = 256;              // 8 warps: all read the accumulator back
 constexpr int kTileM = 128;
 constexpr int kKBlockBytes = 128;            // one 128-byte swizzle row per operand row
 constexpr uint32_t kWaitLimit = 1u << 22;
@@ -236,12 +237,15 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   __syncthreads();
   if (ready && *fail == 0) {
-    const int r = m0 + warp * 32 + lane;           // weight row = TMEM lane
-    const uint32_t tw = tmem + ((uint32_t)(warp * 32) << 16);
+    // warp w reads TMEM lanes 32 (w % 4) .. + 31 (its lane quarter) and the
+    // columns of half w / 4 of the tile
+    const int quarter = warp & 3, half = warp >> 2;
+    const int r = m0 + quarter * 32 + lane;        // weight row = TMEM lane
+    const uint32_t tw = tmem + ((uint32_t)(quarter * 32) << 16);
     float ws = 1.f;
     if (!KIND_BF16 && r < g.M) ws = g.w_scale[r];
 #pragma unroll 1
-    for (int c = 0; c < BN; c += 16) {
+    for (int c = half * (BN / 2); c < (half + 1) * (BN / 2); c += 16) {
       float v[16];
       tmem_ld16(tw + (uint32_t)c, v);
       // loads of this 16-column group first (row scales, residuals), so
