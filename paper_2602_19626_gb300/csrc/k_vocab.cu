@@ -159,14 +159,16 @@ __device__ __forceinline__ void store_run(float* dst, int v0, int V, const float
   }
 }
 
-// Round 1 of the step: the softmax of s over the cluster's vocabulary in
-// two passes.  The maximum M (exact, order-free), then the numerators
-// e_i = exp(s_i - M) and their sum S: thread (i in order) -> warp (xor tree)
-// -> CTA (warps in order) -> cluster (ranks in order).  e_i is returned for
-// p_i = e_i / S.
+// Round 1 of the step: the softmax of s over the cluster's vocabulary.
+// Each CTA takes its own maximum m_c (exact) and its numerators
+// e_i = exp(s_i - m_c) with their sum s_c (thread, i in order -> warp, xor
+// tree -> CTA, warps in order); one cluster round then gives
+// M = max m_c and S = sum_c s_c exp(m_c - M) (ranks in order), and this
+// CTA's factor exp(m_c - M) / S turns e_i into p_i.  A second sum (the
+// N-gram entropy terms h_in) is reduced alongside, unscaled.
 template <int E, int CL, typename Sh>
-__device__ MS softmax_two_pass(const float (&s)[E], float (&e)[E], float h_in, float& h_out, cg::cluster_group& cl,
-                               Sh& sh) {
+__device__ MS softmax_round(const float (&s)[E], float (&e)[E], float h_in, float& h_out, float& scale,
+                            cg::cluster_group& cl, Sh& sh) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   float m = -INFINITY;
 #pragma unroll
@@ -174,28 +176,19 @@ __device__ MS softmax_two_pass(const float (&s)[E], float (&e)[E], float h_in, f
   m = warp_max(m);
   if (lane == 0) sh.wm[w] = m;
   __syncthreads();
-  if (threadIdx.x == 0) {
-    float b = sh.wm[0];
-    for (int i = 1; i < Sh::kNW; ++i) b = fmaxf(b, sh.wm[i]);
-    sh.cl_m = b;
-  }
-  cl.sync();
-  float M = -INFINITY;
-#pragma unroll
-  for (int r = 0; r < CL; ++r) M = fmaxf(M, cl.map_shared_rank(&sh, r)->cl_m);
+  float mc = sh.wm[0];
+  for (int i = 1; i < Sh::kNW; ++i) mc = fmaxf(mc, sh.wm[i]);
   float t = 0.f;
-  if (M != -INFINITY) {
+  if (mc != -INFINITY) {
 #pragma unroll
     for (int i = 0; i < E; ++i) {
-      e[i] = expf(s[i] - M);
+      e[i] = expf(s[i] - mc);
       t += e[i];
     }
   } else {
 #pragma unroll
     for (int i = 0; i < E; ++i) e[i] = 0.f;
   }
-  // the second sum of the round: h_in, this thread's share of another sum
-  // (the N-gram entropy), reduced in the same order
   t = warp_sum(t);
   const float hw = warp_sum(h_in);
   if (lane == 0) {
@@ -209,17 +202,23 @@ __device__ MS softmax_two_pass(const float (&s)[E], float (&e)[E], float h_in, f
       b += sh.wsum[i];
       bh += sh.wh[i];
     }
+    sh.cl_m = mc;
     sh.cl_s = b;
     sh.cl_h = bh;
   }
   cl.sync();
+  float M = -INFINITY;
+#pragma unroll
+  for (int r = 0; r < CL; ++r) M = fmaxf(M, cl.map_shared_rank(&sh, r)->cl_m);
   float S = 0.f, H = 0.f;
 #pragma unroll
   for (int r = 0; r < CL; ++r) {
-    S += cl.map_shared_rank(&sh, r)->cl_s;
-    H += cl.map_shared_rank(&sh, r)->cl_h;
+    const Sh* o = cl.map_shared_rank(&sh, r);
+    if (o->cl_m != -INFINITY) S = fmaf(o->cl_s, expf(o->cl_m - M), S);
+    H += o->cl_h;
   }
   h_out = H;
+  scale = mc != -INFINITY ? expf(mc - M) / S : 0.f;
   return MS{M, S};
 }
 
@@ -513,13 +512,12 @@ __device__ bool vocab_pass(const Dims& D, const Batch& b, const VocabIO& io, int
     for (int i = 0; i < E; ++i)
       if (v0 + i < V && png[i] > 0.f) h_in -= png[i] * log2f(png[i]);
   }
-  float pt[E], H = 0.f;
-  const MS ms = softmax_two_pass<E, kStepCluster>(s, pt, h_in, H, cl, sh);
+  float pt[E], H = 0.f, f_cta = 0.f;
+  const MS ms = softmax_round<E, kStepCluster>(s, pt, h_in, H, f_cta, cl, sh);
   const bool skipped = D.skip && H < kSkipBits;
   const float M = ms.m, S = ms.s;
-  const float inv_S = 1.0f / S;
 #pragma unroll
-  for (int i = 0; i < E; ++i) pt[i] = (v0 + i < V) ? pt[i] * inv_S : 0.f;
+  for (int i = 0; i < E; ++i) pt[i] = (v0 + i < V) ? pt[i] * f_cta : 0.f;
   if (io.probe_pt) store_run<E>(io.probe_pt + (size_t)j * V, v0, V, pt);
 
   // ---- mix (Sec. 3.5): LLM alone during warm-up
