@@ -32,6 +32,7 @@ namespace {
 using namespace dev;
 
 constexpr int kTileStride = kHeadDim + 8;            // BF16 elements per smem row (bank-conflict-free ldmatrix)
+constexpr int kTcThreads = 512;                      // 16 warps: one per (block, m-tile)
 constexpr int kMaxRowsTc = 8;                        // query rows per CTA (prefill)
 constexpr int kMaxTileRows = 32;                     // (row, head) pairs: 8 rows x 4 heads
 
@@ -211,11 +212,11 @@ __device__ void load_tile(const Dims& D, const StreamDev& st, int layer, int g, 
   const __nv_bfloat16* kv = static_cast<const __nv_bfloat16*>(st.kv);
   // 256 rows x 8 segments of 16 bytes, for K and for V: every load of this
   // thread is issued before the first store, so they are in flight together
-  constexpr int kPer = kAttnChunk * 8 / kAttnThreads;
+  constexpr int kPer = kAttnChunk * 8 / kTcThreads;
   uint4 uk[kPer], uv[kPer];
 #pragma unroll
   for (int i = 0; i < kPer; ++i) {
-    const int e = tid + i * kAttnThreads;
+    const int e = tid + i * kTcThreads;
     const int row = e >> 3, seg = e & 7;
     const int p = c_lo + row;
     uk[i] = uv[i] = make_uint4(0, 0, 0, 0);
@@ -227,7 +228,7 @@ __device__ void load_tile(const Dims& D, const StreamDev& st, int layer, int g, 
   }
 #pragma unroll
   for (int i = 0; i < kPer; ++i) {
-    const int e = tid + i * kAttnThreads;
+    const int e = tid + i * kTcThreads;
     const int row = e >> 3, seg = e & 7;
     *reinterpret_cast<uint4*>(kt + row * kTileStride + seg * 8) = uk[i];
     *reinterpret_cast<uint4*>(vt + row * kTileStride + seg * 8) = uv[i];
@@ -239,7 +240,7 @@ __device__ void load_tile(const Dims& D, const StreamDev& st, int layer, int g, 
 // one stream and KV head, by a cluster of S CTAs owning chunks rank,
 // rank + S, ...
 template <int S>
-__global__ void __launch_bounds__(kAttnThreads, 1) k_attn_tc(Dims D, Batch b, int layer, int rq, AttnIO io) {
+__global__ void __launch_bounds__(kTcThreads, 1) k_attn_tc(Dims D, Batch b, int layer, int rq, AttnIO io) {
   extern __shared__ float4 dyn4[];
   char* sm = reinterpret_cast<char*>(dyn4);
   const int rank = S > 1 ? (int)cg::this_cluster().block_rank() : 0;
@@ -267,7 +268,7 @@ __global__ void __launch_bounds__(kAttnThreads, 1) k_attn_tc(Dims D, Batch b, in
   if (a_max < 0) {                                 // prefill rows past the stream's end
     pdl_wait();
     pdl_trigger();
-    for (int e = tid; e < rq * grp * kd; e += kAttnThreads) {
+    for (int e = tid; e < rq * grp * kd; e += kTcThreads) {
       const int r = e / (grp * kd), h = (e / kd) % grp, dl = e % kd;
       io.attn_out[(size_t)(i0 + r) * D.hq * kHeadDim + (g * grp + h) * kHeadDim + rank * kd + dl] = 0.f;
     }
@@ -290,7 +291,7 @@ __global__ void __launch_bounds__(kAttnThreads, 1) k_attn_tc(Dims D, Batch b, in
     attn_qkv<1>(D, st, layer, i0 + r, g, a, !prefill && (nc_max - 1) % S == rank, tid, qv[r], io);
   }
   // BF16 query tile: row r * grp + h, padding rows zero
-  for (int e = tid; e < kMaxTileRows * kHeadDim; e += kAttnThreads) {
+  for (int e = tid; e < kMaxTileRows * kHeadDim; e += kTcThreads) {
     const int row = e / kHeadDim, d = e % kHeadDim;
     float v = 0.f;
     if (row < R) {
@@ -317,12 +318,14 @@ __global__ void __launch_bounds__(kAttnThreads, 1) k_attn_tc(Dims D, Batch b, in
       vt[(a_max - c_lo) * kTileStride + tid] = __float2bfloat16_rn(qv[0].vn[tid]);
     }
     __syncthreads();
-    for (int mt = 0; mt < nmt; ++mt)
-      attn_block_tc(c_lo + warp * 32, c_lo, mt, R, grp, a_row, q16, kt, vt, wm, wl, wacc, warp, lane);
+    {
+      const int blk = warp & (kAttnWarps - 1), mt = warp / kAttnWarps;   // block of 32 positions, m-tile
+      if (mt < nmt) attn_block_tc(c_lo + blk * 32, c_lo, mt, R, grp, a_row, q16, kt, vt, wm, wl, wacc, blk, lane);
+    }
     __syncthreads();
     // per (row, head): the block factors exp(m_w - M), M and the sum, over
     // the blocks holding positions of this row (block order)
-    for (int t = tid; t < R; t += kAttnThreads) {
+    for (int t = tid; t < R; t += kTcThreads) {
       const int a = a_row[t / grp];
       if (a < c_lo) continue;
       const int nblk = (min(c_lo + kAttnChunk, a + 1) - c_lo + 31) / 32;
@@ -338,7 +341,7 @@ __global__ void __launch_bounds__(kAttnThreads, 1) k_attn_tc(Dims D, Batch b, in
       cL[t] = l;
     }
     __syncthreads();
-    for (int e = tid; e < R * kHeadDim; e += kAttnThreads) {
+    for (int e = tid; e < R * kHeadDim; e += kTcThreads) {
       const int t = e / kHeadDim, dd = e % kHeadDim, r = t / grp, h = t % grp;
       const int a = a_row[r];
       if (a < c_lo) continue;
@@ -362,7 +365,7 @@ __global__ void __launch_bounds__(kAttnThreads, 1) k_attn_tc(Dims D, Batch b, in
   float* mf = reinterpret_cast<float*>(sm + L.mf);
   float* mL = reinterpret_cast<float*>(sm + L.mL);
   // every (row, head): the chunk factors, then every output dim
-  for (int t = tid; t < R; t += kAttnThreads) {
+  for (int t = tid; t < R; t += kTcThreads) {
     const int r = t / grp, h = t % grp;
     const int a = a_row[r];
     const int nc = a < 0 ? 0 : (a - start) / kAttnChunk + 1;
@@ -378,7 +381,7 @@ __global__ void __launch_bounds__(kAttnThreads, 1) k_attn_tc(Dims D, Batch b, in
     mL[t] = l;
   }
   __syncthreads();
-  for (int e = tid; e < R * kd; e += kAttnThreads) {
+  for (int e = tid; e < R * kd; e += kTcThreads) {
     const int t = e / kd, dl = e % kd, r = t / grp, h = t % grp;
     const int a = a_row[r];
     const int nc = a < 0 ? 0 : (a - start) / kAttnChunk + 1;
@@ -394,7 +397,7 @@ template <int S>
 cudaError_t launch_tc_s(const Dims& D, const Batch& b, int layer, int rq, const AttnIO& io, cudaStream_t s) {
   const size_t smem = TcLayout(rq, D.hq / D.hkv, kHeadDim / S).total;
   dim3 grid(S, D.hkv, b.Bmax / rq);
-  return launch_kernel_cluster(k_attn_tc<S>, grid, dim3(kAttnThreads), smem, s, D.pdl, S, D, b, layer, rq, io);
+  return launch_kernel_cluster(k_attn_tc<S>, grid, dim3(kTcThreads), smem, s, D.pdl, S, D, b, layer, rq, io);
 }
 
 template <int S>
