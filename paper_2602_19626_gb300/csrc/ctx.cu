@@ -9,6 +9,7 @@
 #include <new>
 #include <string>
 #include <thread>
+#include <map>
 #include <unordered_map>
 #include <vector>
 
@@ -1045,24 +1046,17 @@ static int prefill_chunk(const nc_ctx* ctx, int n, int64_t max_len) {
 // every row kept), then the m vocabulary passes and updates of each stream
 // in order.  Every row's arithmetic is the decode step's, so the intervals
 // are those of one position per step.  Streams sorted longest first.
-static int encode_prefill(nc_ctx* ctx, int n, int m, const int32_t* tok_dev, const int64_t* offs_dev,
+static int encode_prefill(nc_ctx* ctx, int n, int m0, const int32_t* tok_dev, const int64_t* offs_dev,
                           const int64_t* lens_dev, const std::vector<int64_t>& lens_h, uint32_t* intervals,
                           int64_t stride, nc_trace* trace) {
   const Dims& D = ctx->D;
   cudaStream_t s = ctx->stream;
   int64_t max_len = 0;
   for (int64_t l : lens_h) max_len = std::max(max_len, l);
-  Batch b = make_batch(ctx);                      // stream rows (slots only)
-  b.Bmax = n;
-  Batch f = make_batch(ctx);                      // (stream, position) rows of the forward
-  f.slots = ctx->f_slots;
-  f.nB = ctx->d_nB_fwd;
-  f.obs = nullptr;
-  f.Bmax = n * m;
-  f.pos = ctx->f_pos;
-  f.tok = ctx->f_tok;
-  f.z_out = ctx->zrows;
-  f.pm = m;
+  // the largest chunk the window allows for one stream
+  int m_max = m0;
+  while ((int64_t)2 * m_max <= ctx->P && D.C % (2 * m_max) == 0 && D.L % (2 * m_max) == 0 && m_max < max_len)
+    m_max *= 2;
   VocabIO io{};
   io.predict = 1;
   io.update = 1;
@@ -1076,10 +1070,23 @@ static int encode_prefill(nc_ctx* ctx, int n, int m, const int32_t* tok_dev, con
     mk.ev.resize(fwd_marks + 1 + 2);
     for (auto& e : mk.ev) NC_TRY(cudaEventCreate(&e));
   }
-  auto one_chunk = [&]() -> cudaError_t {
+  // One chunk of m positions of the first ne streams (the longest; every
+  // stream with positions left is among them).
+  auto one_chunk = [&](int m, int ne) -> cudaError_t {
+    Batch b = make_batch(ctx);                    // stream rows (slots only)
+    b.Bmax = ne;
+    Batch f = make_batch(ctx);                    // (stream, position) rows of the forward
+    f.slots = ctx->f_slots;
+    f.nB = ctx->d_nB_fwd;
+    f.obs = nullptr;
+    f.Bmax = ne * m;
+    f.pos = ctx->f_pos;
+    f.tok = ctx->f_tok;
+    f.z_out = ctx->zrows;
+    f.pm = m;
     cudaError_t e = mk.begin(s);
     if (e == cudaSuccess)
-      e = launch_prepare_prefill(b, n, m, D.V, tok_dev, offs_dev, lens_dev, ctx->f_slots, ctx->f_pos, ctx->f_tok,
+      e = launch_prepare_prefill(b, ne, m, D.V, tok_dev, offs_dev, lens_dev, ctx->f_slots, ctx->f_pos, ctx->f_tok,
                                  ctx->d_nB_fwd, ctx->f_obs, ctx->f_nb, ctx->d_zidx, s);
     if (e == cudaSuccess) e = mk.mark(s, TK_PREPARE);
     if (e == cudaSuccess) e = launch_model(ctx, f, &mk);
@@ -1091,27 +1098,45 @@ static int encode_prefill(nc_ctx* ctx, int n, int m, const int32_t* tok_dev, con
     if (e == cudaSuccess) e = mk.mark(s, TK_VOCAB);
     return e;
   };
-  cudaGraph_t g = nullptr;
-  cudaGraphExec_t ge = nullptr;
-  if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
-    mk.capturing = true;
-    cudaError_t e = one_chunk();
-    mk.capturing = false;
-    cudaError_t e2 = cudaStreamEndCapture(s, &g);
-    if (e != cudaSuccess || e2 != cudaSuccess || cudaGraphInstantiate(&ge, g, 0) != cudaSuccess) ge = nullptr;
-    if (g) cudaGraphDestroy(g);
-    cudaGetLastError();
-  }
+  // one captured graph per chunk length (captured on first use)
+  std::map<int, cudaGraphExec_t> graphs;
+  auto graph_for = [&](int m, int ne) -> cudaGraphExec_t {
+    auto it = graphs.find(m);
+    if (it != graphs.end()) return it->second;
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t ge = nullptr;
+    if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+      mk.capturing = true;
+      cudaError_t e = one_chunk(m, ne);
+      mk.capturing = false;
+      cudaError_t e2 = cudaStreamEndCapture(s, &g);
+      if (e != cudaSuccess || e2 != cudaSuccess || cudaGraphInstantiate(&ge, g, 0) != cudaSuccess) ge = nullptr;
+      if (g) cudaGraphDestroy(g);
+      cudaGetLastError();
+    }
+    graphs[m] = ge;
+    return ge;
+  };
   if (trace) {
     std::memset(trace, 0, sizeof(*trace));
-    trace->graphed = ge != nullptr;
+    trace->graphed = 1;
     trace->n_kinds = TK_COUNT;
     for (int k = 0; k < TK_COUNT; ++k) std::snprintf(trace->name[k], sizeof(trace->name[k]), "%s", kTraceNames[k]);
   }
   auto start_at = [&](int64_t a) -> int64_t { return a < D.L ? 0 : ((a - D.L) / D.C + 1) * D.C; };
   int st = NC_OK;
+  int m = m0;
   for (int64_t p = 0; p < max_len; p += m) {
-    cudaError_t e = ge ? cudaGraphLaunch(ge, s) : one_chunk();
+    // the largest chunk for the streams still coding, aligned to it (so it
+    // never crosses a slide): it only grows as streams end
+    int live = 0;
+    while (live < n && lens_h[live] > p) ++live;
+    m = m_max;
+    while (m > m0 && ((int64_t)live * m > ctx->P || p % m != 0)) m /= 2;
+    const int ne = std::min(n, ctx->P / m);
+    cudaGraphExec_t ge = graph_for(m, ne);
+    if (trace && !ge) trace->graphed = 0;
+    cudaError_t e = ge ? cudaGraphLaunch(ge, s) : one_chunk(m, ne);
     if (e != cudaSuccess) {
       st = fail_cuda(ctx, e, "prefill encode chunk");
       break;
@@ -1131,7 +1156,7 @@ static int encode_prefill(nc_ctx* ctx, int n, int m, const int32_t* tok_dev, con
       }
       double fwd[TK_COUNT], ffl[TK_COUNT];
       step_cost(ctx, (int)rows, ctx_sum, kv_unique, fwd, ffl);
-      fwd[TK_PREPARE] = n * (double)m * 28;
+      fwd[TK_PREPARE] = ne * (double)m * 28;
       e = cudaEventSynchronize(mk.ev[mk.n]);
       if (e != cudaSuccess) {
         st = fail_cuda(ctx, e, "trace sync");
@@ -1160,7 +1185,8 @@ static int encode_prefill(nc_ctx* ctx, int n, int m, const int32_t* tok_dev, con
       }
     }
   }
-  if (ge) cudaGraphExecDestroy(ge);
+  for (auto& kv : graphs)
+    if (kv.second) cudaGraphExecDestroy(kv.second);
   for (auto& e : mk.ev) cudaEventDestroy(e);
   return st;
 }
