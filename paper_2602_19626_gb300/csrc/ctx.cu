@@ -84,6 +84,9 @@ struct nc_ctx {
   int32_t* f_obs = nullptr;          // [P] observed token of (position, stream)
   int32_t* f_nb = nullptr;           // [P] active streams per position
   float* zrows = nullptr;            // [P][V] logits of the forward rows
+  NgSnap* snap = nullptr;            // [P] N-gram state of each (stream, position) prediction
+  cudaStream_t side = nullptr;       // the N-gram pass of a chunk runs here beside its forward
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   uint32_t* cdf = nullptr;
   int32_t* d_slots = nullptr;
   int32_t* d_nB = nullptr;
@@ -274,6 +277,9 @@ extern "C" void nc_ctx_destroy(nc_ctx* ctx) {
   cudaFreeHost(ctx->h_i32);
   cudaFreeHost(ctx->h_u32);
   cudaFreeHost(ctx->h_status);
+  if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
+  if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
+  if (ctx->side) cudaStreamDestroy(ctx->side);
   if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
   delete ctx;
 }
@@ -548,6 +554,13 @@ extern "C" int nc_ctx_create(const nc_config* cfg, const void* weights, size_t n
        dalloc(ctx, &ctx->d_zidx, B * 4) || dalloc(ctx, &ctx->zrows, (size_t)ctx->P * D.V * 4) ||
        dalloc(ctx, &ctx->f_obs, (size_t)ctx->P * 4) || dalloc(ctx, &ctx->f_nb, (size_t)ctx->P * 4)))
     return bail(NC_ENOMEM);
+  if (ctx->P > 0 && D.order > 0) {
+    if (dalloc(ctx, &ctx->snap, (size_t)ctx->P * sizeof(NgSnap))) return bail(NC_ENOMEM);
+    if (cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming) != cudaSuccess)
+      return bail(NC_ECUDA);
+  }
   if (dalloc(ctx, &ctx->x, RA * D.d * 4) || dalloc(ctx, &ctx->qkv, RA * D.qkv_rows * 4) ||
       dalloc(ctx, &ctx->attn_out, RA * D.hq * kHeadDim * 4) ||
       dalloc(ctx, &ctx->h, RA * D.F * 4) || dalloc(ctx, &ctx->cdf, B * (D.V + 1) * 4) ||
@@ -1067,7 +1080,7 @@ static int encode_prefill(nc_ctx* ctx, int n, int m0, const int32_t* tok_dev, co
   mk.on = trace != nullptr;
   const int fwd_marks = 1 + 1 + 5 * D.n_layers + 1;   // prepare, embed, 5 per layer, LM head
   if (mk.on) {
-    mk.ev.resize(fwd_marks + 1 + 2);
+    mk.ev.resize(fwd_marks + 2 + 2);
     for (auto& e : mk.ev) NC_TRY(cudaEventCreate(&e));
   }
   // One chunk of m positions of the first ne streams (the longest; every
@@ -1089,12 +1102,22 @@ static int encode_prefill(nc_ctx* ctx, int n, int m0, const int32_t* tok_dev, co
       e = launch_prepare_prefill(b, ne, m, D.V, tok_dev, offs_dev, lens_dev, ctx->f_slots, ctx->f_pos, ctx->f_tok,
                                  ctx->d_nB_fwd, ctx->f_obs, ctx->f_nb, ctx->d_zidx, s);
     if (e == cudaSuccess) e = mk.mark(s, TK_PREPARE);
+    Batch br = b;                                   // every stream's m positions, in order
+    br.z_idx = ctx->d_zidx;
+    // the N-gram pass needs only the tokens: beside the forward on the side
+    // stream (in order on the main stream when each kernel is timed)
+    const bool side = ctx->snap && !mk.on;
+    if (side && e == cudaSuccess) e = cudaEventRecord(ctx->ev_fork, s);
+    if (side && e == cudaSuccess) e = cudaStreamWaitEvent(ctx->side, ctx->ev_fork, 0);
+    if (side && e == cudaSuccess) e = launch_ngram_seq(D, br, m, ctx->f_nb, ctx->f_obs, ctx->snap, ctx->side);
+    if (side && e == cudaSuccess) e = cudaEventRecord(ctx->ev_join, ctx->side);
     if (e == cudaSuccess) e = launch_model(ctx, f, &mk);
-    if (e == cudaSuccess) {
-      Batch br = b;                                 // every stream's m positions, in order
-      br.z_idx = ctx->d_zidx;
-      e = launch_vocab_seq(D, br, io, m, ctx->zrows, ctx->f_nb, ctx->f_obs, s);
+    if (ctx->snap && !side && e == cudaSuccess) {
+      e = launch_ngram_seq(D, br, m, ctx->f_nb, ctx->f_obs, ctx->snap, s);
+      if (e == cudaSuccess) e = mk.mark(s, TK_NGRAM);
     }
+    if (side && e == cudaSuccess) e = cudaStreamWaitEvent(s, ctx->ev_join, 0);
+    if (e == cudaSuccess) e = launch_vocab_seq(D, br, io, m, ctx->zrows, ctx->f_nb, ctx->f_obs, ctx->snap, s);
     if (e == cudaSuccess) e = mk.mark(s, TK_VOCAB);
     return e;
   };

@@ -36,6 +36,18 @@ struct NgEntry {
   int32_t cnt[kMaxSlots];
 };
 
+// The N-gram state one prediction reads (Sec. 3.4): per order the context
+// entry's slots (ns[k] = 0: no entry) and the closed form's weights
+// beta_k / n_k and A / (N + V).  1,584 bytes, a multiple of 16.
+struct alignas(16) NgSnap {
+  int32_t ns[4];
+  float coef[4];
+  float cu;
+  int32_t pad[3];
+  int2 tc[kMaxOrder][kMaxSlots];   // (token, count)
+};
+static_assert(sizeof(NgSnap) % 16 == 0, "NgSnap is copied in 16-byte pieces");
+
 // Per-stream device state (one per slot).
 struct StreamDev {
   int32_t n_coded;          // tokens coded so far; absolute position of the next fed token
@@ -199,9 +211,17 @@ struct VocabIO {
 cudaError_t launch_vocab(const Dims& D, const Batch& b, const VocabIO& io, cudaStream_t s);
 // The vocabulary passes of a prefill chunk in one launch: stream row j runs
 // positions 0 .. m - 1 of the chunk in order while j < nb_step[r], with the
-// observed tokens obs_step[r Bmax + j] and the logits zrows + (z_idx[j] + r) V.
+// observed tokens obs_step[r Bmax + j], the logits zrows + (z_idx[j] + r) V
+// and (N-gram on) the N-gram state snap[z_idx[j] + r] of each prediction.
 cudaError_t launch_vocab_seq(const Dims& D, const Batch& b, const VocabIO& io, int m, const float* zrows,
-                             const int32_t* nb_step, const int32_t* obs_step, cudaStream_t s);
+                             const int32_t* nb_step, const int32_t* obs_step, const NgSnap* snap, cudaStream_t s);
+// The N-gram side of the same chunk, ahead of the vocabulary passes (it needs
+// only the tokens): for each position of stream row j, in order, the state of
+// its prediction into snap[z_idx[j] + r], then the update with the observed
+// token (tables, context entries, history, unigram total N).  Leaves the
+// unigram counts, the position and the window to the vocabulary passes.
+cudaError_t launch_ngram_seq(const Dims& D, const Batch& b, int m, const int32_t* nb_step, const int32_t* obs_step,
+                             NgSnap* snap, cudaStream_t s);
 cudaError_t launch_prepare_encode(const Batch& b, int n_streams, const int32_t* tok_flat,
                                   const int64_t* offs, const int64_t* lens, int32_t* obs,
                                   int32_t* nB, cudaStream_t s);

@@ -32,35 +32,34 @@ __device__ __forceinline__ float warp_max(float v) {
   for (int o = 16; o; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
   return v;
 }
-__device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v) {
-#pragma unroll
-  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
 
 // floor(p * K) for a binary32 p in [0, 2) and K < 2^24, exactly: p = m 2^(e-150)
 // with a 24-bit significand m, so m * K < 2^48 is an exact integer product.
-// Sets `bad` for negative, >= 2, infinite or NaN inputs.
+// Sets `bad` (and returns 0) for negative, >= 2, infinite or NaN inputs.
 __device__ __forceinline__ uint32_t floor_prod(float p, uint32_t K, bool& bad) {
   const uint32_t u = __float_as_uint(p);
-  if (u == 0u || u == 0x80000000u) return 0u;
-  if (u >> 31) {
-    bad = true;
-    return 0u;
-  }
-  uint32_t e = u >> 23;
-  if (e >= 128u) {
-    bad = true;
-    return 0u;
-  }
-  uint32_t m = u & 0x7FFFFFu;
-  if (e == 0u)
-    e = 1u;
-  else
-    m |= 0x800000u;
+  const uint32_t a = u & 0x7FFFFFFFu;
+  const bool out = (u != a && a != 0u) || a >= 0x40000000u;
+  bad |= out;
+  const uint32_t e = a >> 23;
+  const uint32_t m = (a & 0x7FFFFFu) | (e ? 0x800000u : 0u);
+  const uint32_t sh = 150u - (e ? e : 1u);            // 23 .. 149 unless out
   const unsigned long long prod = (unsigned long long)m * K;
-  const uint32_t sh = 150u - e;
-  return sh >= 64u ? 0u : (uint32_t)(prod >> sh);
+  const uint32_t q = sh >= 48u ? 0u : (uint32_t)(prod >> sh);
+  return out ? 0u : q;
+}
+
+// floor(p K) exactly for a binary32 p in [0, 2) and K < 2^24.  Below 2^24 the
+// product rounded toward zero has the exact product's integer part (the
+// integers there are representable, so floor(x) <= rz(x) <= x); at or above
+// 2^24 (p > 2^24 / K > 1 only) the 48-bit integer product decides.  Sets
+// `bad` for negative, >= 2 or NaN inputs.
+__device__ __forceinline__ uint32_t floor_count(float p, uint32_t K, float Kf, bool& bad) {
+  bad |= !(p >= 0.f && p < 2.f);
+  const float x = __fmul_rz(p, Kf);
+  uint32_t q = __float2uint_rz(x);
+  if (x >= 16777216.f) q = floor_prod(p, K, bad);
+  return q;
 }
 
 struct ArgMax {
@@ -73,33 +72,22 @@ __device__ __forceinline__ ArgMax better(ArgMax a, ArgMax b) {
   return a;
 }
 
-// Shared scratch of one CTA: block-reduction slots, the values it publishes
-// to the other CTAs of its cluster, and the step's N-gram coefficients.
+// Shared scratch of one CTA of the standalone kernels: block-reduction
+// slots and the values it publishes to the other CTAs of its cluster.
 template <int NW>
 struct VocabSharedT {
   static constexpr int kNW = NW;
-  float wm[NW], wsum[NW], wh[NW];
-  unsigned long long wc[NW], wb[NW];
+  float wm[NW], wsum[NW];
+  unsigned long long wc[NW];
   ArgMax wa[NW];
   uint32_t wscan[NW];
   // published to the cluster
-  float cl_m, cl_s, cl_h;
-  unsigned long long cl_csum, cl_below;
+  unsigned long long cl_csum;
   ArgMax cl_arg;
   uint32_t cl_bad;
   uint32_t cl_total;
-  float cl_obs[3];          // p_tilde(t*), p_ng(t*), log p_tilde(t*) (owner CTA of t*)
-  // N-gram coefficients of this step
-  float cu, coef[kMaxOrder], nk[kMaxOrder];
-  const NgEntry* ent[kMaxOrder];
-  // the N-gram state one prediction reads: per order the context entry's
-  // (token, count) slots (ns < 0: no entry) and the closed form's weights
-  int ng_ns[kMaxOrder];
-  int ng_tok[kMaxOrder][kMaxSlots], ng_cnt[kMaxOrder][kMaxSlots];
-  float ng_coef[kMaxOrder], ng_cu;
 };
-using VocabShared = VocabSharedT<kWarps>;                         // standalone quantiser
-using StepShared = VocabSharedT<kStepThreads / 32>;               // the per-token step
+using VocabShared = VocabSharedT<kWarps>;
 
 template <typename Sh>
 __device__ float block_max(float v, Sh& sh) {
@@ -123,11 +111,6 @@ __device__ float block_sum(float v, Sh& sh) {
   __syncthreads();
   return r;
 }
-
-// Softmax statistics: the maximum and the sum of exp(s - max).
-struct MS {
-  float m, s;
-};
 
 template <int E>
 __device__ __forceinline__ void load_run(const float* src, int v0, int V, float (&out)[E], float fill) {
@@ -159,169 +142,118 @@ __device__ __forceinline__ void store_run(float* dst, int v0, int V, const float
   }
 }
 
-// Round 1 of the step: the softmax of s over the cluster's vocabulary.
-// Each CTA takes its own maximum m_c (exact) and its numerators
-// e_i = exp(s_i - m_c) with their sum s_c (thread, i in order -> warp, xor
-// tree -> CTA, warps in order); one cluster round then gives
-// M = max m_c and S = sum_c s_c exp(m_c - M) (ranks in order), and this
-// CTA's factor exp(m_c - M) / S turns e_i into p_i.  A second sum (the
-// N-gram entropy terms h_in) is reduced alongside, unscaled.
-template <int E, int CL, typename Sh>
-__device__ MS softmax_round(const float (&s)[E], float (&e)[E], float h_in, float& h_out, float& scale,
-                            cg::cluster_group& cl, Sh& sh) {
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  float m = -INFINITY;
+template <int E>
+__device__ __forceinline__ void load_counts(const int32_t* src, int v0, int V, int (&out)[E]) {
+  if (v0 + E <= V && (reinterpret_cast<uintptr_t>(src + v0) & 15) == 0) {
+    const int4* s4 = reinterpret_cast<const int4*>(src + v0);
 #pragma unroll
-  for (int i = 0; i < E; ++i) m = fmaxf(m, s[i]);
-  m = warp_max(m);
-  if (lane == 0) sh.wm[w] = m;
-  __syncthreads();
-  float mc = sh.wm[0];
-  for (int i = 1; i < Sh::kNW; ++i) mc = fmaxf(mc, sh.wm[i]);
-  float t = 0.f;
-  if (mc != -INFINITY) {
-#pragma unroll
-    for (int i = 0; i < E; ++i) {
-      e[i] = expf(s[i] - mc);
-      t += e[i];
+    for (int q = 0; q < E / 4; ++q) {
+      const int4 u = s4[q];
+      out[4 * q] = u.x;
+      out[4 * q + 1] = u.y;
+      out[4 * q + 2] = u.z;
+      out[4 * q + 3] = u.w;
     }
   } else {
 #pragma unroll
-    for (int i = 0; i < E; ++i) e[i] = 0.f;
+    for (int i = 0; i < E; ++i) out[i] = (v0 + i < V) ? src[v0 + i] : 0;
   }
-  t = warp_sum(t);
-  const float hw = warp_sum(h_in);
-  if (lane == 0) {
-    sh.wsum[w] = t;
-    sh.wh[w] = hw;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    float b = 0.f, bh = 0.f;
-    for (int i = 0; i < Sh::kNW; ++i) {
-      b += sh.wsum[i];
-      bh += sh.wh[i];
-    }
-    sh.cl_m = mc;
-    sh.cl_s = b;
-    sh.cl_h = bh;
-  }
-  cl.sync();
-  float M = -INFINITY;
+}
+template <int E>
+__device__ __forceinline__ void store_counts(int32_t* dst, int v0, int V, const int (&in)[E]) {
+  if (v0 + E <= V && (reinterpret_cast<uintptr_t>(dst + v0) & 15) == 0) {
+    int4* d4 = reinterpret_cast<int4*>(dst + v0);
 #pragma unroll
-  for (int r = 0; r < CL; ++r) M = fmaxf(M, cl.map_shared_rank(&sh, r)->cl_m);
-  float S = 0.f, H = 0.f;
+    for (int q = 0; q < E / 4; ++q) d4[q] = make_int4(in[4 * q], in[4 * q + 1], in[4 * q + 2], in[4 * q + 3]);
+  } else {
 #pragma unroll
-  for (int r = 0; r < CL; ++r) {
-    const Sh* o = cl.map_shared_rank(&sh, r);
-    if (o->cl_m != -INFINITY) S = fmaf(o->cl_s, expf(o->cl_m - M), S);
-    H += o->cl_h;
+    for (int i = 0; i < E; ++i)
+      if (v0 + i < V) dst[v0 + i] = in[i];
   }
-  h_out = H;
-  scale = mc != -INFINITY ? expf(mc - M) / S : 0.f;
-  return MS{M, S};
 }
 
+// ------------------------------------------------ standalone quantiser rounds
 struct QuantResult {
   long long resid;          // T - sum of floored counts, added to the first maximum
   int argmax;
-  unsigned long long below; // sum of floored counts of symbols below `want`
   bool bad;                 // non-finite / out-of-range probability, or floor underflow
 };
 
-// Round 2: floor-quantise the thread's E probabilities into c[], reduce the
-// count sum, the first argmax and (for `want` >= 0) the count sum below
-// `want` over the cluster.  The CTA owning `want` also publishes obs[3]
-// (read by every CTA after this round through cl_obs of the owner rank).
+// Floor-quantise the thread's E probabilities into c[], reduce the count sum
+// and the first argmax over the cluster (thread -> warp -> CTA -> ranks in
+// order), and add the residual to the first maximum.
 template <int E, int CL, typename Sh>
 __device__ QuantResult quantise_round(const float (&p)[E], int v0, int V, int log2T, uint32_t floor_c,
-                                      bool quantise, int want, const float* obs, uint32_t (&c)[E],
-                                      cg::cluster_group& cl, Sh& sh) {
+                                      uint32_t (&c)[E], cg::cluster_group& cl, Sh& sh) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const uint32_t T = 1u << log2T;
   const uint32_t K = T - (uint32_t)V * floor_c;
   bool bad = false;
-  unsigned long long csum = 0, below = 0;
+  unsigned long long csum = 0;
   ArgMax am{-INFINITY, 0x7fffffff};
 #pragma unroll
   for (int i = 0; i < E; ++i) {
     const int v = v0 + i;
     c[i] = 0;
-    if (quantise && v < V) {
-      const uint32_t q = floor_prod(p[i], K, bad);
+    if (v < V) {
+      const uint32_t q = floor_count(p[i], K, (float)K, bad);
       c[i] = q > floor_c ? q : floor_c;
       csum += c[i];
-      if (v < want) below += c[i];
       if (p[i] > am.v) am = ArgMax{p[i], v};   // strict: keeps the first maximum
-      bad |= !(p[i] == p[i]);
     }
   }
-  if (obs && want >= v0 && want < v0 + E) {
-    sh.cl_obs[0] = obs[0];
-    sh.cl_obs[1] = obs[1];
-    sh.cl_obs[2] = obs[2];
-  }
-  if (quantise) {
 #pragma unroll
-    for (int o = 16; o; o >>= 1) {
-      csum += __shfl_xor_sync(0xffffffffu, csum, o);
-      below += __shfl_xor_sync(0xffffffffu, below, o);
-      ArgMax b2;
-      b2.v = __shfl_xor_sync(0xffffffffu, am.v, o);
-      b2.i = __shfl_xor_sync(0xffffffffu, am.i, o);
-      am = better(am, b2);
+  for (int o = 16; o; o >>= 1) {
+    csum += __shfl_xor_sync(0xffffffffu, csum, o);
+    ArgMax b2;
+    b2.v = __shfl_xor_sync(0xffffffffu, am.v, o);
+    b2.i = __shfl_xor_sync(0xffffffffu, am.i, o);
+    am = better(am, b2);
+  }
+  const unsigned any_bad = __ballot_sync(0xffffffffu, bad);
+  if (lane == 0) {
+    sh.wc[w] = csum;
+    sh.wa[w] = am;
+    sh.wscan[w] = any_bad ? 1u : 0u;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long tc = 0;
+    ArgMax ta{-INFINITY, 0x7fffffff};
+    uint32_t tbad = 0;
+    for (int i = 0; i < Sh::kNW; ++i) {
+      tc += sh.wc[i];
+      ta = better(ta, sh.wa[i]);
+      tbad |= sh.wscan[i];
     }
-    const unsigned any_bad = __ballot_sync(0xffffffffu, bad);
-    if (lane == 0) {
-      sh.wc[w] = csum;
-      sh.wb[w] = below;
-      sh.wa[w] = am;
-      sh.wscan[w] = any_bad ? 1u : 0u;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      unsigned long long tc = 0, tb = 0;
-      ArgMax ta{-INFINITY, 0x7fffffff};
-      uint32_t tbad = 0;
-      for (int i = 0; i < Sh::kNW; ++i) {
-        tc += sh.wc[i];
-        tb += sh.wb[i];
-        ta = better(ta, sh.wa[i]);
-        tbad |= sh.wscan[i];
-      }
-      sh.cl_csum = tc;
-      sh.cl_below = tb;
-      sh.cl_arg = ta;
-      sh.cl_bad = tbad;
-    }
+    sh.cl_csum = tc;
+    sh.cl_arg = ta;
+    sh.cl_bad = tbad;
   }
   cl.sync();
-  QuantResult r{0, -1, 0, false};
-  if (quantise) {
-    unsigned long long total = 0;
-    ArgMax g{-INFINITY, 0x7fffffff};
-    for (int q = 0; q < CL; ++q) {
-      const Sh* o = cl.map_shared_rank(&sh, q);
-      total += o->cl_csum;
-      r.below += o->cl_below;
-      g = better(g, o->cl_arg);
-      r.bad |= o->cl_bad != 0;
-    }
-    r.resid = (long long)T - (long long)total;
-    r.argmax = g.i;
+  QuantResult r{0, -1, false};
+  unsigned long long total = 0;
+  ArgMax g{-INFINITY, 0x7fffffff};
+  for (int q = 0; q < CL; ++q) {
+    const Sh* o = cl.map_shared_rank(&sh, q);
+    total += o->cl_csum;
+    g = better(g, o->cl_arg);
+    r.bad |= o->cl_bad != 0;
+  }
+  r.resid = (long long)T - (long long)total;
+  r.argmax = g.i;
 #pragma unroll
-    for (int i = 0; i < E; ++i) {
-      if (v0 + i == g.i) {
-        const long long ci = (long long)c[i] + r.resid;
-        if (ci < (long long)floor_c || ci > (long long)T) r.bad = true;
-        c[i] = (uint32_t)ci;
-      }
+  for (int i = 0; i < E; ++i) {
+    if (v0 + i == g.i) {
+      const long long ci = (long long)c[i] + r.resid;
+      if (ci < (long long)floor_c || ci > (long long)T) r.bad = true;
+      c[i] = (uint32_t)ci;
     }
   }
   return r;
 }
 
-// Round 3: exclusive prefix sum of the final counts into cdf_row.
+// Exclusive prefix sum of the final counts into cdf_row.
 template <int E, typename Sh>
 __device__ void scan_round(const uint32_t (&c)[E], int v0, int V, uint32_t T, uint32_t* cdf_row,
                            cg::cluster_group& cl, Sh& sh) {
@@ -339,6 +271,7 @@ __device__ void scan_round(const uint32_t (&c)[E], int v0, int V, uint32_t T, ui
     const uint32_t t = __shfl_up_sync(0xffffffffu, inc, o);
     if (lane >= o) inc += t;
   }
+  __syncthreads();                                 // wscan was read by the quantiser round
   if (lane == 31) sh.wscan[w] = inc;
   __syncthreads();
   uint32_t before = 0, total = 0;
@@ -357,303 +290,780 @@ __device__ void scan_round(const uint32_t (&c)[E], int v0, int V, uint32_t T, ui
   if (v0 <= V - 1 && V - 1 < v0 + E) cdf_row[V] = T;
 }
 
-// One stream per cluster.  predict: p -> counts -> CDF and / or the coder
-// interval of the observed token.  update: head and mixer update with the
-// observed token.  Both may run in one pass (encoder) or in two (decoder,
-// which learns the token in between); the arithmetic is the same in either
-// case.
-__device__ void ngram_update_row(const Dims& D, const Batch& b, int j, int warp, int lane, StepShared* push,
-                                 cg::cluster_group* cl);
+// ======================================================================= step
+// The per-token step of one stream (Sec. 3.3-3.7) on a cluster of
+// kStepCluster CTAs.  CTA `rank` owns the vocabulary chunk from
+// base = rank kStepThreads E, its warp w the 32 E symbols from
+// wbase = base + 32 E w, lane l the E symbols from v0 = wbase + E l.
+// A reduction over the vocabulary takes one cluster barrier: every warp
+// publishes its partials in a slot of its CTA's shared memory, and after the
+// barrier every warp reads all kStepCluster x kStepWarps of them (lane l the
+// four of global warp index 4l .. 4l + 3) and reduces them with the same
+// shuffles, so every warp of the cluster holds the same result, whatever the
+// batch, the slot or the launch.  The arithmetic is written with explicitly
+// rounded operations and fixed approximations, so the single-step and the
+// multi-position kernels below compute the same bits.  FULL: the vocabulary
+// fills the cluster's E kStepThreads kStepCluster symbols exactly (no
+// symbol past V, every run 16-byte aligned).
 
-// The closed form's weights of the interpolation (Sec. 3.4): lambda_k =
-// n_k / (n_k + 5), A = prod (1 - lambda_k), beta_k = lambda_k prod_{j>k}
-// (1 - lambda_j), coefficient beta_k / n_k, and cu = A / (N + V).
-__device__ void ng_weights(const float (&nk)[kMaxOrder], const bool (&has)[kMaxOrder], int N, int V,
-                           float (&coef)[kMaxOrder], float& cu) {
-  float lam[kMaxOrder];
-  for (int k = 0; k < kMaxOrder; ++k) lam[k] = has[k] ? nk[k] / (nk[k] + 5.0f) : 0.f;
-  float A = 1.f;
-  for (int k = 0; k < kMaxOrder; ++k) A *= (1.f - lam[k]);
-  for (int k = 0; k < kMaxOrder; ++k) {
-    float beta = lam[k];
-    for (int q = k + 1; q < kMaxOrder; ++q) beta *= (1.f - lam[q]);
-    coef[k] = has[k] ? beta / nk[k] : 0.f;
-  }
-  cu = A / (float)(N + V);
+constexpr int kStepWarps = kStepThreads / 32;
+static_assert(kStepCluster * kStepWarps == 128, "four warp partials per lane");
+// A valid warp's count sum is at most T + eps K < 1.5 2^24 (T <= 2^24), so
+// 128 clamped warp sums stay below 2^32; larger sums are flagged bad.
+constexpr uint32_t kWarpCountCap = 3u << 23;
+constexpr float kLog2e = 1.4426950408889634f;
+
+// 2^x (PTX ex2.approx, flushing subnormal results to zero).
+__device__ __forceinline__ float ex2_approx(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
 }
+// e^x = 2^(x log2 e) for the few scalar exponentials of a step.
+__device__ __forceinline__ float exp_fast(float x) { return ex2_approx(__fmul_rn(x, kLog2e)); }
 
-// The N-gram state of the next prediction from the stream's tables: the
-// context entries' slots and the weights, into shared memory.
-template <typename Sh>
-__device__ void ng_gather(const Dims& D, const StreamDev& st, Sh& sh) {
-  if (threadIdx.x < kMaxOrder) {
-    const int k = threadIdx.x;
-    const int ei = (k < D.order) ? st.ctx_ent[k] : -1;
-    const NgEntry* en = ei >= 0 ? st.ent[k] + ei : nullptr;
-    sh.ent[k] = en;
-    sh.nk[k] = en ? (float)en->n : 0.f;
-    sh.ng_ns[k] = en ? en->nslots : 0;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    float nk[kMaxOrder];
-    bool has[kMaxOrder];
-    for (int k = 0; k < kMaxOrder; ++k) {
-      nk[k] = sh.nk[k];
-      has[k] = sh.ent[k] != nullptr;
-    }
-    ng_weights(nk, has, st.N, D.V, sh.ng_coef, sh.ng_cu);
-  }
-  for (int e = threadIdx.x; e < kMaxOrder * kMaxSlots; e += blockDim.x) {
-    const int k = e / kMaxSlots, q = e % kMaxSlots;
-    if (q < sh.ng_ns[k]) {
-      sh.ng_tok[k][q] = sh.ent[k]->tok[q];
-      sh.ng_cnt[k][q] = sh.ent[k]->cnt[q];
-    }
-  }
-  __syncthreads();
+__device__ __forceinline__ void cluster_arrive() {
+  asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
 }
+__device__ __forceinline__ void cluster_wait() { asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory"); }
 
-// One position of stream row j, by the cluster CTA `rank`: predict (biased
-// softmax, N-gram, mix, quantise; the coder interval or the CDF) and the
-// head and mixer update.  `bias` and `cnt` hold this thread's bias run and
-// unigram counts (loaded here unless have_bias / have_cnt; cnt gains the
-// coded token); ng_ready: the N-gram context state is already in shared
-// memory; `waited`: the caller already waited on the previous kernel.  Returns false when the observed token is out of range (flagged,
-// nothing updated).  The caller runs the N-gram update after it.
+// What the CTAs publish before one cluster barrier (two slots alternate).
+struct StepSlot {
+  float4 sm[kStepWarps];   // softmax: warp maximum m_w, sum of exp(s - m_w), N-gram entropy part
+  uint4 qn[kStepWarps];    // quantiser: count sum, first maximum (value bits, index), bad flag
+  float4 obs;              // the observed token's owner: p_tilde(t), p_ng(t), log p_tilde(t)
+};
+
+constexpr int kSnapBufs = 3;   // N-gram states in flight in the prefill loop
+struct StepShared {
+  StepSlot slot[2];
+  NgSnap ng[kSnapBufs];
+};
+
+// This thread's place in the cluster's split of the vocabulary.
+struct Lanes {
+  int rank, w, lane, gw, wbase, v0;
+};
 template <int E>
-__device__ bool vocab_pass(const Dims& D, const Batch& b, const VocabIO& io, int j, int rank, cg::cluster_group& cl,
-                           StepShared& sh, float* sp, float (&bias)[E], bool have_bias, int (&cnt)[E], bool have_cnt,
-                           bool ng_ready, bool waited) {
-  StreamDev& st = b.st[b.slots[j]];
-  const int V = D.V;
-  const int chunk = kStepThreads * E;
-  const int base = rank * chunk;
-  const int v0 = base + threadIdx.x * E;
-  const int i_tok = st.n_coded + 1;              // 1-based index of the token being coded
-  const float th0 = st.theta[0], th1 = st.theta[1];
+__device__ __forceinline__ Lanes lanes_of(int rank) {
+  Lanes L;
+  L.rank = rank;
+  L.w = threadIdx.x >> 5;
+  L.lane = threadIdx.x & 31;
+  L.gw = rank * kStepWarps + L.w;
+  L.wbase = rank * kStepThreads * E + L.w * 32 * E;
+  L.v0 = L.wbase + L.lane * E;
+  return L;
+}
 
-  // ---- before waiting on the LM head: bias and the N-gram distribution
-  // (state of earlier steps only)
-  if (!have_bias) {
-    if (D.use_head) {
-      load_run<E>(st.bias, v0, V, bias, 0.f);
-    } else {
+template <bool FULL>
+__device__ __forceinline__ bool in_vocab(int v, int V) {
+  return FULL || v < V;
+}
+template <int E, bool FULL>
+__device__ __forceinline__ void load_runf(const float* src, int v0, int V, float (&out)[E], float fill) {
+  if (FULL) {
+    const float4* s4 = reinterpret_cast<const float4*>(src + v0);
 #pragma unroll
-      for (int i = 0; i < E; ++i) bias[i] = 0.f;
+    for (int q = 0; q < E / 4; ++q) {
+      const float4 u = s4[q];
+      out[4 * q] = u.x;
+      out[4 * q + 1] = u.y;
+      out[4 * q + 2] = u.z;
+      out[4 * q + 3] = u.w;
     }
-  }
-  // N-gram: P = A (c + 1) / (N + V) + sum_k beta_k cnt_k / n_k, the closed
-  // form of the interpolation recursion with lambda_k = n_k / (n_k + 5).
-  float png[E];
-  // logits: after a prefill they are final already (the wait came first)
-  float s[E];
-  if (b.z_in) load_run<E>(b.z_in + (size_t)b.z_idx[j] * V, v0, V, s, -INFINITY);
-  const bool ngram = D.order > 0;
-  if (ngram) {
-    // unigram counts first (unless kept from the previous position):
-    // independent of the context entries below
-    if (have_cnt) {
-    } else if (v0 + E <= V && (reinterpret_cast<uintptr_t>(st.uni + v0) & 15) == 0) {
-      const int4* u4 = reinterpret_cast<const int4*>(st.uni + v0);
-#pragma unroll
-      for (int q = 0; q < E / 4; ++q) {
-        const int4 u = u4[q];
-        cnt[4 * q] = u.x;
-        cnt[4 * q + 1] = u.y;
-        cnt[4 * q + 2] = u.z;
-        cnt[4 * q + 3] = u.w;
-      }
-    } else {
-#pragma unroll
-      for (int i = 0; i < E; ++i) cnt[i] = (v0 + i < V) ? st.uni[v0 + i] : 0;
-    }
-    if (!ng_ready) ng_gather(D, st, sh);         // else pushed by the previous position
-    for (int i = threadIdx.x; i < chunk; i += kStepThreads) sp[i] = 0.f;
-    __syncthreads();
-    for (int k = 0; k < kMaxOrder; ++k) {
-      const int ns = sh.ng_ns[k];
-      for (int q = threadIdx.x; q < ns; q += kStepThreads) {
-        const int t = sh.ng_tok[k][q] - base;
-        if (t >= 0 && t < chunk) sp[t] += sh.ng_coef[k] * (float)sh.ng_cnt[k][q];
-      }
-      __syncthreads();
-    }
-    const float cu = sh.ng_cu;
-#pragma unroll
-    for (int i = 0; i < E; ++i) png[i] = (v0 + i < V) ? cu * (float)(cnt[i] + 1) + sp[threadIdx.x * E + i] : 0.f;
   } else {
-#pragma unroll
-    for (int i = 0; i < E; ++i) png[i] = 0.f;
+    load_run<E>(src, v0, V, out, fill);
   }
+}
 
-  if (!waited) {
-    pdl_wait();
-    pdl_trigger();
+// The partials of global warps 4 lane .. 4 lane + 3 of the cluster.
+template <typename T>
+__device__ __forceinline__ void read_parts(cg::cluster_group& cl, T* mine, int lane, T (&v)[4]) {
+  const T* src = cl.map_shared_rank(mine, lane >> 2) + 4 * (lane & 3);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) v[i] = src[i];
+}
+
+// p_ng of the thread's symbols (Sec. 3.4), the closed form
+// P(t) = A (c(t) + 1) / (N + V) + sum_k beta_k cnt_k(t) / n_k with the weights
+// in g.  Each warp adds the context slots' masses of its own 32 E symbols into
+// its region spw of shared memory (order by order, so a symbol's sum is taken
+// in the order k = 0, 1, 2); each lane then reads its E sums and zeroes them.
+template <int E, bool FULL>
+__device__ __forceinline__ void ngram_probs(const NgSnap& g, float* spw, const Lanes& L, int V, const int (&cnt)[E],
+                                            float (&png)[E]) {
+  constexpr int kSpan = 32 * E;
+#pragma unroll
+  for (int k = 0; k < kMaxOrder; ++k) {
+    const int ns = g.ns[k];
+    const float coef = g.coef[k];
+#pragma unroll
+    for (int h = 0; h < kMaxSlots / 32; ++h) {
+      const int q = L.lane + 32 * h;
+      if (q < ns) {
+        const int2 tc = g.tc[k][q];
+        const int t = tc.x - L.wbase;
+        if ((unsigned)t < (unsigned)kSpan) spw[t] = __fadd_rn(spw[t], __fmul_rn(coef, (float)tc.y));
+      }
+    }
+    __syncwarp();
   }
-  const int t_obs = (io.update || io.intervals) ? b.obs[j] : -1;
-  if (io.update && (t_obs < 0 || t_obs >= V)) {   // rejected on the host; never index with it
-    if (rank == 0 && threadIdx.x == 0) atomicOr(&st.status, ST_BAD_TOKEN);
-    return false;                                 // uniform across the cluster
+  const float cu = g.cu;
+  float4* s4 = reinterpret_cast<float4*>(spw + L.lane * E);
+#pragma unroll
+  for (int q = 0; q < E / 4; ++q) {
+    const float4 u = s4[q];
+    const float sv[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int ii = 4 * q + i;
+      png[ii] = in_vocab<FULL>(L.v0 + ii, V) ? __fmaf_rn(cu, (float)(cnt[ii] + 1), sv[i]) : 0.f;
+    }
+    s4[q] = make_float4(0.f, 0.f, 0.f, 0.f);
   }
-  if (io.probe_png && ngram) store_run<E>(io.probe_png + (size_t)j * V, v0, V, png);
+}
 
-  // ---- biased logits s = z / tau + b and their softmax (round 1)
-  if (!b.z_in) load_run<E>(st.z, v0, V, s, -INFINITY);
-  if (io.probe_z) store_run<E>(io.probe_z + (size_t)j * V, v0, V, s);
-  const float inv_tau = 1.0f / D.tau;             // exact for tau = 1
+template <int E>
+__device__ __forceinline__ void zero_region(float* spw, int lane) {
+  float4* s4 = reinterpret_cast<float4*>(spw + lane * E);
 #pragma unroll
-  for (int i = 0; i < E; ++i) s[i] = (v0 + i < V) ? fmaf(s[i], inv_tau, bias[i]) : -INFINITY;
-  // the N-gram entropy in bits (confidence skip, Sec. 3.7), -p log2 p summed
-  // with the softmax normaliser
-  float h_in = 0.f;
-  if (D.skip) {
-#pragma unroll
-    for (int i = 0; i < E; ++i)
-      if (v0 + i < V && png[i] > 0.f) h_in -= png[i] * log2f(png[i]);
-  }
-  float pt[E], H = 0.f, f_cta = 0.f;
-  const MS ms = softmax_round<E, kStepCluster>(s, pt, h_in, H, f_cta, cl, sh);
-  const bool skipped = D.skip && H < kSkipBits;
-  const float M = ms.m, S = ms.s;
-#pragma unroll
-  for (int i = 0; i < E; ++i) pt[i] = (v0 + i < V) ? pt[i] * f_cta : 0.f;
-  if (io.probe_pt) store_run<E>(io.probe_pt + (size_t)j * V, v0, V, pt);
+  for (int q = 0; q < E / 4; ++q) s4[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+}
 
-  // ---- mix (Sec. 3.5): LLM alone during warm-up
-  const bool mixing = ngram && i_tok > D.warmup;
-  const float tm = fmaxf(th0, th1);
-  const float e0 = expf(th0 - tm), e1 = expf(th1 - tm);
-  const float w0 = e0 / (e0 + e1), w1 = e1 / (e0 + e1);
-  float p[E];
+// Biased logits s = z / tau + b (Sec. 3.6); -inf past the vocabulary.
+template <int E, bool FULL>
+__device__ __forceinline__ void biased_logits(const float (&z)[E], const float (&bias)[E], float inv_tau, int v0,
+                                              int V, float (&s)[E]) {
 #pragma unroll
-  for (int i = 0; i < E; ++i) p[i] = skipped ? png[i] : mixing ? w0 * pt[i] + w1 * png[i] : pt[i];
-  if (io.probe_p) store_run<E>(io.probe_p + (size_t)j * V, v0, V, p);
+  for (int i = 0; i < E; ++i) s[i] = in_vocab<FULL>(v0 + i, V) ? __fmaf_rn(z[i], inv_tau, bias[i]) : -INFINITY;
+}
 
-  // ---- round 2: counts, residual, argmax, interval; publish t*'s values
-  float obs[3] = {0.f, 0.f, 0.f};
-  if (t_obs >= v0 && t_obs < v0 + E) {
+// The thread's part of the N-gram entropy in bits, -sum p log2 p (Sec. 3.7).
+template <int E>
+__device__ __forceinline__ float entropy_part(const float (&png)[E]) {
+  float h = 0.f;
+#pragma unroll
+  for (int i = 0; i < E; ++i)
+    if (png[i] > 0.f) h = __fmaf_rn(-png[i], log2f(png[i]), h);
+  return h;
+}
+
+// Softmax partials of the warp: its maximum m_w of s, e_i = exp(s_i - m_w)
+// = 2^(s_i log2 e - m_w log2 e) and the sum of the e_i; h (a second sum) is
+// reduced alongside.
+template <int E>
+__device__ __forceinline__ float4 softmax_part(const float (&s)[E], float (&e)[E], float h) {
+  float m = -INFINITY;
+#pragma unroll
+  for (int i = 0; i < E; ++i) m = fmaxf(m, s[i]);
+  m = warp_max(m);
+  float t = 0.f;
+  if (m == -INFINITY) {                           // no symbol of the warp in the vocabulary
+#pragma unroll
+    for (int i = 0; i < E; ++i) e[i] = 0.f;
+  } else {
+    const float mb = -__fmul_rn(m, kLog2e);
 #pragma unroll
     for (int i = 0; i < E; ++i) {
-      if (v0 + i == t_obs) {
-        obs[0] = pt[i];
-        obs[1] = png[i];
-        obs[2] = s[i] - M - logf(S);
-      }
+      e[i] = ex2_approx(__fmaf_rn(s[i], kLog2e, mb));
+      t = __fadd_rn(t, e[i]);
     }
   }
-  uint32_t c[E];
-  const QuantResult q = quantise_round<E, kStepCluster>(p, v0, V, D.log2T, D.floor, io.predict != 0, t_obs,
-                                          io.update ? obs : nullptr, c, cl, sh);
-  if (io.predict) {
-    if (q.bad && threadIdx.x == 0 && rank == 0) atomicOr(&st.status, ST_NUMERIC);
-    if (io.intervals && t_obs >= v0 && t_obs < v0 + E) {
-      const unsigned long long lo = q.below + (q.argmax < t_obs ? (unsigned long long)q.resid : 0ull);
-#pragma unroll
-      for (int i = 0; i < E; ++i) {
-        if (v0 + i == t_obs) {
-          uint32_t* iv = io.intervals + 2 * ((size_t)j * io.interval_stride + (i_tok - 1));
-          iv[0] = (uint32_t)lo;
-          iv[1] = (uint32_t)(lo + c[i]);
-        }
-      }
-    }
-    if (io.cdf) scan_round<E>(c, v0, V, 1u << D.log2T, io.cdf + (size_t)j * (V + 1), cl, sh);
-  }
-
-  if (io.update && !skipped) {                     // a skipped token teaches the N-gram only
-    const StepShared* o = cl.map_shared_rank(&sh, t_obs / chunk);
-    const float pts = o->cl_obs[0], pngs = o->cl_obs[1], lpt = o->cl_obs[2];
-    float scale = 1.f;
-    float nth0 = th0, nth1 = th1;
-    if (D.rule == NC_RULE_MIXED_NLL) {
-      if (mixing) {
-        const float pm = w0 * pts + w1 * pngs;
-        scale = w0 * pts / pm;
-        nth0 = th0 - D.alpha * (w0 - w0 * pts / pm);
-        nth1 = th1 - D.alpha * (w1 - w1 * pngs / pm);
-      }
-    } else if (mixing) {
-      const float a0 = th0 + D.eta * lpt, a1 = th1 + D.eta * logf(pngs);
-      const float am = fmaxf(a0, a1);
-      const float lse = am + logf(expf(a0 - am) + expf(a1 - am));
-      nth0 = a0 - lse;
-      nth1 = a1 - lse;
-    }
-    if (D.use_head) {
-      const float step = D.alpha * scale;
-#pragma unroll
-      for (int i = 0; i < E; ++i) bias[i] = bias[i] - step * (pt[i] - (v0 + i == t_obs ? 1.f : 0.f));
-      store_run<E>(st.bias, v0, V, bias);
-    }
-    if (rank == 0 && threadIdx.x == 0) {
-      st.theta[0] = nth0;
-      st.theta[1] = nth1;
-      st.pt_obs = pts;
-      st.png_obs = pngs;
-    }
-  }
-  // the unigram count of the coded token, for a caller that keeps the
-  // counts from one position to the next (the N-gram update adds it in memory)
-  if (ngram && io.update && t_obs >= v0 && t_obs < v0 + E) {
-#pragma unroll
-    for (int i = 0; i < E; ++i)
-      if (v0 + i == t_obs) cnt[i] += 1;
-  }
-  return true;
+  return make_float4(m, warp_sum(t), warp_sum(h), 0.f);
 }
 
+// The cluster's softmax: M = max m_w, S = sum_w t_w exp(m_w - M), and the
+// second sum H.
+struct Soft {
+  float M, S, H;
+};
+__device__ __forceinline__ Soft softmax_reduce(const float4 (&v)[4]) {
+  const float M = warp_max(fmaxf(fmaxf(v[0].x, v[1].x), fmaxf(v[2].x, v[3].x)));
+  float s = 0.f, h = 0.f;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    if (v[i].y > 0.f) s = __fmaf_rn(v[i].y, exp_fast(__fsub_rn(v[i].x, M)), s);
+    h = __fadd_rn(h, v[i].z);
+  }
+  return Soft{M, warp_sum(s), warp_sum(h)};
+}
+
+// p_tilde of the thread's symbols: e_i exp(m_w - M) / S.
 template <int E>
+__device__ __forceinline__ void probs_tilde(const float (&e)[E], float m_w, const Soft& sm, float (&pt)[E]) {
+  const float f = m_w == -INFINITY ? 0.f : __fdividef(exp_fast(__fsub_rn(m_w, sm.M)), sm.S);
+#pragma unroll
+  for (int i = 0; i < E; ++i) pt[i] = __fmul_rn(e[i], f);
+}
+
+// The mixer's weights softmax(theta) (Sec. 3.5).
+__device__ __forceinline__ float2 mix_weights(float th0, float th1) {
+  const float tm = fmaxf(th0, th1);
+  const float e0 = exp_fast(__fsub_rn(th0, tm)), e1 = exp_fast(__fsub_rn(th1, tm));
+  const float z = __fadd_rn(e0, e1);
+  return make_float2(__fdividef(e0, z), __fdividef(e1, z));
+}
+
+// The coded distribution: p_ng under the confidence skip (Sec. 3.7), the mix
+// w0 p_tilde + w1 p_ng (Sec. 3.5), or p_tilde alone during the warm-up.
+template <int E>
+__device__ __forceinline__ void coded_probs(const float (&pt)[E], const float (&png)[E], float2 w, bool skipped,
+                                            bool mixing, float (&p)[E]) {
+  if (skipped) {
+#pragma unroll
+    for (int i = 0; i < E; ++i) p[i] = png[i];
+  } else if (mixing) {
+#pragma unroll
+    for (int i = 0; i < E; ++i) p[i] = __fmaf_rn(w.x, pt[i], __fmul_rn(w.y, png[i]));
+  } else {
+#pragma unroll
+    for (int i = 0; i < E; ++i) p[i] = pt[i];
+  }
+}
+
+// Quantiser partials (Sec. 3.3): the thread's counts c_i = max(floor(p_i K),
+// floor) and the warp's count sum, first maximum and bad flag, packed for
+// publication.  scan: also excl = the counts of the warp's lanes below this
+// one.  am_i / am_c = the thread's first maximum and its count.
+template <int E, bool FULL>
+__device__ __forceinline__ uint4 quant_part(const float (&p)[E], const Lanes& L, int V, uint32_t K, float Kf,
+                                            uint32_t floor_c, bool scan, uint32_t (&c)[E], uint32_t& excl, int& am_i,
+                                            uint32_t& am_c) {
+  bool bad = false;
+  uint32_t ts = 0;
+  float amv = -INFINITY;
+  am_i = 0x7fffffff;
+  am_c = 0;
+#pragma unroll
+  for (int i = 0; i < E; ++i) {
+    const bool in = in_vocab<FULL>(L.v0 + i, V);
+    const uint32_t q = floor_count(p[i], K, Kf, bad);
+    c[i] = in ? max(q, floor_c) : 0u;
+    ts += c[i];
+    if (in && p[i] > amv) {                        // strict: keeps the first maximum
+      amv = p[i];
+      am_i = L.v0 + i;
+      am_c = c[i];
+    }
+  }
+  if (ts > kWarpCountCap) {                      // invalid: keeps the warp's sum below 2^32
+    bad = true;
+    ts = kWarpCountCap;
+  }
+  uint32_t wsum;
+  if (scan) {
+    uint32_t inc = ts;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t t = __shfl_up_sync(0xffffffffu, inc, o);
+      if (L.lane >= o) inc += t;
+    }
+    excl = inc - ts;
+    wsum = __shfl_sync(0xffffffffu, inc, 31);
+  } else {
+    wsum = ts;
+#pragma unroll
+    for (int o = 16; o; o >>= 1) wsum += __shfl_xor_sync(0xffffffffu, wsum, o);
+  }
+  // first maximum: value bits (p >= 0 orders as unsigned) over the inverted index
+  unsigned long long key =
+      ((unsigned long long)(amv > 0.f ? __float_as_uint(amv) : 0u) << 32) | (uint32_t)~(uint32_t)am_i;
+#pragma unroll
+  for (int o = 16; o; o >>= 1) {
+    const unsigned long long k2 = __shfl_xor_sync(0xffffffffu, key, o);
+    key = k2 > key ? k2 : key;
+  }
+  bad = __any_sync(0xffffffffu, bad) || wsum > kWarpCountCap;
+  return make_uint4(bad ? kWarpCountCap : wsum, (uint32_t)(key >> 32), ~(uint32_t)key, bad ? 1u : 0u);
+}
+
+// The cluster's quantiser results: the residual T - sum c (added to the first
+// maximum), the first maximum, and the counts of the warps before this one.
+struct Quant {
+  long long resid, woff;
+  int argmax;
+  bool bad;
+};
+__device__ __forceinline__ Quant quant_reduce(const uint4 (&v)[4], const Lanes& L, uint32_t T) {
+  uint32_t tot = 0, off = 0;
+  unsigned long long key = 0;
+  bool bad = false;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    tot += v[i].x;
+    if (4 * L.lane + i < L.gw) off += v[i].x;
+    const unsigned long long k = ((unsigned long long)v[i].y << 32) | (uint32_t)~v[i].z;
+    key = k > key ? k : key;
+    bad |= v[i].w != 0u;
+  }
+#pragma unroll
+  for (int o = 16; o; o >>= 1) {
+    tot += __shfl_xor_sync(0xffffffffu, tot, o);
+    off += __shfl_xor_sync(0xffffffffu, off, o);
+    const unsigned long long k2 = __shfl_xor_sync(0xffffffffu, key, o);
+    key = k2 > key ? k2 : key;
+  }
+  Quant q;
+  q.resid = (long long)T - (long long)tot;
+  q.woff = (long long)off;
+  q.argmax = (int)~(uint32_t)key;
+  q.bad = __any_sync(0xffffffffu, bad);
+  return q;
+}
+
+// Mixer update with the observed token (Sec. 3.5): exponential weights with
+// rate eta, or one gradient step of the mixed NLL; scale = the head's step
+// factor (1, or w0 p_tilde(t) / p(t) under the mixed NLL).
+__device__ __forceinline__ void mixer_update(const Dims& D, bool mixing, float2 w, float pts, float pngs, float lpt,
+                                             float& th0, float& th1, float& scale) {
+  scale = 1.f;
+  if (!mixing) return;
+  if (D.rule == NC_RULE_MIXED_NLL) {
+    const float pm = __fmaf_rn(w.x, pts, __fmul_rn(w.y, pngs));
+    const float r0 = __fdividef(__fmul_rn(w.x, pts), pm), r1 = __fdividef(__fmul_rn(w.y, pngs), pm);
+    scale = r0;
+    th0 = __fsub_rn(th0, __fmul_rn(D.alpha, __fsub_rn(w.x, r0)));
+    th1 = __fsub_rn(th1, __fmul_rn(D.alpha, __fsub_rn(w.y, r1)));
+  } else {
+    const float a0 = __fmaf_rn(D.eta, lpt, th0), a1 = __fmaf_rn(D.eta, __logf(pngs), th1);
+    const float am = fmaxf(a0, a1);
+    const float lse = __fadd_rn(am, __logf(__fadd_rn(exp_fast(__fsub_rn(a0, am)), exp_fast(__fsub_rn(a1, am)))));
+    th0 = __fsub_rn(a0, lse);
+    th1 = __fsub_rn(a1, lse);
+  }
+}
+
+// Head update (Sec. 3.6): b <- b - step (p_tilde - onehot(t)); `own`: t is
+// one of the thread's symbols (for the others p_tilde - 0 = p_tilde exactly).
+template <int E>
+__device__ __forceinline__ void head_update(float (&bias)[E], const float (&pt)[E], float step, int v0, int t,
+                                            bool own) {
+  if (own) {
+#pragma unroll
+    for (int i = 0; i < E; ++i) bias[i] = __fmaf_rn(-step, __fsub_rn(pt[i], v0 + i == t ? 1.f : 0.f), bias[i]);
+  } else {
+#pragma unroll
+    for (int i = 0; i < E; ++i) bias[i] = __fmaf_rn(-step, pt[i], bias[i]);
+  }
+}
+
+// The owner's value at its symbol t (no dynamic register indexing).
+template <int E, typename T>
+__device__ __forceinline__ T pick(const T (&a)[E], int v0, int t) {
+  T r = T(0);
+#pragma unroll
+  for (int i = 0; i < E; ++i)
+    if (v0 + i == t) r = a[i];
+  return r;
+}
+// Counts of the thread's symbols below t, and t's own.
+template <int E>
+__device__ __forceinline__ void counts_around(const uint32_t (&c)[E], int v0, int t, uint32_t& below, uint32_t& ct) {
+  below = 0;
+  ct = 0;
+#pragma unroll
+  for (int i = 0; i < E; ++i) {
+    if (v0 + i < t) below += c[i];
+    if (v0 + i == t) ct = c[i];
+  }
+}
+
+// The coder interval [lo, hi) of t (Sec. 3.3) from the cluster's quantiser
+// results and the owner's counts below t within its warp.
+__device__ __forceinline__ void write_interval(uint32_t* iv, const Quant& q, int t, uint32_t below, uint32_t ct) {
+  const long long lo = q.woff + below + (q.argmax < t ? q.resid : 0);
+  const long long hi = lo + ct + (q.argmax == t ? q.resid : 0);
+  iv[0] = (uint32_t)lo;
+  iv[1] = (uint32_t)hi;
+}
+
+// The first maximum's final count must stay within [floor, T].
+__device__ __forceinline__ bool final_count_bad(const Quant& q, int am_i, uint32_t am_c, uint32_t floor_c, uint32_t T) {
+  if (am_i != q.argmax) return false;
+  const long long cf = (long long)am_c + q.resid;
+  return cf < (long long)floor_c || cf > (long long)T;
+}
+
+__device__ __forceinline__ void cp_async16(void* dst_smem, const void* src) {
+  const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst_smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// Copy one N-gram state into shared memory (asynchronously, 16 bytes per thread).
+__device__ __forceinline__ void snap_copy_async(NgSnap* dst, const NgSnap* src) {
+  constexpr int kPieces = (int)(sizeof(NgSnap) / 16);
+  static_assert(kPieces <= kStepThreads, "one piece per thread");
+  if ((int)threadIdx.x < kPieces)
+    cp_async16(reinterpret_cast<char*>(dst) + 16 * threadIdx.x, reinterpret_cast<const char*>(src) + 16 * threadIdx.x);
+  cp_async_commit();
+}
+
+__device__ void ngram_update_row(const Dims& D, const Batch& b, int j, int warp, int lane);
+__device__ void ng_snapshot(const Dims& D, const StreamDev& st, NgSnap* out, int tid, int nthr);
+
+// One position of stream row j: predict (the coded distribution's CDF and /
+// or the coder interval of the observed token) and / or update (head and
+// mixer, then the N-gram and the stream's bookkeeping).  The decoder runs
+// the two in separate launches (it learns the token in between); the
+// arithmetic is the same in either case.
+template <int E, bool FULL>
 __global__ void __launch_bounds__(kStepThreads, 1) k_vocab(Dims D, Batch b, VocabIO io) {
   extern __shared__ float4 dyn4[];
-  float* sp = reinterpret_cast<float*>(dyn4);    // sparse N-gram mass of this CTA's chunk
   __shared__ StepShared sh;
   cg::cluster_group cl = cg::this_cluster();
   const int j = blockIdx.x / kStepCluster;
-  // after a prefill the previous kernel is the N-gram update of the previous
-  // position: nothing of the stream's state may be read before it completed
+  // after a prefill the previous kernel updated the stream's state: nothing
+  // of it may be read before that kernel completed
   if (b.z_in) {
     pdl_wait();
     pdl_trigger();
   }
   if (j >= *b.nB) return;                        // uniform across the cluster
-  const int rank = (int)cl.block_rank();
+  const Lanes L = lanes_of<E>((int)cl.block_rank());
+  StreamDev& st = b.st[b.slots[j]];
+  const int V = D.V;
+  const bool ngram = D.order > 0;
+  float* spw = reinterpret_cast<float*>(dyn4) + L.w * 32 * E;
+
+  // ---- the stream's state of earlier steps, before the wait on the LM head
   float bias[E];
   int cnt[E];
-  if (!vocab_pass<E>(D, b, io, j, rank, cl, sh, sp, bias, false, cnt, false, false, b.z_in != nullptr)) return;
-  cl.sync();   // keep this CTA's shared memory alive until the cluster has read it
-  // the N-gram update and bookkeeping of this row, once every CTA has read
-  // the stream's state
-  if (io.update && io.ngram && rank == 0)
-    ngram_update_row(D, b, j, threadIdx.x >> 5, threadIdx.x & 31, nullptr, nullptr);
+  if (D.use_head) {
+    load_runf<E, FULL>(st.bias, L.v0, V, bias, 0.f);
+  } else {
+#pragma unroll
+    for (int i = 0; i < E; ++i) bias[i] = 0.f;
+  }
+  if (ngram) {
+    load_counts<E>(st.uni, L.v0, V, cnt);
+    zero_region<E>(spw, L.lane);
+    ng_snapshot(D, st, &sh.ng[0], threadIdx.x, kStepThreads);
+    __syncthreads();
+  }
+  const int i_tok = st.n_coded + 1;              // 1-based index of the token being coded
+  float th0 = st.theta[0], th1 = st.theta[1];
+  float z[E];
+  if (b.z_in) load_runf<E, FULL>(b.z_in + (size_t)b.z_idx[j] * V, L.v0, V, z, -INFINITY);
+  if (!b.z_in) {
+    pdl_wait();
+    pdl_trigger();
+  }
+  const int t = (io.update || io.intervals) ? b.obs[j] : -1;
+  if (io.update && (t < 0 || t >= V)) {          // rejected on the host; never index with it
+    if (L.rank == 0 && threadIdx.x == 0) atomicOr(&st.status, ST_BAD_TOKEN);
+    return;                                      // uniform across the cluster
+  }
+  if (!b.z_in) load_runf<E, FULL>(st.z, L.v0, V, z, -INFINITY);
+  if (io.probe_z) store_run<E>(io.probe_z + (size_t)j * V, L.v0, V, z);
+
+  // ---- softmax (Sec. 3.6) and the N-gram distribution
+  float png[E];
+  if (ngram) {
+    ngram_probs<E, FULL>(sh.ng[0], spw, L, V, cnt, png);
+    if (io.probe_png) store_run<E>(io.probe_png + (size_t)j * V, L.v0, V, png);
+  } else {
+#pragma unroll
+    for (int i = 0; i < E; ++i) png[i] = 0.f;
+  }
+  float s[E], e[E];
+  biased_logits<E, FULL>(z, bias, 1.0f / D.tau, L.v0, V, s);
+  const bool owner = t >= L.v0 && t < L.v0 + E;
+  float s_t = 0.f, png_t = 0.f;
+  if (owner) {
+    s_t = pick<E>(s, L.v0, t);
+    png_t = pick<E>(png, L.v0, t);
+  }
+  const float4 part = softmax_part<E>(s, e, D.skip ? entropy_part<E>(png) : 0.f);
+  if (L.lane == 0) sh.slot[0].sm[L.w] = part;
+  cl.sync();
+  float4 smv[4];
+  read_parts(cl, sh.slot[0].sm, L.lane, smv);
+  const Soft sm = softmax_reduce(smv);
+  const bool skipped = D.skip && sm.H < kSkipBits;
+  float pt[E];
+  probs_tilde<E>(e, part.x, sm, pt);
+  if (io.probe_pt) store_run<E>(io.probe_pt + (size_t)j * V, L.v0, V, pt);
+
+  // ---- the coded distribution and its counts (Sec. 3.3, 3.5)
+  const bool mixing = ngram && i_tok > D.warmup;
+  const float2 w = mix_weights(th0, th1);
+  float p[E];
+  coded_probs<E>(pt, png, w, skipped, mixing, p);
+  if (io.probe_p) store_run<E>(io.probe_p + (size_t)j * V, L.v0, V, p);
+  if (owner) sh.slot[1].obs = make_float4(pick<E>(pt, L.v0, t), png_t, __fsub_rn(__fsub_rn(s_t, sm.M), __logf(sm.S)), 0.f);
+  const uint32_t T = 1u << D.log2T, K = T - (uint32_t)V * D.floor;
+  uint32_t c[E], excl = 0, am_c = 0, below_t = 0, c_t = 0;
+  int am_i = 0x7fffffff;
+  if (io.predict) {
+    const bool scan = io.cdf || (t >= L.wbase && t < L.wbase + 32 * E);
+    const uint4 qp = quant_part<E, FULL>(p, L, V, K, (float)K, D.floor, scan, c, excl, am_i, am_c);
+    if (L.lane == 0) sh.slot[1].qn[L.w] = qp;
+    if (owner) {
+      counts_around<E>(c, L.v0, t, below_t, c_t);
+      below_t += excl;
+    }
+  }
+  cl.sync();
+  if (io.predict) {
+    uint4 qnv[4];
+    read_parts(cl, sh.slot[1].qn, L.lane, qnv);
+    const Quant q = quant_reduce(qnv, L, T);
+    if (io.intervals && owner)
+      write_interval(io.intervals + 2 * ((size_t)j * io.interval_stride + (i_tok - 1)), q, t, below_t, c_t);
+    if (io.cdf) {
+      uint32_t* row = io.cdf + (size_t)j * (V + 1);
+      long long run = q.woff + excl;
+#pragma unroll
+      for (int i = 0; i < E; ++i) {
+        const int v = L.v0 + i;
+        if (in_vocab<FULL>(v, V)) {
+          row[v] = (uint32_t)(run + (q.argmax < v ? q.resid : 0));
+          run += c[i];
+        }
+      }
+      if (L.v0 <= V - 1 && V - 1 < L.v0 + E) row[V] = T;
+    }
+    if ((q.bad && L.rank == 0 && threadIdx.x == 0) || final_count_bad(q, am_i, am_c, D.floor, T))
+      atomicOr(&st.status, ST_NUMERIC);
+  }
+
+  // ---- head and mixer update (a skipped token teaches the N-gram only)
+  if (io.update && !skipped) {
+    const float4 o = cl.map_shared_rank(&sh.slot[1], t / (kStepThreads * E))->obs;
+    float scale;
+    mixer_update(D, mixing, w, o.x, o.y, o.z, th0, th1, scale);
+    if (D.use_head) {
+      head_update<E>(bias, pt, __fmul_rn(D.alpha, scale), L.v0, t, owner);
+      store_run<E>(st.bias, L.v0, V, bias);
+    }
+    if (L.rank == 0 && threadIdx.x == 0) {
+      st.theta[0] = th0;
+      st.theta[1] = th1;
+      st.pt_obs = o.x;
+      st.png_obs = o.y;
+    }
+  }
+  cl.sync();   // every CTA has read the others' slots and the stream's state
+  if (io.update && io.ngram && L.rank == 0) ngram_update_row(D, b, j, L.w, L.lane);
 }
 
-// The vocabulary passes of a prefill chunk: the cluster of stream row j runs
-// positions p0 .. p0 + m - 1 in order (while the stream has tokens), each
-// one vocab_pass and the N-gram update, with the bias kept in registers and
-// a cluster barrier between positions.
-template <int E>
+// The vocabulary passes of a prefill chunk (encoder): the cluster of stream
+// row j runs its positions r = 0 .. m - 1 in order while j < nb_step[r],
+// with the bias, the unigram counts, the mixer's log-weights and the position
+// kept on chip and the N-gram state of each prediction read from snap (made
+// ahead by k_ngram_seq).  Under the log-loss mixer the head's step does not
+// wait for the mixer, so position r's quantiser and mixer results share the
+// cluster barrier of position r + 1's softmax: one barrier per position.
+// The next position's logits, token and activity and the N-gram state two
+// positions ahead are fetched between the barrier's arrive and wait, so the
+// barrier's release never waits for them.
+template <int E, bool FULL>
 __global__ void __launch_bounds__(kStepThreads, 1)
     k_vocab_seq(Dims D, Batch b, VocabIO io, int m, int n_streams, const float* zrows, const int32_t* nb_step,
-                const int32_t* obs_step) {
+                const int32_t* obs_step, const NgSnap* snap) {
   extern __shared__ float4 dyn4[];
-  float* sp = reinterpret_cast<float*>(dyn4);
   __shared__ StepShared sh;
   cg::cluster_group cl = cg::this_cluster();
   const int j = blockIdx.x / kStepCluster;
   pdl_wait();
   pdl_trigger();
-  const int rank = (int)cl.block_rank();
-  float bias[E];
+  if (m < 1 || j >= nb_step[0]) return;          // uniform across the cluster
+  const Lanes L = lanes_of<E>((int)cl.block_rank());
+  StreamDev& st = b.st[b.slots[j]];
+  const int V = D.V;
+  const bool ngram = D.order > 0;
+  const bool fused = D.rule != NC_RULE_MIXED_NLL;
+  const float inv_tau = 1.0f / D.tau;
+  const uint32_t T = 1u << D.log2T, K = T - (uint32_t)V * D.floor;
+  const float Kf = (float)K;
+  float* spw = reinterpret_cast<float*>(dyn4) + L.w * 32 * E;
+  const float* zj = zrows + (size_t)b.z_idx[j] * V;
+  const NgSnap* gj = ngram ? snap + b.z_idx[j] : nullptr;
+  const int32_t* obs_j = obs_step + j;
+
+  float bias[E], z[E];
   int cnt[E];
-  for (int r = 0; r < m; ++r) {
-    if (j >= nb_step[r]) break;                    // uniform across the cluster
-    Batch br = b;
-    br.obs = obs_step + (size_t)r * n_streams;
-    br.z_in = zrows + (size_t)r * D.V;
-    if (!vocab_pass<E>(D, br, io, j, rank, cl, sh, sp, bias, r > 0, cnt, r > 0, r > 0, true)) break;
-    if (io.ngram && rank == 0) ngram_update_row(D, br, j, threadIdx.x >> 5, threadIdx.x & 31, &sh, &cl);
-    cl.sync();   // the stream's state of this position is final for the next
+  if (D.use_head) {
+    load_runf<E, FULL>(st.bias, L.v0, V, bias, 0.f);
+  } else {
+#pragma unroll
+    for (int i = 0; i < E; ++i) bias[i] = 0.f;
+  }
+  bool act1 = 1 < m && j < nb_step[1];           // position r + 1 exists
+  if (ngram) {
+    load_counts<E>(st.uni, L.v0, V, cnt);
+    zero_region<E>(spw, L.lane);
+    snap_copy_async(&sh.ng[0], gj);
+    if (act1) snap_copy_async(&sh.ng[1], gj + 1);
+  } else {
+#pragma unroll
+    for (int i = 0; i < E; ++i) cnt[i] = 0;
+  }
+  load_runf<E, FULL>(zj, L.v0, V, z, -INFINITY);
+  int t = obs_j[0];
+  float th0 = st.theta[0], th1 = st.theta[1];
+  const int n0 = st.n_coded;
+  if (ngram) cp_async_wait_all();
+  __syncthreads();                               // the first N-gram states are in shared memory
+
+  // the previous position's values its quantiser and mixer step need
+  bool pend = false, p_skip = false, p_mix = false, p_own = false;
+  int p_t = 0, p_pos = 0, p_am_i = 0x7fffffff;
+  uint32_t p_below = 0, p_ct = 0, p_am_c = 0;
+  float2 p_w = make_float2(0.f, 0.f);
+  float last_pts = st.pt_obs, last_pngs = st.png_obs;
+  int nb = 0;                                    // cluster barriers taken
+  int r = 0, t_last = -1;
+
+  // interval, numeric checks and mixer step of the pending position from the
+  // quantiser partials qv and the observed values o (read from its slot)
+  auto finish = [&](const uint4 (&qv)[4], float4 o, const float (&pt)[E], bool with_head) {
+    const Quant q = quant_reduce(qv, L, T);
+    if (p_own)
+      write_interval(io.intervals + 2 * ((size_t)j * io.interval_stride + p_pos), q, p_t, p_below, p_ct);
+    if ((q.bad && L.rank == 0 && threadIdx.x == 0) || final_count_bad(q, p_am_i, p_am_c, D.floor, T))
+      atomicOr(&st.status, ST_NUMERIC);
+    if (!p_skip) {
+      float scale;
+      mixer_update(D, p_mix, p_w, o.x, o.y, o.z, th0, th1, scale);
+      if (with_head && D.use_head)
+        head_update<E>(bias, pt, __fmul_rn(D.alpha, scale), L.v0, p_t, p_t >= L.v0 && p_t < L.v0 + E);
+      last_pts = o.x;
+      last_pngs = o.y;
+    }
+  };
+
+  bool live = true;
+  while (live) {
+    if (t < 0 || t >= V) {                       // rejected on the host; never index with it
+      if (L.rank == 0 && threadIdx.x == 0) atomicOr(&st.status, ST_BAD_TOKEN);
+      break;                                     // uniform across the cluster
+    }
+    const bool more = act1;
+
+    // ---- softmax partials of position r
+    float png[E];
+    if (ngram) {
+      ngram_probs<E, FULL>(sh.ng[r % kSnapBufs], spw, L, V, cnt, png);
+    } else {
+#pragma unroll
+      for (int i = 0; i < E; ++i) png[i] = 0.f;
+    }
+    float s[E], e[E];
+    biased_logits<E, FULL>(z, bias, inv_tau, L.v0, V, s);
+    const bool owner = t >= L.v0 && t < L.v0 + E;
+    float s_t = 0.f, png_t = 0.f;
+    if (owner) {
+      s_t = pick<E>(s, L.v0, t);
+      png_t = pick<E>(png, L.v0, t);
+    }
+    const float4 part = softmax_part<E>(s, e, D.skip ? entropy_part<E>(png) : 0.f);
+    StepSlot& in = sh.slot[nb & 1];
+    if (L.lane == 0) in.sm[L.w] = part;
+    if (ngram) cp_async_wait_all();              // the state of position r + 1, read after this barrier
+    cluster_arrive();
+    // fetched outside the barrier's release: position r + 1's logits, token
+    // and activity, the N-gram state of r + 2
+    int t_n = 0;
+    bool act2 = false;
+    if (more) {
+      load_runf<E, FULL>(zj + (size_t)(r + 1) * V, L.v0, V, z, -INFINITY);
+      t_n = obs_j[(size_t)(r + 1) * n_streams];
+      act2 = r + 2 < m && j < nb_step[r + 2];
+      if (ngram && act2) snap_copy_async(&sh.ng[(r + 2) % kSnapBufs], gj + r + 2);
+    }
+    cluster_wait();
+    ++nb;
+    float4 smv[4];
+    read_parts(cl, in.sm, L.lane, smv);
+    float pt[E];
+    if (pend) {                                  // position r - 1 (log-loss mixer: no head step here)
+      uint4 qv[4];
+      read_parts(cl, in.qn, L.lane, qv);
+      const float4 o = p_skip ? make_float4(0.f, 0.f, 0.f, 0.f)
+                              : cl.map_shared_rank(&in, p_t / (kStepThreads * E))->obs;
+      finish(qv, o, pt, false);
+      pend = false;
+    }
+
+    // ---- position r: probabilities, counts, head step
+    const Soft sm = softmax_reduce(smv);
+    const bool skipped = D.skip && sm.H < kSkipBits;
+    probs_tilde<E>(e, part.x, sm, pt);
+    const bool mixing = ngram && n0 + r + 1 > D.warmup;
+    const float2 w = mix_weights(th0, th1);
+    float p[E];
+    coded_probs<E>(pt, png, w, skipped, mixing, p);
+    StepSlot& nx = sh.slot[nb & 1];
+    if (owner) nx.obs = make_float4(pick<E>(pt, L.v0, t), png_t, __fsub_rn(__fsub_rn(s_t, sm.M), __logf(sm.S)), 0.f);
+    uint32_t c[E], excl = 0;
+    const bool scan = io.intervals && t >= L.wbase && t < L.wbase + 32 * E;
+    const uint4 qp = quant_part<E, FULL>(p, L, V, K, Kf, D.floor, scan, c, excl, p_am_i, p_am_c);
+    if (L.lane == 0) nx.qn[L.w] = qp;
+    p_own = owner && io.intervals;
+    if (owner) {
+      counts_around<E>(c, L.v0, t, p_below, p_ct);
+      p_below += excl;
+      if (ngram) {
+#pragma unroll
+        for (int i = 0; i < E; ++i)
+          if (L.v0 + i == t) cnt[i] += 1;
+      }
+    }
+    p_t = t;
+    p_pos = n0 + r;                              // the token's index in its stream
+    p_skip = skipped;
+    p_mix = mixing;
+    p_w = w;
+    t_last = t;
+    if (fused) {
+      if (!skipped && D.use_head) head_update<E>(bias, pt, __fmul_rn(D.alpha, 1.f), L.v0, t, owner);
+      pend = true;
+    } else {
+      cl.sync();
+      ++nb;
+      uint4 qv[4];
+      read_parts(cl, nx.qn, L.lane, qv);
+      const float4 o = skipped ? make_float4(0.f, 0.f, 0.f, 0.f) : cl.map_shared_rank(&nx, t / (kStepThreads * E))->obs;
+      finish(qv, o, pt, true);
+    }
+    ++r;
+    t = t_n;
+    act1 = act2;
+    live = more;
+  }
+  if (pend) {
+    cl.sync();
+    ++nb;
+    StepSlot& in = sh.slot[(nb - 1) & 1];
+    uint4 qv[4];
+    read_parts(cl, in.qn, L.lane, qv);
+    const float4 o = p_skip ? make_float4(0.f, 0.f, 0.f, 0.f) : cl.map_shared_rank(&in, p_t / (kStepThreads * E))->obs;
+    float none[E];
+    finish(qv, o, none, false);
+  }
+  if (ngram) cp_async_wait_all();                // no copy outlives the kernel
+  cl.sync();   // every CTA is done with the others' shared memory
+  if (r == 0) return;
+
+  // ---- the stream's state after the chunk's r positions
+  if (D.use_head) store_run<E>(st.bias, L.v0, V, bias);
+  if (ngram) store_counts<E>(st.uni, L.v0, V, cnt);
+  if (L.rank == 0 && threadIdx.x == 0) {
+    st.theta[0] = th0;
+    st.theta[1] = th1;
+    st.pt_obs = last_pts;
+    st.png_obs = last_pngs;
+    // the window slides by C whenever it is full before a token is coded
+    const int last = n0 + r - 1;
+    int start = st.kv_start;
+    for (int a = start + D.L; a <= last; a += D.C) start += D.C;
+    st.kv_start = start;
+    st.n_coded = n0 + r;
+    st.last_tok = t_last;
   }
 }
 
@@ -705,18 +1115,58 @@ __device__ int ng_find(StreamDev& st, int k, unsigned long long key, bool insert
   return -1;
 }
 
-// One warp per stream: count the observed token in every context order,
-// the unigram counts, then advance the stream (window, history, position) and
-// look up the contexts of the next prediction.
-// The N-gram update of row j and the stream's bookkeeping for the next step.
-// Warp k (k < 3) owns order k: it counts the observed token t in the entry
-// of the context of length k + 1 (inserting the context if new), then looks
-// up the entry of the next context (t appended) for the next prediction.
-// The orders use separate tables, so the warps run concurrently; within an
-// order the lookup follows the update.  Warp 0 also updates the unigram
-// counts and the stream's position, history and window start.
-__device__ void ngram_update_order(const Dims& D, StreamDev& st, int t, int k, int lane) {
-  const int nh = min(3, st.n_coded);               // contexts before t
+// The closed form's weights of the interpolation (Sec. 3.4): lambda_k =
+// n_k / (n_k + 5), A = prod (1 - lambda_k), beta_k = lambda_k prod_{j>k}
+// (1 - lambda_j), coefficient beta_k / n_k, and cu = A / (N + V).
+__device__ void ng_weights(const float (&nk)[kMaxOrder], const bool (&has)[kMaxOrder], int N, int V,
+                           float (&coef)[kMaxOrder], float& cu) {
+  float lam[kMaxOrder];
+  for (int k = 0; k < kMaxOrder; ++k) lam[k] = has[k] ? nk[k] / (nk[k] + 5.0f) : 0.f;
+  float A = 1.f;
+  for (int k = 0; k < kMaxOrder; ++k) A *= (1.f - lam[k]);
+  for (int k = 0; k < kMaxOrder; ++k) {
+    float beta = lam[k];
+    for (int q = k + 1; q < kMaxOrder; ++q) beta *= (1.f - lam[q]);
+    coef[k] = has[k] ? beta / nk[k] : 0.f;
+  }
+  cu = A / (float)(N + V);
+}
+
+// The N-gram state of the stream's next prediction into *out (the context
+// entries the last update found), by threads tid = 0 .. nthr - 1.
+__device__ void ng_snapshot(const Dims& D, const StreamDev& st, NgSnap* out, int tid, int nthr) {
+  for (int e = tid; e < kMaxOrder * kMaxSlots; e += nthr) {
+    const int k = e / kMaxSlots, q = e - k * kMaxSlots;
+    const int ei = k < D.order ? st.ctx_ent[k] : -1;
+    if (ei >= 0) {
+      const NgEntry& en = st.ent[k][ei];
+      if (q < en.nslots) out->tc[k][q] = make_int2(en.tok[q], en.cnt[q]);
+    }
+  }
+  if (tid == 0) {
+    float nk[kMaxOrder], coef[kMaxOrder], cu;
+    bool has[kMaxOrder];
+    for (int k = 0; k < kMaxOrder; ++k) {
+      const int ei = k < D.order ? st.ctx_ent[k] : -1;
+      has[k] = ei >= 0;
+      nk[k] = has[k] ? (float)st.ent[k][ei].n : 0.f;
+      out->ns[k] = has[k] ? st.ent[k][ei].nslots : 0;
+    }
+    ng_weights(nk, has, st.N, D.V, coef, cu);
+    for (int k = 0; k < kMaxOrder; ++k) out->coef[k] = coef[k];
+    out->ns[3] = 0;
+    out->coef[3] = 0.f;
+    out->cu = cu;
+  }
+}
+
+// Warp k (k < 3) owns order k: it counts the observed token t in the entry of
+// the context of length k + 1 (inserting the context if new; a full entry
+// evicts its lowest count), then looks up the entry of the next context (t
+// appended) for the next prediction.  The orders use separate tables, so the
+// warps run concurrently.  n_coded: tokens coded before t.
+__device__ void ngram_update_order(const Dims& D, StreamDev& st, int t, int k, int lane, int n_coded) {
+  const int nh = min(3, n_coded);                  // contexts before t
   if (k < D.order && k < nh) {
     int ei = 0;
     if (lane == 0) ei = ng_find(st, k, ctx_key(st.hist, k + 1), true);
@@ -773,23 +1223,21 @@ __device__ void ngram_update_order(const Dims& D, StreamDev& st, int t, int k, i
   // the next context: the last k + 1 tokens with t appended
   if (lane == 0) {
     int nhist[3] = {st.hist[1], st.hist[2], t};
-    const int nh2 = min(3, st.n_coded + 1);
+    const int nh2 = min(3, n_coded + 1);
     st.ctx_ent[k] = (k < D.order && k < nh2) ? ng_find(st, k, ctx_key(nhist, k + 1), false) : -1;
   }
 }
 
-// push (the persistent loop): afterwards the N-gram state of the stream's
-// next prediction is written into the shared memory of every CTA of the
-// cluster (the same values ng_gather would read from the tables).
-__device__ void ngram_update_row(const Dims& D, const Batch& b, int j, int warp, int lane, StepShared* push,
-                                 cg::cluster_group* cl) {
+// The N-gram update of row j and the stream's bookkeeping for the next step
+// (one position of the step kernel).
+__device__ void ngram_update_row(const Dims& D, const Batch& b, int j, int warp, int lane) {
   StreamDev& st = b.st[b.slots[j]];
   const int t = b.obs[j];
   if (t < 0 || t >= D.V) {
     if (warp == 0 && lane == 0) atomicOr(&st.status, ST_BAD_TOKEN);
     return;
   }
-  if (warp < kMaxOrder) ngram_update_order(D, st, t, warp, lane);
+  if (warp < kMaxOrder) ngram_update_order(D, st, t, warp, lane, st.n_coded);
   __syncthreads();                                 // every order has read the old history
   if (warp == 0 && lane == 0) {
     if (D.order > 0) {
@@ -805,35 +1253,36 @@ __device__ void ngram_update_row(const Dims& D, const Batch& b, int j, int warp,
     st.n_coded += 1;
     st.last_tok = t;
   }
-  if (!push || D.order == 0) return;
-  __syncthreads();                                 // every order's lookup and the unigram total are final
-  if (warp < kMaxOrder) {
-    const int k = warp;
-    const int ei = k < D.order ? st.ctx_ent[k] : -1;
-    const NgEntry* en = ei >= 0 ? st.ent[k] + ei : nullptr;
-    const int ns = en ? en->nslots : 0;
-    for (int r = 0; r < kStepCluster; ++r) {
-      StepShared* o = cl->map_shared_rank(push, r);
-      if (lane == 0) o->ng_ns[k] = ns;
-      for (int q = lane; q < ns; q += 32) {
-        o->ng_tok[k][q] = en->tok[q];
-        o->ng_cnt[k][q] = en->cnt[q];
-      }
+}
+
+// The N-gram side of a prefill chunk, one CTA per stream row: for each
+// position in order, the state of its prediction into snap, then the update
+// with the observed token (tables, context entries, history and N; the
+// unigram counts and the position stay with the vocabulary passes).  It needs
+// only the tokens, so it runs beside the chunk's forward pass.
+__global__ void __launch_bounds__(128) k_ngram_seq(Dims D, Batch b, int m, int n_streams, const int32_t* nb_step,
+                                                   const int32_t* obs_step, const int32_t* z_idx, NgSnap* snap) {
+  const int j = blockIdx.x;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  StreamDev& st = b.st[b.slots[j]];
+  int n_coded = st.n_coded;
+  NgSnap* out = snap + z_idx[j];
+  for (int r = 0; r < m; ++r) {
+    if (j >= nb_step[r]) break;
+    const int t = obs_step[(size_t)r * n_streams + j];
+    ng_snapshot(D, st, out + r, threadIdx.x, blockDim.x);
+    if (t < 0 || t >= D.V) break;                  // flagged by the vocabulary pass
+    __syncthreads();                               // this prediction's entries are copied
+    if (warp < kMaxOrder) ngram_update_order(D, st, t, warp, lane, n_coded);
+    __syncthreads();                               // every order has read the old history
+    if (threadIdx.x == 0) {
+      st.N += 1;
+      st.hist[0] = st.hist[1];
+      st.hist[1] = st.hist[2];
+      st.hist[2] = t;
     }
-  } else if (warp == kMaxOrder && lane == 0) {
-    float nk[kMaxOrder], coef[kMaxOrder], cu;
-    bool has[kMaxOrder];
-    for (int k = 0; k < kMaxOrder; ++k) {
-      const int ei = k < D.order ? st.ctx_ent[k] : -1;
-      has[k] = ei >= 0;
-      nk[k] = has[k] ? (float)st.ent[k][ei].n : 0.f;
-    }
-    ng_weights(nk, has, st.N, D.V, coef, cu);
-    for (int r = 0; r < kStepCluster; ++r) {
-      StepShared* o = cl->map_shared_rank(push, r);
-      for (int k = 0; k < kMaxOrder; ++k) o->ng_coef[k] = coef[k];
-      o->ng_cu = cu;
-    }
+    ++n_coded;
+    __syncthreads();                               // history and N are final for the next position
   }
 }
 
@@ -912,7 +1361,7 @@ __global__ void __cluster_dims__(kVocabCluster, 1, 1) __launch_bounds__(kVocabTh
   float pr[E];
   load_run<E>(p + (size_t)j * V, v0, V, pr, 0.f);
   uint32_t c[E];
-  const QuantResult q = quantise_round<E, kVocabCluster>(pr, v0, V, log2T, floor_c, true, -1, nullptr, c, cl, sh);
+  const QuantResult q = quantise_round<E, kVocabCluster>(pr, v0, V, log2T, floor_c, c, cl, sh);
   if (q.bad && threadIdx.x == 0 && rank == 0) atomicOr(status + j, ST_NUMERIC);
   scan_round<E>(c, v0, V, 1u << log2T, cdf + (size_t)j * (V + 1), cl, sh);
   cl.sync();
@@ -923,7 +1372,7 @@ __global__ void k_floor_counts(const float* p, int64_t n, uint32_t K, uint32_t f
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     bool bad = false;
-    const uint32_t q = floor_prod(p[i], K, bad);
+    const uint32_t q = floor_count(p[i], K, (float)K, bad);
     c[i] = bad ? 0xFFFFFFFFu : (q > floor_c ? q : floor_c);
   }
 }
@@ -1008,50 +1457,70 @@ static int vocab_E(int V, int ctas = kVocabCluster, int threads = kVocabThreads)
   return e < 4 ? 4 : e;
 }
 
+// FULL: the vocabulary fills the step cluster's symbols exactly.
 template <int E>
-static cudaError_t vocab_t(const Dims& D, const Batch& b, const VocabIO& io, cudaStream_t s) {
-  const size_t smem = (size_t)kStepThreads * E * sizeof(float);
-  return launch_kernel_cluster(k_vocab<E>, dim3(b.Bmax * kStepCluster), dim3(kStepThreads), smem, s, D.pdl,
-                               kStepCluster, D, b, io);
+static bool step_full(int V) {
+  return V == kStepCluster * kStepThreads * E;
 }
 
 template <int E>
-static cudaError_t prepare_vocab_t() {
-  cudaError_t e = cudaFuncSetAttribute(k_vocab<E>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+static cudaError_t vocab_t(const Dims& D, const Batch& b, const VocabIO& io, cudaStream_t s) {
+  const size_t smem = (size_t)kStepThreads * E * sizeof(float);
+  return launch_kernel_cluster(step_full<E>(D.V) ? &k_vocab<E, true> : &k_vocab<E, false>, dim3(b.Bmax * kStepCluster),
+                               dim3(kStepThreads), smem, s, D.pdl, kStepCluster, D, b, io);
+}
+
+template <int E, bool FULL>
+static cudaError_t prepare_vocab_tf() {
+  cudaError_t e = cudaFuncSetAttribute(k_vocab<E, FULL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        kStepThreads * E * (int)sizeof(float));
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_vocab_seq<E>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    e = cudaFuncSetAttribute(k_vocab_seq<E, FULL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              kStepThreads * E * (int)sizeof(float));
   return e;
+}
+template <int E>
+static cudaError_t prepare_vocab_t(int V) {
+  return step_full<E>(V) ? prepare_vocab_tf<E, true>() : prepare_vocab_tf<E, false>();
 }
 
 cudaError_t prepare_vocab_kernels(const Dims& D) {
   switch (vocab_E(D.V, kStepCluster, kStepThreads)) {
-    case 4: return prepare_vocab_t<4>();
-    case 8: return prepare_vocab_t<8>();
-    case 12: return prepare_vocab_t<12>();
-    case 16: return prepare_vocab_t<16>();
+    case 4: return prepare_vocab_t<4>(D.V);
+    case 8: return prepare_vocab_t<8>(D.V);
+    case 12: return prepare_vocab_t<12>(D.V);
+    case 16: return prepare_vocab_t<16>(D.V);
   }
   return cudaErrorInvalidValue;
 }
 
 template <int E>
 static cudaError_t vocab_seq_t(const Dims& D, const Batch& b, const VocabIO& io, int m, const float* zrows,
-                               const int32_t* nb_step, const int32_t* obs_step, cudaStream_t s) {
+                               const int32_t* nb_step, const int32_t* obs_step, const NgSnap* snap,
+                               cudaStream_t s) {
   const size_t smem = (size_t)kStepThreads * E * sizeof(float);
-  return launch_kernel_cluster(k_vocab_seq<E>, dim3(b.Bmax * kStepCluster), dim3(kStepThreads), smem, s, D.pdl,
-                               kStepCluster, D, b, io, m, b.Bmax, zrows, nb_step, obs_step);
+  return launch_kernel_cluster(step_full<E>(D.V) ? &k_vocab_seq<E, true> : &k_vocab_seq<E, false>,
+                               dim3(b.Bmax * kStepCluster), dim3(kStepThreads), smem, s, D.pdl, kStepCluster, D, b,
+                               io, m, b.Bmax, zrows, nb_step, obs_step, snap);
 }
 
 cudaError_t launch_vocab_seq(const Dims& D, const Batch& b, const VocabIO& io, int m, const float* zrows,
-                             const int32_t* nb_step, const int32_t* obs_step, cudaStream_t s) {
+                             const int32_t* nb_step, const int32_t* obs_step, const NgSnap* snap, cudaStream_t s) {
+  if (D.order > 0 && !snap) return cudaErrorInvalidValue;
   switch (vocab_E(D.V, kStepCluster, kStepThreads)) {
-    case 4: return vocab_seq_t<4>(D, b, io, m, zrows, nb_step, obs_step, s);
-    case 8: return vocab_seq_t<8>(D, b, io, m, zrows, nb_step, obs_step, s);
-    case 12: return vocab_seq_t<12>(D, b, io, m, zrows, nb_step, obs_step, s);
-    case 16: return vocab_seq_t<16>(D, b, io, m, zrows, nb_step, obs_step, s);
+    case 4: return vocab_seq_t<4>(D, b, io, m, zrows, nb_step, obs_step, snap, s);
+    case 8: return vocab_seq_t<8>(D, b, io, m, zrows, nb_step, obs_step, snap, s);
+    case 12: return vocab_seq_t<12>(D, b, io, m, zrows, nb_step, obs_step, snap, s);
+    case 16: return vocab_seq_t<16>(D, b, io, m, zrows, nb_step, obs_step, snap, s);
   }
   return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_ngram_seq(const Dims& D, const Batch& b, int m, const int32_t* nb_step, const int32_t* obs_step,
+                             NgSnap* snap, cudaStream_t s) {
+  if (D.order <= 0 || b.Bmax < 1) return cudaSuccess;
+  return launch_kernel(k_ngram_seq, dim3(b.Bmax), dim3(128), 0, s, false, D, b, m, b.Bmax, nb_step, obs_step,
+                       b.z_idx, snap);
 }
 
 cudaError_t launch_vocab(const Dims& D, const Batch& b, const VocabIO& io, cudaStream_t s) {
