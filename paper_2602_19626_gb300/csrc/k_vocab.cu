@@ -334,11 +334,26 @@ struct StepSlot {
   float4 obs;              // the observed token's owner: p_tilde(t), p_ng(t), log p_tilde(t)
 };
 
+// What warp 0 of each CTA reduces from the cluster's partials after a
+// barrier, for every warp of its CTA (read after a CTA barrier): only one
+// warp per CTA reads the other CTAs' shared memory.
+struct StepComb {
+  float M, S, H;           // softmax: maximum, normaliser, second sum
+  int argmax, bad;         // quantiser: first maximum, any bad partial
+  uint32_t cbase;          // counts of the cluster's CTAs before this one
+  long long resid;         // T - sum of the floored counts
+  float4 obs;              // the observed token's values of the position being finished
+};
+
 constexpr int kSnapBufs = 3;   // N-gram states in flight in the prefill loop
 struct StepShared {
   StepSlot slot[2];
+  StepComb comb;
   NgSnap ng[kSnapBufs];
 };
+
+// All warps of the CTA (named barrier 1; __syncthreads keeps barrier 0).
+__device__ __forceinline__ void bar_cta() { asm volatile("bar.sync 1, %0;" ::"r"(kStepThreads) : "memory"); }
 
 // This thread's place in the cluster's split of the vocabulary.
 struct Lanes {
@@ -585,14 +600,26 @@ struct Quant {
   int argmax;
   bool bad;
 };
-__device__ __forceinline__ Quant quant_reduce(const uint4 (&v)[4], const Lanes& L, uint32_t T) {
-  uint32_t tot = 0, off = 0;
+// Warp 0: the cluster's softmax into cb.
+__device__ __forceinline__ void gather_soft(const float4 (&v)[4], int lane, StepComb& cb) {
+  const Soft sm = softmax_reduce(v);
+  if (lane == 0) {
+    cb.M = sm.M;
+    cb.S = sm.S;
+    cb.H = sm.H;
+  }
+}
+
+// Warp 0: the cluster's quantiser sums into cb (the count total, the counts
+// of the CTAs before this one, the first maximum, any bad partial).
+__device__ __forceinline__ void gather_quant(const uint4 (&v)[4], int lane, int rank, uint32_t T, StepComb& cb) {
+  uint32_t tot = 0, before = 0;
   unsigned long long key = 0;
   bool bad = false;
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
     tot += v[i].x;
-    if (4 * L.lane + i < L.gw) off += v[i].x;
+    if (4 * lane + i < rank * kStepWarps) before += v[i].x;
     const unsigned long long k = ((unsigned long long)v[i].y << 32) | (uint32_t)~v[i].z;
     key = k > key ? k : key;
     bad |= v[i].w != 0u;
@@ -600,15 +627,33 @@ __device__ __forceinline__ Quant quant_reduce(const uint4 (&v)[4], const Lanes& 
 #pragma unroll
   for (int o = 16; o; o >>= 1) {
     tot += __shfl_xor_sync(0xffffffffu, tot, o);
-    off += __shfl_xor_sync(0xffffffffu, off, o);
+    before += __shfl_xor_sync(0xffffffffu, before, o);
     const unsigned long long k2 = __shfl_xor_sync(0xffffffffu, key, o);
     key = k2 > key ? k2 : key;
   }
+  bad = __any_sync(0xffffffffu, bad);
+  if (lane == 0) {
+    cb.resid = (long long)T - (long long)tot;
+    cb.cbase = before;
+    cb.argmax = (int)~(uint32_t)key;
+    cb.bad = bad;
+  }
+}
+
+// A warp's quantiser results from cb; off: also the counts of the warps
+// before it (its CTA's earlier warps from the local slot).
+__device__ __forceinline__ Quant quant_of(const StepComb& cb, const StepSlot& slot, const Lanes& L, bool off) {
   Quant q;
-  q.resid = (long long)T - (long long)tot;
-  q.woff = (long long)off;
-  q.argmax = (int)~(uint32_t)key;
-  q.bad = __any_sync(0xffffffffu, bad);
+  q.resid = cb.resid;
+  q.argmax = cb.argmax;
+  q.bad = cb.bad != 0;
+  q.woff = cb.cbase;
+  if (off) {
+    uint32_t x = L.lane < L.w ? slot.qn[L.lane].x : 0u;
+#pragma unroll
+    for (int o = 16; o; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    q.woff += x;
+  }
   return q;
 }
 
@@ -779,9 +824,13 @@ __global__ void __launch_bounds__(kStepThreads, 1) k_vocab(Dims D, Batch b, Voca
   const float4 part = softmax_part<E>(s, e, D.skip ? entropy_part<E>(png) : 0.f);
   if (L.lane == 0) sh.slot[0].sm[L.w] = part;
   cl.sync();
-  float4 smv[4];
-  read_parts(cl, sh.slot[0].sm, L.lane, smv);
-  const Soft sm = softmax_reduce(smv);
+  if (L.w == 0) {
+    float4 smv[4];
+    read_parts(cl, sh.slot[0].sm, L.lane, smv);
+    gather_soft(smv, L.lane, sh.comb);
+  }
+  bar_cta();
+  const Soft sm{sh.comb.M, sh.comb.S, sh.comb.H};
   const bool skipped = D.skip && sm.H < kSkipBits;
   float pt[E];
   probs_tilde<E>(e, part.x, sm, pt);
@@ -797,8 +846,8 @@ __global__ void __launch_bounds__(kStepThreads, 1) k_vocab(Dims D, Batch b, Voca
   const uint32_t T = 1u << D.log2T, K = T - (uint32_t)V * D.floor;
   uint32_t c[E], excl = 0, am_c = 0, below_t = 0, c_t = 0;
   int am_i = 0x7fffffff;
+  const bool scan = io.cdf || (t >= L.wbase && t < L.wbase + 32 * E);
   if (io.predict) {
-    const bool scan = io.cdf || (t >= L.wbase && t < L.wbase + 32 * E);
     const uint4 qp = quant_part<E, FULL>(p, L, V, K, (float)K, D.floor, scan, c, excl, am_i, am_c);
     if (L.lane == 0) sh.slot[1].qn[L.w] = qp;
     if (owner) {
@@ -808,9 +857,13 @@ __global__ void __launch_bounds__(kStepThreads, 1) k_vocab(Dims D, Batch b, Voca
   }
   cl.sync();
   if (io.predict) {
-    uint4 qnv[4];
-    read_parts(cl, sh.slot[1].qn, L.lane, qnv);
-    const Quant q = quant_reduce(qnv, L, T);
+    if (L.w == 0) {
+      uint4 qnv[4];
+      read_parts(cl, sh.slot[1].qn, L.lane, qnv);
+      gather_quant(qnv, L.lane, L.rank, T, sh.comb);
+    }
+    bar_cta();
+    const Quant q = quant_of(sh.comb, sh.slot[1], L, scan);
     if (io.intervals && owner)
       write_interval(io.intervals + 2 * ((size_t)j * io.interval_stride + (i_tok - 1)), q, t, below_t, c_t);
     if (io.cdf) {
@@ -910,7 +963,7 @@ __global__ void __launch_bounds__(kStepThreads, 1)
   __syncthreads();                               // the first N-gram states are in shared memory
 
   // the previous position's values its quantiser and mixer step need
-  bool pend = false, p_skip = false, p_mix = false, p_own = false;
+  bool pend = false, p_skip = false, p_mix = false, p_own = false, p_own_w = false;
   int p_t = 0, p_pos = 0, p_am_i = 0x7fffffff;
   uint32_t p_below = 0, p_ct = 0, p_am_c = 0;
   float2 p_w = make_float2(0.f, 0.f);
@@ -918,10 +971,11 @@ __global__ void __launch_bounds__(kStepThreads, 1)
   int nb = 0;                                    // cluster barriers taken
   int r = 0, t_last = -1;
 
-  // interval, numeric checks and mixer step of the pending position from the
-  // quantiser partials qv and the observed values o (read from its slot)
-  auto finish = [&](const uint4 (&qv)[4], float4 o, const float (&pt)[E], bool with_head) {
-    const Quant q = quant_reduce(qv, L, T);
+  // interval, numeric checks and mixer step of the pending position from
+  // warp 0's sums in sh.comb and the partials of the local `slot`
+  auto finish = [&](const StepSlot& slot, const float (&pt)[E], bool with_head) {
+    const Quant q = quant_of(sh.comb, slot, L, p_own_w);
+    const float4 o = sh.comb.obs;
     if (p_own)
       write_interval(io.intervals + 2 * ((size_t)j * io.interval_stride + p_pos), q, p_t, p_below, p_ct);
     if ((q.bad && L.rank == 0 && threadIdx.x == 0) || final_count_bad(q, p_am_i, p_am_c, D.floor, T))
@@ -977,20 +1031,26 @@ __global__ void __launch_bounds__(kStepThreads, 1)
     }
     cluster_wait();
     ++nb;
-    float4 smv[4];
-    read_parts(cl, in.sm, L.lane, smv);
+    if (L.w == 0) {                              // position r's softmax, r - 1's quantiser and mixer values
+      float4 smv[4];
+      uint4 qv[4];
+      read_parts(cl, in.sm, L.lane, smv);
+      if (pend) read_parts(cl, in.qn, L.lane, qv);
+      float4 o = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (pend && !p_skip && L.lane == 0) o = cl.map_shared_rank(&in, p_t / (kStepThreads * E))->obs;
+      gather_soft(smv, L.lane, sh.comb);
+      if (pend) gather_quant(qv, L.lane, L.rank, T, sh.comb);
+      if (L.lane == 0) sh.comb.obs = o;
+    }
+    bar_cta();
+    const Soft sm{sh.comb.M, sh.comb.S, sh.comb.H};
     float pt[E];
     if (pend) {                                  // position r - 1 (log-loss mixer: no head step here)
-      uint4 qv[4];
-      read_parts(cl, in.qn, L.lane, qv);
-      const float4 o = p_skip ? make_float4(0.f, 0.f, 0.f, 0.f)
-                              : cl.map_shared_rank(&in, p_t / (kStepThreads * E))->obs;
-      finish(qv, o, pt, false);
+      finish(in, pt, false);
       pend = false;
     }
 
     // ---- position r: probabilities, counts, head step
-    const Soft sm = softmax_reduce(smv);
     const bool skipped = D.skip && sm.H < kSkipBits;
     probs_tilde<E>(e, part.x, sm, pt);
     const bool mixing = ngram && n0 + r + 1 > D.warmup;
@@ -1004,6 +1064,7 @@ __global__ void __launch_bounds__(kStepThreads, 1)
     const uint4 qp = quant_part<E, FULL>(p, L, V, K, Kf, D.floor, scan, c, excl, p_am_i, p_am_c);
     if (L.lane == 0) nx.qn[L.w] = qp;
     p_own = owner && io.intervals;
+    p_own_w = scan;
     if (owner) {
       counts_around<E>(c, L.v0, t, p_below, p_ct);
       p_below += excl;
@@ -1025,10 +1086,16 @@ __global__ void __launch_bounds__(kStepThreads, 1)
     } else {
       cl.sync();
       ++nb;
-      uint4 qv[4];
-      read_parts(cl, nx.qn, L.lane, qv);
-      const float4 o = skipped ? make_float4(0.f, 0.f, 0.f, 0.f) : cl.map_shared_rank(&nx, t / (kStepThreads * E))->obs;
-      finish(qv, o, pt, true);
+      if (L.w == 0) {
+        uint4 qv[4];
+        read_parts(cl, nx.qn, L.lane, qv);
+        float4 o = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (!skipped && L.lane == 0) o = cl.map_shared_rank(&nx, t / (kStepThreads * E))->obs;
+        gather_quant(qv, L.lane, L.rank, T, sh.comb);
+        if (L.lane == 0) sh.comb.obs = o;
+      }
+      bar_cta();
+      finish(nx, pt, true);
     }
     ++r;
     t = t_n;
@@ -1039,11 +1106,17 @@ __global__ void __launch_bounds__(kStepThreads, 1)
     cl.sync();
     ++nb;
     StepSlot& in = sh.slot[(nb - 1) & 1];
-    uint4 qv[4];
-    read_parts(cl, in.qn, L.lane, qv);
-    const float4 o = p_skip ? make_float4(0.f, 0.f, 0.f, 0.f) : cl.map_shared_rank(&in, p_t / (kStepThreads * E))->obs;
+    if (L.w == 0) {
+      uint4 qv[4];
+      read_parts(cl, in.qn, L.lane, qv);
+      float4 o = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (!p_skip && L.lane == 0) o = cl.map_shared_rank(&in, p_t / (kStepThreads * E))->obs;
+      gather_quant(qv, L.lane, L.rank, T, sh.comb);
+      if (L.lane == 0) sh.comb.obs = o;
+    }
+    bar_cta();
     float none[E];
-    finish(qv, o, none, false);
+    finish(in, none, false);
   }
   if (ngram) cp_async_wait_all();                // no copy outlives the kernel
   cl.sync();   // every CTA is done with the others' shared memory
