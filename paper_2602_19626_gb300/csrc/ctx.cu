@@ -80,13 +80,18 @@ struct nc_ctx {
   int32_t* f_pos = nullptr;
   int32_t* f_tok = nullptr;
   int32_t* d_nB_fwd = nullptr;       // forward rows
-  int32_t* d_zidx = nullptr;         // [max_streams] first forward row of each stream
-  int32_t* f_obs = nullptr;          // [P] observed token of (position, stream)
-  int32_t* f_nb = nullptr;           // [P] active streams per position
-  float* zrows = nullptr;            // [P][V] logits of the forward rows
-  NgSnap* snap = nullptr;            // [P] N-gram state of each (stream, position) prediction
+  // what a chunk's forward hands to its vocabulary passes, in two sets: chunk
+  // c uses set c & 1 while the passes of chunk c - 1 still read the other
+  int32_t* d_zidx[2] = {};           // [max_streams] first forward row of each stream
+  int32_t* f_obs[2] = {};            // [P] observed token of (position, stream)
+  int32_t* f_nb[2] = {};             // [P] active streams per position
+  float* zrows[2] = {};              // [P][V] logits of the forward rows
+  NgSnap* snap[2] = {};              // [P] N-gram state of each (stream, position) prediction
+  int32_t* d_p0 = nullptr;           // [3] first position of each set's chunk; [2] the next chunk's
   cudaStream_t side = nullptr;       // the N-gram pass of a chunk runs here beside its forward
-  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  cudaStream_t vstream = nullptr;    // the vocabulary passes, beside the next chunk's forward
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_done = nullptr;
+  cudaEvent_t ev_fwd[2] = {}, ev_voc[2] = {};
   uint32_t* cdf = nullptr;
   int32_t* d_slots = nullptr;
   int32_t* d_nB = nullptr;
@@ -277,9 +282,11 @@ extern "C" void nc_ctx_destroy(nc_ctx* ctx) {
   cudaFreeHost(ctx->h_i32);
   cudaFreeHost(ctx->h_u32);
   cudaFreeHost(ctx->h_status);
-  if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
-  if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
+  for (cudaEvent_t e : {ctx->ev_fork, ctx->ev_join, ctx->ev_done, ctx->ev_fwd[0], ctx->ev_fwd[1], ctx->ev_voc[0],
+                        ctx->ev_voc[1]})
+    if (e) cudaEventDestroy(e);
   if (ctx->side) cudaStreamDestroy(ctx->side);
+  if (ctx->vstream) cudaStreamDestroy(ctx->vstream);
   if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
   delete ctx;
 }
@@ -551,15 +558,21 @@ extern "C" int nc_ctx_create(const nc_config* cfg, const void* weights, size_t n
   if (ctx->P > 0 &&
       (dalloc(ctx, &ctx->f_slots, (size_t)ctx->P * 4) || dalloc(ctx, &ctx->f_pos, (size_t)ctx->P * 4) ||
        dalloc(ctx, &ctx->f_tok, (size_t)ctx->P * 4) || dalloc(ctx, &ctx->d_nB_fwd, 16) ||
-       dalloc(ctx, &ctx->d_zidx, B * 4) || dalloc(ctx, &ctx->zrows, (size_t)ctx->P * D.V * 4) ||
-       dalloc(ctx, &ctx->f_obs, (size_t)ctx->P * 4) || dalloc(ctx, &ctx->f_nb, (size_t)ctx->P * 4)))
+       dalloc(ctx, &ctx->d_p0, 16)))
     return bail(NC_ENOMEM);
-  if (ctx->P > 0 && D.order > 0) {
-    if (dalloc(ctx, &ctx->snap, (size_t)ctx->P * sizeof(NgSnap))) return bail(NC_ENOMEM);
-    if (cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming) != cudaSuccess)
-      return bail(NC_ECUDA);
+  for (int k = 0; k < 2 && ctx->P > 0; ++k) {
+    if (dalloc(ctx, &ctx->d_zidx[k], B * 4) || dalloc(ctx, &ctx->zrows[k], (size_t)ctx->P * D.V * 4) ||
+        dalloc(ctx, &ctx->f_obs[k], (size_t)ctx->P * 4) || dalloc(ctx, &ctx->f_nb[k], (size_t)ctx->P * 4) ||
+        (D.order > 0 && dalloc(ctx, &ctx->snap[k], (size_t)ctx->P * sizeof(NgSnap))))
+      return bail(NC_ENOMEM);
+  }
+  if (ctx->P > 0) {
+    bool ok = cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking) == cudaSuccess &&
+              cudaStreamCreateWithFlags(&ctx->vstream, cudaStreamNonBlocking) == cudaSuccess;
+    for (cudaEvent_t* e : {&ctx->ev_fork, &ctx->ev_join, &ctx->ev_done, &ctx->ev_fwd[0], &ctx->ev_fwd[1],
+                           &ctx->ev_voc[0], &ctx->ev_voc[1]})
+      ok = ok && cudaEventCreateWithFlags(e, cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) return bail(NC_ECUDA);
   }
   if (dalloc(ctx, &ctx->x, RA * D.d * 4) || dalloc(ctx, &ctx->qkv, RA * D.qkv_rows * 4) ||
       dalloc(ctx, &ctx->attn_out, RA * D.hq * kHeadDim * 4) ||
@@ -1084,8 +1097,16 @@ static int encode_prefill(nc_ctx* ctx, int n, int m0, const int32_t* tok_dev, co
     for (auto& e : mk.ev) NC_TRY(cudaEventCreate(&e));
   }
   // One chunk of m positions of the first ne streams (the longest; every
-  // stream with positions left is among them).
-  auto one_chunk = [&](int m, int ne) -> cudaError_t {
+  // stream with positions left is among them), with buffer set `par`: the
+  // forward (its N-gram pass beside it) and, with_vocab, the vocabulary
+  // passes after it on the same stream.
+  auto vocab_batch = [&](int ne, int par) {
+    Batch br = make_batch(ctx);                   // every stream's m positions, in order
+    br.Bmax = ne;
+    br.z_idx = ctx->d_zidx[par];
+    return br;
+  };
+  auto one_chunk = [&](int m, int ne, int par, bool with_vocab) -> cudaError_t {
     Batch b = make_batch(ctx);                    // stream rows (slots only)
     b.Bmax = ne;
     Batch f = make_batch(ctx);                    // (stream, position) rows of the forward
@@ -1095,51 +1116,63 @@ static int encode_prefill(nc_ctx* ctx, int n, int m0, const int32_t* tok_dev, co
     f.Bmax = ne * m;
     f.pos = ctx->f_pos;
     f.tok = ctx->f_tok;
-    f.z_out = ctx->zrows;
+    f.z_out = ctx->zrows[par];
     f.pm = m;
+    int32_t* p0 = ctx->d_p0 + par;
     cudaError_t e = mk.begin(s);
+    if (e == cudaSuccess) e = launch_chunk_start(ctx->d_p0, par, m, s);
     if (e == cudaSuccess)
-      e = launch_prepare_prefill(b, ne, m, D.V, tok_dev, offs_dev, lens_dev, ctx->f_slots, ctx->f_pos, ctx->f_tok,
-                                 ctx->d_nB_fwd, ctx->f_obs, ctx->f_nb, ctx->d_zidx, s);
+      e = launch_prepare_prefill(b, ne, m, D.V, p0, tok_dev, offs_dev, lens_dev, ctx->f_slots, ctx->f_pos,
+                                 ctx->f_tok, ctx->d_nB_fwd, ctx->f_obs[par], ctx->f_nb[par], ctx->d_zidx[par], s);
     if (e == cudaSuccess) e = mk.mark(s, TK_PREPARE);
-    Batch br = b;                                   // every stream's m positions, in order
-    br.z_idx = ctx->d_zidx;
+    const Batch br = vocab_batch(ne, par);
     // the N-gram pass needs only the tokens: beside the forward on the side
     // stream (in order on the main stream when each kernel is timed)
-    const bool side = ctx->snap && !mk.on;
+    const bool ng = ctx->snap[par] != nullptr;
+    const bool side = ng && !mk.on;
     if (side && e == cudaSuccess) e = cudaEventRecord(ctx->ev_fork, s);
     if (side && e == cudaSuccess) e = cudaStreamWaitEvent(ctx->side, ctx->ev_fork, 0);
-    if (side && e == cudaSuccess) e = launch_ngram_seq(D, br, m, ctx->f_nb, ctx->f_obs, ctx->snap, ctx->side);
+    if (side && e == cudaSuccess)
+      e = launch_ngram_seq(D, br, m, ctx->f_nb[par], ctx->f_obs[par], p0, ctx->snap[par], ctx->side);
     if (side && e == cudaSuccess) e = cudaEventRecord(ctx->ev_join, ctx->side);
     if (e == cudaSuccess) e = launch_model(ctx, f, &mk);
-    if (ctx->snap && !side && e == cudaSuccess) {
-      e = launch_ngram_seq(D, br, m, ctx->f_nb, ctx->f_obs, ctx->snap, s);
+    if (ng && !side && e == cudaSuccess) {
+      e = launch_ngram_seq(D, br, m, ctx->f_nb[par], ctx->f_obs[par], p0, ctx->snap[par], s);
       if (e == cudaSuccess) e = mk.mark(s, TK_NGRAM);
     }
     if (side && e == cudaSuccess) e = cudaStreamWaitEvent(s, ctx->ev_join, 0);
-    if (e == cudaSuccess) e = launch_vocab_seq(D, br, io, m, ctx->zrows, ctx->f_nb, ctx->f_obs, ctx->snap, s);
-    if (e == cudaSuccess) e = mk.mark(s, TK_VOCAB);
+    if (with_vocab && e == cudaSuccess) {
+      e = launch_vocab_seq(D, br, io, m, ctx->zrows[par], ctx->f_nb[par], ctx->f_obs[par], ctx->snap[par], s);
+      if (e == cudaSuccess) e = mk.mark(s, TK_VOCAB);
+    }
     return e;
   };
-  // one captured graph per chunk length (captured on first use)
+  // one captured graph per chunk length and buffer set (captured on first use)
   std::map<int, cudaGraphExec_t> graphs;
-  auto graph_for = [&](int m, int ne) -> cudaGraphExec_t {
-    auto it = graphs.find(m);
+  auto graph_for = [&](int m, int ne, int par, bool with_vocab) -> cudaGraphExec_t {
+    const int key = 2 * m + par;
+    auto it = graphs.find(key);
     if (it != graphs.end()) return it->second;
     cudaGraph_t g = nullptr;
     cudaGraphExec_t ge = nullptr;
     if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
       mk.capturing = true;
-      cudaError_t e = one_chunk(m, ne);
+      cudaError_t e = one_chunk(m, ne, par, with_vocab);
       mk.capturing = false;
       cudaError_t e2 = cudaStreamEndCapture(s, &g);
       if (e != cudaSuccess || e2 != cudaSuccess || cudaGraphInstantiate(&ge, g, 0) != cudaSuccess) ge = nullptr;
       if (g) cudaGraphDestroy(g);
       cudaGetLastError();
     }
-    graphs[m] = ge;
+    graphs[key] = ge;
     return ge;
   };
+  // chunk c's vocabulary passes run on vstream after its forward, beside
+  // chunk c + 1's forward; chunk c + 2 reuses set c & 1 after they are done
+  // (timed runs keep every kernel in order on the main stream)
+  const bool piped = !mk.on;
+  cudaStream_t vs = piped ? ctx->vstream : s;
+  NC_TRY(cudaMemsetAsync(ctx->d_p0, 0, 16, s));
   if (trace) {
     std::memset(trace, 0, sizeof(*trace));
     trace->graphed = 1;
@@ -1149,7 +1182,8 @@ static int encode_prefill(nc_ctx* ctx, int n, int m0, const int32_t* tok_dev, co
   auto start_at = [&](int64_t a) -> int64_t { return a < D.L ? 0 : ((a - D.L) / D.C + 1) * D.C; };
   int st = NC_OK;
   int m = m0;
-  for (int64_t p = 0; p < max_len; p += m) {
+  int chunk = 0;
+  for (int64_t p = 0; p < max_len; p += m, ++chunk) {
     // the largest chunk for the streams still coding, aligned to it (so it
     // never crosses a slide): it only grows as streams end
     int live = 0;
@@ -1157,9 +1191,23 @@ static int encode_prefill(nc_ctx* ctx, int n, int m0, const int32_t* tok_dev, co
     m = m_max;
     while (m > m0 && ((int64_t)live * m > ctx->P || p % m != 0)) m /= 2;
     const int ne = std::min(n, ctx->P / m);
-    cudaGraphExec_t ge = graph_for(m, ne);
+    const int par = chunk & 1;
+    cudaError_t e = cudaSuccess;
+    if (piped && chunk >= 2) e = cudaStreamWaitEvent(s, ctx->ev_voc[par], 0);
+    cudaGraphExec_t ge = e == cudaSuccess ? graph_for(m, ne, par, !piped) : nullptr;
     if (trace && !ge) trace->graphed = 0;
-    cudaError_t e = ge ? cudaGraphLaunch(ge, s) : one_chunk(m, ne);
+    if (e == cudaSuccess) e = ge ? cudaGraphLaunch(ge, s) : one_chunk(m, ne, par, !piped);
+    if (piped) {
+      if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_fwd[par], s);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(vs, ctx->ev_fwd[par], 0);
+      // without PDL: it would sit on 8 SMs while the previous passes run
+      Dims Dv = D;
+      Dv.pdl = 0;
+      if (e == cudaSuccess)
+        e = launch_vocab_seq(Dv, vocab_batch(ne, par), io, m, ctx->zrows[par], ctx->f_nb[par], ctx->f_obs[par],
+                             ctx->snap[par], vs);
+      if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_voc[par], vs);
+    }
     if (e != cudaSuccess) {
       st = fail_cuda(ctx, e, "prefill encode chunk");
       break;
@@ -1207,6 +1255,11 @@ static int encode_prefill(nc_ctx* ctx, int n, int m0, const int32_t* tok_dev, co
         trace->flops[kd] += fo;
       }
     }
+  }
+  if (piped) {                                    // the caller's stream sees the last passes
+    cudaError_t e = cudaEventRecord(ctx->ev_done, vs);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ctx->ev_done, 0);
+    if (e != cudaSuccess && st == NC_OK) st = fail_cuda(ctx, e, "prefill encode join");
   }
   for (auto& kv : graphs)
     if (kv.second) cudaGraphExecDestroy(kv.second);

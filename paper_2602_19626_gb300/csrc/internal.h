@@ -221,20 +221,23 @@ cudaError_t launch_vocab_seq(const Dims& D, const Batch& b, const VocabIO& io, i
 // token (tables, context entries, history, unigram total N).  Leaves the
 // unigram counts, the position and the window to the vocabulary passes.
 cudaError_t launch_ngram_seq(const Dims& D, const Batch& b, int m, const int32_t* nb_step, const int32_t* obs_step,
-                             NgSnap* snap, cudaStream_t s);
+                             const int32_t* p0, NgSnap* snap, cudaStream_t s);
 cudaError_t launch_prepare_encode(const Batch& b, int n_streams, const int32_t* tok_flat,
                                   const int64_t* offs, const int64_t* lens, int32_t* obs,
                                   int32_t* nB, cudaStream_t s);
-// Encoder prefill of positions p0 .. p0 + m - 1 (p0 = n_coded of row 0, the
-// longest stream) for n_streams rows: forward row i = j m + r gets the slot of
+// The first position of the next prefill chunk, from a device counter:
+// p0s[par] = p0s[2]; p0s[2] += m (so captured chunks replay in order).
+cudaError_t launch_chunk_start(int32_t* p0s, int par, int m, cudaStream_t s);
+// Encoder prefill of positions p0 .. p0 + m - 1 (p0 = *p0, every live
+// stream's position) for n_streams rows: forward row i = j m + r gets the slot of
 // stream row j, position p0 + r (or -1 past the stream's end) and its input
 // token; *nB_fwd = m x (streams with tokens left).  For the sequential pass
 // of position p0 + r: nb_step[r] active rows, observed tokens
 // obs_step[r n + j], logits at forward row z_idx[j] + r (z_idx[j] = j m).
-cudaError_t launch_prepare_prefill(const Batch& b, int n_streams, int m, int V, const int32_t* tok_flat,
-                                   const int64_t* offs, const int64_t* lens, int32_t* f_slots, int32_t* f_pos,
-                                   int32_t* f_tok, int32_t* nB_fwd, int32_t* obs_step, int32_t* nb_step,
-                                   int32_t* z_idx, cudaStream_t s);
+cudaError_t launch_prepare_prefill(const Batch& b, int n_streams, int m, int V, const int32_t* p0,
+                                   const int32_t* tok_flat, const int64_t* offs, const int64_t* lens,
+                                   int32_t* f_slots, int32_t* f_pos, int32_t* f_tok, int32_t* nB_fwd,
+                                   int32_t* obs_step, int32_t* nb_step, int32_t* z_idx, cudaStream_t s);
 // Attention over a BF16 KV cache on the tensor cores (k_attn_tc.cu): rq
 // query rows per CTA group (1: a decode step), S CTAs per group.
 cudaError_t prepare_attn_tc(const Dims& D);

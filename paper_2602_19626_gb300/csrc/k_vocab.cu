@@ -1334,11 +1334,12 @@ __device__ void ngram_update_row(const Dims& D, const Batch& b, int j, int warp,
 // unigram counts and the position stay with the vocabulary passes).  It needs
 // only the tokens, so it runs beside the chunk's forward pass.
 __global__ void __launch_bounds__(128) k_ngram_seq(Dims D, Batch b, int m, int n_streams, const int32_t* nb_step,
-                                                   const int32_t* obs_step, const int32_t* z_idx, NgSnap* snap) {
+                                                   const int32_t* obs_step, const int32_t* z_idx, const int32_t* p0_at,
+                                                   NgSnap* snap) {
   const int j = blockIdx.x;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   StreamDev& st = b.st[b.slots[j]];
-  int n_coded = st.n_coded;
+  int n_coded = *p0_at;                            // every live stream is at the chunk's first position
   NgSnap* out = snap + z_idx[j];
   for (int r = 0; r < m; ++r) {
     if (j >= nb_step[r]) break;
@@ -1384,17 +1385,29 @@ __global__ void k_prepare_encode(Batch b, int n_streams, const int32_t* tok_flat
   }
 }
 
-// Encoder prefill of positions p0 .. p0 + m - 1 (p0 = n_coded of row 0;
-// rows sorted longest first, so the streams with tokens left are a prefix).
+// The next prefill chunk's first position: p0s[par] = p0s[2], p0s[2] += m.
+__global__ void k_chunk_start(int32_t* p0s, int par, int m) {
+  pdl_wait();
+  pdl_trigger();
+  if (threadIdx.x == 0) {
+    const int p0 = p0s[2];
+    p0s[par] = p0;
+    p0s[2] = p0 + m;
+  }
+}
+
+// Encoder prefill of positions p0 .. p0 + m - 1 (p0 = *p0_at; rows sorted
+// longest first, so the streams with tokens left are a prefix).
 // Forward row i = j m + r: slot, position (-1 past the stream's end) and
 // input token.  Sequential pass r: active rows nb_step[r], observed tokens
 // obs_step[r n + j]; row j's logits sit at forward row z_idx[j] + r.
-__global__ void k_prepare_prefill(Batch b, int n_streams, int m, int V, const int32_t* tok_flat, const int64_t* offs,
-                                  const int64_t* lens, int32_t* f_slots, int32_t* f_pos, int32_t* f_tok,
-                                  int32_t* nB_fwd, int32_t* obs_step, int32_t* nb_step, int32_t* z_idx) {
+__global__ void k_prepare_prefill(Batch b, int n_streams, int m, int V, const int32_t* p0_at, const int32_t* tok_flat,
+                                  const int64_t* offs, const int64_t* lens, int32_t* f_slots, int32_t* f_pos,
+                                  int32_t* f_tok, int32_t* nB_fwd, int32_t* obs_step, int32_t* nb_step,
+                                  int32_t* z_idx) {
   pdl_wait();
   pdl_trigger();
-  const int p0 = b.st[b.slots[0]].n_coded;
+  const int p0 = *p0_at;
   const int tid = threadIdx.x + blockIdx.x * blockDim.x, nthr = blockDim.x * gridDim.x;
   for (int i = tid; i < n_streams * m; i += nthr) {
     const int j = i / m, r = i % m;
@@ -1590,10 +1603,10 @@ cudaError_t launch_vocab_seq(const Dims& D, const Batch& b, const VocabIO& io, i
 }
 
 cudaError_t launch_ngram_seq(const Dims& D, const Batch& b, int m, const int32_t* nb_step, const int32_t* obs_step,
-                             NgSnap* snap, cudaStream_t s) {
+                             const int32_t* p0, NgSnap* snap, cudaStream_t s) {
   if (D.order <= 0 || b.Bmax < 1) return cudaSuccess;
   return launch_kernel(k_ngram_seq, dim3(b.Bmax), dim3(128), 0, s, false, D, b, m, b.Bmax, nb_step, obs_step,
-                       b.z_idx, snap);
+                       b.z_idx, p0, snap);
 }
 
 cudaError_t launch_vocab(const Dims& D, const Batch& b, const VocabIO& io, cudaStream_t s) {
@@ -1614,14 +1627,18 @@ cudaError_t launch_prepare_encode(const Batch& b, int n_streams, const int32_t* 
                        obs, nB);
 }
 
-cudaError_t launch_prepare_prefill(const Batch& b, int n_streams, int m, int V, const int32_t* tok_flat,
-                                   const int64_t* offs, const int64_t* lens, int32_t* f_slots, int32_t* f_pos,
-                                   int32_t* f_tok, int32_t* nB_fwd, int32_t* obs_step, int32_t* nb_step,
-                                   int32_t* z_idx, cudaStream_t s) {
+cudaError_t launch_chunk_start(int32_t* p0s, int par, int m, cudaStream_t s) {
+  return launch_kernel(k_chunk_start, dim3(1), dim3(32), 0, s, true, p0s, par, m);
+}
+
+cudaError_t launch_prepare_prefill(const Batch& b, int n_streams, int m, int V, const int32_t* p0,
+                                   const int32_t* tok_flat, const int64_t* offs, const int64_t* lens,
+                                   int32_t* f_slots, int32_t* f_pos, int32_t* f_tok, int32_t* nB_fwd,
+                                   int32_t* obs_step, int32_t* nb_step, int32_t* z_idx, cudaStream_t s) {
   const int rows = n_streams * m;
   const int blocks = std::min((rows + 255) / 256, 64);
-  return launch_kernel(k_prepare_prefill, dim3(blocks), dim3(256), 0, s, true, b, n_streams, m, V, tok_flat, offs,
-                       lens, f_slots, f_pos, f_tok, nB_fwd, obs_step, nb_step, z_idx);
+  return launch_kernel(k_prepare_prefill, dim3(blocks), dim3(256), 0, s, true, b, n_streams, m, V, p0, tok_flat,
+                       offs, lens, f_slots, f_pos, f_tok, nB_fwd, obs_step, nb_step, z_idx);
 }
 
 template <int E>
