@@ -467,7 +467,9 @@ extern "C" int nc_ctx_create(const nc_config* cfg, const void* weights, size_t n
   D.kv_bf16 = c.weight_fmt != NC_FP32;
   {
     // Attention CTAs per (stream, KV head) are picked per launch from its
-    // rows (results do not depend on them); NC24_ATTN_CLUSTER=1|2|4|8 fixes them.
+    // rows (results do not depend on them); NC24_ATTN_CLUSTER=1|2|4|8 fixes
+    // them and keeps prefill rows on the decode kernel (else groups of 32
+    // prefill positions take the row-tile kernel).
     int nsm = 0;
     if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c.device) != cudaSuccess || nsm <= 0)
       return bail(NC_ECUDA);

@@ -242,6 +242,11 @@ cudaError_t launch_prepare_prefill(const Batch& b, int n_streams, int m, int V, 
 // query rows per CTA group (1: a decode step), S CTAs per group.
 cudaError_t prepare_attn_tc(const Dims& D);
 size_t attn_tc_smem(int rq, int grp, int S);
+// Prefill rows (b.pos set) in groups of 32 positions, each warp walking one
+// 16-row tile through a chunk's blocks (same bits as launch_attn_tc).
+bool attn_pf_fits(const Dims& D, const Batch& b);
+cudaError_t launch_attn_pf(const Dims& D, const Batch& b, int layer, const float* qkv, float* attn_out,
+                           cudaStream_t s);
 cudaError_t launch_attn_tc(const Dims& D, const Batch& b, int layer, int rq, int S, const float* qkv,
                            float* attn_out, cudaStream_t s);
 // Prefill: rotate and append the k, v of every row to the KV ring of `layer`.

@@ -544,6 +544,7 @@ static cudaError_t launch_attn_rows(const Dims& D, const Batch& b, int layer, co
 // Tensor-core attention (BF16 cache): rows per CTA group and CTAs per group.
 static cudaError_t launch_attn_bf16(const Dims& D, const Batch& b, int layer, const float* qkv, float* attn_out,
                                     cudaStream_t s) {
+  if (attn_pf_fits(D, b) && !D.attn_cluster) return launch_attn_pf(D, b, layer, qkv, attn_out, s);
   const int grp = D.hq / D.hkv;
   int rq = 1;
   if (b.pos && b.pm >= 2) {

@@ -348,20 +348,32 @@ struct AttnPre {
   float2 vf[KBF16 ? 1 : 32];
 };
 
-// cos / sin of position a for the 32 rotation pairs: the product of the
-// three table rotations (a split into 8-bit digits).
+// (cos, sin) of position a for rotation pair dd: the product of the three
+// table rotations (a split into 8-bit digits), with explicit roundings (no
+// multiply-add contraction), so every kernel that rotates a position gets the
+// same bits.
+__device__ __forceinline__ float2 rope_cs(const Dims& D, int a, int dd) {
+  const float2 t1 = D.rope_tab[(0 * 256 + (a & 255)) * 32 + dd];
+  const float2 t2 = D.rope_tab[(1 * 256 + ((a >> 8) & 255)) * 32 + dd];
+  const float2 t3 = D.rope_tab[(2 * 256 + ((a >> 16) & 255)) * 32 + dd];
+  const float c12 = __fsub_rn(__fmul_rn(t1.x, t2.x), __fmul_rn(t1.y, t2.y));
+  const float s12 = __fadd_rn(__fmul_rn(t1.x, t2.y), __fmul_rn(t1.y, t2.x));
+  return make_float2(__fsub_rn(__fmul_rn(c12, t3.x), __fmul_rn(s12, t3.y)),
+                     __fadd_rn(__fmul_rn(c12, t3.y), __fmul_rn(s12, t3.x)));
+}
+// The rotated pair (x1, x2) -> (x1 c - x2 s, x2 c + x1 s).
+__device__ __forceinline__ float2 rope_rotate(float x1, float x2, float2 cs) {
+  return make_float2(__fsub_rn(__fmul_rn(x1, cs.x), __fmul_rn(x2, cs.y)),
+                     __fadd_rn(__fmul_rn(x2, cs.x), __fmul_rn(x1, cs.y)));
+}
+
+// cos / sin of position a for the 32 rotation pairs.
 template <typename Sm>
 __device__ __forceinline__ void attn_rope(const Dims& D, int a, int tid, Sm& sm) {
   if (tid < kHeadDim / 2) {
-    const float2 t1 = D.rope_tab[(0 * 256 + (a & 255)) * 32 + tid];
-    const float2 t2 = D.rope_tab[(1 * 256 + ((a >> 8) & 255)) * 32 + tid];
-    const float2 t3 = D.rope_tab[(2 * 256 + ((a >> 16) & 255)) * 32 + tid];
-    // explicit roundings: no multiply-add contraction, so every kernel that
-    // rotates a position gets the same bits
-    const float c12 = __fsub_rn(__fmul_rn(t1.x, t2.x), __fmul_rn(t1.y, t2.y));
-    const float s12 = __fadd_rn(__fmul_rn(t1.x, t2.y), __fmul_rn(t1.y, t2.x));
-    sm.cs[tid] = __fsub_rn(__fmul_rn(c12, t3.x), __fmul_rn(s12, t3.y));
-    sm.sn[tid] = __fadd_rn(__fmul_rn(c12, t3.y), __fmul_rn(s12, t3.x));
+    const float2 cs = rope_cs(D, a, tid);
+    sm.cs[tid] = cs.x;
+    sm.sn[tid] = cs.y;
   }
 }
 
@@ -429,8 +441,8 @@ __device__ void attn_qkv(const Dims& D, StreamDev& st, int layer, int j, int g, 
     const int h = e / (kHeadDim / 2), dd = e % (kHeadDim / 2);
     const float* src = h < grp ? row + (g * grp + h) * kHeadDim : row + D.hq * kHeadDim + g * kHeadDim;
     const float x1 = __ldcg(src + dd), x2 = __ldcg(src + dd + kHeadDim / 2);
-    const float r1 = __fsub_rn(__fmul_rn(x1, sm.cs[dd]), __fmul_rn(x2, sm.sn[dd]));
-    const float r2 = __fadd_rn(__fmul_rn(x2, sm.cs[dd]), __fmul_rn(x1, sm.sn[dd]));
+    const float2 rr = rope_rotate(x1, x2, make_float2(sm.cs[dd], sm.sn[dd]));
+    const float r1 = rr.x, r2 = rr.y;
     if (h < grp) {   // the 1/sqrt(64) score scale is a power of two: exact
       sm.qs[h][dd] = r1 * 0.125f;
       sm.qs[h][dd + kHeadDim / 2] = r2 * 0.125f;

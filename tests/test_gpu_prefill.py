@@ -80,11 +80,12 @@ def test_prefill_container_decodes_per_position(nc):
         assert np.array_equal(a, b)
 
 
-@pytest.mark.parametrize("split", ["1", "2", "4", "8"])
+@pytest.mark.parametrize("split", ["0", "1", "2", "4", "8"])
 def test_prefill_attention_split(nc, monkeypatch, split):
     """Windows up to 2,048 positions (8 chunks) with a slide: the prefill's
-    multi-row attention with 1, 2, 4 or 8 CTAs per row group gives the
-    decode intervals exactly."""
+    attention gives the decode intervals exactly, both the row-tile kernel
+    (32 positions per cluster of 8 CTAs, split "0") and the decode kernel
+    over 8 rows with 1, 2, 4 or 8 CTAs per row group."""
     shape, seed = dataclasses.replace(S.SMALL, ctx_len=2048, slide=512), 8
     w = S.flat_weights(shape, seed)
     toks = [S.token_stream(seed, j, n, shape.vocab) for j, n in enumerate([2300, 700])]
