@@ -327,33 +327,22 @@ __device__ __forceinline__ void cluster_arrive() {
 }
 __device__ __forceinline__ void cluster_wait() { asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory"); }
 
-// What the CTAs publish before one cluster barrier (two slots alternate).
+// Every CTA's inbox for one cluster barrier (two alternate): each warp of
+// the cluster stores its partials at its global index rank kStepWarps + w in
+// every CTA's inbox before the barrier (posted remote stores, made visible by
+// the barrier's release), so after it every warp reduces them from its own
+// CTA's shared memory.
 struct StepSlot {
-  float4 sm[kStepWarps];   // softmax: warp maximum m_w, sum of exp(s - m_w), N-gram entropy part
-  uint4 qn[kStepWarps];    // quantiser: count sum, first maximum (value bits, index), bad flag
-  float4 obs;              // the observed token's owner: p_tilde(t), p_ng(t), log p_tilde(t)
-};
-
-// What warp 0 of each CTA reduces from the cluster's partials after a
-// barrier, for every warp of its CTA (read after a CTA barrier): only one
-// warp per CTA reads the other CTAs' shared memory.
-struct StepComb {
-  float M, S, H;           // softmax: maximum, normaliser, second sum
-  int argmax, bad;         // quantiser: first maximum, any bad partial
-  uint32_t cbase;          // counts of the cluster's CTAs before this one
-  long long resid;         // T - sum of the floored counts
-  float4 obs;              // the observed token's values of the position being finished
+  float4 sm[kStepCluster * kStepWarps];   // softmax: warp maximum m_w, sum of exp(s - m_w), entropy part
+  uint4 qn[kStepCluster * kStepWarps];    // quantiser: count sum, first maximum (value bits, index), bad flag
+  float4 obs;                             // the observed token's p_tilde(t), p_ng(t), log p_tilde(t)
 };
 
 constexpr int kSnapBufs = 3;   // N-gram states in flight in the prefill loop
 struct StepShared {
   StepSlot slot[2];
-  StepComb comb;
   NgSnap ng[kSnapBufs];
 };
-
-// All warps of the CTA (named barrier 1; __syncthreads keeps barrier 0).
-__device__ __forceinline__ void bar_cta() { asm volatile("bar.sync 1, %0;" ::"r"(kStepThreads) : "memory"); }
 
 // This thread's place in the cluster's split of the vocabulary.
 struct Lanes {
@@ -392,12 +381,22 @@ __device__ __forceinline__ void load_runf(const float* src, int v0, int V, float
   }
 }
 
-// The partials of global warps 4 lane .. 4 lane + 3 of the cluster.
+// Lanes 0 .. kStepCluster - 1 store the warp's (warp-uniform) partial v at
+// its global index in the inbox array `mine` of every CTA.
 template <typename T>
-__device__ __forceinline__ void read_parts(cg::cluster_group& cl, T* mine, int lane, T (&v)[4]) {
-  const T* src = cl.map_shared_rank(mine, lane >> 2) + 4 * (lane & 3);
+__device__ __forceinline__ void push_part(cg::cluster_group& cl, T* mine, const Lanes& L, T v) {
+  if (L.lane < kStepCluster) cl.map_shared_rank(mine, L.lane)[L.gw] = v;
+}
+// The observed token's values into every CTA's inbox.
+__device__ __forceinline__ void push_obs(cg::cluster_group& cl, float4* mine, float4 v) {
 #pragma unroll
-  for (int i = 0; i < 4; ++i) v[i] = src[i];
+  for (int r = 0; r < kStepCluster; ++r) *cl.map_shared_rank(mine, r) = v;
+}
+// The inbox entries of global warps 4 lane .. 4 lane + 3.
+template <typename T>
+__device__ __forceinline__ void local_parts(const T* arr, int lane, T (&v)[4]) {
+#pragma unroll
+  for (int i = 0; i < 4; ++i) v[i] = arr[4 * lane + i];
 }
 
 // p_ng of the thread's symbols (Sec. 3.4), the closed form
@@ -405,10 +404,10 @@ __device__ __forceinline__ void read_parts(cg::cluster_group& cl, T* mine, int l
 // in g.  Each warp adds the context slots' masses of its own 32 E symbols into
 // its region spw of shared memory (order by order, so a symbol's sum is taken
 // in the order k = 0, 1, 2); each lane then reads its E sums and zeroes them.
-template <int E, bool FULL>
-__device__ __forceinline__ void ngram_probs(const NgSnap& g, float* spw, const Lanes& L, int V, const int (&cnt)[E],
-                                            float (&png)[E]) {
+template <int E>
+__device__ __forceinline__ void ngram_scatter(const NgSnap& g, float* spw, const Lanes& L) {
   constexpr int kSpan = 32 * E;
+  __syncwarp();                                    // the region's last reads and zeroes are done
 #pragma unroll
   for (int k = 0; k < kMaxOrder; ++k) {
     const int ns = g.ns[k];
@@ -424,7 +423,11 @@ __device__ __forceinline__ void ngram_probs(const NgSnap& g, float* spw, const L
     }
     __syncwarp();
   }
-  const float cu = g.cu;
+}
+template <int E, bool FULL>
+__device__ __forceinline__ void ngram_read(float cu, float* spw, const Lanes& L, int V, const int (&cnt)[E],
+                                           float (&png)[E]) {
+  __syncwarp();                                    // every lane's slot masses are in
   float4* s4 = reinterpret_cast<float4*>(spw + L.lane * E);
 #pragma unroll
   for (int q = 0; q < E / 4; ++q) {
@@ -437,6 +440,12 @@ __device__ __forceinline__ void ngram_probs(const NgSnap& g, float* spw, const L
     }
     s4[q] = make_float4(0.f, 0.f, 0.f, 0.f);
   }
+}
+template <int E, bool FULL>
+__device__ __forceinline__ void ngram_probs(const NgSnap& g, float* spw, const Lanes& L, int V, const int (&cnt)[E],
+                                            float (&png)[E]) {
+  ngram_scatter<E>(g, spw, L);
+  ngram_read<E, FULL>(g.cu, spw, L, V, cnt, png);
 }
 
 template <int E>
@@ -600,26 +609,14 @@ struct Quant {
   int argmax;
   bool bad;
 };
-// Warp 0: the cluster's softmax into cb.
-__device__ __forceinline__ void gather_soft(const float4 (&v)[4], int lane, StepComb& cb) {
-  const Soft sm = softmax_reduce(v);
-  if (lane == 0) {
-    cb.M = sm.M;
-    cb.S = sm.S;
-    cb.H = sm.H;
-  }
-}
-
-// Warp 0: the cluster's quantiser sums into cb (the count total, the counts
-// of the CTAs before this one, the first maximum, any bad partial).
-__device__ __forceinline__ void gather_quant(const uint4 (&v)[4], int lane, int rank, uint32_t T, StepComb& cb) {
-  uint32_t tot = 0, before = 0;
+__device__ __forceinline__ Quant quant_reduce(const uint4 (&v)[4], const Lanes& L, uint32_t T) {
+  uint32_t tot = 0, off = 0;
   unsigned long long key = 0;
   bool bad = false;
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
     tot += v[i].x;
-    if (4 * lane + i < rank * kStepWarps) before += v[i].x;
+    if (4 * L.lane + i < L.gw) off += v[i].x;
     const unsigned long long k = ((unsigned long long)v[i].y << 32) | (uint32_t)~v[i].z;
     key = k > key ? k : key;
     bad |= v[i].w != 0u;
@@ -627,33 +624,15 @@ __device__ __forceinline__ void gather_quant(const uint4 (&v)[4], int lane, int 
 #pragma unroll
   for (int o = 16; o; o >>= 1) {
     tot += __shfl_xor_sync(0xffffffffu, tot, o);
-    before += __shfl_xor_sync(0xffffffffu, before, o);
+    off += __shfl_xor_sync(0xffffffffu, off, o);
     const unsigned long long k2 = __shfl_xor_sync(0xffffffffu, key, o);
     key = k2 > key ? k2 : key;
   }
-  bad = __any_sync(0xffffffffu, bad);
-  if (lane == 0) {
-    cb.resid = (long long)T - (long long)tot;
-    cb.cbase = before;
-    cb.argmax = (int)~(uint32_t)key;
-    cb.bad = bad;
-  }
-}
-
-// A warp's quantiser results from cb; off: also the counts of the warps
-// before it (its CTA's earlier warps from the local slot).
-__device__ __forceinline__ Quant quant_of(const StepComb& cb, const StepSlot& slot, const Lanes& L, bool off) {
   Quant q;
-  q.resid = cb.resid;
-  q.argmax = cb.argmax;
-  q.bad = cb.bad != 0;
-  q.woff = cb.cbase;
-  if (off) {
-    uint32_t x = L.lane < L.w ? slot.qn[L.lane].x : 0u;
-#pragma unroll
-    for (int o = 16; o; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-    q.woff += x;
-  }
+  q.resid = (long long)T - (long long)tot;
+  q.woff = (long long)off;
+  q.argmax = (int)~(uint32_t)key;
+  q.bad = __any_sync(0xffffffffu, bad);
   return q;
 }
 
@@ -822,15 +801,11 @@ __global__ void __launch_bounds__(kStepThreads, 1) k_vocab(Dims D, Batch b, Voca
     png_t = pick<E>(png, L.v0, t);
   }
   const float4 part = softmax_part<E>(s, e, D.skip ? entropy_part<E>(png) : 0.f);
-  if (L.lane == 0) sh.slot[0].sm[L.w] = part;
+  push_part(cl, sh.slot[0].sm, L, part);
   cl.sync();
-  if (L.w == 0) {
-    float4 smv[4];
-    read_parts(cl, sh.slot[0].sm, L.lane, smv);
-    gather_soft(smv, L.lane, sh.comb);
-  }
-  bar_cta();
-  const Soft sm{sh.comb.M, sh.comb.S, sh.comb.H};
+  float4 smv[4];
+  local_parts(sh.slot[0].sm, L.lane, smv);
+  const Soft sm = softmax_reduce(smv);
   const bool skipped = D.skip && sm.H < kSkipBits;
   float pt[E];
   probs_tilde<E>(e, part.x, sm, pt);
@@ -842,14 +817,16 @@ __global__ void __launch_bounds__(kStepThreads, 1) k_vocab(Dims D, Batch b, Voca
   float p[E];
   coded_probs<E>(pt, png, w, skipped, mixing, p);
   if (io.probe_p) store_run<E>(io.probe_p + (size_t)j * V, L.v0, V, p);
-  if (owner) sh.slot[1].obs = make_float4(pick<E>(pt, L.v0, t), png_t, __fsub_rn(__fsub_rn(s_t, sm.M), __logf(sm.S)), 0.f);
+  if (owner)
+    push_obs(cl, &sh.slot[1].obs,
+             make_float4(pick<E>(pt, L.v0, t), png_t, __fsub_rn(__fsub_rn(s_t, sm.M), __logf(sm.S)), 0.f));
   const uint32_t T = 1u << D.log2T, K = T - (uint32_t)V * D.floor;
   uint32_t c[E], excl = 0, am_c = 0, below_t = 0, c_t = 0;
   int am_i = 0x7fffffff;
   const bool scan = io.cdf || (t >= L.wbase && t < L.wbase + 32 * E);
   if (io.predict) {
     const uint4 qp = quant_part<E, FULL>(p, L, V, K, (float)K, D.floor, scan, c, excl, am_i, am_c);
-    if (L.lane == 0) sh.slot[1].qn[L.w] = qp;
+    push_part(cl, sh.slot[1].qn, L, qp);
     if (owner) {
       counts_around<E>(c, L.v0, t, below_t, c_t);
       below_t += excl;
@@ -857,13 +834,9 @@ __global__ void __launch_bounds__(kStepThreads, 1) k_vocab(Dims D, Batch b, Voca
   }
   cl.sync();
   if (io.predict) {
-    if (L.w == 0) {
-      uint4 qnv[4];
-      read_parts(cl, sh.slot[1].qn, L.lane, qnv);
-      gather_quant(qnv, L.lane, L.rank, T, sh.comb);
-    }
-    bar_cta();
-    const Quant q = quant_of(sh.comb, sh.slot[1], L, scan);
+    uint4 qnv[4];
+    local_parts(sh.slot[1].qn, L.lane, qnv);
+    const Quant q = quant_reduce(qnv, L, T);
     if (io.intervals && owner)
       write_interval(io.intervals + 2 * ((size_t)j * io.interval_stride + (i_tok - 1)), q, t, below_t, c_t);
     if (io.cdf) {
@@ -885,7 +858,7 @@ __global__ void __launch_bounds__(kStepThreads, 1) k_vocab(Dims D, Batch b, Voca
 
   // ---- head and mixer update (a skipped token teaches the N-gram only)
   if (io.update && !skipped) {
-    const float4 o = cl.map_shared_rank(&sh.slot[1], t / (kStepThreads * E))->obs;
+    const float4 o = sh.slot[1].obs;
     float scale;
     mixer_update(D, mixing, w, o.x, o.y, o.z, th0, th1, scale);
     if (D.use_head) {
@@ -945,12 +918,14 @@ __global__ void __launch_bounds__(kStepThreads, 1)
 #pragma unroll
     for (int i = 0; i < E; ++i) bias[i] = 0.f;
   }
-  bool act1 = 1 < m && j < nb_step[1];           // position r + 1 exists
+  bool act1 = 1 < m && j < nb_step[1];           // positions r + 1 and r + 2 exist
+  bool act2 = act1 && 2 < m && j < nb_step[2];
   if (ngram) {
     load_counts<E>(st.uni, L.v0, V, cnt);
     zero_region<E>(spw, L.lane);
     snap_copy_async(&sh.ng[0], gj);
     if (act1) snap_copy_async(&sh.ng[1], gj + 1);
+    if (act2) snap_copy_async(&sh.ng[2], gj + 2);
   } else {
 #pragma unroll
     for (int i = 0; i < E; ++i) cnt[i] = 0;
@@ -961,9 +936,10 @@ __global__ void __launch_bounds__(kStepThreads, 1)
   const int n0 = st.n_coded;
   if (ngram) cp_async_wait_all();
   __syncthreads();                               // the first N-gram states are in shared memory
+  if (ngram) ngram_scatter<E>(sh.ng[0], spw, L);
 
   // the previous position's values its quantiser and mixer step need
-  bool pend = false, p_skip = false, p_mix = false, p_own = false, p_own_w = false;
+  bool pend = false, p_skip = false, p_mix = false, p_own = false;
   int p_t = 0, p_pos = 0, p_am_i = 0x7fffffff;
   uint32_t p_below = 0, p_ct = 0, p_am_c = 0;
   float2 p_w = make_float2(0.f, 0.f);
@@ -971,11 +947,13 @@ __global__ void __launch_bounds__(kStepThreads, 1)
   int nb = 0;                                    // cluster barriers taken
   int r = 0, t_last = -1;
 
-  // interval, numeric checks and mixer step of the pending position from
-  // warp 0's sums in sh.comb and the partials of the local `slot`
+  // interval, numeric checks and mixer step of the pending position from its
+  // inbox `slot`
   auto finish = [&](const StepSlot& slot, const float (&pt)[E], bool with_head) {
-    const Quant q = quant_of(sh.comb, slot, L, p_own_w);
-    const float4 o = sh.comb.obs;
+    uint4 qv[4];
+    local_parts(slot.qn, L.lane, qv);
+    const Quant q = quant_reduce(qv, L, T);
+    const float4 o = slot.obs;
     if (p_own)
       write_interval(io.intervals + 2 * ((size_t)j * io.interval_stride + p_pos), q, p_t, p_below, p_ct);
     if ((q.bad && L.rank == 0 && threadIdx.x == 0) || final_count_bad(q, p_am_i, p_am_c, D.floor, T))
@@ -998,10 +976,10 @@ __global__ void __launch_bounds__(kStepThreads, 1)
     }
     const bool more = act1;
 
-    // ---- softmax partials of position r
+    // ---- softmax partials of position r (its slot masses are in spw)
     float png[E];
     if (ngram) {
-      ngram_probs<E, FULL>(sh.ng[r % kSnapBufs], spw, L, V, cnt, png);
+      ngram_read<E, FULL>(sh.ng[r % kSnapBufs].cu, spw, L, V, cnt, png);
     } else {
 #pragma unroll
       for (int i = 0; i < E; ++i) png[i] = 0.f;
@@ -1016,34 +994,27 @@ __global__ void __launch_bounds__(kStepThreads, 1)
     }
     const float4 part = softmax_part<E>(s, e, D.skip ? entropy_part<E>(png) : 0.f);
     StepSlot& in = sh.slot[nb & 1];
-    if (L.lane == 0) in.sm[L.w] = part;
-    if (ngram) cp_async_wait_all();              // the state of position r + 1, read after this barrier
+    push_part(cl, in.sm, L, part);
+    if (ngram) cp_async_wait_all();              // the state of position r + 2, added after this barrier
     cluster_arrive();
-    // fetched outside the barrier's release: position r + 1's logits, token
-    // and activity, the N-gram state of r + 2
+    // outside the barrier's release: position r + 1's logits, token and slot
+    // masses (its state arrived two barriers ago), the activity of r + 3
     int t_n = 0;
-    bool act2 = false;
+    bool act3 = false;
     if (more) {
       load_runf<E, FULL>(zj + (size_t)(r + 1) * V, L.v0, V, z, -INFINITY);
       t_n = obs_j[(size_t)(r + 1) * n_streams];
-      act2 = r + 2 < m && j < nb_step[r + 2];
-      if (ngram && act2) snap_copy_async(&sh.ng[(r + 2) % kSnapBufs], gj + r + 2);
+      act3 = act2 && r + 3 < m && j < nb_step[r + 3];
+      if (ngram) ngram_scatter<E>(sh.ng[(r + 1) % kSnapBufs], spw, L);
     }
     cluster_wait();
+    // every warp has added position r's masses (before this barrier's
+    // arrive): its buffer takes the state of r + 3
+    if (ngram && act3) snap_copy_async(&sh.ng[(r + 3) % kSnapBufs], gj + r + 3);
     ++nb;
-    if (L.w == 0) {                              // position r's softmax, r - 1's quantiser and mixer values
-      float4 smv[4];
-      uint4 qv[4];
-      read_parts(cl, in.sm, L.lane, smv);
-      if (pend) read_parts(cl, in.qn, L.lane, qv);
-      float4 o = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (pend && !p_skip && L.lane == 0) o = cl.map_shared_rank(&in, p_t / (kStepThreads * E))->obs;
-      gather_soft(smv, L.lane, sh.comb);
-      if (pend) gather_quant(qv, L.lane, L.rank, T, sh.comb);
-      if (L.lane == 0) sh.comb.obs = o;
-    }
-    bar_cta();
-    const Soft sm{sh.comb.M, sh.comb.S, sh.comb.H};
+    float4 smv[4];
+    local_parts(in.sm, L.lane, smv);
+    const Soft sm = softmax_reduce(smv);
     float pt[E];
     if (pend) {                                  // position r - 1 (log-loss mixer: no head step here)
       finish(in, pt, false);
@@ -1058,13 +1029,14 @@ __global__ void __launch_bounds__(kStepThreads, 1)
     float p[E];
     coded_probs<E>(pt, png, w, skipped, mixing, p);
     StepSlot& nx = sh.slot[nb & 1];
-    if (owner) nx.obs = make_float4(pick<E>(pt, L.v0, t), png_t, __fsub_rn(__fsub_rn(s_t, sm.M), __logf(sm.S)), 0.f);
+    if (owner)
+      push_obs(cl, &nx.obs,
+               make_float4(pick<E>(pt, L.v0, t), png_t, __fsub_rn(__fsub_rn(s_t, sm.M), __logf(sm.S)), 0.f));
     uint32_t c[E], excl = 0;
     const bool scan = io.intervals && t >= L.wbase && t < L.wbase + 32 * E;
     const uint4 qp = quant_part<E, FULL>(p, L, V, K, Kf, D.floor, scan, c, excl, p_am_i, p_am_c);
-    if (L.lane == 0) nx.qn[L.w] = qp;
+    push_part(cl, nx.qn, L, qp);
     p_own = owner && io.intervals;
-    p_own_w = scan;
     if (owner) {
       counts_around<E>(c, L.v0, t, p_below, p_ct);
       p_below += excl;
@@ -1086,35 +1058,18 @@ __global__ void __launch_bounds__(kStepThreads, 1)
     } else {
       cl.sync();
       ++nb;
-      if (L.w == 0) {
-        uint4 qv[4];
-        read_parts(cl, nx.qn, L.lane, qv);
-        float4 o = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (!skipped && L.lane == 0) o = cl.map_shared_rank(&nx, t / (kStepThreads * E))->obs;
-        gather_quant(qv, L.lane, L.rank, T, sh.comb);
-        if (L.lane == 0) sh.comb.obs = o;
-      }
-      bar_cta();
       finish(nx, pt, true);
     }
     ++r;
     t = t_n;
     act1 = act2;
+    act2 = act3;
     live = more;
   }
   if (pend) {
     cl.sync();
     ++nb;
     StepSlot& in = sh.slot[(nb - 1) & 1];
-    if (L.w == 0) {
-      uint4 qv[4];
-      read_parts(cl, in.qn, L.lane, qv);
-      float4 o = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (!p_skip && L.lane == 0) o = cl.map_shared_rank(&in, p_t / (kStepThreads * E))->obs;
-      gather_quant(qv, L.lane, L.rank, T, sh.comb);
-      if (L.lane == 0) sh.comb.obs = o;
-    }
-    bar_cta();
     float none[E];
     finish(in, none, false);
   }
