@@ -107,6 +107,8 @@ struct nc_ctx {
   // tensor-core path
   std::vector<TcMat> tc;             // per layer: qkv, o, gate/up, down; then the LM head
   void* opnd = nullptr;              // [rows][max(d, F)] BF16 / E4M3 GEMM operand
+  void* opnd2 = nullptr;             // BF16: [rows][F] the down projection's operand, written by the
+                                     // gate/up epilogue while that GEMM still reads opnd
   float* opnd_scale = nullptr;       // [rows] E4M3 row scales
 
   StreamDev* d_st = nullptr;
@@ -316,6 +318,10 @@ static int tc_setup(nc_ctx* ctx) {
     return fail(ctx, NC_ENOMEM, "tensor-core operand allocation");
   NC_TRY(cudaMemset(ctx->opnd, 0, (size_t)R * Kmax * esz));
   NC_TRY(cudaMemset(ctx->opnd_scale, 0, (size_t)R * 4));
+  if (kb) {
+    if (dalloc(ctx, &ctx->opnd2, (size_t)R * D.F * 2)) return fail(ctx, NC_ENOMEM, "tensor-core operand allocation");
+    NC_TRY(cudaMemset(ctx->opnd2, 0, (size_t)R * D.F * 2));
+  }
   auto add = [&](const Mat& m) {
     TcMat t;
     t.M = m.rows;
@@ -396,11 +402,12 @@ static int tc_setup(nc_ctx* ctx) {
   for (size_t i = 0; i < ctx->tc.size(); ++i) {
     TcMat& t = ctx->tc[i];
     const int q = (i + 1 == ctx->tc.size()) ? 4 : (int)(i % 4);
+    const void* src = (kb && q == 3) ? ctx->opnd2 : ctx->opnd;   // BF16: the down projection reads opnd2
     t.bn = chosen[q];
-    if (!tc_encode_tmap(&t.b, ctx->opnd, esz, t.K, B, t.bn)) return fail(ctx, NC_ECUDA, "tensor map encoding failed");
+    if (!tc_encode_tmap(&t.b, src, esz, t.K, B, t.bn)) return fail(ctx, NC_ECUDA, "tensor map encoding failed");
     if (ctx->P > 0) {
       t.bnp = chosen_p[q];
-      if (!tc_encode_tmap(&t.bp, ctx->opnd, esz, t.K, ctx->P, t.bnp))
+      if (!tc_encode_tmap(&t.bp, src, esz, t.K, ctx->P, t.bnp))
         return fail(ctx, NC_ECUDA, "tensor map encoding failed");
     }
   }
@@ -811,12 +818,15 @@ static cudaError_t launch_model(nc_ctx* ctx, const Batch& b, StepMarks* mk = nul
 }
 
 // Model forward on the tensor-core path: each projection is one tcgen05 GEMM
-// over the batch, fed by a small kernel that writes its BF16 / E4M3 operand.
+// over the batch.  Its operand is written by a small kernel (the RMSNorm
+// ones; every E4M3 one, for its row scale) or, for BF16, by the producer
+// itself: the attention writes the O projection's operand and the gate/up
+// epilogue the down projection's (into opnd2).
 static cudaError_t launch_model_tc(nc_ctx* ctx, const Batch& b, StepMarks& m) {
   const Dims& D = ctx->D;
   cudaStream_t s = ctx->stream;
   const int kb = ctx->fmt == NC_BF16;
-  auto gemm = [&](const TcMat& t, int epi, float* y, float* h) {
+  auto gemm = [&](const TcMat& t, int epi, float* y, float* h, void* h16 = nullptr) {
     const bool pf = b.pos != nullptr;               // prefill forward: P-row operand map
     TcGemm g{};
     g.tmap_a = &t.a;
@@ -832,6 +842,7 @@ static cudaError_t launch_model_tc(nc_ctx* ctx, const Batch& b, StepMarks& m) {
     g.x_scale = ctx->opnd_scale;
     g.y = y;
     g.h_out = h;
+    g.h16 = h16;
     g.st = b.st;
     g.slots = b.slots;
     g.status = ctx->d_status;
@@ -846,15 +857,16 @@ static cudaError_t launch_model_tc(nc_ctx* ctx, const Batch& b, StepMarks& m) {
     if (e == cudaSuccess) e = gemm(T[0], EPI_STORE, ctx->qkv, nullptr);
     if (e == cudaSuccess && b.pos) e = launch_kv_append(D, b, l, ctx->qkv, s);
     if (e == cudaSuccess) e = m.mark(s, TK_QKV);
-    if (e == cudaSuccess) e = launch_attn(D, b, l, ctx->qkv, ctx->attn_out, s);
+    if (e == cudaSuccess) e = launch_attn(D, b, l, ctx->qkv, ctx->attn_out, s, kb ? ctx->opnd : nullptr);
     if (e == cudaSuccess) e = m.mark(s, TK_ATTN);
-    if (e == cudaSuccess) e = launch_act_plain(D, b, ctx->attn_out, D.hq * kHeadDim, kb, ctx->opnd, ctx->opnd_scale, s);
+    if (e == cudaSuccess && !kb)
+      e = launch_act_plain(D, b, ctx->attn_out, D.hq * kHeadDim, kb, ctx->opnd, ctx->opnd_scale, s);
     if (e == cudaSuccess) e = gemm(T[1], EPI_RESID, ctx->x, nullptr);
     if (e == cudaSuccess) e = m.mark(s, TK_O);
     if (e == cudaSuccess) e = launch_act_rmsnorm(D, b, ctx->x, L.g_ffn, D.d, kb, ctx->opnd, ctx->opnd_scale, s);
-    if (e == cudaSuccess) e = gemm(T[2], EPI_SWIGLU, nullptr, ctx->h);
+    if (e == cudaSuccess) e = gemm(T[2], EPI_SWIGLU, nullptr, ctx->h, kb ? ctx->opnd2 : nullptr);
     if (e == cudaSuccess) e = m.mark(s, TK_GU);
-    if (e == cudaSuccess) e = launch_act_plain(D, b, ctx->h, D.F, kb, ctx->opnd, ctx->opnd_scale, s);
+    if (e == cudaSuccess && !kb) e = launch_act_plain(D, b, ctx->h, D.F, kb, ctx->opnd, ctx->opnd_scale, s);
     if (e == cudaSuccess) e = gemm(T[3], EPI_RESID, ctx->x, nullptr);
     if (e == cudaSuccess) e = m.mark(s, TK_DOWN);
   }

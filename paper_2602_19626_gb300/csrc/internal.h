@@ -192,9 +192,9 @@ cudaError_t launch_embed(const Dims& D, const Batch& b, const void* E, const flo
 cudaError_t launch_gemv(const Dims& D, const Batch& b, const Mat& m, int fmt, int pro, int epi,
                         const GemvIO& io, cudaStream_t s);
 // Decode attention (one cluster per row and KV head) into attn_out
-// [Bmax][hq * 64].
+// [Bmax][hq * 64], or (BF16 cache, out16 set) rounded to BF16 into out16.
 cudaError_t launch_attn(const Dims& D, const Batch& b, int layer, const float* qkv, float* attn_out,
-                        cudaStream_t s);
+                        cudaStream_t s, void* out16 = nullptr);
 
 struct VocabIO {
   uint32_t* cdf;            // [Bmax][V+1] or nullptr
@@ -246,9 +246,9 @@ size_t attn_tc_smem(int rq, int grp, int S);
 // 16-row tile through a chunk's blocks (same bits as launch_attn_tc).
 bool attn_pf_fits(const Dims& D, const Batch& b);
 cudaError_t launch_attn_pf(const Dims& D, const Batch& b, int layer, const float* qkv, float* attn_out,
-                           cudaStream_t s);
-cudaError_t launch_attn_tc(const Dims& D, const Batch& b, int layer, int rq, int S, const float* qkv,
-                           float* attn_out, cudaStream_t s);
+                           void* out16, cudaStream_t s);
+cudaError_t launch_attn_tc(const Dims& D, const Batch& b, int layer, int rq, int S, const float* qkv, float* attn_out,
+                           void* out16, cudaStream_t s);
 // Prefill: rotate and append the k, v of every row to the KV ring of `layer`.
 cudaError_t launch_kv_append(const Dims& D, const Batch& b, int layer, const float* qkv, cudaStream_t s);
 // Decoder: row j's symbol is the s with cdf[s] <= target[j] < cdf[s+1]; writes
@@ -271,6 +271,7 @@ struct TcGemm {
   const float* x_scale;     // FP8: [Bmax]
   float* y;                 // EPI_STORE / EPI_RESID: [Bmax][M]
   float* h_out;             // EPI_SWIGLU: [Bmax][M / 2]
+  void* h16;                // EPI_SWIGLU: or, when set, h rounded to BF16 there (the next operand)
   StreamDev* st;            // EPI_LOGITS: each stream's z, or
   float* zrows;             // EPI_LOGITS: [Bmax][M] when set
   const int32_t* slots;

@@ -247,6 +247,14 @@ __device__ void attn_block_tc(int p_lo, int c_lo, int mt, int R, int grp, const 
   }
 }
 
+// One attention output: FP32 into attn_out, or rounded to BF16 into out16.
+__device__ __forceinline__ void store_out(const AttnIO& io, size_t i, float v) {
+  if (io.out16)
+    static_cast<__nv_bfloat16*>(io.out16)[i] = __float2bfloat16_rn(v);
+  else
+    io.attn_out[i] = v;
+}
+
 // The K and V tile rows of positions c_lo .. c_lo + 255: ring entries for
 // positions <= last (the fed token's own entry is written separately in
 // decode), zeros above.
@@ -316,7 +324,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_attn_tc(Dims D, Batch b, int 
     pdl_trigger();
     for (int e = tid; e < rq * grp * kd; e += kTcThreads) {
       const int r = e / (grp * kd), h = (e / kd) % grp, dl = e % kd;
-      io.attn_out[(size_t)(i0 + r) * D.hq * kHeadDim + (g * grp + h) * kHeadDim + rank * kd + dl] = 0.f;
+      store_out(io, (size_t)(i0 + r) * D.hq * kHeadDim + (g * grp + h) * kHeadDim + rank * kd + dl, 0.f);
     }
     return;                                        // uniform across the cluster
   }
@@ -434,8 +442,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_attn_tc(Dims D, Batch b, int 
     float o = 0.f;
     for (int c = 0; c < nc; ++c)
       o = fmaf(racc[((r * kAttnMaxChunks + c) * grp + h) * kd + dl], mf[t * kAttnMaxChunks + c], o);
-    io.attn_out[(size_t)(i0 + r) * D.hq * kHeadDim + (g * grp + h) * kHeadDim + rank * kd + dl] =
-        nc ? o / mL[t] : 0.f;
+    store_out(io, (size_t)(i0 + r) * D.hq * kHeadDim + (g * grp + h) * kHeadDim + rank * kd + dl,
+              nc ? o / mL[t] : 0.f);
   }
 }
 
@@ -541,13 +549,13 @@ __global__ void __launch_bounds__(kPfThreads, 2)
   __syncthreads();
   int a_max = -1;
   for (int r = 0; r < kPfRows; ++r) a_max = max(a_max, a_row[r]);
-  auto out_at = [&](int r, int h, int d) -> float& {
-    return io.attn_out[(size_t)(i0 + r) * D.hq * kHeadDim + (g * grp + h) * kHeadDim + d];
+  auto out_at = [&](int r, int h, int d) -> size_t {
+    return (size_t)(i0 + r) * D.hq * kHeadDim + (g * grp + h) * kHeadDim + d;
   };
   if (a_max < 0) {                                 // rows past the stream's end
     for (int e = tid; e < R * kPfKd; e += kPfThreads) {
       const int t = e / kPfKd;
-      out_at(t / grp, t % grp, rank * kPfKd + e % kPfKd) = 0.f;
+      store_out(io, out_at(t / grp, t % grp, rank * kPfKd + e % kPfKd), 0.f);
     }
     return;                                        // uniform across the cluster
   }
@@ -660,7 +668,7 @@ __global__ void __launch_bounds__(kPfThreads, 2)
     const int nc = a < 0 ? 0 : (a - start) / kAttnChunk + 1;
     float o = 0.f;
     for (int c = 0; c < nc; ++c) o = fmaf(racc[(t * kAttnMaxChunks + c) * kPfKd + dl], mf[t * kAttnMaxChunks + c], o);
-    out_at(t / grp, t % grp, rank * kPfKd + dl) = nc ? o / mL[t] : 0.f;
+    store_out(io, out_at(t / grp, t % grp, rank * kPfKd + dl), nc ? o / mL[t] : 0.f);
   }
 }
 
@@ -699,8 +707,8 @@ bool attn_pf_fits(const Dims& D, const Batch& b) {
 }
 
 cudaError_t launch_attn_pf(const Dims& D, const Batch& b, int layer, const float* qkv, float* attn_out,
-                           cudaStream_t s) {
-  const AttnIO io{qkv, attn_out};
+                           void* out16, cudaStream_t s) {
+  const AttnIO io{qkv, attn_out, out16};
   static bool attr = false;                        // the kernel's shared-memory limit: once per process
   const size_t smem = PfLayout(D.hq / D.hkv).total;
   if (!attr) {
@@ -714,8 +722,8 @@ cudaError_t launch_attn_pf(const Dims& D, const Batch& b, int layer, const float
 }
 
 cudaError_t launch_attn_tc(const Dims& D, const Batch& b, int layer, int rq, int S, const float* qkv,
-                           float* attn_out, cudaStream_t s) {
-  const AttnIO io{qkv, attn_out};
+                           float* attn_out, void* out16, cudaStream_t s) {
+  const AttnIO io{qkv, attn_out, out16};
   switch (S) {
     case 1: return launch_tc_s<1>(D, b, layer, rq, io, s);
     case 2: return launch_tc_s<2>(D, b, layer, rq, io, s);

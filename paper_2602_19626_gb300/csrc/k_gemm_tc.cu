@@ -266,7 +266,10 @@ __global__ void __launch_bounds__(kTcThreads, 1)
           const float up = __shfl_xor_sync(0xffffffffu, y, 1);   // rows 2j (gate), 2j + 1 (up)
           if (n < B && r < g.M && (r & 1) == 0) {
             const float h = silu_tc(y) * up;
-            g.h_out[(size_t)n * (g.M / 2) + (r >> 1)] = h;
+            if (g.h16)
+              static_cast<__nv_bfloat16*>(g.h16)[(size_t)n * (g.M / 2) + (r >> 1)] = __float2bfloat16_rn(h);
+            else
+              g.h_out[(size_t)n * (g.M / 2) + (r >> 1)] = h;
           }
         } else if (n < B && r < g.M) {
           if (EPI == EPI_STORE) {

@@ -336,6 +336,7 @@ struct __align__(16) AttnSmem {
 struct AttnIO {
   const float* qkv;      // [B][qkv_rows], written by the QKV projection
   float* attn_out;       // [B][hq * 64]
+  void* out16;           // or, when set, the output rounded to BF16 there (the tensor-core O operand)
 };
 
 // Values of a lane that do not depend on the QKV projection: the cached key
