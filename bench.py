@@ -373,10 +373,16 @@ def run_gpu(args, wl):
     try:
         trace = ctx.encode_intervals(tok_dev, offs, lens, iv, stride, trace=True)
         tot_ms = sum(k["ms"] for k in trace) or 1.0
-        dom = max(trace, key=lambda k: k["ms"])
+        # with the prefill, a chunk's N-gram pass runs beside its forward and
+        # its vocabulary loop beside the next chunk's forward (the trace runs
+        # them in order): the dominant kernel is taken on the forward, the
+        # critical path of the timed run
+        beside = ["ngram_update", "vocab"] if prefill_positions(wl, len(streams), int(lens.max())) >= 2 else []
+        dom = max([k for k in trace if k["name"] not in beside] or trace, key=lambda k: k["ms"])
         n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
         roofline = roofline_of(dom, wl.get("path", "gemv"), wl["fmt"], n_sm, 2070.0)
         roofline["share"] = dom["ms"] / tot_ms
+        roofline["beside_critical_path"] = beside
         roofline["traffic"] = ncu_traffic(dom["name"], args.workload)
         kernels = {k["name"]: {"launches": k["launches"], "ms": round(k["ms"], 3),
                                "share": round(k["ms"] / tot_ms, 4),
