@@ -278,10 +278,12 @@ def ncu_traffic(kind: str, workload: str):
 
 
 def kernel_sources_hash() -> str:
+    """Hash of the device code (the kernel files and the headers they
+    include); host-only orchestration and the host coder are left out."""
     d = os.path.join(ROOT, "paper_2602_19626_gb300", "csrc")
     m = hashlib.sha256()
     for name in sorted(os.listdir(d)):
-        if name.endswith((".cu", ".cuh", ".h", ".cpp")):
+        if (name.startswith("k_") and name.endswith(".cu")) or name.endswith(".cuh") or name == "internal.h":
             with open(os.path.join(d, name), "rb") as fh:
                 m.update(fh.read())
     return m.hexdigest()[:12]

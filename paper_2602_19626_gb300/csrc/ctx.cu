@@ -304,9 +304,10 @@ static int tc_bn_candidates(int Bmax, int* out) {
 
 // Tensor maps of every projection on the tensor-core path, and the autotuned
 // batch tile bn per projection shape: each candidate is timed on the real
-// weights with max_streams rows, and again with prefill_rows rows for the
-// encoder's prefill forward (the batch tile does not change the arithmetic
-// of any output element, so the choice never changes results).
+// weights, with the epilogue that projection runs, with max_streams rows and
+// again with prefill_rows rows for the encoder's prefill forward (the batch
+// tile does not change the arithmetic of any output element, so the choice
+// never changes results).
 static int tc_setup(nc_ctx* ctx) {
   const Dims& D = ctx->D;
   const int B = ctx->cfg.max_streams;
@@ -347,6 +348,7 @@ static int tc_setup(nc_ctx* ctx) {
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
   const int probe_idx[5] = {0, 1, 2, 3, (int)ctx->tc.size() - 1};
+  const int probe_epi[5] = {EPI_STORE, EPI_RESID, EPI_SWIGLU, EPI_RESID, EPI_LOGITS};
   auto tune = [&](int rows, int* chosen) -> int {
     int cands[4];
     const int nc = tc_bn_candidates(rows, cands);
@@ -370,12 +372,15 @@ static int tc_setup(nc_ctx* ctx) {
         g.nB = nB;
         g.w_scale = t.scale;
         g.x_scale = ctx->opnd_scale;
-        g.y = scratch;
+        g.y = scratch;                              // the residual too: its values do not matter here
+        g.h_out = scratch;
+        g.h16 = kb ? scratch : nullptr;             // the forward's SwiGLU output format
+        g.zrows = scratch;
         g.status = ctx->d_status;
         float ms_sum = 0.f;
         for (int rep = 0; rep < 4; ++rep) {
           cudaEventRecord(e0, ctx->stream);
-          cudaError_t e = launch_gemm_tc(g, EPI_STORE, ctx->stream, false);
+          cudaError_t e = launch_gemm_tc(g, probe_epi[q], ctx->stream, false);
           cudaEventRecord(e1, ctx->stream);
           if (e == cudaSuccess) e = cudaEventSynchronize(e1);
           if (e != cudaSuccess) return fail_cuda(ctx, e, "tensor-core autotune");
