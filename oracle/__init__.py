@@ -13,6 +13,8 @@ slow and written to be checked against the paper by eye:
                   differentiable update rule.
 * ``cdf``       - CDF quantisation with per-symbol floors (Sec. 3.3).
 * ``coder``     - 32-bit arithmetic coder (Sec. 3.8), pure-Python integers.
+* ``ans``       - rANS coder on the same integer CDFs (the ANS coder named as
+                  future work in Sec. 6), pure-Python integers.
 * ``container`` - NC05-style container (Sec. 3.12).
 * ``compress``  - the compression / decompression loop (Algorithm 1).
 * ``numerics``  - bf16 / fp8-e4m3 rounding used to derive the dequantised
