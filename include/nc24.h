@@ -65,6 +65,13 @@ enum { NC_RULE_PAPER = 0, NC_RULE_MIXED_NLL = 1 };
  *                activations (FP8 activations for NC_FP8E4M3), FP32 accumulation. */
 enum { NC_PATH_GEMV = 0, NC_PATH_TC = 1 };
 
+/* Host entropy coder of the coded streams.
+ *  NC_CODER_ARITH: the 32-bit arithmetic coder (Sec. 3.8).
+ *  NC_CODER_RANS:  rANS with a 64-bit state and 32-bit words, the ANS coder
+ *                  named as future work (Sec. 6); same CDFs, same model
+ *                  work, recorded in the container's flags (bit 4). */
+enum { NC_CODER_ARITH = 0, NC_CODER_RANS = 1 };
+
 typedef struct {
   /* model shape (Sec. 3.2): 30, 576, 9, 3, 1536, 49152 for SmolLM2-135M */
   int n_layers, d_model, n_heads, n_kv_heads, d_ffn, vocab;
@@ -99,6 +106,7 @@ typedef struct {
                                        coded with p = p_ng, and only the N-gram learns from
                                        it.  Needs ngram_order > 0.  Recorded in the
                                        container's flags. */
+  int coder;                        /* NC_CODER_ARITH | NC_CODER_RANS */
 } nc_config;
 
 /* Fill *cfg with the SmolLM2-135M shape and the paper's defaults
@@ -154,7 +162,8 @@ int nc_step_cdf(nc_ctx* ctx, int n, const int32_t* stream_ids, const int32_t* pr
 int nc_update_bias(nc_ctx* ctx, int n, const int32_t* stream_ids, const int32_t* observed);
 
 /* Whole-stream compression into an NC05-style container (Sec. 3.12):
- * 9-byte header (magic "NC05", flags, tau as binary16, stream count), one
+ * 9-byte header (magic "NC05", flags: bit 0 N-gram, 1 head, 2 skip,
+ * 3 mixed-NLL rule, 4 rANS coder; tau as binary16, stream count), one
  * extension byte (weight format | path << 4), 12 bytes per stream (token
  * count, bit count, byte count, little-endian uint32), then the coded streams.
  *   tokens HOST array of n_streams HOST int32 pointers; lens HOST int64[n_streams].
@@ -304,6 +313,27 @@ int nc_ac_encode(const uint32_t* lo, const uint32_t* hi, int64_t n, int log2_tot
  * Errors: NC_EINVAL, NC_ECORRUPT (a CDF that is not a valid CDF). */
 int nc_ac_decode(const uint8_t* bits, uint64_t nbits, const uint32_t* cdfs, int V, int64_t n,
                  int log2_total, int32_t* symbols);
+
+/* rANS coder (the ANS coder of Sec. 6) on the host, for callers that produce
+ * their own CDFs.  State x in [2^31, 2^63): a symbol [lo, hi) of a total
+ * M = 2^log2_total (1..31), f = hi - lo, encodes as
+ * x -> floor(x / f) M + (x mod f) + lo after moving the low 32 bits of x out
+ * while x >= 2^(63 - log2_total) f, and decodes as x -> f floor(x / M) +
+ * (x mod M) - lo, refilling 32 bits while x < 2^31.  The encoder takes the
+ * symbols in reverse from x = 2^31 and writes the final state (8 bytes, little-
+ * endian) and then the moved-out words (4 bytes each) in the order the decoder
+ * reads them.
+ * nc_ans_encode: n intervals (HOST uint32 lo, hi) into out (HOST, capacity
+ *   *inout_nbytes; the size returned; out == NULL queries it).
+ *   Errors: NC_EINVAL (empty or out-of-range interval, buffer too small).
+ * nc_ans_decode: n symbols, one CDF per symbol (HOST uint32[n * (V + 1)]),
+ *   into symbols HOST int32[n].  Errors: NC_EINVAL, NC_ECORRUPT (a CDF that is
+ *   not a valid CDF, a length that is not 8 + 4 k bytes, or a final state
+ *   other than 2^31 with every word read). */
+int nc_ans_encode(const uint32_t* lo, const uint32_t* hi, int64_t n, int log2_total, uint8_t* out,
+                  size_t* inout_nbytes);
+int nc_ans_decode(const uint8_t* data, size_t nbytes, const uint32_t* cdfs, int V, int64_t n, int log2_total,
+                  int32_t* symbols);
 
 /* Mixed-distribution NLL L = -log(w0 p_tilde(t*) + w1 p_ng(t*)), w = softmax(theta),
  * p_tilde = softmax(z / tau + b), for n rows (the differentiable update rule).

@@ -77,7 +77,11 @@ class Decoder:
     def consume(self, lo: int, hi: int):
         f = hi - lo
         self.x = f * (self.x >> self.log2M) + self.target() - lo
-        while self.x < L:
+        # a valid stream leaves x >= f >= 1 here, so one refill reaches L;
+        # the bound keeps a corrupt one (x = 0, zero words) from looping
+        for _ in range(2):
+            if self.x >= L:
+                break
             w = 0
             if self.pos + 4 <= len(self.data):
                 w = int.from_bytes(self.data[self.pos:self.pos + 4], "little")

@@ -30,6 +30,7 @@ import numpy as np
 
 from . import cdf as cdfmod
 from . import container
+from . import ans
 from .coder import Decoder, Encoder
 from .head import BiasHead, p_llm as llm_softmax
 from .mixer import Mixer, mixed_nll_grad
@@ -50,6 +51,7 @@ class StepConfig:
     use_head: bool = True
     rule: str = "paper"          # or "mixed_nll"
     skip: bool = False           # confidence-based LLM skip (Sec. 3.7)
+    coder: str = "arith"         # or "rans" (the ANS coder of Sec. 6)
 
     @property
     def T(self) -> int:
@@ -65,6 +67,8 @@ class StepConfig:
             f |= container.FLAG_MIXED_NLL
         if self.skip:
             f |= container.FLAG_SKIP
+        if self.coder == "rans":
+            f |= container.FLAG_RANS
         return f
 
 
@@ -160,18 +164,23 @@ class StreamState:
 def compress_stream(model, tokens, cfg: StepConfig, record_steps: int = 0):
     st = StreamState.new(model, cfg)
     enc = Encoder(cfg.T)
+    intervals = []
     for k, t in enumerate(np.asarray(tokens)):
         _, _, cdf = st.predict(record=k < record_steps)
+        intervals.append((int(cdf[int(t)]), int(cdf[int(t) + 1])))
         enc.encode(cdf, int(t))
         st.update(int(t))
     payload, nbits = enc.finish()
+    if cfg.coder == "rans":                       # the same intervals, coded in reverse by rANS
+        payload = ans.encode(intervals, cfg.cdf_log2_total)
+        nbits = 8 * len(payload)
     return dict(payload=payload, nbits=nbits, ideal_bits=st.ideal_bits,
                 records=st.records, min_range=enc.min_range, slides=st.cache.slides, skipped=st.skipped)
 
 
 def decompress_stream(model, payload: bytes, nbits: int, n: int, cfg: StepConfig):
     st = StreamState.new(model, cfg)
-    dec = Decoder(payload, nbits, cfg.T)
+    dec = ans.Decoder(payload, cfg.cdf_log2_total) if cfg.coder == "rans" else Decoder(payload, nbits, cfg.T)
     out = np.empty(n, dtype=np.int32)
     for k in range(n):
         _, _, cdf = st.predict()

@@ -6,7 +6,8 @@ count, bit count, stream byte length), then the concatenated coded streams.
 
 Readings where the paper is silent: byte order little-endian; tau is IEEE
 binary16; flag bits: bit0 N-gram, bit1 adaptive head, bit2 confidence skip,
-bit3 mixed-NLL update rule.  One extension byte follows the 9-byte header and
+bit3 mixed-NLL update rule, bit4 the rANS coder (ans.py) in place of the
+arithmetic coder.  One extension byte follows the 9-byte header and
 records the numeric path (weight format in the low nibble, kernel path in the
 high nibble), because a decoder must replay the encoder's exact arithmetic.
 """
@@ -17,7 +18,7 @@ import struct
 import numpy as np
 
 MAGIC = b"NC05"
-FLAG_NGRAM, FLAG_HEAD, FLAG_SKIP, FLAG_MIXED_NLL = 1, 2, 4, 8
+FLAG_NGRAM, FLAG_HEAD, FLAG_SKIP, FLAG_MIXED_NLL, FLAG_RANS = 1, 2, 4, 8, 16
 HEADER = 9
 RECORD = 12
 

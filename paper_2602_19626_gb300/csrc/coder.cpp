@@ -75,6 +75,62 @@ void AcDecoder::consume(uint32_t lo, uint32_t hi) {
   }
 }
 
+// ------------------------------------------------------------------ rANS
+namespace {
+constexpr uint64_t kRansL = 1ull << 31;
+constexpr int kWordBits = 32;
+
+uint64_t load_le(const uint8_t* p, int nbytes) {
+  uint64_t v = 0;
+  for (int i = nbytes - 1; i >= 0; --i) v = (v << 8) | p[i];
+  return v;
+}
+void store_le(uint8_t* p, uint64_t v, int nbytes) {
+  for (int i = 0; i < nbytes; ++i) p[i] = (uint8_t)(v >> (8 * i));
+}
+}  // namespace
+
+bool rans_encode(const uint32_t* lo, const uint32_t* hi, int64_t n, int log2T, std::vector<uint8_t>* out) {
+  if (log2T < 1 || log2T > 31) return false;
+  const uint64_t M = 1ull << log2T;
+  uint64_t x = kRansL;
+  std::vector<uint32_t> words;
+  for (int64_t i = n - 1; i >= 0; --i) {
+    if (lo[i] >= hi[i] || hi[i] > M) return false;
+    const uint64_t f = hi[i] - lo[i];
+    const uint64_t x_max = ((kRansL >> log2T) << kWordBits) * f;   // <= 2^63
+    while (x >= x_max) {
+      words.push_back((uint32_t)x);
+      x >>= kWordBits;
+    }
+    x = (x / f) * M + (x % f) + lo[i];
+  }
+  out->assign(8 + 4 * words.size(), 0);
+  store_le(out->data(), x, 8);
+  uint8_t* p = out->data() + 8;
+  for (size_t k = words.size(); k-- > 0; p += 4) store_le(p, words[k], 4);
+  return true;
+}
+
+RansDecoder::RansDecoder(const uint8_t* data, size_t nbytes, int log2T)
+    : data_(data), nbytes_(nbytes), log2T_(log2T), mask_((1ull << log2T) - 1) {
+  if (valid()) x_ = load_le(data_, 8);
+}
+
+void RansDecoder::consume(uint32_t lo, uint32_t hi) {
+  const uint64_t f = hi - lo;
+  x_ = f * (x_ >> log2T_) + (x_ & mask_) - lo;
+  // a valid stream leaves x >= f >= 1 here, so one refill reaches L; the
+  // bound keeps a corrupt one (x = 0, zero words) from looping
+  for (int k = 0; k < 2 && x_ < kRansL; ++k) {
+    const uint64_t w = pos_ + 4 <= nbytes_ ? load_le(data_ + pos_, 4) : 0;
+    pos_ += 4;
+    x_ = (x_ << kWordBits) | w;
+  }
+}
+
+bool RansDecoder::finished() const { return x_ == kRansL && pos_ == nbytes_; }
+
 // IEEE binary16 conversion, round to nearest even (for the 2-byte tau field).
 uint16_t float_to_half_bits(float f) {
   uint32_t x;

@@ -58,6 +58,37 @@ class AcDecoder {
   uint64_t low_ = 0, high_ = 0xFFFFFFFFull, value_ = 0;
 };
 
+// rANS coder on the same integer CDFs (the ANS coder named as future work in
+// Sec. 6): state x in [L, 2^32 L), L = 2^31, total M = 2^log2T (log2T <= 31).
+// A symbol [lo, hi) with f = hi - lo encodes as x -> floor(x / f) M +
+// (x mod f) + lo after moving the low 32 bits of x out while
+// x >= (L / M) 2^32 f; it decodes as x -> f floor(x / M) + (x mod M) - lo,
+// refilling 32 bits while x < L.  The encoder runs the symbols in reverse
+// from x = L; its output is the final state (8 bytes, little-endian) and then
+// the moved-out words in reverse order of writing (4 bytes each), which is
+// the order the decoder reads them in.
+// false for an empty or out-of-range interval
+bool rans_encode(const uint32_t* lo, const uint32_t* hi, int64_t n, int log2T, std::vector<uint8_t>* out);
+
+class RansDecoder {
+ public:
+  RansDecoder(const uint8_t* data, size_t nbytes, int log2T);
+  // false for a length that is not 8 + 4 k bytes
+  bool valid() const { return nbytes_ >= 8 && (nbytes_ - 8) % 4 == 0; }
+  // the count in [0, M) that selects the next symbol
+  uint32_t target() const { return (uint32_t)(x_ & mask_); }
+  // consume the decoded symbol's interval [lo, hi)
+  void consume(uint32_t lo, uint32_t hi);
+  // every word read and the state back at L
+  bool finished() const;
+
+ private:
+  const uint8_t* data_;
+  size_t nbytes_, pos_ = 8;
+  int log2T_;
+  uint64_t mask_, x_ = 0;
+};
+
 // Container: "NC05", flags, tau (binary16), stream count, extension byte
 // (weight format | path << 4), then per stream (tokens, bits, bytes) as
 // little-endian uint32, then the payloads.

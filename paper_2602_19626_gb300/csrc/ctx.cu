@@ -184,6 +184,7 @@ extern "C" void nc_config_default(nc_config* c) {
   c->cuda_stream = nullptr;
   c->prefill_rows = 0;
   c->skip = 0;
+  c->coder = NC_CODER_ARITH;
 }
 
 extern "C" const char* nc_status_str(int s) {
@@ -226,6 +227,7 @@ static std::string validate(const nc_config& c) {
   if (c.max_streams < 1 || c.max_streams > 4096) return "max_streams must be 1..4096";
   if (c.warmup < 0) return "warmup must be >= 0";
   if (c.prefill_rows < 0 || c.prefill_rows > 32768) return "prefill_rows must be 0..32768";
+  if (c.coder != NC_CODER_ARITH && c.coder != NC_CODER_RANS) return "unknown coder";
   return "";
 }
 
@@ -1070,6 +1072,7 @@ static uint8_t flags_byte(const nc_config& c) {
   if (c.use_head) f |= 2;
   if (c.ngram_order > 0 && c.skip) f |= 4;
   if (c.update_rule == NC_RULE_MIXED_NLL) f |= 8;
+  if (c.coder == NC_CODER_RANS) f |= 16;
   return f;
 }
 static uint8_t path_byte(const nc_config& c) { return (uint8_t)(c.weight_fmt | (c.path << 4)); }
@@ -1491,7 +1494,9 @@ extern "C" int nc_encode(nc_ctx* ctx, int n_streams, const int32_t* const* token
   // worst case: about 24 bits + 2 per token plus 2 bits per stream
   std::vector<StreamRecord> bound(n_streams);
   for (int j = 0; j < n_streams; ++j) {
-    const uint64_t bits = (uint64_t)lens[j] * (D.log2T + 2) + 4;
+    // arithmetic coder: at most log2 T + 2 bits per token; rANS: log2 T plus
+    // under 0.02 per token, the 31-bit start and the 64-bit final state
+    const uint64_t bits = (uint64_t)lens[j] * (D.log2T + 2) + 192;
     bound[j] = StreamRecord{(uint32_t)lens[j], (uint32_t)bits, (uint32_t)((bits + 7) / 8)};
   }
   if (!out) {
@@ -1558,15 +1563,29 @@ extern "C" int nc_encode(nc_ctx* ctx, int n_streams, const int32_t* const* token
   close_all();
   if (st != NC_OK) return st;
   // host coder, streams in parallel
+  const bool rans = ctx->cfg.coder == NC_CODER_RANS;
   std::vector<AcEncoder> enc;
   enc.reserve(n_streams);
   for (int j = 0; j < n_streams; ++j) enc.emplace_back(D.log2T);
+  std::vector<std::vector<uint8_t>> rans_out(n_streams);
   std::vector<int> bad(n_streams, 0);
   auto work = [&](int r0, int r1) {
+    std::vector<uint32_t> lo, hi;
     for (int r = r0; r < r1; ++r) {
       const uint32_t* p = h_iv.data() + (size_t)r * max_len * 2;
+      const int64_t len = lens[order[r]];
+      if (rans) {
+        lo.resize(len);
+        hi.resize(len);
+        for (int64_t i = 0; i < len; ++i) {
+          lo[i] = p[2 * i];
+          hi[i] = p[2 * i + 1];
+        }
+        if (!rans_encode(lo.data(), hi.data(), len, D.log2T, &rans_out[order[r]])) bad[order[r]] = 1;
+        continue;
+      }
       AcEncoder& e = enc[order[r]];
-      for (int64_t i = 0; i < lens[order[r]]; ++i)
+      for (int64_t i = 0; i < len; ++i)
         if (!e.encode(p[2 * i], p[2 * i + 1])) bad[order[r]] = 1;
       e.finish();
     }
@@ -1588,9 +1607,11 @@ extern "C" int nc_encode(nc_ctx* ctx, int n_streams, const int32_t* const* token
   std::vector<StreamRecord> recs(n_streams);
   std::vector<const std::vector<uint8_t>*> pays(n_streams);
   for (int j = 0; j < n_streams; ++j) {
-    if (enc[j].nbits() > 0xffffffffull) return fail(ctx, NC_EINVAL, "stream too long for the container");
-    recs[j] = StreamRecord{(uint32_t)lens[j], (uint32_t)enc[j].nbits(), (uint32_t)enc[j].bytes().size()};
-    pays[j] = &enc[j].bytes();
+    const std::vector<uint8_t>& bytes = rans ? rans_out[j] : enc[j].bytes();
+    const uint64_t nbits = rans ? 8ull * bytes.size() : enc[j].nbits();
+    if (nbits > 0xffffffffull) return fail(ctx, NC_EINVAL, "stream too long for the container");
+    recs[j] = StreamRecord{(uint32_t)lens[j], (uint32_t)nbits, (uint32_t)bytes.size()};
+    pays[j] = &bytes;
   }
   const size_t need = container_size(recs);
   if (*inout_nbytes < need) {
@@ -1643,9 +1664,20 @@ extern "C" int nc_decode(nc_ctx* ctx, const uint8_t* in, size_t nbytes, int32_t*
     close_all();
     return st;
   }
+  // the stream coder the container records (its flags equal the context's)
+  const bool rans = (flags & 16) != 0;
   std::vector<AcDecoder> dec;
+  std::vector<RansDecoder> rdec;
   dec.reserve(n);
-  for (int r = 0; r < n; ++r) dec.emplace_back(pays[order[r]], recs[order[r]].nbits, D.log2T);
+  rdec.reserve(n);
+  for (int r = 0; r < n; ++r) {
+    dec.emplace_back(pays[order[r]], recs[order[r]].nbits, D.log2T);
+    rdec.emplace_back(pays[order[r]], recs[order[r]].nbytes, D.log2T);
+    if (rans && !rdec.back().valid()) {
+      close_all();
+      return fail(ctx, NC_ECORRUPT, "rANS stream length is not 8 + 4k bytes");
+    }
+  }
   for (int r = 0; r < n; ++r) ctx->h_i32[1 + r] = slot_of[r];
   int64_t max_len = recs[order[0]].ntok;
   Batch b = make_batch(ctx);
@@ -1659,7 +1691,7 @@ extern "C" int nc_decode(nc_ctx* ctx, const uint8_t* in, size_t nbytes, int32_t*
     for (int64_t k = 0; k < max_len && st == NC_OK; ++k) {
       while (active > 0 && recs[order[active - 1]].ntok <= k) --active;
       ctx->h_i32[0] = active;
-      for (int r = 0; r < active; ++r) ctx->h_u32[r] = dec[r].target();
+      for (int r = 0; r < active; ++r) ctx->h_u32[r] = rans ? rdec[r].target() : dec[r].target();
       cudaError_t e = cudaMemcpyAsync(ctx->d_nB, ctx->h_i32, 4, cudaMemcpyHostToDevice, s);
       if (e == cudaSuccess) e = cudaMemcpyAsync(ctx->d_target, ctx->h_u32, (size_t)active * 4, cudaMemcpyHostToDevice, s);
       if (e == cudaSuccess) e = launch_model(ctx, b);
@@ -1682,11 +1714,16 @@ extern "C" int nc_decode(nc_ctx* ctx, const uint8_t* in, size_t nbytes, int32_t*
       }
       for (int r = 0; r < active; ++r) {
         const uint32_t lo = ctx->h_u32[n + 2 * r], hi = ctx->h_u32[n + 2 * r + 1];
-        dec[r].consume(lo, hi);
+        if (rans)
+          rdec[r].consume(lo, hi);
+        else
+          dec[r].consume(lo, hi);
         tokens_out[order[r]][k] = ctx->h_i32[1 + 2 * ctx->cfg.max_streams + r];
       }
     }
     if (st == NC_OK) st = check_status(ctx, slot_of);
+    for (int r = 0; r < n && st == NC_OK && rans; ++r)
+      if (!rdec[r].finished()) st = fail(ctx, NC_ECORRUPT, "rANS stream does not end in its initial state");
   } while (0);
   close_all();
   return st;
@@ -1800,6 +1837,48 @@ extern "C" int nc_ac_decode(const uint8_t* bits, uint64_t nbits, const uint32_t*
     d.consume(c[lo], c[lo + 1]);
   }
   return NC_OK;
+}
+
+extern "C" int nc_ans_encode(const uint32_t* lo, const uint32_t* hi, int64_t n, int log2_total, uint8_t* out,
+                             size_t* inout_nbytes) {
+  if ((!lo || !hi) && n > 0) return NC_EINVAL;
+  if (!inout_nbytes || n < 0 || log2_total < 1 || log2_total > 31) return NC_EINVAL;
+  std::vector<uint8_t> bytes;
+  if (!rans_encode(lo, hi, n, log2_total, &bytes)) return NC_EINVAL;
+  const size_t need = bytes.size();
+  if (!out || *inout_nbytes < need) {
+    *inout_nbytes = need;
+    return out ? NC_EINVAL : NC_OK;
+  }
+  std::memcpy(out, bytes.data(), need);
+  *inout_nbytes = need;
+  return NC_OK;
+}
+
+extern "C" int nc_ans_decode(const uint8_t* data, size_t nbytes, const uint32_t* cdfs, int V, int64_t n,
+                             int log2_total, int32_t* symbols) {
+  if (!data || (n > 0 && (!cdfs || !symbols)) || V < 1 || n < 0 || log2_total < 1 || log2_total > 31)
+    return NC_EINVAL;
+  const uint64_t T = 1ull << log2_total;
+  RansDecoder d(data, nbytes, log2_total);
+  if (!d.valid()) return NC_ECORRUPT;
+  for (int64_t i = 0; i < n; ++i) {
+    const uint32_t* c = cdfs + (size_t)i * (V + 1);
+    if (c[0] != 0 || c[V] != T) return NC_ECORRUPT;
+    const uint32_t t = d.target();
+    int lo = 0, hi = V - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (c[mid] <= t)
+        lo = mid;
+      else
+        hi = mid - 1;
+    }
+    if (c[lo + 1] <= c[lo]) return NC_ECORRUPT;
+    symbols[i] = lo;
+    d.consume(c[lo], c[lo + 1]);
+  }
+  return d.finished() ? NC_OK : NC_ECORRUPT;
 }
 
 extern "C" int nc_mix_nll_fwd(const float* z, const float* b, const float* p_ng, const float* theta,

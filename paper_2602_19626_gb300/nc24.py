@@ -25,6 +25,8 @@ NC_OK, NC_EINVAL, NC_ENOMEM, NC_ECUDA, NC_ETIMEOUT, NC_ECORRUPT, NC_ESTATE, NC_E
 NC_FP32, NC_BF16, NC_FP8E4M3 = 0, 1, 2
 NC_RULE_PAPER, NC_RULE_MIXED_NLL = 0, 1
 NC_PATH_GEMV, NC_PATH_TC = 0, 1
+NC_CODER_ARITH, NC_CODER_RANS = 0, 1
+CODER = {"arith": NC_CODER_ARITH, "rans": NC_CODER_RANS}
 FMT = {"fp32": NC_FP32, "bf16": NC_BF16, "fp8": NC_FP8E4M3}
 RULE = {"paper": NC_RULE_PAPER, "mixed_nll": NC_RULE_MIXED_NLL}
 
@@ -41,7 +43,7 @@ class nc_config(C.Structure):
         ("temperature", C.c_float),
         ("warmup", C.c_int), ("weight_fmt", C.c_int), ("update_rule", C.c_int), ("path", C.c_int),
         ("max_streams", C.c_int), ("device", C.c_int), ("cuda_stream", C.c_void_p),
-        ("prefill_rows", C.c_int), ("skip", C.c_int),
+        ("prefill_rows", C.c_int), ("skip", C.c_int), ("coder", C.c_int),
     ]
 
 
@@ -84,6 +86,8 @@ _SIGS = {
     "nc_gemm_tc": (C.c_int, [_P, _P, _P, _P, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, _P, _P]),
     "nc_ac_encode": (C.c_int, [_P, _P, C.c_int64, C.c_int, _P, _SZP, C.POINTER(C.c_uint64)]),
     "nc_ac_decode": (C.c_int, [_P, C.c_uint64, _P, C.c_int, C.c_int64, C.c_int, _P]),
+    "nc_ans_encode": (C.c_int, [_P, _P, C.c_int64, C.c_int, _P, _SZP]),
+    "nc_ans_decode": (C.c_int, [_P, C.c_size_t, _P, C.c_int, C.c_int64, C.c_int, _P]),
     "nc_mix_nll_fwd": (C.c_int, [_P, _P, _P, _P, _P, _P, C.c_int, C.c_int, C.c_float, _P, _P]),
     "nc_mix_nll_bwd": (C.c_int, [_P, _P, _P, _P, _P, _P, _P, C.c_int, C.c_int, C.c_float, _P, _P, _P]),
 }
@@ -193,6 +197,32 @@ def nc_ac_decode(data: bytes, nbits: int, cdfs: np.ndarray, log2_total: int) -> 
     return sym
 
 
+def nc_ans_encode(lo: np.ndarray, hi: np.ndarray, log2_total: int) -> bytes:
+    """rANS-code intervals on the host; returns the bytes."""
+    lo = np.ascontiguousarray(lo, dtype=np.uint32)
+    hi = np.ascontiguousarray(hi, dtype=np.uint32)
+    nb = C.c_size_t(0)
+    st = lib.nc_ans_encode(_ptr(lo), _ptr(hi), lo.size, log2_total, None, C.byref(nb))
+    if st:
+        raise NcError(st, "nc_ans_encode")
+    out = np.zeros(max(nb.value, 1), dtype=np.uint8)
+    st = lib.nc_ans_encode(_ptr(lo), _ptr(hi), lo.size, log2_total, _ptr(out), C.byref(nb))
+    if st:
+        raise NcError(st, "nc_ans_encode")
+    return out[: nb.value].tobytes()
+
+
+def nc_ans_decode(data: bytes, cdfs: np.ndarray, log2_total: int) -> np.ndarray:
+    cdfs = np.ascontiguousarray(cdfs, dtype=np.uint32)
+    n, V1 = cdfs.shape
+    buf = np.frombuffer(data, dtype=np.uint8).copy() if data else np.zeros(1, np.uint8)
+    sym = np.zeros(n, dtype=np.int32)
+    st = lib.nc_ans_decode(_ptr(buf), len(data), _ptr(cdfs), V1 - 1, n, log2_total, _ptr(sym))
+    if st:
+        raise NcError(st, "nc_ans_decode")
+    return sym
+
+
 def nc_mix_nll_fwd(z, b, p_ng, theta, target, warm, tau, loss, stream=None) -> int:
     n, V = z.shape
     return lib.nc_mix_nll_fwd(_ptr(z), _ptr(b), _ptr(p_ng), _ptr(theta), _ptr(target), _ptr(warm),
@@ -209,7 +239,7 @@ def nc_mix_nll_bwd(z, b, p_ng, theta, target, warm, gout, tau, db, dtheta, strea
 
 def make_config(shape, fmt="bf16", rule="paper", max_streams=1, ngram_order=3, use_head=True,
                 warmup=100, log2_total=24, floor=1, alpha=1e-3, eta=1.0, w_llm=0.85, tau=1.0,
-                device=0, stream=None, path="gemv", prefill_rows=0, skip=False) -> nc_config:
+                device=0, stream=None, path="gemv", prefill_rows=0, skip=False, coder="arith") -> nc_config:
     """nc_config from a shape with the fields of synthetic.ModelShape."""
     c = nc_config_default()
     c.n_layers, c.d_model, c.n_heads = shape.n_layers, shape.d_model, shape.n_heads
@@ -227,6 +257,7 @@ def make_config(shape, fmt="bf16", rule="paper", max_streams=1, ngram_order=3, u
     c.cuda_stream = _stream_ptr(stream) if stream is not None else None
     c.prefill_rows = prefill_rows
     c.skip = int(bool(skip))
+    c.coder = CODER[coder] if isinstance(coder, str) else coder
     return c
 
 

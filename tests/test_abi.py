@@ -92,6 +92,44 @@ def test_host_coder_rejects_bad_input(nc24):
         nc24.nc_ac_decode(b"\x00", 8, np.array([[0, 3, 3, 255]], np.uint32), 8)
 
 
+@pytest.mark.parametrize("log2T", [24, 16, 31])
+def test_host_rans_matches_oracle(nc24, log2T):
+    """The C++ rANS coder writes the oracle's bytes and decodes its symbols."""
+    from oracle import ans
+    T = 1 << log2T
+    rng = np.random.default_rng(100 + log2T)
+    n, V = 2500, 29
+    lo = np.empty(n, np.uint32)
+    hi = np.empty(n, np.uint32)
+    cdfs = np.empty((n, V + 1), np.uint32)
+    for i in range(n):
+        c = rng.multinomial(T - V, rng.dirichlet(np.full(V, 0.2))) + 1
+        cdf = np.concatenate([[0], np.cumsum(c)]).astype(np.uint64)
+        s = int(rng.integers(V))
+        cdfs[i] = cdf
+        lo[i], hi[i] = cdf[s], cdf[s + 1]
+    data = nc24.nc_ans_encode(lo, hi, log2T)
+    ref = ans.encode(zip(lo.tolist(), hi.tolist()), log2T)
+    assert data == ref
+    sym = nc24.nc_ans_decode(data, cdfs, log2T)
+    assert np.all(cdfs[np.arange(n), sym] == lo)
+    assert len(nc24.nc_ans_encode(lo[:0], hi[:0], log2T)) == 8          # the initial state alone
+
+
+def test_host_rans_rejects_bad_input(nc24):
+    with pytest.raises(nc24.NcError):
+        nc24.nc_ans_encode(np.array([5], np.uint32), np.array([5], np.uint32), 8)
+    with pytest.raises(nc24.NcError):
+        nc24.nc_ans_encode(np.array([0], np.uint32), np.array([257], np.uint32), 8)
+    cdf = np.array([[0, 100, 200, 256]], np.uint32)
+    data = nc24.nc_ans_encode(np.array([100], np.uint32), np.array([200], np.uint32), 8)
+    with pytest.raises(nc24.NcError):                                  # not 8 + 4k bytes
+        nc24.nc_ans_decode(data + b"\x00", cdf, 8)
+    with pytest.raises(nc24.NcError):                                  # one symbol too many
+        nc24.nc_ans_decode(data, np.repeat(cdf, 2, axis=0), 8)
+    assert list(nc24.nc_ans_decode(data, cdf, 8)) == [1]
+
+
 def test_container_parse(nc24):
     import ctypes as C
     from oracle import container

@@ -262,6 +262,29 @@ def test_roundtrip_small_config_with_slides_and_bpb(nc):
     ctx.close()
 
 
+@pytest.mark.parametrize("prefill_rows", [0, 256])
+def test_rans_container_roundtrip(nc, prefill_rows):
+    """Containers written with the rANS coder decode losslessly (stepwise
+    decode of a prefill encode too) and stay within 96 bits plus 0.02 bit per
+    token of the arithmetic coder's size on the same streams."""
+    shape, seed = S.SMALL, 3
+    w = S.flat_weights(shape, seed)
+    streams = [S.token_stream(seed, j, n, shape.vocab) for j, n in enumerate([700, 0, 33])]
+    enc = nc.Context(nc.make_config(shape, fmt="bf16", max_streams=3, prefill_rows=prefill_rows,
+                                    coder="rans"), w)
+    blob = enc.encode(streams)
+    enc.close()
+    dec = nc.Context(nc.make_config(shape, fmt="bf16", max_streams=3, coder="rans"), w)
+    back = dec.decode(blob)
+    dec.close()
+    for a, b in zip(streams, back):
+        assert np.array_equal(a, b)
+    ar = nc.Context(nc.make_config(shape, fmt="bf16", max_streams=3), w)
+    blob_ac = ar.encode(streams)
+    ar.close()
+    assert abs(len(blob) - len(blob_ac)) * 8 <= 3 * 96 + 0.02 * sum(len(t) for t in streams) + 3 * 40
+
+
 def test_multi_stream_container_ragged(nc):
     """Ragged lengths, including empty and one-token streams, BF16."""
     shape, seed = S.SMALL, 3

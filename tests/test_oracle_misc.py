@@ -87,6 +87,27 @@ def test_multi_stream_container_roundtrip():
         decompress(m, buf, StepConfig(warmup=5, use_ngram=False))
 
 
+def test_rans_container_roundtrip_and_size():
+    """The loop with the rANS coder (the ANS coder of Sec. 6): lossless, flagged
+    in the container, and within 96 bits plus 0.02 bit per token of the
+    arithmetic coder's stream on the same CDFs."""
+    w = S.weights(TINY, 13)
+    m = Model(TINY, w)
+    cfg = StepConfig(warmup=5, coder="rans")
+    streams = [S.token_stream(13, j, n, TINY.vocab) for j, n in enumerate([0, 9, 60])]
+    buf = compress(m, streams, cfg, path_byte=0)
+    flags = container.unpack(buf)[0]
+    assert flags & container.FLAG_RANS
+    for a, b in zip(streams, decompress(m, buf, cfg)):
+        assert np.array_equal(a, b)
+    with pytest.raises(container.ContainerError):
+        decompress(m, buf, StepConfig(warmup=5))
+    for toks in streams[1:]:
+        r = compress_stream(m, toks, cfg)
+        a = compress_stream(m, toks, StepConfig(warmup=5))
+        assert abs(r["nbits"] - a["nbits"]) <= 96 + 0.02 * len(toks) + 32
+
+
 def test_ideal_bits_match_quantised_bits_closely():
     """With V = 97 the floors cost log2(T / (T - V)) ~ 8e-6 bits per token at
     most, so quantised and ideal code lengths agree closely."""
