@@ -98,9 +98,11 @@ typedef struct {
                                        with the per-token vocabulary pass and updates after
                                        it in order.  0 or 1: one position per step.  Changes
                                        no result; the decoder replays the same CDFs one
-                                       position at a time.  At most 32768; needs
-                                       prefill_rows x vocab x 4 bytes of logits on the
-                                       device. */
+                                       position at a time.  At most 32768; two chunks are
+                                       in flight (one forward beside the previous chunk's
+                                       vocabulary passes), so it needs 2 x prefill_rows x
+                                       (vocab x 4 + 1,584) bytes on the device for the
+                                       logits and the N-gram states. */
   int skip;                         /* 1: confidence-based LLM skip (Sec. 3.7): a token whose
                                        N-gram distribution has entropy below 1.5 bits is
                                        coded with p = p_ng, and only the N-gram learns from
