@@ -20,17 +20,19 @@ def gpu_bits(blob, n_streams):
     return [int.from_bytes(blob[off + 12 * j + 4: off + 12 * j + 8], "little") for j in range(n_streams)]
 
 
-@pytest.mark.parametrize("fmt,path,rule,n,tol", [
-    ("bf16", "gemv", "paper", 512, 5e-3),        # full model, single stream (first 512 tokens)
-    ("bf16", "gemv", "mixed_nll", 300, 5e-3),    # the differentiable update rule
-    ("bf16", "tc", "paper", 300, 5e-3),          # the tensor-core path
-    ("fp8", "tc", "paper", 300, None),           # FP8 E4M3: reported
+@pytest.mark.parametrize("fmt,path,rule,n,tol,prefill_rows", [
+    ("bf16", "gemv", "paper", 512, 5e-3, 0),        # full model, single stream (first 512 tokens)
+    ("bf16", "gemv", "mixed_nll", 300, 5e-3, 0),    # the differentiable update rule
+    ("bf16", "tc", "paper", 300, 5e-3, 0),          # the tensor-core path
+    ("bf16", "tc", "paper", 640, 5e-3, 4096),       # bench.py's configuration: prefill chunks of 512
+    ("fp8", "tc", "paper", 300, None, 0),           # FP8 E4M3: reported
 ])
-def test_full_model_bits_vs_oracle(gpu_lib, fmt, path, rule, n, tol):
+def test_full_model_bits_vs_oracle(gpu_lib, fmt, path, rule, n, tol, prefill_rows):
     nc = gpu_lib
     shape, seed = S.FULL, 1
     toks = S.token_stream(seed, 0, n, shape.vocab)
-    ctx = nc.Context(nc.make_config(shape, fmt=fmt, rule=rule, path=path), S.flat_weights(shape, seed))
+    ctx = nc.Context(nc.make_config(shape, fmt=fmt, rule=rule, path=path, prefill_rows=prefill_rows),
+                     S.flat_weights(shape, seed))
     blob = ctx.encode([toks])
     back = ctx.decode(blob)
     assert np.array_equal(back[0], toks)
