@@ -5,9 +5,11 @@
 // One stream is handled by a cluster of CTAs (kStepCluster for the per-token
 // step, kVocabCluster for the standalone quantiser); each CTA owns a
 // contiguous chunk of the vocabulary and each thread a contiguous run of E
-// symbols.  Reductions go thread -> warp (fixed xor tree) -> CTA (warps in
-// order) -> cluster (ranks in order through distributed shared memory), so
-// every result is independent of the batch, the slot and the launch.
+// symbols.  The standalone quantiser reduces thread -> warp (fixed xor tree)
+// -> CTA (warps in order) -> cluster (ranks in order through distributed
+// shared memory); the per-token step goes thread -> warp -> every CTA's inbox
+// (one cluster barrier) -> the same fixed reduction in every warp.  Every
+// result is independent of the batch, the slot and the launch.
 #include <algorithm>
 
 #include <cooperative_groups.h>
