@@ -40,6 +40,7 @@ def test_config_default_and_status(nc24):
     assert (c.n_layers, c.d_model, c.n_heads, c.n_kv_heads, c.d_ffn, c.vocab) == (30, 576, 9, 3, 1536, 49152)
     assert (c.ctx_len, c.slide, c.cdf_log2_total, c.floor, c.warmup) == (2048, 512, 24, 1, 100)
     assert abs(c.bias_lr - 1e-3) < 1e-9 and abs(c.w_llm_init - 0.85) < 1e-7
+    assert (c.prefill_rows, c.skip, c.coder) == (0, 0, nc24.NC_CODER_ARITH)
     assert nc24.nc_status_str(nc24.NC_ENUMERIC) == "NC_ENUMERIC"
 
 
@@ -50,6 +51,9 @@ def test_ctx_create_rejects_bad_config_without_gpu(nc24):
     h = C.c_void_p()
     assert nc24.lib.nc_ctx_create(C.byref(c), w.ctypes.data, w.nbytes, C.byref(h)) == nc24.NC_EINVAL
     c.d_model = 100
+    assert nc24.lib.nc_ctx_create(C.byref(c), w.ctypes.data, w.nbytes, C.byref(h)) == nc24.NC_EINVAL
+    c = nc24.nc_config_default()
+    c.coder = 7
     assert nc24.lib.nc_ctx_create(C.byref(c), w.ctypes.data, w.nbytes, C.byref(h)) == nc24.NC_EINVAL
     assert not h.value
 
