@@ -16,6 +16,8 @@ slow and written to be checked against the paper by eye:
 * ``ans``       - rANS coder on the same integer CDFs (the ANS coder named as
                   future work in Sec. 6), pure-Python integers.
 * ``container`` - NC05-style container (Sec. 3.12).
+* ``chunking``  - file-level split into chunks at line ends (Sec. 3.11), on
+                  token ids.
 * ``compress``  - the compression / decompression loop (Algorithm 1).
 * ``numerics``  - bf16 / fp8-e4m3 rounding used to derive the dequantised
                   weight variants from the FP32 canonical weights.
