@@ -337,6 +337,19 @@ int nc_ans_encode(const uint32_t* lo, const uint32_t* hi, int64_t n, int log2_to
 int nc_ans_decode(const uint8_t* data, size_t nbytes, const uint32_t* cdfs, int V, int64_t n, int log2_total,
                   int32_t* symbols);
 
+/* File-level chunking (Sec. 3.11) on token ids, for coding one file as up to
+ * n_chunks independent streams of one container (nc_encode): cut k of
+ * n_chunks - 1 falls just after the first line-ending token at or after
+ * position ceil(k n / n_chunks) - 1; cuts without a line end after them, at
+ * or before the previous cut, or at n are dropped.
+ *   tokens HOST int32[n] in [0, V); is_boundary HOST uint8[V], non-zero for
+ *   an id that ends a line (the tokenizer's knowledge, the caller's);
+ *   cuts HOST int64[n_chunks + 1] receives 0 = c_0 < ... < c_m = n, and
+ *   *n_chunks_out = m (0 for n = 0): chunk j is tokens[c_j, c_{j+1}).
+ * Errors: NC_EINVAL (NULL pointers, n_chunks < 1, an id out of range). */
+int nc_split_chunks(const int32_t* tokens, int64_t n, const uint8_t* is_boundary, int V, int n_chunks,
+                    int64_t* cuts, int* n_chunks_out);
+
 /* Mixed-distribution NLL L = -log(w0 p_tilde(t*) + w1 p_ng(t*)), w = softmax(theta),
  * p_tilde = softmax(z / tau + b), for n rows (the differentiable update rule).
  *   z, b, p_ng DEVICE float[n * V]; theta DEVICE float[n * 2]; target DEVICE int32[n];

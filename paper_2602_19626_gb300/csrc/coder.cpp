@@ -131,6 +131,26 @@ void RansDecoder::consume(uint32_t lo, uint32_t hi) {
 
 bool RansDecoder::finished() const { return x_ == kRansL && pos_ == nbytes_; }
 
+// ------------------------------------------------------- file-level chunks
+bool split_points(const int32_t* tokens, int64_t n, const uint8_t* is_boundary, int V, int n_chunks,
+                  std::vector<int64_t>* cuts) {
+  cuts->assign(1, 0);
+  if (n_chunks < 1) return false;
+  for (int64_t i = 0; i < n; ++i)
+    if (tokens[i] < 0 || tokens[i] >= V) return false;
+  if (n == 0) return true;
+  for (int k = 1; k < n_chunks; ++k) {
+    const int64_t target = (k * n + n_chunks - 1) / n_chunks;      // ceil(k n / N)
+    int64_t p = target > 0 ? target - 1 : 0;
+    while (p < n && !is_boundary[tokens[p]]) ++p;
+    if (p >= n) break;                                               // no line end after the target
+    const int64_t c = p + 1;
+    if (c > cuts->back() && c < n) cuts->push_back(c);
+  }
+  cuts->push_back(n);
+  return true;
+}
+
 // IEEE binary16 conversion, round to nearest even (for the 2-byte tau field).
 uint16_t float_to_half_bits(float f) {
   uint32_t x;

@@ -89,6 +89,15 @@ class RansDecoder {
   uint64_t mask_, x_ = 0;
 };
 
+// File-level chunking (Sec. 3.11) on token ids: cut k of n_chunks - 1 falls
+// just after the first line-ending token (is_boundary[id] != 0) at or after
+// position ceil(k n / n_chunks) - 1; cuts without a line end after them, at
+// or before the previous cut, or at n are dropped.  cuts receives
+// 0 = c_0 < ... < c_m = n (m <= n_chunks chunks; m = 0 for n = 0).
+// false for out-of-range ids or n_chunks < 1.
+bool split_points(const int32_t* tokens, int64_t n, const uint8_t* is_boundary, int V, int n_chunks,
+                  std::vector<int64_t>* cuts);
+
 // Container: "NC05", flags, tau (binary16), stream count, extension byte
 // (weight format | path << 4), then per stream (tokens, bits, bytes) as
 // little-endian uint32, then the payloads.

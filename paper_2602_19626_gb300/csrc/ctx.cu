@@ -1839,6 +1839,18 @@ extern "C" int nc_ac_decode(const uint8_t* bits, uint64_t nbits, const uint32_t*
   return NC_OK;
 }
 
+extern "C" int nc_split_chunks(const int32_t* tokens, int64_t n, const uint8_t* is_boundary, int V, int n_chunks,
+                               int64_t* cuts, int* n_chunks_out) {
+  if ((!tokens && n > 0) || !is_boundary || !cuts || !n_chunks_out || n < 0 || V < 1 || n_chunks < 1)
+    return NC_EINVAL;
+  std::vector<int64_t> c;
+  if (!split_points(tokens, n, is_boundary, V, n_chunks, &c)) return NC_EINVAL;
+  const int m = n == 0 ? 0 : (int)c.size() - 1;
+  for (int j = 0; j <= m; ++j) cuts[j] = c[j];
+  *n_chunks_out = m;
+  return NC_OK;
+}
+
 extern "C" int nc_ans_encode(const uint32_t* lo, const uint32_t* hi, int64_t n, int log2_total, uint8_t* out,
                              size_t* inout_nbytes) {
   if ((!lo || !hi) && n > 0) return NC_EINVAL;

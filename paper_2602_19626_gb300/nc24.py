@@ -87,6 +87,7 @@ _SIGS = {
     "nc_ac_encode": (C.c_int, [_P, _P, C.c_int64, C.c_int, _P, _SZP, C.POINTER(C.c_uint64)]),
     "nc_ac_decode": (C.c_int, [_P, C.c_uint64, _P, C.c_int, C.c_int64, C.c_int, _P]),
     "nc_ans_encode": (C.c_int, [_P, _P, C.c_int64, C.c_int, _P, _SZP]),
+    "nc_split_chunks": (C.c_int, [_P, C.c_int64, _P, C.c_int, C.c_int, _P, C.POINTER(C.c_int)]),
     "nc_ans_decode": (C.c_int, [_P, C.c_size_t, _P, C.c_int, C.c_int64, C.c_int, _P]),
     "nc_mix_nll_fwd": (C.c_int, [_P, _P, _P, _P, _P, _P, C.c_int, C.c_int, C.c_float, _P, _P]),
     "nc_mix_nll_bwd": (C.c_int, [_P, _P, _P, _P, _P, _P, _P, C.c_int, C.c_int, C.c_float, _P, _P, _P]),
@@ -195,6 +196,18 @@ def nc_ac_decode(data: bytes, nbits: int, cdfs: np.ndarray, log2_total: int) -> 
     if st:
         raise NcError(st, "nc_ac_decode")
     return sym
+
+
+def nc_split_chunks(tokens: np.ndarray, is_boundary: np.ndarray, n_chunks: int) -> np.ndarray:
+    """Cut positions 0 = c_0 < ... < c_m = n of a file's tokens (Sec. 3.11)."""
+    tokens = np.ascontiguousarray(tokens, dtype=np.int32)
+    bnd = np.ascontiguousarray(is_boundary, dtype=np.uint8)
+    cuts = np.zeros(n_chunks + 1, dtype=np.int64)
+    m = C.c_int(0)
+    st = lib.nc_split_chunks(_ptr(tokens), tokens.size, _ptr(bnd), bnd.size, n_chunks, _ptr(cuts), C.byref(m))
+    if st:
+        raise NcError(st, "nc_split_chunks")
+    return cuts[: m.value + 1] if m.value else cuts[:1]
 
 
 def nc_ans_encode(lo: np.ndarray, hi: np.ndarray, log2_total: int) -> bytes:
@@ -330,6 +343,19 @@ class Context:
         out = np.zeros(nb.value, dtype=np.uint8)
         self._check(lib.nc_encode(self.h, len(arrs), ptrs, _ptr(lens), _ptr(out), C.byref(nb)), "nc_encode")
         return out[: nb.value].tobytes()
+
+    def encode_file(self, tokens, is_boundary, n_chunks: int = 8) -> bytes:
+        """One file's tokens as up to n_chunks streams of one container, cut
+        at line-ending tokens (Sec. 3.11; nc_split_chunks)."""
+        toks = np.ascontiguousarray(tokens, dtype=np.int32)
+        c = nc_split_chunks(toks, is_boundary, n_chunks)
+        parts = [toks[c[i]:c[i + 1]] for i in range(len(c) - 1)] or [toks[:0]]
+        return self.encode(parts)
+
+    def decode_file(self, data: bytes) -> np.ndarray:
+        """Inverse of encode_file: the chunks in order, concatenated."""
+        parts = self.decode(data)
+        return np.concatenate(parts).astype(np.int32) if parts else np.zeros(0, np.int32)
 
     def encode_intervals(self, tokens_dev, offsets, lens, intervals_dev, stride: int, trace: bool = False):
         """Device half of encode: tokens_dev CUDA int32 (flat), offsets/lens

@@ -134,6 +134,22 @@ def test_host_rans_rejects_bad_input(nc24):
     assert list(nc24.nc_ans_decode(data, cdf, 8)) == [1]
 
 
+def test_split_chunks_matches_oracle(nc24):
+    """File-level chunking (Sec. 3.11): the library's cuts are the oracle's."""
+    from oracle import chunking
+    rng = np.random.default_rng(7)
+    V = 300
+    bnd = (rng.random(V) < 0.05).astype(np.uint8)
+    for n, N in ((0, 4), (1, 8), (37, 3), (5000, 8), (5000, 1), (999, 16)):
+        toks = rng.integers(0, V, n).astype(np.int32)
+        got = nc24.nc_split_chunks(toks, bnd, N)
+        assert list(got) == chunking.split_points(toks, bnd, N)
+    with pytest.raises(nc24.NcError):
+        nc24.nc_split_chunks(np.array([V], np.int32), bnd, 2)           # id out of range
+    with pytest.raises(nc24.NcError):
+        nc24.nc_split_chunks(np.array([1], np.int32), bnd, 0)
+
+
 def test_container_parse(nc24):
     import ctypes as C
     from oracle import container

@@ -285,6 +285,23 @@ def test_rans_container_roundtrip(nc, prefill_rows):
     assert abs(len(blob) - len(blob_ac)) * 8 <= 3 * 96 + 0.02 * sum(len(t) for t in streams) + 3 * 40
 
 
+def test_file_chunks_roundtrip(nc):
+    """A file coded as 8 chunks cut at line-ending tokens (Sec. 3.11) in one
+    container decodes to the original tokens; the chunks are independent
+    streams, so the container holds 8 of them."""
+    shape, seed = S.SMALL, 4
+    w = S.flat_weights(shape, seed)
+    toks = S.token_stream(seed, 0, 1500, shape.vocab)
+    bnd = np.zeros(shape.vocab, np.uint8)
+    bnd[np.unique(toks)[::7]] = 1                                       # some ids end a line
+    ctx = nc.Context(nc.make_config(shape, fmt="bf16", max_streams=8), w)
+    blob = ctx.encode_file(toks, bnd, 8)
+    n = int.from_bytes(blob[7:9], "little")
+    assert n == len(nc.nc_split_chunks(toks, bnd, 8)) - 1
+    assert np.array_equal(ctx.decode_file(blob), toks)
+    ctx.close()
+
+
 def test_multi_stream_container_ragged(nc):
     """Ragged lengths, including empty and one-token streams, BF16."""
     shape, seed = S.SMALL, 3
