@@ -23,7 +23,7 @@ def has_gpu() -> bool:
 
 @pytest.fixture(scope="session")
 def gpu_lib():
-    """The loaded C-ABI library on a GPU machine (fails loudly if it is missing)."""
+    """The loaded C-ABI library on a machine with a GPU (fails loudly if it is missing)."""
     if not has_gpu():
         pytest.fail("a GPU test ran without a CUDA device")
     from paper_2602_19626_gb300 import nc24
