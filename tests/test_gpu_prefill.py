@@ -22,13 +22,13 @@ def nc(gpu_lib):
     return gpu_lib
 
 
-def intervals(nc, shape, w, fmt, path, toks, prefill_rows, max_streams):
+def intervals(nc, shape, w, fmt, path, toks, prefill_rows, max_streams, rule="paper"):
     lens = np.array([len(t) for t in toks], dtype=np.int64)
     offs = np.concatenate([[0], np.cumsum(lens)[:-1]]).astype(np.int64)
     flat = torch.from_numpy(np.concatenate(toks).astype(np.int32)).cuda()
     stride = max(int(lens.max()), 1)
     ctx = nc.Context(nc.make_config(shape, fmt=fmt, path=path, warmup=20, max_streams=max_streams,
-                                    prefill_rows=prefill_rows), w)
+                                    prefill_rows=prefill_rows, rule=rule), w)
     iv = torch.full((len(toks), stride, 2), -1, dtype=torch.int32, device="cuda")
     ctx.encode_intervals(flat, offs, lens, iv, stride)
     out = iv.cpu().numpy()
@@ -49,6 +49,19 @@ def test_prefill_intervals_equal_decode(nc, fmt, path):
     assert np.array_equal(got, ref)
     one = intervals(nc, shape, w, fmt, path, toks[:1], 1024, 1)
     assert np.array_equal(one[0], ref[0])
+
+
+@pytest.mark.parametrize("path", ["gemv", "tc"])
+def test_prefill_mixed_nll_equals_decode(nc, path):
+    """The mixed-NLL update rule (its head step waits for the mixer, so the
+    prefill loop takes a second barrier per position): prefill chunks give the
+    decode intervals exactly."""
+    shape, seed = S.SMALL, 9
+    w = S.flat_weights(shape, seed)
+    toks = [S.token_stream(seed, j, n, shape.vocab) for j, n in enumerate([600, 97])]
+    ref = intervals(nc, shape, w, "bf16", path, toks, 0, 2, rule="mixed_nll")
+    got = intervals(nc, shape, w, "bf16", path, toks, 256, 2, rule="mixed_nll")
+    assert np.array_equal(got, ref)
 
 
 def test_prefill_full_model_single_stream(nc):
