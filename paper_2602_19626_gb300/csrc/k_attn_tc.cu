@@ -15,9 +15,12 @@
 // The rows of the MMA tile are (query row, head) pairs, padding rows zero.
 // A row's products do not depend on the other rows of the tile, so a query
 // computed alone (decode, one row) and among the rows of a prefill gives the
-// same bits: one kernel serves both.  These tiles have 3 to 32 rows, which is
-// why the warp-level MMA is used here rather than tcgen05 with its 64- or
-// 128-row tiles held in tensor memory.
+// same bits.  Two kernels share the per-block code: k_attn_tc (decode, and
+// prefill groups of up to 8 rows: block partials in shared memory) and
+// k_attn_pf (prefill groups of 32 positions: each warp walks its 16-row tile
+// through a chunk's blocks).  A decode step has 3 rows per KV head and must
+// give the prefill's bits, which is why the warp-level MMA is used here rather
+// than tcgen05 with its 64- or 128-row tiles and its own accumulation order.
 #include <cooperative_groups.h>
 #include <cuda_bf16.h>
 
