@@ -291,8 +291,8 @@ def kernel_sources_hash() -> str:
 
 def prefill_positions(wl, n_streams: int, max_len: int) -> int:
     """Positions per model forward: the library's rule (largest power of two m
-    with n m <= prefill_rows dividing the window and the slide, below the
-    longest stream), or 1."""
+    with n m <= prefill_rows dividing the window and the slide, doubling only
+    while m is below the longest stream), or 1."""
     shape, rows = wl["shape"], wl.get("prefill_rows", 0)
     if rows < 2:
         return 1
@@ -300,6 +300,17 @@ def prefill_positions(wl, n_streams: int, max_len: int) -> int:
     while 2 * m * n_streams <= rows and shape.slide % (2 * m) == 0 and shape.ctx_len % (2 * m) == 0 and m < max_len:
         m *= 2
     return m if m >= 2 else 1
+
+
+def dominant_kind(trace, wl, n_streams: int, max_len: int):
+    """The traced kernel kind the roofline reports, and the kinds left out.
+    With the prefill, a chunk's N-gram pass runs beside its forward and its
+    vocabulary loop beside the next chunk's forward (the trace runs them in
+    order): the dominant kind is taken on the forward, the critical path of
+    the timed run."""
+    beside = ["ngram_update", "vocab"] if prefill_positions(wl, n_streams, max_len) >= 2 else []
+    dom = max([k for k in trace if k["name"] not in beside] or trace, key=lambda k: k["ms"])
+    return dom, beside
 
 
 def run_gpu(args, wl):
@@ -375,12 +386,7 @@ def run_gpu(args, wl):
     try:
         trace = ctx.encode_intervals(tok_dev, offs, lens, iv, stride, trace=True)
         tot_ms = sum(k["ms"] for k in trace) or 1.0
-        # with the prefill, a chunk's N-gram pass runs beside its forward and
-        # its vocabulary loop beside the next chunk's forward (the trace runs
-        # them in order): the dominant kernel is taken on the forward, the
-        # critical path of the timed run
-        beside = ["ngram_update", "vocab"] if prefill_positions(wl, len(streams), int(lens.max())) >= 2 else []
-        dom = max([k for k in trace if k["name"] not in beside] or trace, key=lambda k: k["ms"])
+        dom, beside = dominant_kind(trace, wl, len(streams), int(lens.max()))
         n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
         roofline = roofline_of(dom, wl.get("path", "gemv"), wl["fmt"], n_sm, 2070.0)
         roofline["share"] = dom["ms"] / tot_ms

@@ -1080,7 +1080,8 @@ static uint8_t path_byte(const nc_config& c) { return (uint8_t)(c.weight_fmt | (
 // Positions per prefill forward for n streams: the largest power of two m
 // with n m <= prefill_rows that divides the window length L and the slide C
 // (so no chunk of positions crosses a slide: every row of a forward sees its
-// window start fixed) and is not above the longest stream; 0 = no prefill.
+// window start fixed), doubling only while m is below the longest stream;
+// 0 = no prefill.
 static int prefill_chunk(const nc_ctx* ctx, int n, int64_t max_len) {
   const Dims& D = ctx->D;
   if (ctx->P < 2 || n < 1) return 0;
