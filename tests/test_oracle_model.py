@@ -123,6 +123,50 @@ def test_slide_keeps_window_and_relabels():
     assert max(ns) == L and cache.slides == (40 - L) // C + (1 if (40 - L) % C else 0)
 
 
+def test_slide_relabelling_equals_absolute_rotation():
+    """Across slides the oracle rotates the query and the cached keys at their
+    relabelled positions.  Attention computed instead at the tokens' absolute
+    positions, with an independent complex-exponential rotation and no
+    relabelling, gives the same output (RoPE scores depend only on position
+    differences): the window slide is a start bump for an absolute-position
+    cache, which is what the GPU's ring buffer does (Sec. 3.9)."""
+    w = S.weights(TINY, 11)
+    m = Model(TINY, w)
+    dh, hq, hkv = TINY.d_head, TINY.n_heads, TINY.n_kv_heads
+    inv = TINY.rope_theta ** (-2.0 * np.arange(dh // 2) / dh)
+
+    def rot(x, pos):                                  # x [..., dh] at absolute positions pos
+        z = (x[..., : dh // 2] + 1j * x[..., dh // 2:]) * np.exp(1j * np.multiply.outer(pos, inv))
+        return np.concatenate([z.real, z.imag], axis=-1)
+
+    state = {"abs": 0, "checked": 0}
+    orig = m.attend
+
+    def attend(q, k_raw, v):
+        out = orig(q, k_raw, v)
+        n, a = k_raw.shape[0], state["abs"]
+        pos = np.arange(a - n + 1, a + 1, dtype=np.float64)     # absolute positions of the window
+        qa = rot(q, np.full(hq, float(a)))
+        ka = rot(k_raw, pos[:, None] * np.ones((1, hkv)))
+        o = np.empty_like(out)
+        for h in range(hq):
+            g = h // (hq // hkv)
+            sc = ka[:, g, :] @ qa[h] / np.sqrt(dh)
+            e = np.exp(sc - sc.max())
+            o[h] = (e / e.sum()) @ v[:, g, :]
+        np.testing.assert_allclose(out, o, rtol=1e-9, atol=1e-12)
+        state["checked"] += 1
+        return out
+
+    m.attend = attend
+    cache = m.new_cache()
+    toks = [0] + list(S.token_stream(11, 2, 60, TINY.vocab))
+    for i, t in enumerate(toks):
+        state["abs"] = i
+        m.step(cache, t)
+    assert cache.slides >= 10 and state["checked"] == len(toks) * TINY.n_layers
+
+
 def test_dequantised_formats():
     w = S.weights(TINY, 7)
     b = Model(TINY, w, "bf16").w["l0.wq"]
