@@ -30,6 +30,8 @@ sys.path.insert(0, ROOT)
 
 import synthetic as S  # noqa: E402
 
+METRIC = "tokens/s compressed on 1 GB300 (batched vs plain) at bpb within 0.5% of FP64 oracle"
+
 # prefill_rows: the encoder runs the model over up to this many (stream,
 # position) rows per forward pass (0: one position per step).  It changes no
 # coded bit; the decoder always steps one position at a time.
@@ -66,7 +68,23 @@ WORKLOADS = {
     # FP8 E4M3 weights, 1,024 streams x 4,096 tokens (first 256 tokens per stream)
     "fp8_tc_1024_256": dict(shape=S.FULL, fmt="fp8", seed=4, n_streams=1024, length=4096, cap=256, path="tc",
                             prefill_rows=4096),
+    # the same 1,024 FP8 streams cut to their first 1,024 tokens: the batch
+    # stays full and the windows grow to half the context
+    "fp8_tc_1024x1024": dict(shape=S.FULL, fmt="fp8", seed=4, n_streams=1024, length=4096, cap=1024, path="tc",
+                             prefill_rows=4096),
+    # the precision workload as stated: 1,024 FP8 streams x 4,096 tokens
+    "fp8_tc_1024x4096": dict(shape=S.FULL, fmt="fp8", seed=4, n_streams=1024, length=4096, path="tc",
+                             prefill_rows=4096),
+    # differentiation: 64 BF16 streams x 4,096 tokens, the head and mixer
+    # updated by the mixed-NLL gradient (hand-written backward in the loop)
+    "diff_bf16_tc_64x4096": dict(shape=S.FULL, fmt="bf16", seed=3, n_streams=64, length=4096, path="tc",
+                                 prefill_rows=4096, rule="mixed_nll"),
 }
+
+# The headline metric's denominator and numerators: batched BF16 / FP8
+# throughput as a multiple of the plain single-stream FP32 path.
+PLAIN = "full_fp32_single"
+BATCHED = ("batched_bf16_tc", "fp8_tc_1024x1024")
 
 
 def dist_env():
@@ -89,31 +107,49 @@ def workload_lengths(wl, world: int = 1):
     return lens
 
 
+def _stream_job(args):
+    seed, j, n, vocab = args
+    return S.token_stream(seed, j, n, vocab)
+
+
 def workload_streams(wl, world: int = 1, rank: int = 0):
-    """This rank's share of the job's streams (longest-first bin packing)."""
+    """This rank's share of the job's streams (longest-first bin packing).
+    Large workloads are drawn by a pool of spawned worker processes (the
+    generator is a per-token Python loop)."""
     from paper_2602_19626_gb300.partition import partition_streams
     shape = wl["shape"]
     lens = workload_lengths(wl, world)
-    mine = partition_streams(lens, world)[rank]
-    return [S.token_stream(wl["seed"], j, int(lens[j]), shape.vocab) for j in sorted(mine)]
+    mine = sorted(partition_streams(lens, world)[rank])
+    jobs = [(wl["seed"], j, int(lens[j]), shape.vocab) for j in mine]
+    if sum(int(lens[j]) for j in mine) < 200_000:
+        return [_stream_job(a) for a in jobs]
+    import multiprocessing as mp
+    from concurrent.futures import ProcessPoolExecutor
+    with ProcessPoolExecutor(max_workers=min(16, os.cpu_count() or 1), mp_context=mp.get_context("spawn")) as ex:
+        return list(ex.map(_stream_job, jobs, chunksize=8))
 
 
 # ------------------------------------------------------------- oracle (CPU)
 
 def oracle_rate(wl, budget_s: float, first_tokens: int | None = None):
     """FP64 oracle on the host cores: tokens/s over the first tokens of the
-    workload's first stream, sized to take about budget_s seconds."""
+    workload's first stream, sized to take about budget_s seconds.  Returns
+    (tokens, seconds, interval bits): the last is sum -log2((hi - lo) / T)
+    over the coded intervals, the code length the coder's intervals give."""
     from oracle.compress import StepConfig, StreamState
     from oracle.model import Model
     shape = wl["shape"]
     toks = S.token_stream(wl["seed"], 0, int(workload_lengths(wl)[0]), shape.vocab)
     model = Model(shape, S.weights(shape, wl["seed"]), wl["fmt"])
-    st = StreamState.new(model, StepConfig())
+    cfg = StepConfig(rule=wl.get("rule", "paper"))
+    st = StreamState.new(model, cfg)
     t0 = time.perf_counter()
     n = 0
+    bits = 0.0
     for t in toks:
-        st.predict()
+        _, _, cdf = st.predict()
         st.update(int(t))
+        bits += -np.log2((int(cdf[int(t) + 1]) - int(cdf[int(t)])) / cfg.T)
         n += 1
         el = time.perf_counter() - t0
         if first_tokens is not None:
@@ -122,7 +158,34 @@ def oracle_rate(wl, budget_s: float, first_tokens: int | None = None):
         elif el >= budget_s:
             break
     el = time.perf_counter() - t0
-    return n, el
+    return n, el, bits
+
+
+def interval_bits(iv_row, n: int, log2_total: int = 24) -> float:
+    """sum -log2((hi - lo) / T) over the first n coded intervals of one stream."""
+    lo = iv_row[:n, 0].astype(np.float64)
+    hi = iv_row[:n, 1].astype(np.float64)
+    return float(np.sum(log2_total - np.log2(hi - lo)))
+
+
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo)."""
+    try:
+        out = subprocess.run(["lscpu"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True,
+                             timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for line in fh:
+                if line.lower().startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return "unknown"
 
 
 def blas_threads() -> int:
@@ -142,21 +205,21 @@ def run_reference(args, wl):
         oracle_rate(wl, 0.0, first_tokens=2)
     n_tot, t_tot = 0, 0.0
     for _ in range(args.steps):
-        n, el = oracle_rate(wl, budget)
+        n, el, _ = oracle_rate(wl, budget)
         n_tot += n
         t_tot += el
     v = n_tot / t_tot
     sample = (f"first {n_tot // max(args.steps, 1)} tokens of the first stream per step "
               f"(about {budget:.0f} s each), FP64 oracle on {wl['fmt']}-dequantised weights")
     line = {
-        "impl": "reference", "metric": "tokens/s compressed", "value": v, "unit": "tokens/s",
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "tokens/s",
         "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1000.0 * t_tot / max(args.steps, 1), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": args.workload, "model": "smollm2-135m-shape random-init",
                    "streams": wl["n_streams"], "tokens": int(workload_lengths(wl).sum())},
-        "cpu_baseline": {"value": v, "unit": "tokens/s", "cores": blas_threads(), "kind": "oracle",
-                         "sample": sample},
+        "cpu_baseline": {"value": v, "unit": "tokens/s", "cores": blas_threads(), "cpu": cpu_model(),
+                         "kind": "oracle", "sample": sample},
         "e2e": {"value": v, "unit": "tokens/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -334,7 +397,8 @@ def run_gpu(args, wl):
     stride = int(lens.max())
     cstream = torch.cuda.Stream()
     cfg = nc24.make_config(shape, fmt=wl["fmt"], max_streams=len(streams), device=dev, stream=cstream,
-                           path=wl.get("path", "gemv"), prefill_rows=wl.get("prefill_rows", 0))
+                           path=wl.get("path", "gemv"), prefill_rows=wl.get("prefill_rows", 0),
+                           rule=wl.get("rule", "paper"))
     ctx = nc24.Context(cfg, S.flat_weights(shape, wl["seed"]))
     tok_dev = torch.from_numpy(flat).to(f"cuda:{dev}")
     iv = torch.empty((len(streams), stride, 2), dtype=torch.int32, device=f"cuda:{dev}")
@@ -409,10 +473,20 @@ def run_gpu(args, wl):
     t0 = time.perf_counter()
     e2e_steps = max(1, min(args.steps, 3))
     nbytes = 0
+    blob = b""
     for _ in range(e2e_steps):
         blob = ctx.encode(host_streams)
         nbytes = len(blob)
     e2e_s = time.perf_counter() - t0
+    # the decoder (one position per step: it learns each token from the
+    # coder) on the same container, through nc_decode
+    decode = None
+    if rank == 0 and not args.no_decode:
+        t0 = time.perf_counter()
+        back = ctx.decode(blob)
+        dec_s = time.perf_counter() - t0
+        decode = {"value": n_tok / dec_s, "unit": "tokens/s", "s": dec_s,
+                  "lossless": bool(all(np.array_equal(a, b) for a, b in zip(back, host_streams)))}
     if ws > 1:
         t = torch.tensor([e2e_s], device=f"cuda:{dev}", dtype=torch.float64)
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
@@ -430,14 +504,30 @@ def run_gpu(args, wl):
         except Exception as exc:
             extras[name] = {"error": str(exc)[:200]}
     cpu = None
+    bpb = None
     if rank == 0 and not args.no_cpu_baseline:
-        n, el = oracle_rate(wl, args.cpu_budget)
-        cpu = {"value": n / el, "unit": "tokens/s", "cores": blas_threads(), "kind": "oracle",
+        n, el, obits = oracle_rate(wl, args.cpu_budget)
+        cpu = {"value": n / el, "unit": "tokens/s", "cores": blas_threads(), "cpu": cpu_model(), "kind": "oracle",
                "sample": f"first {n} tokens of the workload's first stream, FP64 oracle on "
                          f"{wl['fmt']}-dequantised weights, {el:.1f} s"}
+        # the timed run's coded intervals on the same prefix against the
+        # oracle's: the "bpb within 0.5% of the FP64 oracle" of the metric
+        gbits = interval_bits(ivh[0], n)
+        nbyt = S.n_bytes(streams[0][:n])
+        rel = (gbits - obits) / obits
+        bpb = {"tokens": n, "gpu_bits": gbits, "oracle_bits": obits, "gpu_bpb": gbits / nbyt,
+               "oracle_bpb": obits / nbyt, "rel": rel, "within_0.5pct": bool(abs(rel) <= 5e-3),
+               "what": "sum -log2((hi - lo) / 2^24) of the timed run's intervals and the oracle's over the "
+                       "cpu_baseline's prefix of the first stream"}
+    ratios = {}
+    if PLAIN in extras and "value" in extras[PLAIN]:
+        for name in BATCHED:
+            if name in extras and "value" in extras[name]:
+                ratios[name] = extras[name]["value"] / extras[PLAIN]["value"]
+        ratios["headline"] = value / extras[PLAIN]["value"]
     if rank == 0:
         line = {
-            "metric": "tokens/s compressed", "value": value, "unit": "tokens/s", "n_gpus": ws,
+            "metric": METRIC, "value": value, "unit": "tokens/s", "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "bf16" if wl.get("path", "gemv") == "tc" else "f32",
@@ -452,7 +542,9 @@ def run_gpu(args, wl):
                              "forward, and each timed step codes the whole workload"},
             "gpu_launches": launches_per_step * args.steps,
             "roofline": roofline, "kernels": kernels, "clocks": clocks, "e2e": e2e,
-            "cpu_baseline": cpu, "intervals_valid": ok,
+            "cpu_baseline": cpu, "bpb_vs_oracle": bpb, "intervals_valid": ok,
+            "decode": decode,
+            "batched_over_plain": ratios or None,
         }
         if extras:
             line["extra"] = extras
@@ -475,7 +567,8 @@ def extra_throughput(name, dev):
     stride = int(lens.max())
     cstream = torch.cuda.Stream()
     cfg = nc24.make_config(shape, fmt=wl["fmt"], max_streams=wl["n_streams"], device=dev, stream=cstream,
-                           path=wl.get("path", "gemv"), prefill_rows=wl.get("prefill_rows", 0))
+                           path=wl.get("path", "gemv"), prefill_rows=wl.get("prefill_rows", 0),
+                           rule=wl.get("rule", "paper"))
     ctx = nc24.Context(cfg, S.flat_weights(shape, wl["seed"]))
     tok_dev = torch.from_numpy(flat).to(f"cuda:{dev}")
     iv = torch.empty((wl["n_streams"], stride, 2), dtype=torch.int32, device=f"cuda:{dev}")
@@ -490,9 +583,13 @@ def extra_throughput(name, dev):
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
     ctx.close()
+    ivh = iv.cpu().numpy().view(np.uint32)
+    bits = sum(interval_bits(ivh[j], int(lens[j])) for j in range(len(lens)))
     return {"value": float(lens.sum()) / (ms / 1000.0), "unit": "tokens/s", "ms": ms,
             "streams": wl["n_streams"], "tokens": int(lens.sum()), "weights": wl["fmt"],
-            "path": wl.get("path", "gemv")}
+            "path": wl.get("path", "gemv"), "rule": wl.get("rule", "paper"),
+            "positions_per_forward": prefill_positions(wl, len(lens), int(lens.max())),
+            "bits_per_token": bits / float(lens.sum())}
 
 
 def main():
@@ -507,8 +604,9 @@ def main():
     ap.add_argument("--tokens", type=int, default=0,
                     help="cut every stream to this many tokens (short runs for profiling)")
     ap.add_argument("--extra", nargs="*",
-                    default=["full_bf16_single_tc_stepwise", "full_bf16_single_stepwise", "batched_bf16_tc_512"],
+                    default=[PLAIN, *BATCHED, "diff_bf16_tc_64x4096", "full_bf16_single_tc_stepwise"],
                     help="further workloads timed once each and reported under 'extra'")
+    ap.add_argument("--no-decode", action="store_true", help="skip timing nc_decode on the headline container")
     args = ap.parse_args()
     wl = WORKLOADS[args.workload]
     if args.tokens > 0:

@@ -215,6 +215,21 @@ int nc_encode_intervals(nc_ctx* ctx, int n_streams, const int32_t* tokens_dev,
                         const int64_t* offsets, const int64_t* lens, uint32_t* intervals_dev,
                         int64_t stride, nc_trace* trace);
 
+/* nc_encode_intervals that also returns the intermediate distributions of
+ * one token of every stream, as the encoder computed them (the prefill
+ * forward when prefill_rows > 1, else the per-token step): at token index
+ * probe_pos (0-based) of each stream with more than probe_pos tokens, row j
+ * of z (the logits, Eq. lm), p_tilde (the biased LLM distribution, Sec. 3.6),
+ * p_ng (the N-gram distribution, Sec. 3.4) and p (the binary32 probabilities
+ * handed to the quantiser) receives stream j's values.  z, p_tilde, p_ng, p:
+ * DEVICE float[n_streams * V] each, any may be NULL; rows of streams that
+ * are too short are left as they were.  Synchronous like nc_encode_intervals
+ * without a trace.  Errors: those of nc_encode_intervals, and NC_EINVAL for
+ * probe_pos < 0 or a probe buffer that is not device memory. */
+int nc_encode_probe(nc_ctx* ctx, int n_streams, const int32_t* tokens_dev, const int64_t* offsets,
+                    const int64_t* lens, uint32_t* intervals_dev, int64_t stride, int64_t probe_pos, float* z,
+                    float* p_tilde, float* p_ng, float* p);
+
 /* Mirror of nc_encode.  tokens_out: HOST array of HOST int32 pointers, one
  * per stream, each with room for that stream's token count; lens_out HOST
  * int64[stream count].  A NULL tokens_out only reads the header: lens_out
@@ -260,7 +275,9 @@ int nc_probs_to_cdf(const float* p, int n, int V, int log2_total, uint32_t floor
  * the process exits.
  *  - n > NC_NOALLOC_MAX_ROWS returns NC_EINVAL (split the rows over calls).
  *  - The first call on a device looks up the array's device address
- *    (cudaGetSymbolAddress); make that first call before any stream capture.
+ *    (cudaGetSymbolAddress) and keeps it; make that first call before any
+ *    stream capture.  The first call after a reset of the device's context
+ *    (cudaDeviceReset) looks it up again.
  *  - Every call, on any stream, shares the one array; each call clears the
  *    words it uses.  Calls whose GPU work overlaps (another host thread, or
  *    another stream) race on it: serialise them.

@@ -1097,7 +1097,7 @@ static int prefill_chunk(const nc_ctx* ctx, int n, int64_t max_len) {
 // are those of one position per step.  Streams sorted longest first.
 static int encode_prefill(nc_ctx* ctx, int n, int m0, const int32_t* tok_dev, const int64_t* offs_dev,
                           const int64_t* lens_dev, const std::vector<int64_t>& lens_h, uint32_t* intervals,
-                          int64_t stride, nc_trace* trace) {
+                          int64_t stride, nc_trace* trace, const VocabIO& probe) {
   const Dims& D = ctx->D;
   cudaStream_t s = ctx->stream;
   int64_t max_len = 0;
@@ -1106,7 +1106,7 @@ static int encode_prefill(nc_ctx* ctx, int n, int m0, const int32_t* tok_dev, co
   int m_max = m0;
   while ((int64_t)2 * m_max <= ctx->P && D.C % (2 * m_max) == 0 && D.L % (2 * m_max) == 0 && m_max < max_len)
     m_max *= 2;
-  VocabIO io{};
+  VocabIO io = probe;
   io.predict = 1;
   io.update = 1;
   io.ngram = 1;
@@ -1296,7 +1296,7 @@ static int encode_prefill(nc_ctx* ctx, int n, int m0, const int32_t* tok_dev, co
 // step are a prefix).  intervals: DEVICE uint32[n][stride][2].
 static int encode_device(nc_ctx* ctx, int n, const std::vector<int>& slot_of, const int32_t* tok_dev,
                          const int64_t* offs_dev, const int64_t* lens_dev, const std::vector<int64_t>& lens_h,
-                         uint32_t* intervals, int64_t stride, nc_trace* trace) {
+                         uint32_t* intervals, int64_t stride, nc_trace* trace, const VocabIO& probe) {
   const Dims& D = ctx->D;
   cudaStream_t s = ctx->stream;
   int64_t max_len = 0;
@@ -1304,10 +1304,10 @@ static int encode_device(nc_ctx* ctx, int n, const std::vector<int>& slot_of, co
   for (int j = 0; j < n; ++j) ctx->h_i32[1 + j] = slot_of[j];
   NC_TRY(cudaMemcpyAsync(ctx->d_slots, ctx->h_i32 + 1, (size_t)n * 4, cudaMemcpyHostToDevice, s));
   const int m = prefill_chunk(ctx, n, max_len);
-  if (m >= 2) return encode_prefill(ctx, n, m, tok_dev, offs_dev, lens_dev, lens_h, intervals, stride, trace);
+  if (m >= 2) return encode_prefill(ctx, n, m, tok_dev, offs_dev, lens_dev, lens_h, intervals, stride, trace, probe);
   Batch b = make_batch(ctx);
   b.Bmax = n;
-  VocabIO io{};
+  VocabIO io = probe;
   io.predict = 1;
   io.update = 1;
   io.ngram = 1;
@@ -1410,8 +1410,11 @@ static void close_rows(nc_ctx* ctx, const std::vector<int32_t>& ids) {
     if (id >= 0 && ctx->id2slot.count(id)) nc_stream_close(ctx, id);
 }
 
-extern "C" int nc_encode_intervals(nc_ctx* ctx, int n_streams, const int32_t* tokens_dev, const int64_t* offsets,
-                                   const int64_t* lens, uint32_t* intervals_dev, int64_t stride, nc_trace* trace) {
+// nc_encode_intervals, with the probes of `probe` (probe_tok > 0) written to
+// the caller's rows.
+static int encode_intervals(nc_ctx* ctx, int n_streams, const int32_t* tokens_dev, const int64_t* offsets,
+                            const int64_t* lens, uint32_t* intervals_dev, int64_t stride, nc_trace* trace,
+                            VocabIO probe) {
   if (!ctx) return NC_EINVAL;
   if (ctx->poisoned) return fail(ctx, NC_ESTATE, "context poisoned by an earlier CUDA error");
   if (!tokens_dev || !offsets || !lens || !intervals_dev || n_streams < 1) return fail(ctx, NC_EINVAL, "bad arguments");
@@ -1437,13 +1440,15 @@ extern "C" int nc_encode_intervals(nc_ctx* ctx, int n_streams, const int32_t* to
   do {
     if (st != NC_OK) break;
     // row r reads stream order[r]: offsets in rows, intervals written per row
-    std::vector<int64_t> h_meta(2 * n_streams);
+    // row r reads stream order[r]: offsets, lengths and the probes' rows
+    std::vector<int64_t> h_meta(3 * n_streams);
     for (int r = 0; r < n_streams; ++r) {
       h_meta[r] = offsets[order[r]];
       h_meta[n_streams + r] = lens[order[r]];
+      h_meta[2 * n_streams + r] = order[r];
       lens_h[r] = lens[order[r]];
     }
-    if (cudaMalloc(&meta, 2 * n_streams * 8) != cudaSuccess) {
+    if (cudaMalloc(&meta, 3 * n_streams * 8) != cudaSuccess) {
       st = fail(ctx, NC_ENOMEM, "meta allocation");
       break;
     }
@@ -1453,12 +1458,14 @@ extern "C" int nc_encode_intervals(nc_ctx* ctx, int n_streams, const int32_t* to
       st = fail(ctx, NC_ENOMEM, "interval staging allocation");
       break;
     }
-    if (cudaMemcpyAsync(meta, h_meta.data(), 2 * n_streams * 8, cudaMemcpyHostToDevice, ctx->stream) != cudaSuccess) {
+    if (cudaMemcpyAsync(meta, h_meta.data(), 3 * n_streams * 8, cudaMemcpyHostToDevice, ctx->stream) != cudaSuccess) {
       st = fail_cuda(ctx, cudaErrorUnknown, "meta upload");
       break;
     }
     uint32_t* target = identity ? intervals_dev : iv_rows;
-    st = encode_device(ctx, n_streams, slot_of, tokens_dev, meta, meta + n_streams, lens_h, target, stride, trace);
+    probe.probe_row = meta + 2 * n_streams;
+    st = encode_device(ctx, n_streams, slot_of, tokens_dev, meta, meta + n_streams, lens_h, target, stride, trace,
+                       probe);
     if (st != NC_OK) break;
     if (!identity)
       for (int r = 0; r < n_streams; ++r)
@@ -1474,6 +1481,27 @@ extern "C" int nc_encode_intervals(nc_ctx* ctx, int n_streams, const int32_t* to
   cudaFree(iv_rows);
   close_rows(ctx, ids);
   return st;
+}
+
+extern "C" int nc_encode_intervals(nc_ctx* ctx, int n_streams, const int32_t* tokens_dev, const int64_t* offsets,
+                                   const int64_t* lens, uint32_t* intervals_dev, int64_t stride, nc_trace* trace) {
+  return encode_intervals(ctx, n_streams, tokens_dev, offsets, lens, intervals_dev, stride, trace, VocabIO{});
+}
+
+extern "C" int nc_encode_probe(nc_ctx* ctx, int n_streams, const int32_t* tokens_dev, const int64_t* offsets,
+                               const int64_t* lens, uint32_t* intervals_dev, int64_t stride, int64_t probe_pos,
+                               float* z, float* p_tilde, float* p_ng, float* p) {
+  if (!ctx) return NC_EINVAL;
+  if (probe_pos < 0) return fail(ctx, NC_EINVAL, "probe position below 0");
+  for (float* q : {z, p_tilde, p_ng, p})
+    if (q && !is_device_ptr(q)) return fail(ctx, NC_EINVAL, "probe buffers must be device memory");
+  VocabIO probe{};
+  probe.probe_tok = probe_pos + 1;
+  probe.probe_z = z;
+  probe.probe_pt = p_tilde;
+  probe.probe_png = p_ng;
+  probe.probe_p = p;
+  return encode_intervals(ctx, n_streams, tokens_dev, offsets, lens, intervals_dev, stride, nullptr, probe);
 }
 
 extern "C" int nc_encode(nc_ctx* ctx, int n_streams, const int32_t* const* tokens, const int64_t* lens,
@@ -1549,7 +1577,8 @@ extern "C" int nc_encode(nc_ctx* ctx, int n_streams, const int32_t* const* token
     }
     std::vector<int64_t> lens_rows(n_streams);
     for (int r = 0; r < n_streams; ++r) lens_rows[r] = lens[order[r]];
-    st = encode_device(ctx, n_streams, slot_of, tok_dev, meta, meta + n_streams, lens_rows, iv, max_len, nullptr);
+    st = encode_device(ctx, n_streams, slot_of, tok_dev, meta, meta + n_streams, lens_rows, iv, max_len, nullptr,
+                       VocabIO{});
     if (st != NC_OK) break;
     h_iv.resize((size_t)n_streams * max_len * 2);
     if (cudaMemcpyAsync(h_iv.data(), iv, h_iv.size() * 4, cudaMemcpyDeviceToHost, ctx->stream) != cudaSuccess) {

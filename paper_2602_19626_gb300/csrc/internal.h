@@ -204,6 +204,8 @@ struct VocabIO {
   float* probe_pt;
   float* probe_png;
   float* probe_p;
+  int64_t probe_tok;        // 0: probe every step; k > 0: only the stream's k-th token (1-based)
+  const int64_t* probe_row; // probe row of batch row j (nullptr: row j)
   int predict;              // quantise (and write cdf / intervals)
   int update;               // apply head + mixer update with b.obs
   int ngram;                // with update: also the N-gram update and the stream's bookkeeping

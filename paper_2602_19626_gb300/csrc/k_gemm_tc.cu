@@ -13,8 +13,10 @@
 // do not depend on how many streams share a step.
 //
 // Every wait on an mbarrier is bounded; a wait that gives up records an error
-// in the context's status word, skips the remaining work and still frees the
-// tensor memory it holds.
+// in the context's status word and skips the remaining work.  Before the CTA
+// frees its tensor memory and exits it waits, with the same bound, for what it
+// already issued: the products (one commit after the last one issued) and the
+// TMA loads no product consumed, so nothing lands in a CTA that has exited.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_fp8.h>
@@ -145,6 +147,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   uint64_t* done = empty + STAGES;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
   uint32_t* fail = tmem_slot + 1;
+  int32_t* n_issued = reinterpret_cast<int32_t*>(fail + 1);     // K blocks whose TMA loads were issued
+  int32_t* n_consumed = n_issued + 1;                          // K blocks the MMA issuer saw land
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int m0 = blockIdx.x * kTileM;
@@ -165,6 +169,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     }
     mbar_init(done, 1);
     *fail = 0;
+    *n_issued = 0;
+    *n_consumed = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) {
@@ -191,7 +197,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 
   if (active && threadIdx.x == 0) {
     // TMA producer
-    for (int kb = 0; kb < nk; ++kb) {
+    int kb = 0;
+    for (; kb < nk; ++kb) {
       const int s = kb % STAGES;
       const uint32_t ph = (uint32_t)(kb / STAGES) & 1u;
       const int kc = kb * kblk;
@@ -205,6 +212,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       }
       tma_load_2d(sB + (size_t)s * BN * kKBlockBytes, &tB, full + s, kc, n0);
     }
+    // the first STAGES weight loads went out before the loop in any case
+    *n_issued = max(kb, min(nk, STAGES));
   } else if (active && threadIdx.x == 32) {
     // MMA issuer: 4 instructions of 32 bytes of K per 128-byte block
     const uint32_t id = idesc(KIND_BF16, kTileM, BN);
@@ -217,6 +226,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         ok = false;
         break;
       }
+      *n_consumed = kb + 1;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const uint32_t a0 = smem_u32(sA + (size_t)s * kTileM * kKBlockBytes);
       const uint32_t b0 = smem_u32(sB + (size_t)s * BN * kKBlockBytes);
@@ -236,6 +246,13 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   }
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   __syncthreads();
+  if (*fail && threadIdx.x == 0) {
+    // give-up path: nothing this CTA issued may land in its shared memory
+    // after it exits.  Every MMA was committed to `done` (waited on above);
+    // wait, with the same bound, for the TMA loads no MMA consumed.
+    for (int kb = *n_consumed; kb < *n_issued; ++kb)
+      if (!mbar_wait(full + kb % STAGES, (uint32_t)(kb / STAGES) & 1u)) break;
+  }
   if (ready && *fail == 0) {
     // warp w reads TMEM lanes 32 (w % 4) .. + 31 (its lane quarter) and the
     // columns of half w / 4 of the tile

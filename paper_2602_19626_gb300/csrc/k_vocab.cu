@@ -783,13 +783,16 @@ __global__ void __launch_bounds__(kStepThreads, 1) k_vocab(Dims D, Batch b, Voca
     return;                                      // uniform across the cluster
   }
   if (!b.z_in) load_runf<E, FULL>(st.z, L.v0, V, z, -INFINITY);
-  if (io.probe_z) store_run<E>(io.probe_z + (size_t)j * V, L.v0, V, z);
+  // probes: every step, or only at the stream's probe_tok-th token
+  const bool probe = io.probe_tok == 0 || io.probe_tok == (int64_t)i_tok;
+  const size_t prow = (size_t)(io.probe_row ? io.probe_row[j] : j) * V;
+  if (probe && io.probe_z) store_run<E>(io.probe_z + prow, L.v0, V, z);
 
   // ---- softmax (Sec. 3.6) and the N-gram distribution
   float png[E];
   if (ngram) {
     ngram_probs<E, FULL>(sh.ng[0], spw, L, V, cnt, png);
-    if (io.probe_png) store_run<E>(io.probe_png + (size_t)j * V, L.v0, V, png);
+    if (probe && io.probe_png) store_run<E>(io.probe_png + prow, L.v0, V, png);
   } else {
 #pragma unroll
     for (int i = 0; i < E; ++i) png[i] = 0.f;
@@ -811,14 +814,14 @@ __global__ void __launch_bounds__(kStepThreads, 1) k_vocab(Dims D, Batch b, Voca
   const bool skipped = D.skip && sm.H < kSkipBits;
   float pt[E];
   probs_tilde<E>(e, part.x, sm, pt);
-  if (io.probe_pt) store_run<E>(io.probe_pt + (size_t)j * V, L.v0, V, pt);
+  if (probe && io.probe_pt) store_run<E>(io.probe_pt + prow, L.v0, V, pt);
 
   // ---- the coded distribution and its counts (Sec. 3.3, 3.5)
   const bool mixing = ngram && i_tok > D.warmup;
   const float2 w = mix_weights(th0, th1);
   float p[E];
   coded_probs<E>(pt, png, w, skipped, mixing, p);
-  if (io.probe_p) store_run<E>(io.probe_p + (size_t)j * V, L.v0, V, p);
+  if (probe && io.probe_p) store_run<E>(io.probe_p + prow, L.v0, V, p);
   if (owner)
     push_obs(cl, &sh.slot[1].obs,
              make_float4(pick<E>(pt, L.v0, t), png_t, __fsub_rn(__fsub_rn(s_t, sm.M), __logf(sm.S)), 0.f));
@@ -977,6 +980,10 @@ __global__ void __launch_bounds__(kStepThreads, 1)
       break;                                     // uniform across the cluster
     }
     const bool more = act1;
+    // probes at the stream's probe_tok-th token (uniform across the cluster)
+    const bool probe = io.probe_tok == (int64_t)(n0 + r + 1);
+    const size_t prow = (size_t)(io.probe_row ? io.probe_row[j] : j) * V;
+    if (probe && io.probe_z) store_run<E>(io.probe_z + prow, L.v0, V, z);
 
     // ---- softmax partials of position r (its slot masses are in spw)
     float png[E];
@@ -986,6 +993,7 @@ __global__ void __launch_bounds__(kStepThreads, 1)
 #pragma unroll
       for (int i = 0; i < E; ++i) png[i] = 0.f;
     }
+    if (probe && io.probe_png) store_run<E>(io.probe_png + prow, L.v0, V, png);
     float s[E], e[E];
     biased_logits<E, FULL>(z, bias, inv_tau, L.v0, V, s);
     const bool owner = t >= L.v0 && t < L.v0 + E;
@@ -1030,6 +1038,8 @@ __global__ void __launch_bounds__(kStepThreads, 1)
     const float2 w = mix_weights(th0, th1);
     float p[E];
     coded_probs<E>(pt, png, w, skipped, mixing, p);
+    if (probe && io.probe_pt) store_run<E>(io.probe_pt + prow, L.v0, V, pt);
+    if (probe && io.probe_p) store_run<E>(io.probe_p + prow, L.v0, V, p);
     StepSlot& nx = sh.slot[nb & 1];
     if (owner)
       push_obs(cl, &nx.obs,
@@ -1438,13 +1448,16 @@ __global__ void __launch_bounds__(kVocabThreads)
     }
     return;
   }
+  // s = z / tau + b as the coding step forms it (Sec. 3.2, Sec. 3.6): one
+  // fused multiply-add by the rounded reciprocal of tau
+  const float inv_tau = 1.0f / tau;
   float mx = -INFINITY;
-  for (int v = threadIdx.x; v < V; v += kVocabThreads) mx = fmaxf(mx, __fdiv_rn(zr[v], tau) + br[v]);
+  for (int v = threadIdx.x; v < V; v += kVocabThreads) mx = fmaxf(mx, __fmaf_rn(zr[v], inv_tau, br[v]));
   const float M = block_max(mx, sh);
   float ls = 0.f;
-  for (int v = threadIdx.x; v < V; v += kVocabThreads) ls += expf(__fdiv_rn(zr[v], tau) + br[v] - M);
+  for (int v = threadIdx.x; v < V; v += kVocabThreads) ls += expf(__fmaf_rn(zr[v], inv_tau, br[v]) - M);
   const float S = block_sum(ls, sh);
-  const float pts = __fdiv_rn(expf(__fdiv_rn(zr[t], tau) + br[t] - M), S);
+  const float pts = __fdiv_rn(expf(__fmaf_rn(zr[t], inv_tau, br[t]) - M), S);
   const float pngs = png[(size_t)j * V + t];
   const float th0 = theta[2 * j], th1 = theta[2 * j + 1];
   const float tm = fmaxf(th0, th1);
@@ -1457,7 +1470,7 @@ __global__ void __launch_bounds__(kVocabThreads)
   if (db) {
     const float rho = wu ? 1.f : w0 * pts / pm;
     for (int v = threadIdx.x; v < V; v += kVocabThreads) {
-      const float ptv = __fdiv_rn(expf(__fdiv_rn(zr[v], tau) + br[v] - M), S);
+      const float ptv = __fdiv_rn(expf(__fmaf_rn(zr[v], inv_tau, br[v]) - M), S);
       db[(size_t)j * V + v] = g * rho * (ptv - (v == t ? 1.f : 0.f));
     }
   }

@@ -1,6 +1,6 @@
-// Device building blocks of the decode step, shared by the one-kernel-per-
-// phase path (k_model.cu) and the persistent step kernel (k_step.cu), so the
-// two compute every value with the same operations in the same order.
+// Device building blocks of the decode step, shared by the model kernels
+// (k_model.cu) and the tensor-core attention (k_attn_tc.cu), so that every
+// kernel computing a value uses the same operations in the same order.
 #pragma once
 
 #include <cuda_bf16.h>

@@ -8,6 +8,8 @@
 // nc_probs_to_cdf_noalloc does the same work, but the status words live in the
 // fixed array below.  The array is part of the library image, so every GPU
 // that loads the library holds it until the process exits.
+#include <cuda.h>
+
 #include <mutex>
 
 #include "internal.h"
@@ -19,19 +21,52 @@ static __device__ __align__(256) int32_t g_noalloc_status[NC_NOALLOC_MAX_ROWS];
 
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
-int32_t* g_status_ptr[kMaxDevices] = {};   // device address of the array, per device
+int32_t* g_status_ptr[kMaxDevices] = {};        // device address of the array, per device
+unsigned long long g_ctx_id[kMaxDevices] = {};  // the context the address belongs to
+
+// Unique id of the current context (0 when it cannot be read).  A device
+// reset gives the device a new primary context with a new id, in which the
+// library image, and so the array, may sit at another address.
+unsigned long long current_ctx_id() {
+  using GetCurrent = CUresult (*)(CUcontext*);
+  using GetId = CUresult (*)(CUcontext, unsigned long long*);
+  static GetCurrent get_current = nullptr;
+  static GetId get_id = nullptr;
+  if (!get_current || !get_id) {
+    void* a = nullptr;
+    void* b = nullptr;
+    cudaDriverEntryPointQueryResult qa, qb;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &a, 12000, cudaEnableDefault, &qa) != cudaSuccess ||
+        qa != cudaDriverEntryPointSuccess ||
+        cudaGetDriverEntryPointByVersion("cuCtxGetId", &b, 12000, cudaEnableDefault, &qb) != cudaSuccess ||
+        qb != cudaDriverEntryPointSuccess)
+      return 0;
+    get_current = reinterpret_cast<GetCurrent>(a);
+    get_id = reinterpret_cast<GetId>(b);
+  }
+  CUcontext c = nullptr;
+  unsigned long long id = 0;
+  if (get_current(&c) != CUDA_SUCCESS || !c || get_id(c, &id) != CUDA_SUCCESS) return 0;
+  return id;
+}
 
 // Device address of the array on the current device.  Host code cannot use
 // the symbol itself: on the host it names a stand-in, not device memory.
-// The first call on a device looks the address up (cudaGetSymbolAddress).
+// Set-up, once per device (again after a reset of that device's context):
+// the address is looked up with cudaGetSymbolAddress while the device is
+// current and kept for later calls.
 int status_words(int32_t** out) {
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return NC_ECUDA;
+  // before the runtime's first call on this device there is no current
+  // context (id 0): the look-up below creates it, and the id is read again
+  const unsigned long long id = current_ctx_id();
   std::lock_guard<std::mutex> lock(g_mu);
-  if (!g_status_ptr[dev]) {
+  if (!g_status_ptr[dev] || id == 0 || id != g_ctx_id[dev]) {
     void* p = nullptr;
     if (cudaGetSymbolAddress(&p, g_noalloc_status) != cudaSuccess || !p) return NC_ECUDA;
     g_status_ptr[dev] = static_cast<int32_t*>(p);
+    g_ctx_id[dev] = id ? id : current_ctx_id();
   }
   *out = g_status_ptr[dev];
   return NC_OK;

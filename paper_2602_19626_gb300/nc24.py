@@ -75,6 +75,7 @@ _SIGS = {
     "nc_encode": (C.c_int, [_P, C.c_int, _P, _P, _P, _SZP]),
     "nc_decode": (C.c_int, [_P, _P, C.c_size_t, _P, _P]),
     "nc_encode_intervals": (C.c_int, [_P, C.c_int, _P, _P, _P, _P, C.c_int64, C.POINTER(nc_trace)]),
+    "nc_encode_probe": (C.c_int, [_P, C.c_int, _P, _P, _P, _P, C.c_int64, C.c_int64, _P, _P, _P, _P]),
     "nc_container_streams": (C.c_int, [_P, C.c_size_t, C.POINTER(C.c_int)]),
     "nc_status_str": (C.c_char_p, [C.c_int]),
     "nc_last_error": (C.c_char_p, [_P]),
@@ -371,6 +372,16 @@ class Context:
             return None
         return [dict(name=tr.name[k].value.decode(), launches=tr.launches[k], ms=tr.ms[k], bytes=tr.bytes[k],
                      flops=tr.flops[k], graphed=bool(tr.graphed)) for k in range(tr.n_kinds)]
+
+    def encode_probe(self, tokens_dev, offsets, lens, intervals_dev, stride: int, probe_pos: int,
+                     z=None, p_tilde=None, p_ng=None, p=None):
+        """encode_intervals that also writes each stream's z, p_tilde, p_ng
+        and p at token index probe_pos (CUDA float32 [n, V] each, or None)."""
+        offs = np.ascontiguousarray(offsets, dtype=np.int64)
+        ln = np.ascontiguousarray(lens, dtype=np.int64)
+        self._check(lib.nc_encode_probe(self.h, ln.size, _ptr(tokens_dev), _ptr(offs), _ptr(ln),
+                                        _ptr(intervals_dev), stride, probe_pos, _ptr(z), _ptr(p_tilde),
+                                        _ptr(p_ng), _ptr(p)), "nc_encode_probe")
 
     def decode(self, data: bytes):
         buf = np.frombuffer(data, dtype=np.uint8).copy()

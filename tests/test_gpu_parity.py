@@ -93,9 +93,9 @@ def test_probs_to_cdf_errors(nc):
 
 # ------------------------------------------------------- per-step parity
 
-def _run_steps(nc, shape, seed, fmt, n_steps, warmup, rule="paper", order=3, tok_seed=None):
+def _run_steps(nc, shape, seed, fmt, n_steps, warmup, rule="paper", order=3, tok_seed=None, tau=1.0):
     toks = S.token_stream(seed if tok_seed is None else tok_seed, 0, n_steps, shape.vocab)
-    cfg = nc.make_config(shape, fmt=fmt, rule=rule, warmup=warmup, ngram_order=order)
+    cfg = nc.make_config(shape, fmt=fmt, rule=rule, warmup=warmup, ngram_order=order, tau=tau)
     ctx = nc.Context(cfg, S.flat_weights(shape, seed))
     V = shape.vocab
     bufs = {k: torch.empty(1, V, device="cuda") for k in ("z", "pt", "png", "p")}
@@ -113,14 +113,16 @@ def _run_steps(nc, shape, seed, fmt, n_steps, warmup, rule="paper", order=3, tok
     return toks, out, (b, th, n)
 
 
-@pytest.mark.parametrize("rule", ["paper", "mixed_nll"])
-def test_small_fp32_step_parity(nc, rule):
+@pytest.mark.parametrize("rule,tau", [("paper", 1.0), ("mixed_nll", 1.0), ("paper", 0.8), ("mixed_nll", 0.7)])
+def test_small_fp32_step_parity(nc, rule, tau):
     """4-layer FP32 model, 48 steps (warm-up 12, so the mix is exercised):
     logits, p_tilde, p_ng and p against the oracle; CDF bit-exact against the
-    oracle quantiser on the GPU's binary32 p; head and mixer state after."""
+    oracle quantiser on the GPU's binary32 p; head and mixer state after.
+    tau != 1 exercises the temperature of p_llm = softmax(z / tau) (Sec. 3.2)."""
     shape, seed = S.SMALL, 0
-    toks, recs, (b, th, n) = _run_steps(nc, shape, seed, "fp32", 48, 12, rule)
-    ref = StreamState.new(Model(shape, S.weights(shape, seed), "fp32"), StepConfig(warmup=12, rule=rule))
+    toks, recs, (b, th, n) = _run_steps(nc, shape, seed, "fp32", 48, 12, rule, tau=tau)
+    ref = StreamState.new(Model(shape, S.weights(shape, seed), "fp32"),
+                          StepConfig(warmup=12, rule=rule, tau=tau))
     zerr = 0.0
     for t, r in zip(toks, recs):
         ref.predict()
@@ -349,7 +351,10 @@ def test_call_order_errors(nc):
 
 # ------------------------------------------------------ differentiation
 
-def test_mixed_nll_kernels_vs_oracle_and_fd(nc):
+@pytest.mark.parametrize("tau", [1.0, 0.7])
+def test_mixed_nll_kernels_vs_oracle_and_fd(nc, tau):
+    """The differentiable update rule's kernels against the oracle's closed
+    form (p_tilde = softmax(z / tau + b)) and central differences."""
     from oracle.mixer import mixed_nll_grad
     from paper_2602_19626_gb300.autograd import mixed_nll
     rng = np.random.default_rng(5)
@@ -363,12 +368,12 @@ def test_mixed_nll_kernels_vs_oracle_and_fd(nc):
     tb = torch.from_numpy(b).cuda().requires_grad_(True)
     tth = torch.from_numpy(theta).cuda().requires_grad_(True)
     args = [torch.from_numpy(a).cuda() for a in (z, png, target, warm)]
-    loss = mixed_nll(tb, tth, *args)
+    loss = mixed_nll(tb, tth, *args, tau=tau)
     loss.sum().backward()
     gb = tb.grad.cpu().numpy()
     gth = tth.grad.cpu().numpy()
     for i in range(n):
-        s = z[i].astype(np.float64) + b[i]
+        s = z[i].astype(np.float64) / tau + b[i]
         pt = np.exp(s - s.max())
         pt /= pt.sum()
         rb, rth = mixed_nll_grad(pt, png[i].astype(np.float64), theta[i].astype(np.float64), int(target[i]), bool(warm[i]))
@@ -382,7 +387,7 @@ def test_mixed_nll_kernels_vs_oracle_and_fd(nc):
             bp[i, k] += eps
             bm = b.copy()
             bm[i, k] -= eps
-            lp = mixed_nll(torch.from_numpy(bp).cuda(), tth.detach(), *args)[i].item()
-            lm = mixed_nll(torch.from_numpy(bm).cuda(), tth.detach(), *args)[i].item()
+            lp = mixed_nll(torch.from_numpy(bp).cuda(), tth.detach(), *args, tau=tau)[i].item()
+            lm = mixed_nll(torch.from_numpy(bm).cuda(), tth.detach(), *args, tau=tau)[i].item()
             assert abs((lp - lm) / (2 * eps) - gb[i, k]) < 2e-3 * max(1.0, abs(gb[i, k]))
 

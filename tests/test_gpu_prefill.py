@@ -64,14 +64,16 @@ def test_prefill_mixed_nll_equals_decode(nc, path):
     assert np.array_equal(got, ref)
 
 
-def test_prefill_full_model_single_stream(nc):
+@pytest.mark.parametrize("path", ["gemv", "tc"])
+def test_prefill_full_model_single_stream(nc, path):
     """Full-size BF16 model, one 700-token stream: a 512-position prefill
-    chunk then a partial one give the decode intervals exactly."""
+    chunk then a partial one give the decode intervals exactly, on the
+    CUDA-core and the tensor-core paths."""
     shape, seed = S.FULL, 1
     w = S.flat_weights(shape, seed)
     toks = [S.token_stream(seed, 0, 700, shape.vocab)]
-    ref = intervals(nc, shape, w, "bf16", "gemv", toks, 0, 1)
-    got = intervals(nc, shape, w, "bf16", "gemv", toks, 4096, 1)
+    ref = intervals(nc, shape, w, "bf16", path, toks, 0, 1)
+    got = intervals(nc, shape, w, "bf16", path, toks, 4096, 1)
     assert np.array_equal(got, ref)
 
 
