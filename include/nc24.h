@@ -319,6 +319,16 @@ int nc_stream_state(nc_ctx* ctx, int32_t stream_id, float* bias, float* mix_logw
 int nc_gemm_tc(const void* W, const void* X, const float* w_scale, const float* x_scale, int fp8, int M,
                int N, int K, int bn, float* Y, void* stream);
 
+/* Diagnostic of the failure path of the device waits: one bounded wait, at
+ * most `polls` polls of an mbarrier that nothing arrives on, through the same
+ * wait routine and status word as the tensor-core pipelines (the projections'
+ * GEMM and the attention).  The wait gives up, and the call reports it as a
+ * stalled pipeline is reported: NC_ETIMEOUT, the context poisoned (every
+ * later call but nc_ctx_destroy / nc_last_error returns NC_ESTATE).  No GPU
+ * fault is involved and the device stays usable; a new context works.
+ * The paper has no counterpart.  Errors: NC_EINVAL, NC_ESTATE, NC_ECUDA. */
+int nc_selftest_wait(nc_ctx* ctx, uint32_t polls);
+
 /* 32-bit arithmetic coder (Sec. 3.8) on the host, for callers that produce
  * their own CDFs.  Encode n intervals [lo[i], hi[i]) of a total 2^log2_total
  * (HOST uint32 arrays) into out (HOST, capacity *inout_nbytes; size and the

@@ -2,6 +2,7 @@
 // sequence (Algorithm 1's loop body), whole-stream encode / decode, and the
 // building-block entry points.  See include/nc24.h for the contract.
 #include <algorithm>
+#include <atomic>
 #include <cstdio>
 #include <cmath>
 #include <cstdlib>
@@ -48,6 +49,7 @@ struct TcMat {
   CUtensorMap b;                     // operand of a decode step (max_streams rows)
   CUtensorMap bp;                    // operand of a prefill forward (prefill_rows rows)
   int M = 0, K = 0, bn = 0, bnp = 0;
+  int ks = 1;                        // split-K (fixed per matrix)
   const float* scale = nullptr;
 };
 
@@ -237,10 +239,29 @@ static size_t n_params(const nc_config& c) {
   return (size_t)c.vocab * d + c.n_layers * per + d;
 }
 
+// Device allocations of the library go through dev_malloc.  Test hook: with
+// NC24_FAIL_ALLOC_AFTER=n in the environment when a context is created, the
+// allocations after the first n (counted from that nc_ctx_create on) fail as
+// an out-of-memory device would, so that tests can check that every error
+// path returns NC_ENOMEM and releases what it holds.
+static std::atomic<long> g_alloc_budget{-1};
+
+template <typename T>
+static cudaError_t dev_malloc(T** p, size_t bytes) {
+  long b = g_alloc_budget.load();
+  while (b > 0 && !g_alloc_budget.compare_exchange_weak(b, b - 1)) {
+  }
+  if (b == 0) {
+    *p = nullptr;
+    return cudaErrorMemoryAllocation;
+  }
+  return cudaMalloc(reinterpret_cast<void**>(p), bytes);
+}
+
 template <typename T>
 static cudaError_t dalloc(nc_ctx* ctx, T** p, size_t bytes) {
   void* q = nullptr;
-  cudaError_t e = cudaMalloc(&q, bytes ? bytes : 16);
+  cudaError_t e = dev_malloc(&q, bytes ? bytes : 16);
   if (e == cudaSuccess) {
     ctx->allocs.push_back(q);
     *p = static_cast<T*>(q);
@@ -325,27 +346,30 @@ static int tc_setup(nc_ctx* ctx) {
     if (dalloc(ctx, &ctx->opnd2, (size_t)R * D.F * 2)) return fail(ctx, NC_ENOMEM, "tensor-core operand allocation");
     NC_TRY(cudaMemset(ctx->opnd2, 0, (size_t)R * D.F * 2));
   }
-  auto add = [&](const Mat& m) {
+  auto add = [&](const Mat& m, bool head) {
     TcMat t;
     t.M = m.rows;
     t.K = m.cols;
     t.scale = m.scale;
+    // the LM head has tiles enough without a K split
+    t.ks = head ? 1 : tc_ksplit(m.cols, kb);
     if (!tc_encode_tmap(&t.a, m.w, esz, m.cols, m.rows, 128)) return false;
     ctx->tc.push_back(t);
     return true;
   };
   for (const LayerW& L : ctx->layers)
-    if (!add(L.qkv) || !add(L.o) || !add(L.gu) || !add(L.down)) return fail(ctx, NC_ECUDA, "tensor map encoding failed");
+    if (!add(L.qkv, false) || !add(L.o, false) || !add(L.gu, false) || !add(L.down, false))
+      return fail(ctx, NC_ECUDA, "tensor map encoding failed");
   Mat head{ctx->embed, ctx->embed_scale, D.V, D.d};
-  if (!add(head)) return fail(ctx, NC_ECUDA, "tensor map encoding failed");
+  if (!add(head, true)) return fail(ctx, NC_ECUDA, "tensor map encoding failed");
   // autotune bn per distinct shape (layer 0's matrices and the LM head), for
   // a decode step (B rows) and for a prefill forward (P rows)
   float* scratch = nullptr;
   size_t maxM = 0;
   for (const TcMat& t : ctx->tc) maxM = std::max(maxM, (size_t)t.M);
-  NC_TRY(cudaMalloc(&scratch, maxM * R * 4));
+  NC_TRY(dev_malloc(&scratch, maxM * R * 4));
   int32_t* nB = nullptr;
-  NC_TRY(cudaMalloc(&nB, 4));
+  NC_TRY(dev_malloc(&nB, 4));
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
@@ -366,6 +390,7 @@ static int tc_setup(nc_ctx* ctx) {
         TcGemm g{};
         g.tmap_a = &tt.a;
         g.tmap_b = &tt.b;
+        g.ks = t.ks;
         g.M = t.M;
         g.K = t.K;
         g.Bmax = rows;
@@ -428,6 +453,10 @@ extern "C" int nc_ctx_create(const nc_config* cfg, const void* weights, size_t n
   const std::string why = validate(*cfg);
   if (!why.empty()) return NC_EINVAL;
   if (nbytes != n_params(*cfg) * sizeof(float)) return NC_EINVAL;
+  {
+    const char* e = std::getenv("NC24_FAIL_ALLOC_AFTER");
+    g_alloc_budget.store(e && e[0] ? std::atol(e) : -1);
+  }
   nc_ctx* ctx = new (std::nothrow) nc_ctx();
   if (!ctx) return NC_ENOMEM;
   cudaGetLastError();                              // a stale error of an earlier call is not ours
@@ -480,10 +509,10 @@ extern "C" int nc_ctx_create(const nc_config* cfg, const void* weights, size_t n
   D.tau = c.temperature;
   D.kv_bf16 = c.weight_fmt != NC_FP32;
   {
-    // Attention CTAs per (stream, KV head) are picked per launch from its
-    // rows (results do not depend on them); NC24_ATTN_CLUSTER=1|2|4|8 fixes
-    // them and keeps prefill rows on the decode kernel (else groups of 32
-    // prefill positions take the row-tile kernel).
+    // CUDA-core attention over an FP32 cache: CTAs per (stream, KV head) are
+    // picked per launch from its rows (results do not depend on them);
+    // NC24_ATTN_CLUSTER=1|2|4|8 fixes them.  The tensor-core attention over a
+    // BF16 cache always takes one CTA per 256-position chunk of the window.
     int nsm = 0;
     if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c.device) != cudaSuccess || nsm <= 0)
       return bail(NC_ECUDA);
@@ -504,7 +533,7 @@ extern "C" int nc_ctx_create(const nc_config* cfg, const void* weights, size_t n
 
   // ---- weights: upload the FP32 buffer once, convert tensor by tensor
   float* src = nullptr;
-  if (cudaMalloc(&src, nbytes) != cudaSuccess) return bail(NC_ENOMEM);
+  if (dev_malloc(&src, nbytes) != cudaSuccess) return bail(NC_ENOMEM);
   int st = NC_OK;
   do {
     if (cudaMemcpy(src, weights, nbytes, cudaMemcpyHostToDevice) != cudaSuccess) {
@@ -623,10 +652,10 @@ static int slot_alloc(nc_ctx* ctx, Slot& s, int64_t max_len) {
   const Dims& D = ctx->D;
   if (!s.kv) {
     const size_t kvb = (size_t)D.n_layers * 2 * D.hkv * D.L * kHeadDim * (D.kv_bf16 ? 2 : 4);
-    NC_TRY(cudaMalloc(&s.kv, kvb));
-    NC_TRY(cudaMalloc(&s.bias, (size_t)D.V * 4));
-    NC_TRY(cudaMalloc(&s.uni, (size_t)D.V * 4));
-    NC_TRY(cudaMalloc(&s.z, (size_t)D.V * 4));
+    NC_TRY(dev_malloc(&s.kv, kvb));
+    NC_TRY(dev_malloc(&s.bias, (size_t)D.V * 4));
+    NC_TRY(dev_malloc(&s.uni, (size_t)D.V * 4));
+    NC_TRY(dev_malloc(&s.z, (size_t)D.V * 4));
   }
   if (D.order > 0 && s.cap_len < max_len) {
     for (int k = 0; k < 3; ++k) {
@@ -640,9 +669,9 @@ static int slot_alloc(nc_ctx* ctx, Slot& s, int64_t max_len) {
     s.cap_len = 0;
     const int64_t cap = next_pow2(std::max<int64_t>(2 * max_len, 16));
     for (int k = 0; k < D.order; ++k) {
-      NC_TRY(cudaMalloc(&s.keys[k], (size_t)cap * 8));
-      NC_TRY(cudaMalloc(&s.idx[k], (size_t)cap * 4));
-      NC_TRY(cudaMalloc(&s.ent[k], (size_t)max_len * sizeof(NgEntry)));
+      NC_TRY(dev_malloc(&s.keys[k], (size_t)cap * 8));
+      NC_TRY(dev_malloc(&s.idx[k], (size_t)cap * 4));
+      NC_TRY(dev_malloc(&s.ent[k], (size_t)max_len * sizeof(NgEntry)));
     }
     s.cap_len = max_len;
     s.cap_hash = cap;
@@ -838,6 +867,7 @@ static cudaError_t launch_model_tc(nc_ctx* ctx, const Batch& b, StepMarks& m) {
     TcGemm g{};
     g.tmap_a = &t.a;
     g.tmap_b = pf ? &t.bp : &t.b;
+    g.ks = t.ks;
     g.M = t.M;
     g.K = t.K;
     g.Bmax = b.Bmax;
@@ -963,6 +993,10 @@ static int check_status(nc_ctx* ctx, const std::vector<int>& slot_idx) {
     for (size_t j = 0; j < slot_idx.size(); ++j)
       NC_TRY(cudaMemsetAsync(reinterpret_cast<char*>(ctx->d_st + slot_idx[j]) + off, 0, 4, ctx->stream));
     NC_TRY(cudaStreamSynchronize(ctx->stream));
+    if (any & ST_TIMEOUT) {
+      ctx->poisoned = true;
+      return fail(ctx, NC_ETIMEOUT, "a bounded device wait gave up");
+    }
     if (any & ST_NUMERIC) return fail(ctx, NC_ENUMERIC, "non-finite probabilities or CDF floor underflow");
     if (any & ST_TABLE_FULL) return fail(ctx, NC_ESTATE, "N-gram tables full (stream longer than expected_len)");
     return fail(ctx, NC_EINVAL, "observed token out of range");
@@ -1448,13 +1482,13 @@ static int encode_intervals(nc_ctx* ctx, int n_streams, const int32_t* tokens_de
       h_meta[2 * n_streams + r] = order[r];
       lens_h[r] = lens[order[r]];
     }
-    if (cudaMalloc(&meta, 3 * n_streams * 8) != cudaSuccess) {
+    if (dev_malloc(&meta, 3 * n_streams * 8) != cudaSuccess) {
       st = fail(ctx, NC_ENOMEM, "meta allocation");
       break;
     }
     bool identity = true;
     for (int r = 0; r < n_streams; ++r) identity &= order[r] == r;
-    if (!identity && cudaMalloc(&iv_rows, (size_t)n_streams * stride * 8) != cudaSuccess) {
+    if (!identity && dev_malloc(&iv_rows, (size_t)n_streams * stride * 8) != cudaSuccess) {
       st = fail(ctx, NC_ENOMEM, "interval staging allocation");
       break;
     }
@@ -1557,9 +1591,9 @@ extern "C" int nc_encode(nc_ctx* ctx, int n_streams, const int32_t* const* token
   }
   std::vector<uint32_t> h_iv;
   do {
-    if (cudaMalloc(&tok_dev, std::max<int64_t>(total, 1) * 4) != cudaSuccess ||
-        cudaMalloc(&meta, 2 * n_streams * 8) != cudaSuccess ||
-        cudaMalloc(&iv, (size_t)n_streams * std::max<int64_t>(max_len, 1) * 8) != cudaSuccess) {
+    if (dev_malloc(&tok_dev, std::max<int64_t>(total, 1) * 4) != cudaSuccess ||
+        dev_malloc(&meta, 2 * n_streams * 8) != cudaSuccess ||
+        dev_malloc(&iv, (size_t)n_streams * std::max<int64_t>(max_len, 1) * 8) != cudaSuccess) {
       st = fail(ctx, NC_ENOMEM, "device allocation for encode failed");
       break;
     }
@@ -1717,13 +1751,14 @@ extern "C" int nc_decode(nc_ctx* ctx, const uint8_t* in, size_t nbytes, int32_t*
       st = fail_cuda(ctx, cudaErrorUnknown, "slot upload");
       break;
     }
-    int active = n;
-    for (int64_t k = 0; k < max_len && st == NC_OK; ++k) {
-      while (active > 0 && recs[order[active - 1]].ntok <= k) --active;
-      ctx->h_i32[0] = active;
-      for (int r = 0; r < active; ++r) ctx->h_u32[r] = rans ? rdec[r].target() : dec[r].target();
+    // one decode step (the decoder learns each token from the coder between
+    // steps): the active count and the coder targets in from pinned host
+    // memory, the model, the CDFs, the search, the updates, the coded
+    // intervals and tokens out.  Captured once in a CUDA graph and replayed
+    // per position; the copies read and write the same pinned buffers.
+    auto one_step = [&]() -> cudaError_t {
       cudaError_t e = cudaMemcpyAsync(ctx->d_nB, ctx->h_i32, 4, cudaMemcpyHostToDevice, s);
-      if (e == cudaSuccess) e = cudaMemcpyAsync(ctx->d_target, ctx->h_u32, (size_t)active * 4, cudaMemcpyHostToDevice, s);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(ctx->d_target, ctx->h_u32, (size_t)n * 4, cudaMemcpyHostToDevice, s);
       if (e == cudaSuccess) e = launch_model(ctx, b);
       VocabIO io{};
       io.cdf = ctx->cdf;
@@ -1734,9 +1769,28 @@ extern "C" int nc_decode(nc_ctx* ctx, const uint8_t* in, size_t nbytes, int32_t*
       up.update = 1;
       up.ngram = 1;
       if (e == cudaSuccess) e = launch_vocab(D, b, up, s);
-      if (e == cudaSuccess) e = cudaMemcpyAsync(ctx->h_u32 + n, ctx->d_lohi, (size_t)active * 8, cudaMemcpyDeviceToHost, s);
-      if (e == cudaSuccess) e = cudaMemcpyAsync(ctx->h_i32 + 1 + 2 * ctx->cfg.max_streams, ctx->d_obs, (size_t)active * 4,
+      if (e == cudaSuccess) e = cudaMemcpyAsync(ctx->h_u32 + n, ctx->d_lohi, (size_t)n * 8, cudaMemcpyDeviceToHost, s);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(ctx->h_i32 + 1 + 2 * ctx->cfg.max_streams, ctx->d_obs, (size_t)n * 4,
                                                 cudaMemcpyDeviceToHost, s);
+      return e;
+    };
+    cudaGraphExec_t ge = nullptr;
+    {
+      cudaGraph_t g = nullptr;
+      if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+        const cudaError_t e = one_step();
+        const cudaError_t e2 = cudaStreamEndCapture(s, &g);
+        if (e != cudaSuccess || e2 != cudaSuccess || cudaGraphInstantiate(&ge, g, 0) != cudaSuccess) ge = nullptr;
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+      }
+    }
+    int active = n;
+    for (int64_t k = 0; k < max_len && st == NC_OK; ++k) {
+      while (active > 0 && recs[order[active - 1]].ntok <= k) --active;
+      ctx->h_i32[0] = active;
+      for (int r = 0; r < active; ++r) ctx->h_u32[r] = rans ? rdec[r].target() : dec[r].target();
+      cudaError_t e = ge ? cudaGraphLaunch(ge, s) : one_step();
       if (e == cudaSuccess) e = cudaStreamSynchronize(s);
       if (e != cudaSuccess) {
         st = fail_cuda(ctx, e, "decode step");
@@ -1751,6 +1805,7 @@ extern "C" int nc_decode(nc_ctx* ctx, const uint8_t* in, size_t nbytes, int32_t*
         tokens_out[order[r]][k] = ctx->h_i32[1 + 2 * ctx->cfg.max_streams + r];
       }
     }
+    if (ge) cudaGraphExecDestroy(ge);
     if (st == NC_OK) st = check_status(ctx, slot_of);
     for (int r = 0; r < n && st == NC_OK && rans; ++r)
       if (!rdec[r].finished()) st = fail(ctx, NC_ECORRUPT, "rANS stream does not end in its initial state");
@@ -1761,6 +1816,22 @@ extern "C" int nc_decode(nc_ctx* ctx, const uint8_t* in, size_t nbytes, int32_t*
 
 // ------------------------------------------------------ building blocks
 
+extern "C" int nc_selftest_wait(nc_ctx* ctx, uint32_t polls) {
+  if (!ctx) return NC_EINVAL;
+  if (ctx->poisoned) return fail(ctx, NC_ESTATE, "context poisoned by an earlier CUDA error");
+  cudaSetDevice(ctx->cfg.device);
+  int32_t w = 0;
+  NC_TRY(cudaMemsetAsync(ctx->d_status, 0, 4, ctx->stream));
+  NC_TRY(launch_wait_selftest(polls, ctx->d_status, ctx->stream));
+  NC_TRY(cudaMemcpyAsync(&w, ctx->d_status, 4, cudaMemcpyDeviceToHost, ctx->stream));
+  NC_TRY(cudaStreamSynchronize(ctx->stream));
+  if (w & ST_TIMEOUT) {
+    ctx->poisoned = true;
+    return fail(ctx, NC_ETIMEOUT, "a bounded device wait gave up");
+  }
+  return NC_OK;
+}
+
 extern "C" int nc_probs_to_cdf(const float* p, int n, int V, int log2_total, uint32_t floor_c, uint32_t* cdf,
                                void* stream) {
   if (!p || !cdf || n < 1 || V < 2 || V > 65535 || log2_total < 1 || log2_total > 24 || floor_c < 1 ||
@@ -1768,7 +1839,7 @@ extern "C" int nc_probs_to_cdf(const float* p, int n, int V, int log2_total, uin
     return NC_EINVAL;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   int32_t* status = nullptr;
-  if (cudaMalloc(&status, (size_t)n * 4) != cudaSuccess) return NC_ENOMEM;
+  if (dev_malloc(&status, (size_t)n * 4) != cudaSuccess) return NC_ENOMEM;
   int rc = NC_OK;
   std::vector<int32_t> hs(n);
   if (cudaMemsetAsync(status, 0, (size_t)n * 4, s) != cudaSuccess ||
@@ -1801,13 +1872,14 @@ extern "C" int nc_gemm_tc(const void* W, const void* X, const float* w_scale, co
   if (!tc_encode_tmap(&t.a, W, esz, K, M, 128) || !tc_encode_tmap(&t.b, X, esz, K, N, bn)) return NC_EINVAL;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   int32_t* dev = nullptr;
-  if (cudaMalloc(&dev, 8) != cudaSuccess) return NC_ENOMEM;
+  if (dev_malloc(&dev, 8) != cudaSuccess) return NC_ENOMEM;
   const int32_t h[2] = {N, 0};
   int rc = NC_OK;
   int32_t back[2] = {0, 0};
   TcGemm g{};
   g.tmap_a = &t.a;
   g.tmap_b = &t.b;
+  g.ks = tc_ksplit(K, !fp8);
   g.M = M;
   g.K = K;
   g.Bmax = N;

@@ -15,8 +15,6 @@ constexpr int kMaxGroup = 4;           // query heads per KV head supported
 constexpr int kVocabCluster = 8;       // CTAs per row in the standalone quantiser kernels
 constexpr int kVocabThreads = 512;
 constexpr float kSkipBits = 1.5f;      // the skip threshold on the N-gram entropy (Sec. 3.7)
-constexpr int kStepCluster = 8;        // CTAs per stream in the per-token vocabulary pass
-constexpr int kStepThreads = 512;
 constexpr unsigned long long kEmptyKey = ~0ull;
 
 // Status bits a kernel can raise in StreamDev::status (sticky).
@@ -84,7 +82,7 @@ struct Dims {
   int qkv_rows;             // (hq + 2 hkv) * 64
   float eps, theta, tau;
   int kv_bf16;              // 1: KV cache in BF16
-  int attn_cluster;         // CTAs per (stream, KV head) in attention: 1, 2, 4 or 8; 0 = by batch size
+  int attn_cluster;         // CTAs per (stream, KV head) in the FP32-cache attention: 1, 2, 4 or 8; 0 = by batch size
   int n_sm;                 // SMs of the device
   int order;                // N-gram order (0 = off)
   int skip;                 // confidence skip: p = p_ng when H(p_ng) < kSkipBits
@@ -240,17 +238,13 @@ cudaError_t launch_prepare_prefill(const Batch& b, int n_streams, int m, int V, 
                                    const int32_t* tok_flat, const int64_t* offs, const int64_t* lens,
                                    int32_t* f_slots, int32_t* f_pos, int32_t* f_tok, int32_t* nB_fwd,
                                    int32_t* obs_step, int32_t* nb_step, int32_t* z_idx, cudaStream_t s);
-// Attention over a BF16 KV cache on the tensor cores (k_attn_tc.cu): rq
-// query rows per CTA group (1: a decode step), S CTAs per group.
-cudaError_t prepare_attn_tc(const Dims& D);
-size_t attn_tc_smem(int rq, int grp, int S);
-// Prefill rows (b.pos set) in groups of 32 positions, each warp walking one
-// 16-row tile through a chunk's blocks (same bits as launch_attn_tc).
-bool attn_pf_fits(const Dims& D, const Batch& b);
-cudaError_t launch_attn_pf(const Dims& D, const Batch& b, int layer, const float* qkv, float* attn_out,
-                           void* out16, cudaStream_t s);
-cudaError_t launch_attn_tc(const Dims& D, const Batch& b, int layer, int rq, int S, const float* qkv, float* attn_out,
-                           void* out16, cudaStream_t s);
+// Attention over a BF16 KV cache on the tcgen05 tensor cores (k_attn_t5.cu):
+// decode rows (b.pos null: one row per stream, position n_coded, the fed
+// k, v appended by the kernel) or prefill rows (b.pm consecutive positions
+// per stream, appended before), into attn_out or, when out16 is set, BF16
+// into out16.  A row's result does not depend on the other rows.
+cudaError_t launch_attn_t5(const Dims& D, const Batch& b, int layer, const float* qkv, float* attn_out, void* out16,
+                           cudaStream_t s);
 // Prefill: rotate and append the k, v of every row to the KV ring of `layer`.
 cudaError_t launch_kv_append(const Dims& D, const Batch& b, int layer, const float* qkv, cudaStream_t s);
 // Decoder: row j's symbol is the s with cdf[s] <= target[j] < cdf[s+1]; writes
@@ -268,6 +262,7 @@ struct TcGemm {
   const void* tmap_a;       // host copy of the weights' CUtensorMap (box 128 rows)
   const void* tmap_b;       // host copy of the operand's CUtensorMap (box bn rows)
   int M, K, Bmax, bn, kind_bf16;
+  int ks;                   // split-K CTAs per output tile (1, 2, 4): a property of the weight matrix
   const int32_t* nB;
   const float* w_scale;     // FP8: [M]
   const float* x_scale;     // FP8: [Bmax]
@@ -280,7 +275,14 @@ struct TcGemm {
   int32_t* status;          // error word (ST_TIMEOUT)
 };
 bool tc_encode_tmap(void* tmap, const void* base, int elem_bytes, int64_t inner, int64_t outer, int box_outer);
+// Split-K of a projection's GEMM from its inner dimension K (1, 2 or 4 CTAs
+// per output tile): fixed per weight matrix, so every batch size, the
+// decode step and the prefill forward add the same partials in the same order.
+int tc_ksplit(int K, int kind_bf16);
 cudaError_t launch_gemm_tc(const TcGemm& g, int epi, cudaStream_t s, bool pdl);
+// One bounded mbarrier wait on a barrier nothing arrives on (at most `polls`
+// polls), recording ST_TIMEOUT in *status when it gives up.
+cudaError_t launch_wait_selftest(uint32_t polls, int32_t* status, cudaStream_t s);
 cudaError_t launch_act_rmsnorm(const Dims& D, const Batch& b, const float* x, const float* gain, int cols,
                                int kind_bf16, void* out, float* out_scale, cudaStream_t s);
 cudaError_t launch_act_plain(const Dims& D, const Batch& b, const float* x, int cols, int kind_bf16, void* out,

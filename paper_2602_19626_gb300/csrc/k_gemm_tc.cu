@@ -21,105 +21,22 @@
 #include <cuda_bf16.h>
 #include <cuda_fp8.h>
 
+#include <cooperative_groups.h>
+
 #include "internal.h"
+#include "tc5.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace nc {
 
 namespace {
 
+using namespace tc5;
+
 constexpr int kTcThreads = 256;              // 8 warps: all read the accumulator back
 constexpr int kTileM = 128;
 constexpr int kKBlockBytes = 128;            // one 128-byte swizzle row per operand row
-constexpr uint32_t kWaitLimit = 1u << 22;
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
-               : "memory");
-}
-
-// Bounded wait for the phase with the given parity; false when it gave up.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
-  const uint32_t a = smem_u32(bar);
-  for (uint32_t it = 0; it < kWaitLimit; ++it) {
-    uint32_t ok;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(ok)
-        : "r"(a), "r"(parity)
-        : "memory");
-    if (ok) return true;
-  }
-  return false;
-}
-
-__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int c0, int c1) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::"r"(
-          smem_u32(dst)),
-      "l"(map), "r"(smem_u32(bar)), "r"(c0), "r"(c1)
-      : "memory");
-}
-
-// Shared-memory matrix descriptor of a K-major operand tile in the 128-byte
-// swizzle layout: rows of 128 bytes, 8-row (1024-byte) swizzle atoms.
-__device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr) {
-  uint64_t d = 0;
-  d |= (uint64_t)((saddr >> 4) & 0x3FFFu);      // start address, 16-byte units
-  d |= (uint64_t)1 << 16;                        // leading byte offset (unused when swizzled)
-  d |= (uint64_t)(1024 >> 4) << 32;              // stride byte offset: between 8-row groups
-  d |= (uint64_t)1 << 46;                        // descriptor version
-  d |= (uint64_t)2 << 61;                        // 128-byte swizzle
-  return d;
-}
-
-// Instruction descriptor: FP32 accumulator, K-major A and B, shape M x N.
-__host__ __device__ constexpr uint32_t idesc(int kind_bf16, int M, int N) {
-  return (1u << 4)                                     // D format F32
-         | ((kind_bf16 ? 1u : 0u) << 7)                // A: BF16 (kind::f16) or E4M3 (kind::f8f6f4)
-         | ((kind_bf16 ? 1u : 0u) << 10)               // B: same type as A
-         | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
-}
-
-__device__ __forceinline__ void mma_issue(int kind_bf16, uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t id,
-                                          uint32_t accum) {
-  if (kind_bf16) {
-    asm volatile(
-        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
-            d_tmem),
-        "l"(a), "l"(b), "r"(id), "r"(accum));
-  } else {
-    asm volatile(
-        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}\n" ::"r"(
-            d_tmem),
-        "l"(a), "l"(b), "r"(id), "r"(accum));
-  }
-}
-
-__device__ __forceinline__ void mma_commit(uint64_t* bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
-               : "memory");
-}
-
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
-  uint32_t r[16];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
-        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
-}
-
 // SiLU of the tensor-core path: a * (1 / (1 + e^-a)) with the fast exponential
 // and a correctly rounded reciprocal (1 / inf = 0 for very negative a).  The
 // decode step and the prefill forward run this same code.
@@ -130,12 +47,56 @@ __host__ __device__ constexpr uint32_t tmem_cols() {
   return BN <= 32 ? 32 : BN <= 64 ? 64 : BN <= 128 ? 128 : 256;
 }
 
-template <int BN, int STAGES>
+// Split-K partials received by one rank, [KS source ranks][128 / KS rows][BN
+// columns] with rows padded by 4 floats (a warp's remote stores to 32 rows
+// then spread over the banks), in the pipeline's stage buffers once every
+// rank of the cluster is done with them.
+template <int BN>
+__host__ __device__ constexpr size_t tc_recv_bytes() {
+  return (size_t)kTileM * (BN + 4) * 4;
+}
+
+template <int BN, int STAGES, int KS>
 __host__ __device__ constexpr size_t tc_smem_bytes() {
   return 1024 /* alignment slack */ + (size_t)STAGES * (kTileM + BN) * kKBlockBytes + 256;
 }
+static_assert(tc_recv_bytes<256>() <= 4 * (kTileM + 256) * kKBlockBytes, "receive buffer within the stages");
+static_assert(tc_recv_bytes<128>() <= 6 * (kTileM + 128) * kKBlockBytes, "receive buffer within the stages");
 
-template <int BN, int STAGES, int KIND_BF16, int EPI>
+// One output element (row r of the weights, batch row n) through the fused
+// epilogue; y already carries the FP8 scales.
+template <int EPI>
+__device__ __forceinline__ void epi_store(const TcGemm& g, int r, int n, int B, float y, float res) {
+  if (EPI == EPI_SWIGLU) {
+    const float up = __shfl_xor_sync(0xffffffffu, y, 1);   // rows 2j (gate), 2j + 1 (up) on adjacent lanes
+    if (n < B && r < g.M && (r & 1) == 0) {
+      const float h = silu_tc(y) * up;
+      if (g.h16)
+        static_cast<__nv_bfloat16*>(g.h16)[(size_t)n * (g.M / 2) + (r >> 1)] = __float2bfloat16_rn(h);
+      else
+        g.h_out[(size_t)n * (g.M / 2) + (r >> 1)] = h;
+    }
+  } else if (n < B && r < g.M) {
+    if (EPI == EPI_STORE) {
+      g.y[(size_t)n * g.M + r] = y;
+    } else if (EPI == EPI_RESID) {
+      g.y[(size_t)n * g.M + r] = res + y;
+    } else {
+      if (g.zrows)
+        g.zrows[(size_t)n * g.M + r] = y;
+      else
+        g.st[g.slots[n]].z[r] = y;
+    }
+  }
+}
+
+// KS > 1: the CTAs of a cluster of KS split the K blocks of one output tile
+// (rank q takes blocks q nk / KS .. (q + 1) nk / KS - 1, each accumulated in
+// its tensor memory in order); rank q receives rows q 128 / KS .. of every
+// rank's partial through distributed shared memory and sums them in rank
+// order before the epilogue.  The split depends on the weight matrix only,
+// so a row's arithmetic does not depend on the batch.
+template <int BN, int STAGES, int KIND_BF16, int EPI, int KS>
 __global__ void __launch_bounds__(kTcThreads, 1)
     k_gemm_tc(const __grid_constant__ CUtensorMap tA, const __grid_constant__ CUtensorMap tB, TcGemm g) {
   extern __shared__ uint8_t smem_raw[];
@@ -149,19 +110,25 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   uint32_t* fail = tmem_slot + 1;
   int32_t* n_issued = reinterpret_cast<int32_t*>(fail + 1);     // K blocks whose TMA loads were issued
   int32_t* n_consumed = n_issued + 1;                          // K blocks the MMA issuer saw land
+  float* recv = reinterpret_cast<float*>(base);                 // split-K, after the products: the stages
+  constexpr int kRecvStride = BN + 4;
+  constexpr int kRows = kTileM / KS;                           // output rows of one rank (split-K)
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int m0 = blockIdx.x * kTileM;
   const int n0 = blockIdx.y * BN;
+  const int rank = KS > 1 ? (int)blockIdx.z : 0;    // the cluster spans z
   const int kblk = KIND_BF16 ? 64 : 128;             // elements per 128-byte K block
-  const int nk = (g.K + kblk - 1) / kblk;            // the tail block reads zeros past K
+  const int nk_all = (g.K + kblk - 1) / kblk;        // the tail block reads zeros past K
+  const int kb0 = rank * nk_all / KS;
+  const int nk = (rank + 1) * nk_all / KS - kb0;     // this rank's K blocks
   constexpr uint32_t kCols = tmem_cols<BN>();
   constexpr uint32_t kStageBytes = (kTileM + BN) * kKBlockBytes;
 
   // the row count was written by the step's prepare kernel, several launches
   // back, so it may be read before the wait on the previous kernel
   const int B = *g.nB;
-  if (n0 >= B) return;                            // uniform across the CTA
+  if (n0 >= B) return;                            // uniform across the CTA (and the cluster)
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
       mbar_init(full + s, 1);
@@ -189,11 +156,24 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   if (threadIdx.x == 0) {
     for (int kb = 0; kb < nk && kb < STAGES; ++kb) {
       mbar_expect_tx(full + kb, kStageBytes);
-      tma_load_2d(sA + (size_t)kb * kTileM * kKBlockBytes, &tA, full + kb, kb * kblk, m0);
+      tma_load_2d(sA + (size_t)kb * kTileM * kKBlockBytes, &tA, full + kb, (kb0 + kb) * kblk, m0);
     }
   }
   pdl_wait();
   pdl_trigger();
+  // split-K: this thread's output elements of the epilogue (rank's rows r =
+  // tid % kRows, batch rows n = tid / kRows + (256 / kRows) i) and, for the
+  // residual epilogue, their residuals, loaded while the products run
+  constexpr int kPerT = KS > 1 ? kRows * BN / kTcThreads : 1;
+  float pres[kPerT];
+  if (KS > 1) {
+    const int r = m0 + rank * kRows + (int)threadIdx.x % kRows;
+#pragma unroll
+    for (int i = 0; i < kPerT; ++i) {
+      const int n = n0 + (int)threadIdx.x / kRows + (kTcThreads / kRows) * i;
+      pres[i] = (EPI == EPI_RESID && n < B && r < g.M) ? __ldcg(g.y + (size_t)n * g.M + r) : 0.f;
+    }
+  }
 
   if (active && threadIdx.x == 0) {
     // TMA producer
@@ -201,7 +181,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     for (; kb < nk; ++kb) {
       const int s = kb % STAGES;
       const uint32_t ph = (uint32_t)(kb / STAGES) & 1u;
-      const int kc = kb * kblk;
+      const int kc = (kb0 + kb) * kblk;
       if (kb >= STAGES) {
         if (!mbar_wait(empty + s, ph ^ 1u)) {
           atomicOr(fail, 1u);
@@ -253,7 +233,44 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     for (int kb = *n_consumed; kb < *n_issued; ++kb)
       if (!mbar_wait(full + kb % STAGES, (uint32_t)(kb / STAGES) & 1u)) break;
   }
-  if (ready && *fail == 0) {
+  if (KS > 1) {
+    // every CTA of the cluster is done with its stage buffers: partials may
+    // go there
+    cg::this_cluster().sync();
+    if (ready && *fail == 0) {
+      // warp w sends TMEM lanes 32 (w % 4) .. + 31, columns of half w / 4, to
+      // the rank owning those rows
+      const int quarter = warp & 3, half = warp >> 2;
+      const int row = quarter * 32 + lane;           // 0 .. 127
+      const int dst = row / kRows, rl = row % kRows;
+      float* tgt = cg::this_cluster().map_shared_rank(recv, dst) + ((size_t)rank * kRows + rl) * kRecvStride;
+      const uint32_t tw = tmem + ((uint32_t)(quarter * 32) << 16);
+#pragma unroll 1
+      for (int c = half * (BN / 2); c < (half + 1) * (BN / 2); c += 16) {
+        float v[16];
+        tmem_ld16(tw + (uint32_t)c, v);
+#pragma unroll
+        for (int i = 0; i < 16; i += 4)
+          *reinterpret_cast<float4*>(tgt + c + i) = make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
+      }
+    }
+    cg::this_cluster().sync();                      // every partial of this rank's rows has arrived
+    if (*fail == 0) {
+      const int rr = (int)threadIdx.x % kRows;
+      const int r = m0 + rank * kRows + rr;
+      const float ws = (!KIND_BF16 && r < g.M) ? g.w_scale[r] : 1.f;
+#pragma unroll
+      for (int i = 0; i < kPerT; ++i) {
+        const int nl = (int)threadIdx.x / kRows + (kTcThreads / kRows) * i;
+        const int n = n0 + nl;
+        float y = recv[(size_t)rr * kRecvStride + nl];
+#pragma unroll
+        for (int q = 1; q < KS; ++q) y = __fadd_rn(y, recv[((size_t)q * kRows + rr) * kRecvStride + nl]);
+        if (!KIND_BF16) y *= ws * (n < B ? __ldg(g.x_scale + n) : 0.f);
+        epi_store<EPI>(g, r, n, B, y, pres[i]);
+      }
+    }
+  } else if (ready && *fail == 0) {
     // warp w reads TMEM lanes 32 (w % 4) .. + 31 (its lane quarter) and the
     // columns of half w / 4 of the tile
     const int quarter = warp & 3, half = warp >> 2;
@@ -279,27 +296,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         const int n = n0 + c + i;
         float y = v[i];
         if (!KIND_BF16) y *= ws * xs[i];
-        if (EPI == EPI_SWIGLU) {
-          const float up = __shfl_xor_sync(0xffffffffu, y, 1);   // rows 2j (gate), 2j + 1 (up)
-          if (n < B && r < g.M && (r & 1) == 0) {
-            const float h = silu_tc(y) * up;
-            if (g.h16)
-              static_cast<__nv_bfloat16*>(g.h16)[(size_t)n * (g.M / 2) + (r >> 1)] = __float2bfloat16_rn(h);
-            else
-              g.h_out[(size_t)n * (g.M / 2) + (r >> 1)] = h;
-          }
-        } else if (n < B && r < g.M) {
-          if (EPI == EPI_STORE) {
-            g.y[(size_t)n * g.M + r] = y;
-          } else if (EPI == EPI_RESID) {
-            g.y[(size_t)n * g.M + r] = res[i] + y;
-          } else {
-            if (g.zrows)
-              g.zrows[(size_t)n * g.M + r] = y;
-            else
-              g.st[g.slots[n]].z[r] = y;
-          }
-        }
+        epi_store<EPI>(g, r, n, B, y, res[i]);
       }
     }
   }
@@ -307,6 +304,16 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kCols));
+}
+
+// The bounded wait's give-up path, exercised without a fault: one thread
+// waits (at most `polls` polls) on an mbarrier nothing arrives on, and
+// records ST_TIMEOUT in *status when the wait gives up, as the pipelines do.
+__global__ void k_wait_selftest(uint32_t polls, int32_t* status) {
+  __shared__ uint64_t bar;
+  mbar_init(&bar, 1);
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  if (!mbar_wait(&bar, 0, polls)) atomicOr(status, ST_TIMEOUT);
 }
 
 using EncodeTiled = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
@@ -326,34 +333,68 @@ EncodeTiled encode_fn() {
   return fn;
 }
 
-template <int BN, int STAGES, int KB, int EPI>
+template <int BN, int STAGES, int KB, int EPI, int KS>
 cudaError_t prepare_tc_t() {
-  return cudaFuncSetAttribute(k_gemm_tc<BN, STAGES, KB, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)tc_smem_bytes<BN, STAGES>());
+  return cudaFuncSetAttribute(k_gemm_tc<BN, STAGES, KB, EPI, KS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)tc_smem_bytes<BN, STAGES, KS>());
+}
+
+template <int KB, int EPI, int KS>
+cudaError_t prepare_tc_ks() {
+  cudaError_t e = prepare_tc_t<32, 6, KB, EPI, KS>();
+  if (e == cudaSuccess) e = prepare_tc_t<64, 6, KB, EPI, KS>();
+  if (e == cudaSuccess) e = prepare_tc_t<128, 6, KB, EPI, KS>();
+  if (e == cudaSuccess) e = prepare_tc_t<256, 4, KB, EPI, KS>();
+  return e;
 }
 
 template <int KB, int EPI>
 cudaError_t prepare_tc_epi() {
-  cudaError_t e = prepare_tc_t<32, 6, KB, EPI>();
-  if (e == cudaSuccess) e = prepare_tc_t<64, 6, KB, EPI>();
-  if (e == cudaSuccess) e = prepare_tc_t<128, 6, KB, EPI>();
-  if (e == cudaSuccess) e = prepare_tc_t<256, 4, KB, EPI>();
+  cudaError_t e = prepare_tc_ks<KB, EPI, 1>();
+  if (e == cudaSuccess) e = prepare_tc_ks<KB, EPI, 2>();
+  if (e == cudaSuccess) e = prepare_tc_ks<KB, EPI, 4>();
   return e;
 }
 
-template <int BN, int STAGES, int KB, int EPI>
+template <int BN, int STAGES, int KB, int EPI, int KS>
 cudaError_t launch_tc_t(const TcGemm& g, cudaStream_t s, bool pdl) {
-  constexpr size_t smem = tc_smem_bytes<BN, STAGES>();
-  auto kern = k_gemm_tc<BN, STAGES, KB, EPI>;
-  dim3 grid((g.M + kTileM - 1) / kTileM, (g.Bmax + BN - 1) / BN);
+  constexpr size_t smem = tc_smem_bytes<BN, STAGES, KS>();
+  auto kern = k_gemm_tc<BN, STAGES, KB, EPI, KS>;
   const CUtensorMap* a = reinterpret_cast<const CUtensorMap*>(g.tmap_a);
   const CUtensorMap* b = reinterpret_cast<const CUtensorMap*>(g.tmap_b);
-  return launch_kernel(kern, grid, dim3(kTcThreads), smem, s, pdl, *a, *b, g);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((g.M + kTileM - 1) / kTileM, (g.Bmax + BN - 1) / BN, KS);
+  cfg.blockDim = dim3(kTcThreads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[2];
+  int na = 0;
+  if (KS > 1) {
+    at[na].id = cudaLaunchAttributeClusterDimension;
+    at[na].val.clusterDim.x = 1;
+    at[na].val.clusterDim.y = 1;
+    at[na].val.clusterDim.z = KS;
+    ++na;
+  }
+  if (pdl) {
+    at[na].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[na].val.programmaticStreamSerializationAllowed = 1;
+    ++na;
+  }
+  cfg.attrs = at;
+  cfg.numAttrs = na;
+  return cudaLaunchKernelEx(&cfg, kern, *a, *b, g);
 }
 
 template <int BN, int KB, int EPI>
 cudaError_t launch_tc_bn(const TcGemm& g, cudaStream_t s, bool pdl) {
-  return launch_tc_t<BN, BN >= 256 ? 4 : 6, KB, EPI>(g, s, pdl);
+  constexpr int ST = BN >= 256 ? 4 : 6;
+  switch (g.ks) {
+    case 1: return launch_tc_t<BN, ST, KB, EPI, 1>(g, s, pdl);
+    case 2: return launch_tc_t<BN, ST, KB, EPI, 2>(g, s, pdl);
+    case 4: return launch_tc_t<BN, ST, KB, EPI, 4>(g, s, pdl);
+  }
+  return cudaErrorInvalidValue;
 }
 
 template <int KB, int EPI>
@@ -458,6 +499,11 @@ __global__ void k_act_plain(Dims D, Batch b, const float* x, int cols, void* out
 
 }  // namespace
 
+cudaError_t launch_wait_selftest(uint32_t polls, int32_t* status, cudaStream_t s) {
+  k_wait_selftest<<<1, 1, 0, s>>>(polls, status);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_act_plain(const Dims& D, const Batch& b, const float* x, int cols, int kind_bf16, void* out,
                              float* out_scale, cudaStream_t s) {
   return launch_kernel(kind_bf16 ? k_act_plain<1> : k_act_plain<0>, dim3(b.Bmax), dim3(256), 0, s, D.pdl, D, b, x,
@@ -475,6 +521,12 @@ bool tc_encode_tmap(void* tmap, const void* base, int elem_bytes, int64_t inner,
   return fn(reinterpret_cast<CUtensorMap*>(tmap), dt, 2, const_cast<void*>(base), dims, strides, box, es,
             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+int tc_ksplit(int K, int kind_bf16) {
+  const int kblk = kind_bf16 ? 64 : 128;
+  const int nk = (K + kblk - 1) / kblk;
+  return nk >= 16 ? 4 : nk >= 8 ? 2 : 1;
 }
 
 cudaError_t prepare_tc_kernels() {

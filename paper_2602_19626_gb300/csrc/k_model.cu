@@ -489,7 +489,6 @@ cudaError_t prepare_model_kernels(const Dims& D, int fmt) {
                   : fmt == NC_BF16 ? prepare_gemv_f<NC_BF16>(cmax)
                                    : prepare_gemv_f<NC_FP8E4M3>(cmax);
   const int grp = D.hq / D.hkv;
-  if (e == cudaSuccess && D.kv_bf16) e = prepare_attn_tc(D);
   if (e == cudaSuccess) e = prepare_rows_s<1>(grp);
   if (e == cudaSuccess) e = prepare_rows_s<2>(grp);
   if (e == cudaSuccess) e = prepare_rows_s<4>(grp);
@@ -541,26 +540,9 @@ static cudaError_t launch_attn_rows(const Dims& D, const Batch& b, int layer, co
   }
 }
 
-// Tensor-core attention (BF16 cache): rows per CTA group and CTAs per group.
-static cudaError_t launch_attn_bf16(const Dims& D, const Batch& b, int layer, const float* qkv, float* attn_out,
-                                    void* out16, cudaStream_t s) {
-  if (attn_pf_fits(D, b) && !D.attn_cluster) return launch_attn_pf(D, b, layer, qkv, attn_out, out16, s);
-  const int grp = D.hq / D.hkv;
-  int rq = 1;
-  if (b.pos && b.pm >= 2) {
-    rq = std::min(8, b.pm);
-    while (rq > 1 && attn_tc_smem(rq, grp, 1) > 220 * 1024) rq /= 2;
-  }
-  int S = 8;
-  if (D.attn_cluster) S = D.attn_cluster;
-  else
-    while (S > 1 && (int64_t)D.hkv * (b.Bmax / rq) * S > 4 * (int64_t)D.n_sm) S /= 2;
-  return launch_attn_tc(D, b, layer, rq, S, qkv, attn_out, out16, s);
-}
-
 cudaError_t launch_attn(const Dims& D, const Batch& b, int layer, const float* qkv, float* attn_out,
                         cudaStream_t s, void* out16) {
-  if (D.kv_bf16) return launch_attn_bf16(D, b, layer, qkv, attn_out, out16, s);
+  if (D.kv_bf16) return launch_attn_t5(D, b, layer, qkv, attn_out, out16, s);
   if (b.pos && b.pm >= 2 && b.pm % 2 == 0 && b.Bmax % std::min(kRowsMax, b.pm) == 0)
     return launch_attn_rows(D, b, layer, AttnIO{qkv, attn_out}, s);
   const int S = attn_split(D, b);

@@ -2,7 +2,7 @@
 // (Sec. 3.4), linear mix (Sec. 3.5), CDF quantisation with floors and the
 // prefix sum (Sec. 3.3), the head / mixer updates, and the N-gram tables.
 //
-// One stream is handled by a cluster of CTAs (kStepCluster for the per-token
+// One stream is handled by a cluster of CTAs (8 or 16 for the per-token
 // step, kVocabCluster for the standalone quantiser); each CTA owns a
 // contiguous chunk of the vocabulary and each thread a contiguous run of E
 // symbols.  The standalone quantiser reduces thread -> warp (fixed xor tree)
@@ -293,23 +293,24 @@ __device__ void scan_round(const uint32_t (&c)[E], int v0, int V, uint32_t T, ui
 }
 
 // ======================================================================= step
-// The per-token step of one stream (Sec. 3.3-3.7) on a cluster of
-// kStepCluster CTAs.  CTA `rank` owns the vocabulary chunk from
-// base = rank kStepThreads E, its warp w the 32 E symbols from
-// wbase = base + 32 E w, lane l the E symbols from v0 = wbase + E l.
-// A reduction over the vocabulary takes one cluster barrier: every warp
-// publishes its partials in a slot of its CTA's shared memory, and after the
-// barrier every warp reads all kStepCluster x kStepWarps of them (lane l the
-// four of global warp index 4l .. 4l + 3) and reduces them with the same
-// shuffles, so every warp of the cluster holds the same result, whatever the
-// batch, the slot or the launch.  The arithmetic is written with explicitly
-// rounded operations and fixed approximations, so the single-step and the
-// multi-position kernels below compute the same bits.  FULL: the vocabulary
-// fills the cluster's E kStepThreads kStepCluster symbols exactly (no
-// symbol past V, every run 16-byte aligned).
-
-constexpr int kStepWarps = kStepThreads / 32;
-static_assert(kStepCluster * kStepWarps == 128, "four warp partials per lane");
+// The per-token step of one stream (Sec. 3.3-3.7) on a cluster of CL CTAs
+// of 4,096 / CL threads (CL = 8 or 16): always 128 warps, global warp
+// gw = rank (128 / CL) + w owning the 32 E symbols from wbase = 32 E gw, lane
+// l the E symbols from v0 = wbase + E l.  A reduction over the vocabulary
+// takes one cluster barrier: every warp publishes its partials in a slot of
+// its CTA's shared memory, and after the barrier every warp reads all 128 of
+// them (lane l the four of global warps 4l .. 4l + 3) and reduces them with
+// the same shuffles, so every warp of the cluster holds the same result,
+// whatever the batch, the slot, the launch or the cluster shape.  The
+// arithmetic is written with explicitly rounded operations and fixed
+// approximations, so the single-step and the multi-position kernels below
+// compute the same bits.  FULL: the vocabulary fills the cluster's 4,096 E
+// symbols exactly (no symbol past V, every run 16-byte aligned).
+constexpr int kClusterWarps = 128;               // four warp partials per lane of a reducing warp
+template <int CL>
+__host__ __device__ constexpr int step_threads() {
+  return kClusterWarps * 32 / CL;
+}
 // A valid warp's count sum is at most T + eps K < 1.5 2^24 (T <= 2^24), so
 // 128 clamped warp sums stay below 2^32; larger sums are flagged bad.
 constexpr uint32_t kWarpCountCap = 3u << 23;
@@ -330,13 +331,12 @@ __device__ __forceinline__ void cluster_arrive() {
 __device__ __forceinline__ void cluster_wait() { asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory"); }
 
 // Every CTA's inbox for one cluster barrier (two alternate): each warp of
-// the cluster stores its partials at its global index rank kStepWarps + w in
-// every CTA's inbox before the barrier (posted remote stores, made visible by
+// the cluster stores its partials at its global index gw in every CTA's inbox before the barrier (posted remote stores, made visible by
 // the barrier's release), so after it every warp reduces them from its own
 // CTA's shared memory.
 struct StepSlot {
-  float4 sm[kStepCluster * kStepWarps];   // softmax: warp maximum m_w, sum of exp(s - m_w), entropy part
-  uint4 qn[kStepCluster * kStepWarps];    // quantiser: count sum, first maximum (value bits, index), bad flag
+  float4 sm[kClusterWarps];   // softmax: warp maximum m_w, sum of exp(s - m_w), entropy part
+  uint4 qn[kClusterWarps];    // quantiser: count sum, first maximum (value bits, index), bad flag
   float4 obs;                             // the observed token's p_tilde(t), p_ng(t), log p_tilde(t)
 };
 
@@ -350,14 +350,14 @@ struct StepShared {
 struct Lanes {
   int rank, w, lane, gw, wbase, v0;
 };
-template <int E>
+template <int E, int CL>
 __device__ __forceinline__ Lanes lanes_of(int rank) {
   Lanes L;
   L.rank = rank;
   L.w = threadIdx.x >> 5;
   L.lane = threadIdx.x & 31;
-  L.gw = rank * kStepWarps + L.w;
-  L.wbase = rank * kStepThreads * E + L.w * 32 * E;
+  L.gw = rank * (kClusterWarps / CL) + L.w;
+  L.wbase = L.gw * 32 * E;
   L.v0 = L.wbase + L.lane * E;
   return L;
 }
@@ -383,16 +383,17 @@ __device__ __forceinline__ void load_runf(const float* src, int v0, int V, float
   }
 }
 
-// Lanes 0 .. kStepCluster - 1 store the warp's (warp-uniform) partial v at
-// its global index in the inbox array `mine` of every CTA.
-template <typename T>
+// Lanes 0 .. CL - 1 store the warp's (warp-uniform) partial v at its global
+// index in the inbox array `mine` of every CTA.
+template <int CL, typename T>
 __device__ __forceinline__ void push_part(cg::cluster_group& cl, T* mine, const Lanes& L, T v) {
-  if (L.lane < kStepCluster) cl.map_shared_rank(mine, L.lane)[L.gw] = v;
+  if (L.lane < CL) cl.map_shared_rank(mine, L.lane)[L.gw] = v;
 }
 // The observed token's values into every CTA's inbox.
+template <int CL>
 __device__ __forceinline__ void push_obs(cg::cluster_group& cl, float4* mine, float4 v) {
 #pragma unroll
-  for (int r = 0; r < kStepCluster; ++r) *cl.map_shared_rank(mine, r) = v;
+  for (int r = 0; r < CL; ++r) *cl.map_shared_rank(mine, r) = v;
 }
 // The inbox entries of global warps 4 lane .. 4 lane + 3.
 template <typename T>
@@ -523,6 +524,12 @@ __device__ __forceinline__ void probs_tilde(const float (&e)[E], float m_w, cons
   for (int i = 0; i < E; ++i) pt[i] = __fmul_rn(e[i], f);
 }
 
+// The step's normaliser, maximum and mixer weights are finite (the quantiser
+// then needs no per-symbol range check).
+__device__ __forceinline__ bool finite_step(const Soft& sm, float2 w) {
+  return isfinite(sm.M) && isfinite(sm.S) && sm.S >= 0.998f && isfinite(w.x) && isfinite(w.y);
+}
+
 // The mixer's weights softmax(theta) (Sec. 3.5).
 __device__ __forceinline__ float2 mix_weights(float th0, float th1) {
   const float tm = fmaxf(th0, th1);
@@ -552,25 +559,47 @@ __device__ __forceinline__ void coded_probs(const float (&pt)[E], const float (&
 // floor) and the warp's count sum, first maximum and bad flag, packed for
 // publication.  scan: also excl = the counts of the warp's lanes below this
 // one.  am_i / am_c = the thread's first maximum and its count.
+// `sure`: the step's softmax normaliser S >= 0.998 (it is at least the
+// maximum's numerator, 1 up to rounding), its maximum and the mixer weights
+// are finite (uniform across the cluster), so every p is a finite value in
+// [0, 1.0021) (numerators e <= 1 + 2^-22 over S, N-gram probabilities <= 1,
+// weights summing to 1): the product p K stays below 2^24, where the
+// round-toward-zero product has the exact product's integer part, and no
+// per-symbol range check is needed.  Otherwise every value is checked.
 template <int E, bool FULL>
 __device__ __forceinline__ uint4 quant_part(const float (&p)[E], const Lanes& L, int V, uint32_t K, float Kf,
-                                            uint32_t floor_c, bool scan, uint32_t (&c)[E], uint32_t& excl, int& am_i,
-                                            uint32_t& am_c) {
+                                            uint32_t floor_c, bool scan, bool sure, uint32_t (&c)[E], uint32_t& excl,
+                                            int& am_i, uint32_t& am_c) {
   bool bad = false;
   uint32_t ts = 0;
   float amv = -INFINITY;
   am_i = 0x7fffffff;
   am_c = 0;
+  if (sure) {
 #pragma unroll
-  for (int i = 0; i < E; ++i) {
-    const bool in = in_vocab<FULL>(L.v0 + i, V);
-    const uint32_t q = floor_count(p[i], K, Kf, bad);
-    c[i] = in ? max(q, floor_c) : 0u;
-    ts += c[i];
-    if (in && p[i] > amv) {                        // strict: keeps the first maximum
-      amv = p[i];
-      am_i = L.v0 + i;
-      am_c = c[i];
+    for (int i = 0; i < E; ++i) {
+      const bool in = in_vocab<FULL>(L.v0 + i, V);
+      const uint32_t q = __float2uint_rz(__fmul_rz(p[i], Kf));
+      c[i] = in ? max(q, floor_c) : 0u;
+      ts += c[i];
+      if (in && p[i] > amv) {                      // strict: keeps the first maximum
+        amv = p[i];
+        am_i = L.v0 + i;
+        am_c = c[i];
+      }
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < E; ++i) {
+      const bool in = in_vocab<FULL>(L.v0 + i, V);
+      const uint32_t q = floor_count(p[i], K, Kf, bad);
+      c[i] = in ? max(q, floor_c) : 0u;
+      ts += c[i];
+      if (in && p[i] > amv) {
+        amv = p[i];
+        am_i = L.v0 + i;
+        am_c = c[i];
+      }
     }
   }
   if (ts > kWarpCountCap) {                      // invalid: keeps the warp's sum below 2^32
@@ -721,7 +750,7 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 // Copy one N-gram state into shared memory (asynchronously, 16 bytes per thread).
 __device__ __forceinline__ void snap_copy_async(NgSnap* dst, const NgSnap* src) {
   constexpr int kPieces = (int)(sizeof(NgSnap) / 16);
-  static_assert(kPieces <= kStepThreads, "one piece per thread");
+  static_assert(kPieces <= step_threads<16>(), "one piece per thread");
   if ((int)threadIdx.x < kPieces)
     cp_async16(reinterpret_cast<char*>(dst) + 16 * threadIdx.x, reinterpret_cast<const char*>(src) + 16 * threadIdx.x);
   cp_async_commit();
@@ -735,12 +764,12 @@ __device__ void ng_snapshot(const Dims& D, const StreamDev& st, NgSnap* out, int
 // mixer, then the N-gram and the stream's bookkeeping).  The decoder runs
 // the two in separate launches (it learns the token in between); the
 // arithmetic is the same in either case.
-template <int E, bool FULL>
-__global__ void __launch_bounds__(kStepThreads, 1) k_vocab(Dims D, Batch b, VocabIO io) {
+template <int E, bool FULL, int CL>
+__global__ void __launch_bounds__(step_threads<CL>(), 1) k_vocab(Dims D, Batch b, VocabIO io) {
   extern __shared__ float4 dyn4[];
   __shared__ StepShared sh;
   cg::cluster_group cl = cg::this_cluster();
-  const int j = blockIdx.x / kStepCluster;
+  const int j = blockIdx.x / CL;
   // after a prefill the previous kernel updated the stream's state: nothing
   // of it may be read before that kernel completed
   if (b.z_in) {
@@ -748,7 +777,7 @@ __global__ void __launch_bounds__(kStepThreads, 1) k_vocab(Dims D, Batch b, Voca
     pdl_trigger();
   }
   if (j >= *b.nB) return;                        // uniform across the cluster
-  const Lanes L = lanes_of<E>((int)cl.block_rank());
+  const Lanes L = lanes_of<E, CL>((int)cl.block_rank());
   StreamDev& st = b.st[b.slots[j]];
   const int V = D.V;
   const bool ngram = D.order > 0;
@@ -766,7 +795,7 @@ __global__ void __launch_bounds__(kStepThreads, 1) k_vocab(Dims D, Batch b, Voca
   if (ngram) {
     load_counts<E>(st.uni, L.v0, V, cnt);
     zero_region<E>(spw, L.lane);
-    ng_snapshot(D, st, &sh.ng[0], threadIdx.x, kStepThreads);
+    ng_snapshot(D, st, &sh.ng[0], threadIdx.x, step_threads<CL>());
     __syncthreads();
   }
   const int i_tok = st.n_coded + 1;              // 1-based index of the token being coded
@@ -806,7 +835,7 @@ __global__ void __launch_bounds__(kStepThreads, 1) k_vocab(Dims D, Batch b, Voca
     png_t = pick<E>(png, L.v0, t);
   }
   const float4 part = softmax_part<E>(s, e, D.skip ? entropy_part<E>(png) : 0.f);
-  push_part(cl, sh.slot[0].sm, L, part);
+  push_part<CL>(cl, sh.slot[0].sm, L, part);
   cl.sync();
   float4 smv[4];
   local_parts(sh.slot[0].sm, L.lane, smv);
@@ -823,15 +852,15 @@ __global__ void __launch_bounds__(kStepThreads, 1) k_vocab(Dims D, Batch b, Voca
   coded_probs<E>(pt, png, w, skipped, mixing, p);
   if (probe && io.probe_p) store_run<E>(io.probe_p + prow, L.v0, V, p);
   if (owner)
-    push_obs(cl, &sh.slot[1].obs,
+    push_obs<CL>(cl, &sh.slot[1].obs,
              make_float4(pick<E>(pt, L.v0, t), png_t, __fsub_rn(__fsub_rn(s_t, sm.M), __logf(sm.S)), 0.f));
   const uint32_t T = 1u << D.log2T, K = T - (uint32_t)V * D.floor;
   uint32_t c[E], excl = 0, am_c = 0, below_t = 0, c_t = 0;
   int am_i = 0x7fffffff;
   const bool scan = io.cdf || (t >= L.wbase && t < L.wbase + 32 * E);
   if (io.predict) {
-    const uint4 qp = quant_part<E, FULL>(p, L, V, K, (float)K, D.floor, scan, c, excl, am_i, am_c);
-    push_part(cl, sh.slot[1].qn, L, qp);
+    const uint4 qp = quant_part<E, FULL>(p, L, V, K, (float)K, D.floor, scan, finite_step(sm, w), c, excl, am_i, am_c);
+    push_part<CL>(cl, sh.slot[1].qn, L, qp);
     if (owner) {
       counts_around<E>(c, L.v0, t, below_t, c_t);
       below_t += excl;
@@ -891,18 +920,18 @@ __global__ void __launch_bounds__(kStepThreads, 1) k_vocab(Dims D, Batch b, Voca
 // The next position's logits, token and activity and the N-gram state two
 // positions ahead are fetched between the barrier's arrive and wait, so the
 // barrier's release never waits for them.
-template <int E, bool FULL>
-__global__ void __launch_bounds__(kStepThreads, 1)
+template <int E, bool FULL, int CL>
+__global__ void __launch_bounds__(step_threads<CL>(), 1)
     k_vocab_seq(Dims D, Batch b, VocabIO io, int m, int n_streams, const float* zrows, const int32_t* nb_step,
                 const int32_t* obs_step, const NgSnap* snap) {
   extern __shared__ float4 dyn4[];
   __shared__ StepShared sh;
   cg::cluster_group cl = cg::this_cluster();
-  const int j = blockIdx.x / kStepCluster;
+  const int j = blockIdx.x / CL;
   pdl_wait();
   pdl_trigger();
   if (m < 1 || j >= nb_step[0]) return;          // uniform across the cluster
-  const Lanes L = lanes_of<E>((int)cl.block_rank());
+  const Lanes L = lanes_of<E, CL>((int)cl.block_rank());
   StreamDev& st = b.st[b.slots[j]];
   const int V = D.V;
   const bool ngram = D.order > 0;
@@ -1004,7 +1033,7 @@ __global__ void __launch_bounds__(kStepThreads, 1)
     }
     const float4 part = softmax_part<E>(s, e, D.skip ? entropy_part<E>(png) : 0.f);
     StepSlot& in = sh.slot[nb & 1];
-    push_part(cl, in.sm, L, part);
+    push_part<CL>(cl, in.sm, L, part);
     if (ngram) cp_async_wait_all();              // the state of position r + 2, added after this barrier
     cluster_arrive();
     // outside the barrier's release: position r + 1's logits, token and slot
@@ -1042,12 +1071,12 @@ __global__ void __launch_bounds__(kStepThreads, 1)
     if (probe && io.probe_p) store_run<E>(io.probe_p + prow, L.v0, V, p);
     StepSlot& nx = sh.slot[nb & 1];
     if (owner)
-      push_obs(cl, &nx.obs,
+      push_obs<CL>(cl, &nx.obs,
                make_float4(pick<E>(pt, L.v0, t), png_t, __fsub_rn(__fsub_rn(s_t, sm.M), __logf(sm.S)), 0.f));
     uint32_t c[E], excl = 0;
     const bool scan = io.intervals && t >= L.wbase && t < L.wbase + 32 * E;
-    const uint4 qp = quant_part<E, FULL>(p, L, V, K, Kf, D.floor, scan, c, excl, p_am_i, p_am_c);
-    push_part(cl, nx.qn, L, qp);
+    const uint4 qp = quant_part<E, FULL>(p, L, V, K, Kf, D.floor, scan, finite_step(sm, w), c, excl, p_am_i, p_am_c);
+    push_part<CL>(cl, nx.qn, L, qp);
     p_own = owner && io.intervals;
     if (owner) {
       counts_around<E>(c, L.v0, t, p_below, p_ct);
@@ -1513,27 +1542,76 @@ static int vocab_E(int V, int ctas = kVocabCluster, int threads = kVocabThreads)
   return e < 4 ? 4 : e;
 }
 
-// FULL: the vocabulary fills the step cluster's symbols exactly.
+// FULL: the vocabulary fills the step cluster's 4,096 E symbols exactly.
 template <int E>
 static bool step_full(int V) {
-  return V == kStepCluster * kStepThreads * E;
+  return V == kClusterWarps * 32 * E;
 }
 
+// 16-CTA clusters (a non-portable size) are used when the device places them.
+static bool g_cl16 = false;
+
+// CTAs per stream of a step launch over `rows` streams: 16 while the
+// clusters fit in one wave (one stream or a few: the per-position latency
+// falls with the work per SM), else 8 (more streams per wave).  Results do
+// not depend on it.
+static int step_cluster(const Dims& D, int rows) {
+  return g_cl16 && rows * 16 <= D.n_sm ? 16 : 8;
+}
+
+template <int E, bool FULL, int CL>
+static cudaError_t vocab_tfc(const Dims& D, const Batch& b, const VocabIO& io, cudaStream_t s) {
+  const size_t smem = (size_t)step_threads<CL>() * E * sizeof(float);
+  return launch_kernel_cluster(&k_vocab<E, FULL, CL>, dim3(b.Bmax * CL), dim3(step_threads<CL>()), smem, s, D.pdl,
+                               CL, D, b, io);
+}
 template <int E>
 static cudaError_t vocab_t(const Dims& D, const Batch& b, const VocabIO& io, cudaStream_t s) {
-  const size_t smem = (size_t)kStepThreads * E * sizeof(float);
-  return launch_kernel_cluster(step_full<E>(D.V) ? &k_vocab<E, true> : &k_vocab<E, false>, dim3(b.Bmax * kStepCluster),
-                               dim3(kStepThreads), smem, s, D.pdl, kStepCluster, D, b, io);
+  const bool full = step_full<E>(D.V);
+  if (step_cluster(D, b.Bmax) == 16)
+    return full ? vocab_tfc<E, true, 16>(D, b, io, s) : vocab_tfc<E, false, 16>(D, b, io, s);
+  return full ? vocab_tfc<E, true, 8>(D, b, io, s) : vocab_tfc<E, false, 8>(D, b, io, s);
 }
 
+template <int E, bool FULL, int CL>
+static cudaError_t prepare_vocab_tfc() {
+  const int smem = step_threads<CL>() * E * (int)sizeof(float);
+  cudaError_t e = cudaFuncSetAttribute(k_vocab<E, FULL, CL>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_vocab_seq<E, FULL, CL>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e == cudaSuccess && CL > 8) {
+    e = cudaFuncSetAttribute(k_vocab<E, FULL, CL>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_vocab_seq<E, FULL, CL>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  }
+  return e;
+}
+// Whether clusters of CL CTAs of the loop kernel can be placed on the device.
+template <int E, bool FULL, int CL>
+static bool clusters_fit() {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(CL);
+  cfg.blockDim = dim3(step_threads<CL>());
+  cfg.dynamicSmemBytes = (size_t)step_threads<CL>() * E * sizeof(float);
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = CL;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  int n = 0;
+  const bool ok = cudaOccupancyMaxActiveClusters(&n, &k_vocab_seq<E, FULL, CL>, &cfg) == cudaSuccess && n > 0;
+  cudaGetLastError();
+  return ok;
+}
 template <int E, bool FULL>
 static cudaError_t prepare_vocab_tf() {
-  cudaError_t e = cudaFuncSetAttribute(k_vocab<E, FULL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       kStepThreads * E * (int)sizeof(float));
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_vocab_seq<E, FULL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             kStepThreads * E * (int)sizeof(float));
-  return e;
+  cudaError_t e = prepare_vocab_tfc<E, FULL, 8>();
+  if (e != cudaSuccess) return e;
+  g_cl16 = prepare_vocab_tfc<E, FULL, 16>() == cudaSuccess && clusters_fit<E, FULL, 16>();
+  cudaGetLastError();
+  return cudaSuccess;
 }
 template <int E>
 static cudaError_t prepare_vocab_t(int V) {
@@ -1541,7 +1619,7 @@ static cudaError_t prepare_vocab_t(int V) {
 }
 
 cudaError_t prepare_vocab_kernels(const Dims& D) {
-  switch (vocab_E(D.V, kStepCluster, kStepThreads)) {
+  switch (vocab_E(D.V, 8, step_threads<8>())) {
     case 4: return prepare_vocab_t<4>(D.V);
     case 8: return prepare_vocab_t<8>(D.V);
     case 12: return prepare_vocab_t<12>(D.V);
@@ -1550,20 +1628,30 @@ cudaError_t prepare_vocab_kernels(const Dims& D) {
   return cudaErrorInvalidValue;
 }
 
+template <int E, bool FULL, int CL>
+static cudaError_t vocab_seq_tfc(const Dims& D, const Batch& b, const VocabIO& io, int m, const float* zrows,
+                                 const int32_t* nb_step, const int32_t* obs_step, const NgSnap* snap,
+                                 cudaStream_t s) {
+  const size_t smem = (size_t)step_threads<CL>() * E * sizeof(float);
+  return launch_kernel_cluster(&k_vocab_seq<E, FULL, CL>, dim3(b.Bmax * CL), dim3(step_threads<CL>()), smem, s,
+                               D.pdl, CL, D, b, io, m, b.Bmax, zrows, nb_step, obs_step, snap);
+}
 template <int E>
 static cudaError_t vocab_seq_t(const Dims& D, const Batch& b, const VocabIO& io, int m, const float* zrows,
                                const int32_t* nb_step, const int32_t* obs_step, const NgSnap* snap,
                                cudaStream_t s) {
-  const size_t smem = (size_t)kStepThreads * E * sizeof(float);
-  return launch_kernel_cluster(step_full<E>(D.V) ? &k_vocab_seq<E, true> : &k_vocab_seq<E, false>,
-                               dim3(b.Bmax * kStepCluster), dim3(kStepThreads), smem, s, D.pdl, kStepCluster, D, b,
-                               io, m, b.Bmax, zrows, nb_step, obs_step, snap);
+  const bool full = step_full<E>(D.V);
+  if (step_cluster(D, b.Bmax) == 16)
+    return full ? vocab_seq_tfc<E, true, 16>(D, b, io, m, zrows, nb_step, obs_step, snap, s)
+                : vocab_seq_tfc<E, false, 16>(D, b, io, m, zrows, nb_step, obs_step, snap, s);
+  return full ? vocab_seq_tfc<E, true, 8>(D, b, io, m, zrows, nb_step, obs_step, snap, s)
+              : vocab_seq_tfc<E, false, 8>(D, b, io, m, zrows, nb_step, obs_step, snap, s);
 }
 
 cudaError_t launch_vocab_seq(const Dims& D, const Batch& b, const VocabIO& io, int m, const float* zrows,
                              const int32_t* nb_step, const int32_t* obs_step, const NgSnap* snap, cudaStream_t s) {
   if (D.order > 0 && !snap) return cudaErrorInvalidValue;
-  switch (vocab_E(D.V, kStepCluster, kStepThreads)) {
+  switch (vocab_E(D.V, 8, step_threads<8>())) {
     case 4: return vocab_seq_t<4>(D, b, io, m, zrows, nb_step, obs_step, snap, s);
     case 8: return vocab_seq_t<8>(D, b, io, m, zrows, nb_step, obs_step, snap, s);
     case 12: return vocab_seq_t<12>(D, b, io, m, zrows, nb_step, obs_step, snap, s);
@@ -1580,7 +1668,7 @@ cudaError_t launch_ngram_seq(const Dims& D, const Batch& b, int m, const int32_t
 }
 
 cudaError_t launch_vocab(const Dims& D, const Batch& b, const VocabIO& io, cudaStream_t s) {
-  switch (vocab_E(D.V, kStepCluster, kStepThreads)) {
+  switch (vocab_E(D.V, 8, step_threads<8>())) {
     case 4: return vocab_t<4>(D, b, io, s);
     case 8: return vocab_t<8>(D, b, io, s);
     case 12: return vocab_t<12>(D, b, io, s);

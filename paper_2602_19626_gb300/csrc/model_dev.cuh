@@ -1,5 +1,5 @@
 // Device building blocks of the decode step, shared by the model kernels
-// (k_model.cu) and the tensor-core attention (k_attn_tc.cu), so that every
+// (k_model.cu) and the tensor-core attention (k_attn_t5.cu), so that every
 // kernel computing a value uses the same operations in the same order.
 #pragma once
 

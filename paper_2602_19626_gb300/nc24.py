@@ -90,6 +90,7 @@ _SIGS = {
     "nc_ans_encode": (C.c_int, [_P, _P, C.c_int64, C.c_int, _P, _SZP]),
     "nc_split_chunks": (C.c_int, [_P, C.c_int64, _P, C.c_int, C.c_int, _P, C.POINTER(C.c_int)]),
     "nc_ans_decode": (C.c_int, [_P, C.c_size_t, _P, C.c_int, C.c_int64, C.c_int, _P]),
+    "nc_selftest_wait": (C.c_int, [_P, C.c_uint32]),
     "nc_mix_nll_fwd": (C.c_int, [_P, _P, _P, _P, _P, _P, C.c_int, C.c_int, C.c_float, _P, _P]),
     "nc_mix_nll_bwd": (C.c_int, [_P, _P, _P, _P, _P, _P, _P, C.c_int, C.c_int, C.c_float, _P, _P, _P]),
 }
@@ -382,6 +383,11 @@ class Context:
         self._check(lib.nc_encode_probe(self.h, ln.size, _ptr(tokens_dev), _ptr(offs), _ptr(ln),
                                         _ptr(intervals_dev), stride, probe_pos, _ptr(z), _ptr(p_tilde),
                                         _ptr(p_ng), _ptr(p)), "nc_encode_probe")
+
+    def selftest_wait(self, polls: int):
+        """One bounded device wait that gives up (nc_selftest_wait): raises
+        NcError(NC_ETIMEOUT) and leaves the context poisoned."""
+        self._check(lib.nc_selftest_wait(self.h, polls), "nc_selftest_wait")
 
     def decode(self, data: bytes):
         buf = np.frombuffer(data, dtype=np.uint8).copy()

@@ -7,6 +7,10 @@ cores while the GPU side of a test runs.
 """
 from __future__ import annotations
 
+import multiprocessing as mp
+import os
+from concurrent.futures import ProcessPoolExecutor
+
 import numpy as np
 
 import synthetic as S
@@ -52,3 +56,32 @@ def logits_recorded(shape, seed: int, fmt: str, tokens, record_at):
             out[k] = z.copy()
         last = int(t)
     return out
+
+
+_BLAS_VARS = ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS")
+
+
+class OraclePool:
+    """A pool of `workers` spawned processes whose BLAS libraries each use
+    cores / workers threads (oversubscribed BLAS threads spin and slow every
+    worker down many times over).  The thread limits sit in the environment
+    from construction to close(), so every worker the pool starts inherits
+    them; the calling process keeps the threads it already has."""
+
+    def __init__(self, workers: int):
+        per = str(max(1, (os.cpu_count() or 1) // workers))
+        self._saved = {k: os.environ.get(k) for k in _BLAS_VARS}
+        for k in _BLAS_VARS:
+            os.environ[k] = per
+        self.pool = ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn"))
+
+    def submit(self, fn, *args):
+        return self.pool.submit(fn, *args)
+
+    def close(self):
+        self.pool.shutdown(wait=True, cancel_futures=True)
+        for k, v in self._saved.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v

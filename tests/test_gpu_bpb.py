@@ -9,9 +9,6 @@ oracle's on the FP32 weights (the format's cost).  The GPU round trip must
 be lossless.  LLM-only cases (N-gram and mixer off, p = p_tilde) show the
 format's cost where the mixer cannot hide it behind the N-gram.
 """
-import multiprocessing as mp
-from concurrent.futures import ProcessPoolExecutor
-
 import numpy as np
 import pytest
 
@@ -43,7 +40,7 @@ def _cfg(rule, order):
 def oracle_bits():
     """Every oracle run of this module, started in spawned workers before the
     module's first GPU call: (case, weights) -> result."""
-    pool = ProcessPoolExecutor(max_workers=4, mp_context=mp.get_context("spawn"))
+    pool = oracle_jobs.OraclePool(4)
     futs = {}
     for fmt, _, rule, n, order in CASES:
         toks = S.token_stream(SEED, 0, n, S.FULL.vocab)
@@ -52,7 +49,7 @@ def oracle_bits():
             if key not in futs:
                 futs[key] = pool.submit(oracle_jobs.compress_recorded, S.FULL, SEED, wf, toks, (), _cfg(rule, order))
     yield futs
-    pool.shutdown(wait=True, cancel_futures=True)
+    pool.close()
 
 
 def gpu_bits(blob, n_streams):

@@ -20,9 +20,6 @@ token 2,048 and again at token 2,560 (Sec. 3.9).
   tokens, and a lossless decode.
 """
 import math
-import multiprocessing as mp
-from concurrent.futures import ProcessPoolExecutor
-
 import numpy as np
 import pytest
 import torch
@@ -48,11 +45,11 @@ def oracle_runs():
     """The two oracle runs, started in spawned workers before the first GPU
     call of this module and collected when a test needs them."""
     toks = S.token_stream(SEED, 0, N_TOK, S.FULL.vocab)
-    pool = ProcessPoolExecutor(max_workers=2, mp_context=mp.get_context("spawn"))
+    pool = oracle_jobs.OraclePool(2)
     fut_full = pool.submit(oracle_jobs.compress_recorded, S.FULL, SEED, "bf16", toks, PROBES)
     fut_z32 = pool.submit(oracle_jobs.logits_recorded, S.FULL, SEED, "fp32", toks, PROBES)
     yield toks, fut_full, fut_z32
-    pool.shutdown(wait=True, cancel_futures=True)
+    pool.close()
 
 
 def _ctx(nc, prefill_rows):

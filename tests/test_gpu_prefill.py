@@ -95,16 +95,19 @@ def test_prefill_container_decodes_per_position(nc):
         assert np.array_equal(a, b)
 
 
-@pytest.mark.parametrize("split", ["0", "1", "2", "4", "8"])
-def test_prefill_attention_split(nc, monkeypatch, split):
-    """Windows up to 2,048 positions (8 chunks) with a slide: the prefill's
-    attention gives the decode intervals exactly, both the row-tile kernel
-    (32 positions per cluster of 8 CTAs, split "0") and the decode kernel
-    over 8 rows with 1, 2, 4 or 8 CTAs per row group."""
+@pytest.mark.parametrize("fmt,path,split", [("bf16", "gemv", "0"), ("bf16", "tc", "0"), ("fp32", "gemv", "0"),
+                                            ("fp32", "gemv", "1"), ("fp32", "gemv", "2"), ("fp32", "gemv", "4"),
+                                            ("fp32", "gemv", "8")])
+def test_prefill_attention_split(nc, monkeypatch, fmt, path, split):
+    """Windows up to 2,048 positions (8 chunks of 256) with a slide: the
+    prefill's attention gives the decode intervals exactly.  BF16 cache: the
+    tensor-core attention (rows of 512-position prefill chunks in tiles of
+    42 rows).  FP32 cache: the CUDA-core row kernel with 1, 2, 4 or 8 CTAs
+    per row group ("0": picked from the rows)."""
     shape, seed = dataclasses.replace(S.SMALL, ctx_len=2048, slide=512), 8
     w = S.flat_weights(shape, seed)
     toks = [S.token_stream(seed, j, n, shape.vocab) for j, n in enumerate([2300, 700])]
-    ref = intervals(nc, shape, w, "bf16", "gemv", toks, 0, 2)
+    ref = intervals(nc, shape, w, fmt, path, toks, 0, 2)
     monkeypatch.setenv("NC24_ATTN_CLUSTER", split)
-    got = intervals(nc, shape, w, "bf16", "gemv", toks, 1024, 2)
+    got = intervals(nc, shape, w, fmt, path, toks, 1024, 2)
     assert np.array_equal(got, ref)
