@@ -49,7 +49,6 @@ struct TcMat {
   CUtensorMap b;                     // operand of a decode step (max_streams rows)
   CUtensorMap bp;                    // operand of a prefill forward (prefill_rows rows)
   int M = 0, K = 0, bn = 0, bnp = 0;
-  int ks = 1;                        // split-K (fixed per matrix)
   const float* scale = nullptr;
 };
 
@@ -346,22 +345,19 @@ static int tc_setup(nc_ctx* ctx) {
     if (dalloc(ctx, &ctx->opnd2, (size_t)R * D.F * 2)) return fail(ctx, NC_ENOMEM, "tensor-core operand allocation");
     NC_TRY(cudaMemset(ctx->opnd2, 0, (size_t)R * D.F * 2));
   }
-  auto add = [&](const Mat& m, bool head) {
+  auto add = [&](const Mat& m) {
     TcMat t;
     t.M = m.rows;
     t.K = m.cols;
     t.scale = m.scale;
-    // the LM head has tiles enough without a K split
-    t.ks = head ? 1 : tc_ksplit(m.cols, kb);
     if (!tc_encode_tmap(&t.a, m.w, esz, m.cols, m.rows, 128)) return false;
     ctx->tc.push_back(t);
     return true;
   };
   for (const LayerW& L : ctx->layers)
-    if (!add(L.qkv, false) || !add(L.o, false) || !add(L.gu, false) || !add(L.down, false))
-      return fail(ctx, NC_ECUDA, "tensor map encoding failed");
+    if (!add(L.qkv) || !add(L.o) || !add(L.gu) || !add(L.down)) return fail(ctx, NC_ECUDA, "tensor map encoding failed");
   Mat head{ctx->embed, ctx->embed_scale, D.V, D.d};
-  if (!add(head, true)) return fail(ctx, NC_ECUDA, "tensor map encoding failed");
+  if (!add(head)) return fail(ctx, NC_ECUDA, "tensor map encoding failed");
   // autotune bn per distinct shape (layer 0's matrices and the LM head), for
   // a decode step (B rows) and for a prefill forward (P rows)
   float* scratch = nullptr;
@@ -390,7 +386,6 @@ static int tc_setup(nc_ctx* ctx) {
         TcGemm g{};
         g.tmap_a = &tt.a;
         g.tmap_b = &tt.b;
-        g.ks = t.ks;
         g.M = t.M;
         g.K = t.K;
         g.Bmax = rows;
@@ -862,12 +857,12 @@ static cudaError_t launch_model_tc(nc_ctx* ctx, const Batch& b, StepMarks& m) {
   const Dims& D = ctx->D;
   cudaStream_t s = ctx->stream;
   const int kb = ctx->fmt == NC_BF16;
+  int layer = 0;
   auto gemm = [&](const TcMat& t, int epi, float* y, float* h, void* h16 = nullptr) {
     const bool pf = b.pos != nullptr;               // prefill forward: P-row operand map
     TcGemm g{};
     g.tmap_a = &t.a;
     g.tmap_b = pf ? &t.bp : &t.b;
-    g.ks = t.ks;
     g.M = t.M;
     g.K = t.K;
     g.Bmax = b.Bmax;
@@ -883,6 +878,12 @@ static cudaError_t launch_model_tc(nc_ctx* ctx, const Batch& b, StepMarks& m) {
     g.st = b.st;
     g.slots = b.slots;
     g.status = ctx->d_status;
+    g.pos = b.pos;
+    g.rope_tab = D.rope_tab;
+    g.L = D.L;
+    g.hq = D.hq;
+    g.hkv = D.hkv;
+    g.layer = layer;
     return launch_gemm_tc(g, epi, s, D.pdl);
   };
   cudaError_t e = launch_embed(D, b, ctx->embed, ctx->embed_scale, ctx->fmt, ctx->x, s);
@@ -890,9 +891,10 @@ static cudaError_t launch_model_tc(nc_ctx* ctx, const Batch& b, StepMarks& m) {
   for (int l = 0; l < D.n_layers && e == cudaSuccess; ++l) {
     const LayerW& L = ctx->layers[l];
     const TcMat* T = &ctx->tc[4 * l];
+    layer = l;
     e = launch_act_rmsnorm(D, b, ctx->x, L.g_attn, D.d, kb, ctx->opnd, ctx->opnd_scale, s);
-    if (e == cudaSuccess) e = gemm(T[0], EPI_STORE, ctx->qkv, nullptr);
-    if (e == cudaSuccess && b.pos) e = launch_kv_append(D, b, l, ctx->qkv, s);
+    // a prefill's QKV epilogue also appends every row's k and v to the ring
+    if (e == cudaSuccess) e = gemm(T[0], b.pos ? EPI_QKV : EPI_STORE, ctx->qkv, nullptr);
     if (e == cudaSuccess) e = m.mark(s, TK_QKV);
     if (e == cudaSuccess) e = launch_attn(D, b, l, ctx->qkv, ctx->attn_out, s, kb ? ctx->opnd : nullptr);
     if (e == cudaSuccess) e = m.mark(s, TK_ATTN);
@@ -1879,7 +1881,6 @@ extern "C" int nc_gemm_tc(const void* W, const void* X, const float* w_scale, co
   TcGemm g{};
   g.tmap_a = &t.a;
   g.tmap_b = &t.b;
-  g.ks = tc_ksplit(K, !fp8);
   g.M = M;
   g.K = K;
   g.Bmax = N;

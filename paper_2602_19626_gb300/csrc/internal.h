@@ -129,6 +129,31 @@ struct Batch {
   const int32_t* z_idx;
 };
 
+// (cos, sin) of position a for rotation pair dd from the RoPE table: the
+// product of the three table rotations (a split into 8-bit digits), with
+// explicit roundings (no multiply-add contraction), so every kernel that
+// rotates a position gets the same bits.
+__device__ __forceinline__ float2 rope_cs_tab(const float2* tab, int a, int dd) {
+  const float2 t1 = tab[(0 * 256 + (a & 255)) * 32 + dd];
+  const float2 t2 = tab[(1 * 256 + ((a >> 8) & 255)) * 32 + dd];
+  const float2 t3 = tab[(2 * 256 + ((a >> 16) & 255)) * 32 + dd];
+  const float c12 = __fsub_rn(__fmul_rn(t1.x, t2.x), __fmul_rn(t1.y, t2.y));
+  const float s12 = __fadd_rn(__fmul_rn(t1.x, t2.y), __fmul_rn(t1.y, t2.x));
+  return make_float2(__fsub_rn(__fmul_rn(c12, t3.x), __fmul_rn(s12, t3.y)),
+                     __fadd_rn(__fmul_rn(c12, t3.y), __fmul_rn(s12, t3.x)));
+}
+// The rotated pair (x1, x2) -> (x1 c - x2 s, x2 c + x1 s).
+__device__ __forceinline__ float2 rope_rotate(float x1, float x2, float2 cs) {
+  return make_float2(__fsub_rn(__fmul_rn(x1, cs.x), __fmul_rn(x2, cs.y)),
+                     __fadd_rn(__fmul_rn(x2, cs.x), __fmul_rn(x1, cs.y)));
+}
+// Element offset of plane `which` (K of KV head g: g; V of head g: hkv + g) of
+// `layer` in a stream's KV ring [layers][2][hkv][L][64].
+__device__ __forceinline__ size_t kv_plane_off(int L, int hkv, int layer, int which) {
+  const size_t plane = (size_t)L * kHeadDim;
+  return (size_t)layer * 2 * hkv * plane + (size_t)which * plane;
+}
+
 // Programmatic dependent launch: a kernel launched with the PDL attribute may
 // start while its predecessor still runs.  Each step kernel loads only data
 // no in-flight kernel writes (weights, KV entries of earlier tokens, state of
@@ -177,7 +202,7 @@ inline cudaError_t launch_kernel_cluster(void (*kern)(KArgs...), dim3 grid, dim3
 
 // ------------------------------------------------------------------ kernels
 enum Prologue { PRO_RMSNORM = 0, PRO_PLAIN = 2 };
-enum Epilogue { EPI_STORE = 0, EPI_RESID = 1, EPI_SWIGLU = 2, EPI_LOGITS = 3 };
+enum Epilogue { EPI_STORE = 0, EPI_RESID = 1, EPI_SWIGLU = 2, EPI_LOGITS = 3, EPI_QKV = 4 };
 
 struct GemvIO {
   const float* x;           // PRO_RMSNORM / PRO_PLAIN input [Bmax][cols]
@@ -262,7 +287,6 @@ struct TcGemm {
   const void* tmap_a;       // host copy of the weights' CUtensorMap (box 128 rows)
   const void* tmap_b;       // host copy of the operand's CUtensorMap (box bn rows)
   int M, K, Bmax, bn, kind_bf16;
-  int ks;                   // split-K CTAs per output tile (1, 2, 4): a property of the weight matrix
   const int32_t* nB;
   const float* w_scale;     // FP8: [M]
   const float* x_scale;     // FP8: [Bmax]
@@ -273,12 +297,14 @@ struct TcGemm {
   float* zrows;             // EPI_LOGITS: [Bmax][M] when set
   const int32_t* slots;
   int32_t* status;          // error word (ST_TIMEOUT)
+  // EPI_QKV (the QKV projection of a prefill forward): besides EPI_STORE,
+  // row n's k rotated at position pos[n] and its v, rounded to BF16, into the
+  // KV ring of `layer` of stream slots[n] (rows with pos[n] < 0 skipped)
+  const int32_t* pos;
+  const float2* rope_tab;
+  int L, hq, hkv, layer;
 };
 bool tc_encode_tmap(void* tmap, const void* base, int elem_bytes, int64_t inner, int64_t outer, int box_outer);
-// Split-K of a projection's GEMM from its inner dimension K (1, 2 or 4 CTAs
-// per output tile): fixed per weight matrix, so every batch size, the
-// decode step and the prefill forward add the same partials in the same order.
-int tc_ksplit(int K, int kind_bf16);
 cudaError_t launch_gemm_tc(const TcGemm& g, int epi, cudaStream_t s, bool pdl);
 // One bounded mbarrier wait on a barrier nothing arrives on (at most `polls`
 // polls), recording ST_TIMEOUT in *status when it gives up.

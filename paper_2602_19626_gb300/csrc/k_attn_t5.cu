@@ -10,31 +10,34 @@
 // among the rows of a prefill gives the same bits.
 //
 // The window [start, a] of a row is cut into chunks of 256 positions (chunk
-// c = [start + 256 c, ...)), a chunk into two blocks of 128.  Cluster rank c
+// c = [start + 256 c, ...)), a chunk into four blocks of 64.  Cluster rank c
 // of the tile's S CTAs owns chunk c:
 //   - the 256 K and V rows of the chunk go to shared memory in the 128-byte
 //     swizzle layout (16-byte asynchronous copies; positions past the tile's
 //     last row are zero), the pairs' rotated 1/8-scaled queries, rounded to
 //     BF16, beside them;
-//   - per block b, one thread issues S_b = Q K_b^T (M 128, N 128, four K
+//   - one thread issues S_b = Q K_b^T for every block b (M 128, N 64, four K
 //     steps of 16 head dims) into tensor memory;
 //   - the pair's thread reads its scores back (one TMEM lane per pair),
 //     masks positions above its row's, and takes the block maximum m_b,
 //     e = 2^(s log2 e - m_b log2 e) (PTX ex2.approx), their sum l_b in FP32
 //     (eight interleaved partial sums, then a fixed tree) and P_b = BF16(e)
-//     into shared memory;
-//   - O_b = P_b V_b (M 128, N 64, eight K steps of 16 positions, V read
-//     MN-major straight from the tile) goes to tensor memory;
+//     into shared memory (two alternating buffers in the K tile's place, which
+//     the score products no longer read);
+//   - O_b = P_b V_b (M 128, N 64, four K steps of 16 positions, V read
+//     MN-major straight from the tile) goes to the columns S_b held;
 //   - the chunk's (M_c, l_c, O_c) = (max m_b, sum l_b f_b, sum O_b f_b),
 //     f_b = exp(m_b - M_c), blocks in order, a block past the row absent;
-//   - each rank receives every chunk's (M_c, l_c) and its 64 / S dims of O_c
-//     in its shared memory (remote stores), and after one cluster barrier
-//     merges the chunks in order: O = sum O_c f_c / sum l_c f_c with
+//   - after a cluster barrier (every rank done with its query and key tiles)
+//     each rank receives, in that memory, every chunk's (M_c, l_c) and its
+//     64 / S dims of O_c (remote stores), and after a second barrier merges
+//     the chunks in order: O = sum O_c f_c / sum l_c f_c with
 //     f_c = exp(M_c - max M_c).
 // The arithmetic of a row is fixed by its window alone.  In a decode step the
 // rank of the chunk holding the fed position a rotates the new k at a, rounds
 // k and v to BF16, appends them to the ring and to its tile; a prefill's rows
 // were appended by k_kv_append (the same rotation code) before this kernel.
+// About 92 KB of shared memory and 256 TMEM columns: two CTAs per SM.
 //
 // Every wait on an mbarrier is bounded; a wait that gives up raises
 // ST_TIMEOUT in the stream's status word, skips the remaining products and,
@@ -58,28 +61,34 @@ using namespace tc5;
 constexpr int kT5Threads = 128;              // 4 warps; warp w reads TMEM lanes 32 w .. 32 w + 31
 constexpr int kT5Pairs = 128;                // MMA M: (row, head) pairs per tile
 constexpr int kT5Chunk = 256;                // positions per chunk (one CTA)
-constexpr int kT5Block = 128;                // positions per block (N of the scores)
+constexpr int kT5Block = 64;                 // positions per block (N of the scores, K of P V)
+constexpr int kT5Blocks = kT5Chunk / kT5Block;
 constexpr int kT5MaxRanks = 8;               // chunks of a window of at most 2,048 positions
 constexpr int kRowB = 128;                   // bytes of one swizzled row: 64 BF16
-constexpr int kT5Cols = 512;                 // TMEM columns: S_0, S_1 (128 each), O_0, O_1 (64 each)
-constexpr uint32_t kColS0 = 0, kColS1 = 128, kColO0 = 256, kColO1 = 320;
+constexpr uint32_t kT5Cols = 256;            // TMEM columns: S_b, then O_b, at 64 b
 
-// Shared memory, byte offsets from a 1024-byte aligned base.
+// Shared memory, byte offsets from a 1024-byte aligned base; `cs` holds the
+// (cos, sin) of the tile rows' positions, RT rows of 32 pairs.
 struct T5Layout {
-  static constexpr int q = 0;                                      // [128 pairs][128 B]
-  static constexpr int k = q + kT5Pairs * kRowB;                   // [256 positions][128 B]
-  static constexpr int v = k + kT5Chunk * kRowB;                   // [256 positions][128 B]
-  static constexpr int p0 = v + kT5Chunk * kRowB;                  // [2 atoms][128 pairs][128 B]
-  static constexpr int p1 = p0 + 2 * kT5Pairs * kRowB;
-  static constexpr int rm = p1 + 2 * kT5Pairs * kRowB;             // [8 chunks][128 pairs] chunk maxima
-  static constexpr int rl = rm + kT5MaxRanks * kT5Pairs * 4;       // [8][128] chunk sums
-  static constexpr int racc = rl + kT5MaxRanks * kT5Pairs * 4;     // [S chunks][128 pairs][64 / S] dims
-  static constexpr int bars = racc + kT5Pairs * kHeadDim * 4;      // 6 mbarriers
-  static constexpr int slot = bars + 64;                           // TMEM address, fail flag
-  static constexpr int arow = slot + 16;                           // [128] row positions
-  static constexpr int total = arow + kT5Pairs * 4;
+  int q, k, v, cs, bars, slot, arow, total;
+  // the inbox, after the first cluster barrier, in the query and key tiles
+  int rm, rl, racc;
+  __host__ __device__ explicit T5Layout(int rt) {
+    q = 0;                                   // [128 pairs][128 B]
+    k = q + kT5Pairs * kRowB;                // [256 positions][128 B]; later P_0, P_1 (16 KB each)
+    v = k + kT5Chunk * kRowB;                // [256 positions][128 B]
+    cs = v + kT5Chunk * kRowB;               // [rt][32] float2
+    bars = cs + rt * 32 * 8;                 // 6 mbarriers
+    slot = bars + 64;                        // TMEM address
+    arow = slot + 16;                        // [128] row positions
+    total = arow + kT5Pairs * 4;
+    rm = 0;                                  // [8 chunks][128 pairs] chunk maxima
+    rl = rm + kT5MaxRanks * kT5Pairs * 4;    // [8][128] chunk sums
+    racc = rl + kT5MaxRanks * kT5Pairs * 4;  // [S chunks][128 pairs][64 / S] dims
+  }
 };
-constexpr size_t kT5Smem = T5Layout::total + 1024;                 // + alignment slack
+static_assert(2 * kT5MaxRanks * kT5Pairs * 4 + kT5Pairs * kHeadDim * 4 <= (kT5Pairs + kT5Chunk) * kRowB,
+              "the inbox fits the query and key tiles");
 
 constexpr float kLog2e = 1.4426950408889634f;
 
@@ -116,9 +125,9 @@ __device__ void load_kv_tile(const Dims& D, const StreamDev& st, int layer, int 
   for (int e = tid; e < kT5Chunk * 8; e += kT5Threads) {
     const int row = e >> 3, seg = e & 7;
     const int p = c_lo + row;
+    if (p == own) continue;                        // written by the caller
     uint8_t* dk = kt + swz(row, seg);
     uint8_t* dv = vt + swz(row, seg);
-    if (p == own) continue;                        // written by the caller
     if (p <= last) {
       const size_t ri = (size_t)(p & (D.L - 1)) * kHeadDim + seg * 8;
       cp_async16(dk, kp + ri);
@@ -138,44 +147,48 @@ __device__ __forceinline__ void store_out(const AttnIO& io, size_t i, float v) {
     io.attn_out[i] = v;
 }
 
-// Softmax of one block for this thread's pair: the block maximum m over the
-// first `nvalid` columns of the scores at TMEM column `col`, the numerators
-// e = 2^(s log2 e - m log2 e) rounded to BF16 into the pair's row of the P
-// tile, and their FP32 sum.  nvalid = 0 writes a zero row (an absent block).
+// Softmax of one 64-position block for this thread's pair: the block
+// maximum m over the first `nvalid` columns of the scores at TMEM column
+// `col`, the numerators e = 2^(s log2 e - m log2 e) rounded to BF16 into the
+// pair's row of the P tile, and their FP32 sum.  nvalid = 0 writes a zero row
+// (an absent block).
 __device__ __forceinline__ void block_softmax(uint32_t tmem_lane, uint32_t col, int nvalid, uint8_t* ptile, int pair,
                                               float& m_out, float& l_out) {
-  uint32_t r[32];
+  uint32_t r[2][32];
+  tmem_ld32_nowait(tmem_lane + col, r[0]);
+  tmem_ld32_nowait(tmem_lane + col + 32, r[1]);
+  tmem_wait_ld();
+  float s[kT5Block];
+#pragma unroll
+  for (int i = 0; i < kT5Block; ++i) s[i] = __uint_as_float(r[i >> 5][i & 31]);
   float m = -INFINITY;
+  if (nvalid == kT5Block) {
 #pragma unroll
-  for (int q = 0; q < kT5Block / 32; ++q) {
-    tmem_ld32_nowait(tmem_lane + col + 32 * q, r);
-    tmem_wait_ld();
+    for (int i = 0; i < kT5Block; ++i) m = fmaxf(m, s[i]);
+  } else {
 #pragma unroll
-    for (int i = 0; i < 32; ++i)
-      if (32 * q + i < nvalid) m = fmaxf(m, __uint_as_float(r[i]));
+    for (int i = 0; i < kT5Block; ++i)
+      if (i < nvalid) m = fmaxf(m, s[i]);
   }
   float acc[8];
 #pragma unroll
   for (int i = 0; i < 8; ++i) acc[i] = 0.f;
   const float mb = nvalid > 0 ? -__fmul_rn(m, kLog2e) : 0.f;
+  float e[kT5Block];
+  if (nvalid == kT5Block) {
 #pragma unroll
-  for (int q = 0; q < kT5Block / 32; ++q) {
-    tmem_ld32_nowait(tmem_lane + col + 32 * q, r);
-    tmem_wait_ld();
-    float e[32];
+    for (int i = 0; i < kT5Block; ++i) e[i] = ex2_approx(__fmaf_rn(s[i], kLog2e, mb));
+  } else {
 #pragma unroll
-    for (int i = 0; i < 32; ++i) {
-      e[i] = 32 * q + i < nvalid ? ex2_approx(__fmaf_rn(__uint_as_float(r[i]), kLog2e, mb)) : 0.f;
-      acc[i & 7] = __fadd_rn(acc[i & 7], e[i]);
-    }
-    // positions 32 q .. 32 q + 31: K-atom q / 2, 16-byte segments 4 (q % 2) .. + 3
-    uint8_t* atom = ptile + (q >> 1) * (kT5Pairs * kRowB);
+    for (int i = 0; i < kT5Block; ++i) e[i] = i < nvalid ? ex2_approx(__fmaf_rn(s[i], kLog2e, mb)) : 0.f;
+  }
 #pragma unroll
-    for (int s4 = 0; s4 < 4; ++s4) {
-      const uint4 u = make_uint4(pack_bf16(e[8 * s4], e[8 * s4 + 1]), pack_bf16(e[8 * s4 + 2], e[8 * s4 + 3]),
-                                 pack_bf16(e[8 * s4 + 4], e[8 * s4 + 5]), pack_bf16(e[8 * s4 + 6], e[8 * s4 + 7]));
-      *reinterpret_cast<uint4*>(atom + swz(pair, 4 * (q & 1) + s4)) = u;
-    }
+  for (int i = 0; i < kT5Block; ++i) acc[i & 7] = __fadd_rn(acc[i & 7], e[i]);
+#pragma unroll
+  for (int sg = 0; sg < 8; ++sg) {
+    const uint4 u = make_uint4(pack_bf16(e[8 * sg], e[8 * sg + 1]), pack_bf16(e[8 * sg + 2], e[8 * sg + 3]),
+                               pack_bf16(e[8 * sg + 4], e[8 * sg + 5]), pack_bf16(e[8 * sg + 6], e[8 * sg + 7]));
+    *reinterpret_cast<uint4*>(ptile + swz(pair, sg)) = u;
   }
   m_out = m;
   l_out = __fadd_rn(__fadd_rn(__fadd_rn(acc[0], acc[1]), __fadd_rn(acc[2], acc[3])),
@@ -183,28 +196,29 @@ __device__ __forceinline__ void block_softmax(uint32_t tmem_lane, uint32_t col, 
 }
 
 template <int S>
-__global__ void __launch_bounds__(kT5Threads, 1) k_attn_t5(Dims D, Batch b, int layer, int tps, AttnIO io) {
+__global__ void __launch_bounds__(kT5Threads, 2) k_attn_t5(Dims D, Batch b, int layer, int tps, AttnIO io) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
-  uint8_t* qt = sm + T5Layout::q;
-  uint8_t* kt = sm + T5Layout::k;
-  uint8_t* vt = sm + T5Layout::v;
-  uint8_t* pt[2] = {sm + T5Layout::p0, sm + T5Layout::p1};
-  float* rm = reinterpret_cast<float*>(sm + T5Layout::rm);
-  float* rl = reinterpret_cast<float*>(sm + T5Layout::rl);
-  float* racc = reinterpret_cast<float*>(sm + T5Layout::racc);
-  uint64_t* bar_s = reinterpret_cast<uint64_t*>(sm + T5Layout::bars);   // [2] scores of block b
-  uint64_t* bar_o = bar_s + 2;                                           // [2] P V of block b
-  uint64_t* bar_done = bar_s + 4;                                        // every product issued
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sm + T5Layout::slot);
-  int* a_row = reinterpret_cast<int*>(sm + T5Layout::arow);
+  const int grp = D.hq / D.hkv;
+  const int RT = kT5Pairs / grp;                   // rows per tile
+  const T5Layout Ly(RT);
+  uint8_t* qt = sm + Ly.q;
+  uint8_t* kt = sm + Ly.k;
+  uint8_t* vt = sm + Ly.v;
+  float2* cs = reinterpret_cast<float2*>(sm + Ly.cs);
+  float* rm = reinterpret_cast<float*>(sm + Ly.rm);
+  float* rl = reinterpret_cast<float*>(sm + Ly.rl);
+  float* racc = reinterpret_cast<float*>(sm + Ly.racc);
+  uint64_t* bar_s = reinterpret_cast<uint64_t*>(sm + Ly.bars);    // every score product
+  uint64_t* bar_o = bar_s + 1;                                     // [4] P V of block b
+  uint64_t* bar_done = bar_s + 5;                                  // every product issued
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sm + Ly.slot);
+  int* a_row = reinterpret_cast<int*>(sm + Ly.arow);
   constexpr int kd = kHeadDim / S;                 // output dims merged by one rank
 
   const int rank = S > 1 ? (int)cg::this_cluster().block_rank() : 0;
   const int g = blockIdx.y;
   const int tid = threadIdx.x, warp = tid >> 5;
-  const int grp = D.hq / D.hkv;
-  const int RT = kT5Pairs / grp;                   // rows per tile
   const bool prefill = b.pos != nullptr;
   int row0, nr;
   if (prefill) {
@@ -227,15 +241,15 @@ __global__ void __launch_bounds__(kT5Threads, 1) k_attn_t5(Dims D, Batch b, int 
   const int nch = a_max < 0 ? 0 : (a_max - start) / kT5Chunk + 1;
   const bool has_chunk = rank < nch;
   const int c_lo = start + rank * kT5Chunk;
-  const bool two_blocks = has_chunk && c_lo + kT5Block <= a_max;
+  const int nblk = has_chunk ? min(kT5Blocks, (a_max - c_lo) / kT5Block + 1) : 0;
   const int npairs = nr * grp;
   // this thread's pair and its row's position (-1: padding or past the stream's end)
   const int my_r = tid / grp, my_h = tid % grp;
   const int my_a = tid < npairs ? a_row[my_r] : -1;
+  const bool mine = 32 * warp < npairs;            // warp-uniform: the warp holds real pairs
 
   if (tid == 0) {
-    for (int i = 0; i < 5; ++i) mbar_init(bar_s + i, 1);
-    *reinterpret_cast<volatile uint32_t*>(tmem_slot + 1) = 0;
+    for (int i = 0; i < 6; ++i) mbar_init(bar_s + i, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (has_chunk && warp == 0) tmem_alloc(tmem_slot, kT5Cols);
@@ -246,7 +260,6 @@ __global__ void __launch_bounds__(kT5Threads, 1) k_attn_t5(Dims D, Batch b, int 
   pdl_wait();
   pdl_trigger();
   if (has_chunk && prefill) load_kv_tile(D, st, layer, g, c_lo, a_max, -1, kt, vt, tid);
-  if (S > 1) asm volatile("barrier.cluster.arrive.relaxed.aligned;" ::: "memory");
 
   bool ok = true;
   float Mc = -INFINITY, Lc = 0.f;
@@ -254,27 +267,29 @@ __global__ void __launch_bounds__(kT5Threads, 1) k_attn_t5(Dims D, Batch b, int 
 #pragma unroll
   for (int d = 0; d < kHeadDim; ++d) oc[d] = 0.f;
   if (has_chunk) {
-    const float* qkv_rows = io.qkv;
+    // (cos, sin) of every tile row's position
+    for (int e = tid; e < nr * (kHeadDim / 2); e += kT5Threads) {
+      const int r = e / (kHeadDim / 2), dd = e % (kHeadDim / 2);
+      if (a_row[r] >= 0) cs[e] = rope_cs(D, a_row[r], dd);
+    }
     // decode: the fed token's k (rotated at a) and v, rounded to BF16, into
     // the ring and into this tile (the rank whose chunk holds a)
     if (!prefill && rank == nch - 1 && tid < kHeadDim) {
-      const float* row = qkv_rows + (size_t)row0 * D.qkv_rows;
+      const float* row = io.qkv + (size_t)row0 * D.qkv_rows;
       const int a = a_max, R = a - c_lo;
-      if (tid < kHeadDim / 2) {
+      const size_t ri = (size_t)(a & (D.L - 1)) * kHeadDim;
+      if (tid < kHeadDim / 2) {                    // dims tid and tid + 32 of k
         const float* src = row + D.hq * kHeadDim + g * kHeadDim;
         const float2 rr = rope_rotate(__ldcg(src + tid), __ldcg(src + tid + kHeadDim / 2), rope_cs(D, a, tid));
-        // this thread writes dims tid and tid + 32 of k
-        const size_t ri = (size_t)(a & (D.L - 1)) * kHeadDim;
         __nv_bfloat16* kv = static_cast<__nv_bfloat16*>(st.kv) + attn_plane_off(D, layer, g) + ri;
         const __nv_bfloat16 k0 = __float2bfloat16_rn(rr.x), k1 = __float2bfloat16_rn(rr.y);
         kv[tid] = k0;
         kv[tid + kHeadDim / 2] = k1;
         *reinterpret_cast<__nv_bfloat16*>(kt + swz(R, tid >> 3) + (tid & 7) * 2) = k0;
         *reinterpret_cast<__nv_bfloat16*>(kt + swz(R, (tid + 32) >> 3) + (tid & 7) * 2) = k1;
-      } else {
-        const int d0 = 2 * (tid - kHeadDim / 2);   // dims d0, d0 + 1 of v
+      } else {                                     // dims d0, d0 + 1 of v
+        const int d0 = 2 * (tid - kHeadDim / 2);
         const float* src = row + (D.hq + D.hkv) * kHeadDim + g * kHeadDim;
-        const size_t ri = (size_t)(a & (D.L - 1)) * kHeadDim;
         __nv_bfloat16* kv = static_cast<__nv_bfloat16*>(st.kv) + attn_plane_off(D, layer, D.hkv + g) + ri;
         const __nv_bfloat16 v0 = __float2bfloat16_rn(__ldcg(src + d0)), v1 = __float2bfloat16_rn(__ldcg(src + d0 + 1));
         kv[d0] = v0;
@@ -283,17 +298,29 @@ __global__ void __launch_bounds__(kT5Threads, 1) k_attn_t5(Dims D, Batch b, int 
         *reinterpret_cast<__nv_bfloat16*>(vt + swz(R, (d0 + 1) >> 3) + ((d0 + 1) & 7) * 2) = v1;
       }
     }
+    __syncthreads();                               // the rotation table is complete
     // the pairs' rotated, 1/8-scaled queries in BF16 (padding rows zero)
-    if (32 * warp < npairs) {
+    if (mine) {
       uint32_t w[kHeadDim / 2];
 #pragma unroll
       for (int i = 0; i < kHeadDim / 2; ++i) w[i] = 0u;
       if (my_a >= 0) {
-        const float* src = qkv_rows + (size_t)(row0 + my_r) * D.qkv_rows + (g * grp + my_h) * kHeadDim;
+        const float4* src =
+            reinterpret_cast<const float4*>(io.qkv + (size_t)(row0 + my_r) * D.qkv_rows + (g * grp + my_h) * kHeadDim);
+        float x[kHeadDim];
+#pragma unroll
+        for (int i = 0; i < kHeadDim / 4; ++i) {
+          const float4 u = __ldcg(src + i);
+          x[4 * i] = u.x;
+          x[4 * i + 1] = u.y;
+          x[4 * i + 2] = u.z;
+          x[4 * i + 3] = u.w;
+        }
+        const float2* csr = cs + my_r * (kHeadDim / 2);
         float qv[kHeadDim];
 #pragma unroll
         for (int dd = 0; dd < kHeadDim / 2; ++dd) {
-          const float2 rr = rope_rotate(__ldcg(src + dd), __ldcg(src + dd + kHeadDim / 2), rope_cs(D, my_a, dd));
+          const float2 rr = rope_rotate(x[dd], x[dd + kHeadDim / 2], csr[dd]);
           qv[dd] = rr.x * 0.125f;   // the 1/sqrt(64) score scale is a power of two: exact
           qv[dd + kHeadDim / 2] = rr.y * 0.125f;
         }
@@ -313,58 +340,64 @@ __global__ void __launch_bounds__(kT5Threads, 1) k_attn_t5(Dims D, Batch b, int 
     const uint32_t tlane = tmem + ((uint32_t)(32 * warp) << 16);
     if (tid == 0) {
       const uint32_t ids = idesc(1, kT5Pairs, kT5Block);
-      for (int bb = 0; bb < (two_blocks ? 2 : 1); ++bb) {
+      for (int bb = 0; bb < nblk; ++bb) {
 #pragma unroll
         for (int k = 0; k < kHeadDim / 16; ++k)
-          mma_issue(1, tmem + (bb ? kColS1 : kColS0), sdesc_sw128(smem_u32(qt) + 32 * k),
+          mma_issue(1, tmem + kT5Block * bb, sdesc_sw128(smem_u32(qt) + 32 * k),
                     sdesc_sw128(smem_u32(kt + bb * kT5Block * kRowB) + 32 * k), ids, k ? 1u : 0u);
-        mma_commit(bar_s + bb);
       }
+      mma_commit(bar_s);
     }
     __syncwarp();
-    const bool mine = 32 * warp < npairs;          // warp-uniform: the warp holds real pairs
-    float mb[2] = {-INFINITY, -INFINITY}, lb[2] = {0.f, 0.f};
-    int nv[2] = {0, 0};
-    for (int bb = 0; bb < (two_blocks ? 2 : 1); ++bb) {
+    // every score product done: the key tile holds the P buffers from here
+    ok = __syncthreads_and(mbar_wait(bar_s, 0));
+    fence_after_sync();
+    float mb[kT5Blocks], lb[kT5Blocks];
+    int nv[kT5Blocks];
+#pragma unroll
+    for (int bb = 0; bb < kT5Blocks; ++bb) {
+      mb[bb] = -INFINITY;
+      lb[bb] = 0.f;
       const int blo = c_lo + bb * kT5Block;
-      nv[bb] = my_a < blo ? 0 : min(kT5Block, my_a - blo + 1);
-      ok = __syncthreads_and(ok && mbar_wait(bar_s + bb, 0));
-      fence_after_sync();
-      if (ok && mine) block_softmax(tlane, bb ? kColS1 : kColS0, nv[bb], pt[bb], tid, mb[bb], lb[bb]);
+      nv[bb] = bb < nblk && my_a >= blo ? min(kT5Block, my_a - blo + 1) : 0;
+    }
+    for (int bb = 0; bb < nblk; ++bb) {
+      uint8_t* pt = kt + (bb & 1) * (kT5Pairs * kRowB);
+      if (bb >= 2) ok = __syncthreads_and(ok && mbar_wait(bar_o + bb - 2, 0));   // P buffer bb & 1 free
+      if (ok && mine) block_softmax(tlane, kT5Block * bb, nv[bb], pt, tid, mb[bb], lb[bb]);
       fence_proxy_async();
       fence_before_sync();
       __syncthreads();
       fence_after_sync();
       if (tid == 0 && ok) {
+        // O_b into the columns of S_b (every thread has read S_b)
         const uint32_t ido = idesc(1, kT5Pairs, kHeadDim, 1);
 #pragma unroll
         for (int s = 0; s < kT5Block / 16; ++s)
-          mma_issue(1, tmem + (bb ? kColO1 : kColO0),
-                    sdesc_sw128(smem_u32(pt[bb]) + (s >> 2) * (kT5Pairs * kRowB) + 32 * (s & 3)),
+          mma_issue(1, tmem + kT5Block * bb, sdesc_sw128(smem_u32(pt) + 32 * s),
                     sdesc_sw128_mn(smem_u32(vt + (bb * kT5Block + 16 * s) * kRowB)), ido, s ? 1u : 0u);
         mma_commit(bar_o + bb);
       }
       __syncwarp();
     }
     // the chunk's partials: blocks in order, a block past the row absent
-    const bool p0 = nv[0] > 0, p1 = nv[1] > 0;
-    Mc = fmaxf(p0 ? mb[0] : -INFINITY, p1 ? mb[1] : -INFINITY);
-    for (int bb = 0; bb < (two_blocks ? 2 : 1); ++bb) {
+#pragma unroll
+    for (int bb = 0; bb < kT5Blocks; ++bb)
+      if (nv[bb] > 0) Mc = fmaxf(Mc, mb[bb]);
+    for (int bb = 0; bb < nblk; ++bb) {
       ok = __syncthreads_and(ok && mbar_wait(bar_o + bb, 0));
       fence_after_sync();
       if (!ok || !mine) continue;
-      const bool pres = bb ? p1 : p0;
+      const bool pres = nv[bb] > 0;
       const float f = pres ? exp_fast(__fsub_rn(mb[bb], Mc)) : 0.f;
       if (pres) Lc = __fmaf_rn(lb[bb], f, Lc);
+      uint32_t r[2][32];
+      tmem_ld32_nowait(tlane + kT5Block * bb, r[0]);
+      tmem_ld32_nowait(tlane + kT5Block * bb + 32, r[1]);
+      tmem_wait_ld();
+      if (pres) {
 #pragma unroll
-      for (int h2 = 0; h2 < 2; ++h2) {
-        uint32_t r[32];
-        tmem_ld32_nowait(tlane + (bb ? kColO1 : kColO0) + 32 * h2, r);
-        tmem_wait_ld();
-        if (pres) {
-#pragma unroll
-          for (int i = 0; i < 32; ++i) oc[32 * h2 + i] = __fmaf_rn(__uint_as_float(r[i]), f, oc[32 * h2 + i]);
-        }
+        for (int d = 0; d < kHeadDim; ++d) oc[d] = __fmaf_rn(__uint_as_float(r[d >> 5][d & 31]), f, oc[d]);
       }
     }
     // give-up path: every product issued has completed before the memory is freed
@@ -375,31 +408,31 @@ __global__ void __launch_bounds__(kT5Threads, 1) k_attn_t5(Dims D, Batch b, int 
       if (tid == 0) atomicOr(&st.status, ST_TIMEOUT);
     }
   }
-  // every CTA of the cluster has started (its shared memory may be written)
-  if (S > 1) asm volatile("barrier.cluster.wait.aligned;" ::: "memory");
-  if (has_chunk && ok) {
+  // every rank is done with its query and key tiles: the inbox takes them
+  if (S > 1)
+    cg::this_cluster().sync();
+  else
+    __syncthreads();
+  if (has_chunk && ok && mine && my_a >= c_lo) {
     // every rank receives the chunk's (M_c, l_c) and its dims of O_c
-    const bool mine = 32 * warp < npairs;
-    if (mine && my_a >= c_lo) {
 #pragma unroll
-      for (int k = 0; k < S; ++k) {
-        float* trm = rm;
-        float* trl = rl;
-        float* tra = racc;
-        if (S > 1) {
-          cg::cluster_group cl = cg::this_cluster();
-          trm = cl.map_shared_rank(rm, k);
-          trl = cl.map_shared_rank(rl, k);
-          tra = cl.map_shared_rank(racc, k);
-        }
-        trm[rank * kT5Pairs + tid] = Mc;
-        trl[rank * kT5Pairs + tid] = Lc;
-        float* dst = tra + ((size_t)rank * kT5Pairs + tid) * kd;
-#pragma unroll
-        for (int d = 0; d < kd; d += 4)
-          *reinterpret_cast<float4*>(dst + d) = make_float4(oc[k * kd + d], oc[k * kd + d + 1], oc[k * kd + d + 2],
-                                                            oc[k * kd + d + 3]);
+    for (int k = 0; k < S; ++k) {
+      float* trm = rm;
+      float* trl = rl;
+      float* tra = racc;
+      if (S > 1) {
+        cg::cluster_group cl = cg::this_cluster();
+        trm = cl.map_shared_rank(rm, k);
+        trl = cl.map_shared_rank(rl, k);
+        tra = cl.map_shared_rank(racc, k);
       }
+      trm[rank * kT5Pairs + tid] = Mc;
+      trl[rank * kT5Pairs + tid] = Lc;
+      float* dst = tra + ((size_t)rank * kT5Pairs + tid) * kd;
+#pragma unroll
+      for (int d = 0; d < kd; d += 4)
+        *reinterpret_cast<float4*>(dst + d) = make_float4(oc[k * kd + d], oc[k * kd + d + 1], oc[k * kd + d + 2],
+                                                          oc[k * kd + d + 3]);
     }
   }
   if (S > 1)
@@ -441,11 +474,14 @@ __global__ void __launch_bounds__(kT5Threads, 1) k_attn_t5(Dims D, Batch b, int 
   }
 }
 
+size_t t5_smem(int grp) { return (size_t)T5Layout(kT5Pairs / grp).total + 1024; }   // + alignment slack
+
 template <int S>
 cudaError_t launch_t5_s(const Dims& D, const Batch& b, int layer, const AttnIO& io, cudaStream_t s) {
   static bool attr = false;                        // the kernel's shared-memory limit, once per process
   if (!attr) {
-    const cudaError_t e = cudaFuncSetAttribute(k_attn_t5<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kT5Smem);
+    const cudaError_t e =
+        cudaFuncSetAttribute(k_attn_t5<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)t5_smem(1));
     if (e != cudaSuccess) return e;
     attr = true;
   }
@@ -457,7 +493,7 @@ cudaError_t launch_t5_s(const Dims& D, const Batch& b, int layer, const AttnIO& 
     tiles = (b.Bmax / b.pm) * tps;
   }
   dim3 grid(S, D.hkv, tiles);
-  return launch_kernel_cluster(k_attn_t5<S>, grid, dim3(kT5Threads), kT5Smem, s, D.pdl, S, D, b, layer, tps, io);
+  return launch_kernel_cluster(k_attn_t5<S>, grid, dim3(kT5Threads), t5_smem(grp), s, D.pdl, S, D, b, layer, tps, io);
 }
 
 }  // namespace

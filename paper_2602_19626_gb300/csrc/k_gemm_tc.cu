@@ -21,12 +21,8 @@
 #include <cuda_bf16.h>
 #include <cuda_fp8.h>
 
-#include <cooperative_groups.h>
-
 #include "internal.h"
 #include "tc5.cuh"
-
-namespace cg = cooperative_groups;
 
 namespace nc {
 
@@ -47,21 +43,10 @@ __host__ __device__ constexpr uint32_t tmem_cols() {
   return BN <= 32 ? 32 : BN <= 64 ? 64 : BN <= 128 ? 128 : 256;
 }
 
-// Split-K partials received by one rank, [KS source ranks][128 / KS rows][BN
-// columns] with rows padded by 4 floats (a warp's remote stores to 32 rows
-// then spread over the banks), in the pipeline's stage buffers once every
-// rank of the cluster is done with them.
-template <int BN>
-__host__ __device__ constexpr size_t tc_recv_bytes() {
-  return (size_t)kTileM * (BN + 4) * 4;
-}
-
-template <int BN, int STAGES, int KS>
+template <int BN, int STAGES>
 __host__ __device__ constexpr size_t tc_smem_bytes() {
   return 1024 /* alignment slack */ + (size_t)STAGES * (kTileM + BN) * kKBlockBytes + 256;
 }
-static_assert(tc_recv_bytes<256>() <= 4 * (kTileM + 256) * kKBlockBytes, "receive buffer within the stages");
-static_assert(tc_recv_bytes<128>() <= 6 * (kTileM + 128) * kKBlockBytes, "receive buffer within the stages");
 
 // One output element (row r of the weights, batch row n) through the fused
 // epilogue; y already carries the FP8 scales.
@@ -77,7 +62,7 @@ __device__ __forceinline__ void epi_store(const TcGemm& g, int r, int n, int B, 
         g.h_out[(size_t)n * (g.M / 2) + (r >> 1)] = h;
     }
   } else if (n < B && r < g.M) {
-    if (EPI == EPI_STORE) {
+    if (EPI == EPI_STORE || EPI == EPI_QKV) {
       g.y[(size_t)n * g.M + r] = y;
     } else if (EPI == EPI_RESID) {
       g.y[(size_t)n * g.M + r] = res + y;
@@ -90,13 +75,42 @@ __device__ __forceinline__ void epi_store(const TcGemm& g, int r, int n, int B, 
   }
 }
 
-// KS > 1: the CTAs of a cluster of KS split the K blocks of one output tile
-// (rank q takes blocks q nk / KS .. (q + 1) nk / KS - 1, each accumulated in
-// its tensor memory in order); rank q receives rows q 128 / KS .. of every
-// rank's partial through distributed shared memory and sums them in rank
-// order before the epilogue.  The split depends on the weight matrix only,
-// so a row's arithmetic does not depend on the batch.
-template <int BN, int STAGES, int KIND_BF16, int EPI, int KS>
+// EPI_QKV, after the group's values y (columns n0c .. n0c + 15 of weight row
+// r) were staged by every warp of this column half: the k rows append
+// rotate(k[dd], k[dd + 32]) at each row's position (the thread of dd < 32
+// writes both, its partner's value from the stage), the v rows their values,
+// all rounded to BF16 into the KV ring; the same rotation and rounding as the
+// decode step's append.
+__device__ __forceinline__ void qkv_append(const TcGemm& g, int r, const float* partner, int n0c, int B,
+                                           const float (&y)[16]) {
+  const int kbase = g.hq * kHeadDim, vbase = kbase + g.hkv * kHeadDim;
+  if (r < kbase || r >= vbase + g.hkv * kHeadDim) return;
+  const bool is_k = r < vbase;
+  const int hk = ((is_k ? r - kbase : r - vbase)) / kHeadDim, dd = (is_k ? r - kbase : r - vbase) % kHeadDim;
+  if (is_k && dd >= kHeadDim / 2) return;           // written by the thread of dd - 32
+  const size_t plane = kv_plane_off(g.L, g.hkv, g.layer, is_k ? hk : g.hkv + hk);
+#pragma unroll
+  for (int i = 0; i < 16; ++i) {
+    const int n = n0c + i;
+    if (n >= B) break;
+    const int a = g.pos[n];
+    if (a < 0) continue;
+    __nv_bfloat16* ring = static_cast<__nv_bfloat16*>(g.st[g.slots[n]].kv) + plane + (size_t)(a & (g.L - 1)) * kHeadDim;
+    if (is_k) {
+      const float2 rr = rope_rotate(y[i], partner[i], rope_cs_tab(g.rope_tab, a, dd));
+      ring[dd] = __float2bfloat16_rn(rr.x);
+      ring[dd + kHeadDim / 2] = __float2bfloat16_rn(rr.y);
+    } else {
+      ring[dd] = __float2bfloat16_rn(y[i]);
+    }
+  }
+}
+
+// The residual epilogue reads the first kPreCols columns' residuals of its
+// row into registers while the products run.
+constexpr int kPreCols = 32;
+
+template <int BN, int STAGES, int KIND_BF16, int EPI>
 __global__ void __launch_bounds__(kTcThreads, 1)
     k_gemm_tc(const __grid_constant__ CUtensorMap tA, const __grid_constant__ CUtensorMap tB, TcGemm g) {
   extern __shared__ uint8_t smem_raw[];
@@ -110,25 +124,19 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   uint32_t* fail = tmem_slot + 1;
   int32_t* n_issued = reinterpret_cast<int32_t*>(fail + 1);     // K blocks whose TMA loads were issued
   int32_t* n_consumed = n_issued + 1;                          // K blocks the MMA issuer saw land
-  float* recv = reinterpret_cast<float*>(base);                 // split-K, after the products: the stages
-  constexpr int kRecvStride = BN + 4;
-  constexpr int kRows = kTileM / KS;                           // output rows of one rank (split-K)
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int m0 = blockIdx.x * kTileM;
   const int n0 = blockIdx.y * BN;
-  const int rank = KS > 1 ? (int)blockIdx.z : 0;    // the cluster spans z
   const int kblk = KIND_BF16 ? 64 : 128;             // elements per 128-byte K block
-  const int nk_all = (g.K + kblk - 1) / kblk;        // the tail block reads zeros past K
-  const int kb0 = rank * nk_all / KS;
-  const int nk = (rank + 1) * nk_all / KS - kb0;     // this rank's K blocks
+  const int nk = (g.K + kblk - 1) / kblk;            // the tail block reads zeros past K
   constexpr uint32_t kCols = tmem_cols<BN>();
   constexpr uint32_t kStageBytes = (kTileM + BN) * kKBlockBytes;
 
   // the row count was written by the step's prepare kernel, several launches
   // back, so it may be read before the wait on the previous kernel
   const int B = *g.nB;
-  if (n0 >= B) return;                            // uniform across the CTA (and the cluster)
+  if (n0 >= B) return;                            // uniform across the CTA
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
       mbar_init(full + s, 1);
@@ -156,23 +164,22 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   if (threadIdx.x == 0) {
     for (int kb = 0; kb < nk && kb < STAGES; ++kb) {
       mbar_expect_tx(full + kb, kStageBytes);
-      tma_load_2d(sA + (size_t)kb * kTileM * kKBlockBytes, &tA, full + kb, (kb0 + kb) * kblk, m0);
+      tma_load_2d(sA + (size_t)kb * kTileM * kKBlockBytes, &tA, full + kb, kb * kblk, m0);
     }
   }
   pdl_wait();
   pdl_trigger();
-  // split-K: this thread's output elements of the epilogue (rank's rows r =
-  // tid % kRows, batch rows n = tid / kRows + (256 / kRows) i) and, for the
-  // residual epilogue, their residuals, loaded while the products run
-  constexpr int kPerT = KS > 1 ? kRows * BN / kTcThreads : 1;
-  float pres[kPerT];
-  if (KS > 1) {
-    const int r = m0 + rank * kRows + (int)threadIdx.x % kRows;
+  // the epilogue's first residuals (warp w: TMEM lanes 32 (w % 4) .., the
+  // columns of half w / 4), in flight beside the products
+  const int quarter = warp & 3, half = warp >> 2;
+  const int r_ep = m0 + quarter * 32 + lane;         // weight row = TMEM lane
+  const int c_ep = half * (BN / 2);
+  constexpr int kPre = BN / 2 < kPreCols ? BN / 2 : kPreCols;
+  float pre[kPre];
 #pragma unroll
-    for (int i = 0; i < kPerT; ++i) {
-      const int n = n0 + (int)threadIdx.x / kRows + (kTcThreads / kRows) * i;
-      pres[i] = (EPI == EPI_RESID && n < B && r < g.M) ? __ldcg(g.y + (size_t)n * g.M + r) : 0.f;
-    }
+  for (int i = 0; i < kPre; ++i) {
+    const int n = n0 + c_ep + i;
+    pre[i] = (EPI == EPI_RESID && n < B && r_ep < g.M) ? __ldcg(g.y + (size_t)n * g.M + r_ep) : 0.f;
   }
 
   if (active && threadIdx.x == 0) {
@@ -181,7 +188,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     for (; kb < nk; ++kb) {
       const int s = kb % STAGES;
       const uint32_t ph = (uint32_t)(kb / STAGES) & 1u;
-      const int kc = (kb0 + kb) * kblk;
+      const int kc = kb * kblk;
       if (kb >= STAGES) {
         if (!mbar_wait(empty + s, ph ^ 1u)) {
           atomicOr(fail, 1u);
@@ -233,53 +240,38 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     for (int kb = *n_consumed; kb < *n_issued; ++kb)
       if (!mbar_wait(full + kb % STAGES, (uint32_t)(kb / STAGES) & 1u)) break;
   }
-  if (KS > 1) {
-    // every CTA of the cluster is done with its stage buffers: partials may
-    // go there
-    cg::this_cluster().sync();
-    if (ready && *fail == 0) {
-      // warp w sends TMEM lanes 32 (w % 4) .. + 31, columns of half w / 4, to
-      // the rank owning those rows
-      const int quarter = warp & 3, half = warp >> 2;
-      const int row = quarter * 32 + lane;           // 0 .. 127
-      const int dst = row / kRows, rl = row % kRows;
-      float* tgt = cg::this_cluster().map_shared_rank(recv, dst) + ((size_t)rank * kRows + rl) * kRecvStride;
-      const uint32_t tw = tmem + ((uint32_t)(quarter * 32) << 16);
-#pragma unroll 1
-      for (int c = half * (BN / 2); c < (half + 1) * (BN / 2); c += 16) {
-        float v[16];
-        tmem_ld16(tw + (uint32_t)c, v);
-#pragma unroll
-        for (int i = 0; i < 16; i += 4)
-          *reinterpret_cast<float4*>(tgt + c + i) = make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
-      }
-    }
-    cg::this_cluster().sync();                      // every partial of this rank's rows has arrived
-    if (*fail == 0) {
-      const int rr = (int)threadIdx.x % kRows;
-      const int r = m0 + rank * kRows + rr;
-      const float ws = (!KIND_BF16 && r < g.M) ? g.w_scale[r] : 1.f;
-#pragma unroll
-      for (int i = 0; i < kPerT; ++i) {
-        const int nl = (int)threadIdx.x / kRows + (kTcThreads / kRows) * i;
-        const int n = n0 + nl;
-        float y = recv[(size_t)rr * kRecvStride + nl];
-#pragma unroll
-        for (int q = 1; q < KS; ++q) y = __fadd_rn(y, recv[((size_t)q * kRows + rr) * kRecvStride + nl]);
-        if (!KIND_BF16) y *= ws * (n < B ? __ldg(g.x_scale + n) : 0.f);
-        epi_store<EPI>(g, r, n, B, y, pres[i]);
-      }
-    }
-  } else if (ready && *fail == 0) {
+  if (ready && *fail == 0) {
     // warp w reads TMEM lanes 32 (w % 4) .. + 31 (its lane quarter) and the
     // columns of half w / 4 of the tile
-    const int quarter = warp & 3, half = warp >> 2;
-    const int r = m0 + quarter * 32 + lane;        // weight row = TMEM lane
+    const int r = r_ep;
     const uint32_t tw = tmem + ((uint32_t)(quarter * 32) << 16);
     float ws = 1.f;
     if (!KIND_BF16 && r < g.M) ws = g.w_scale[r];
+    // EPI_QKV: every warp stages its group's values ([column half][group
+    // parity][128 rows][16]) in the stage buffers, free after the products
+    float* stage = reinterpret_cast<float*>(base);
+    auto qkv_group = [&](int c, int gi, const float (&y)[16]) {
+      float* mine = stage + ((half * 2 + (gi & 1)) * kTileM + quarter * 32 + lane) * 16;
+#pragma unroll
+      for (int i = 0; i < 16; i += 4) *reinterpret_cast<float4*>(mine + i) = make_float4(y[i], y[i + 1], y[i + 2], y[i + 3]);
+      __syncthreads();
+      qkv_append(g, r, mine + 32 * 16, n0 + c, B, y);
+    };
+    // the columns whose residuals are already in registers
+#pragma unroll
+    for (int c0 = 0; c0 < kPre; c0 += 16) {
+      float v[16];
+      tmem_ld16(tw + (uint32_t)(c_ep + c0), v);
+#pragma unroll
+      for (int i = 0; i < 16; ++i) {
+        const int n = n0 + c_ep + c0 + i;
+        if (!KIND_BF16) v[i] *= ws * (n < B ? __ldg(g.x_scale + n) : 0.f);
+        epi_store<EPI>(g, r, n, B, v[i], pre[c0 + i]);
+      }
+      if (EPI == EPI_QKV) qkv_group(c_ep + c0, c0 / 16, v);
+    }
 #pragma unroll 1
-    for (int c = half * (BN / 2); c < (half + 1) * (BN / 2); c += 16) {
+    for (int c = c_ep + kPre; c < c_ep + BN / 2; c += 16) {
       float v[16];
       tmem_ld16(tw + (uint32_t)c, v);
       // loads of this 16-column group first (row scales, residuals), so
@@ -294,10 +286,10 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 #pragma unroll
       for (int i = 0; i < 16; ++i) {
         const int n = n0 + c + i;
-        float y = v[i];
-        if (!KIND_BF16) y *= ws * xs[i];
-        epi_store<EPI>(g, r, n, B, y, res[i]);
+        if (!KIND_BF16) v[i] *= ws * xs[i];
+        epi_store<EPI>(g, r, n, B, v[i], res[i]);
       }
+      if (EPI == EPI_QKV) qkv_group(c, (c - c_ep) / 16, v);
     }
   }
   if (threadIdx.x == 0 && *fail && g.status) atomicOr(g.status, ST_TIMEOUT);
@@ -333,77 +325,38 @@ EncodeTiled encode_fn() {
   return fn;
 }
 
-template <int BN, int STAGES, int KB, int EPI, int KS>
+template <int BN, int STAGES, int KB, int EPI>
 cudaError_t prepare_tc_t() {
-  return cudaFuncSetAttribute(k_gemm_tc<BN, STAGES, KB, EPI, KS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)tc_smem_bytes<BN, STAGES, KS>());
-}
-
-template <int KB, int EPI, int KS>
-cudaError_t prepare_tc_ks() {
-  cudaError_t e = prepare_tc_t<32, 6, KB, EPI, KS>();
-  if (e == cudaSuccess) e = prepare_tc_t<64, 6, KB, EPI, KS>();
-  if (e == cudaSuccess) e = prepare_tc_t<128, 6, KB, EPI, KS>();
-  if (e == cudaSuccess) e = prepare_tc_t<256, 4, KB, EPI, KS>();
-  return e;
+  return cudaFuncSetAttribute(k_gemm_tc<BN, STAGES, KB, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)tc_smem_bytes<BN, STAGES>());
 }
 
 template <int KB, int EPI>
 cudaError_t prepare_tc_epi() {
-  cudaError_t e = prepare_tc_ks<KB, EPI, 1>();
-  if (e == cudaSuccess) e = prepare_tc_ks<KB, EPI, 2>();
-  if (e == cudaSuccess) e = prepare_tc_ks<KB, EPI, 4>();
+  cudaError_t e = prepare_tc_t<32, 6, KB, EPI>();
+  if (e == cudaSuccess) e = prepare_tc_t<64, 6, KB, EPI>();
+  if (e == cudaSuccess) e = prepare_tc_t<128, 6, KB, EPI>();
+  if (e == cudaSuccess) e = prepare_tc_t<256, 4, KB, EPI>();
   return e;
 }
 
-template <int BN, int STAGES, int KB, int EPI, int KS>
+template <int BN, int STAGES, int KB, int EPI>
 cudaError_t launch_tc_t(const TcGemm& g, cudaStream_t s, bool pdl) {
-  constexpr size_t smem = tc_smem_bytes<BN, STAGES, KS>();
-  auto kern = k_gemm_tc<BN, STAGES, KB, EPI, KS>;
+  constexpr size_t smem = tc_smem_bytes<BN, STAGES>();
+  auto kern = k_gemm_tc<BN, STAGES, KB, EPI>;
+  dim3 grid((g.M + kTileM - 1) / kTileM, (g.Bmax + BN - 1) / BN);
   const CUtensorMap* a = reinterpret_cast<const CUtensorMap*>(g.tmap_a);
   const CUtensorMap* b = reinterpret_cast<const CUtensorMap*>(g.tmap_b);
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3((g.M + kTileM - 1) / kTileM, (g.Bmax + BN - 1) / BN, KS);
-  cfg.blockDim = dim3(kTcThreads);
-  cfg.dynamicSmemBytes = smem;
-  cfg.stream = s;
-  cudaLaunchAttribute at[2];
-  int na = 0;
-  if (KS > 1) {
-    at[na].id = cudaLaunchAttributeClusterDimension;
-    at[na].val.clusterDim.x = 1;
-    at[na].val.clusterDim.y = 1;
-    at[na].val.clusterDim.z = KS;
-    ++na;
-  }
-  if (pdl) {
-    at[na].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    at[na].val.programmaticStreamSerializationAllowed = 1;
-    ++na;
-  }
-  cfg.attrs = at;
-  cfg.numAttrs = na;
-  return cudaLaunchKernelEx(&cfg, kern, *a, *b, g);
-}
-
-template <int BN, int KB, int EPI>
-cudaError_t launch_tc_bn(const TcGemm& g, cudaStream_t s, bool pdl) {
-  constexpr int ST = BN >= 256 ? 4 : 6;
-  switch (g.ks) {
-    case 1: return launch_tc_t<BN, ST, KB, EPI, 1>(g, s, pdl);
-    case 2: return launch_tc_t<BN, ST, KB, EPI, 2>(g, s, pdl);
-    case 4: return launch_tc_t<BN, ST, KB, EPI, 4>(g, s, pdl);
-  }
-  return cudaErrorInvalidValue;
+  return launch_kernel(kern, grid, dim3(kTcThreads), smem, s, pdl, *a, *b, g);
 }
 
 template <int KB, int EPI>
 cudaError_t launch_tc_epi(const TcGemm& g, cudaStream_t s, bool pdl) {
   switch (g.bn) {
-    case 32: return launch_tc_bn<32, KB, EPI>(g, s, pdl);
-    case 64: return launch_tc_bn<64, KB, EPI>(g, s, pdl);
-    case 128: return launch_tc_bn<128, KB, EPI>(g, s, pdl);
-    case 256: return launch_tc_bn<256, KB, EPI>(g, s, pdl);
+    case 32: return launch_tc_t<32, 6, KB, EPI>(g, s, pdl);
+    case 64: return launch_tc_t<64, 6, KB, EPI>(g, s, pdl);
+    case 128: return launch_tc_t<128, 6, KB, EPI>(g, s, pdl);
+    case 256: return launch_tc_t<256, 4, KB, EPI>(g, s, pdl);
   }
   return cudaErrorInvalidValue;
 }
@@ -523,12 +476,6 @@ bool tc_encode_tmap(void* tmap, const void* base, int elem_bytes, int64_t inner,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-int tc_ksplit(int K, int kind_bf16) {
-  const int kblk = kind_bf16 ? 64 : 128;
-  const int nk = (K + kblk - 1) / kblk;
-  return nk >= 16 ? 4 : nk >= 8 ? 2 : 1;
-}
-
 cudaError_t prepare_tc_kernels() {
   static bool done = false;                        // per-kernel attributes: once per process
   if (done) return cudaSuccess;
@@ -536,11 +483,13 @@ cudaError_t prepare_tc_kernels() {
   for (int kb = 0; kb < 2 && e == cudaSuccess; ++kb) {
     if (kb) {
       e = prepare_tc_epi<1, EPI_STORE>();
+      if (e == cudaSuccess) e = prepare_tc_epi<1, EPI_QKV>();
       if (e == cudaSuccess) e = prepare_tc_epi<1, EPI_RESID>();
       if (e == cudaSuccess) e = prepare_tc_epi<1, EPI_SWIGLU>();
       if (e == cudaSuccess) e = prepare_tc_epi<1, EPI_LOGITS>();
     } else {
       e = prepare_tc_epi<0, EPI_STORE>();
+      if (e == cudaSuccess) e = prepare_tc_epi<0, EPI_QKV>();
       if (e == cudaSuccess) e = prepare_tc_epi<0, EPI_RESID>();
       if (e == cudaSuccess) e = prepare_tc_epi<0, EPI_SWIGLU>();
       if (e == cudaSuccess) e = prepare_tc_epi<0, EPI_LOGITS>();
@@ -554,6 +503,7 @@ cudaError_t launch_gemm_tc(const TcGemm& g, int epi, cudaStream_t s, bool pdl) {
   if (g.kind_bf16) {
     switch (epi) {
       case EPI_STORE: return launch_tc_epi<1, EPI_STORE>(g, s, pdl);
+      case EPI_QKV: return launch_tc_epi<1, EPI_QKV>(g, s, pdl);
       case EPI_RESID: return launch_tc_epi<1, EPI_RESID>(g, s, pdl);
       case EPI_SWIGLU: return launch_tc_epi<1, EPI_SWIGLU>(g, s, pdl);
       case EPI_LOGITS: return launch_tc_epi<1, EPI_LOGITS>(g, s, pdl);
@@ -561,6 +511,7 @@ cudaError_t launch_gemm_tc(const TcGemm& g, int epi, cudaStream_t s, bool pdl) {
   } else {
     switch (epi) {
       case EPI_STORE: return launch_tc_epi<0, EPI_STORE>(g, s, pdl);
+      case EPI_QKV: return launch_tc_epi<0, EPI_QKV>(g, s, pdl);
       case EPI_RESID: return launch_tc_epi<0, EPI_RESID>(g, s, pdl);
       case EPI_SWIGLU: return launch_tc_epi<0, EPI_SWIGLU>(g, s, pdl);
       case EPI_LOGITS: return launch_tc_epi<0, EPI_LOGITS>(g, s, pdl);

@@ -349,24 +349,7 @@ struct AttnPre {
   float2 vf[KBF16 ? 1 : 32];
 };
 
-// (cos, sin) of position a for rotation pair dd: the product of the three
-// table rotations (a split into 8-bit digits), with explicit roundings (no
-// multiply-add contraction), so every kernel that rotates a position gets the
-// same bits.
-__device__ __forceinline__ float2 rope_cs(const Dims& D, int a, int dd) {
-  const float2 t1 = D.rope_tab[(0 * 256 + (a & 255)) * 32 + dd];
-  const float2 t2 = D.rope_tab[(1 * 256 + ((a >> 8) & 255)) * 32 + dd];
-  const float2 t3 = D.rope_tab[(2 * 256 + ((a >> 16) & 255)) * 32 + dd];
-  const float c12 = __fsub_rn(__fmul_rn(t1.x, t2.x), __fmul_rn(t1.y, t2.y));
-  const float s12 = __fadd_rn(__fmul_rn(t1.x, t2.y), __fmul_rn(t1.y, t2.x));
-  return make_float2(__fsub_rn(__fmul_rn(c12, t3.x), __fmul_rn(s12, t3.y)),
-                     __fadd_rn(__fmul_rn(c12, t3.y), __fmul_rn(s12, t3.x)));
-}
-// The rotated pair (x1, x2) -> (x1 c - x2 s, x2 c + x1 s).
-__device__ __forceinline__ float2 rope_rotate(float x1, float x2, float2 cs) {
-  return make_float2(__fsub_rn(__fmul_rn(x1, cs.x), __fmul_rn(x2, cs.y)),
-                     __fadd_rn(__fmul_rn(x2, cs.x), __fmul_rn(x1, cs.y)));
-}
+__device__ __forceinline__ float2 rope_cs(const Dims& D, int a, int dd) { return rope_cs_tab(D.rope_tab, a, dd); }
 
 // cos / sin of position a for the 32 rotation pairs.
 template <typename Sm>
@@ -379,8 +362,7 @@ __device__ __forceinline__ void attn_rope(const Dims& D, int a, int tid, Sm& sm)
 }
 
 __device__ __forceinline__ size_t attn_plane_off(const Dims& D, int layer, int which) {
-  const size_t plane = (size_t)D.L * kHeadDim;
-  return (size_t)layer * 2 * D.hkv * plane + (size_t)which * plane;
+  return kv_plane_off(D.L, D.hkv, layer, which);
 }
 
 // Cached K of position p_lo + lane and V of positions p_lo .. p_lo + 31
