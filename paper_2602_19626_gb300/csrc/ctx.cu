@@ -399,19 +399,22 @@ static int tc_setup(nc_ctx* ctx) {
         g.h16 = kb ? scratch : nullptr;             // the forward's SwiGLU output format
         g.zrows = scratch;
         g.status = ctx->d_status;
-        float ms_sum = 0.f;
+        // the best of four samples of five back-to-back launches (the first
+        // sample also loads the kernel)
+        float ms_best = 1e30f;
         for (int rep = 0; rep < 4; ++rep) {
           cudaEventRecord(e0, ctx->stream);
-          cudaError_t e = launch_gemm_tc(g, probe_epi[q], ctx->stream, false);
+          cudaError_t e = cudaSuccess;
+          for (int k = 0; k < 5 && e == cudaSuccess; ++k) e = launch_gemm_tc(g, probe_epi[q], ctx->stream, false);
           cudaEventRecord(e1, ctx->stream);
           if (e == cudaSuccess) e = cudaEventSynchronize(e1);
           if (e != cudaSuccess) return fail_cuda(ctx, e, "tensor-core autotune");
           float ms = 0.f;
           cudaEventElapsedTime(&ms, e0, e1);
-          if (rep) ms_sum += ms;
+          if (rep) ms_best = std::min(ms_best, ms);
         }
-        if (ms_sum < best) {
-          best = ms_sum;
+        if (ms_best < best) {
+          best = ms_best;
           chosen[q] = cands[ci];
         }
       }
@@ -857,7 +860,6 @@ static cudaError_t launch_model_tc(nc_ctx* ctx, const Batch& b, StepMarks& m) {
   const Dims& D = ctx->D;
   cudaStream_t s = ctx->stream;
   const int kb = ctx->fmt == NC_BF16;
-  int layer = 0;
   auto gemm = [&](const TcMat& t, int epi, float* y, float* h, void* h16 = nullptr) {
     const bool pf = b.pos != nullptr;               // prefill forward: P-row operand map
     TcGemm g{};
@@ -878,12 +880,6 @@ static cudaError_t launch_model_tc(nc_ctx* ctx, const Batch& b, StepMarks& m) {
     g.st = b.st;
     g.slots = b.slots;
     g.status = ctx->d_status;
-    g.pos = b.pos;
-    g.rope_tab = D.rope_tab;
-    g.L = D.L;
-    g.hq = D.hq;
-    g.hkv = D.hkv;
-    g.layer = layer;
     return launch_gemm_tc(g, epi, s, D.pdl);
   };
   cudaError_t e = launch_embed(D, b, ctx->embed, ctx->embed_scale, ctx->fmt, ctx->x, s);
@@ -891,10 +887,9 @@ static cudaError_t launch_model_tc(nc_ctx* ctx, const Batch& b, StepMarks& m) {
   for (int l = 0; l < D.n_layers && e == cudaSuccess; ++l) {
     const LayerW& L = ctx->layers[l];
     const TcMat* T = &ctx->tc[4 * l];
-    layer = l;
     e = launch_act_rmsnorm(D, b, ctx->x, L.g_attn, D.d, kb, ctx->opnd, ctx->opnd_scale, s);
-    // a prefill's QKV epilogue also appends every row's k and v to the ring
-    if (e == cudaSuccess) e = gemm(T[0], b.pos ? EPI_QKV : EPI_STORE, ctx->qkv, nullptr);
+    if (e == cudaSuccess) e = gemm(T[0], EPI_STORE, ctx->qkv, nullptr);
+    if (e == cudaSuccess && b.pos) e = launch_kv_append(D, b, l, ctx->qkv, s);
     if (e == cudaSuccess) e = m.mark(s, TK_QKV);
     if (e == cudaSuccess) e = launch_attn(D, b, l, ctx->qkv, ctx->attn_out, s, kb ? ctx->opnd : nullptr);
     if (e == cudaSuccess) e = m.mark(s, TK_ATTN);

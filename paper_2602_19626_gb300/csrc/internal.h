@@ -202,7 +202,7 @@ inline cudaError_t launch_kernel_cluster(void (*kern)(KArgs...), dim3 grid, dim3
 
 // ------------------------------------------------------------------ kernels
 enum Prologue { PRO_RMSNORM = 0, PRO_PLAIN = 2 };
-enum Epilogue { EPI_STORE = 0, EPI_RESID = 1, EPI_SWIGLU = 2, EPI_LOGITS = 3, EPI_QKV = 4 };
+enum Epilogue { EPI_STORE = 0, EPI_RESID = 1, EPI_SWIGLU = 2, EPI_LOGITS = 3 };
 
 struct GemvIO {
   const float* x;           // PRO_RMSNORM / PRO_PLAIN input [Bmax][cols]
@@ -297,12 +297,6 @@ struct TcGemm {
   float* zrows;             // EPI_LOGITS: [Bmax][M] when set
   const int32_t* slots;
   int32_t* status;          // error word (ST_TIMEOUT)
-  // EPI_QKV (the QKV projection of a prefill forward): besides EPI_STORE,
-  // row n's k rotated at position pos[n] and its v, rounded to BF16, into the
-  // KV ring of `layer` of stream slots[n] (rows with pos[n] < 0 skipped)
-  const int32_t* pos;
-  const float2* rope_tab;
-  int L, hq, hkv, layer;
 };
 bool tc_encode_tmap(void* tmap, const void* base, int elem_bytes, int64_t inner, int64_t outer, int box_outer);
 cudaError_t launch_gemm_tc(const TcGemm& g, int epi, cudaStream_t s, bool pdl);

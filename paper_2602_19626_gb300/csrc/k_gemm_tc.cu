@@ -62,7 +62,7 @@ __device__ __forceinline__ void epi_store(const TcGemm& g, int r, int n, int B, 
         g.h_out[(size_t)n * (g.M / 2) + (r >> 1)] = h;
     }
   } else if (n < B && r < g.M) {
-    if (EPI == EPI_STORE || EPI == EPI_QKV) {
+    if (EPI == EPI_STORE) {
       g.y[(size_t)n * g.M + r] = y;
     } else if (EPI == EPI_RESID) {
       g.y[(size_t)n * g.M + r] = res + y;
@@ -71,37 +71,6 @@ __device__ __forceinline__ void epi_store(const TcGemm& g, int r, int n, int B, 
         g.zrows[(size_t)n * g.M + r] = y;
       else
         g.st[g.slots[n]].z[r] = y;
-    }
-  }
-}
-
-// EPI_QKV, after the group's values y (columns n0c .. n0c + 15 of weight row
-// r) were staged by every warp of this column half: the k rows append
-// rotate(k[dd], k[dd + 32]) at each row's position (the thread of dd < 32
-// writes both, its partner's value from the stage), the v rows their values,
-// all rounded to BF16 into the KV ring; the same rotation and rounding as the
-// decode step's append.
-__device__ __forceinline__ void qkv_append(const TcGemm& g, int r, const float* partner, int n0c, int B,
-                                           const float (&y)[16]) {
-  const int kbase = g.hq * kHeadDim, vbase = kbase + g.hkv * kHeadDim;
-  if (r < kbase || r >= vbase + g.hkv * kHeadDim) return;
-  const bool is_k = r < vbase;
-  const int hk = ((is_k ? r - kbase : r - vbase)) / kHeadDim, dd = (is_k ? r - kbase : r - vbase) % kHeadDim;
-  if (is_k && dd >= kHeadDim / 2) return;           // written by the thread of dd - 32
-  const size_t plane = kv_plane_off(g.L, g.hkv, g.layer, is_k ? hk : g.hkv + hk);
-#pragma unroll
-  for (int i = 0; i < 16; ++i) {
-    const int n = n0c + i;
-    if (n >= B) break;
-    const int a = g.pos[n];
-    if (a < 0) continue;
-    __nv_bfloat16* ring = static_cast<__nv_bfloat16*>(g.st[g.slots[n]].kv) + plane + (size_t)(a & (g.L - 1)) * kHeadDim;
-    if (is_k) {
-      const float2 rr = rope_rotate(y[i], partner[i], rope_cs_tab(g.rope_tab, a, dd));
-      ring[dd] = __float2bfloat16_rn(rr.x);
-      ring[dd + kHeadDim / 2] = __float2bfloat16_rn(rr.y);
-    } else {
-      ring[dd] = __float2bfloat16_rn(y[i]);
     }
   }
 }
@@ -247,16 +216,6 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     const uint32_t tw = tmem + ((uint32_t)(quarter * 32) << 16);
     float ws = 1.f;
     if (!KIND_BF16 && r < g.M) ws = g.w_scale[r];
-    // EPI_QKV: every warp stages its group's values ([column half][group
-    // parity][128 rows][16]) in the stage buffers, free after the products
-    float* stage = reinterpret_cast<float*>(base);
-    auto qkv_group = [&](int c, int gi, const float (&y)[16]) {
-      float* mine = stage + ((half * 2 + (gi & 1)) * kTileM + quarter * 32 + lane) * 16;
-#pragma unroll
-      for (int i = 0; i < 16; i += 4) *reinterpret_cast<float4*>(mine + i) = make_float4(y[i], y[i + 1], y[i + 2], y[i + 3]);
-      __syncthreads();
-      qkv_append(g, r, mine + 32 * 16, n0 + c, B, y);
-    };
     // the columns whose residuals are already in registers
 #pragma unroll
     for (int c0 = 0; c0 < kPre; c0 += 16) {
@@ -268,7 +227,6 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         if (!KIND_BF16) v[i] *= ws * (n < B ? __ldg(g.x_scale + n) : 0.f);
         epi_store<EPI>(g, r, n, B, v[i], pre[c0 + i]);
       }
-      if (EPI == EPI_QKV) qkv_group(c_ep + c0, c0 / 16, v);
     }
 #pragma unroll 1
     for (int c = c_ep + kPre; c < c_ep + BN / 2; c += 16) {
@@ -289,7 +247,6 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         if (!KIND_BF16) v[i] *= ws * xs[i];
         epi_store<EPI>(g, r, n, B, v[i], res[i]);
       }
-      if (EPI == EPI_QKV) qkv_group(c, (c - c_ep) / 16, v);
     }
   }
   if (threadIdx.x == 0 && *fail && g.status) atomicOr(g.status, ST_TIMEOUT);
@@ -483,13 +440,11 @@ cudaError_t prepare_tc_kernels() {
   for (int kb = 0; kb < 2 && e == cudaSuccess; ++kb) {
     if (kb) {
       e = prepare_tc_epi<1, EPI_STORE>();
-      if (e == cudaSuccess) e = prepare_tc_epi<1, EPI_QKV>();
       if (e == cudaSuccess) e = prepare_tc_epi<1, EPI_RESID>();
       if (e == cudaSuccess) e = prepare_tc_epi<1, EPI_SWIGLU>();
       if (e == cudaSuccess) e = prepare_tc_epi<1, EPI_LOGITS>();
     } else {
       e = prepare_tc_epi<0, EPI_STORE>();
-      if (e == cudaSuccess) e = prepare_tc_epi<0, EPI_QKV>();
       if (e == cudaSuccess) e = prepare_tc_epi<0, EPI_RESID>();
       if (e == cudaSuccess) e = prepare_tc_epi<0, EPI_SWIGLU>();
       if (e == cudaSuccess) e = prepare_tc_epi<0, EPI_LOGITS>();
@@ -503,7 +458,6 @@ cudaError_t launch_gemm_tc(const TcGemm& g, int epi, cudaStream_t s, bool pdl) {
   if (g.kind_bf16) {
     switch (epi) {
       case EPI_STORE: return launch_tc_epi<1, EPI_STORE>(g, s, pdl);
-      case EPI_QKV: return launch_tc_epi<1, EPI_QKV>(g, s, pdl);
       case EPI_RESID: return launch_tc_epi<1, EPI_RESID>(g, s, pdl);
       case EPI_SWIGLU: return launch_tc_epi<1, EPI_SWIGLU>(g, s, pdl);
       case EPI_LOGITS: return launch_tc_epi<1, EPI_LOGITS>(g, s, pdl);
@@ -511,7 +465,6 @@ cudaError_t launch_gemm_tc(const TcGemm& g, int epi, cudaStream_t s, bool pdl) {
   } else {
     switch (epi) {
       case EPI_STORE: return launch_tc_epi<0, EPI_STORE>(g, s, pdl);
-      case EPI_QKV: return launch_tc_epi<0, EPI_QKV>(g, s, pdl);
       case EPI_RESID: return launch_tc_epi<0, EPI_RESID>(g, s, pdl);
       case EPI_SWIGLU: return launch_tc_epi<0, EPI_SWIGLU>(g, s, pdl);
       case EPI_LOGITS: return launch_tc_epi<0, EPI_LOGITS>(g, s, pdl);

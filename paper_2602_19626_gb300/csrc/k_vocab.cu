@@ -477,10 +477,10 @@ __device__ __forceinline__ float entropy_part(const float (&png)[E]) {
 }
 
 // Softmax partials of the warp: its maximum m_w of s, e_i = exp(s_i - m_w)
-// = 2^(s_i log2 e - m_w log2 e) and the sum of the e_i; h (a second sum) is
-// reduced alongside.
+// = 2^(s_i log2 e - m_w log2 e) and the sum of the e_i; h (a second sum, the
+// entropy part of the confidence skip) is reduced alongside when `with_h`.
 template <int E>
-__device__ __forceinline__ float4 softmax_part(const float (&s)[E], float (&e)[E], float h) {
+__device__ __forceinline__ float4 softmax_part(const float (&s)[E], float (&e)[E], float h, bool with_h) {
   float m = -INFINITY;
 #pragma unroll
   for (int i = 0; i < E; ++i) m = fmaxf(m, s[i]);
@@ -497,7 +497,7 @@ __device__ __forceinline__ float4 softmax_part(const float (&s)[E], float (&e)[E
       t = __fadd_rn(t, e[i]);
     }
   }
-  return make_float4(m, warp_sum(t), warp_sum(h), 0.f);
+  return make_float4(m, warp_sum(t), with_h ? warp_sum(h) : 0.f, 0.f);
 }
 
 // The cluster's softmax: M = max m_w, S = sum_w t_w exp(m_w - M), and the
@@ -505,7 +505,7 @@ __device__ __forceinline__ float4 softmax_part(const float (&s)[E], float (&e)[E
 struct Soft {
   float M, S, H;
 };
-__device__ __forceinline__ Soft softmax_reduce(const float4 (&v)[4]) {
+__device__ __forceinline__ Soft softmax_reduce(const float4 (&v)[4], bool with_h) {
   const float M = warp_max(fmaxf(fmaxf(v[0].x, v[1].x), fmaxf(v[2].x, v[3].x)));
   float s = 0.f, h = 0.f;
 #pragma unroll
@@ -513,7 +513,7 @@ __device__ __forceinline__ Soft softmax_reduce(const float4 (&v)[4]) {
     if (v[i].y > 0.f) s = __fmaf_rn(v[i].y, exp_fast(__fsub_rn(v[i].x, M)), s);
     h = __fadd_rn(h, v[i].z);
   }
-  return Soft{M, warp_sum(s), warp_sum(h)};
+  return Soft{M, warp_sum(s), with_h ? warp_sum(h) : 0.f};
 }
 
 // p_tilde of the thread's symbols: e_i exp(m_w - M) / S.
@@ -834,12 +834,12 @@ __global__ void __launch_bounds__(step_threads<CL>(), 1) k_vocab(Dims D, Batch b
     s_t = pick<E>(s, L.v0, t);
     png_t = pick<E>(png, L.v0, t);
   }
-  const float4 part = softmax_part<E>(s, e, D.skip ? entropy_part<E>(png) : 0.f);
+  const float4 part = softmax_part<E>(s, e, D.skip ? entropy_part<E>(png) : 0.f, D.skip != 0);
   push_part<CL>(cl, sh.slot[0].sm, L, part);
   cl.sync();
   float4 smv[4];
   local_parts(sh.slot[0].sm, L.lane, smv);
-  const Soft sm = softmax_reduce(smv);
+  const Soft sm = softmax_reduce(smv, D.skip != 0);
   const bool skipped = D.skip && sm.H < kSkipBits;
   float pt[E];
   probs_tilde<E>(e, part.x, sm, pt);
@@ -1031,7 +1031,7 @@ __global__ void __launch_bounds__(step_threads<CL>(), 1)
       s_t = pick<E>(s, L.v0, t);
       png_t = pick<E>(png, L.v0, t);
     }
-    const float4 part = softmax_part<E>(s, e, D.skip ? entropy_part<E>(png) : 0.f);
+    const float4 part = softmax_part<E>(s, e, D.skip ? entropy_part<E>(png) : 0.f, D.skip != 0);
     StepSlot& in = sh.slot[nb & 1];
     push_part<CL>(cl, in.sm, L, part);
     if (ngram) cp_async_wait_all();              // the state of position r + 2, added after this barrier
@@ -1053,7 +1053,7 @@ __global__ void __launch_bounds__(step_threads<CL>(), 1)
     ++nb;
     float4 smv[4];
     local_parts(in.sm, L.lane, smv);
-    const Soft sm = softmax_reduce(smv);
+    const Soft sm = softmax_reduce(smv, D.skip != 0);
     float pt[E];
     if (pend) {                                  // position r - 1 (log-loss mixer: no head step here)
       finish(in, pt, false);
