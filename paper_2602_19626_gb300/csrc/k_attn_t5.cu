@@ -29,15 +29,18 @@
 //   - the chunk's (M_c, l_c, O_c) = (max m_b, sum l_b f_b, sum O_b f_b),
 //     f_b = exp(m_b - M_c), blocks in order, a block past the row absent;
 //   - after a cluster barrier (every rank done with its query and key tiles)
-//     each rank receives, in that memory, every chunk's (M_c, l_c) and its
-//     64 / S dims of O_c (remote stores), and after a second barrier merges
-//     the chunks in order: O = sum O_c f_c / sum l_c f_c with
-//     f_c = exp(M_c - max M_c).
+//     rank k receives, in that memory, every chunk's (O_c, M_c, l_c) of the
+//     pairs 128 k / S .. 128 (k + 1) / S - 1 (remote stores), and after a
+//     second barrier merges them over the chunks in order:
+//     O = sum O_c f_c / sum l_c f_c with f_c = exp(M_c - max M_c).
 // The arithmetic of a row is fixed by its window alone.  In a decode step the
 // rank of the chunk holding the fed position a rotates the new k at a, rounds
 // k and v to BF16, appends them to the ring and to its tile; a prefill's rows
 // were appended by k_kv_append (the same rotation code) before this kernel.
-// About 92 KB of shared memory and 256 TMEM columns: two CTAs per SM.
+// About 92 KB of shared memory and 256 TMEM columns: two CTAs per SM; the
+// clusters are launched with the load-balancing placement, so that a
+// cluster's CTAs may share SMs (spread placement admits about 15 clusters of
+// 8 at a time).
 //
 // Every wait on an mbarrier is bounded; a wait that gives up raises
 // ST_TIMEOUT in the stream's status word, skips the remaining products and,
@@ -71,8 +74,9 @@ constexpr uint32_t kT5Cols = 256;            // TMEM columns: S_b, then O_b, at 
 // (cos, sin) of the tile rows' positions, RT rows of 32 pairs.
 struct T5Layout {
   int q, k, v, cs, bars, slot, arow, total;
-  // the inbox, after the first cluster barrier, in the query and key tiles
-  int rm, rl, racc;
+  // the inbox, after the first cluster barrier, in the query and key tiles:
+  // [S chunks][128 / S pairs][68] floats (O_c[64], M_c, l_c, padding)
+  int inbox;
   __host__ __device__ explicit T5Layout(int rt) {
     q = 0;                                   // [128 pairs][128 B]
     k = q + kT5Pairs * kRowB;                // [256 positions][128 B]; later P_0, P_1 (16 KB each)
@@ -82,13 +86,11 @@ struct T5Layout {
     slot = bars + 64;                        // TMEM address
     arow = slot + 16;                        // [128] row positions
     total = arow + kT5Pairs * 4;
-    rm = 0;                                  // [8 chunks][128 pairs] chunk maxima
-    rl = rm + kT5MaxRanks * kT5Pairs * 4;    // [8][128] chunk sums
-    racc = rl + kT5MaxRanks * kT5Pairs * 4;  // [S chunks][128 pairs][64 / S] dims
+    inbox = 0;
   }
 };
-static_assert(2 * kT5MaxRanks * kT5Pairs * 4 + kT5Pairs * kHeadDim * 4 <= (kT5Pairs + kT5Chunk) * kRowB,
-              "the inbox fits the query and key tiles");
+constexpr int kInboxRow = kHeadDim + 4;      // floats per (chunk, pair) record
+static_assert(kT5Pairs * kInboxRow * 4 <= (kT5Pairs + kT5Chunk) * kRowB, "the inbox fits the query and key tiles");
 
 constexpr float kLog2e = 1.4426950408889634f;
 
@@ -137,14 +139,6 @@ __device__ void load_kv_tile(const Dims& D, const StreamDev& st, int layer, int 
       *reinterpret_cast<uint4*>(dv) = make_uint4(0, 0, 0, 0);
     }
   }
-}
-
-// One output value: FP32 into attn_out, or rounded to BF16 into out16.
-__device__ __forceinline__ void store_out(const AttnIO& io, size_t i, float v) {
-  if (io.out16)
-    static_cast<__nv_bfloat16*>(io.out16)[i] = __float2bfloat16_rn(v);
-  else
-    io.attn_out[i] = v;
 }
 
 // Softmax of one 64-position block for this thread's pair: the block
@@ -206,15 +200,13 @@ __global__ void __launch_bounds__(kT5Threads, 2) k_attn_t5(Dims D, Batch b, int 
   uint8_t* kt = sm + Ly.k;
   uint8_t* vt = sm + Ly.v;
   float2* cs = reinterpret_cast<float2*>(sm + Ly.cs);
-  float* rm = reinterpret_cast<float*>(sm + Ly.rm);
-  float* rl = reinterpret_cast<float*>(sm + Ly.rl);
-  float* racc = reinterpret_cast<float*>(sm + Ly.racc);
+  float* inbox = reinterpret_cast<float*>(sm + Ly.inbox);
   uint64_t* bar_s = reinterpret_cast<uint64_t*>(sm + Ly.bars);    // every score product
   uint64_t* bar_o = bar_s + 1;                                     // [4] P V of block b
   uint64_t* bar_done = bar_s + 5;                                  // every product issued
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sm + Ly.slot);
   int* a_row = reinterpret_cast<int*>(sm + Ly.arow);
-  constexpr int kd = kHeadDim / S;                 // output dims merged by one rank
+  constexpr int kPR = kT5Pairs / S;                // pairs merged by one rank
 
   const int rank = S > 1 ? (int)cg::this_cluster().block_rank() : 0;
   const int g = blockIdx.y;
@@ -268,6 +260,7 @@ __global__ void __launch_bounds__(kT5Threads, 2) k_attn_t5(Dims D, Batch b, int 
   for (int d = 0; d < kHeadDim; ++d) oc[d] = 0.f;
   if (has_chunk) {
     // (cos, sin) of every tile row's position
+#pragma unroll 12
     for (int e = tid; e < nr * (kHeadDim / 2); e += kT5Threads) {
       const int r = e / (kHeadDim / 2), dd = e % (kHeadDim / 2);
       if (a_row[r] >= 0) cs[e] = rope_cs(D, a_row[r], dd);
@@ -414,57 +407,60 @@ __global__ void __launch_bounds__(kT5Threads, 2) k_attn_t5(Dims D, Batch b, int 
   else
     __syncthreads();
   if (has_chunk && ok && mine && my_a >= c_lo) {
-    // every rank receives the chunk's (M_c, l_c) and its dims of O_c
+    // the chunk's (O_c, M_c, l_c) of this pair to the rank merging it
+    float* dst = inbox + ((size_t)rank * kPR + tid % kPR) * kInboxRow;
+    if (S > 1) dst = cg::this_cluster().map_shared_rank(dst, tid / kPR);
 #pragma unroll
-    for (int k = 0; k < S; ++k) {
-      float* trm = rm;
-      float* trl = rl;
-      float* tra = racc;
-      if (S > 1) {
-        cg::cluster_group cl = cg::this_cluster();
-        trm = cl.map_shared_rank(rm, k);
-        trl = cl.map_shared_rank(rl, k);
-        tra = cl.map_shared_rank(racc, k);
-      }
-      trm[rank * kT5Pairs + tid] = Mc;
-      trl[rank * kT5Pairs + tid] = Lc;
-      float* dst = tra + ((size_t)rank * kT5Pairs + tid) * kd;
-#pragma unroll
-      for (int d = 0; d < kd; d += 4)
-        *reinterpret_cast<float4*>(dst + d) = make_float4(oc[k * kd + d], oc[k * kd + d + 1], oc[k * kd + d + 2],
-                                                          oc[k * kd + d + 3]);
-    }
+    for (int d = 0; d < kHeadDim; d += 4)
+      *reinterpret_cast<float4*>(dst + d) = make_float4(oc[d], oc[d + 1], oc[d + 2], oc[d + 3]);
+    *reinterpret_cast<float4*>(dst + kHeadDim) = make_float4(Mc, Lc, 0.f, 0.f);
   }
   if (S > 1)
     cg::this_cluster().sync();                     // every chunk's partials have arrived
   else
     __syncthreads();
-  // merge this rank's dims over the row's chunks, in chunk order
-  if (tid < npairs) {
-    const size_t out = (size_t)(row0 + my_r) * D.hq * kHeadDim + (g * grp + my_h) * kHeadDim + rank * kd;
-    if (my_a < 0) {
-      for (int d = 0; d < kd; ++d) store_out(io, out + d, 0.f);
-    } else {
-      const int ncp = (my_a - start) / kT5Chunk + 1;
+  // merge this rank's pairs over the row's chunks, in chunk order: work item
+  // (pair, group of 8 dims)
+#pragma unroll 1
+  for (int it = tid; it < kPR * (kHeadDim / 8); it += kT5Threads) {
+    const int lp = it / (kHeadDim / 8), dg = it % (kHeadDim / 8);
+    const int p = rank * kPR + lp;
+    if (p >= npairs) continue;
+    const int r = p / grp, h = p % grp, a = a_row[r];
+    const size_t out = (size_t)(row0 + r) * D.hq * kHeadDim + (g * grp + h) * kHeadDim + dg * 8;
+    float o[8];
+#pragma unroll
+    for (int d = 0; d < 8; ++d) o[d] = 0.f;
+    if (a >= 0) {
+      const int ncp = (a - start) / kT5Chunk + 1;
+      const float* rec = inbox + (size_t)lp * kInboxRow;           // chunk c at + c kPR kInboxRow
       float M = -INFINITY;
-      for (int c = 0; c < ncp; ++c) M = fmaxf(M, rm[c * kT5Pairs + tid]);
-      float fc[kT5MaxRanks];
+      for (int c = 0; c < ncp; ++c) M = fmaxf(M, rec[(size_t)c * kPR * kInboxRow + kHeadDim]);
       float l = 0.f;
-#pragma unroll
-      for (int c = 0; c < kT5MaxRanks; ++c) {
-        fc[c] = 0.f;
-        if (c < ncp) {
-          fc[c] = exp_fast(__fsub_rn(rm[c * kT5Pairs + tid], M));
-          l = __fmaf_rn(rl[c * kT5Pairs + tid], fc[c], l);
-        }
+      for (int c = 0; c < ncp; ++c) {
+        const float* rc = rec + (size_t)c * kPR * kInboxRow;
+        const float f = exp_fast(__fsub_rn(rc[kHeadDim], M));
+        l = __fmaf_rn(rc[kHeadDim + 1], f, l);
+        const float4 u0 = *reinterpret_cast<const float4*>(rc + dg * 8);
+        const float4 u1 = *reinterpret_cast<const float4*>(rc + dg * 8 + 4);
+        o[0] = __fmaf_rn(u0.x, f, o[0]);
+        o[1] = __fmaf_rn(u0.y, f, o[1]);
+        o[2] = __fmaf_rn(u0.z, f, o[2]);
+        o[3] = __fmaf_rn(u0.w, f, o[3]);
+        o[4] = __fmaf_rn(u1.x, f, o[4]);
+        o[5] = __fmaf_rn(u1.y, f, o[5]);
+        o[6] = __fmaf_rn(u1.z, f, o[6]);
+        o[7] = __fmaf_rn(u1.w, f, o[7]);
       }
-      for (int d = 0; d < kd; ++d) {
-        float o = 0.f;
 #pragma unroll
-        for (int c = 0; c < kT5MaxRanks; ++c)
-          if (c < ncp) o = __fmaf_rn(racc[((size_t)c * kT5Pairs + tid) * kd + d], fc[c], o);
-        store_out(io, out + d, __fdiv_rn(o, l));
-      }
+      for (int d = 0; d < 8; ++d) o[d] = __fdiv_rn(o[d], l);
+    }
+    if (io.out16) {
+      *reinterpret_cast<uint4*>(static_cast<__nv_bfloat16*>(io.out16) + out) =
+          make_uint4(pack_bf16(o[0], o[1]), pack_bf16(o[2], o[3]), pack_bf16(o[4], o[5]), pack_bf16(o[6], o[7]));
+    } else {
+      *reinterpret_cast<float4*>(io.attn_out + out) = make_float4(o[0], o[1], o[2], o[3]);
+      *reinterpret_cast<float4*>(io.attn_out + out + 4) = make_float4(o[4], o[5], o[6], o[7]);
     }
   }
   if (has_chunk) {
@@ -480,8 +476,10 @@ template <int S>
 cudaError_t launch_t5_s(const Dims& D, const Batch& b, int layer, const AttnIO& io, cudaStream_t s) {
   static bool attr = false;                        // the kernel's shared-memory limit, once per process
   if (!attr) {
-    const cudaError_t e =
-        cudaFuncSetAttribute(k_attn_t5<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)t5_smem(1));
+    cudaError_t e = cudaFuncSetAttribute(k_attn_t5<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)t5_smem(1));
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_attn_t5<S>, cudaFuncAttributeClusterSchedulingPolicyPreference,
+                               cudaClusterSchedulingPolicyLoadBalancing);
     if (e != cudaSuccess) return e;
     attr = true;
   }
