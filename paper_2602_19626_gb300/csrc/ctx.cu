@@ -32,6 +32,7 @@ struct Slot {
   int64_t max_len = 0;
   // device buffers owned by the slot (kept across reopen when large enough)
   void* kv = nullptr;
+  bool kv_ready = false;     // kv zeroed and its TMA map written
   float* bias = nullptr;
   int32_t* uni = nullptr;
   float* z = nullptr;
@@ -625,6 +626,19 @@ extern "C" int nc_ctx_create(const nc_config* cfg, const void* weights, size_t n
       dalloc(ctx, &ctx->d_lohi, B * 8) || dalloc(ctx, &ctx->d_status, B * 4) ||
       dalloc(ctx, &ctx->d_st, B * sizeof(StreamDev)))
     return bail(NC_ENOMEM);
+  if (D.kv_bf16) {
+    attn_t5_scratch(D, (int)B, ctx->P, &D.attn_part_cap, &D.attn_tickets);
+    if (dalloc(ctx, &D.attn_part, D.attn_part_cap * 4) || dalloc(ctx, &D.attn_ticket, (size_t)D.attn_tickets * 4))
+      return bail(NC_ENOMEM);
+    if (cudaMemset(D.attn_ticket, 0, (size_t)D.attn_tickets * 4) != cudaSuccess) return bail(NC_ECUDA);
+    if (ctx->P > 0 && dalloc(ctx, &D.q16, (size_t)ctx->P * D.hq * kHeadDim * 2)) return bail(NC_ENOMEM);
+    // the attention loads 64-row boxes of the KV rings through one TMA map per slot
+    void* maps = nullptr;
+    if (D.L >= 64) {
+      if (dalloc(ctx, &maps, B * kTmapBytes)) return bail(NC_ENOMEM);
+      D.kv_tmap = maps;
+    }
+  }
   if (cudaMallocHost(&ctx->h_i32, (3 * B + 4) * 4) != cudaSuccess ||
       cudaMallocHost(&ctx->h_u32, 3 * B * 4) != cudaSuccess ||
       cudaMallocHost(&ctx->h_status, B * 4) != cudaSuccess)
@@ -646,6 +660,8 @@ extern "C" int nc_ctx_create(const nc_config* cfg, const void* weights, size_t n
 
 // ---------------------------------------------------------------- streams
 
+static_assert(sizeof(CUtensorMap) == kTmapBytes, "one TMA map per slot");
+
 static int slot_alloc(nc_ctx* ctx, Slot& s, int64_t max_len) {
   const Dims& D = ctx->D;
   if (!s.kv) {
@@ -654,6 +670,21 @@ static int slot_alloc(nc_ctx* ctx, Slot& s, int64_t max_len) {
     NC_TRY(dev_malloc(&s.bias, (size_t)D.V * 4));
     NC_TRY(dev_malloc(&s.uni, (size_t)D.V * 4));
     NC_TRY(dev_malloc(&s.z, (size_t)D.V * 4));
+  }
+  if (!s.kv_ready) {
+    // every ring entry finite from the start: the tensor-core attention
+    // multiplies the entries past a row's position by zero probabilities
+    const size_t kvb = (size_t)D.n_layers * 2 * D.hkv * D.L * kHeadDim * (D.kv_bf16 ? 2 : 4);
+    NC_TRY(cudaMemset(s.kv, 0, kvb));
+    if (D.kv_tmap) {
+      CUtensorMap map;
+      if (!tc_encode_tmap(&map, s.kv, 2, kHeadDim, (int64_t)D.n_layers * 2 * D.hkv * D.L, 64))
+        return fail(ctx, NC_ECUDA, "KV tensor map encoding failed");
+      const int si = (int)(&s - ctx->slots.data());
+      NC_TRY(cudaMemcpy(static_cast<unsigned char*>(const_cast<void*>(D.kv_tmap)) + (size_t)si * kTmapBytes, &map,
+                        kTmapBytes, cudaMemcpyHostToDevice));
+    }
+    s.kv_ready = true;
   }
   if (D.order > 0 && s.cap_len < max_len) {
     for (int k = 0; k < 3; ++k) {

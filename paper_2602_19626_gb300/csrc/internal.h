@@ -75,6 +75,8 @@ struct StreamDev {
 constexpr int kRopeLevels = 3;
 constexpr int kMaxPosition = 1 << 24;
 
+constexpr int kTmapBytes = 128;             // one CUtensorMap
+
 struct Dims {
   int pdl;                  // launch step kernels with programmatic dependent launch
   const float2* rope_tab;   // [kRopeLevels][256][32]
@@ -92,6 +94,15 @@ struct Dims {
   int log2T;
   uint32_t floor;
   float alpha, eta;
+  // tensor-core attention over a BF16 cache: per (tile, KV head) the chunks'
+  // partial results and the ticket that picks the CTA merging them
+  const void* kv_tmap;      // [max_streams] TMA maps (kTmapBytes each) of the slots' BF16 KV
+                            // rings as 64-wide rows; nullptr: the attention copies rows itself
+  void* q16;                // [prefill_rows][hq * 64] BF16 rotated 1/8-scaled queries of a prefill
+  float* attn_part;         // attn_part_cap floats
+  int32_t* attn_ticket;     // attn_tickets counters, zero between launches
+  size_t attn_part_cap;
+  int attn_tickets;
 };
 
 // Weights of one dense projection in the storage format.
@@ -268,8 +279,14 @@ cudaError_t launch_prepare_prefill(const Batch& b, int n_streams, int m, int V, 
 // k, v appended by the kernel) or prefill rows (b.pm consecutive positions
 // per stream, appended before), into attn_out or, when out16 is set, BF16
 // into out16.  A row's result does not depend on the other rows.
+// D.attn_part / D.attn_ticket must hold what attn_t5_scratch gives for the
+// context's largest batches (tickets zeroed once).
 cudaError_t launch_attn_t5(const Dims& D, const Batch& b, int layer, const float* qkv, float* attn_out, void* out16,
                            cudaStream_t s);
+void attn_t5_scratch(const Dims& D, int max_streams, int prefill_rows, size_t* part_floats, int* tickets);
+// Prefill with a BF16 cache: rotate and append every row's k, v to the ring
+// of `layer` and write its rotated, 1/8-scaled BF16 queries to D.q16.
+cudaError_t launch_kv_append_t5(const Dims& D, const Batch& b, int layer, const float* qkv, cudaStream_t s);
 // Prefill: rotate and append the k, v of every row to the KV ring of `layer`.
 cudaError_t launch_kv_append(const Dims& D, const Batch& b, int layer, const float* qkv, cudaStream_t s);
 // Decoder: row j's symbol is the s with cdf[s] <= target[j] < cdf[s+1]; writes

@@ -559,6 +559,7 @@ cudaError_t launch_attn(const Dims& D, const Batch& b, int layer, const float* q
 }
 
 cudaError_t launch_kv_append(const Dims& D, const Batch& b, int layer, const float* qkv, cudaStream_t s) {
+  if (D.kv_bf16) return launch_kv_append_t5(D, b, layer, qkv, s);
   AttnIO io{qkv, nullptr};
   return launch_kernel(D.kv_bf16 ? k_kv_append<1> : k_kv_append<0>, dim3(D.hkv, b.Bmax), dim3(kAttnThreads), 0, s,
                        D.pdl, D, b, layer, io);

@@ -11,6 +11,7 @@ namespace nc {
 namespace tc5 {
 
 constexpr uint32_t kWaitLimit = 1u << 22;     // polls of one bounded mbarrier wait
+constexpr uint64_t kWaitNs = 200000000ull;    // and at most 0.2 s of it (a poll may suspend the thread)
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -23,10 +24,17 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
                : "memory");
 }
 
-// Bounded wait for the phase with the given parity: at most `polls` polls;
-// false when it gave up.
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Bounded wait for the phase with the given parity: at most `polls` polls
+// and about kWaitNs of global time; false when it gave up.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint32_t polls = kWaitLimit) {
   const uint32_t a = smem_u32(bar);
+  uint64_t t0 = 0;
   for (uint32_t it = 0; it < polls; ++it) {
     uint32_t ok;
     asm volatile(
@@ -35,6 +43,11 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint32
         : "r"(a), "r"(parity)
         : "memory");
     if (ok) return true;
+    if ((it & 63) == 63) {
+      const uint64_t t = global_ns();
+      if (t0 == 0) t0 = t;
+      else if (t - t0 > kWaitNs) return false;
+    }
   }
   return false;
 }

@@ -111,3 +111,39 @@ def test_prefill_attention_split(nc, monkeypatch, fmt, path, split):
     monkeypatch.setenv("NC24_ATTN_CLUSTER", split)
     got = intervals(nc, shape, w, fmt, path, toks, 1024, 2)
     assert np.array_equal(got, ref)
+
+
+@pytest.mark.parametrize("path,ctx_len,slide", [("tc", 256, 40), ("gemv", 256, 40), ("tc", 32, 8)])
+def test_bf16_cache_ring_wrap_windows(nc, path, ctx_len, slide):
+    """BF16 KV cache with windows whose 64-position attention blocks wrap
+    around the ring (a slide of 40: the window starts at multiples of 40) and
+    with a ring shorter than one block (window 32): the per-token step's
+    logits against the oracle on the dequantised BF16 weights (Sec. 3.9
+    window, slides included), and the prefill's intervals equal the
+    per-token step's bit for bit."""
+    from oracle.model import Model
+
+    shape, seed = dataclasses.replace(S.SMALL, ctx_len=ctx_len, slide=slide), 11
+    w = S.flat_weights(shape, seed)
+    n = 2 * ctx_len + 3 * slide + 5
+    toks = S.token_stream(seed, 0, n, shape.vocab)
+    ctx = nc.Context(nc.make_config(shape, fmt="bf16", path=path, warmup=20), w)
+    z = torch.empty(1, shape.vocab, device="cuda")
+    ctx.stream_open(0, n)
+    m = Model(shape, S.weights(shape, seed), "bf16")
+    cache = m.new_cache()
+    last = Model.BOS
+    err = 0.0
+    for t in toks:
+        ctx.step_probe([0], z=z)
+        ref = m.step(cache, last)
+        err = max(err, float(np.max(np.abs(z[0].cpu().numpy() - ref))))
+        ctx.update_bias([0], [int(t)])
+        last = int(t)
+    ctx.close()
+    assert cache.slides >= 3
+    print(f"{path} window {ctx_len} slide {slide}: logits max abs err {err:.3e}")
+    assert err <= 1.5e-2
+    ref_iv = intervals(nc, shape, w, "bf16", path, [toks], 0, 1)
+    got_iv = intervals(nc, shape, w, "bf16", path, [toks], 4 * slide, 1)
+    assert np.array_equal(got_iv, ref_iv)
