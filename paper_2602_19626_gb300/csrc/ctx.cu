@@ -44,14 +44,18 @@ struct Slot {
 };
 
 // One projection on the tensor-core path: tensor maps of the weights (box of
-// 128 rows) and of the batch operand (box of bn rows), and the tuned bn.
+// 128 rows) and of the batch operand (all its rows, one map per batch tile
+// bn = 32, 64, 128, 256), and the bn tuned for a decode step (max_streams
+// rows) and for prefill forwards of prefill_rows >> k rows, k < kPfBuckets.
+constexpr int kPfBuckets = 4;
 struct TcMat {
   CUtensorMap a;
-  CUtensorMap b;                     // operand of a decode step (max_streams rows)
-  CUtensorMap bp;                    // operand of a prefill forward (prefill_rows rows)
-  int M = 0, K = 0, bn = 0, bnp = 0;
+  CUtensorMap b[4];
+  int M = 0, K = 0;
+  int bn_dec = 0, bn_pf[kPfBuckets] = {};
   const float* scale = nullptr;
 };
+static int bn_index(int bn) { return bn == 32 ? 0 : bn == 64 ? 1 : bn == 128 ? 2 : 3; }
 
 }  // namespace
 
@@ -360,7 +364,7 @@ static int tc_setup(nc_ctx* ctx) {
   Mat head{ctx->embed, ctx->embed_scale, D.V, D.d};
   if (!add(head)) return fail(ctx, NC_ECUDA, "tensor map encoding failed");
   // autotune bn per distinct shape (layer 0's matrices and the LM head), for
-  // a decode step (B rows) and for a prefill forward (P rows)
+  // a decode step (B rows) and for prefill forwards of P, P / 2, P / 4, P / 8 rows
   float* scratch = nullptr;
   size_t maxM = 0;
   for (const TcMat& t : ctx->tc) maxM = std::max(maxM, (size_t)t.M);
@@ -382,11 +386,11 @@ static int tc_setup(nc_ctx* ctx) {
       chosen[q] = cands[0];
       for (int ci = 0; ci < nc; ++ci) {
         TcMat tt = t;
-        if (!tc_encode_tmap(&tt.b, ctx->opnd, esz, t.K, rows, cands[ci]))
+        if (!tc_encode_tmap(&tt.b[0], ctx->opnd, esz, t.K, rows, cands[ci]))
           return fail(ctx, NC_ECUDA, "tensor map encoding failed");
         TcGemm g{};
         g.tmap_a = &tt.a;
-        g.tmap_b = &tt.b;
+        g.tmap_b = &tt.b[0];
         g.M = t.M;
         g.K = t.K;
         g.Bmax = rows;
@@ -422,9 +426,10 @@ static int tc_setup(nc_ctx* ctx) {
     }
     return NC_OK;
   };
-  int chosen[5] = {0, 0, 0, 0, 0}, chosen_p[5] = {0, 0, 0, 0, 0};
+  int chosen[5] = {0, 0, 0, 0, 0}, chosen_p[kPfBuckets][5] = {};
   int st = tune(B, chosen);
-  if (st == NC_OK && ctx->P > 0) st = tune(ctx->P, chosen_p);
+  for (int k = 0; k < kPfBuckets && st == NC_OK && ctx->P > 0; ++k)
+    st = tune(std::max(ctx->P >> k, 1), chosen_p[k]);
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   cudaFree(scratch);
@@ -434,13 +439,10 @@ static int tc_setup(nc_ctx* ctx) {
     TcMat& t = ctx->tc[i];
     const int q = (i + 1 == ctx->tc.size()) ? 4 : (int)(i % 4);
     const void* src = (kb && q == 3) ? ctx->opnd2 : ctx->opnd;   // BF16: the down projection reads opnd2
-    t.bn = chosen[q];
-    if (!tc_encode_tmap(&t.b, src, esz, t.K, B, t.bn)) return fail(ctx, NC_ECUDA, "tensor map encoding failed");
-    if (ctx->P > 0) {
-      t.bnp = chosen_p[q];
-      if (!tc_encode_tmap(&t.bp, src, esz, t.K, ctx->P, t.bnp))
-        return fail(ctx, NC_ECUDA, "tensor map encoding failed");
-    }
+    t.bn_dec = chosen[q];
+    for (int k = 0; k < kPfBuckets; ++k) t.bn_pf[k] = ctx->P > 0 ? chosen_p[k][q] : chosen[q];
+    for (int bi = 0; bi < 4; ++bi)
+      if (!tc_encode_tmap(&t.b[bi], src, esz, t.K, R, 32 << bi)) return fail(ctx, NC_ECUDA, "tensor map encoding failed");
   }
   return NC_OK;
 }
@@ -892,14 +894,21 @@ static cudaError_t launch_model_tc(nc_ctx* ctx, const Batch& b, StepMarks& m) {
   cudaStream_t s = ctx->stream;
   const int kb = ctx->fmt == NC_BF16;
   auto gemm = [&](const TcMat& t, int epi, float* y, float* h, void* h16 = nullptr) {
-    const bool pf = b.pos != nullptr;               // prefill forward: P-row operand map
+    // the batch tile tuned for this many rows: a decode step's, or the
+    // smallest prefill bucket that holds the forward's rows
+    int bn = t.bn_dec;
+    if (b.pos) {
+      int k = 0;
+      while (k + 1 < kPfBuckets && (ctx->P >> (k + 1)) >= b.Bmax) ++k;
+      bn = t.bn_pf[k];
+    }
     TcGemm g{};
     g.tmap_a = &t.a;
-    g.tmap_b = pf ? &t.bp : &t.b;
+    g.tmap_b = &t.b[bn_index(bn)];
     g.M = t.M;
     g.K = t.K;
     g.Bmax = b.Bmax;
-    g.bn = pf ? t.bnp : t.bn;
+    g.bn = bn;
     g.zrows = b.z_out;
     g.kind_bf16 = kb;
     g.nB = b.nB;
@@ -1897,7 +1906,7 @@ extern "C" int nc_gemm_tc(const void* W, const void* X, const float* w_scale, co
   const int esz = fp8 ? 1 : 2;
   if ((K * esz) % 16 || (reinterpret_cast<uintptr_t>(W) | reinterpret_cast<uintptr_t>(X)) % 16) return NC_EINVAL;
   TcMat t;
-  if (!tc_encode_tmap(&t.a, W, esz, K, M, 128) || !tc_encode_tmap(&t.b, X, esz, K, N, bn)) return NC_EINVAL;
+  if (!tc_encode_tmap(&t.a, W, esz, K, M, 128) || !tc_encode_tmap(&t.b[0], X, esz, K, N, bn)) return NC_EINVAL;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   int32_t* dev = nullptr;
   if (dev_malloc(&dev, 8) != cudaSuccess) return NC_ENOMEM;
@@ -1906,7 +1915,7 @@ extern "C" int nc_gemm_tc(const void* W, const void* X, const float* w_scale, co
   int32_t back[2] = {0, 0};
   TcGemm g{};
   g.tmap_a = &t.a;
-  g.tmap_b = &t.b;
+  g.tmap_b = &t.b[0];
   g.M = M;
   g.K = K;
   g.Bmax = N;
