@@ -76,8 +76,9 @@ __device__ __forceinline__ void epi_store(const TcGemm& g, int r, int n, int B, 
 }
 
 // The residual epilogue reads the first kPreCols columns' residuals of its
-// row into registers while the products run.
-constexpr int kPreCols = 32;
+// row into registers while the products run; the rest, 16 columns at a
+// time, one group ahead of the group it stores.
+constexpr int kPreCols = 64;
 
 template <int BN, int STAGES, int KIND_BF16, int EPI>
 __global__ void __launch_bounds__(kTcThreads, 1)
@@ -228,24 +229,34 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         epi_store<EPI>(g, r, n, B, v[i], pre[c0 + i]);
       }
     }
+    // the remaining columns: the loads of group c + 16 (row scales,
+    // residuals) are issued before group c is stored
+    float xs[16], res[16];
+    auto load_group = [&](int c) {
+#pragma unroll
+      for (int i = 0; i < 16; ++i) {
+        const int n = n0 + c + i;
+        const bool in = c < c_ep + BN / 2 && n < B;
+        xs[i] = (!KIND_BF16 && in) ? __ldg(g.x_scale + n) : 0.f;
+        res[i] = (EPI == EPI_RESID && in && r < g.M) ? __ldcg(g.y + (size_t)n * g.M + r) : 0.f;
+      }
+    };
+    if (kPre < BN / 2) load_group(c_ep + kPre);
 #pragma unroll 1
     for (int c = c_ep + kPre; c < c_ep + BN / 2; c += 16) {
-      float v[16];
-      tmem_ld16(tw + (uint32_t)c, v);
-      // loads of this 16-column group first (row scales, residuals), so
-      // they are in flight together
-      float xs[16], res[16];
+      float v[16], xc[16], rc[16];
 #pragma unroll
       for (int i = 0; i < 16; ++i) {
-        const int n = n0 + c + i;
-        xs[i] = (!KIND_BF16 && n < B) ? __ldg(g.x_scale + n) : 0.f;
-        res[i] = (EPI == EPI_RESID && n < B && r < g.M) ? __ldcg(g.y + (size_t)n * g.M + r) : 0.f;
+        xc[i] = xs[i];
+        rc[i] = res[i];
       }
+      load_group(c + 16);
+      tmem_ld16(tw + (uint32_t)c, v);
 #pragma unroll
       for (int i = 0; i < 16; ++i) {
         const int n = n0 + c + i;
-        if (!KIND_BF16) v[i] *= ws * xs[i];
-        epi_store<EPI>(g, r, n, B, v[i], res[i]);
+        if (!KIND_BF16) v[i] *= ws * xc[i];
+        epi_store<EPI>(g, r, n, B, v[i], rc[i]);
       }
     }
   }

@@ -113,3 +113,24 @@ def test_mixed_nll_gradient_fd_and_reduction():
     g_paper[t] -= 1
     np.testing.assert_allclose(gb, g_paper, rtol=1e-12, atol=1e-15)
     assert np.allclose(gth, 0, atol=1e-300)
+
+
+def test_temperature_softmax_power_identity_and_limits():
+    """p_llm at temperature tau (Sec. 3.2) against facts that do not restate
+    its formula: softmax(z / tau) is the tau-th root power of softmax(z),
+    renormalised; tau = 1 is the plain softmax; tau -> 0 tends to the one-hot
+    argmax and large tau to the uniform distribution; the order of the
+    probabilities never changes."""
+    rng = np.random.default_rng(3)
+    z = rng.normal(0, 2, 500)
+    e = np.exp(z - z.max())
+    p1 = e / e.sum()
+    assert np.allclose(p_llm(z, 1.0), p1, rtol=1e-13, atol=0)
+    for tau in (0.7, 0.8, 1.3, 2.5):
+        q = p1 ** (1.0 / tau)
+        assert np.allclose(p_llm(z, tau), q / q.sum(), rtol=1e-10, atol=1e-300)
+        assert np.array_equal(np.argsort(p_llm(z, tau), kind="stable"), np.argsort(p1, kind="stable"))
+    cold = p_llm(z, 1e-3)
+    assert abs(cold[np.argmax(z)] - 1.0) < 1e-12
+    hot = p_llm(z, 1e6)
+    assert np.max(np.abs(hot * len(z) - 1.0)) < 1e-4
