@@ -48,20 +48,29 @@ __host__ __device__ constexpr size_t tc_smem_bytes() {
   return 1024 /* alignment slack */ + (size_t)STAGES * (kTileM + BN) * kKBlockBytes + 256;
 }
 
-// One output element (row r of the weights, batch row n) through the fused
-// epilogue; y already carries the FP8 scales.
+// SwiGLU of two adjacent batch columns n, n + 1: rows 2j (gate) and 2j + 1
+// (up) sit on adjacent lanes; the even lane computes h_j of column n, the odd
+// lane h_j of column n + 1, each from one exchanged value; y0, y1 already
+// carry the FP8 scales.
+__device__ __forceinline__ void swiglu_pair(const TcGemm& g, int r, int n, int B, float y0, float y1) {
+  const bool odd = r & 1;
+  const float got = __shfl_xor_sync(0xffffffffu, odd ? y0 : y1, 1);
+  const float gate = odd ? got : y0, up = odd ? y1 : got;
+  const int col = n + (odd ? 1 : 0);
+  if (col < B && r < g.M) {
+    const float h = silu_tc(gate) * up;
+    if (g.h16)
+      static_cast<__nv_bfloat16*>(g.h16)[(size_t)col * (g.M / 2) + (r >> 1)] = __float2bfloat16_rn(h);
+    else
+      g.h_out[(size_t)col * (g.M / 2) + (r >> 1)] = h;
+  }
+}
+
+// One output element (row r of the weights, batch row n) through the store,
+// residual or logits epilogue; y already carries the FP8 scales.
 template <int EPI>
 __device__ __forceinline__ void epi_store(const TcGemm& g, int r, int n, int B, float y, float res) {
-  if (EPI == EPI_SWIGLU) {
-    const float up = __shfl_xor_sync(0xffffffffu, y, 1);   // rows 2j (gate), 2j + 1 (up) on adjacent lanes
-    if (n < B && r < g.M && (r & 1) == 0) {
-      const float h = silu_tc(y) * up;
-      if (g.h16)
-        static_cast<__nv_bfloat16*>(g.h16)[(size_t)n * (g.M / 2) + (r >> 1)] = __float2bfloat16_rn(h);
-      else
-        g.h_out[(size_t)n * (g.M / 2) + (r >> 1)] = h;
-    }
-  } else if (n < B && r < g.M) {
+  if (n < B && r < g.M) {
     if (EPI == EPI_STORE) {
       g.y[(size_t)n * g.M + r] = y;
     } else if (EPI == EPI_RESID) {
@@ -226,7 +235,11 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       for (int i = 0; i < 16; ++i) {
         const int n = n0 + c_ep + c0 + i;
         if (!KIND_BF16) v[i] *= ws * (n < B ? __ldg(g.x_scale + n) : 0.f);
-        epi_store<EPI>(g, r, n, B, v[i], pre[c0 + i]);
+        if (EPI != EPI_SWIGLU) epi_store<EPI>(g, r, n, B, v[i], pre[c0 + i]);
+      }
+      if (EPI == EPI_SWIGLU) {
+#pragma unroll
+        for (int i = 0; i < 16; i += 2) swiglu_pair(g, r, n0 + c_ep + c0 + i, B, v[i], v[i + 1]);
       }
     }
     // the remaining columns: the loads of group c + 16 (row scales,
@@ -256,7 +269,11 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       for (int i = 0; i < 16; ++i) {
         const int n = n0 + c + i;
         if (!KIND_BF16) v[i] *= ws * xc[i];
-        epi_store<EPI>(g, r, n, B, v[i], rc[i]);
+        if (EPI != EPI_SWIGLU) epi_store<EPI>(g, r, n, B, v[i], rc[i]);
+      }
+      if (EPI == EPI_SWIGLU) {
+#pragma unroll
+        for (int i = 0; i < 16; i += 2) swiglu_pair(g, r, n0 + c + i, B, v[i], v[i + 1]);
       }
     }
   }
@@ -301,8 +318,8 @@ cudaError_t prepare_tc_t() {
 
 template <int KB, int EPI>
 cudaError_t prepare_tc_epi() {
-  cudaError_t e = prepare_tc_t<32, 6, KB, EPI>();
-  if (e == cudaSuccess) e = prepare_tc_t<64, 6, KB, EPI>();
+  cudaError_t e = prepare_tc_t<32, 10, KB, EPI>();
+  if (e == cudaSuccess) e = prepare_tc_t<64, 8, KB, EPI>();
   if (e == cudaSuccess) e = prepare_tc_t<128, 6, KB, EPI>();
   if (e == cudaSuccess) e = prepare_tc_t<256, 4, KB, EPI>();
   return e;
@@ -321,8 +338,8 @@ cudaError_t launch_tc_t(const TcGemm& g, cudaStream_t s, bool pdl) {
 template <int KB, int EPI>
 cudaError_t launch_tc_epi(const TcGemm& g, cudaStream_t s, bool pdl) {
   switch (g.bn) {
-    case 32: return launch_tc_t<32, 6, KB, EPI>(g, s, pdl);
-    case 64: return launch_tc_t<64, 6, KB, EPI>(g, s, pdl);
+    case 32: return launch_tc_t<32, 10, KB, EPI>(g, s, pdl);
+    case 64: return launch_tc_t<64, 8, KB, EPI>(g, s, pdl);
     case 128: return launch_tc_t<128, 6, KB, EPI>(g, s, pdl);
     case 256: return launch_tc_t<256, 4, KB, EPI>(g, s, pdl);
   }
