@@ -331,7 +331,7 @@ def ncu_traffic(kind: str, workload: str):
     path = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
     if not os.path.exists(path):
         return None
-    h = kernel_sources_hash()
+    h = kernel_sources_hash(kind)
     with open(path) as fh:
         for line in fh:
             f = line.split()
@@ -340,15 +340,28 @@ def ncu_traffic(kind: str, workload: str):
     return None
 
 
-def kernel_sources_hash() -> str:
-    """Hash of the device code (the kernel files and the headers they
-    include); host-only orchestration and the host coder are left out."""
+# The device sources each traced kernel kind is built from; a kind not listed
+# is keyed by every device source.
+KIND_SOURCES = {
+    "attn": ("k_attn_t5.cu", "model_dev.cuh", "tc5.cuh", "internal.h"),
+    "vocab": ("k_vocab.cu", "internal.h"),
+    "ngram_update": ("k_vocab.cu", "internal.h"),
+}
+
+
+def kernel_sources_hash(kind: str = "") -> str:
+    """Hash of the device code a kernel kind is built from (its kernel file
+    and the headers it includes; every kernel file and header for other
+    kinds); host-only orchestration and the host coder are left out."""
     d = os.path.join(ROOT, "paper_2602_19626_gb300", "csrc")
+    names = KIND_SOURCES.get(kind)
+    if names is None:
+        names = [n for n in os.listdir(d)
+                 if (n.startswith("k_") and n.endswith(".cu")) or n.endswith(".cuh") or n == "internal.h"]
     m = hashlib.sha256()
-    for name in sorted(os.listdir(d)):
-        if (name.startswith("k_") and name.endswith(".cu")) or name.endswith(".cuh") or name == "internal.h":
-            with open(os.path.join(d, name), "rb") as fh:
-                m.update(fh.read())
+    for name in sorted(names):
+        with open(os.path.join(d, name), "rb") as fh:
+            m.update(fh.read())
     return m.hexdigest()[:12]
 
 

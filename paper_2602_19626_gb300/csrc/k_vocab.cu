@@ -341,6 +341,7 @@ struct StepSlot {
 };
 
 constexpr int kSnapBufs = 3;   // N-gram states in flight in the prefill loop
+constexpr int kSeqMax = 1024;  // positions of one prefill chunk at most (a power of two dividing C < L <= 2,048)
 struct StepShared {
   StepSlot slot[2];
   NgSnap ng[kSnapBufs];
@@ -926,11 +927,16 @@ __global__ void __launch_bounds__(step_threads<CL>(), 1)
                 const int32_t* obs_step, const NgSnap* snap) {
   extern __shared__ float4 dyn4[];
   __shared__ StepShared sh;
+  __shared__ int32_t s_obs[kSeqMax], s_nb[kSeqMax];   // the chunk's tokens and active rows, per position
   cg::cluster_group cl = cg::this_cluster();
   const int j = blockIdx.x / CL;
   pdl_wait();
   pdl_trigger();
   if (m < 1 || j >= nb_step[0]) return;          // uniform across the cluster
+  for (int i = threadIdx.x; i < m; i += blockDim.x) {
+    s_obs[i] = obs_step[(size_t)i * n_streams + j];
+    s_nb[i] = nb_step[i];
+  }
   const Lanes L = lanes_of<E, CL>((int)cl.block_rank());
   StreamDev& st = b.st[b.slots[j]];
   const int V = D.V;
@@ -942,7 +948,6 @@ __global__ void __launch_bounds__(step_threads<CL>(), 1)
   float* spw = reinterpret_cast<float*>(dyn4) + L.w * 32 * E;
   const float* zj = zrows + (size_t)b.z_idx[j] * V;
   const NgSnap* gj = ngram ? snap + b.z_idx[j] : nullptr;
-  const int32_t* obs_j = obs_step + j;
 
   float bias[E], z[E];
   int cnt[E];
@@ -952,8 +957,9 @@ __global__ void __launch_bounds__(step_threads<CL>(), 1)
 #pragma unroll
     for (int i = 0; i < E; ++i) bias[i] = 0.f;
   }
-  bool act1 = 1 < m && j < nb_step[1];           // positions r + 1 and r + 2 exist
-  bool act2 = act1 && 2 < m && j < nb_step[2];
+  __syncthreads();                               // the tokens and active rows are in shared memory
+  bool act1 = 1 < m && j < s_nb[1];              // positions r + 1 and r + 2 exist
+  bool act2 = act1 && 2 < m && j < s_nb[2];
   if (ngram) {
     load_counts<E>(st.uni, L.v0, V, cnt);
     zero_region<E>(spw, L.lane);
@@ -965,7 +971,7 @@ __global__ void __launch_bounds__(step_threads<CL>(), 1)
     for (int i = 0; i < E; ++i) cnt[i] = 0;
   }
   load_runf<E, FULL>(zj, L.v0, V, z, -INFINITY);
-  int t = obs_j[0];
+  int t = s_obs[0];
   float th0 = st.theta[0], th1 = st.theta[1];
   const int n0 = st.n_coded;
   if (ngram) cp_async_wait_all();
@@ -1042,8 +1048,8 @@ __global__ void __launch_bounds__(step_threads<CL>(), 1)
     bool act3 = false;
     if (more) {
       load_runf<E, FULL>(zj + (size_t)(r + 1) * V, L.v0, V, z, -INFINITY);
-      t_n = obs_j[(size_t)(r + 1) * n_streams];
-      act3 = act2 && r + 3 < m && j < nb_step[r + 3];
+      t_n = s_obs[r + 1];
+      act3 = act2 && r + 3 < m && j < s_nb[r + 3];
       if (ngram) ngram_scatter<E>(sh.ng[(r + 1) % kSnapBufs], spw, L);
     }
     cluster_wait();
@@ -1633,6 +1639,7 @@ static cudaError_t vocab_seq_tfc(const Dims& D, const Batch& b, const VocabIO& i
                                  const int32_t* nb_step, const int32_t* obs_step, const NgSnap* snap,
                                  cudaStream_t s) {
   const size_t smem = (size_t)step_threads<CL>() * E * sizeof(float);
+  if (m > kSeqMax) return cudaErrorInvalidValue;
   return launch_kernel_cluster(&k_vocab_seq<E, FULL, CL>, dim3(b.Bmax * CL), dim3(step_threads<CL>()), smem, s,
                                D.pdl, CL, D, b, io, m, b.Bmax, zrows, nb_step, obs_step, snap);
 }
