@@ -52,10 +52,22 @@ struct TcMat {
   CUtensorMap a;
   CUtensorMap b[4];
   int M = 0, K = 0;
+  int kp = 1;                        // 2: 3D maps, two K blocks per pipeline stage (TcGemm::kp)
   int bn_dec = 0, bn_pf[kPfBuckets] = {};
   const float* scale = nullptr;
 };
 static int bn_index(int bn) { return bn == 32 ? 0 : bn == 64 ? 1 : bn == 128 ? 2 : 3; }
+
+// The weights' map (box of 128 rows) and its stage shape: BF16 with K a
+// multiple of 64 takes 3D maps and two K blocks per stage.
+static bool tc_encode_weights(TcMat& t, const void* w, int esz) {
+  t.kp = (esz == 2 && t.K % 64 == 0) ? 2 : 1;
+  return t.kp == 2 ? tc_encode_tmap3(&t.a, w, esz, t.K, t.M, 128) : tc_encode_tmap(&t.a, w, esz, t.K, t.M, 128);
+}
+// An operand map of `rows` rows with a box of bn rows, in the weights' shape.
+static bool tc_encode_operand(const TcMat& t, CUtensorMap* m, const void* x, int esz, int rows, int bn) {
+  return t.kp == 2 ? tc_encode_tmap3(m, x, esz, t.K, rows, bn) : tc_encode_tmap(m, x, esz, t.K, rows, bn);
+}
 
 }  // namespace
 
@@ -355,7 +367,7 @@ static int tc_setup(nc_ctx* ctx) {
     t.M = m.rows;
     t.K = m.cols;
     t.scale = m.scale;
-    if (!tc_encode_tmap(&t.a, m.w, esz, m.cols, m.rows, 128)) return false;
+    if (!tc_encode_weights(t, m.w, esz)) return false;
     ctx->tc.push_back(t);
     return true;
   };
@@ -386,7 +398,7 @@ static int tc_setup(nc_ctx* ctx) {
       chosen[q] = cands[0];
       for (int ci = 0; ci < nc; ++ci) {
         TcMat tt = t;
-        if (!tc_encode_tmap(&tt.b[0], ctx->opnd, esz, t.K, rows, cands[ci]))
+        if (!tc_encode_operand(tt, &tt.b[0], ctx->opnd, esz, rows, cands[ci]))
           return fail(ctx, NC_ECUDA, "tensor map encoding failed");
         TcGemm g{};
         g.tmap_a = &tt.a;
@@ -395,6 +407,7 @@ static int tc_setup(nc_ctx* ctx) {
         g.K = t.K;
         g.Bmax = rows;
         g.bn = cands[ci];
+        g.kp = tt.kp;
         g.kind_bf16 = kb;
         g.nB = nB;
         g.w_scale = t.scale;
@@ -442,7 +455,7 @@ static int tc_setup(nc_ctx* ctx) {
     t.bn_dec = chosen[q];
     for (int k = 0; k < kPfBuckets; ++k) t.bn_pf[k] = ctx->P > 0 ? chosen_p[k][q] : chosen[q];
     for (int bi = 0; bi < 4; ++bi)
-      if (!tc_encode_tmap(&t.b[bi], src, esz, t.K, R, 32 << bi)) return fail(ctx, NC_ECUDA, "tensor map encoding failed");
+      if (!tc_encode_operand(t, &t.b[bi], src, esz, R, 32 << bi)) return fail(ctx, NC_ECUDA, "tensor map encoding failed");
   }
   return NC_OK;
 }
@@ -909,6 +922,7 @@ static cudaError_t launch_model_tc(nc_ctx* ctx, const Batch& b, StepMarks& m) {
     g.K = t.K;
     g.Bmax = b.Bmax;
     g.bn = bn;
+    g.kp = t.kp;
     g.zrows = b.z_out;
     g.kind_bf16 = kb;
     g.nB = b.nB;
@@ -1906,7 +1920,9 @@ extern "C" int nc_gemm_tc(const void* W, const void* X, const float* w_scale, co
   const int esz = fp8 ? 1 : 2;
   if ((K * esz) % 16 || (reinterpret_cast<uintptr_t>(W) | reinterpret_cast<uintptr_t>(X)) % 16) return NC_EINVAL;
   TcMat t;
-  if (!tc_encode_tmap(&t.a, W, esz, K, M, 128) || !tc_encode_tmap(&t.b[0], X, esz, K, N, bn)) return NC_EINVAL;
+  t.M = M;
+  t.K = K;
+  if (!tc_encode_weights(t, W, esz) || !tc_encode_operand(t, &t.b[0], X, esz, N, bn)) return NC_EINVAL;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   int32_t* dev = nullptr;
   if (dev_malloc(&dev, 8) != cudaSuccess) return NC_ENOMEM;
@@ -1920,6 +1936,7 @@ extern "C" int nc_gemm_tc(const void* W, const void* X, const float* w_scale, co
   g.K = K;
   g.Bmax = N;
   g.bn = bn;
+  g.kp = t.kp;
   g.kind_bf16 = !fp8;
   g.nB = dev;
   g.w_scale = w_scale;

@@ -304,6 +304,8 @@ struct TcGemm {
   const void* tmap_a;       // host copy of the weights' CUtensorMap (box 128 rows)
   const void* tmap_b;       // host copy of the operand's CUtensorMap (box bn rows)
   int M, K, Bmax, bn, kind_bf16;
+  int kp;                   // 2: both maps 3D ([K blocks][rows][128 B], tc_encode_tmap3), two K blocks
+                            // per stage (BF16, K a multiple of 64); otherwise 2D maps, one per stage
   const int32_t* nB;
   const float* w_scale;     // FP8: [M]
   const float* x_scale;     // FP8: [Bmax]
@@ -316,6 +318,7 @@ struct TcGemm {
   int32_t* status;          // error word (ST_TIMEOUT)
 };
 bool tc_encode_tmap(void* tmap, const void* base, int elem_bytes, int64_t inner, int64_t outer, int box_outer);
+bool tc_encode_tmap3(void* tmap, const void* base, int elem_bytes, int64_t K, int64_t rows, int box_rows);
 cudaError_t launch_gemm_tc(const TcGemm& g, int epi, cudaStream_t s, bool pdl);
 // One bounded mbarrier wait on a barrier nothing arrives on (at most `polls`
 // polls), recording ST_TIMEOUT in *status when it gives up.

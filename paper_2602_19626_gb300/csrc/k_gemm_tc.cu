@@ -43,9 +43,9 @@ __host__ __device__ constexpr uint32_t tmem_cols() {
   return BN <= 32 ? 32 : BN <= 64 ? 64 : BN <= 128 ? 128 : 256;
 }
 
-template <int BN, int STAGES>
+template <int BN, int STAGES, int KP>
 __host__ __device__ constexpr size_t tc_smem_bytes() {
-  return 1024 /* alignment slack */ + (size_t)STAGES * (kTileM + BN) * kKBlockBytes + 256;
+  return 1024 /* alignment slack */ + (size_t)STAGES * KP * (kTileM + BN) * kKBlockBytes + 256;
 }
 
 // SwiGLU of two adjacent batch columns n, n + 1: rows 2j (gate) and 2j + 1
@@ -89,28 +89,43 @@ __device__ __forceinline__ void epi_store(const TcGemm& g, int r, int n, int B, 
 // time, one group ahead of the group it stores.
 constexpr int kPreCols = 64;
 
-template <int BN, int STAGES, int KIND_BF16, int EPI>
+// KP: K blocks per pipeline stage.  KP = 2 takes both operands' two K blocks
+// in one 3D TMA box each (maps [K blocks][rows][128 bytes], K a multiple of
+// the block), halving the copies; the products and their order are those of
+// KP = 1.
+template <int BN, int STAGES, int KIND_BF16, int EPI, int KP>
 __global__ void __launch_bounds__(kTcThreads, 1)
     k_gemm_tc(const __grid_constant__ CUtensorMap tA, const __grid_constant__ CUtensorMap tB, TcGemm g) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+  constexpr size_t kStageA = (size_t)KP * kTileM * kKBlockBytes, kStageB = (size_t)KP * BN * kKBlockBytes;
   uint8_t* sA = base;
-  uint8_t* sB = base + (size_t)STAGES * kTileM * kKBlockBytes;
-  uint64_t* full = reinterpret_cast<uint64_t*>(sB + (size_t)STAGES * BN * kKBlockBytes);
+  uint8_t* sB = base + STAGES * kStageA;
+  uint64_t* full = reinterpret_cast<uint64_t*>(sB + STAGES * kStageB);
   uint64_t* empty = full + STAGES;
   uint64_t* done = empty + STAGES;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
   uint32_t* fail = tmem_slot + 1;
-  int32_t* n_issued = reinterpret_cast<int32_t*>(fail + 1);     // K blocks whose TMA loads were issued
-  int32_t* n_consumed = n_issued + 1;                          // K blocks the MMA issuer saw land
+  int32_t* n_issued = reinterpret_cast<int32_t*>(fail + 1);     // stages whose TMA loads were issued
+  int32_t* n_consumed = n_issued + 1;                          // stages the MMA issuer saw land
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int m0 = blockIdx.x * kTileM;
   const int n0 = blockIdx.y * BN;
   const int kblk = KIND_BF16 ? 64 : 128;             // elements per 128-byte K block
   const int nk = (g.K + kblk - 1) / kblk;            // the tail block reads zeros past K
+  const int ns = (nk + KP - 1) / KP;                 // stages
   constexpr uint32_t kCols = tmem_cols<BN>();
-  constexpr uint32_t kStageBytes = (kTileM + BN) * kKBlockBytes;
+  constexpr uint32_t kStageBytes = (uint32_t)(kStageA + kStageB);
+  // stage ks's loads: K block ks of a 2D map, or K blocks KP ks .. of a 3D map
+  auto load_a = [&](int ks, int s) {
+    if (KP == 1) tma_load_2d(sA + s * kStageA, &tA, full + s, ks * kblk, m0);
+    else tma_load_3d(sA + s * kStageA, &tA, full + s, 0, m0, KP * ks);
+  };
+  auto load_b = [&](int ks, int s) {
+    if (KP == 1) tma_load_2d(sB + s * kStageB, &tB, full + s, ks * kblk, n0);
+    else tma_load_3d(sB + s * kStageB, &tB, full + s, 0, n0, KP * ks);
+  };
 
   // the row count was written by the step's prepare kernel, several launches
   // back, so it may be read before the wait on the previous kernel
@@ -141,9 +156,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   // weight tiles of the first stages do not depend on the previous kernel:
   // in flight before waiting on it; the operand tiles only after
   if (threadIdx.x == 0) {
-    for (int kb = 0; kb < nk && kb < STAGES; ++kb) {
-      mbar_expect_tx(full + kb, kStageBytes);
-      tma_load_2d(sA + (size_t)kb * kTileM * kKBlockBytes, &tA, full + kb, kb * kblk, m0);
+    for (int ks = 0; ks < ns && ks < STAGES; ++ks) {
+      mbar_expect_tx(full + ks, kStageBytes);
+      load_a(ks, ks);
     }
   }
   pdl_wait();
@@ -163,42 +178,46 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 
   if (active && threadIdx.x == 0) {
     // TMA producer
-    int kb = 0;
-    for (; kb < nk; ++kb) {
-      const int s = kb % STAGES;
-      const uint32_t ph = (uint32_t)(kb / STAGES) & 1u;
-      const int kc = kb * kblk;
-      if (kb >= STAGES) {
+    int ks = 0;
+    for (; ks < ns; ++ks) {
+      const int s = ks % STAGES;
+      const uint32_t ph = (uint32_t)(ks / STAGES) & 1u;
+      if (ks >= STAGES) {
         if (!mbar_wait(empty + s, ph ^ 1u)) {
           atomicOr(fail, 1u);
           break;
         }
         mbar_expect_tx(full + s, kStageBytes);
-        tma_load_2d(sA + (size_t)s * kTileM * kKBlockBytes, &tA, full + s, kc, m0);
+        load_a(ks, s);
       }
-      tma_load_2d(sB + (size_t)s * BN * kKBlockBytes, &tB, full + s, kc, n0);
+      load_b(ks, s);
     }
     // the first STAGES weight loads went out before the loop in any case
-    *n_issued = max(kb, min(nk, STAGES));
+    *n_issued = max(ks, min(ns, STAGES));
   } else if (active && threadIdx.x == 32) {
     // MMA issuer: 4 instructions of 32 bytes of K per 128-byte block
     const uint32_t id = idesc(KIND_BF16, kTileM, BN);
     bool ok = true;
-    for (int kb = 0; kb < nk && ok; ++kb) {
-      const int s = kb % STAGES;
-      const uint32_t ph = (uint32_t)(kb / STAGES) & 1u;
+    for (int ks = 0; ks < ns && ok; ++ks) {
+      const int s = ks % STAGES;
+      const uint32_t ph = (uint32_t)(ks / STAGES) & 1u;
       if (!mbar_wait(full + s, ph)) {
         atomicOr(fail, 2u);
         ok = false;
         break;
       }
-      *n_consumed = kb + 1;
+      *n_consumed = ks + 1;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const uint32_t a0 = smem_u32(sA + (size_t)s * kTileM * kKBlockBytes);
-      const uint32_t b0 = smem_u32(sB + (size_t)s * BN * kKBlockBytes);
 #pragma unroll
-      for (int k = 0; k < 4; ++k)
-        mma_issue(KIND_BF16, tmem, sdesc_sw128(a0 + 32 * k), sdesc_sw128(b0 + 32 * k), id, (kb | k) ? 1u : 0u);
+      for (int kk = 0; kk < KP; ++kk) {
+        const int kb = KP * ks + kk;
+        if (kb >= nk) break;                       // a 3D box's block past K: zeros, not multiplied
+        const uint32_t a0 = smem_u32(sA + s * kStageA + (size_t)kk * kTileM * kKBlockBytes);
+        const uint32_t b0 = smem_u32(sB + s * kStageB + (size_t)kk * BN * kKBlockBytes);
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+          mma_issue(KIND_BF16, tmem, sdesc_sw128(a0 + 32 * k), sdesc_sw128(b0 + 32 * k), id, (kb | k) ? 1u : 0u);
+      }
       mma_commit(empty + s);
     }
     mma_commit(done);
@@ -310,25 +329,31 @@ EncodeTiled encode_fn() {
   return fn;
 }
 
-template <int BN, int STAGES, int KB, int EPI>
+template <int BN, int STAGES, int KB, int EPI, int KP>
 cudaError_t prepare_tc_t() {
-  return cudaFuncSetAttribute(k_gemm_tc<BN, STAGES, KB, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)tc_smem_bytes<BN, STAGES>());
+  return cudaFuncSetAttribute(k_gemm_tc<BN, STAGES, KB, EPI, KP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)tc_smem_bytes<BN, STAGES, KP>());
 }
 
 template <int KB, int EPI>
 cudaError_t prepare_tc_epi() {
-  cudaError_t e = prepare_tc_t<32, 10, KB, EPI>();
-  if (e == cudaSuccess) e = prepare_tc_t<64, 8, KB, EPI>();
-  if (e == cudaSuccess) e = prepare_tc_t<128, 6, KB, EPI>();
-  if (e == cudaSuccess) e = prepare_tc_t<256, 4, KB, EPI>();
+  cudaError_t e = prepare_tc_t<32, 10, KB, EPI, 1>();
+  if (e == cudaSuccess) e = prepare_tc_t<64, 8, KB, EPI, 1>();
+  if (e == cudaSuccess) e = prepare_tc_t<128, 6, KB, EPI, 1>();
+  if (e == cudaSuccess) e = prepare_tc_t<256, 4, KB, EPI, 1>();
+  if (KB) {
+    if (e == cudaSuccess) e = prepare_tc_t<32, 5, KB, EPI, 2>();
+    if (e == cudaSuccess) e = prepare_tc_t<64, 4, KB, EPI, 2>();
+    if (e == cudaSuccess) e = prepare_tc_t<128, 3, KB, EPI, 2>();
+    if (e == cudaSuccess) e = prepare_tc_t<256, 2, KB, EPI, 2>();
+  }
   return e;
 }
 
-template <int BN, int STAGES, int KB, int EPI>
+template <int BN, int STAGES, int KB, int EPI, int KP>
 cudaError_t launch_tc_t(const TcGemm& g, cudaStream_t s, bool pdl) {
-  constexpr size_t smem = tc_smem_bytes<BN, STAGES>();
-  auto kern = k_gemm_tc<BN, STAGES, KB, EPI>;
+  constexpr size_t smem = tc_smem_bytes<BN, STAGES, KP>();
+  auto kern = k_gemm_tc<BN, STAGES, KB, EPI, KP>;
   dim3 grid((g.M + kTileM - 1) / kTileM, (g.Bmax + BN - 1) / BN);
   const CUtensorMap* a = reinterpret_cast<const CUtensorMap*>(g.tmap_a);
   const CUtensorMap* b = reinterpret_cast<const CUtensorMap*>(g.tmap_b);
@@ -337,11 +362,21 @@ cudaError_t launch_tc_t(const TcGemm& g, cudaStream_t s, bool pdl) {
 
 template <int KB, int EPI>
 cudaError_t launch_tc_epi(const TcGemm& g, cudaStream_t s, bool pdl) {
+  if (KB && g.kp == 2 && g.K % 64 == 0) {
+    switch (g.bn) {
+      case 32: return launch_tc_t<32, 5, KB, EPI, 2>(g, s, pdl);
+      case 64: return launch_tc_t<64, 4, KB, EPI, 2>(g, s, pdl);
+      case 128: return launch_tc_t<128, 3, KB, EPI, 2>(g, s, pdl);
+      case 256: return launch_tc_t<256, 2, KB, EPI, 2>(g, s, pdl);
+    }
+    return cudaErrorInvalidValue;
+  }
+  if (g.kp == 2) return cudaErrorInvalidValue;
   switch (g.bn) {
-    case 32: return launch_tc_t<32, 10, KB, EPI>(g, s, pdl);
-    case 64: return launch_tc_t<64, 8, KB, EPI>(g, s, pdl);
-    case 128: return launch_tc_t<128, 6, KB, EPI>(g, s, pdl);
-    case 256: return launch_tc_t<256, 4, KB, EPI>(g, s, pdl);
+    case 32: return launch_tc_t<32, 10, KB, EPI, 1>(g, s, pdl);
+    case 64: return launch_tc_t<64, 8, KB, EPI, 1>(g, s, pdl);
+    case 128: return launch_tc_t<128, 6, KB, EPI, 1>(g, s, pdl);
+    case 256: return launch_tc_t<256, 4, KB, EPI, 1>(g, s, pdl);
   }
   return cudaErrorInvalidValue;
 }
@@ -446,6 +481,21 @@ cudaError_t launch_act_plain(const Dims& D, const Batch& b, const float* x, int 
                              float* out_scale, cudaStream_t s) {
   return launch_kernel(kind_bf16 ? k_act_plain<1> : k_act_plain<0>, dim3(b.Bmax), dim3(256), 0, s, D.pdl, D, b, x,
                        cols, out, out_scale);
+}
+
+bool tc_encode_tmap3(void* tmap, const void* base, int elem_bytes, int64_t K, int64_t rows, int box_rows) {
+  // [K / kblk][rows][kblk]: element (j, r, i) at base + r K + j kblk + i
+  EncodeTiled fn = encode_fn();
+  const int64_t kblk = kKBlockBytes / elem_bytes;
+  if (!fn || K % kblk) return false;
+  cuuint64_t dims[3] = {(cuuint64_t)kblk, (cuuint64_t)rows, (cuuint64_t)(K / kblk)};
+  cuuint64_t strides[2] = {(cuuint64_t)(K * elem_bytes), (cuuint64_t)kKBlockBytes};
+  cuuint32_t box[3] = {(cuuint32_t)kblk, (cuuint32_t)box_rows, 2};
+  cuuint32_t es[3] = {1, 1, 1};
+  const CUtensorMapDataType dt = elem_bytes == 2 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_UINT8;
+  return fn(reinterpret_cast<CUtensorMap*>(tmap), dt, 3, const_cast<void*>(base), dims, strides, box, es,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 bool tc_encode_tmap(void* tmap, const void* base, int elem_bytes, int64_t inner, int64_t outer, int box_outer) {

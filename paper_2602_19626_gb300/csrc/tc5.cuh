@@ -62,6 +62,15 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const void* map, uint64_t
       : "memory");
 }
 
+// 3D tiled TMA load of the box at (c0, c1, c2).
+__device__ __forceinline__ void tma_load_3d(void* dst, const void* map, uint64_t* bar, int c0, int c1, int c2) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5}], [%2];" ::"r"(
+          smem_u32(dst)),
+      "l"(map), "r"(smem_u32(bar)), "r"(c0), "r"(c1), "r"(c2)
+      : "memory");
+}
+
 // Shared-memory matrix descriptor of a K-major operand tile in the 128-byte
 // swizzle layout: rows (M or N) of 128 bytes of K (64 BF16 / 128 E4M3), in
 // 8-row (1024-byte) swizzle atoms; `saddr` is the 1024-byte aligned atom plus
