@@ -44,13 +44,13 @@ struct Slot {
 };
 
 // One projection on the tensor-core path: tensor maps of the weights (box of
-// 128 rows) and of the batch operand (all its rows, one map per batch tile
-// bn = 32, 64, 128, 256), and the bn tuned for a decode step (max_streams
+// 128 rows) and of the batch operand of each forward buffer set (all its
+// rows, one map per batch tile bn = 32, 64, 128, 256), and the bn tuned for a decode step (max_streams
 // rows) and for prefill forwards of prefill_rows >> k rows, k < kPfBuckets.
 constexpr int kPfBuckets = 4;
 struct TcMat {
   CUtensorMap a;
-  CUtensorMap b[4];
+  CUtensorMap b[2][4];               // per forward buffer set
   int M = 0, K = 0;
   int kp = 1;                        // 2: 3D maps, two K blocks per pipeline stage (TcGemm::kp)
   int bn_dec = 0, bn_pf[kPfBuckets] = {};
@@ -117,6 +117,13 @@ struct nc_ctx {
   uint32_t* d_target = nullptr;
   uint32_t* d_lohi = nullptr;
   int32_t* d_status = nullptr;       // scratch status for building blocks
+  int64_t* d_meta = nullptr;         // [3 max_streams] an encoder call's row offsets, lengths, caller rows
+  // nc_encode's device tokens and intervals, kept (grown as needed) so that
+  // repeated calls reuse the same buffers and the captured pass
+  int32_t* enc_tok = nullptr;
+  size_t enc_tok_cap = 0;
+  uint32_t* enc_iv = nullptr;
+  size_t enc_iv_cap = 0;
   // pinned host staging
   int32_t* h_i32 = nullptr;          // 3 * max_streams + 1
   uint32_t* h_u32 = nullptr;         // 3 * max_streams: targets, then (lo, hi) pairs
@@ -128,6 +135,26 @@ struct nc_ctx {
   void* opnd2 = nullptr;             // BF16: [rows][F] the down projection's operand, written by the
                                      // gate/up epilogue while that GEMM still reads opnd
   float* opnd_scale = nullptr;       // [rows] E4M3 row scales
+
+  // The buffers one forward writes.  Set 0 is the fields above; with a
+  // second set (encoder prefill on the tensor-core path) chunk c + 1's
+  // forward runs on stream s2 beside chunk c's.
+  struct FwdSet {
+    float *x = nullptr, *qkv = nullptr, *attn_out = nullptr, *h = nullptr;
+    void *opnd = nullptr, *opnd2 = nullptr;
+    float* opnd_scale = nullptr;
+    void* q16 = nullptr;
+    float* attn_part = nullptr;
+    int32_t *f_slots = nullptr, *f_pos = nullptr, *f_tok = nullptr, *nB_fwd = nullptr;
+  } fs[2];
+  int n_fs = 1;
+  cudaStream_t s2 = nullptr;
+  std::vector<cudaEvent_t> ev_layer[2];     // [set][layer]: that set's chunk has finished layer l's attention
+  cudaEvent_t ev_prep[2] = {};              // [set]: that set's chunk has taken its first position
+  // the encoder's captured pass of every chunk (two forward sets), kept for
+  // the next call with the same chunk plan and buffers
+  std::vector<int64_t> pass_key;
+  cudaGraphExec_t pass_graph = nullptr;
 
   StreamDev* d_st = nullptr;
   std::vector<StreamDev> h_st;
@@ -323,9 +350,16 @@ extern "C" void nc_ctx_destroy(nc_ctx* ctx) {
   cudaFreeHost(ctx->h_i32);
   cudaFreeHost(ctx->h_u32);
   cudaFreeHost(ctx->h_status);
+  if (ctx->pass_graph) cudaGraphExecDestroy(ctx->pass_graph);
+  cudaFree(ctx->enc_tok);
+  cudaFree(ctx->enc_iv);
   for (cudaEvent_t e : {ctx->ev_fork, ctx->ev_join, ctx->ev_done, ctx->ev_fwd[0], ctx->ev_fwd[1], ctx->ev_voc[0],
-                        ctx->ev_voc[1]})
+                        ctx->ev_voc[1], ctx->ev_prep[0], ctx->ev_prep[1]})
     if (e) cudaEventDestroy(e);
+  for (auto& v : ctx->ev_layer)
+    for (cudaEvent_t e : v)
+      if (e) cudaEventDestroy(e);
+  if (ctx->s2) cudaStreamDestroy(ctx->s2);
   if (ctx->side) cudaStreamDestroy(ctx->side);
   if (ctx->vstream) cudaStreamDestroy(ctx->vstream);
   if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
@@ -361,6 +395,43 @@ static int tc_setup(nc_ctx* ctx) {
   if (kb) {
     if (dalloc(ctx, &ctx->opnd2, (size_t)R * D.F * 2)) return fail(ctx, NC_ENOMEM, "tensor-core operand allocation");
     NC_TRY(cudaMemset(ctx->opnd2, 0, (size_t)R * D.F * 2));
+  }
+  // forward buffer sets: set 0 is the context's own; an encoder prefill over
+  // a BF16 cache gets a second one (P rows), its stream and its events
+  nc_ctx::FwdSet& f0 = ctx->fs[0];
+  f0.x = ctx->x;
+  f0.qkv = ctx->qkv;
+  f0.attn_out = ctx->attn_out;
+  f0.h = ctx->h;
+  f0.opnd = ctx->opnd;
+  f0.opnd2 = ctx->opnd2;
+  f0.opnd_scale = ctx->opnd_scale;
+  f0.q16 = D.q16;
+  f0.attn_part = D.attn_part;
+  f0.f_slots = ctx->f_slots;
+  f0.f_pos = ctx->f_pos;
+  f0.f_tok = ctx->f_tok;
+  f0.nB_fwd = ctx->d_nB_fwd;
+  if (ctx->P > 0 && D.kv_bf16) {
+    nc_ctx::FwdSet& f1 = ctx->fs[1];
+    const size_t P = ctx->P;
+    if (dalloc(ctx, &f1.x, P * D.d * 4) || dalloc(ctx, &f1.qkv, P * D.qkv_rows * 4) ||
+        dalloc(ctx, &f1.attn_out, P * D.hq * kHeadDim * 4) || dalloc(ctx, &f1.h, P * D.F * 4) ||
+        dalloc(ctx, &f1.opnd, P * Kmax * esz) || dalloc(ctx, &f1.opnd_scale, P * 4) ||
+        (kb && dalloc(ctx, &f1.opnd2, P * D.F * 2)) || dalloc(ctx, &f1.q16, P * D.hq * kHeadDim * 2) ||
+        dalloc(ctx, &f1.attn_part, D.attn_part_cap * 4) || dalloc(ctx, &f1.f_slots, P * 4) ||
+        dalloc(ctx, &f1.f_pos, P * 4) || dalloc(ctx, &f1.f_tok, P * 4) || dalloc(ctx, &f1.nB_fwd, 16))
+      return fail(ctx, NC_ENOMEM, "second forward buffer set");
+    NC_TRY(cudaMemset(f1.opnd, 0, P * Kmax * esz));
+    NC_TRY(cudaMemset(f1.opnd_scale, 0, P * 4));
+    if (kb) NC_TRY(cudaMemset(f1.opnd2, 0, P * D.F * 2));
+    NC_TRY(cudaStreamCreateWithFlags(&ctx->s2, cudaStreamNonBlocking));
+    for (int k = 0; k < 2; ++k) {
+      NC_TRY(cudaEventCreateWithFlags(&ctx->ev_prep[k], cudaEventDisableTiming));
+      ctx->ev_layer[k].assign(D.n_layers, nullptr);
+      for (auto& e : ctx->ev_layer[k]) NC_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    }
+    ctx->n_fs = 2;
   }
   auto add = [&](const Mat& m) {
     TcMat t;
@@ -398,11 +469,11 @@ static int tc_setup(nc_ctx* ctx) {
       chosen[q] = cands[0];
       for (int ci = 0; ci < nc; ++ci) {
         TcMat tt = t;
-        if (!tc_encode_operand(tt, &tt.b[0], ctx->opnd, esz, rows, cands[ci]))
+        if (!tc_encode_operand(tt, &tt.b[0][0], ctx->opnd, esz, rows, cands[ci]))
           return fail(ctx, NC_ECUDA, "tensor map encoding failed");
         TcGemm g{};
         g.tmap_a = &tt.a;
-        g.tmap_b = &tt.b[0];
+        g.tmap_b = &tt.b[0][0];
         g.M = t.M;
         g.K = t.K;
         g.Bmax = rows;
@@ -455,7 +526,14 @@ static int tc_setup(nc_ctx* ctx) {
     t.bn_dec = chosen[q];
     for (int k = 0; k < kPfBuckets; ++k) t.bn_pf[k] = ctx->P > 0 ? chosen_p[k][q] : chosen[q];
     for (int bi = 0; bi < 4; ++bi)
-      if (!tc_encode_operand(t, &t.b[bi], src, esz, R, 32 << bi)) return fail(ctx, NC_ECUDA, "tensor map encoding failed");
+      if (!tc_encode_operand(t, &t.b[0][bi], src, esz, R, 32 << bi))
+        return fail(ctx, NC_ECUDA, "tensor map encoding failed");
+    if (ctx->n_fs == 2) {
+      const void* src1 = (kb && q == 3) ? ctx->fs[1].opnd2 : ctx->fs[1].opnd;
+      for (int bi = 0; bi < 4; ++bi)
+        if (!tc_encode_operand(t, &t.b[1][bi], src1, esz, ctx->P, 32 << bi))
+          return fail(ctx, NC_ECUDA, "tensor map encoding failed");
+    }
   }
   return NC_OK;
 }
@@ -638,7 +716,7 @@ extern "C" int nc_ctx_create(const nc_config* cfg, const void* weights, size_t n
       dalloc(ctx, &ctx->h, RA * D.F * 4) || dalloc(ctx, &ctx->cdf, B * (D.V + 1) * 4) ||
       dalloc(ctx, &ctx->d_slots, B * 4) || dalloc(ctx, &ctx->d_nB, 16) ||
       dalloc(ctx, &ctx->d_obs, B * 4) || dalloc(ctx, &ctx->d_target, B * 4) ||
-      dalloc(ctx, &ctx->d_lohi, B * 8) || dalloc(ctx, &ctx->d_status, B * 4) ||
+      dalloc(ctx, &ctx->d_lohi, B * 8) || dalloc(ctx, &ctx->d_status, B * 4) || dalloc(ctx, &ctx->d_meta, B * 24) ||
       dalloc(ctx, &ctx->d_st, B * sizeof(StreamDev)))
     return bail(NC_ENOMEM);
   if (D.kv_bf16) {
@@ -841,8 +919,19 @@ struct StepMarks {
   }
 };
 
+// Ordering of a prefill forward with the other buffer set's: before layer
+// l's append it waits for wait[l] (the other chunk has finished layer l's
+// attention, so no ring entry it reads is overwritten, and the entries it
+// appended are in); after layer l's attention it records rec[l].
+struct LayerSync {
+  const cudaEvent_t* wait = nullptr;
+  const cudaEvent_t* rec = nullptr;
+  bool no_pdl = false;      // launch without programmatic dependent launch
+};
+
 // Model forward of every active row: logits into each stream's z.
-static cudaError_t launch_model_tc(nc_ctx* ctx, const Batch& b, StepMarks& m);
+static cudaError_t launch_model_tc(nc_ctx* ctx, const Batch& b, StepMarks& m, int set = 0, cudaStream_t st = nullptr,
+                                   LayerSync sync = {});
 
 static cudaError_t launch_model(nc_ctx* ctx, const Batch& b, StepMarks* mk = nullptr) {
   const Dims& D = ctx->D;
@@ -902,9 +991,14 @@ static cudaError_t launch_model(nc_ctx* ctx, const Batch& b, StepMarks* mk = nul
 // ones; every E4M3 one, for its row scale) or, for BF16, by the producer
 // itself: the attention writes the O projection's operand and the gate/up
 // epilogue the down projection's (into opnd2).
-static cudaError_t launch_model_tc(nc_ctx* ctx, const Batch& b, StepMarks& m) {
-  const Dims& D = ctx->D;
-  cudaStream_t s = ctx->stream;
+static cudaError_t launch_model_tc(nc_ctx* ctx, const Batch& b, StepMarks& m, int set, cudaStream_t st,
+                                   LayerSync sync) {
+  const nc_ctx::FwdSet& F = ctx->fs[set];
+  Dims D = ctx->D;
+  D.attn_part = F.attn_part;
+  D.q16 = F.q16;
+  if (sync.no_pdl) D.pdl = 0;
+  cudaStream_t s = st ? st : ctx->stream;
   const int kb = ctx->fmt == NC_BF16;
   auto gemm = [&](const TcMat& t, int epi, float* y, float* h, void* h16 = nullptr) {
     // the batch tile tuned for this many rows: a decode step's, or the
@@ -917,7 +1011,7 @@ static cudaError_t launch_model_tc(nc_ctx* ctx, const Batch& b, StepMarks& m) {
     }
     TcGemm g{};
     g.tmap_a = &t.a;
-    g.tmap_b = &t.b[bn_index(bn)];
+    g.tmap_b = &t.b[set][bn_index(bn)];
     g.M = t.M;
     g.K = t.K;
     g.Bmax = b.Bmax;
@@ -927,7 +1021,7 @@ static cudaError_t launch_model_tc(nc_ctx* ctx, const Batch& b, StepMarks& m) {
     g.kind_bf16 = kb;
     g.nB = b.nB;
     g.w_scale = t.scale;
-    g.x_scale = ctx->opnd_scale;
+    g.x_scale = F.opnd_scale;
     g.y = y;
     g.h_out = h;
     g.h16 = h16;
@@ -936,29 +1030,31 @@ static cudaError_t launch_model_tc(nc_ctx* ctx, const Batch& b, StepMarks& m) {
     g.status = ctx->d_status;
     return launch_gemm_tc(g, epi, s, D.pdl);
   };
-  cudaError_t e = launch_embed(D, b, ctx->embed, ctx->embed_scale, ctx->fmt, ctx->x, s);
+  cudaError_t e = launch_embed(D, b, ctx->embed, ctx->embed_scale, ctx->fmt, F.x, s);
   if (e == cudaSuccess) e = m.mark(s, TK_EMBED);
   for (int l = 0; l < D.n_layers && e == cudaSuccess; ++l) {
     const LayerW& L = ctx->layers[l];
     const TcMat* T = &ctx->tc[4 * l];
-    e = launch_act_rmsnorm(D, b, ctx->x, L.g_attn, D.d, kb, ctx->opnd, ctx->opnd_scale, s);
-    if (e == cudaSuccess) e = gemm(T[0], EPI_STORE, ctx->qkv, nullptr);
-    if (e == cudaSuccess && b.pos) e = launch_kv_append(D, b, l, ctx->qkv, s);
+    e = launch_act_rmsnorm(D, b, F.x, L.g_attn, D.d, kb, F.opnd, F.opnd_scale, s);
+    if (e == cudaSuccess) e = gemm(T[0], EPI_STORE, F.qkv, nullptr);
+    if (e == cudaSuccess && b.pos && sync.wait) e = cudaStreamWaitEvent(s, sync.wait[l], 0);
+    if (e == cudaSuccess && b.pos) e = launch_kv_append(D, b, l, F.qkv, s);
     if (e == cudaSuccess) e = m.mark(s, TK_QKV);
-    if (e == cudaSuccess) e = launch_attn(D, b, l, ctx->qkv, ctx->attn_out, s, kb ? ctx->opnd : nullptr);
+    if (e == cudaSuccess) e = launch_attn(D, b, l, F.qkv, F.attn_out, s, kb ? F.opnd : nullptr);
+    if (e == cudaSuccess && sync.rec) e = cudaEventRecord(sync.rec[l], s);
     if (e == cudaSuccess) e = m.mark(s, TK_ATTN);
     if (e == cudaSuccess && !kb)
-      e = launch_act_plain(D, b, ctx->attn_out, D.hq * kHeadDim, kb, ctx->opnd, ctx->opnd_scale, s);
-    if (e == cudaSuccess) e = gemm(T[1], EPI_RESID, ctx->x, nullptr);
+      e = launch_act_plain(D, b, F.attn_out, D.hq * kHeadDim, kb, F.opnd, F.opnd_scale, s);
+    if (e == cudaSuccess) e = gemm(T[1], EPI_RESID, F.x, nullptr);
     if (e == cudaSuccess) e = m.mark(s, TK_O);
-    if (e == cudaSuccess) e = launch_act_rmsnorm(D, b, ctx->x, L.g_ffn, D.d, kb, ctx->opnd, ctx->opnd_scale, s);
-    if (e == cudaSuccess) e = gemm(T[2], EPI_SWIGLU, nullptr, ctx->h, kb ? ctx->opnd2 : nullptr);
+    if (e == cudaSuccess) e = launch_act_rmsnorm(D, b, F.x, L.g_ffn, D.d, kb, F.opnd, F.opnd_scale, s);
+    if (e == cudaSuccess) e = gemm(T[2], EPI_SWIGLU, nullptr, F.h, kb ? F.opnd2 : nullptr);
     if (e == cudaSuccess) e = m.mark(s, TK_GU);
-    if (e == cudaSuccess && !kb) e = launch_act_plain(D, b, ctx->h, D.F, kb, ctx->opnd, ctx->opnd_scale, s);
-    if (e == cudaSuccess) e = gemm(T[3], EPI_RESID, ctx->x, nullptr);
+    if (e == cudaSuccess && !kb) e = launch_act_plain(D, b, F.h, D.F, kb, F.opnd, F.opnd_scale, s);
+    if (e == cudaSuccess) e = gemm(T[3], EPI_RESID, F.x, nullptr);
     if (e == cudaSuccess) e = m.mark(s, TK_DOWN);
   }
-  if (e == cudaSuccess) e = launch_act_rmsnorm(D, b, ctx->x, ctx->g_final, D.d, kb, ctx->opnd, ctx->opnd_scale, s);
+  if (e == cudaSuccess) e = launch_act_rmsnorm(D, b, F.x, ctx->g_final, D.d, kb, F.opnd, F.opnd_scale, s);
   if (e == cudaSuccess) e = gemm(ctx->tc.back(), EPI_LOGITS, nullptr, nullptr);
   if (e == cudaSuccess) e = m.mark(s, TK_LMHEAD);
   return e;
@@ -1288,6 +1384,112 @@ static int encode_prefill(nc_ctx* ctx, int n, int m0, const int32_t* tok_dev, co
     for (int k = 0; k < TK_COUNT; ++k) std::snprintf(trace->name[k], sizeof(trace->name[k]), "%s", kTraceNames[k]);
   }
   auto start_at = [&](int64_t a) -> int64_t { return a < D.L ? 0 : ((a - D.L) / D.C + 1) * D.C; };
+  // Two forward buffer sets: the whole pass is one captured graph.  Chunk
+  // c's forward runs on the stream of set c & 1 (s, s2) beside chunk c - 1's,
+  // each layer's append after chunk c - 1's attention of that layer; the
+  // N-gram passes run in chunk order on the side stream and the vocabulary
+  // passes in chunk order on vstream; set c & 1 is reused by chunk c + 2
+  // after chunk c's vocabulary passes.  The graph is kept for the next call
+  // with the same chunk plan and buffers.
+  if (piped && ctx->n_fs == 2) {
+    std::vector<std::pair<int, int>> plan;
+    {
+      int mm = m0;
+      for (int64_t p = 0; p < max_len; p += mm) {
+        int live = 0;
+        while (live < n && lens_h[live] > p) ++live;
+        mm = m_max;
+        while (mm > m0 && ((int64_t)live * mm > ctx->P || p % mm != 0)) mm /= 2;
+        plan.emplace_back(mm, std::min(n, ctx->P / mm));
+      }
+    }
+    auto ptr = [](const void* q) { return (int64_t)(uintptr_t)q; };
+    std::vector<int64_t> key = {n, ptr(tok_dev), ptr(offs_dev), ptr(lens_dev), ptr(intervals), stride,
+                                ptr(io.probe_z), ptr(io.probe_pt), ptr(io.probe_png), ptr(io.probe_p), io.probe_tok,
+                                ptr(io.probe_row)};
+    for (const auto& pc : plan) {
+      key.push_back(pc.first);
+      key.push_back(pc.second);
+    }
+    if (!ctx->pass_graph || ctx->pass_key != key) {
+      if (ctx->pass_graph) cudaGraphExecDestroy(ctx->pass_graph);
+      ctx->pass_graph = nullptr;
+      ctx->pass_key.clear();
+      cudaStream_t fst[2] = {s, ctx->s2};
+      cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+      auto fork = [&](cudaStream_t from, cudaStream_t to, cudaEvent_t ev) {
+        if (e == cudaSuccess) e = cudaEventRecord(ev, from);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(to, ev, 0);
+      };
+      fork(s, ctx->s2, ctx->ev_fork);
+      fork(s, ctx->side, ctx->ev_fork);
+      fork(s, vs, ctx->ev_fork);
+      Dims Dv = D;
+      Dv.pdl = 0;                                   // the vocabulary passes: see below
+      for (size_t c = 0; c < plan.size() && e == cudaSuccess; ++c) {
+        const int mc = plan[c].first, ne = plan[c].second, set = (int)(c & 1);
+        cudaStream_t sc = fst[set];
+        const nc_ctx::FwdSet& F = ctx->fs[set];
+        if (c >= 2) e = cudaStreamWaitEvent(sc, ctx->ev_voc[set], 0);      // chunk c - 2's passes read set
+        if (c >= 1 && e == cudaSuccess) e = cudaStreamWaitEvent(sc, ctx->ev_prep[set ^ 1], 0);   // positions in order
+        Batch b = make_batch(ctx);
+        b.Bmax = ne;
+        if (e == cudaSuccess) e = launch_chunk_start(ctx->d_p0, set, mc, sc);
+        int32_t* p0 = ctx->d_p0 + set;
+        if (e == cudaSuccess)
+          e = launch_prepare_prefill(b, ne, mc, D.V, p0, tok_dev, offs_dev, lens_dev, F.f_slots, F.f_pos, F.f_tok,
+                                     F.nB_fwd, ctx->f_obs[set], ctx->f_nb[set], ctx->d_zidx[set], sc);
+        if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_prep[set], sc);
+        const Batch br = vocab_batch(ne, set);
+        const bool ng = ctx->snap[set] != nullptr;
+        if (ng && e == cudaSuccess) e = cudaStreamWaitEvent(ctx->side, ctx->ev_prep[set], 0);
+        if (ng && e == cudaSuccess)
+          e = launch_ngram_seq(D, br, mc, ctx->f_nb[set], ctx->f_obs[set], p0, ctx->snap[set], ctx->side);
+        if (ng && e == cudaSuccess) e = cudaEventRecord(ctx->ev_join, ctx->side);
+        Batch f = make_batch(ctx);
+        f.slots = F.f_slots;
+        f.nB = F.nB_fwd;
+        f.obs = nullptr;
+        f.Bmax = ne * mc;
+        f.pos = F.f_pos;
+        f.tok = F.f_tok;
+        f.z_out = ctx->zrows[set];
+        f.pm = mc;
+        LayerSync sync;
+        sync.wait = c >= 1 ? ctx->ev_layer[set ^ 1].data() : nullptr;
+        sync.rec = ctx->ev_layer[set].data();
+        // a kernel launched early would hold its SMs waiting for its
+        // predecessor while the other forward could use them
+        sync.no_pdl = true;
+        StepMarks none;
+        if (e == cudaSuccess) e = launch_model_tc(ctx, f, none, set, sc, sync);
+        if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_fwd[set], sc);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(vs, ctx->ev_fwd[set], 0);
+        if (ng && e == cudaSuccess) e = cudaStreamWaitEvent(vs, ctx->ev_join, 0);
+        // without PDL: it would sit on its SMs while the previous passes run
+        if (e == cudaSuccess)
+          e = launch_vocab_seq(Dv, br, io, mc, ctx->zrows[set], ctx->f_nb[set], ctx->f_obs[set], ctx->snap[set], vs);
+        if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_voc[set], vs);
+      }
+      // join every stream back into s
+      fork(ctx->s2, s, ctx->ev_prep[0]);
+      fork(ctx->side, s, ctx->ev_join);
+      fork(vs, s, ctx->ev_done);
+      cudaGraph_t g = nullptr;
+      const cudaError_t e2 = cudaStreamEndCapture(s, &g);
+      if (e == cudaSuccess) e = e2;
+      cudaGraphExec_t ge = nullptr;
+      if (e == cudaSuccess) e = cudaGraphInstantiate(&ge, g, 0);
+      if (g) cudaGraphDestroy(g);
+      if (e != cudaSuccess) return fail_cuda(ctx, e, "prefill pass capture");
+      ctx->pass_graph = ge;
+      ctx->pass_key = key;
+    }
+    const cudaError_t e = cudaGraphLaunch(ctx->pass_graph, s);
+    if (e != cudaSuccess) return fail_cuda(ctx, e, "prefill pass");
+    for (auto& ev : mk.ev) cudaEventDestroy(ev);
+    return NC_OK;
+  }
   int st = NC_OK;
   int m = m0;
   int chunk = 0;
@@ -1518,8 +1720,7 @@ static int encode_intervals(nc_ctx* ctx, int n_streams, const int32_t* tokens_de
   std::vector<int> order, slot_of;
   std::vector<int32_t> ids;
   int st = open_rows(ctx, n_streams, lens, &order, &slot_of, &ids, 0x60000000);
-  int64_t* meta = nullptr;
-  int32_t* tok_rows = nullptr;
+  int64_t* meta = ctx->d_meta;
   uint32_t* iv_rows = nullptr;
   std::vector<int64_t> lens_h(n_streams);
   do {
@@ -1532,10 +1733,6 @@ static int encode_intervals(nc_ctx* ctx, int n_streams, const int32_t* tokens_de
       h_meta[n_streams + r] = lens[order[r]];
       h_meta[2 * n_streams + r] = order[r];
       lens_h[r] = lens[order[r]];
-    }
-    if (dev_malloc(&meta, 3 * n_streams * 8) != cudaSuccess) {
-      st = fail(ctx, NC_ENOMEM, "meta allocation");
-      break;
     }
     bool identity = true;
     for (int r = 0; r < n_streams; ++r) identity &= order[r] == r;
@@ -1561,8 +1758,6 @@ static int encode_intervals(nc_ctx* ctx, int n_streams, const int32_t* tokens_de
         }
     if (st == NC_OK) st = check_status(ctx, slot_of);
   } while (0);
-  cudaFree(meta);
-  cudaFree(tok_rows);
   cudaFree(iv_rows);
   close_rows(ctx, ids);
   return st;
@@ -1630,9 +1825,7 @@ extern "C" int nc_encode(nc_ctx* ctx, int n_streams, const int32_t* const* token
     return st;
   }
   // tokens, offsets and lengths to the device (row order = longest first)
-  int32_t* tok_dev = nullptr;
-  int64_t* meta = nullptr;
-  uint32_t* iv = nullptr;
+  int64_t* meta = ctx->d_meta;
   std::vector<int64_t> h_meta(2 * n_streams);
   int64_t off = 0;
   for (int r = 0; r < n_streams; ++r) {
@@ -1642,12 +1835,26 @@ extern "C" int nc_encode(nc_ctx* ctx, int n_streams, const int32_t* const* token
   }
   std::vector<uint32_t> h_iv;
   do {
-    if (dev_malloc(&tok_dev, std::max<int64_t>(total, 1) * 4) != cudaSuccess ||
-        dev_malloc(&meta, 2 * n_streams * 8) != cudaSuccess ||
-        dev_malloc(&iv, (size_t)n_streams * std::max<int64_t>(max_len, 1) * 8) != cudaSuccess) {
+    const size_t need_tok = (size_t)std::max<int64_t>(total, 1);
+    const size_t need_iv = (size_t)n_streams * std::max<int64_t>(max_len, 1) * 2;
+    if (ctx->enc_tok_cap < need_tok) {
+      cudaFree(ctx->enc_tok);
+      ctx->enc_tok = nullptr;
+      ctx->enc_tok_cap = 0;
+      if (dev_malloc(&ctx->enc_tok, need_tok * 4) == cudaSuccess) ctx->enc_tok_cap = need_tok;
+    }
+    if (ctx->enc_iv_cap < need_iv) {
+      cudaFree(ctx->enc_iv);
+      ctx->enc_iv = nullptr;
+      ctx->enc_iv_cap = 0;
+      if (dev_malloc(&ctx->enc_iv, need_iv * 4) == cudaSuccess) ctx->enc_iv_cap = need_iv;
+    }
+    if (ctx->enc_tok_cap < need_tok || ctx->enc_iv_cap < need_iv) {
       st = fail(ctx, NC_ENOMEM, "device allocation for encode failed");
       break;
     }
+    int32_t* tok_dev = ctx->enc_tok;
+    uint32_t* iv = ctx->enc_iv;
     for (int r = 0; r < n_streams; ++r)
       if (lens[order[r]] > 0 &&
           cudaMemcpyAsync(tok_dev + h_meta[r], tokens[order[r]], lens[order[r]] * 4, cudaMemcpyHostToDevice,
@@ -1672,9 +1879,6 @@ extern "C" int nc_encode(nc_ctx* ctx, int n_streams, const int32_t* const* token
     }
     st = check_status(ctx, slot_of);
   } while (0);
-  cudaFree(tok_dev);
-  cudaFree(meta);
-  cudaFree(iv);
   close_all();
   if (st != NC_OK) return st;
   // host coder, streams in parallel
@@ -1922,7 +2126,7 @@ extern "C" int nc_gemm_tc(const void* W, const void* X, const float* w_scale, co
   TcMat t;
   t.M = M;
   t.K = K;
-  if (!tc_encode_weights(t, W, esz) || !tc_encode_operand(t, &t.b[0], X, esz, N, bn)) return NC_EINVAL;
+  if (!tc_encode_weights(t, W, esz) || !tc_encode_operand(t, &t.b[0][0], X, esz, N, bn)) return NC_EINVAL;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   int32_t* dev = nullptr;
   if (dev_malloc(&dev, 8) != cudaSuccess) return NC_ENOMEM;
@@ -1931,7 +2135,7 @@ extern "C" int nc_gemm_tc(const void* W, const void* X, const float* w_scale, co
   int32_t back[2] = {0, 0};
   TcGemm g{};
   g.tmap_a = &t.a;
-  g.tmap_b = &t.b[0];
+  g.tmap_b = &t.b[0][0];
   g.M = M;
   g.K = K;
   g.Bmax = N;

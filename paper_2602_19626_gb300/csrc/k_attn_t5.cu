@@ -513,7 +513,7 @@ __global__ void __launch_bounds__(kT5Threads, 2) k_attn_t5(Dims D, Batch b, int 
     const float Lc = __fadd_rn(red[p], red[kT5Pairs + p]);
     // the chunk's (O_c, M_c, l_c) of the present pairs: warpgroup h writes
     // dims 32 h .. 32 h + 31
-    const int tp = prefill ? kT5Pairs : grp;       // pairs a tile can hold
+    const int tp = prefill ? min(kT5Pairs, b.pm * grp) : grp;   // pairs a tile can hold
     float4* part = part_base(D, (size_t)blockIdx.z * D.hkv + g, tp);
     if (ok && mine) {
       uint32_t r[32];
@@ -577,9 +577,10 @@ __global__ void __launch_bounds__(kT5Threads) k_attn_merge(Dims D, Batch b, int 
   const int my_r = (T.pb + p) / grp, my_h = (T.pb + p) % grp;
   const int a = b.pos[T.row0 + my_r];
   const int ncp = a < 0 ? 0 : (a - window_start_at(D, a)) / kT5Chunk + 1;
-  const float4* part = part_base(D, (size_t)blockIdx.x * D.hkv + g, kT5Pairs);
+  const int tp = min(kT5Pairs, b.pm * grp);
+  const float4* part = part_base(D, (size_t)blockIdx.x * D.hkv + g, tp);
   store_out(io, (size_t)(T.row0 + my_r) * D.hq * kHeadDim + (g * grp + my_h) * kHeadDim + 4 * i,
-            merge_item(part, kT5Pairs, p, i, ncp));
+            merge_item(part, tp, p, i, ncp));
 }
 
 // Prefill append: row j's k (rotated at its position a) and v, rounded to
@@ -627,11 +628,11 @@ void attn_t5_scratch(const Dims& D, int max_streams, int prefill_rows, size_t* p
   const int grp = D.hq / D.hkv;
   // a decode tile is one stream's row (grp pairs); a prefill chunk of n
   // streams and m <= prefill_rows / n positions each takes n ceil(m grp / 128)
-  // tiles of 128 pairs, at most max_streams + ceil(prefill_rows grp / 128)
-  const size_t pf_tiles =
-      prefill_rows >= 2 ? (size_t)max_streams + ((size_t)prefill_rows * grp + kT5Pairs - 1) / kT5Pairs : 0;
+  // tiles of min(128, m grp) pairs: at most 2 prefill_rows grp pairs (n < 128
+  // prefill_rows / (m grp 128) when m grp > 128)
+  const size_t pf_pairs = prefill_rows >= 2 ? 2 * (size_t)prefill_rows * grp : 0;
   const size_t per = (size_t)D.hkv * kT5MaxRanks * kPartRow;
-  *part_floats = std::max((size_t)max_streams * grp, pf_tiles * kT5Pairs) * per;
+  *part_floats = std::max((size_t)max_streams * grp, pf_pairs) * per;
   *tickets = max_streams * D.hkv;                  // decode rows only
 }
 
@@ -652,7 +653,7 @@ cudaError_t launch_attn_t5(const Dims& D, const Batch& b, int layer, const float
     tps = (b.pm * grp + kT5Pairs - 1) / kT5Pairs;
     tiles = (b.Bmax / b.pm) * tps;
   }
-  const size_t tp = b.pos ? kT5Pairs : grp;
+  const size_t tp = b.pos ? std::min(kT5Pairs, b.pm * grp) : grp;
   if ((!b.pos && (size_t)tiles * D.hkv > (size_t)D.attn_tickets) ||
       (size_t)tiles * D.hkv * kT5MaxRanks * tp * kPartRow > D.attn_part_cap)
     return cudaErrorInvalidValue;
