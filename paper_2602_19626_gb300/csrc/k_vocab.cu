@@ -345,6 +345,7 @@ constexpr int kSeqMax = 1024;  // positions of one prefill chunk at most (a powe
 struct StepShared {
   StepSlot slot[2];
   NgSnap ng[kSnapBufs];
+  uint64_t xbar[2];           // the prefill loop's exchange rounds, by slot
 };
 
 // This thread's place in the cluster's split of the vocabulary.
@@ -396,6 +397,69 @@ __device__ __forceinline__ void push_obs(cg::cluster_group& cl, float4* mine, fl
 #pragma unroll
   for (int r = 0; r < CL; ++r) *cl.map_shared_rank(mine, r) = v;
 }
+// Exchange rounds of the prefill loop without a cluster barrier: each
+// value goes to every CTA's inbox as an asynchronous remote store that
+// completes its bytes on that CTA's mbarrier of the round's slot; a CTA
+// arms its own mbarrier with the round's byte count and waits on it (acquire
+// at cluster scope).  Slot s serves rounds s, s + 2, ...: a sender reaches
+// round k + 2 only after every CTA's round k + 1 values, sent after each CTA
+// finished reading round k.
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ uint32_t remote_addr(uint32_t a, int rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
+  return r;
+}
+__device__ __forceinline__ void st_async16(uint32_t raddr, uint32_t rbar, uint4 v) {
+  asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v4.b32 [%0], {%1, %2, %3, %4}, [%5];" ::"r"(raddr),
+               "r"(v.x), "r"(v.y), "r"(v.z), "r"(v.w), "r"(rbar)
+               : "memory");
+}
+template <typename T>
+__device__ __forceinline__ uint4 as_u4(const T& v) {
+  static_assert(sizeof(T) == 16, "16-byte values");
+  return *reinterpret_cast<const uint4*>(&v);
+}
+// Lanes 0 .. CL - 1: the warp's partial v to its global index in the array
+// `mine` of CTA `lane`.
+template <int CL, typename T>
+__device__ __forceinline__ void push_part_async(T* mine, const Lanes& L, T v, uint64_t* bar) {
+  if (L.lane < CL) st_async16(remote_addr(smem_addr(mine + L.gw), L.lane), remote_addr(smem_addr(bar), L.lane), as_u4(v));
+}
+template <int CL>
+__device__ __forceinline__ void push_obs_async(float4* mine, float4 v, uint64_t* bar) {
+#pragma unroll
+  for (int r = 0; r < CL; ++r) st_async16(remote_addr(smem_addr(mine), r), remote_addr(smem_addr(bar), r), as_u4(v));
+}
+__device__ __forceinline__ void xbar_arm(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
+}
+// Bounded wait (2^22 polls, about 0.2 s) for the round's bytes; false when it gave up.
+__device__ __forceinline__ bool xbar_wait(uint64_t* bar, uint32_t parity) {
+  const uint32_t a = smem_addr(bar);
+  unsigned long long t0 = 0;
+  for (uint32_t it = 0; it < (1u << 22); ++it) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (ok) return true;
+    if ((it & 63) == 63) {
+      unsigned long long t;
+      asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+      if (t0 == 0) t0 = t;
+      else if (t - t0 > 200000000ull) return false;
+    }
+  }
+  return false;
+}
+// Bytes of one round: the softmax partials and / or the quantiser partials
+// with the observed token's values.
+constexpr uint32_t kRoundSm = kClusterWarps * 16, kRoundQ = kClusterWarps * 16 + 16;
+
 // The inbox entries of global warps 4 lane .. 4 lane + 3.
 template <typename T>
 __device__ __forceinline__ void local_parts(const T* arr, int lane, T (&v)[4]) {
@@ -937,6 +1001,11 @@ __global__ void __launch_bounds__(step_threads<CL>(), 1)
     s_obs[i] = obs_step[(size_t)i * n_streams + j];
     s_nb[i] = nb_step[i];
   }
+  if (threadIdx.x == 0) {
+    for (int k = 0; k < 2; ++k)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&sh.xbar[k])) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
   const Lanes L = lanes_of<E, CL>((int)cl.block_rank());
   StreamDev& st = b.st[b.slots[j]];
   const int V = D.V;
@@ -975,7 +1044,8 @@ __global__ void __launch_bounds__(step_threads<CL>(), 1)
   float th0 = st.theta[0], th1 = st.theta[1];
   const int n0 = st.n_coded;
   if (ngram) cp_async_wait_all();
-  __syncthreads();                               // the first N-gram states are in shared memory
+  cl.sync();                                     // the first N-gram states are in shared memory, every
+                                                 // CTA's exchange barriers initialised
   if (ngram) ngram_scatter<E>(sh.ng[0], spw, L);
 
   // the previous position's values its quantiser and mixer step need
@@ -984,7 +1054,8 @@ __global__ void __launch_bounds__(step_threads<CL>(), 1)
   uint32_t p_below = 0, p_ct = 0, p_am_c = 0;
   float2 p_w = make_float2(0.f, 0.f);
   float last_pts = st.pt_obs, last_pngs = st.png_obs;
-  int nb = 0;                                    // cluster barriers taken
+  int nb = 0;                                    // exchange rounds taken
+  bool xok = true;                               // no exchange wait has given up
   int r = 0, t_last = -1;
 
   // interval, numeric checks and mixer step of the pending position from its
@@ -1039,11 +1110,12 @@ __global__ void __launch_bounds__(step_threads<CL>(), 1)
     }
     const float4 part = softmax_part<E>(s, e, D.skip ? entropy_part<E>(png) : 0.f, D.skip != 0);
     StepSlot& in = sh.slot[nb & 1];
-    push_part<CL>(cl, in.sm, L, part);
-    if (ngram) cp_async_wait_all();              // the state of position r + 2, added after this barrier
-    cluster_arrive();
-    // outside the barrier's release: position r + 1's logits, token and slot
-    // masses (its state arrived two barriers ago), the activity of r + 3
+    uint64_t* xb = &sh.xbar[nb & 1];
+    push_part_async<CL>(in.sm, L, part, xb);
+    if (ngram) cp_async_wait_all();              // the state of position r + 2, added after this round
+    if (threadIdx.x == 0) xbar_arm(xb, kRoundSm + (pend ? kRoundQ : 0));
+    // while the round's values travel: position r + 1's logits, token and
+    // slot masses (its state arrived two rounds ago), the activity of r + 3
     int t_n = 0;
     bool act3 = false;
     if (more) {
@@ -1052,9 +1124,13 @@ __global__ void __launch_bounds__(step_threads<CL>(), 1)
       act3 = act2 && r + 3 < m && j < s_nb[r + 3];
       if (ngram) ngram_scatter<E>(sh.ng[(r + 1) % kSnapBufs], spw, L);
     }
-    cluster_wait();
-    // every warp has added position r's masses (before this barrier's
-    // arrive): its buffer takes the state of r + 3
+    if (!__all_sync(0xffffffffu, xbar_wait(xb, (uint32_t)(nb >> 1) & 1u))) {
+      xok = false;
+      pend = false;
+      break;                                     // the other warps give up on their next round
+    }
+    // every warp of the cluster has added position r's masses (before its
+    // partials went out): its buffer takes the state of r + 3
     if (ngram && act3) snap_copy_async(&sh.ng[(r + 3) % kSnapBufs], gj + r + 3);
     ++nb;
     float4 smv[4];
@@ -1077,12 +1153,13 @@ __global__ void __launch_bounds__(step_threads<CL>(), 1)
     if (probe && io.probe_p) store_run<E>(io.probe_p + prow, L.v0, V, p);
     StepSlot& nx = sh.slot[nb & 1];
     if (owner)
-      push_obs<CL>(cl, &nx.obs,
-               make_float4(pick<E>(pt, L.v0, t), png_t, __fsub_rn(__fsub_rn(s_t, sm.M), __logf(sm.S)), 0.f));
+      push_obs_async<CL>(&nx.obs,
+                         make_float4(pick<E>(pt, L.v0, t), png_t, __fsub_rn(__fsub_rn(s_t, sm.M), __logf(sm.S)), 0.f),
+                         &sh.xbar[nb & 1]);
     uint32_t c[E], excl = 0;
     const bool scan = io.intervals && t >= L.wbase && t < L.wbase + 32 * E;
     const uint4 qp = quant_part<E, FULL>(p, L, V, K, Kf, D.floor, scan, finite_step(sm, w), c, excl, p_am_i, p_am_c);
-    push_part<CL>(cl, nx.qn, L, qp);
+    push_part_async<CL>(nx.qn, L, qp, &sh.xbar[nb & 1]);
     p_own = owner && io.intervals;
     if (owner) {
       counts_around<E>(c, L.v0, t, p_below, p_ct);
@@ -1103,7 +1180,11 @@ __global__ void __launch_bounds__(step_threads<CL>(), 1)
       if (!skipped && D.use_head) head_update<E>(bias, pt, __fmul_rn(D.alpha, 1.f), L.v0, t, owner);
       pend = true;
     } else {
-      cl.sync();
+      if (threadIdx.x == 0) xbar_arm(&sh.xbar[nb & 1], kRoundQ);
+      if (!__all_sync(0xffffffffu, xbar_wait(&sh.xbar[nb & 1], (uint32_t)(nb >> 1) & 1u))) {
+        xok = false;
+        break;
+      }
       ++nb;
       finish(nx, pt, true);
     }
@@ -1114,12 +1195,17 @@ __global__ void __launch_bounds__(step_threads<CL>(), 1)
     live = more;
   }
   if (pend) {
-    cl.sync();
-    ++nb;
-    StepSlot& in = sh.slot[(nb - 1) & 1];
-    float none[E];
-    finish(in, none, false);
+    if (threadIdx.x == 0) xbar_arm(&sh.xbar[nb & 1], kRoundQ);
+    if (__all_sync(0xffffffffu, xbar_wait(&sh.xbar[nb & 1], (uint32_t)(nb >> 1) & 1u))) {
+      ++nb;
+      StepSlot& in = sh.slot[(nb - 1) & 1];
+      float none[E];
+      finish(in, none, false);
+    } else {
+      xok = false;
+    }
   }
+  if (!xok && L.lane == 0) atomicOr(&st.status, ST_TIMEOUT);
   if (ngram) cp_async_wait_all();                // no copy outlives the kernel
   cl.sync();   // every CTA is done with the others' shared memory
   if (r == 0) return;
