@@ -1416,35 +1416,247 @@ __device__ void ngram_update_row(const Dims& D, const Batch& b, int j, int warp,
   }
 }
 
+// Context of length len ending at a2 (a0, a1 the tokens before it), packed
+// as ctx_key packs the history.
+__device__ __forceinline__ unsigned long long ctx_key3(int a0, int a1, int a2, int len) {
+  unsigned long long key = 0;
+  if (len >= 3) key = (unsigned long long)(uint32_t)a0;
+  if (len >= 2) key = (key << 16) | (unsigned long long)(uint32_t)a1;
+  return (key << 16) | (unsigned long long)(uint32_t)a2;
+}
+
+// Lane-parallel step of a linear probe: lane l holds kk, the key of index
+// slot home + l (in = false past the capacity).  Returns the first lane, in
+// probe order, whose slot holds `key` or is empty (-1: none of the 32), and
+// in *hit whether that slot holds the key.
+__device__ __forceinline__ int ng_resolve(unsigned long long kk, bool in, unsigned long long key, bool* hit) {
+  const unsigned mh = __ballot_sync(0xffffffffu, in && kk == key);
+  const unsigned me = __ballot_sync(0xffffffffu, in && kk == kEmptyKey);
+  if ((mh | me) == 0) return -1;
+  const int f = __ffs(mh | me) - 1;
+  *hit = (mh >> f) & 1u;
+  return f;
+}
+
 // The N-gram side of a prefill chunk, one CTA per stream row: for each
 // position in order, the state of its prediction into snap, then the update
 // with the observed token (tables, context entries, history and N; the
 // unigram counts and the position stay with the vocabulary passes).  It needs
 // only the tokens, so it runs beside the chunk's forward pass.
+//
+// Warp k (k < 3) owns order k, with the history, N and the entry of the
+// next prediction's context in registers for the whole chunk:
+// - the context a token is counted in is the one its prediction used, so
+//   its entry is known from the previous position (the look-up made then);
+// - one round of loads per position: that entry's 64 slots (two per lane),
+//   the 32 index slots from the home of the context when it has to be
+//   inserted, and the keys and entry numbers of the 32 index slots from the
+//   home of the next context;
+// - a new context goes into the first empty slot of its probe.  The next
+//   context's slots are read before that insert: a key found there stays
+//   where it is (entries are never removed), one found absent stays absent
+//   unless it is the context just counted.
+// The counting and eviction are those of ngram_update_order, so the tables,
+// and so the coded bits, equal those of one update per step.  Warp 3 forms
+// the closed form's weights of each position from the orders' counts.
 __global__ void __launch_bounds__(128) k_ngram_seq(Dims D, Batch b, int m, int n_streams, const int32_t* nb_step,
                                                    const int32_t* obs_step, const int32_t* z_idx, const int32_t* p0_at,
                                                    NgSnap* snap) {
+  __shared__ int32_t s_obs[kSeqMax], s_nb[kSeqMax];       // the chunk's tokens and active rows, per position
+  __shared__ int32_t s_n[2][kMaxOrder], s_ns[2][kMaxOrder];  // by position parity: the orders' n_k (-1: no entry), slots
   const int j = blockIdx.x;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   StreamDev& st = b.st[b.slots[j]];
+  for (int i = threadIdx.x; i < m; i += blockDim.x) {
+    s_obs[i] = obs_step[(size_t)i * n_streams + j];
+    s_nb[i] = nb_step[i];
+  }
   int n_coded = *p0_at;                            // every live stream is at the chunk's first position
+  int h0 = st.hist[0], h1 = st.hist[1], h2 = st.hist[2];
+  int N = st.N;
+  const int k = warp;                              // order of this warp; warp 3 forms the weights
+  const bool ord = k < kMaxOrder && k < D.order;
+  const int mask = st.cap_mask, max_len = st.max_len;
+  const bool in = lane <= mask;                    // lanes within the index capacity
+  unsigned long long* keys = ord ? st.keys[k] : nullptr;
+  int32_t* idx = ord ? st.idx[k] : nullptr;
+  NgEntry* ent = ord ? st.ent[k] : nullptr;
+  int ce = ord ? st.ctx_ent[k] : -1;               // entry of the next prediction's context
+  int n_ent = ord ? st.n_ent[k] : 0;
   NgSnap* out = snap + z_idx[j];
-  for (int r = 0; r < m; ++r) {
-    if (j >= nb_step[r]) break;
-    const int t = obs_step[(size_t)r * n_streams + j];
-    ng_snapshot(D, st, out + r, threadIdx.x, blockDim.x);
-    if (t < 0 || t >= D.V) break;                  // flagged by the vocabulary pass
-    __syncthreads();                               // this prediction's entries are copied
-    if (warp < kMaxOrder) ngram_update_order(D, st, t, warp, lane, n_coded);
-    __syncthreads();                               // every order has read the old history
-    if (threadIdx.x == 0) {
-      st.N += 1;
-      st.hist[0] = st.hist[1];
-      st.hist[1] = st.hist[2];
-      st.hist[2] = t;
+  __syncthreads();
+  int r = 0;
+  for (; r < m; ++r) {
+    if (j >= s_nb[r]) break;
+    const int t = s_obs[r];
+    const bool tok_ok = t >= 0 && t < D.V;
+    if (ord) {
+      const bool cur = k < min(3, n_coded);        // the context of length k + 1 before t exists
+      const bool nxt = k < min(3, n_coded + 1);
+      const unsigned long long ckey = ctx_key3(h0, h1, h2, k + 1), nkey = ctx_key3(h1, h2, t, k + 1);
+      const int home_c = (int)(mix64(ckey) & (unsigned long long)mask);
+      const int home_n = (int)(mix64(nkey) & (unsigned long long)mask);
+      const bool ins = tok_ok && cur && ce < 0;    // a new context: inserted below
+      const bool probe_n = tok_ok && nxt && !(cur && nkey == ckey);
+      // one round of loads
+      int tok0 = 0, tok1 = 0, cnt0 = 0, cnt1 = 0, ens = 0, en_n = 0, in_n = -1;
+      unsigned long long kc = 0, kn = 0;
+      if (ce >= 0) {
+        const NgEntry& en = ent[ce];
+        tok0 = en.tok[lane];
+        tok1 = en.tok[lane + 32];
+        cnt0 = en.cnt[lane];
+        cnt1 = en.cnt[lane + 32];
+        ens = en.nslots;
+        en_n = en.n;
+      }
+      if (ins && in) kc = keys[(home_c + lane) & mask];
+      if (probe_n && in) {
+        kn = keys[(home_n + lane) & mask];
+        in_n = idx[(home_n + lane) & mask];
+      }
+      // the prediction's state: the entry before t is counted
+      NgSnap& o = out[r];
+      if (lane < ens) o.tc[k][lane] = make_int2(tok0, cnt0);
+      if (lane + 32 < ens) o.tc[k][lane + 32] = make_int2(tok1, cnt1);
+      if (lane == 0) {
+        s_n[r & 1][k] = ce >= 0 ? en_n : -1;
+        s_ns[r & 1][k] = ens;
+      }
+      if (tok_ok) {
+        // count t in the context's entry
+        if (ins) {
+          bool hit = false;
+          const int f = ng_resolve(kc, in, ckey, &hit);
+          int ei = -1;
+          if (f < 0) {                             // more than 32 probes: the one-slot-at-a-time walk
+            if (lane == 0) ei = ng_find(st, k, ckey, true);
+            ei = __shfl_sync(0xffffffffu, ei, 0);
+            __syncwarp();
+            n_ent = st.n_ent[k];
+          } else if (hit) {
+            ei = idx[(home_c + f) & mask];
+          } else if (n_ent >= max_len) {
+            if (lane == 0) atomicOr(&st.status, ST_TABLE_FULL);
+          } else {                                 // insert into the empty slot, counting t
+            const int slot = (home_c + f) & mask;
+            ei = n_ent++;
+            if (lane == 0) {
+              NgEntry& en = ent[ei];
+              en.tok[0] = t;
+              en.cnt[0] = 1;
+              en.nslots = 1;
+              en.n = 1;
+              keys[slot] = ckey;
+              idx[slot] = ei;
+              st.n_ent[k] = n_ent;
+            }
+            ce = ei;
+            ens = -1;                              // counted
+          }
+          if (ei >= 0 && ens == 0) {               // an entry that exists (or the walk made): its slots
+            const NgEntry& en = ent[ei];
+            tok0 = en.tok[lane];
+            tok1 = en.tok[lane + 32];
+            cnt0 = en.cnt[lane];
+            cnt1 = en.cnt[lane + 32];
+            ens = en.nslots;
+            en_n = en.n;
+            ce = ei;
+          }
+        }
+        if (cur && ce >= 0 && ens >= 0) {
+          NgEntry& en = ent[ce];
+          const unsigned m0 = __ballot_sync(0xffffffffu, lane < ens && tok0 == t);
+          const unsigned m1 = __ballot_sync(0xffffffffu, lane + 32 < ens && tok1 == t);
+          if (m0 | m1) {
+            const int q = m0 ? __ffs(m0) - 1 : 32 + __ffs(m1) - 1;
+            const int cq = __shfl_sync(0xffffffffu, q < 32 ? cnt0 : cnt1, q & 31);
+            if (lane == 0) {
+              en.cnt[q] = cq + 1;
+              en.n = en_n + 1;
+            }
+          } else if (ens < kMaxSlots) {
+            if (lane == 0) {
+              en.tok[ens] = t;
+              en.cnt[ens] = 1;
+              en.nslots = ens + 1;
+              en.n = en_n + 1;
+            }
+          } else {
+            // evict the lowest count, lowest slot index on ties
+            int bc = cnt0, bi = lane;
+            if (cnt1 < bc) {
+              bc = cnt1;
+              bi = lane + 32;
+            }
+#pragma unroll
+            for (int off = 16; off; off >>= 1) {
+              const int oc = __shfl_xor_sync(0xffffffffu, bc, off);
+              const int oi = __shfl_xor_sync(0xffffffffu, bi, off);
+              if (oc < bc || (oc == bc && oi < bi)) {
+                bc = oc;
+                bi = oi;
+              }
+            }
+            if (lane == 0) {
+              en.n = en_n + 1 - bc;
+              en.tok[bi] = t;
+              en.cnt[bi] = 1;
+            }
+          }
+        }
+        // the next prediction's context (t appended)
+        int nx = -1;
+        if (nxt) {
+          if (cur && nkey == ckey) {
+            nx = ce;                               // the context just counted (-1: its table is full)
+          } else {
+            bool hit = false;
+            const int f = ng_resolve(kn, in, nkey, &hit);
+            if (f < 0) {
+              if (lane == 0) nx = ng_find(st, k, nkey, false);
+              nx = __shfl_sync(0xffffffffu, nx, 0);
+            } else if (hit) {
+              nx = __shfl_sync(0xffffffffu, in_n, f);
+            }
+          }
+        }
+        ce = nx;
+      }
     }
+    __syncthreads();                               // the orders' counts of this prediction are in shared memory
+    if (warp == 3 && lane == 0) {
+      float nk[kMaxOrder], coef[kMaxOrder], cu;
+      bool has[kMaxOrder];
+      NgSnap& o = out[r];
+      for (int q = 0; q < kMaxOrder; ++q) {
+        has[q] = q < D.order && s_n[r & 1][q] >= 0;
+        nk[q] = has[q] ? (float)s_n[r & 1][q] : 0.f;
+        o.ns[q] = has[q] ? s_ns[r & 1][q] : 0;
+      }
+      ng_weights(nk, has, N, D.V, coef, cu);
+      for (int q = 0; q < kMaxOrder; ++q) o.coef[q] = coef[q];
+      o.ns[3] = 0;
+      o.coef[3] = 0.f;
+      o.cu = cu;
+    }
+    if (!tok_ok) break;                            // flagged by the vocabulary pass
+    N += 1;
+    h0 = h1;
+    h1 = h2;
+    h2 = t;
     ++n_coded;
-    __syncthreads();                               // history and N are final for the next position
+  }
+  // the stream's N-gram bookkeeping for the next chunk or step
+  if (r > 0) {
+    if (k < kMaxOrder && lane == 0) st.ctx_ent[k] = ce;
+    if (threadIdx.x == 0) {
+      st.N = N;
+      st.hist[0] = h0;
+      st.hist[1] = h1;
+      st.hist[2] = h2;
+    }
   }
 }
 
@@ -1756,6 +1968,7 @@ cudaError_t launch_vocab_seq(const Dims& D, const Batch& b, const VocabIO& io, i
 cudaError_t launch_ngram_seq(const Dims& D, const Batch& b, int m, const int32_t* nb_step, const int32_t* obs_step,
                              const int32_t* p0, NgSnap* snap, cudaStream_t s) {
   if (D.order <= 0 || b.Bmax < 1) return cudaSuccess;
+  if (m > kSeqMax) return cudaErrorInvalidValue;
   return launch_kernel(k_ngram_seq, dim3(b.Bmax), dim3(128), 0, s, false, D, b, m, b.Bmax, nb_step, obs_step,
                        b.z_idx, p0, snap);
 }
