@@ -71,6 +71,10 @@ static bool tc_encode_operand(const TcMat& t, CUtensorMap* m, const void* x, int
 
 }  // namespace
 
+// Sets of the buffers a prefill chunk's forward hands to its vocabulary
+// passes (logits, tokens, N-gram states).
+constexpr int kCodeSets = 3;
+
 struct nc_ctx {
   nc_config cfg{};
   Dims D{};
@@ -98,18 +102,20 @@ struct nc_ctx {
   int32_t* f_pos = nullptr;
   int32_t* f_tok = nullptr;
   int32_t* d_nB_fwd = nullptr;       // forward rows
-  // what a chunk's forward hands to its vocabulary passes, in two sets: chunk
-  // c uses set c & 1 while the passes of chunk c - 1 still read the other
-  int32_t* d_zidx[2] = {};           // [max_streams] first forward row of each stream
-  int32_t* f_obs[2] = {};            // [P] observed token of (position, stream)
-  int32_t* f_nb[2] = {};             // [P] active streams per position
-  float* zrows[2] = {};              // [P][V] logits of the forward rows
-  NgSnap* snap[2] = {};              // [P] N-gram state of each (stream, position) prediction
-  int32_t* d_p0 = nullptr;           // [3] first position of each set's chunk; [2] the next chunk's
+  // what a chunk's forward hands to its vocabulary passes (its coding set):
+  // chunk c uses set c & 1 while the passes of chunk c - 1 still read the
+  // other; with two forward buffer sets, set c mod 3, so that chunk c + 2's
+  // forward need not wait for chunk c's passes
+  int32_t* d_zidx[kCodeSets] = {};   // [max_streams] first forward row of each stream
+  int32_t* f_obs[kCodeSets] = {};    // [P] observed token of (position, stream)
+  int32_t* f_nb[kCodeSets] = {};     // [P] active streams per position
+  float* zrows[kCodeSets] = {};      // [P][V] logits of the forward rows
+  NgSnap* snap[kCodeSets] = {};      // [P] N-gram state of each (stream, position) prediction
+  int32_t* d_p0 = nullptr;           // [4]: [0..2] first position of each set's chunk; [3] the next chunk's
   cudaStream_t side = nullptr;       // the N-gram pass of a chunk runs here beside its forward
   cudaStream_t vstream = nullptr;    // the vocabulary passes, beside the next chunk's forward
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_done = nullptr;
-  cudaEvent_t ev_fwd[2] = {}, ev_voc[2] = {};
+  cudaEvent_t ev_fwd[kCodeSets] = {}, ev_voc[kCodeSets] = {};
   uint32_t* cdf = nullptr;
   int32_t* d_slots = nullptr;
   int32_t* d_nB = nullptr;
@@ -353,8 +359,8 @@ extern "C" void nc_ctx_destroy(nc_ctx* ctx) {
   if (ctx->pass_graph) cudaGraphExecDestroy(ctx->pass_graph);
   cudaFree(ctx->enc_tok);
   cudaFree(ctx->enc_iv);
-  for (cudaEvent_t e : {ctx->ev_fork, ctx->ev_join, ctx->ev_done, ctx->ev_fwd[0], ctx->ev_fwd[1], ctx->ev_voc[0],
-                        ctx->ev_voc[1], ctx->ev_prep[0], ctx->ev_prep[1]})
+  for (cudaEvent_t e : {ctx->ev_fork, ctx->ev_join, ctx->ev_done, ctx->ev_fwd[0], ctx->ev_fwd[1], ctx->ev_fwd[2],
+                        ctx->ev_voc[0], ctx->ev_voc[1], ctx->ev_voc[2], ctx->ev_prep[0], ctx->ev_prep[1]})
     if (e) cudaEventDestroy(e);
   for (auto& v : ctx->ev_layer)
     for (cudaEvent_t e : v)
@@ -431,6 +437,13 @@ static int tc_setup(nc_ctx* ctx) {
       ctx->ev_layer[k].assign(D.n_layers, nullptr);
       for (auto& e : ctx->ev_layer[k]) NC_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
     }
+    // the third coding set
+    if (dalloc(ctx, &ctx->d_zidx[2], (size_t)ctx->cfg.max_streams * 4) ||
+        dalloc(ctx, &ctx->zrows[2], P * D.V * 4) || dalloc(ctx, &ctx->f_obs[2], P * 4) ||
+        dalloc(ctx, &ctx->f_nb[2], P * 4) || (D.order > 0 && dalloc(ctx, &ctx->snap[2], P * sizeof(NgSnap))))
+      return fail(ctx, NC_ENOMEM, "third coding set");
+    NC_TRY(cudaEventCreateWithFlags(&ctx->ev_fwd[2], cudaEventDisableTiming));
+    NC_TRY(cudaEventCreateWithFlags(&ctx->ev_voc[2], cudaEventDisableTiming));
     ctx->n_fs = 2;
   }
   auto add = [&](const Mat& m) {
@@ -1385,12 +1398,14 @@ static int encode_prefill(nc_ctx* ctx, int n, int m0, const int32_t* tok_dev, co
   }
   auto start_at = [&](int64_t a) -> int64_t { return a < D.L ? 0 : ((a - D.L) / D.C + 1) * D.C; };
   // Two forward buffer sets: the whole pass is one captured graph.  Chunk
-  // c's forward runs on the stream of set c & 1 (s, s2) beside chunk c - 1's,
-  // each layer's append after chunk c - 1's attention of that layer; the
-  // N-gram passes run in chunk order on the side stream and the vocabulary
-  // passes in chunk order on vstream; set c & 1 is reused by chunk c + 2
-  // after chunk c's vocabulary passes.  The graph is kept for the next call
-  // with the same chunk plan and buffers.
+  // c's forward runs on the stream of forward set c & 1 (s, s2) beside chunk
+  // c - 1's, each layer's append after chunk c - 1's attention of that layer;
+  // the N-gram passes run in chunk order on the side stream and the
+  // vocabulary passes in chunk order on vstream.  Chunk c hands its logits,
+  // tokens and N-gram states to its passes in coding set c mod 3, which
+  // chunk c + 3 reuses after chunk c's vocabulary passes: a forward may run
+  // two chunks ahead of the passes.  The graph is kept for the next call with
+  // the same chunk plan and buffers.
   if (piped && ctx->n_fs == 2) {
     std::vector<std::pair<int, int>> plan;
     {
@@ -1427,24 +1442,24 @@ static int encode_prefill(nc_ctx* ctx, int n, int m0, const int32_t* tok_dev, co
       Dims Dv = D;
       Dv.pdl = 0;                                   // the vocabulary passes: see below
       for (size_t c = 0; c < plan.size() && e == cudaSuccess; ++c) {
-        const int mc = plan[c].first, ne = plan[c].second, set = (int)(c & 1);
+        const int mc = plan[c].first, ne = plan[c].second, set = (int)(c & 1), cs = (int)(c % kCodeSets);
         cudaStream_t sc = fst[set];
         const nc_ctx::FwdSet& F = ctx->fs[set];
-        if (c >= 2) e = cudaStreamWaitEvent(sc, ctx->ev_voc[set], 0);      // chunk c - 2's passes read set
+        if (c >= kCodeSets) e = cudaStreamWaitEvent(sc, ctx->ev_voc[cs], 0);   // chunk c - 3's passes read cs
         if (c >= 1 && e == cudaSuccess) e = cudaStreamWaitEvent(sc, ctx->ev_prep[set ^ 1], 0);   // positions in order
         Batch b = make_batch(ctx);
         b.Bmax = ne;
-        if (e == cudaSuccess) e = launch_chunk_start(ctx->d_p0, set, mc, sc);
-        int32_t* p0 = ctx->d_p0 + set;
+        if (e == cudaSuccess) e = launch_chunk_start(ctx->d_p0, cs, mc, sc);
+        int32_t* p0 = ctx->d_p0 + cs;
         if (e == cudaSuccess)
           e = launch_prepare_prefill(b, ne, mc, D.V, p0, tok_dev, offs_dev, lens_dev, F.f_slots, F.f_pos, F.f_tok,
-                                     F.nB_fwd, ctx->f_obs[set], ctx->f_nb[set], ctx->d_zidx[set], sc);
+                                     F.nB_fwd, ctx->f_obs[cs], ctx->f_nb[cs], ctx->d_zidx[cs], sc);
         if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_prep[set], sc);
-        const Batch br = vocab_batch(ne, set);
-        const bool ng = ctx->snap[set] != nullptr;
+        const Batch br = vocab_batch(ne, cs);
+        const bool ng = ctx->snap[cs] != nullptr;
         if (ng && e == cudaSuccess) e = cudaStreamWaitEvent(ctx->side, ctx->ev_prep[set], 0);
         if (ng && e == cudaSuccess)
-          e = launch_ngram_seq(D, br, mc, ctx->f_nb[set], ctx->f_obs[set], p0, ctx->snap[set], ctx->side);
+          e = launch_ngram_seq(D, br, mc, ctx->f_nb[cs], ctx->f_obs[cs], p0, ctx->snap[cs], ctx->side);
         if (ng && e == cudaSuccess) e = cudaEventRecord(ctx->ev_join, ctx->side);
         Batch f = make_batch(ctx);
         f.slots = F.f_slots;
@@ -1453,7 +1468,7 @@ static int encode_prefill(nc_ctx* ctx, int n, int m0, const int32_t* tok_dev, co
         f.Bmax = ne * mc;
         f.pos = F.f_pos;
         f.tok = F.f_tok;
-        f.z_out = ctx->zrows[set];
+        f.z_out = ctx->zrows[cs];
         f.pm = mc;
         LayerSync sync;
         sync.wait = c >= 1 ? ctx->ev_layer[set ^ 1].data() : nullptr;
@@ -1463,13 +1478,13 @@ static int encode_prefill(nc_ctx* ctx, int n, int m0, const int32_t* tok_dev, co
         sync.no_pdl = true;
         StepMarks none;
         if (e == cudaSuccess) e = launch_model_tc(ctx, f, none, set, sc, sync);
-        if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_fwd[set], sc);
-        if (e == cudaSuccess) e = cudaStreamWaitEvent(vs, ctx->ev_fwd[set], 0);
+        if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_fwd[cs], sc);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(vs, ctx->ev_fwd[cs], 0);
         if (ng && e == cudaSuccess) e = cudaStreamWaitEvent(vs, ctx->ev_join, 0);
         // without PDL: it would sit on its SMs while the previous passes run
         if (e == cudaSuccess)
-          e = launch_vocab_seq(Dv, br, io, mc, ctx->zrows[set], ctx->f_nb[set], ctx->f_obs[set], ctx->snap[set], vs);
-        if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_voc[set], vs);
+          e = launch_vocab_seq(Dv, br, io, mc, ctx->zrows[cs], ctx->f_nb[cs], ctx->f_obs[cs], ctx->snap[cs], vs);
+        if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_voc[cs], vs);
       }
       // join every stream back into s
       fork(ctx->s2, s, ctx->ev_prep[0]);

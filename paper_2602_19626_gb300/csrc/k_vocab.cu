@@ -1685,14 +1685,14 @@ __global__ void k_prepare_encode(Batch b, int n_streams, const int32_t* tok_flat
   }
 }
 
-// The next prefill chunk's first position: p0s[par] = p0s[2], p0s[2] += m.
+// The next prefill chunk's first position: p0s[par] = p0s[3], p0s[3] += m (par < 3).
 __global__ void k_chunk_start(int32_t* p0s, int par, int m) {
   pdl_wait();
   pdl_trigger();
   if (threadIdx.x == 0) {
-    const int p0 = p0s[2];
+    const int p0 = p0s[3];
     p0s[par] = p0;
-    p0s[2] = p0 + m;
+    p0s[3] = p0 + m;
   }
 }
 
