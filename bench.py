@@ -65,6 +65,10 @@ WORKLOADS = {
     # tokens, 4,096 forward rows (128 positions per stream), 1.5 GB of KV
     "prof_tc_32x256": dict(shape=S.FULL, fmt="bf16", seed=2, n_streams=32, length=256, path="tc",
                            prefill_rows=4096),
+    # a small case of the single-stream prefill for profiling: the headline's
+    # stream and kernels with 512 forward rows (about 1 GB on the device)
+    "prof_single_p512": dict(shape=S.FULL, fmt="bf16", seed=1, n_streams=1, length=8192, path="tc",
+                             prefill_rows=512),
     # FP8 E4M3 weights, 1,024 streams x 4,096 tokens (first 256 tokens per stream)
     "fp8_tc_1024_256": dict(shape=S.FULL, fmt="fp8", seed=4, n_streams=1024, length=4096, cap=256, path="tc",
                             prefill_rows=4096),
@@ -379,13 +383,21 @@ def prefill_positions(wl, n_streams: int, max_len: int) -> int:
 
 
 def dominant_kind(trace, wl, n_streams: int, max_len: int):
-    """The traced kernel kind the roofline reports, and the kinds left out.
-    With the prefill, a chunk's N-gram pass runs beside its forward and its
-    vocabulary loop beside the next chunk's forward (the trace runs them in
-    order): the dominant kind is taken on the forward, the critical path of
-    the timed run."""
-    beside = ["ngram_update", "vocab"] if prefill_positions(wl, n_streams, max_len) >= 2 else []
-    dom = max([k for k in trace if k["name"] not in beside] or trace, key=lambda k: k["ms"])
+    """The traced kernel kind the roofline reports, and the kinds that run
+    beside it.  The dominant kind is the one with the largest share of the
+    trace.  With the prefill, a chunk's N-gram pass runs beside its forward,
+    and its vocabulary loop beside the next two chunks' forwards: when the
+    loop dominates, it is the chain that paces the timed run and the forward
+    kinds and the N-gram pass run beside it; when a forward kind dominates,
+    the loop and the N-gram pass run beside the forwards."""
+    dom = max(trace, key=lambda k: k["ms"])
+    if prefill_positions(wl, n_streams, max_len) < 2:
+        return dom, []
+    loop = {"ngram_update", "vocab"}
+    if dom["name"] in loop:
+        beside = [k["name"] for k in trace if k["name"] != dom["name"] and k["launches"]]
+    else:
+        beside = sorted(loop)
     return dom, beside
 
 
@@ -469,6 +481,12 @@ def run_gpu(args, wl):
         roofline["share"] = dom["ms"] / tot_ms
         roofline["beside_critical_path"] = beside
         roofline["traffic"] = ncu_traffic(dom["name"], args.workload)
+        # the largest kernel of the model forward, beside the loop that paces the run
+        fwd = [k for k in trace if k["name"] not in ("vocab", "ngram_update", "prepare") and k["launches"]]
+        if dom["name"] in ("vocab", "ngram_update") and fwd:
+            fk = max(fwd, key=lambda k: k["ms"])
+            roofline["forward"] = roofline_of(fk, wl.get("path", "gemv"), wl["fmt"], n_sm, 2070.0)
+            roofline["forward"]["share"] = fk["ms"] / tot_ms
         kernels = {k["name"]: {"launches": k["launches"], "ms": round(k["ms"], 3),
                                "share": round(k["ms"] / tot_ms, 4),
                                "GBps": round(k["bytes"] / (k["ms"] / 1000.0) / 1e9, 1) if k["ms"] > 0 else None,

@@ -1565,14 +1565,20 @@ static int encode_prefill(nc_ctx* ctx, int n, int m0, const int32_t* tok_dev, co
         double by = fwd[kd], fo = ffl[kd];
         if (i >= fwd_marks) {                       // the chunk's vocabulary passes
           by = fo = 0;
+          int live = 0;
           for (int64_t a = p; a < p + m; ++a) {
             int act = 0;
             for (int j = 0; j < n; ++j) act += lens_h[j] > a;
+            live = std::max(live, act);
             double per[TK_COUNT], pfl[TK_COUNT];
             step_cost(ctx, act, 0.0, 0.0, per, pfl);
-            by += per[kd];
+            // the loop keeps a stream's bias and unigram counts in registers
+            // over the chunk: per position it reads the logits and the
+            // N-gram state and writes the interval
+            by += kd == TK_VOCAB ? act * (D.V * 4.0 + sizeof(NgSnap) + 8.0) : per[kd];
             fo += pfl[kd];
           }
+          if (kd == TK_VOCAB) by += live * D.V * 16.0;   // bias and counts read and written once
         }
         trace->ms[kd] += ms;
         trace->launches[kd] += 1;

@@ -1,7 +1,7 @@
 """bench.py's reporting logic on CPU: the positions per forward it reports,
-the dominant kernel it takes for the roofline (the forward's, when the
-vocabulary loop and the N-gram pass run beside it), and the bound chosen from
-the arithmetic intensity."""
+the dominant kernel it takes for the roofline (the largest share of the
+trace, with the kinds that run beside it), and the bound chosen from the
+arithmetic intensity."""
 import bench
 
 
@@ -17,12 +17,18 @@ def test_positions_per_forward():
 
 
 def test_dominant_kind_on_the_critical_path():
-    trace = [kind("vocab", 37.0), kind("ngram_update", 24.0), kind("attn", 22.0), kind("gemv_gate_up", 13.0)]
     wl = bench.WORKLOADS["full_bf16_single"]
+    # the vocabulary loop paces the pass: the forwards and the N-gram pass run beside it
+    trace = [kind("vocab", 26.0), kind("ngram_update", 8.0), kind("attn", 10.0), kind("gemv_gate_up", 8.0)]
+    dom, beside = bench.dominant_kind(trace, wl, 1, 8192)
+    assert dom["name"] == "vocab" and set(beside) == {"ngram_update", "attn", "gemv_gate_up"}
+    # a forward kind that dominates: the loop and the N-gram pass run beside the forwards
+    trace = [kind("vocab", 9.0), kind("ngram_update", 8.0), kind("attn", 22.0), kind("gemv_gate_up", 13.0)]
     dom, beside = bench.dominant_kind(trace, wl, 1, 8192)
     assert dom["name"] == "attn" and set(beside) == {"vocab", "ngram_update"}
+    # one position per step: every kernel is on the chain
     dom, beside = bench.dominant_kind(trace, dict(wl, prefill_rows=0), 1, 8192)
-    assert dom["name"] == "vocab" and beside == []
+    assert dom["name"] == "attn" and beside == []
 
 
 def test_bound_from_intensity():

@@ -147,3 +147,49 @@ def test_bf16_cache_ring_wrap_windows(nc, path, ctx_len, slide):
     ref_iv = intervals(nc, shape, w, "bf16", path, [toks], 0, 1)
     got_iv = intervals(nc, shape, w, "bf16", path, [toks], 4 * slide, 1)
     assert np.array_equal(got_iv, ref_iv)
+
+
+_M64 = (1 << 64) - 1
+
+
+def _mix64(x: int) -> int:
+    """The N-gram index's home-slot hash (a 64-bit finaliser), to build keys
+    whose home slots crowd together."""
+    x ^= x >> 33
+    x = (x * 0xFF51AFD7ED558CCD) & _M64
+    x ^= x >> 33
+    x = (x * 0xC4CEB9FE1A85EC53) & _M64
+    x ^= x >> 33
+    return x
+
+
+@pytest.mark.parametrize("fmt,path", [("fp32", "gemv"), ("bf16", "tc")])
+def test_prefill_ngram_long_probes(nc, fmt, path):
+    """The prefill's N-gram pass reads 32 index slots per load; a key whose
+    probe runs past them takes the one-slot-at-a-time walk (look-up and
+    insert).  48 distinct tokens whose order-1 keys (the token ids) home in
+    4 neighbouring slots of the stream's 1,024-slot index fill a run of 48
+    slots, so inserting or finding the later ones probes past 32 slots; the
+    intervals still equal those of one update per step."""
+    shape, seed = S.SMALL, 12
+    n = 300
+    cap = 1 << (2 * n - 1).bit_length()          # the index capacity for an n-token stream
+    assert cap == 1024
+    home = 100
+    crowd = [t for t in range(1, shape.vocab) if home <= (_mix64(t) & (cap - 1)) < home + 4][:48]
+    assert len(crowd) == 48
+    # linear probing in insertion order: some key sits more than 32 slots past its home
+    used, far = set(), 0
+    for t in crowd:
+        h = _mix64(t) & (cap - 1)
+        d = 0
+        while (h + d) % cap in used:
+            d += 1
+        used.add((h + d) % cap)
+        far = max(far, d)
+    assert far > 32
+    toks = np.array((crowd * (n // len(crowd) + 1))[:n], dtype=np.int32)
+    w = S.flat_weights(shape, seed)
+    ref = intervals(nc, shape, w, fmt, path, [toks], 0, 1)
+    got = intervals(nc, shape, w, fmt, path, [toks], 256, 1)
+    assert np.array_equal(got, ref)
