@@ -18,6 +18,8 @@ slow and written to be checked against the paper by eye:
 * ``container`` - NC05-style container (Sec. 3.12).
 * ``chunking``  - file-level split into chunks at line ends (Sec. 3.11), on
                   token ids.
+* ``hybrid``    - NC06 hybrid binary format (Sec. 3.10): text / binary
+                  segmentation, the binary blob and the container layout.
 * ``compress``  - the compression / decompression loop (Algorithm 1).
 * ``numerics``  - bf16 / fp8-e4m3 rounding used to derive the dequantised
                   weight variants from the FP32 canonical weights.

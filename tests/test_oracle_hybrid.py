@@ -1,0 +1,112 @@
+"""NC06 hybrid segmentation and container (oracle/hybrid.py, Sec. 3.10, Sec.
+3.12) against what the four rules fix: hand-worked inputs for each rule,
+one that decides the order in which rules 2 and 3 apply, the character
+classes of rule 1, and invariants on random structured inputs (the runs
+cover the input and alternate, text runs hold at least 64 bytes, binary runs
+under 64 bytes only without text, and splitting then joining gives the
+input back); the blob's size rule and the container layout round trip."""
+import gzip
+import lzma
+
+import numpy as np
+
+from oracle import hybrid as H
+
+T, B = H.TEXT, H.BINARY
+
+
+def txt(n):
+    return b"a" * n
+
+
+def bin_(n):
+    return b"\x00" * n
+
+
+def test_rule_1_classes():
+    assert all(H.is_text_byte(b) for b in range(32, 127))
+    assert all(H.is_text_byte(b) for b in (9, 10, 13))
+    assert not any(H.is_text_byte(b) for b in (0, 8, 11, 12, 14, 31, 127, 128, 255))
+    assert H.segment(b"\t\n\r" + txt(61)) == [(T, 64)]
+
+
+def test_rule_2_short_text_demoted():
+    assert H.segment(txt(64)) == [(T, 64)]
+    assert H.segment(txt(63)) == [(B, 63)]
+    assert H.segment(bin_(200) + txt(30) + bin_(200)) == [(B, 430)]
+
+
+def test_rule_3_gaps_bridged_before_demotion():
+    # a gap of 8 joins two 40-byte text runs into one run of 88 that rule 2 keeps
+    assert H.segment(txt(40) + bin_(8) + txt(40)) == [(T, 88)]
+    # a gap of 9 does not: both runs are too short and become binary
+    assert H.segment(txt(40) + bin_(9) + txt(40)) == [(B, 89)]
+    # a one-byte DEL inside text is a gap
+    assert H.segment(txt(32) + b"\x7f" + txt(31)) == [(T, 64)]
+    # a gap at either end is not between two text runs
+    assert H.segment(bin_(3) + txt(10)) == [(B, 13)]
+
+
+def test_rule_4_small_binary_absorbed():
+    assert H.segment(bin_(10) + txt(100) + bin_(10)) == [(T, 120)]
+    assert H.segment(txt(100) + bin_(63) + txt(100)) == [(T, 263)]
+    assert H.segment(txt(100) + bin_(64) + txt(100)) == [(T, 100), (B, 64), (T, 100)]
+    assert H.segment(bin_(64) + txt(100)) == [(B, 64), (T, 100)]
+    assert H.segment(bin_(5)) == [(B, 5)]                   # no text to be absorbed into
+    assert H.segment(b"") == []
+
+
+def _random_input(rng, n_runs):
+    parts = []
+    for _ in range(n_runs):
+        n = int(rng.integers(1, 120))
+        if rng.random() < 0.5:
+            parts.append(bytes(rng.choice(np.r_[9, 10, 13, 32:127], n).astype(np.uint8)))
+        else:
+            parts.append(bytes(rng.choice(np.r_[0:9, 11, 12, 14:32, 127:256], n).astype(np.uint8)))
+    return b"".join(parts)
+
+
+def test_invariants_random():
+    rng = np.random.default_rng(5)
+    for trial in range(400):
+        data = _random_input(rng, int(rng.integers(0, 12)))
+        runs = H.segment(data)
+        assert sum(n for _, n in runs) == len(data)
+        assert all(n > 0 for _, n in runs)
+        assert all(runs[i][0] != runs[i + 1][0] for i in range(len(runs) - 1))
+        assert all(n >= H.MIN_TEXT for k, n in runs if k == T)
+        assert all(n >= H.MIN_BINARY or len(runs) == 1 for k, n in runs if k == B)
+        texts, blob = H.split(data, runs)
+        assert H.join(runs, texts, blob) == data
+        assert len(blob) == sum(n for k, n in runs if k == B)
+        # all text-like input: one text run, or one binary run when short
+        if data and all(H.is_text_byte(b) for b in data):
+            assert runs == [(T if len(data) >= 64 else B, len(data))]
+
+
+def test_blob_size_rule():
+    small = b"ab" * 2000                                     # 4,000 bytes: gzip
+    m, s = H.pack_blob(small)
+    assert m == H.GZIP and gzip.decompress(s) == small
+    big = b"ab" * 2048                                       # 4,096 bytes: LZMA
+    m, s = H.pack_blob(big)
+    assert m == H.LZMA and lzma.decompress(s) == big
+    noise = bytes(np.random.default_rng(1).integers(0, 256, 5000, dtype=np.uint8))
+    assert H.pack_blob(noise) == (H.RAW, noise)              # compression does not help
+    assert H.pack_blob(b"") == (H.RAW, b"")
+    for blob in (small, big, noise, b""):
+        assert H.unpack_blob(*H.pack_blob(blob)) == blob
+
+
+def test_container_round_trip():
+    data = bin_(100) + txt(300) + bin_(70) + txt(80)
+    runs = H.segment(data)
+    texts, blob = H.split(data, runs)
+    m, s = H.pack_blob(blob)
+    buf = H.pack(3, 0x3C00, runs, m, s, b"NC05-stand-in")
+    assert buf[:4] == b"NC06" and buf[4] == 1 and buf[5] == 3
+    assert len(buf) == 12 + 5 * len(runs) + 5 + len(s) + len(b"NC05-stand-in")
+    flags, tau, runs2, m2, s2, tc = H.unpack(buf)
+    assert (flags, tau, runs2, m2, s2, tc) == (3, 0x3C00, runs, m, s, b"NC05-stand-in")
+    assert H.join(runs2, texts, H.unpack_blob(m2, s2)) == data
