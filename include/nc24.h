@@ -377,6 +377,44 @@ int nc_ans_decode(const uint8_t* data, size_t nbytes, const uint32_t* cdfs, int 
 int nc_split_chunks(const int32_t* tokens, int64_t n, const uint8_t* is_boundary, int V, int n_chunks,
                     int64_t* cuts, int* n_chunks_out);
 
+/* NC06 hybrid binary format (Sec. 3.10): the runs of text (kind 0) and
+ * binary (kind 1) bytes of an arbitrary byte string, alternating.  Bytes are
+ * text-like when printable ASCII (32..126), tab, LF or CR; binary gaps of at
+ * most 8 bytes between two text runs become text; text runs shorter than 64
+ * bytes become binary; binary runs shorter than 64 bytes next to a text run
+ * become text (the four rules applied in the order 1, 3, 2, 4; adjacent runs
+ * of one kind merge after each).  Text runs are coded as the streams of one
+ * NC05 container, binary runs concatenated into one blob.
+ *   data HOST uint8[n]; kinds HOST uint8[cap], lens HOST int64[cap] receive
+ *   the runs in order, *n_runs their count.  cap = 0 queries the count only.
+ * Errors: NC_EINVAL (NULL pointers, n < 0, cap below the count). */
+int nc_hybrid_segments(const uint8_t* data, int64_t n, uint8_t* kinds, int64_t* lens, int64_t cap,
+                       int64_t* n_runs);
+
+/* Assemble an NC06 container into HOST out (size query when out is NULL,
+ * as nc_encode): "NC06", version 1, a flags byte and the temperature
+ * (binary16), the run count (u32), per run its kind (u8) and length (u32),
+ * the binary blob's method (u8: 0 raw, 1 gzip, 2 LZMA; the caller
+ * compresses) and stored length (u32), the stored blob, then `text`, the
+ * NC05 container of the text runs' streams (nc_encode), empty when there is
+ * no text run.  The flags byte and temperature are that container's (a
+ * decoder replays them); without text runs, 0 and 1.0.  Little-endian.
+ * Errors: NC_EINVAL (NULL pointers, a kind other than 0 / 1, a length
+ * outside [1, 2^32), a method other than 0..2, a blob of 2^32 bytes or more,
+ * a non-empty text that is not an NC05 container, out too small:
+ * *inout_nbytes then holds the size needed). */
+int nc_hybrid_pack(const uint8_t* kinds, const int64_t* lens, int64_t n_runs, int method, const uint8_t* stored,
+                   size_t n_stored, const uint8_t* text, size_t n_text, uint8_t* out, size_t* inout_nbytes);
+
+/* Read an NC06 container (HOST buf[n]): the runs as nc_hybrid_segments
+ * gives them (cap = 0: count only), the blob's method, the stored blob at
+ * buf[*stored_off .. + *stored_len), the text runs' NC05 container from
+ * buf[*text_off] to the end.  Errors: NC_ECORRUPT (not an NC06 version 1
+ * container, a bad run or method, a truncated section), NC_EINVAL (NULL
+ * pointers, cap below the count). */
+int nc_hybrid_parse(const uint8_t* buf, size_t n, uint8_t* kinds, int64_t* lens, int64_t cap, int64_t* n_runs,
+                    int* method, size_t* stored_off, size_t* stored_len, size_t* text_off);
+
 /* Mixed-distribution NLL L = -log(w0 p_tilde(t*) + w1 p_ng(t*)), w = softmax(theta),
  * p_tilde = softmax(z / tau + b), for n rows (the differentiable update rule).
  *   z, b, p_ng DEVICE float[n * V]; theta DEVICE float[n * 2]; target DEVICE int32[n];

@@ -20,6 +20,7 @@ one NC05 container (the caller supplies its bytes).
 
 Container (little-endian):
     "NC06", version 1 (u8), flags (u8), tau (binary16), entry count E (u32),
+    (the flags and tau of the text runs' NC05 container; 0 and 1.0 without text)
     E entries of kind (u8: 0 text, 1 binary) and length (u32),
     blob method (u8: 0 raw, 1 gzip, 2 LZMA), blob length (u32), blob,
     the text runs' NC05 container (empty when there is no text run).
@@ -107,7 +108,15 @@ def unpack_blob(method: int, stored: bytes) -> bytes:
     raise ValueError(f"unknown blob method {method}")
 
 
-def pack(flags: int, tau_half: int, runs, method: int, stored: bytes, text_container: bytes) -> bytes:
+def pack(runs, method: int, stored: bytes, text_container: bytes) -> bytes:
+    """The container; its flags byte and temperature are those of the text
+    runs' NC05 container (bytes 4 and 5..6), or 0 and 1.0 without text."""
+    if text_container:
+        if text_container[:4] != b"NC05" or len(text_container) < 9:
+            raise ValueError("the text section is not an NC05 container")
+        flags, tau_half = text_container[4], struct.unpack_from("<H", text_container, 5)[0]
+    else:
+        flags, tau_half = 0, 0x3C00                      # 1.0 in binary16
     out = bytearray(b"NC06")
     out += struct.pack("<BBHI", 1, flags, tau_half, len(runs))
     for kind, n in runs:

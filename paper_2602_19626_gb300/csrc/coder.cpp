@@ -233,6 +233,92 @@ void container_write(uint8_t* out, uint8_t flags, float tau, uint8_t path_byte,
   }
 }
 
+namespace {
+bool text_like(uint8_t b) { return (b >= 32 && b <= 126) || b == 9 || b == 10 || b == 13; }
+void merge_runs(std::vector<HybridRun>* r) {
+  std::vector<HybridRun> out;
+  for (const HybridRun& x : *r) {
+    if (x.len == 0) continue;
+    if (!out.empty() && out.back().kind == x.kind) out.back().len += x.len;
+    else out.push_back(x);
+  }
+  r->swap(out);
+}
+}  // namespace
+
+void hybrid_segments(const uint8_t* data, int64_t n, std::vector<HybridRun>* runs) {
+  std::vector<HybridRun>& r = *runs;
+  r.clear();
+  for (int64_t i = 0; i < n; ++i) {                      // rule 1: maximal runs of one class
+    const uint8_t k = text_like(data[i]) ? kRunText : kRunBinary;
+    if (!r.empty() && r.back().kind == k) ++r.back().len;
+    else r.push_back({k, 1});
+  }
+  // rule 3: a binary run with a run on both sides lies between two text runs
+  for (size_t i = 1; i + 1 < r.size(); ++i)
+    if (r[i].kind == kRunBinary && r[i].len <= 8) r[i].kind = kRunText;
+  merge_runs(runs);
+  for (HybridRun& x : r)                                 // rule 2
+    if (x.kind == kRunText && x.len < 64) x.kind = kRunBinary;
+  merge_runs(runs);
+  // rule 4, decided on the runs rule 2 left: runs alternate, so a binary run
+  // has a text neighbour unless it is the only run
+  if (r.size() > 1)
+    for (HybridRun& x : r)
+      if (x.kind == kRunBinary && x.len < 64) x.kind = kRunText;
+  merge_runs(runs);
+}
+
+size_t hybrid_size(size_t n_runs, size_t n_stored, size_t n_text) {
+  return kHybridHeaderBytes + kHybridRunBytes * n_runs + kHybridBlobBytes + n_stored + n_text;
+}
+
+void hybrid_write(uint8_t* out, uint8_t flags, uint16_t tau_half, const std::vector<HybridRun>& runs, uint8_t method,
+                  const uint8_t* stored, size_t n_stored, const uint8_t* text, size_t n_text) {
+  std::memcpy(out, "NC06", 4);
+  out[4] = 1;
+  out[5] = flags;
+  put_u16(out + 6, tau_half);
+  put_u32(out + 8, (uint32_t)runs.size());
+  size_t off = kHybridHeaderBytes;
+  for (const HybridRun& x : runs) {
+    out[off] = x.kind;
+    put_u32(out + off + 1, (uint32_t)x.len);
+    off += kHybridRunBytes;
+  }
+  out[off] = method;
+  put_u32(out + off + 1, (uint32_t)n_stored);
+  off += kHybridBlobBytes;
+  if (n_stored) std::memcpy(out + off, stored, n_stored);
+  off += n_stored;
+  if (n_text) std::memcpy(out + off, text, n_text);
+}
+
+bool hybrid_read(const uint8_t* in, size_t n, uint8_t* flags, uint16_t* tau_half, std::vector<HybridRun>* runs,
+                 uint8_t* method, size_t* stored_off, size_t* stored_len, size_t* text_off) {
+  if (!in || n < kHybridHeaderBytes + kHybridBlobBytes || std::memcmp(in, "NC06", 4) != 0 || in[4] != 1) return false;
+  *flags = in[5];
+  *tau_half = get_u16(in + 6);
+  const size_t nr = get_u32(in + 8);
+  if ((n - kHybridHeaderBytes - kHybridBlobBytes) / kHybridRunBytes < nr) return false;
+  size_t off = kHybridHeaderBytes;
+  runs->resize(nr);
+  for (size_t j = 0; j < nr; ++j) {
+    const uint8_t k = in[off];
+    const uint32_t len = get_u32(in + off + 1);
+    if (k > kRunBinary || len == 0) return false;
+    (*runs)[j] = {k, (int64_t)len};
+    off += kHybridRunBytes;
+  }
+  *method = in[off];
+  *stored_len = get_u32(in + off + 1);
+  off += kHybridBlobBytes;
+  if (*method > 2 || *stored_len > n - off) return false;
+  *stored_off = off;
+  *text_off = off + *stored_len;
+  return true;
+}
+
 bool container_read(const uint8_t* in, size_t n, uint8_t* flags, float* tau, uint8_t* path_byte,
                     std::vector<StreamRecord>* recs, std::vector<const uint8_t*>* payloads) {
   if (!in || n < kHeaderBytes + 1 || std::memcmp(in, "NC05", 4) != 0) return false;

@@ -119,4 +119,31 @@ void container_write(uint8_t* out, uint8_t flags, float tau, uint8_t path_byte,
 bool container_read(const uint8_t* in, size_t n, uint8_t* flags, float* tau, uint8_t* path_byte,
                     std::vector<StreamRecord>* recs, std::vector<const uint8_t*>* payloads);
 
+// NC06 hybrid format (Sec. 3.10).  The runs of text (kind 0) and binary
+// (kind 1) bytes of a byte string, alternating, by the four rules applied
+// in the order 1, 3, 2, 4: bytes classed text-like when printable ASCII
+// (32..126), tab, LF or CR; binary gaps of at most 8 bytes between two text
+// runs become text; text runs under 64 bytes become binary; binary runs
+// under 64 bytes next to a text run become text.  Adjacent runs of one kind
+// merge after each rule.  (Listed order would make rule 3 a no-op: every gap
+// it bridges is a binary run under 64 bytes next to text.)
+constexpr uint8_t kRunText = 0, kRunBinary = 1;
+struct HybridRun {
+  uint8_t kind;
+  int64_t len;
+};
+void hybrid_segments(const uint8_t* data, int64_t n, std::vector<HybridRun>* runs);
+
+// NC06 container: "NC06", version 1, flags, tau (binary16), run count (u32),
+// per run kind (u8) and length (u32), the binary blob's method (u8: 0 raw,
+// 1 gzip, 2 LZMA) and stored length (u32), the stored blob, then the text
+// runs' NC05 container to the end.  Little-endian.
+constexpr size_t kHybridHeaderBytes = 12, kHybridRunBytes = 5, kHybridBlobBytes = 5;
+size_t hybrid_size(size_t n_runs, size_t n_stored, size_t n_text);
+void hybrid_write(uint8_t* out, uint8_t flags, uint16_t tau_half, const std::vector<HybridRun>& runs, uint8_t method,
+                  const uint8_t* stored, size_t n_stored, const uint8_t* text, size_t n_text);
+// false on malformed input; offsets are into `in`
+bool hybrid_read(const uint8_t* in, size_t n, uint8_t* flags, uint16_t* tau_half, std::vector<HybridRun>* runs,
+                 uint8_t* method, size_t* stored_off, size_t* stored_len, size_t* text_off);
+
 }  // namespace nc

@@ -2231,6 +2231,68 @@ extern "C" int nc_split_chunks(const int32_t* tokens, int64_t n, const uint8_t* 
   return NC_OK;
 }
 
+extern "C" int nc_hybrid_segments(const uint8_t* data, int64_t n, uint8_t* kinds, int64_t* lens, int64_t cap,
+                                  int64_t* n_runs) {
+  if ((!data && n > 0) || n < 0 || !n_runs || cap < 0 || (cap > 0 && (!kinds || !lens))) return NC_EINVAL;
+  std::vector<HybridRun> runs;
+  hybrid_segments(data, n, &runs);
+  *n_runs = (int64_t)runs.size();
+  if (cap == 0) return NC_OK;                                  // size query
+  if (cap < (int64_t)runs.size()) return NC_EINVAL;
+  for (size_t j = 0; j < runs.size(); ++j) {
+    kinds[j] = runs[j].kind;
+    lens[j] = runs[j].len;
+  }
+  return NC_OK;
+}
+
+extern "C" int nc_hybrid_pack(const uint8_t* kinds, const int64_t* lens, int64_t n_runs, int method,
+                              const uint8_t* stored, size_t n_stored, const uint8_t* text, size_t n_text,
+                              uint8_t* out, size_t* inout_nbytes) {
+  if (!inout_nbytes || n_runs < 0 || n_runs > (int64_t)UINT32_MAX || (n_runs > 0 && (!kinds || !lens)) ||
+      method < 0 || method > 2 || n_stored > UINT32_MAX || (n_stored && !stored) || (n_text && !text))
+    return NC_EINVAL;
+  // the flags byte and temperature of the text runs' container (NC05: bytes 4 and 5..6)
+  const bool nc05 = n_text >= kHeaderBytes && std::memcmp(text, "NC05", 4) == 0;
+  if (n_text && !nc05) return NC_EINVAL;
+  const uint8_t flags = nc05 ? text[4] : 0;
+  const uint16_t tau = nc05 ? (uint16_t)(text[5] | (text[6] << 8)) : float_to_half_bits(1.0f);
+  std::vector<HybridRun> runs((size_t)n_runs);
+  for (int64_t j = 0; j < n_runs; ++j) {
+    if (kinds[j] > kRunBinary || lens[j] < 1 || lens[j] > (int64_t)UINT32_MAX) return NC_EINVAL;
+    runs[j] = {kinds[j], lens[j]};
+  }
+  const size_t need = hybrid_size(runs.size(), n_stored, n_text);
+  if (!out || *inout_nbytes < need) {
+    *inout_nbytes = need;
+    return out ? NC_EINVAL : NC_OK;
+  }
+  hybrid_write(out, flags, tau, runs, (uint8_t)method, stored, n_stored, text, n_text);
+  *inout_nbytes = need;
+  return NC_OK;
+}
+
+extern "C" int nc_hybrid_parse(const uint8_t* buf, size_t n, uint8_t* kinds, int64_t* lens, int64_t cap,
+                               int64_t* n_runs, int* method, size_t* stored_off, size_t* stored_len,
+                               size_t* text_off) {
+  if (!buf || !n_runs || cap < 0 || (cap > 0 && (!kinds || !lens)) || !method || !stored_off || !stored_len ||
+      !text_off)
+    return NC_EINVAL;
+  uint8_t flags = 0, m = 0;
+  uint16_t tau = 0;
+  std::vector<HybridRun> runs;
+  if (!hybrid_read(buf, n, &flags, &tau, &runs, &m, stored_off, stored_len, text_off)) return NC_ECORRUPT;
+  *n_runs = (int64_t)runs.size();
+  *method = m;
+  if (cap == 0) return NC_OK;
+  if (cap < (int64_t)runs.size()) return NC_EINVAL;
+  for (size_t j = 0; j < runs.size(); ++j) {
+    kinds[j] = runs[j].kind;
+    lens[j] = runs[j].len;
+  }
+  return NC_OK;
+}
+
 extern "C" int nc_ans_encode(const uint32_t* lo, const uint32_t* hi, int64_t n, int log2_total, uint8_t* out,
                              size_t* inout_nbytes) {
   if ((!lo || !hi) && n > 0) return NC_EINVAL;

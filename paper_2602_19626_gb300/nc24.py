@@ -89,6 +89,10 @@ _SIGS = {
     "nc_ac_decode": (C.c_int, [_P, C.c_uint64, _P, C.c_int, C.c_int64, C.c_int, _P]),
     "nc_ans_encode": (C.c_int, [_P, _P, C.c_int64, C.c_int, _P, _SZP]),
     "nc_split_chunks": (C.c_int, [_P, C.c_int64, _P, C.c_int, C.c_int, _P, C.POINTER(C.c_int)]),
+    "nc_hybrid_segments": (C.c_int, [_P, C.c_int64, _P, _P, C.c_int64, _I64P]),
+    "nc_hybrid_pack": (C.c_int, [_P, _P, C.c_int64, C.c_int, _P, C.c_size_t, _P, C.c_size_t, _P, _SZP]),
+    "nc_hybrid_parse": (C.c_int, [_P, C.c_size_t, _P, _P, C.c_int64, _I64P, C.POINTER(C.c_int), _SZP, _SZP,
+                                  _SZP]),
     "nc_ans_decode": (C.c_int, [_P, C.c_size_t, _P, C.c_int, C.c_int64, C.c_int, _P]),
     "nc_selftest_wait": (C.c_int, [_P, C.c_uint32]),
     "nc_mix_nll_fwd": (C.c_int, [_P, _P, _P, _P, _P, _P, C.c_int, C.c_int, C.c_float, _P, _P]),
@@ -210,6 +214,80 @@ def nc_split_chunks(tokens: np.ndarray, is_boundary: np.ndarray, n_chunks: int) 
     if st:
         raise NcError(st, "nc_split_chunks")
     return cuts[: m.value + 1] if m.value else cuts[:1]
+
+
+def _host_bytes(data: bytes) -> np.ndarray:
+    return np.frombuffer(data, dtype=np.uint8).copy() if len(data) else np.zeros(1, np.uint8)
+
+
+def nc_hybrid_segments(data: bytes):
+    """The text (0) / binary (1) runs of a byte string (Sec. 3.10): kinds uint8, lengths int64."""
+    buf = _host_bytes(data)
+    n = C.c_int64(0)
+    st = lib.nc_hybrid_segments(_ptr(buf), len(data), None, None, 0, C.byref(n))
+    if st:
+        raise NcError(st, "nc_hybrid_segments")
+    kinds = np.zeros(max(n.value, 1), dtype=np.uint8)
+    lens = np.zeros(max(n.value, 1), dtype=np.int64)
+    st = lib.nc_hybrid_segments(_ptr(buf), len(data), _ptr(kinds), _ptr(lens), kinds.size, C.byref(n))
+    if st:
+        raise NcError(st, "nc_hybrid_segments")
+    return kinds[: n.value], lens[: n.value]
+
+
+def nc_hybrid_pack(kinds, lens, method: int, stored: bytes, text: bytes) -> bytes:
+    """An NC06 container from its runs, the stored blob and the text runs' NC05 container."""
+    kinds = np.ascontiguousarray(kinds, dtype=np.uint8)
+    lens = np.ascontiguousarray(lens, dtype=np.int64)
+    sb, tb = _host_bytes(stored), _host_bytes(text)
+    nb = C.c_size_t(0)
+    st = lib.nc_hybrid_pack(_ptr(kinds), _ptr(lens), kinds.size, method, _ptr(sb), len(stored), _ptr(tb),
+                            len(text), None, C.byref(nb))
+    if st:
+        raise NcError(st, "nc_hybrid_pack(size)")
+    out = np.zeros(nb.value, dtype=np.uint8)
+    st = lib.nc_hybrid_pack(_ptr(kinds), _ptr(lens), kinds.size, method, _ptr(sb), len(stored), _ptr(tb),
+                            len(text), _ptr(out), C.byref(nb))
+    if st:
+        raise NcError(st, "nc_hybrid_pack")
+    return out[: nb.value].tobytes()
+
+
+def nc_hybrid_parse(data: bytes):
+    """(kinds, lens, method, stored_off, stored_len, text_off) of an NC06 container."""
+    buf = _host_bytes(data)
+    n, m = C.c_int64(0), C.c_int(0)
+    so, sl, to = C.c_size_t(0), C.c_size_t(0), C.c_size_t(0)
+    args = (C.byref(n), C.byref(m), C.byref(so), C.byref(sl), C.byref(to))
+    st = lib.nc_hybrid_parse(_ptr(buf), len(data), None, None, 0, *args)
+    if st:
+        raise NcError(st, "nc_hybrid_parse")
+    kinds = np.zeros(max(n.value, 1), dtype=np.uint8)
+    lens = np.zeros(max(n.value, 1), dtype=np.int64)
+    st = lib.nc_hybrid_parse(_ptr(buf), len(data), _ptr(kinds), _ptr(lens), kinds.size, *args)
+    if st:
+        raise NcError(st, "nc_hybrid_parse")
+    return kinds[: n.value], lens[: n.value], m.value, so.value, sl.value, to.value
+
+
+# The binary blob of an NC06 container (Sec. 3.10): LZMA from 4 KB up, gzip
+# below, stored raw when the compressed form is not shorter.
+_BLOB_RAW, _BLOB_GZIP, _BLOB_LZMA = 0, 1, 2
+
+
+def _blob_pack(blob: bytes):
+    import gzip
+    import lzma
+    if not blob:
+        return _BLOB_RAW, b""
+    m, s = (_BLOB_LZMA, lzma.compress(blob)) if len(blob) >= 4096 else (_BLOB_GZIP, gzip.compress(blob, mtime=0))
+    return (m, s) if len(s) < len(blob) else (_BLOB_RAW, blob)
+
+
+def _blob_unpack(method: int, stored: bytes) -> bytes:
+    import gzip
+    import lzma
+    return {_BLOB_RAW: lambda b: b, _BLOB_GZIP: gzip.decompress, _BLOB_LZMA: lzma.decompress}[method](stored)
 
 
 def nc_ans_encode(lo: np.ndarray, hi: np.ndarray, log2_total: int) -> bytes:
@@ -358,6 +436,40 @@ class Context:
         """Inverse of encode_file: the chunks in order, concatenated."""
         parts = self.decode(data)
         return np.concatenate(parts).astype(np.int32) if parts else np.zeros(0, np.int32)
+
+    def encode_hybrid(self, data: bytes) -> bytes:
+        """An arbitrary byte string as one NC06 container (Sec. 3.10): its
+        text runs coded as the streams of one NC05 container (one batch), its
+        binary runs as one blob.  Without the tokenizer, a text byte enters
+        the model as the token id equal to its value."""
+        kinds, lens = nc_hybrid_segments(data)
+        buf = np.frombuffer(data, dtype=np.uint8)
+        offs = np.concatenate([[0], np.cumsum(lens)]).astype(np.int64)
+        texts = [buf[offs[i]:offs[i + 1]].astype(np.int32) for i in range(kinds.size) if kinds[i] == 0]
+        blob = b"".join(data[offs[i]:offs[i + 1]] for i in range(kinds.size) if kinds[i] == 1)
+        method, stored = _blob_pack(blob)
+        return nc_hybrid_pack(kinds, lens, method, stored, self.encode(texts) if texts else b"")
+
+    def decode_hybrid(self, data: bytes) -> bytes:
+        """Inverse of encode_hybrid."""
+        kinds, lens, method, so, sl, to = nc_hybrid_parse(data)
+        blob = _blob_unpack(method, data[so:so + sl])
+        n_text = int((kinds == 0).sum())
+        texts = self.decode(data[to:]) if n_text else []
+        if len(texts) != n_text or len(blob) != int(lens[kinds == 1].sum()):
+            raise NcError(NC_ECORRUPT, "NC06 sections disagree with the run table")
+        out, ti, bo = [], 0, 0
+        for k, n in zip(kinds, lens):
+            if k == 0:
+                t = texts[ti]
+                ti += 1
+                if t.size != n:
+                    raise NcError(NC_ECORRUPT, "NC06 text run length")
+                out.append(t.astype(np.uint8).tobytes())
+            else:
+                out.append(blob[bo:bo + int(n)])
+                bo += int(n)
+        return b"".join(out)
 
     def encode_intervals(self, tokens_dev, offsets, lens, intervals_dev, stride: int, trace: bool = False):
         """Device half of encode: tokens_dev CUDA int32 (flat), offsets/lens

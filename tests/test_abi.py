@@ -160,3 +160,66 @@ def test_container_parse(nc24):
     for cut in (arr[:-1], arr[:9], np.concatenate([arr, [0]]).astype(np.uint8)):
         cut = np.ascontiguousarray(cut)
         assert nc24.lib.nc_container_streams(cut.ctypes.data, cut.size, C.byref(n)) == nc24.NC_ECORRUPT
+
+
+def _hybrid_inputs():
+    """Byte strings for the NC06 segmentation: each rule's edges, and random
+    mixes of text-like and binary runs of 1..150 bytes."""
+    t, b = b"x", b"\x00"
+    yield from (b"", t * 63, t * 64, b * 5, t * 40 + b * 8 + t * 40, t * 40 + b * 9 + t * 40,
+                b * 10 + t * 100 + b * 10, t * 100 + b * 63 + t * 100, t * 100 + b * 64 + t * 100,
+                b"\t\n\r" + t * 61, t * 32 + b"\x7f" + t * 31)
+    rng = np.random.default_rng(11)
+    text_bytes = np.r_[9, 10, 13, 32:127].astype(np.uint8)
+    bin_bytes = np.r_[0:9, 11, 12, 14:32, 127:256].astype(np.uint8)
+    for _ in range(300):
+        parts = [rng.choice(text_bytes if rng.random() < 0.5 else bin_bytes, int(rng.integers(1, 150)))
+                 for _ in range(int(rng.integers(1, 16)))]
+        yield np.concatenate(parts).tobytes()
+
+
+def test_hybrid_segments_match_oracle(nc24):
+    """NC06 segmentation (Sec. 3.10): the library's runs are the oracle's."""
+    from oracle import hybrid
+    for data in _hybrid_inputs():
+        kinds, lens = nc24.nc_hybrid_segments(data)
+        assert list(zip(kinds.tolist(), lens.tolist())) == hybrid.segment(data)
+
+
+def test_hybrid_container_matches_oracle(nc24):
+    """NC06 layout: the library's container is the oracle's byte for byte, and
+    its parse gives back the runs and sections."""
+    from oracle import hybrid
+    rng = np.random.default_rng(12)
+    text = b"NC05" + bytes([7]) + (0x3B33).to_bytes(2, "little") + bytes(rng.integers(0, 256, 40, dtype=np.uint8))
+    for data in list(_hybrid_inputs())[:60]:
+        runs = hybrid.segment(data)
+        if not runs:
+            continue
+        texts, blob = hybrid.split(data, runs)
+        method, stored = hybrid.pack_blob(blob)
+        tc = text if texts else b""
+        kinds = np.array([k for k, _ in runs], np.uint8)
+        lens = np.array([n for _, n in runs], np.int64)
+        buf = nc24.nc_hybrid_pack(kinds, lens, method, stored, tc)
+        assert buf == hybrid.pack(runs, method, stored, tc)
+        k2, l2, m2, so, sl, to = nc24.nc_hybrid_parse(buf)
+        assert list(zip(k2.tolist(), l2.tolist())) == runs and m2 == method
+        assert buf[so:so + sl] == stored and buf[to:] == tc
+
+
+def test_hybrid_rejects_bad_input(nc24):
+    good = nc24.nc_hybrid_pack(np.array([1], np.uint8), np.array([3], np.int64), 0, b"abc", b"")
+    assert nc24.nc_hybrid_parse(good)[:3][2] == 0
+    for bad in (good[:-1], b"NC07" + good[4:], good[:4] + b"\x02" + good[5:], good[:12] + b"\x02" + good[13:]):
+        with pytest.raises(nc24.NcError) as e:
+            nc24.nc_hybrid_parse(bad)
+        assert e.value.status == nc24.NC_ECORRUPT
+    with pytest.raises(nc24.NcError):
+        nc24.nc_hybrid_pack(np.array([2], np.uint8), np.array([3], np.int64), 0, b"abc", b"")      # kind
+    with pytest.raises(nc24.NcError):
+        nc24.nc_hybrid_pack(np.array([0], np.uint8), np.array([0], np.int64), 0, b"", b"")         # length 0
+    with pytest.raises(nc24.NcError):
+        nc24.nc_hybrid_pack(np.array([0], np.uint8), np.array([3], np.int64), 3, b"", b"")         # method
+    with pytest.raises(nc24.NcError):
+        nc24.nc_hybrid_pack(np.array([0], np.uint8), np.array([3], np.int64), 0, b"", b"not NC05")  # text

@@ -104,9 +104,14 @@ def test_container_round_trip():
     runs = H.segment(data)
     texts, blob = H.split(data, runs)
     m, s = H.pack_blob(blob)
-    buf = H.pack(3, 0x3C00, runs, m, s, b"NC05-stand-in")
-    assert buf[:4] == b"NC06" and buf[4] == 1 and buf[5] == 3
-    assert len(buf) == 12 + 5 * len(runs) + 5 + len(s) + len(b"NC05-stand-in")
+    text = b"NC05" + bytes([3]) + (0x3A66).to_bytes(2, "little") + b"\x02\x00rest"   # flags 3, tau 0.8
+    buf = H.pack(runs, m, s, text)
+    assert buf[:4] == b"NC06" and buf[4] == 1 and buf[5] == 3 and buf[6:8] == bytes([0x66, 0x3A])
+    assert len(buf) == 12 + 5 * len(runs) + 5 + len(s) + len(text)
     flags, tau, runs2, m2, s2, tc = H.unpack(buf)
-    assert (flags, tau, runs2, m2, s2, tc) == (3, 0x3C00, runs, m, s, b"NC05-stand-in")
+    assert (flags, tau, runs2, m2, s2, tc) == (3, 0x3A66, runs, m, s, text)
     assert H.join(runs2, texts, H.unpack_blob(m2, s2)) == data
+    # no text run: flags 0 and tau 1.0, nothing after the blob
+    runs = H.segment(bin_(20))
+    buf = H.pack(runs, H.RAW, bin_(20), b"")
+    assert H.unpack(buf) == (0, 0x3C00, [(B, 20)], H.RAW, bin_(20), b"")
