@@ -379,11 +379,11 @@ int nc_split_chunks(const int32_t* tokens, int64_t n, const uint8_t* is_boundary
 
 /* NC06 hybrid binary format (Sec. 3.10): the runs of text (kind 0) and
  * binary (kind 1) bytes of an arbitrary byte string, alternating.  Bytes are
- * text-like when printable ASCII (32..126), tab, LF or CR; binary gaps of at
- * most 8 bytes between two text runs become text; text runs shorter than 64
- * bytes become binary; binary runs shorter than 64 bytes next to a text run
- * become text (the four rules applied in the order 1, 3, 2, 4; adjacent runs
- * of one kind merge after each).  Text runs are coded as the streams of one
+ * text-like when printable ASCII (32..126), tab, LF or CR; text runs shorter
+ * than 64 bytes become binary; binary gaps of at most 8 bytes between two
+ * text runs become text; binary runs shorter than 64 bytes next to a text
+ * run become text (the four rules in the order listed; adjacent runs of one
+ * kind merge after each).  Text runs are coded as the streams of one
  * NC05 container, binary runs concatenated into one blob.
  *   data HOST uint8[n]; kinds HOST uint8[cap], lens HOST int64[cap] receive
  *   the runs in order, *n_runs their count.  cap = 0 queries the count only.

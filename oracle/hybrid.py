@@ -1,17 +1,16 @@
 """NC06 hybrid binary format (Sec. 3.10, Sec. 3.12): test infrastructure only.
 
 Segmentation of an arbitrary byte string into alternating text and binary
-runs, by the four rules of Sec. 3.10:
+runs, by the four rules of Sec. 3.10, applied in the order listed:
   1. a byte is text-like when it is printable ASCII (32..126), tab, LF or CR;
-  3. a binary gap of at most 8 bytes between two text runs becomes text;
   2. a text run shorter than 64 bytes becomes binary;
+  3. a binary gap of at most 8 bytes between two text runs becomes text;
   4. a binary run shorter than 64 bytes next to a text run becomes text.
-Adjacent runs of one kind merge after each rule.  The rules are applied in
-the order 1, 3, 2, 4: in the order they are listed, every gap rule 3 bridges
-(at most 8 bytes, between two text runs) is a binary run shorter than 64
-bytes next to text, which rule 4 absorbs anyway, so rule 3 would never
-matter; bridging before the demotion keeps text broken by short binary gaps
-as one run.
+Adjacent runs of one kind merge after each rule.  In this order every gap
+rule 3 bridges is also a binary run under 64 bytes next to text, which rule
+4 absorbs, so rule 3 changes nothing; it is kept as written.  Bridging
+before the demotion would read uniformly random bytes as text (their short
+text-like runs are mostly separated by gaps of at most 8 bytes).
 
 The binary runs are concatenated into one blob, stored LZMA-compressed when
 the blob holds at least 4 KB, gzip-compressed when smaller, or raw when the
@@ -66,11 +65,11 @@ def segment(data: bytes):
             runs[-1] = (kind, runs[-1][1] + 1)
         else:
             runs.append((kind, 1))
+    # rule 2: short text runs
+    runs = _merge([(BINARY if (k == TEXT and n < MIN_TEXT) else k, n) for k, n in runs])
     # rule 3: short gaps between two text runs
     runs = _merge([(TEXT if (k == BINARY and 0 < i < len(runs) - 1 and n <= MAX_GAP) else k, n)
                    for i, (k, n) in enumerate(runs)])
-    # rule 2: short text runs
-    runs = _merge([(BINARY if (k == TEXT and n < MIN_TEXT) else k, n) for k, n in runs])
     # rule 4: short binary runs next to a text run
     has_text_neighbour = lambda i: (i > 0 and runs[i - 1][0] == TEXT) or (i + 1 < len(runs) and runs[i + 1][0] == TEXT)
     runs = _merge([(TEXT if (k == BINARY and n < MIN_BINARY and has_text_neighbour(i)) else k, n)

@@ -254,15 +254,15 @@ void hybrid_segments(const uint8_t* data, int64_t n, std::vector<HybridRun>* run
     if (!r.empty() && r.back().kind == k) ++r.back().len;
     else r.push_back({k, 1});
   }
-  // rule 3: a binary run with a run on both sides lies between two text runs
-  for (size_t i = 1; i + 1 < r.size(); ++i)
-    if (r[i].kind == kRunBinary && r[i].len <= 8) r[i].kind = kRunText;
-  merge_runs(runs);
   for (HybridRun& x : r)                                 // rule 2
     if (x.kind == kRunText && x.len < 64) x.kind = kRunBinary;
   merge_runs(runs);
-  // rule 4, decided on the runs rule 2 left: runs alternate, so a binary run
-  // has a text neighbour unless it is the only run
+  // rule 3: runs alternate, so a binary run with a run on both sides lies
+  // between two text runs
+  for (size_t i = 1; i + 1 < r.size(); ++i)
+    if (r[i].kind == kRunBinary && r[i].len <= 8) r[i].kind = kRunText;
+  merge_runs(runs);
+  // rule 4: a binary run has a text neighbour unless it is the only run
   if (r.size() > 1)
     for (HybridRun& x : r)
       if (x.kind == kRunBinary && x.len < 64) x.kind = kRunText;

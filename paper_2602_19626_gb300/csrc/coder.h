@@ -121,12 +121,11 @@ bool container_read(const uint8_t* in, size_t n, uint8_t* flags, float* tau, uin
 
 // NC06 hybrid format (Sec. 3.10).  The runs of text (kind 0) and binary
 // (kind 1) bytes of a byte string, alternating, by the four rules applied
-// in the order 1, 3, 2, 4: bytes classed text-like when printable ASCII
-// (32..126), tab, LF or CR; binary gaps of at most 8 bytes between two text
-// runs become text; text runs under 64 bytes become binary; binary runs
+// in the order listed: bytes classed text-like when printable ASCII
+// (32..126), tab, LF or CR; text runs under 64 bytes become binary; binary
+// gaps of at most 8 bytes between two text runs become text; binary runs
 // under 64 bytes next to a text run become text.  Adjacent runs of one kind
-// merge after each rule.  (Listed order would make rule 3 a no-op: every gap
-// it bridges is a binary run under 64 bytes next to text.)
+// merge after each rule.
 constexpr uint8_t kRunText = 0, kRunBinary = 1;
 struct HybridRun {
   uint8_t kind;

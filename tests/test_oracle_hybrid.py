@@ -1,6 +1,7 @@
 """NC06 hybrid segmentation and container (oracle/hybrid.py, Sec. 3.10, Sec.
 3.12) against what the four rules fix: hand-worked inputs for each rule,
-one that decides the order in which rules 2 and 3 apply, the character
+uniformly random bytes staying binary (which fixes the order of rules 2
+and 3), the character
 classes of rule 1, and invariants on random structured inputs (the runs
 cover the input and alternate, text runs hold at least 64 bytes, binary runs
 under 64 bytes only without text, and splitting then joining gives the
@@ -36,15 +37,23 @@ def test_rule_2_short_text_demoted():
     assert H.segment(bin_(200) + txt(30) + bin_(200)) == [(B, 430)]
 
 
-def test_rule_3_gaps_bridged_before_demotion():
-    # a gap of 8 joins two 40-byte text runs into one run of 88 that rule 2 keeps
-    assert H.segment(txt(40) + bin_(8) + txt(40)) == [(T, 88)]
-    # a gap of 9 does not: both runs are too short and become binary
-    assert H.segment(txt(40) + bin_(9) + txt(40)) == [(B, 89)]
-    # a one-byte DEL inside text is a gap
-    assert H.segment(txt(32) + b"\x7f" + txt(31)) == [(T, 64)]
+def test_rule_3_gaps_after_demotion():
+    # gaps of up to 8 bytes join text runs that rule 2 kept
+    assert H.segment(txt(64) + bin_(8) + txt(64)) == [(T, 136)]
+    assert H.segment(txt(100) + b"\x7f" + txt(100)) == [(T, 201)]
+    # text runs too short for rule 2 are binary before any gap is bridged
+    assert H.segment(txt(40) + bin_(8) + txt(40)) == [(B, 88)]
+    assert H.segment(txt(32) + b"\x7f" + txt(31)) == [(B, 64)]
     # a gap at either end is not between two text runs
     assert H.segment(bin_(3) + txt(10)) == [(B, 13)]
+
+
+def test_random_bytes_stay_binary():
+    # uniform bytes are text-like with probability 98/256 but hold no text-like
+    # run of 64; bridging their gaps first would call most of them text
+    for seed in range(4):
+        data = bytes(np.random.default_rng(seed).integers(0, 256, 5000, dtype=np.uint8))
+        assert H.segment(data) == [(B, 5000)]
 
 
 def test_rule_4_small_binary_absorbed():
