@@ -91,6 +91,13 @@ PLAIN = "full_fp32_single"
 BATCHED = ("batched_bf16_tc", "fp8_tc_1024x1024")
 
 
+# Kernels of one decode step on the tensor-core path with BF16 weights: the
+# embedding; per layer the RMSNorm operand, QKV, attention (with the append),
+# O, RMSNorm operand, gate/up and down; the final RMSNorm operand, the LM
+# head; the vocabulary step and the coder's device search.
+DECODE_STEP_LAUNCHES = 1 + 7 * 30 + 2 + 2
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -518,6 +525,12 @@ def run_gpu(args, wl):
         dec_s = time.perf_counter() - t0
         decode = {"value": n_tok / dec_s, "unit": "tokens/s", "s": dec_s,
                   "lossless": bool(all(np.array_equal(a, b) for a, b in zip(back, host_streams)))}
+        # the floor of the decode step's chain of dependent launches: a
+        # captured graph of empty kernels, one per kernel of a step
+        links = DECODE_STEP_LAUNCHES
+        us = nc24.nc_launch_chain_floor(dev, links, 152, 256, 20)
+        decode["launch_chain_floor"] = {"links": links, "us_per_link": us, "us_per_step": us * links,
+                                        "blocks": 152, "threads": 256}
     if ws > 1:
         t = torch.tensor([e2e_s], device=f"cuda:{dev}", dtype=torch.float64)
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)

@@ -329,6 +329,17 @@ int nc_gemm_tc(const void* W, const void* X, const float* w_scale, const float* 
  * The paper has no counterpart.  Errors: NC_EINVAL, NC_ESTATE, NC_ECUDA. */
 int nc_selftest_wait(nc_ctx* ctx, uint32_t polls);
 
+/* Diagnostic of the latency floor of the decode step's chain of dependent
+ * kernels: a captured CUDA graph of n_links empty kernels of blocks x
+ * threads, each launched with programmatic dependent launch and waiting for
+ * its predecessor as the step's kernels do, replayed 3 times untimed and
+ * `reps` times between CUDA events on device `device`.  *us_per_link (HOST)
+ * receives the device time per link in microseconds.  No device memory is
+ * allocated.  The paper has no counterpart.
+ * Errors: NC_EINVAL (n_links outside 1..4096, blocks outside 1..65535,
+ * threads not a multiple of 32 in 32..1024, reps < 1, NULL output), NC_ECUDA. */
+int nc_launch_chain_floor(int device, int n_links, int blocks, int threads, int reps, float* us_per_link);
+
 /* 32-bit arithmetic coder (Sec. 3.8) on the host, for callers that produce
  * their own CDFs.  Encode n intervals [lo[i], hi[i]) of a total 2^log2_total
  * (HOST uint32 arrays) into out (HOST, capacity *inout_nbytes; size and the

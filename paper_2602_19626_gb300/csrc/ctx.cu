@@ -2108,6 +2108,43 @@ extern "C" int nc_selftest_wait(nc_ctx* ctx, uint32_t polls) {
   return NC_OK;
 }
 
+extern "C" int nc_launch_chain_floor(int device, int n_links, int blocks, int threads, int reps,
+                                    float* us_per_link) {
+  if (n_links < 1 || n_links > 4096 || blocks < 1 || blocks > 65535 || threads < 32 || threads > 1024 ||
+      threads % 32 || reps < 1 || !us_per_link)
+    return NC_EINVAL;
+  if (cudaSetDevice(device) != cudaSuccess) return NC_ECUDA;
+  cudaStream_t s = nullptr;
+  cudaGraph_t g = nullptr;
+  cudaGraphExec_t ge = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  if (e == cudaSuccess) e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    cudaError_t el = cudaSuccess;
+    for (int i = 0; i < n_links && el == cudaSuccess; ++i) el = launch_chain_link(dim3(blocks), dim3(threads), s);
+    e = cudaStreamEndCapture(s, &g);
+    if (el != cudaSuccess) e = el;
+  }
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&ge, g, 0);
+  for (int i = 0; i < 3 && e == cudaSuccess; ++i) e = cudaGraphLaunch(ge, s);   // warm-up
+  if (e == cudaSuccess) e = cudaEventRecord(e0, s);
+  for (int i = 0; i < reps && e == cudaSuccess; ++i) e = cudaGraphLaunch(ge, s);
+  if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+  if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+  float ms = 0.f;
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+  if (e == cudaSuccess) *us_per_link = ms * 1000.f / ((float)reps * (float)n_links);
+  if (ge) cudaGraphExecDestroy(ge);
+  if (g) cudaGraphDestroy(g);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (s) cudaStreamDestroy(s);
+  return e == cudaSuccess ? NC_OK : NC_ECUDA;
+}
+
 extern "C" int nc_probs_to_cdf(const float* p, int n, int V, int log2_total, uint32_t floor_c, uint32_t* cdf,
                                void* stream) {
   if (!p || !cdf || n < 1 || V < 2 || V > 65535 || log2_total < 1 || log2_total > 24 || floor_c < 1 ||

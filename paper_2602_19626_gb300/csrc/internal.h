@@ -323,6 +323,7 @@ cudaError_t launch_gemm_tc(const TcGemm& g, int epi, cudaStream_t s, bool pdl);
 // One bounded mbarrier wait on a barrier nothing arrives on (at most `polls`
 // polls), recording ST_TIMEOUT in *status when it gives up.
 cudaError_t launch_wait_selftest(uint32_t polls, int32_t* status, cudaStream_t s);
+cudaError_t launch_chain_link(dim3 grid, dim3 block, cudaStream_t s);
 cudaError_t launch_act_rmsnorm(const Dims& D, const Batch& b, const float* x, const float* gain, int cols,
                                int kind_bf16, void* out, float* out_scale, cudaStream_t s);
 cudaError_t launch_act_plain(const Dims& D, const Batch& b, const float* x, int cols, int kind_bf16, void* out,

@@ -405,6 +405,18 @@ __global__ void k_interleave(const float* gate, const float* up, float* dst, int
 }  // namespace
 
 
+// One link of an empty chain of dependent launches: it waits for its
+// predecessor and lets its successor launch, as the decode step's kernels do
+// around their work.
+__global__ void k_chain_link() {
+  pdl_wait();
+  pdl_trigger();
+}
+
+cudaError_t launch_chain_link(dim3 grid, dim3 block, cudaStream_t s) {
+  return launch_kernel(k_chain_link, grid, block, 0, s, true);
+}
+
 cudaError_t launch_embed(const Dims& D, const Batch& b, const void* E, const float* Escale,
                          int fmt, float* x, cudaStream_t s) {
   const int thr = 256;

@@ -95,6 +95,7 @@ _SIGS = {
                                   _SZP]),
     "nc_ans_decode": (C.c_int, [_P, C.c_size_t, _P, C.c_int, C.c_int64, C.c_int, _P]),
     "nc_selftest_wait": (C.c_int, [_P, C.c_uint32]),
+    "nc_launch_chain_floor": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, _F32P]),
     "nc_mix_nll_fwd": (C.c_int, [_P, _P, _P, _P, _P, _P, C.c_int, C.c_int, C.c_float, _P, _P]),
     "nc_mix_nll_bwd": (C.c_int, [_P, _P, _P, _P, _P, _P, _P, C.c_int, C.c_int, C.c_float, _P, _P, _P]),
 }
@@ -214,6 +215,16 @@ def nc_split_chunks(tokens: np.ndarray, is_boundary: np.ndarray, n_chunks: int) 
     if st:
         raise NcError(st, "nc_split_chunks")
     return cuts[: m.value + 1] if m.value else cuts[:1]
+
+
+def nc_launch_chain_floor(device: int, n_links: int, blocks: int = 152, threads: int = 256,
+                          reps: int = 20) -> float:
+    """Microseconds per link of a graph-captured chain of empty dependent launches."""
+    us = C.c_float(0.0)
+    st = lib.nc_launch_chain_floor(device, n_links, blocks, threads, reps, C.byref(us))
+    if st:
+        raise NcError(st, "nc_launch_chain_floor")
+    return us.value
 
 
 def _host_bytes(data: bytes) -> np.ndarray:

@@ -223,3 +223,12 @@ def test_hybrid_rejects_bad_input(nc24):
         nc24.nc_hybrid_pack(np.array([0], np.uint8), np.array([3], np.int64), 3, b"", b"")         # method
     with pytest.raises(nc24.NcError):
         nc24.nc_hybrid_pack(np.array([0], np.uint8), np.array([3], np.int64), 0, b"", b"not NC05")  # text
+
+
+def test_launch_chain_floor_rejects_bad_arguments(nc24):
+    """The launch-floor diagnostic checks its arguments before touching a device."""
+    for args in ((0, 0, 152, 256, 1), (0, 16, 0, 256, 1), (0, 16, 152, 33, 1), (0, 16, 152, 256, 0),
+                 (0, 5000, 152, 256, 1)):
+        with pytest.raises(nc24.NcError) as e:
+            nc24.nc_launch_chain_floor(*args)
+        assert e.value.status == nc24.NC_EINVAL
