@@ -8,8 +8,9 @@
 // symbols.  The standalone quantiser reduces thread -> warp (fixed xor tree)
 // -> CTA (warps in order) -> cluster (ranks in order through distributed
 // shared memory); the per-token step goes thread -> warp -> every CTA's inbox
-// (one cluster barrier) -> the same fixed reduction in every warp.  Every
-// result is independent of the batch, the slot and the launch.
+// (one cluster barrier in the step kernel, one exchange round on each CTA's
+// mbarrier in the prefill loop) -> the same fixed reduction in every warp.
+// Every result is independent of the batch, the slot and the launch.
 #include <algorithm>
 
 #include <cooperative_groups.h>
@@ -297,12 +298,12 @@ __device__ void scan_round(const uint32_t (&c)[E], int v0, int V, uint32_t T, ui
 // of 4,096 / CL threads (CL = 8 or 16): always 128 warps, global warp
 // gw = rank (128 / CL) + w owning the 32 E symbols from wbase = 32 E gw, lane
 // l the E symbols from v0 = wbase + E l.  A reduction over the vocabulary
-// takes one cluster barrier: every warp publishes its partials in a slot of
-// its CTA's shared memory, and after the barrier every warp reads all 128 of
-// them (lane l the four of global warps 4l .. 4l + 3) and reduces them with
-// the same shuffles, so every warp of the cluster holds the same result,
-// whatever the batch, the slot, the launch or the cluster shape.  The
-// arithmetic is written with explicitly rounded operations and fixed
+// takes one exchange: every warp sends its partials into every CTA's inbox,
+// and once they are all there every warp reads the 128 of them from its own
+// CTA's shared memory (lane l the four of global warps 4l .. 4l + 3) and
+// reduces them with the same shuffles, so every warp of the cluster holds
+// the same result, whatever the batch, the slot, the launch or the cluster
+// shape.  The arithmetic is written with explicitly rounded operations and fixed
 // approximations, so the single-step and the multi-position kernels below
 // compute the same bits.  FULL: the vocabulary fills the cluster's 4,096 E
 // symbols exactly (no symbol past V, every run 16-byte aligned).
@@ -325,15 +326,12 @@ __device__ __forceinline__ float ex2_approx(float x) {
 // e^x = 2^(x log2 e) for the few scalar exponentials of a step.
 __device__ __forceinline__ float exp_fast(float x) { return ex2_approx(__fmul_rn(x, kLog2e)); }
 
-__device__ __forceinline__ void cluster_arrive() {
-  asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
-}
-__device__ __forceinline__ void cluster_wait() { asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory"); }
-
-// Every CTA's inbox for one cluster barrier (two alternate): each warp of
-// the cluster stores its partials at its global index gw in every CTA's inbox before the barrier (posted remote stores, made visible by
-// the barrier's release), so after it every warp reduces them from its own
-// CTA's shared memory.
+// Every CTA's inbox for one exchange (two alternate): each warp of the
+// cluster stores its partials at its global index gw in every CTA's inbox,
+// as posted remote stores made visible by a cluster barrier's release (the
+// step kernel) or as asynchronous remote stores that complete their bytes on
+// the receiving CTA's mbarrier (the prefill loop), so that afterwards every
+// warp reduces them from its own CTA's shared memory.
 struct StepSlot {
   float4 sm[kClusterWarps];   // softmax: warp maximum m_w, sum of exp(s - m_w), entropy part
   uint4 qn[kClusterWarps];    // quantiser: count sum, first maximum (value bits, index), bad flag
@@ -981,10 +979,10 @@ __global__ void __launch_bounds__(step_threads<CL>(), 1) k_vocab(Dims D, Batch b
 // kept on chip and the N-gram state of each prediction read from snap (made
 // ahead by k_ngram_seq).  Under the log-loss mixer the head's step does not
 // wait for the mixer, so position r's quantiser and mixer results share the
-// cluster barrier of position r + 1's softmax: one barrier per position.
-// The next position's logits, token and activity and the N-gram state two
-// positions ahead are fetched between the barrier's arrive and wait, so the
-// barrier's release never waits for them.
+// exchange round of position r + 1's softmax: one round per position, with
+// no cluster barrier (each CTA waits on its own mbarrier for the round's
+// bytes).  The next position's logits, token and activity and the N-gram
+// state two positions ahead are fetched while the round's values travel.
 template <int E, bool FULL, int CL>
 __global__ void __launch_bounds__(step_threads<CL>(), 1)
     k_vocab_seq(Dims D, Batch b, VocabIO io, int m, int n_streams, const float* zrows, const int32_t* nb_step,
