@@ -452,7 +452,8 @@ class Context:
         """An arbitrary byte string as one NC06 container (Sec. 3.10): its
         text runs coded as the streams of one NC05 container (one batch), its
         binary runs as one blob.  Without the tokenizer, a text byte enters
-        the model as the token id equal to its value."""
+        the model as the token id equal to its value.  The context's
+        max_streams bounds the number of text runs of one file."""
         kinds, lens = nc_hybrid_segments(data)
         buf = np.frombuffer(data, dtype=np.uint8)
         offs = np.concatenate([[0], np.cumsum(lens)]).astype(np.int64)
