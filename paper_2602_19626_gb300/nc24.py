@@ -298,7 +298,11 @@ def _blob_pack(blob: bytes):
 def _blob_unpack(method: int, stored: bytes) -> bytes:
     import gzip
     import lzma
-    return {_BLOB_RAW: lambda b: b, _BLOB_GZIP: gzip.decompress, _BLOB_LZMA: lzma.decompress}[method](stored)
+    import zlib
+    try:
+        return {_BLOB_RAW: lambda b: b, _BLOB_GZIP: gzip.decompress, _BLOB_LZMA: lzma.decompress}[method](stored)
+    except (OSError, EOFError, lzma.LZMAError, zlib.error) as exc:
+        raise NcError(NC_ECORRUPT, f"NC06 binary section: {exc}") from exc
 
 
 def nc_ans_encode(lo: np.ndarray, hi: np.ndarray, log2_total: int) -> bytes:

@@ -232,3 +232,13 @@ def test_launch_chain_floor_rejects_bad_arguments(nc24):
         with pytest.raises(nc24.NcError) as e:
             nc24.nc_launch_chain_floor(*args)
         assert e.value.status == nc24.NC_EINVAL
+
+
+def test_hybrid_blob_errors_are_corrupt_containers(nc24):
+    """A damaged compressed binary section reads as a corrupt container."""
+    import gzip
+    for method, stored in ((1, b"not gzip"), (2, b"not xz"), (1, gzip.compress(b"abc")[:-3])):
+        with pytest.raises(nc24.NcError) as e:
+            nc24._blob_unpack(method, stored)
+        assert e.value.status == nc24.NC_ECORRUPT
+    assert nc24._blob_unpack(*nc24._blob_pack(b"y" * 5000)) == b"y" * 5000
